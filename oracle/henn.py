@@ -1,0 +1,444 @@
+"""Encrypted layers under the fragment encoding: HE convolution (Sec. 3, Eq. 2
+with inner and outer rotations), x^2 activation, 2x2 average pooling, fully
+connected layers, Arch-aware Ciphertext Compression (AAC), and the LeNet-shaped
+network built from them.
+
+Test infrastructure only (see oracle/__init__.py).
+
+HE convolution (the algorithm, in the order it is evaluated here):
+ 1. Inner rotations (spatial dependency, Sec. 3 "inner rotations", Eq. 3):
+    output pixel (h, w) = (bi S + u', bj S + v') sits in the slot of input pixel
+    (h, w).  Tap (i, j) reads input pixel (h + i, w + j), which lives in input
+    fragment u = (u' + i) mod S at block row bi + a, a = (u' + i) div S (same for
+    columns).  Every input ciphertext is therefore rotated by
+    r = (a m + b) BS for each needed block offset (a, b) != (0, 0); the ModUp of
+    its c1 is computed once and shared by all of its rotations (hoisting).
+ 2. PMult-MAC over fragment masks (Fig. 2): for output ciphertext (group h,
+    fragment (u', v')) and diagonal d, P_d = sum_g sum_taps R ⊙ pt, where pt
+    holds W[o][c][i][j] in the slots of input channel position c_loc for output
+    channel position o_loc = (c_loc - d) mod cpc, and zero at every output
+    position that is not a valid output of the (strided) valid convolution.
+ 3. Outer rotations (channel dependency, Eq. 4): out = P_0 + sum_{d != 0}
+    Rot(P_d, d m^2 BS), before any rescale; all-zero diagonals are skipped.
+ 4. One rescale.
+Weights are encoded at scale q_level by default, so the output scale equals the
+input scale.  Stride 2 keeps the output fragments with even (u', v') and halves S
+(Sec. 4 implementation paragraph: stride by discarding ciphertexts).
+"""
+import math
+
+import numpy as np
+
+from . import _core as C
+from . import ckks
+from . import counts
+from .fragment import Layout
+
+
+class Counters:
+    def __init__(self):
+        self.rot = 0
+        self.keyswitch = 0
+        self.pmult = 0
+        self.cmult = 0
+        self.rescale = 0
+        self.modup = 0
+
+    def as_dict(self):
+        return dict(self.__dict__)
+
+
+def _add(pr, acc, x):
+    if acc is None:
+        return x.copy()
+    return ckks.add(pr, acc, x)
+
+
+def out_layout_conv(lay, Cout, K, stride):
+    if lay.S % stride and lay.S != 1:
+        raise ValueError("stride must divide S")
+    if stride != 1 and lay.S == 1:
+        raise ValueError("stride > 1 needs S >= 2 (stride by discarding fragments)")
+    Ho = (lay.H - K) // stride + 1
+    Wo = (lay.W - K) // stride + 1
+    return Layout(lay.N, Ho, Wo, Cout, lay.BS, lay.S // stride, m=lay.m)
+
+
+def conv_diagonals(lay, Cin, Cout, h, depthwise, in_period):
+    cpc = lay.cpc
+    if depthwise:
+        return [0]
+    if in_period is not None:
+        return list(range(in_period))
+    ds = set()
+    for c in range(Cin):
+        for o_loc in range(cpc):
+            if h * cpc + o_loc < Cout:
+                ds.add(((c % cpc) - o_loc) % cpc)
+    return sorted(ds)
+
+
+def conv_rotation_steps(lay, Cin, Cout, K, stride=1, depthwise=False, in_period=None):
+    offs = counts.inner_offsets(lay.S, K, stride)
+    steps = set()
+    for u in range(lay.S):
+        for v in range(lay.S):
+            for a in offs[u]:
+                for b in offs[v]:
+                    if (a, b) != (0, 0):
+                        steps.add((a * lay.m + b) * lay.BS)
+    G_out = lay.groups if depthwise else -(-Cout // lay.cpc)
+    for h in range(G_out):
+        for d in conv_diagonals(lay, Cin, Cout, h, depthwise, in_period):
+            if d:
+                steps.add(d * lay.blk)
+    return sorted(steps)
+
+
+def conv_weight_slots(lay, W, h, up, vp, d, g, i, j, *, stride, depthwise, in_period, wmul, Cout):
+    """Slot vector of the plaintext for output (group h, fragment (up, vp)),
+    diagonal d, input group g, tap (i, j)."""
+    K = W.shape[-1]
+    Cin = W.shape[1] if not depthwise else W.shape[0]
+    z = np.zeros(lay.N // 2, dtype=np.float64)
+    cpc = lay.cpc
+    for c_loc in range(cpc):
+        if in_period is not None:
+            c = c_loc % in_period
+        else:
+            c = g * cpc + c_loc
+            if c >= Cin:
+                continue
+        o_loc = (c_loc - d) % cpc
+        o = h * cpc + o_loc
+        if o >= Cout:
+            continue
+        if depthwise:
+            if o != c:
+                continue
+            wv = W[c, 0, i, j]
+        else:
+            wv = W[o, c, i, j]
+        wv = wv * wmul
+        for bi in range(lay.m):
+            hp = bi * lay.S + up
+            if hp > lay.H - K:
+                break
+            if hp % stride:
+                continue
+            for bj in range(lay.m):
+                wp = bj * lay.S + vp
+                if wp > lay.W - K:
+                    break
+                if wp % stride:
+                    continue
+                base = lay.slot(c_loc, bi, bj, 0)
+                z[base:base + lay.BS] = wv
+    return z
+
+
+def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None, wmul=1.0,
+            w_scale=None, cnt=None):
+    """Encrypted convolution of the fragment-packed input `cts` (list in (g, u, v)
+    order).  Returns (output ciphertexts in (h, u'', v'') order, output layout)."""
+    cnt = cnt if cnt is not None else Counters()
+    level = cts[0].level
+    Cout = W.shape[0]
+    Cin = W.shape[0] if depthwise else W.shape[1]
+    K = W.shape[-1]
+    olay = out_layout_conv(lay, Cout, K, stride)
+    S, m, BS = lay.S, lay.m, lay.BS
+    dw = float(pr.moduli[level]) if w_scale is None else w_scale
+    G_in = 1 if in_period is not None else lay.groups
+    G_out = olay.groups
+
+    # 1. inner rotations, hoisted per input ciphertext
+    offs = counts.inner_offsets(S, K, stride)
+    R = {}
+    for g in range(G_in):
+        for u in range(S):
+            for v in range(S):
+                ct = cts[lay.ct_index(g, u, v)]
+                pairs = [(a, b) for a in offs[u] for b in offs[v]]
+                if any(p != (0, 0) for p in pairs):
+                    ext = ckks.mod_up(pr, ct.c1, ct.level)
+                    cnt.modup += 1
+                for (a, b) in pairs:
+                    if (a, b) == (0, 0):
+                        R[(g, u, v, a, b)] = ct
+                    else:
+                        R[(g, u, v, a, b)] = ckks.rotate_ext(pr, keys, ct, ext, (a * m + b) * BS)
+                        cnt.rot += 1
+                        cnt.keyswitch += 1
+
+    # 2-4. MAC per diagonal, outer rotations, rescale
+    out = [None] * olay.n_ct
+    for h in range(G_out):
+        diags = conv_diagonals(lay, Cin, Cout, h, depthwise, in_period)
+        for up in range(0, S, stride):
+            for vp in range(0, S, stride):
+                total = None
+                for d in diags:
+                    acc = None
+                    for g in range(G_in):
+                        for i in range(K):
+                            u, a = (up + i) % S, (up + i) // S
+                            for j in range(K):
+                                v, b = (vp + j) % S, (vp + j) // S
+                                z = conv_weight_slots(lay, W, h, up, vp, d, g, i, j, stride=stride,
+                                                      depthwise=depthwise, in_period=in_period,
+                                                      wmul=wmul, Cout=Cout)
+                                if not z.any():
+                                    continue
+                                pt = ckks.encode(pr, z, level, dw)
+                                acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b)], pt))
+                                cnt.pmult += 1
+                    if acc is None:
+                        continue
+                    if d:
+                        acc = ckks.rotate(pr, keys, acc, d * lay.blk)
+                        cnt.rot += 1
+                        cnt.keyswitch += 1
+                        cnt.modup += 1
+                    total = _add(pr, total, acc)
+                res = ckks.rescale(pr, total)
+                cnt.rescale += 1
+                out[olay.ct_index(h, up // stride, vp // stride)] = res
+    return out, olay
+
+
+def he_square(pr, keys, cts, cnt=None):
+    """x^2 activation: CMult with relinearisation, then rescale."""
+    cnt = cnt if cnt is not None else Counters()
+    out = []
+    for ct in cts:
+        out.append(ckks.rescale(pr, ckks.cmult_relin(pr, keys, ct, ct)))
+        cnt.cmult += 1
+        cnt.keyswitch += 1
+        cnt.modup += 1
+        cnt.rescale += 1
+    return out
+
+
+def he_avgpool2(pr, cts, lay):
+    """2x2 average pooling by summing fragment ciphertexts (S even): output fragment
+    (u'', v'') = sum of input fragments (2u''+di, 2v''+dj).  The 1/4 is left to the
+    next linear layer (its weights are multiplied by 1/4)."""
+    if lay.S % 2:
+        raise ValueError("pooling by fragment sums needs an even S")
+    olay = Layout(lay.N, lay.H // 2, lay.W // 2, lay.C, lay.BS, lay.S // 2, m=lay.m)
+    out = []
+    for g in range(lay.groups):
+        for u in range(olay.S):
+            for v in range(olay.S):
+                acc = None
+                for di in range(2):
+                    for dj in range(2):
+                        acc = _add(pr, acc, cts[lay.ct_index(g, 2 * u + di, 2 * v + dj)])
+                out.append(acc)
+    return out, olay
+
+
+def aac_compress(pr, keys, cts, lay, c_valid, cnt=None):
+    """Arch-aware Ciphertext Compression: a ciphertext whose first c_valid channel
+    positions are valid and the rest empty is filled by rotate-and-add doubling,
+    ct <- ct + Rot(ct, -s m^2 BS) for s = c_valid, 2 c_valid, ..., cpc/2, so that
+    position c_loc holds channel c_loc mod c_valid (Fig. 6).  No plaintext mask is
+    needed because the empty positions hold zeros (the preceding layer's weight
+    plaintexts are zero there, which merges the mask into those weights at their
+    single scale).  Consumes no level."""
+    cnt = cnt if cnt is not None else Counters()
+    if lay.cpc % c_valid:
+        raise ValueError("c_valid must divide cpc")
+    out = []
+    for ct in cts:
+        acc = ct.copy()
+        s = c_valid
+        while s < lay.cpc:
+            acc = ckks.add(pr, acc, ckks.rotate(pr, keys, acc, -s * lay.blk))
+            cnt.rot += 1
+            cnt.keyswitch += 1
+            cnt.modup += 1
+            s *= 2
+        out.append(acc)
+    return out
+
+
+def aac_rotation_steps(lay, c_valid):
+    steps = []
+    s = c_valid
+    while s < lay.cpc:
+        steps.append(-s * lay.blk)
+        s *= 2
+    return steps
+
+
+# ---------------------------------------------------------------------------
+# Fully connected layers: diagonal method with baby-step / giant-step over the
+# P = cpc m^2 block positions of a ciphertext (rotation by one position is a
+# rotation by BS slots).
+# ---------------------------------------------------------------------------
+
+def fc_bsgs_split(P):
+    k = P.bit_length() - 1
+    n1 = 1 << ((k + 1) // 2)
+    return n1, P // n1
+
+
+def fc_rotation_steps(P, BS):
+    n1, n2 = fc_bsgs_split(P)
+    return sorted({b * BS for b in range(1, n1)} | {n1 * g * BS for g in range(1, n2)})
+
+
+def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None):
+    """y = Wfc x.  cts: input ciphertexts; feat_of(c, p) -> feature index or -1 for
+    position p of input ciphertext c.  Output neuron n sits in ciphertext n // P at
+    position n % P (for every batch slot)."""
+    cnt = cnt if cnt is not None else Counters()
+    level = cts[0].level
+    dw = float(pr.moduli[level]) if w_scale is None else w_scale
+    F_out = Wfc.shape[0]
+    T = -(-F_out // P)
+    n1, n2 = fc_bsgs_split(P)
+
+    def diag(t, c, delta):
+        z = np.zeros(P)
+        for p in range(P):
+            n = t * P + p
+            f = feat_of(c, (p + delta) % P)
+            if n < F_out and f >= 0:
+                z[p] = Wfc[n, f]
+        return z
+
+    # plaintext diagonals, rotated for the giant steps
+    pts = {}
+    for t in range(T):
+        for c in range(len(cts)):
+            for gam in range(n2):
+                for beta in range(n1):
+                    dz = diag(t, c, n1 * gam + beta)
+                    dz = np.roll(dz, n1 * gam)  # dz'[p] = diag[(p - n1 gam) mod P]
+                    if dz.any():
+                        pts[(t, c, gam, beta)] = np.repeat(dz, BS)
+    # baby steps, hoisted per input ciphertext
+    baby = {}
+    for c, ct in enumerate(cts):
+        need = sorted({k[3] for k in pts if k[1] == c})
+        ext = None
+        for beta in need:
+            if beta == 0:
+                baby[(c, 0)] = ct
+            else:
+                if ext is None:
+                    ext = ckks.mod_up(pr, ct.c1, ct.level)
+                    cnt.modup += 1
+                baby[(c, beta)] = ckks.rotate_ext(pr, keys, ct, ext, beta * BS)
+                cnt.rot += 1
+                cnt.keyswitch += 1
+    out = []
+    for t in range(T):
+        total = None
+        for gam in range(n2):
+            acc = None
+            for c in range(len(cts)):
+                for beta in range(n1):
+                    key = (t, c, gam, beta)
+                    if key not in pts:
+                        continue
+                    pt = ckks.encode(pr, pts[key], level, dw)
+                    acc = _add(pr, acc, ckks.pmult(pr, baby[(c, beta)], pt))
+                    cnt.pmult += 1
+            if acc is None:
+                continue
+            if gam:
+                acc = ckks.rotate(pr, keys, acc, n1 * gam * BS)
+                cnt.rot += 1
+                cnt.keyswitch += 1
+                cnt.modup += 1
+            total = _add(pr, total, acc)
+        out.append(ckks.rescale(pr, total))
+        cnt.rescale += 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Scale rule for a chain of layers and the LeNet-shaped network
+# ---------------------------------------------------------------------------
+
+def weight_scale(pr, level, s_in, delta, square_follows):
+    """Scale at which a linear layer at `level` encodes its weights: the output
+    scale after its rescale is delta, or sqrt(delta q_{level-1}) when an x^2
+    activation follows (so that the activation's rescale lands back near delta).
+    Evaluated as written, in IEEE double arithmetic."""
+    t = math.sqrt(delta * float(pr.moduli[level - 1])) if square_follows else delta
+    return (t / s_in) * float(pr.moduli[level])
+
+
+def lenet_layouts(N, BS, S=4):
+    l0 = Layout(N, 28, 28, 1, BS, S)
+    return l0
+
+
+def lenet_rotation_steps(N, BS, S=4):
+    """Every rotation step the LeNet-shaped network uses (for key generation)."""
+    l0 = lenet_layouts(N, BS, S)
+    steps = set(conv_rotation_steps(l0, 1, 6, 5))
+    l1 = out_layout_conv(l0, 6, 5, 1)
+    l1p = Layout(N, l1.H // 2, l1.W // 2, 6, BS, l1.S // 2, m=l1.m)
+    steps |= set(conv_rotation_steps(l1p, 6, 16, 5))
+    P = l1p.cpc * l1p.m * l1p.m
+    steps |= set(fc_rotation_steps(P, BS))
+    return sorted(steps)
+
+
+def he_lenet(pr, keys, cts, lay, weights, delta, cnt=None):
+    """conv5x5 1->6, x^2, avgpool2, conv5x5 6->16, x^2, avgpool2, FC 256->120->84->10.
+    Returns the output ciphertexts (neuron n at position n of the FC layout)."""
+    cnt = cnt if cnt is not None else Counters()
+    lv = cts[0].level
+    h, l1 = he_conv(pr, keys, cts, lay, weights["conv1"],
+                    w_scale=weight_scale(pr, lv, cts[0].scale, delta, True), cnt=cnt)
+    h = he_square(pr, keys, h, cnt)
+    h, l1 = he_avgpool2(pr, h, l1)
+    lv = h[0].level
+    h, l2 = he_conv(pr, keys, h, l1, weights["conv2"], wmul=0.25,
+                    w_scale=weight_scale(pr, lv, h[0].scale, delta, True), cnt=cnt)
+    h = he_square(pr, keys, h, cnt)
+    h, l2 = he_avgpool2(pr, h, l2)
+    assert l2.S == 1
+    P = l2.cpc * l2.m * l2.m
+    m = l2.m
+
+    def feat_conv(c_ct, p):
+        c_loc, k = divmod(p, m * m)
+        c = c_ct * l2.cpc + c_loc
+        bi, bj = divmod(k, m)
+        if c >= l2.C or bi >= l2.H or bj >= l2.W:
+            return -1
+        return (c * l2.H + bi) * l2.W + bj
+
+    BS = l2.BS
+    Wf1 = weights["fc1"] * 0.25
+    lv = h[0].level
+    h = he_fc(pr, keys, h, feat_conv, P, BS, Wf1,
+              w_scale=weight_scale(pr, lv, h[0].scale, delta, False), cnt=cnt)
+    for name in ("fc2", "fc3"):
+        F_in = weights[name].shape[1]
+
+        def feat_fc(c_ct, p, F_in=F_in):
+            f = c_ct * P + p
+            return f if f < F_in else -1
+
+        lv = h[0].level
+        h = he_fc(pr, keys, h, feat_fc, P, BS, weights[name],
+                  w_scale=weight_scale(pr, lv, h[0].scale, delta, False), cnt=cnt)
+    return h, P
+
+
+def lenet_decode_logits(slots_list, P, BS, n_out=10):
+    """Read the FC output layout back: logits[b, n] = slot (n mod P) * BS + b of ct n // P."""
+    y = np.zeros((BS, n_out))
+    for n in range(n_out):
+        t, p = divmod(n, P)
+        y[:, n] = slots_list[t][p * BS:(p + 1) * BS]
+    return y

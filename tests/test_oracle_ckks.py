@@ -1,0 +1,160 @@
+"""Pins of the oracle's RNS-CKKS operations: exact CRT identities for the base
+conversions, ModDown and rescale (checked with Python big integers), and
+decryption identities for key switching and rotation (Eq. 1)."""
+from math import prod
+
+import numpy as np
+import pytest
+
+from oracle import _core as C
+from oracle import ckks
+
+
+def crt(residues, moduli):
+    """Centred integer from residues (Python ints)."""
+    Q = prod(moduli)
+    x = 0
+    for r, q in zip(residues, moduli):
+        Qh = Q // q
+        x += int(r) * Qh * pow(Qh % q, -1, q)
+    x %= Q
+    return x - Q if x > Q // 2 else x
+
+
+@pytest.fixture(scope="module")
+def pr():
+    return ckks.Params(5, 5, 2, 36)
+
+
+def test_centred_bconv_identity(pr):
+    rng = np.random.default_rng(0)
+    src = [1, 2]
+    coef = [rng.integers(0, pr.moduli[i], pr.N, dtype=np.uint64) for i in src]
+    dst = [0, 3, 4, pr.p_index(0), pr.p_index(1)]
+    out = ckks.centred_bconv(pr, coef, src, dst)
+    B = prod(pr.moduli[i] for i in src)
+    for n in range(pr.N):
+        x = crt([coef[0][n], coef[1][n]], [pr.moduli[i] for i in src])
+        Y = 0
+        for pos, i in enumerate(src):
+            bi = pr.moduli[i]
+            yi = int(coef[pos][n]) * pow((B // bi) % bi, -1, bi) % bi
+            yi = yi - bi if yi > bi // 2 else yi
+            Y += yi * (B // bi)
+        assert (Y - x) % B == 0 and abs((Y - x) // B) <= 1
+        for t in dst:
+            assert int(out[t][n]) == Y % pr.moduli[t]
+
+
+def test_mod_down_is_rounded_division(pr):
+    """ModDown(x) = (x - Y) / P with Y = centred conversion of [x]_P (an exact integer identity)."""
+    rng = np.random.default_rng(1)
+    level = 3
+    limbs = pr.ks_limbs(level)
+    xc = {t: rng.integers(0, pr.moduli[t], pr.N, dtype=np.uint64) for t in limbs}
+    x = {t: pr.ntt(xc[t], t) for t in limbs}
+    out = ckks.mod_down(pr, x, level)
+    outc = [pr.intt(out[i], i) for i in range(level + 1)]
+    ps = [pr.p_index(j) for j in range(pr.k)]
+    P = pr.P
+    Q = prod(pr.moduli[i] for i in range(level + 1))
+    for n in range(pr.N):
+        X = crt([xc[t][n] for t in limbs], [pr.moduli[t] for t in limbs])
+        Y = 0
+        for t in ps:
+            pj = pr.moduli[t]
+            yj = int(xc[t][n]) * pow((P // pj) % pj, -1, pj) % pj
+            yj = yj - pj if yj > pj // 2 else yj
+            Y += yj * (P // pj)
+        assert (X - Y) % P == 0
+        want = (X - Y) // P
+        got = crt([outc[i][n] for i in range(level + 1)], [pr.moduli[i] for i in range(level + 1)])
+        assert (got - want) % Q == 0
+        # and it is round(X / P) up to the conversion error |u| <= k/2
+        assert abs(want - (2 * X + P) // (2 * P)) <= pr.k // 2 + 1
+
+
+def test_rescale_is_rounded_division(pr):
+    rng = np.random.default_rng(2)
+    lv = 3
+    c = [rng.integers(0, pr.moduli[t], pr.N, dtype=np.uint64) for t in range(lv + 1)]
+    ct = ckks.Ciphertext(np.stack([pr.ntt(c[t], t) for t in range(lv + 1)]),
+                         np.stack([pr.ntt(c[t], t) for t in range(lv + 1)]), lv, 1.0)
+    out = ckks.rescale(pr, ct)
+    ql = pr.moduli[lv]
+    outc = [pr.intt(out.c0[i], i) for i in range(lv)]
+    for n in range(pr.N):
+        X = crt([c[t][n] for t in range(lv + 1)], pr.moduli[:lv + 1])
+        r = int(c[lv][n]) % ql
+        r = r - ql if r > ql // 2 else r
+        want = (X - r) // ql
+        assert (X - r) % ql == 0
+        got = crt([outc[i][n] for i in range(lv)], pr.moduli[:lv])
+        assert got == want
+
+
+@pytest.fixture(scope="module")
+def keyed():
+    pr = ckks.Params(7, 4, 2, 40)
+    keys = ckks.KeySet(pr, 5, rot_steps=[1, 2, 5, -3, 32], relin=True)
+    return pr, keys
+
+
+def test_encrypt_decrypt(keyed):
+    pr, keys = keyed
+    z = np.random.default_rng(3).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 30), 1, 0)
+    assert np.abs(ckks.decrypt(pr, keys.sk, ct) - z).max() < 1e-6
+    # b + a s = m + e exactly, with e the centred binomial noise
+    m = C.encode(z, pr.logN, 2.0 ** 30)
+    e = ckks.decrypt_coef(pr, keys.sk, ct) - m
+    assert np.abs(e).max() <= 21
+
+
+def test_switch_key_decrypts_under_source(keyed):
+    """Key switching identity: KS(c) = (d0, d1) with d0 + d1 s_dst ~ c s_src."""
+    pr, keys = keyed
+    lv = pr.L
+    rng = np.random.default_rng(4)
+    c = np.stack([rng.integers(0, pr.moduli[t], pr.N, dtype=np.uint64) for t in range(lv + 1)])
+    d0, d1 = ckks.key_switch_ext(pr, ckks.mod_up(pr, c, lv), keys.relin, lv)
+    for t in range(lv + 1):
+        q = pr.moduli[t]
+        s2 = C.vec_mul(keys.sk.ntt[t], keys.sk.ntt[t], q)
+        lhs = C.vec_add(d0[t], C.vec_mul(d1[t], keys.sk.ntt[t], q), q)
+        diff = C.centre(pr.intt(C.vec_sub(lhs, C.vec_mul(c[t], s2, q), q), t), q)
+        assert np.abs(diff).max() < 2 ** 14
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, -3, 32])
+def test_rotation_decrypts_to_shifted_slots(keyed, r):
+    pr, keys = keyed
+    z = np.random.default_rng(6).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 30), 1, 1)
+    out = ckks.decrypt(pr, keys.sk, ckks.rotate(pr, keys, ct, r))
+    assert np.abs(out - np.roll(z, -r)).max() < 1e-4
+
+
+def test_hoisted_rotation_equals_plain_rotation(keyed):
+    pr, keys = keyed
+    z = np.random.default_rng(7).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 30), 1, 2)
+    ext = ckks.mod_up(pr, ct.c1, ct.level)
+    for r in [1, 5]:
+        a = ckks.rotate_ext(pr, keys, ct, ext, r)
+        b = ckks.rotate(pr, keys, ct, r)
+        assert np.array_equal(a.as_array(), b.as_array())
+
+
+def test_pmult_rescale_and_cmult(keyed):
+    pr, keys = keyed
+    rng = np.random.default_rng(8)
+    z = rng.uniform(-1, 1, pr.N // 2)
+    w = rng.uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 30), 1, 3)
+    pt = ckks.encode(pr, w, pr.L, float(pr.q[pr.L]))
+    out = ckks.rescale(pr, ckks.pmult(pr, ct, pt))
+    assert out.level == pr.L - 1 and out.scale == 2.0 ** 30
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z * w).max() < 1e-5
+    sq = ckks.rescale(pr, ckks.cmult_relin(pr, keys, ct, ct))
+    assert np.abs(ckks.decrypt(pr, keys.sk, sq) - z * z).max() < 1e-3
