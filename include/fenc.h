@@ -1,0 +1,282 @@
+/*
+ * fenc.h - C ABI of the B300 (sm_103a) encrypted-convolution library.
+ *
+ * The library evaluates the hot path of FEnc^2's encrypted CNN inference: the
+ * homomorphic convolution under the conv-aware fragment encoding (Algorithm 1,
+ * Sec. 3), with hoisted inner rotations, PMult multiply-accumulate over
+ * fragment masks, outer rotations (Eq. 1 rotations, counted by Eq. 3 - Eq. 5),
+ * one rescale, and the layers around it: x^2 activation, 2x2 average pooling,
+ * fully connected layers, and Arch-aware Ciphertext Compression (Sec. 3, Fig. 6).
+ * The calls follow the usage flow of the problem statement (Sec. 4): the client
+ * sends shape metadata, receives the slot mapping, encodes and encrypts; the
+ * server evaluates; the client decrypts.
+ *
+ * Conventions (apply to every entry point):
+ *  - Return value: FE_OK (0) on success, a negative FE_E* code otherwise; the
+ *    message of the last error on the calling thread is fe_last_error().
+ *    Arguments are validated before any launch; no kernel traps or spins
+ *    without a bound.
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors);
+ *    *_host are host pointers.  Device buffers passed in are owned by the
+ *    caller; the library never frees them.  Library objects (fe_ctx, fe_evk,
+ *    fe_plan, fe_graph) are opaque handles released with their *_destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work and return without synchronising unless stated.
+ *  - Ring degree N = 2^logN.  Moduli are indexed q_0..q_L (L = n_q - 1, largest
+ *    first) followed by the special primes p_0..p_{k-1}.
+ *  - Polynomials are uint64 residues in NTT form, limb-major: a polynomial at
+ *    level l is [l+1][N]; a ciphertext at level l is [2][l+1][N] (c0, c1);
+ *    an array of n ciphertexts is [n][2][l+1][N], contiguous.
+ *  - NTT form: NTT(a)[i] = a(psi^(2 brv(i) + 1)) mod q with psi the smallest
+ *    primitive 2N-th root of unity mod q.  Slot l is the evaluation at
+ *    zeta^(5^l), zeta = exp(i pi / N); a left rotation by r slots uses the
+ *    Galois element 5^r mod 2N.
+ */
+#ifndef FENC_H
+#define FENC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FE_OK 0
+#define FE_EINVAL (-1)   /* bad argument or shape */
+#define FE_ENOMEM (-2)   /* buffer too small / allocation failed */
+#define FE_ELEVEL (-3)   /* no level left for the operation */
+#define FE_ESCALE (-4)   /* scale mismatch */
+#define FE_EKEY (-5)     /* a needed rotation key is missing */
+#define FE_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define FE_ECUDA (-7)    /* CUDA runtime error */
+#define FE_EENCODE (-8)  /* a coefficient lies within 2^-40 of a rounding tie */
+
+typedef struct fe_ctx fe_ctx;
+typedef struct fe_evk fe_evk;
+typedef struct fe_plan fe_plan;
+typedef struct fe_graph fe_graph;
+
+/* Parameter set.  q primes: the n_q largest primes below 2^qbits with
+ * q = 1 (mod 2N); special primes: the k largest primes below 2^pbits with the
+ * same congruence that are not among the q's. */
+typedef struct {
+    uint32_t logN, n_q, k, qbits, pbits;
+} fe_params;
+
+/* Fragment layout of a BS x C x H x W activation (Algorithm 1).
+ * Inputs: H, W, C, BS, S, m (m = 0: derive m = 2^ceil(log2(ceil(max(H,W)/S)))).
+ * Outputs filled by fe_layout_make: m, M = S m, cpc = N / (2 m^2 BS) channels per
+ * ciphertext, groups = ceil(C / cpc), n_ct = groups S^2.
+ * Slot of element (b, c, h, w): ciphertext (g S + u) S + v with g = c / cpc,
+ * u = h mod S, v = w mod S; slot ((c mod cpc) m^2 + (h / S) m + w / S) BS + b. */
+typedef struct {
+    uint32_t H, W, C, BS, S, m;
+    uint32_t M, cpc, groups, n_ct;
+} fe_layout;
+
+/* Operation counters (the columns of the paper's Table 4): rotations,
+ * key switches, forward+inverse limb NTTs, plaintext mults, ciphertext mults,
+ * rescales, and kernel launches issued by the library. */
+typedef struct {
+    uint64_t rot, keyswitch, ntt, pmult, cmult, rescale, launches;
+} fe_counters;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on the current CUDA device: generates the moduli and the
+ * NTT / base-conversion tables and uploads them (library-owned, freed by
+ * fe_ctx_destroy).  Errors: FE_EINVAL (logN outside [4,17], n_q < 1, k outside
+ * [1,8], primes above 61 bits), FE_ECUDA. */
+int fe_ctx_create(const fe_params* params, fe_ctx** out);
+void fe_ctx_destroy(fe_ctx* ctx);
+/* Copy the n_q + k moduli (q_0..q_L, p_0..p_{k-1}) to moduli_host. */
+int fe_ctx_moduli(const fe_ctx* ctx, uint64_t* moduli_host);
+/* Read / reset the operation counters of the context. */
+int fe_get_counters(const fe_ctx* ctx, fe_counters* out);
+int fe_counters_reset(fe_ctx* ctx);
+/* Message of the last error on this thread (never NULL). */
+const char* fe_last_error(void);
+
+/* ---- keys (client) ------------------------------------------------------- */
+
+/* Secret key: ternary s sampled from the counter-based generator (SplitMix64
+ * words addressed by seed and stream), written in NTT form on every modulus:
+ * sk_dev holds [n_q + k][N] uint64. */
+int fe_sk_gen(fe_ctx* ctx, uint64_t seed, void* sk_dev, void* stream);
+
+/* Bytes of the switching keys for n_steps rotations (+1 relinearisation key if
+ * relin != 0): per key dnum = ceil(n_q / k) digits x [2][n_q + k][N] uint64. */
+size_t fe_evk_bytes(const fe_ctx* ctx, uint32_t n_steps, int relin);
+
+/* Hybrid key-switching keys (Eq. 1's evk^k_rot, with the special primes as the
+ * "large modulus" P), written into the caller buffer evk_dev of at least
+ * fe_evk_bytes bytes.  A rotation key for step r switches from s to
+ * sigma_{g^-1}(s), g = 5^r mod 2N, so that a rotation key-switches first and
+ * applies sigma_g afterwards.  steps_host: n_steps slot offsets (negative =
+ * right rotation; duplicates and multiples of N/2 are rejected).  The handle
+ * keeps pointers into evk_dev; the buffer must outlive it.
+ * Errors: FE_EINVAL, FE_ENOMEM (buffer too small). */
+int fe_evk_gen(fe_ctx* ctx, const void* sk_dev, uint64_t seed, const int32_t* steps_host,
+               uint32_t n_steps, int relin, void* evk_dev, size_t evk_bytes, void* stream,
+               fe_evk** out);
+void fe_evk_destroy(fe_evk* evk);
+
+/* ---- layout, packing, encode / encrypt / decrypt (client) ----------------- */
+
+/* Fill the derived fields of a layout (Algorithm 1 steps 1-2) for the
+ * context's ring degree.  Errors: FE_EINVAL when one channel block does not fit
+ * a ciphertext (m^2 BS > N/2). */
+int fe_layout_make(const fe_ctx* ctx, fe_layout* lay);
+
+/* Algorithm 1 step 3 on the device: x_dev float64 (BS, C, H, W) -> slots_dev
+ * float64 [n_ct][N/2], zero padded. */
+int fe_fragment_pack(const fe_ctx* ctx, const fe_layout* lay, const double* x_dev,
+                     double* slots_dev, void* stream);
+/* Inverse of fe_fragment_pack on the valid region. */
+int fe_fragment_unpack(const fe_ctx* ctx, const fe_layout* lay, const double* slots_dev,
+                       double* y_dev, void* stream);
+
+/* Encode n slot vectors (slots_dev, [n][N/2] float64) at `scale` into
+ * plaintexts [n][level+1][N] (NTT form): m = round(scale * tau^-1(z)),
+ * evaluated in double-double.  Errors: FE_EENCODE (a coefficient within 2^-40
+ * of a rounding tie). */
+int fe_encode(fe_ctx* ctx, const double* slots_dev, uint32_t n, uint32_t level, double scale,
+              void* pt_dev, void* stream);
+
+/* Encode n_ct slot vectors and encrypt them with the secret key at `level`:
+ * c1 = a uniform, c0 = -a s + m + e, e centred binomial (eta = 21).
+ * Ciphertext j uses random streams (seed, ct_id0 + j).
+ * Output ct_dev: [n_ct][2][level+1][N].  Errors: FE_EENCODE, FE_EINVAL. */
+int fe_encode_encrypt(fe_ctx* ctx, const void* sk_dev, const double* slots_dev, uint32_t n_ct,
+                      uint32_t level, double scale, uint64_t seed, uint64_t ct_id0, void* ct_dev,
+                      void* stream);
+
+/* Decrypt and decode n_ct ciphertexts at `level` and `scale`:
+ * m = c0 + c1 s, centred mod q_0 (q_0 q_1 when level >= 1), slots
+ * z_l = Re(sum_j m_j zeta^(5^l j)) / scale -> slots_dev [n_ct][N/2] float64. */
+int fe_decrypt_decode(fe_ctx* ctx, const void* sk_dev, const void* ct_dev, uint32_t n_ct,
+                      uint32_t level, double scale, double* slots_dev, void* stream);
+
+/* ---- CKKS primitives (server) --------------------------------------------- */
+
+/* Forward (inverse != 0: inverse) NTT of n_poly polynomials [n_poly][n_limbs][N]
+ * in place; limb j of every polynomial uses modulus index first_mod + j. */
+int fe_ntt(fe_ctx* ctx, void* data_dev, uint32_t n_poly, uint32_t n_limbs, uint32_t first_mod,
+           int inverse, void* stream);
+/* Left rotation of n_ct ciphertexts by r slots (Eq. 1): out = sigma_g((c0,0) + KS(c1)).
+ * Errors: FE_EKEY when the key for r is missing. */
+int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
+              int32_t r, void* out_dev, void* stream);
+/* Rescale n_ct ciphertexts from `level` to level-1: (c - [c]_{q_l}) q_l^-1 with
+ * the centred representative.  Errors: FE_ELEVEL at level 0. */
+int fe_rescale(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
+               void* stream);
+/* out = ct (x) pt per limb (PMult), n_ct ciphertexts times one plaintext each. */
+int fe_pmult(fe_ctx* ctx, const void* ct_dev, const void* pt_dev, uint32_t n_ct, uint32_t level,
+             void* out_dev, void* stream);
+/* out = a + b (Add), n_ct pairs. */
+int fe_add(fe_ctx* ctx, const void* a_dev, const void* b_dev, uint32_t n_ct, uint32_t level,
+           void* out_dev, void* stream);
+
+/* ---- encrypted layers (server) -------------------------------------------- */
+
+/* Plan one HE convolution layer under the fragment encoding (Sec. 3):
+ *   in: input layout, Cout, K, stride (1, or 2 with S even), depthwise (Cout = C,
+ *   one filter per channel), in_period (0, or c_v when the input was replicated
+ *   by fe_compress so that channel position c holds channel c mod c_v), level of
+ *   the input ciphertexts.
+ * The plan records the inner rotation offsets, the nonzero diagonals, the
+ * multiply-accumulate term lists and the output layout (out_lay).
+ * Errors: FE_EINVAL (shape), FE_ELEVEL (level 0). */
+int fe_plan_conv(fe_ctx* ctx, const fe_layout* in_lay, uint32_t Cout, uint32_t K, uint32_t stride,
+                 int depthwise, uint32_t in_period, uint32_t level, fe_layout* out_lay,
+                 fe_plan** out);
+/* Plan a fully connected layer y = W x on ciphertexts whose positions
+ * (P = cpc m^2 per ciphertext, BS slots each) hold features:
+ *   feat_host[c * P + p] = feature index of position p of input ciphertext c, or -1.
+ * Output neuron n sits in ciphertext n / P at position n mod P.  Baby-step /
+ * giant-step split n1 = 2^ceil(log2(P)/2), n2 = P / n1. */
+int fe_plan_fc(fe_ctx* ctx, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat_host,
+               uint32_t F_in, uint32_t F_out, uint32_t level, fe_plan** out);
+void fe_plan_destroy(fe_plan* plan);
+
+/* Sizes of a plan's buffers: encoded weight plaintexts, input / output
+ * ciphertext arrays, and the default device workspace for fe_he_conv /
+ * fe_he_fc (a larger workspace lets the batched path take larger chunks). */
+typedef struct {
+    size_t pt_bytes, in_bytes, out_bytes, workspace_bytes, workspace_min_bytes;
+    uint32_t n_in_ct, n_out_ct, n_pt, n_inner_rot, n_outer_rot;
+} fe_plan_info;
+int fe_plan_query(const fe_plan* plan, fe_plan_info* info);
+/* Rotation steps the plan needs keys for (steps_host has room for max entries;
+ * *n_steps receives the count). */
+int fe_plan_rotation_steps(const fe_plan* plan, int32_t* steps_host, uint32_t max,
+                           uint32_t* n_steps);
+
+/* Encode the layer's weights into plaintexts (pt_dev, plan pt_bytes) at
+ * `w_scale` (the scale the layer multiplies in; q_level keeps the ciphertext
+ * scale unchanged across the layer).  weights_host: float64, conv
+ * (Cout, Cin, K, K) or (C, 1, K, K) when depthwise; FC (F_out, F_in).  Every
+ * weight is multiplied by wmul first (a folded 1/4 of a preceding pooling).
+ * Zero weights at invalid output positions make the plaintexts the fragment
+ * masks of Fig. 2. */
+int fe_plan_load_weights(fe_ctx* ctx, fe_plan* plan, const double* weights_host, double wmul,
+                         double w_scale, void* pt_dev, void* stream);
+
+/* Run a planned HE convolution: in_dev [n_in_ct][2][level+1][N] -> out_dev
+ * [n_out_ct][2][level][N] (rescaled once).  mode 0 = plain path (one launch per
+ * primitive per ciphertext), mode 1 = batched path (all ciphertexts of a stage
+ * in one launch per primitive, key-stationary inner products, summed
+ * rotate-and-add).  Both produce identical residues.
+ * Errors: FE_EKEY, FE_ENOMEM (workspace too small). */
+int fe_he_conv(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev,
+               const void* in_dev, void* out_dev, void* workspace_dev, size_t workspace_bytes,
+               int mode, void* stream);
+/* Run a planned FC layer (same buffer conventions as fe_he_conv). */
+int fe_he_fc(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev,
+             const void* in_dev, void* out_dev, void* workspace_dev, size_t workspace_bytes,
+             int mode, void* stream);
+
+/* x^2 activation (the a x^2 + b x + c polynomial of Sec. 4 with a = 1,
+ * b = c = 0): CMult with relinearisation, then rescale.  in: [n_ct][2][level+1][N],
+ * out: [n_ct][2][level][N].  Workspace: fe_square_workspace_bytes. */
+size_t fe_square_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
+int fe_he_square(fe_ctx* ctx, const fe_evk* evk, const void* in_dev, uint32_t n_ct, uint32_t level,
+                 void* out_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* 2x2 average pooling by summing fragment ciphertexts (S even; Sec. 4): output
+ * fragment (u, v) = sum of input fragments (2u + di, 2v + dj); the 1/4 is left
+ * to the next layer's weights.  out_lay receives the output layout (S / 2). */
+int fe_he_avgpool(fe_ctx* ctx, const fe_layout* lay, const void* in_dev, uint32_t level,
+                  void* out_dev, fe_layout* out_lay, void* stream);
+
+/* Arch-aware Ciphertext Compression (Sec. 3, Fig. 6): ciphertexts whose first
+ * c_valid channel positions hold data and whose other positions are zero are
+ * filled by rotate-and-add doubling, ct += Rot(ct, -s m^2 BS) for
+ * s = c_valid, 2 c_valid, ..., cpc / 2; position c then holds channel c mod c_valid.
+ * Consumes no level.  Needs rotation keys for -s m^2 BS.  Workspace:
+ * fe_compress_workspace_bytes. */
+size_t fe_compress_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
+int fe_compress(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid,
+                const void* in_dev, uint32_t n_ct, uint32_t level, void* out_dev,
+                void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* ---- batched, graph-captured execution ------------------------------------- */
+
+/* Capture the batched path of n planned layers (conv or FC), run back to back,
+ * into one CUDA graph (stream capture on `stream`).  pts_host[i] is layer i's
+ * plaintext buffer, bufs_host[i] its input and bufs_host[i+1] its output; all
+ * layers share workspace_dev.  The item tables of every layer are uploaded into
+ * the workspace before capture, so the graph replays kernels only. */
+int fe_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
+                     const void* const* pts_host, uint32_t n, void* const* bufs_host,
+                     void* workspace_dev, size_t workspace_bytes, void* stream, fe_graph** out);
+int fe_graph_launch(fe_graph* graph, void* stream);
+void fe_graph_destroy(fe_graph* graph);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FENC_H */

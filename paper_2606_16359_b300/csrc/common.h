@@ -1,0 +1,101 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fenc.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+namespace fe {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message, integer status codes)
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define FE_CUDA_TRY(expr)                                                                  \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            return ::fe::fail(FE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+#define FE_TRY(expr)                  \
+    do {                              \
+        int _rc = (expr);             \
+        if (_rc != FE_OK) return _rc; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// A modulus with the constants its reductions need.
+//   ratio = floor(2^128 / q) as (hi, lo) words, for 128-bit Barrett reduction.
+// ---------------------------------------------------------------------------
+struct Modulus {
+    u64 q;
+    u64 ratio_hi, ratio_lo;
+};
+
+#if defined(__CUDACC__)
+// ---------------------------------------------------------------------------
+// Device modular arithmetic.  All moduli are odd primes below 2^61, inputs to
+// the *_mod helpers are fully reduced (< q) unless stated.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+// Shoup multiplication by a constant w with wq = floor(w 2^64 / q); any a < 2^64.
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wq, u64 q) {
+    u64 hi = __umul64hi(a, wq);
+    u64 r = a * w - hi * q;
+    return r >= q ? r - q : r;
+}
+// 128-bit Barrett reduction of x = (hi, lo) modulo m.q (< 2^62).  The quotient
+// estimate floor(x * ratio / 2^128) drops the low word of lo * ratio_lo and is at
+// most 2 below floor(x / q), so two conditional subtractions finish the job.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const Modulus& m) {
+    u64 c0 = __umul64hi(lo, m.ratio_lo);
+    u128 p1 = (u128)lo * m.ratio_hi;
+    u128 p2 = (u128)hi * m.ratio_lo;
+    u128 mid = (u128)c0 + (u64)p1 + (u64)p2;
+    u64 qhat = hi * m.ratio_hi + (u64)(p1 >> 64) + (u64)(p2 >> 64) + (u64)(mid >> 64);
+    u64 r = lo - qhat * m.q;
+    if (r >= m.q) r -= m.q;
+    if (r >= m.q) r -= m.q;
+    return r;
+}
+__device__ __forceinline__ u64 reduce128(u128 x, const Modulus& m) {
+    return reduce128((u64)(x >> 64), (u64)x, m);
+}
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
+    return reduce128((u128)a * b, m);
+}
+// signed value (|v| < 2^63) to its residue mod q
+__device__ __forceinline__ u64 from_signed(i64 v, u64 q) {
+    i64 r = v % (i64)q;
+    return (u64)(r < 0 ? r + (i64)q : r);
+}
+// centred representative of a residue: (-q/2, q/2]
+__device__ __forceinline__ i64 centre(u64 a, u64 q) { return a > (q >> 1) ? (i64)a - (i64)q : (i64)a; }
+#endif
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+Modulus make_modulus(u64 q);
+u64 shoup_of(u64 w, u64 q);  // floor(w 2^64 / q)
+
+}  // namespace fe

@@ -1,0 +1,113 @@
+// Context: moduli, device tables, counters, and the internal launch helpers.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "common.h"
+
+namespace fe {
+
+// Approximate base conversion with centred digits from `src` moduli to `dst`
+// moduli (device pointers into the context's constant pool):
+//   y_i = [x_i * (B/b_i)^-1]_{b_i}, taken in (-b_i/2, b_i/2];
+//   out_t = sum_i y_i (B/b_i)  mod m_t
+// evaluated as sum_i y'_i mat[t][i] + negB[t] * #{i : y'_i > b_i/2} with the
+// unsigned y'_i and negB[t] = -B mod m_t.
+struct BConvTab {
+    int n_src, n_dst;
+    const int* src;     // [n_src] modulus indices
+    const int* dst;     // [n_dst]
+    const u64* inv;     // [n_src] (B/b_i)^-1 mod b_i
+    const u64* inv_sh;  // Shoup companions
+    const u64* mat;     // [n_dst][n_src] (B/b_i) mod m_t (destination-major: truncatable)
+    const u64* negB;    // [n_dst]
+};
+
+struct LevelTabs {
+    std::vector<BConvTab> modup;  // one per digit
+    BConvTab rescale;             // {q_l} -> q_0..q_{l-1}
+    std::vector<int> ks_limbs;    // q_0..q_l, p_0..p_{k-1}
+    const int* d_ks_limbs;        // device copy
+};
+
+}  // namespace fe
+
+struct fe_evk {
+    fe_ctx* ctx;
+    u64* base;                     // caller buffer
+    std::map<uint32_t, u64*> rot;  // galois element -> key [dnum][2][n_mod][N]
+    u64* relin;                    // or nullptr
+    std::vector<int32_t> steps;
+};
+
+struct fe_ctx {
+    fe_params prm;
+    int logN, N, L, k, n_mod, dnum;
+    std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
+    std::vector<u64> psi;
+    fe::Modulus* d_mod;             // [n_mod]
+    u64 *d_tw, *d_tw_sh;            // [n_mod][N]  psi^brv(j) and Shoup companions
+    u64 *d_itw, *d_itw_sh;          // [n_mod][N]  psi^-brv(j)
+    u64 *d_ninv, *d_ninv_sh;        // [n_mod] N^-1
+    u64 *d_pinv, *d_pinv_sh;        // [n_mod] P^-1 mod q_i (i <= L)
+    u64 *d_qlinv, *d_qlinv_sh;      // [L+1][L+1]: q_l^-1 mod q_i at [l][i]
+    double* d_dd_w;                 // [N][4]: exp(-2 pi i j / 2N) as (re_hi, re_lo, im_hi, im_lo)
+    int* d_identity_map;            // [n_mod] j -> j
+    int* d_t2slot;                  // [N]   slot whose root is zeta^(2t+1) or its conjugate
+    int* d_slot2t;                  // [N/2] (5^l mod 2N - 1) / 2
+    u64 q0inv_q1;                   // q_0^-1 mod q_1 (CRT of two limbs at decryption)
+    fe::BConvTab moddown;           // P -> q_0..q_L
+    std::vector<fe::LevelTabs> lv;  // per level 0..L
+    void* pool;                     // all small device tables live here
+    std::vector<void*> allocs;
+    fe_counters cnt;
+    cudaDeviceProp prop;
+    int n_sm;
+
+    int slot_count() const { return N / 2; }
+    size_t limb_bytes() const { return (size_t)N * sizeof(u64); }
+    uint32_t galois(int32_t r) const;
+};
+
+namespace fe {
+
+// NTT over a set of limbs: limb b lives at base + (b / per_poly) * poly_stride
+// + (b % per_poly) * N and uses modulus mod_map[b % per_poly].
+struct LimbSet {
+    u64* base;
+    size_t poly_stride;  // in words
+    int per_poly;
+    int n_poly;
+    const int* mod_map;  // device [per_poly]
+};
+void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st);
+void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st);
+
+int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st);
+int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
+                 cudaStream_t st);
+int decode_batch(fe_ctx* c, const double* mdd, int n, double scale, double* slots, cudaStream_t st);
+
+// scratch allocation helper: carve 256-byte aligned chunks out of a caller workspace
+struct Carver {
+    char* p;
+    size_t left;
+    bool ok = true;
+    Carver(void* base, size_t bytes) : p((char*)base), left(bytes) {}
+    template <class T>
+    T* take(size_t count) {
+        size_t b = (count * sizeof(T) + 255) & ~(size_t)255;
+        if (b > left) {
+            ok = false;
+            return nullptr;
+        }
+        T* r = (T*)p;
+        p += b;
+        left -= b;
+        return r;
+    }
+};
+
+}  // namespace fe

@@ -1,0 +1,732 @@
+// Encrypted layers under the fragment encoding: planning and execution of the
+// HE convolution (Sec. 3) and of the fully connected layers, and fragment
+// pack / unpack.
+//
+// A conv plan follows the algorithm order of Sec. 3:
+//  1. inner rotations: input ciphertext (g, u, v) is rotated by (a m + b) BS
+//     for every block offset (a, b) != (0, 0) that some tap needs; one ModUp of
+//     its c1 serves all of its rotations (hoisting);
+//  2. PMult-MAC over fragment masks: for output (h, u', v') and diagonal d,
+//     P_d = sum_g sum_taps R(g, u, v, a, b) (x) pt(h, u', v', d, g, i, j) with
+//     u = (u' + i) mod S, a = (u' + i) div S (same for columns);
+//  3. outer rotations before rescale: out = P_0 + sum_{d != 0} Rot(P_d, d m^2 BS);
+//  4. one rescale.
+// An FC plan has the same shape: baby-step rotations of the inputs (1), MAC of
+// the rotated diagonals (2), giant-step rotate-and-sum (3), rescale (4).
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <set>
+#include <tuple>
+
+#include "plan.h"
+
+namespace fe {
+
+namespace {
+constexpr int kB = 256;
+
+// block offsets a of source fragment row u needed by kept output rows u' (u' % stride == 0)
+std::vector<std::vector<int>> inner_offsets(int S, int K, int stride) {
+    std::vector<std::vector<int>> r(S);
+    for (int u = 0; u < S; u++) {
+        std::set<int> offs;
+        for (int up = 0; up < S; up += stride)
+            for (int i = 0; i < K; i++)
+                if ((up + i) % S == u) offs.insert((up + i) / S);
+        r[u].assign(offs.begin(), offs.end());
+    }
+    return r;
+}
+
+// ---- weight slot vectors -------------------------------------------------
+struct ConvPtArgs {
+    const fe_plan::ConvPt* pts;
+    const double* W;
+    double wmul;
+    int S, m, BS, cpc, H, Wd, K, stride, Cin, Cout, depthwise, in_period;
+};
+
+__global__ void k_conv_pt_slots(ConvPtArgs a, double* z, int slots) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= slots) return;
+    const fe_plan::ConvPt p = a.pts[blockIdx.y];
+    const int blk = a.m * a.m * a.BS;
+    const int c_loc = l / blk, rem = l % blk;
+    const int kblk = rem / a.BS;
+    const int bi = kblk / a.m, bj = kblk % a.m;
+    double v = 0.0;
+    const int c = a.in_period ? c_loc % a.in_period : p.g * a.cpc + c_loc;
+    const int o_loc = ((c_loc - p.d) % a.cpc + a.cpc) % a.cpc;
+    const int o = p.h * a.cpc + o_loc;
+    const int hp = bi * a.S + p.up, wp = bj * a.S + p.vp;
+    bool ok = (a.in_period || c < a.Cin) && o < a.Cout && hp <= a.H - a.K && wp <= a.Wd - a.K &&
+              hp % a.stride == 0 && wp % a.stride == 0;
+    if (ok && a.depthwise && o != c) ok = false;
+    if (ok) {
+        const int K = a.K;
+        const double w = a.depthwise ? a.W[((size_t)c * K + p.i) * K + p.j]
+                                     : a.W[(((size_t)o * a.Cin + c) * K + p.i) * K + p.j];
+        v = w * a.wmul;
+    }
+    z[(size_t)blockIdx.y * slots + l] = v;
+}
+
+struct FcPtArgs {
+    const fe_plan::FcPt* pts;
+    const double* W;
+    const int* feat;  // [n_in][P]
+    double wmul;
+    int P, BS, n1, F_in, F_out;
+};
+
+// rotated diagonal: z[p BS + b] = W[t P + ((p - n1 gam) mod P)][feat(c, (p + beta) mod P)]
+__global__ void k_fc_pt_slots(FcPtArgs a, double* z, int slots) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= slots) return;
+    const fe_plan::FcPt q = a.pts[blockIdx.y];
+    const int p = l / a.BS;
+    const int p0 = ((p - a.n1 * q.gam) % a.P + a.P) % a.P;
+    const int n = q.t * a.P + p0;
+    const int f = a.feat[(size_t)q.c * a.P + (p + q.beta) % a.P];
+    double v = 0.0;
+    if (n < a.F_out && f >= 0) v = a.W[(size_t)n * a.F_in + f] * a.wmul;
+    z[(size_t)blockIdx.y * slots + l] = v;
+}
+
+// ---- fragment pack / unpack ------------------------------------------------
+__global__ void k_pack(const double* x, double* slots, fe_layout L, int N) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = N / 2;
+    if (l >= half) return;
+    const int ci = blockIdx.y;
+    const int S = L.S, m = L.m, BS = L.BS;
+    const int g = ci / (S * S), u = (ci / S) % S, v = ci % S;
+    const int blk = m * m * BS;
+    const int c_loc = l / blk, rem = l % blk, kk = rem / BS, b = rem % BS;
+    const int bi = kk / m, bj = kk % m;
+    const int c = g * L.cpc + c_loc, h = bi * S + u, w = bj * S + v;
+    double val = 0.0;
+    if (c < (int)L.C && h < (int)L.H && w < (int)L.W) val = x[(((size_t)b * L.C + c) * L.H + h) * L.W + w];
+    slots[(size_t)ci * half + l] = val;
+}
+
+__global__ void k_unpack(const double* slots, double* y, fe_layout L, int N) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)L.BS * L.C * L.H * L.W;
+    if (idx >= total) return;
+    const int w = idx % L.W, h = (idx / L.W) % L.H, c = (idx / ((size_t)L.W * L.H)) % L.C,
+              b = idx / ((size_t)L.W * L.H * L.C);
+    const int S = L.S, m = L.m;
+    const int g = c / L.cpc, c_loc = c % L.cpc, u = h % S, v = w % S, bi = h / S, bj = w / S;
+    const int ci = (g * S + u) * S + v;
+    const size_t slot = ((size_t)c_loc * m * m + bi * m + bj) * L.BS + b;
+    y[idx] = slots[(size_t)ci * (N / 2) + slot];
+}
+
+struct Sizes {
+    size_t ctw, nlN, extw, accw;
+};
+Sizes sizes_of(const fe_ctx* c, int level) {
+    return {ct_words(c, level), (size_t)(level + 1) * c->N, ext_words(c, level), acc_words(c, level)};
+}
+
+// rotated groups (output, group index), sorted by step so that groups sharing a key are adjacent
+std::vector<std::pair<int, int>> outer_order(const fe_plan* p) {
+    std::vector<std::pair<int, int>> v;
+    for (int o = 0; o < p->n_out; o++)
+        for (int gi = 0; gi < (int)p->outs[o].groups.size(); gi++)
+            if (p->outs[o].groups[gi].step) v.push_back({o, gi});
+    std::stable_sort(v.begin(), v.end(), [&](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+        return p->outs[a.first].groups[a.second].step < p->outs[b.first].groups[b.second].step;
+    });
+    return v;
+}
+
+size_t item_bytes(const fe_plan* p, size_t chunk) {
+    size_t groups = 0;
+    for (auto& o : p->outs) groups += o.groups.size();
+    size_t n_chunks = p->n_outer ? (p->n_outer + chunk - 1) / chunk : 0;
+    size_t n = p->inner.size() * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(CombineItem));
+    n += (size_t)p->n_outer * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(SumEntry));
+    n += n_chunks * p->n_out * sizeof(SumItem);
+    n += groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm);
+    return n + 16 * 256;
+}
+
+}  // namespace
+
+int layout_fill(int N, fe_layout* l) {
+    if (!l->H || !l->W || !l->C || !l->BS || !l->S) return fail(FE_EINVAL, "layout has a zero extent");
+    uint32_t m = l->m;
+    if (m == 0) {
+        uint32_t side = (std::max(l->H, l->W) + l->S - 1) / l->S;
+        m = 1;
+        while (m < side) m *= 2;
+    } else if (l->S * m < std::max(l->H, l->W)) {
+        return fail(FE_EINVAL, "block grid too small for the map");
+    }
+    uint64_t slots = (uint64_t)N / 2, blk = (uint64_t)m * m * l->BS;
+    if (blk > slots || slots % blk) return fail(FE_EINVAL, "one channel block does not fit a ciphertext");
+    l->m = m;
+    l->M = l->S * m;
+    l->cpc = (uint32_t)(slots / blk);
+    l->groups = (l->C + l->cpc - 1) / l->cpc;
+    l->n_ct = l->groups * l->S * l->S;
+    return FE_OK;
+}
+
+size_t plan_workspace(const fe_plan* p, size_t chunk) {
+    const fe_ctx* c = p->c;
+    Sizes z = sizes_of(c, p->level);
+    size_t n_mu = p->modup_cts.size(), n_in_rot = p->inner.size();
+    size_t persist = (n_in_rot + p->n_out) * z.ctw;
+    size_t inner = n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + z.ctw);
+    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw);
+    size_t rs = rescale_tmp_words(c, p->n_out, p->level);
+    size_t words = persist + std::max(std::max(inner, outer), rs);
+    return words * 8 + item_bytes(p, chunk) + 32 * 256;
+}
+
+// Both phases derive every pointer from (plan, buffers, workspace) alone, so a
+// graph can be captured from the launch phase after an upload phase.
+int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, const u64* b_pt, u64* b_out,
+             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase) {
+    const int N = c->N, lv = p->level;
+    Sizes z = sizes_of(c, lv);
+    size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, p->n_outer);
+    while (chunk > 1 && plan_workspace(p, chunk) > ws_bytes) chunk = (chunk + 1) / 2;
+    if (plan_workspace(p, chunk) > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the plan");
+    std::map<int32_t, const u64*> keys;
+    for (int32_t s : p->steps) {
+        const u64* k = evk_key(evk, c->galois(s));
+        if (!k) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(s));
+        keys[s] = k;
+    }
+    // ---- carve the workspace ----
+    Carver cv(ws, ws_bytes);
+    const size_t n_in_rot = p->inner.size(), n_mu = p->modup_cts.size();
+    u64* R = cv.take<u64>(n_in_rot * z.ctw);
+    u64* total = cv.take<u64>((size_t)p->n_out * z.ctw);
+    size_t n_groups_all = 0;
+    for (auto& o : p->outs) n_groups_all += o.groups.size();
+    auto order = outer_order(p);
+    const size_t n_chunks = order.empty() ? 0 : (order.size() + chunk - 1) / chunk;
+    KsItem* d_in_ks = cv.take<KsItem>(std::max<size_t>(1, n_in_rot));
+    KsGroup* d_in_kg = cv.take<KsGroup>(std::max<size_t>(1, n_in_rot));
+    CombineItem* d_in_cb = cv.take<CombineItem>(std::max<size_t>(1, n_in_rot));
+    MacItem* d_mac = cv.take<MacItem>(std::max<size_t>(1, n_groups_all));
+    MacTerm* d_terms = cv.take<MacTerm>(std::max<size_t>(1, p->terms.size()));
+    KsItem* d_out_ks = cv.take<KsItem>(std::max<size_t>(1, order.size()));
+    KsGroup* d_out_kg = cv.take<KsGroup>(std::max<size_t>(1, order.size()));
+    SumEntry* d_ent = cv.take<SumEntry>(std::max<size_t>(1, order.size()));
+    SumItem* d_sum = cv.take<SumItem>(std::max<size_t>(1, n_chunks * p->n_out));
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
+    char* scratch = cv.p;
+    const size_t scratch_bytes = cv.left;
+    Carver s1(scratch, scratch_bytes);  // stage 1
+    u64* coef1 = s1.take<u64>(n_mu * z.nlN);
+    u64* ext1 = s1.take<u64>(n_mu * z.extw);
+    u64* acc1 = s1.take<u64>(n_in_rot * z.accw);
+    u64* conv1 = s1.take<u64>(n_in_rot * z.ctw);
+    Carver s3(scratch, scratch_bytes);  // stage 3 (same region)
+    u64* Pd = s3.take<u64>(chunk * z.ctw);
+    u64* coef3 = s3.take<u64>(chunk * z.nlN);
+    u64* ext3 = s3.take<u64>(chunk * z.extw);
+    u64* acc3 = s3.take<u64>(chunk * z.accw);
+    u64* conv3 = s3.take<u64>(chunk * z.ctw);
+    Carver s4(scratch, scratch_bytes);  // stage 4 (same region)
+    u64* rs_tmp = s4.take<u64>(2 * (size_t)p->n_out * N);
+    u64* rs_lift = s4.take<u64>(2 * (size_t)p->n_out * lv * N);
+    if (!s1.ok || !s3.ok || !s4.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
+
+    auto src_ptr = [&](int src) -> const u64* {
+        return src >= 0 ? R + (size_t)src * z.ctw : b_in + (size_t)(-src - 1) * z.ctw;
+    };
+
+    // ---- host item tables ----
+    std::vector<int> iorder(n_in_rot);
+    for (size_t r = 0; r < n_in_rot; r++) iorder[r] = (int)r;
+    std::stable_sort(iorder.begin(), iorder.end(), [&](int x, int y) { return p->inner[x].step < p->inner[y].step; });
+    std::vector<KsItem> iks(n_in_rot);
+    std::vector<KsGroup> ikg;
+    std::vector<CombineItem> icb(n_in_rot);
+    for (size_t q = 0; q < n_in_rot; q++) {
+        int r = iorder[q];
+        const auto& in = p->inner[r];
+        iks[q] = KsItem{ext1 + (size_t)p->modup_slot[in.ci] * z.extw, keys[in.step], acc1 + (size_t)r * z.accw};
+        if (q == 0 || in.step != p->inner[iorder[q - 1]].step) ikg.push_back(KsGroup{keys[in.step], (int)q, 0});
+        ikg.back().n_items++;
+    }
+    for (size_t r = 0; r < n_in_rot; r++) {
+        const auto& in = p->inner[r];
+        icb[r] = CombineItem{acc1 + r * z.accw, conv1 + r * z.ctw, b_in + (size_t)in.ci * z.ctw, nullptr,
+                             R + r * z.ctw, c->galois(in.step), 0};
+    }
+    std::vector<MacTerm> mterms;
+    mterms.reserve(p->terms.size());
+    for (const auto& t : p->terms) mterms.push_back(MacTerm{src_ptr(t.src), b_pt + (size_t)t.pt * z.nlN});
+    std::vector<MacItem> macs;
+    std::vector<int> no_base;
+    for (int o = 0; o < p->n_out; o++) {
+        bool base = false;
+        for (const auto& g : p->outs[o].groups)
+            if (g.step == 0) {
+                macs.push_back(MacItem{total + (size_t)o * z.ctw, g.t0, g.nt});
+                base = true;
+            }
+        if (!base) no_base.push_back(o);
+    }
+    const size_t n_base = macs.size();
+    for (size_t k = 0; k < order.size(); k++) {
+        const auto& g = p->outs[order[k].first].groups[order[k].second];
+        macs.push_back(MacItem{Pd + (k % chunk) * z.ctw, g.t0, g.nt});
+    }
+    std::vector<KsItem> oks(order.size());
+    std::vector<KsGroup> okg;
+    std::vector<SumEntry> ents;
+    std::vector<SumItem> sums;
+    std::vector<std::pair<int, int>> kg_range, sum_range;
+    for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
+        size_t c1 = std::min(order.size(), c0 + chunk);
+        int kg0 = (int)okg.size();
+        std::map<int, std::vector<int>> by_out;
+        for (size_t k = c0; k < c1; k++) {
+            const auto& g = p->outs[order[k].first].groups[order[k].second];
+            size_t s = k - c0;
+            oks[k] = KsItem{ext3 + s * z.extw, keys[g.step], acc3 + s * z.accw};
+            if (k == c0 || g.step != p->outs[order[k - 1].first].groups[order[k - 1].second].step)
+                okg.push_back(KsGroup{keys[g.step], (int)k, 0});
+            okg.back().n_items++;
+            by_out[order[k].first].push_back((int)k);
+        }
+        kg_range.push_back({kg0, (int)okg.size() - kg0});
+        int s0 = (int)sums.size();
+        for (auto& kv : by_out) {
+            SumItem si{total + (size_t)kv.first * z.ctw, nullptr, (int)ents.size(), (int)kv.second.size(), 1};
+            for (int k : kv.second) {
+                size_t s = k - c0;
+                const auto& g = p->outs[order[k].first].groups[order[k].second];
+                ents.push_back(SumEntry{acc3 + s * z.accw, conv3 + s * z.ctw, Pd + s * z.ctw, c->galois(g.step)});
+            }
+            sums.push_back(si);
+        }
+        sum_range.push_back({s0, (int)sums.size() - s0});
+    }
+
+    if (phase & 1) {
+        FE_TRY(upload(iks, d_in_ks, st));
+        FE_TRY(upload(ikg, d_in_kg, st));
+        FE_TRY(upload(icb, d_in_cb, st));
+        FE_TRY(upload(mterms, d_terms, st));
+        FE_TRY(upload(macs, d_mac, st));
+        FE_TRY(upload(oks, d_out_ks, st));
+        FE_TRY(upload(okg, d_out_kg, st));
+        FE_TRY(upload(ents, d_ent, st));
+        FE_TRY(upload(sums, d_sum, st));
+    }
+    if (!(phase & 2)) return FE_OK;
+
+    // ---- stage 1: inner rotations (hoisted ModUp per input ciphertext) ----
+    if (mode == 0) {
+        for (size_t i = 0; i < n_mu; i++)
+            modup(c, b_in + (size_t)p->modup_cts[i] * z.ctw + z.nlN, z.ctw, 1, lv, coef1 + i * z.nlN,
+                  ext1 + i * z.extw, st);
+        for (size_t q = 0; q < n_in_rot; q++) {
+            launch_keyip(c, d_in_ks + q, 1, lv, st);
+            moddown_prepare(c, acc1 + (size_t)iorder[q] * z.accw, 1, lv, conv1 + (size_t)iorder[q] * z.ctw, st);
+        }
+        for (size_t r = 0; r < n_in_rot; r++) launch_combine(c, d_in_cb + r, 1, lv, st);
+    } else {
+        size_t i = 0;
+        while (i < n_mu) {  // consecutive runs of rotated inputs are converted together
+            size_t j = i + 1;
+            while (j < n_mu && p->modup_cts[j] == p->modup_cts[j - 1] + 1) j++;
+            modup(c, b_in + (size_t)p->modup_cts[i] * z.ctw + z.nlN, z.ctw, (int)(j - i), lv, coef1 + i * z.nlN,
+                  ext1 + i * z.extw, st);
+            i = j;
+        }
+        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), lv, st);
+        moddown_prepare(c, acc1, (int)n_in_rot, lv, conv1, st);
+        launch_combine(c, d_in_cb, (int)n_in_rot, lv, st);
+    }
+    c->cnt.rot += n_in_rot;
+    c->cnt.keyswitch += n_in_rot;
+
+    // ---- stage 2: groups without rotation, straight into the totals ----
+    for (int o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + (size_t)o * z.ctw, 0, z.ctw * 8, st));
+    if (mode == 0) {
+        for (size_t i = 0; i < n_base; i++)
+            for (int t = 0; t < macs[i].n_terms; t++) {
+                const MacTerm& tm = mterms[macs[i].term0 + t];
+                launch_pmult(c, tm.ct, tm.pt, macs[i].out, 1, lv, t > 0, st);
+            }
+    } else {
+        launch_mac(c, d_mac, d_terms, (int)n_base, lv, st);
+    }
+
+    // ---- stage 3: outer rotations in chunks, summed into the totals ----
+    for (size_t c0 = 0, ch = 0; c0 < order.size(); c0 += chunk, ch++) {
+        size_t c1 = std::min(order.size(), c0 + chunk);
+        int cn = (int)(c1 - c0);
+        if (mode == 0) {
+            for (size_t k = c0; k < c1; k++) {
+                const MacItem& m = macs[n_base + k];
+                for (int t = 0; t < m.n_terms; t++) {
+                    const MacTerm& tm = mterms[m.term0 + t];
+                    launch_pmult(c, tm.ct, tm.pt, m.out, 1, lv, t > 0, st);
+                }
+                size_t s = k - c0;
+                modup(c, Pd + s * z.ctw + z.nlN, z.ctw, 1, lv, coef3 + s * z.nlN, ext3 + s * z.extw, st);
+                launch_keyip(c, d_out_ks + k, 1, lv, st);
+                moddown_prepare(c, acc3 + s * z.accw, 1, lv, conv3 + s * z.ctw, st);
+            }
+            for (int si = 0; si < sum_range[ch].second; si++)
+                launch_combine_sum(c, d_sum + sum_range[ch].first + si, d_ent, 1, lv, st);
+        } else {
+            launch_mac(c, d_mac + n_base + c0, d_terms, cn, lv, st);
+            modup(c, Pd + z.nlN, z.ctw, cn, lv, coef3, ext3, st);
+            launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, lv, st);
+            moddown_prepare(c, acc3, cn, lv, conv3, st);
+            launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, sum_range[ch].second, lv, st);
+        }
+    }
+    c->cnt.rot += order.size();
+    c->cnt.keyswitch += order.size();
+    c->cnt.pmult += p->terms.size();
+
+    // ---- stage 4: rescale ----
+    if (mode == 0) {
+        for (int o = 0; o < p->n_out; o++)
+            rescale_batch(c, total + (size_t)o * z.ctw, 1, lv, b_out + (size_t)o * ct_words(c, lv - 1), rs_tmp,
+                          rs_lift, st);
+    } else {
+        rescale_batch(c, total, p->n_out, lv, b_out, rs_tmp, rs_lift, st);
+    }
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int fe_layout_make(const fe_ctx* c, fe_layout* l) {
+    if (!c || !l) return fail(FE_EINVAL, "null argument");
+    return layout_fill(c->N, l);
+}
+
+extern "C" int fe_fragment_pack(const fe_ctx* c, const fe_layout* lay, const double* x, double* slots,
+                                void* stream) {
+    if (!c || !lay || !x || !slots) return fail(FE_EINVAL, "null argument");
+    fe_layout L = *lay;
+    FE_TRY(layout_fill(c->N, &L));
+    k_pack<<<dim3((c->N / 2 + kB - 1) / kB, L.n_ct), kB, 0, (cudaStream_t)stream>>>(x, slots, L, c->N);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_fragment_unpack(const fe_ctx* c, const fe_layout* lay, const double* slots, double* y,
+                                  void* stream) {
+    if (!c || !lay || !slots || !y) return fail(FE_EINVAL, "null argument");
+    fe_layout L = *lay;
+    FE_TRY(layout_fill(c->N, &L));
+    size_t total = (size_t)L.BS * L.C * L.H * L.W;
+    k_unpack<<<(unsigned)((total + kB - 1) / kB), kB, 0, (cudaStream_t)stream>>>(slots, y, L, c->N);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+static void finish_plan(fe_plan* p) {
+    std::set<int32_t> st;
+    for (auto& in : p->inner) st.insert(in.step);
+    p->n_outer = 0;
+    for (auto& o : p->outs)
+        for (auto& g : o.groups)
+            if (g.step) {
+                st.insert(g.step);
+                p->n_outer++;
+            }
+    p->steps.assign(st.begin(), st.end());
+    p->modup_slot.assign(p->n_in, -1);
+    std::set<int> mu;
+    for (auto& in : p->inner) mu.insert(in.ci);
+    p->modup_cts.assign(mu.begin(), mu.end());
+    for (size_t i = 0; i < p->modup_cts.size(); i++) p->modup_slot[p->modup_cts[i]] = (int)i;
+}
+
+extern "C" int fe_plan_conv(fe_ctx* c, const fe_layout* in_lay, uint32_t Cout, uint32_t K, uint32_t stride,
+                            int depthwise, uint32_t in_period, uint32_t level, fe_layout* out_lay,
+                            fe_plan** out) {
+    if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
+    if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "conv needs a level to rescale");
+    if (K == 0 || Cout == 0 || (stride != 1 && stride != 2)) return fail(FE_EINVAL, "bad conv shape");
+    fe_layout L = *in_lay;
+    FE_TRY(layout_fill(c->N, &L));
+    if (K > L.H || K > L.W) return fail(FE_EINVAL, "kernel larger than the map");
+    if (stride == 2 && L.S % 2) return fail(FE_EINVAL, "stride 2 needs an even fragment size");
+    if (depthwise && Cout != L.C) return fail(FE_EINVAL, "depthwise conv keeps the channel count");
+    if (in_period && (L.cpc % in_period || L.C > in_period || L.groups != 1))
+        return fail(FE_EINVAL, "replicated input needs c_valid | cpc and one group");
+    std::unique_ptr<fe_plan> p(new fe_plan());
+    p->c = c;
+    p->kind = 0;
+    p->level = level;
+    p->lin = L;
+    p->Cin = L.C;
+    p->Cout = Cout;
+    p->K = K;
+    p->stride = stride;
+    p->depthwise = depthwise;
+    p->in_period = in_period;
+    fe_layout O{};
+    O.H = (L.H - K) / stride + 1;
+    O.W = (L.W - K) / stride + 1;
+    O.C = Cout;
+    O.BS = L.BS;
+    O.S = L.S / stride;
+    O.m = L.m;
+    FE_TRY(layout_fill(c->N, &O));
+    p->lout = O;
+    p->n_in = L.n_ct;
+    p->n_out = O.n_ct;
+    const int S = L.S, m = L.m, BS = L.BS, cpc = L.cpc, blk = m * m * BS;
+    const int G_in = in_period ? 1 : L.groups, G_out = O.groups;
+    auto offs = inner_offsets(S, K, stride);
+    std::map<std::tuple<int, int, int>, int> rslot;  // (ci, a, b) -> R slot
+    for (int g = 0; g < G_in; g++)
+        for (int u = 0; u < S; u++)
+            for (int v = 0; v < S; v++) {
+                int ci = (g * S + u) * S + v;
+                for (int a : offs[u])
+                    for (int bb : offs[v])
+                        if (a || bb) {
+                            rslot[std::make_tuple(ci, a, bb)] = (int)p->inner.size();
+                            p->inner.push_back({ci, (a * m + bb) * BS});
+                        }
+            }
+    auto spatial_ok = [&](int up, int extent) {
+        for (int bi = 0; bi < m; bi++) {
+            int hp = bi * S + up;
+            if (hp > extent - (int)K) break;
+            if (hp % stride == 0) return true;
+        }
+        return false;
+    };
+    p->outs.resize(p->n_out);
+    for (int h = 0; h < G_out; h++) {
+        std::vector<int> diags;
+        if (depthwise)
+            diags = {0};
+        else if (in_period)
+            for (uint32_t d = 0; d < in_period; d++) diags.push_back(d);
+        else {
+            std::set<int> ds;
+            for (uint32_t cc = 0; cc < L.C; cc++)
+                for (int ol = 0; ol < cpc; ol++)
+                    if (h * cpc + ol < (int)Cout) ds.insert((((int)(cc % cpc) - ol) % cpc + cpc) % cpc);
+            diags.assign(ds.begin(), ds.end());
+        }
+        for (int up = 0; up < S; up += stride)
+            for (int vp = 0; vp < S; vp += stride) {
+                int oi = (h * O.S + up / stride) * O.S + vp / stride;
+                fe_plan::Out& ou = p->outs[oi];
+                bool sp = spatial_ok(up, L.H) && spatial_ok(vp, L.W);
+                for (int d : diags) {
+                    fe_plan::Group grp{d ? d * blk : 0, (int)p->terms.size(), 0};
+                    for (int g = 0; g < G_in; g++) {
+                        // structurally nonzero: some channel pair and some valid output position
+                        bool chan = false;
+                        for (int cl = 0; cl < cpc && !chan; cl++) {
+                            int cc = in_period ? cl % (int)in_period : g * cpc + cl;
+                            if (!in_period && cc >= (int)L.C) continue;
+                            int o = h * cpc + ((cl - d) % cpc + cpc) % cpc;
+                            if (o >= (int)Cout) continue;
+                            if (depthwise && o != cc) continue;
+                            chan = true;
+                        }
+                        if (!chan || !sp) continue;
+                        for (uint32_t i = 0; i < K; i++)
+                            for (uint32_t j = 0; j < K; j++) {
+                                int u = (up + i) % S, a = (up + i) / S;
+                                int v = (vp + j) % S, bb = (vp + j) / S;
+                                int ci = (g * S + u) * S + v;
+                                int src = (a || bb) ? rslot.at(std::make_tuple(ci, a, bb)) : -(ci + 1);
+                                p->terms.push_back({src, p->n_pt});
+                                p->cpts.push_back({h, up, vp, d, g, (int)i, (int)j});
+                                p->n_pt++;
+                                grp.nt++;
+                            }
+                    }
+                    if (grp.nt) ou.groups.push_back(grp);
+                }
+            }
+    }
+    finish_plan(p.get());
+    if (out_lay) *out_lay = O;
+    *out = p.release();
+    return FE_OK;
+}
+
+extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat,
+                          uint32_t F_in, uint32_t F_out, uint32_t level, fe_plan** out) {
+    if (!c || !feat || !out) return fail(FE_EINVAL, "null argument");
+    if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "fc needs a level to rescale");
+    if ((uint64_t)P * BS != (uint64_t)c->N / 2 || (P & (P - 1)) || !n_in_ct || !F_out)
+        return fail(FE_EINVAL, "fc needs P BS = N/2 with P a power of two");
+    std::unique_ptr<fe_plan> p(new fe_plan());
+    p->c = c;
+    p->kind = 1;
+    p->level = level;
+    p->P = P;
+    p->BS = BS;
+    p->F_in = F_in;
+    p->F_out = F_out;
+    for (size_t i = 0; i < (size_t)n_in_ct * P; i++)
+        if (feat[i] >= (int)F_in) return fail(FE_EINVAL, "feature index out of range");
+    p->feat.assign(feat, feat + (size_t)n_in_ct * P);
+    int kbits = 0;
+    while ((1u << kbits) < P) kbits++;
+    p->n1 = 1 << ((kbits + 1) / 2);
+    p->n2 = P / p->n1;
+    p->n_in = n_in_ct;
+    const int T = (F_out + P - 1) / P;
+    p->n_out = T;
+    auto present = [&](int t, int cc, int gam, int beta) {
+        for (uint32_t q = 0; q < P; q++) {
+            int p0 = (((int)q - p->n1 * gam) % (int)P + (int)P) % (int)P;
+            int n = t * P + p0;
+            int f = p->feat[(size_t)cc * P + (q + beta) % P];
+            if (n < (int)F_out && f >= 0) return true;
+        }
+        return false;
+    };
+    std::map<std::pair<int, int>, int> rslot;
+    for (int cc = 0; cc < (int)n_in_ct; cc++) {
+        std::set<int> need;
+        for (int t = 0; t < T; t++)
+            for (int gam = 0; gam < p->n2; gam++)
+                for (int beta = 0; beta < p->n1; beta++)
+                    if (present(t, cc, gam, beta)) need.insert(beta);
+        for (int beta : need)
+            if (beta) {
+                rslot[{cc, beta}] = (int)p->inner.size();
+                p->inner.push_back({cc, beta * (int32_t)BS});
+            }
+    }
+    p->outs.resize(T);
+    for (int t = 0; t < T; t++) {
+        for (int gam = 0; gam < p->n2; gam++) {
+            fe_plan::Group grp{gam ? p->n1 * gam * (int32_t)BS : 0, (int)p->terms.size(), 0};
+            for (int cc = 0; cc < (int)n_in_ct; cc++)
+                for (int beta = 0; beta < p->n1; beta++)
+                    if (present(t, cc, gam, beta)) {
+                        int src = beta ? rslot.at({cc, beta}) : -(cc + 1);
+                        p->terms.push_back({src, p->n_pt});
+                        p->fpts.push_back({t, cc, gam, beta});
+                        p->n_pt++;
+                        grp.nt++;
+                    }
+            if (grp.nt) p->outs[t].groups.push_back(grp);
+        }
+    }
+    finish_plan(p.get());
+    *out = p.release();
+    return FE_OK;
+}
+
+extern "C" void fe_plan_destroy(fe_plan* p) { delete p; }
+
+extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
+    if (!p || !info) return fail(FE_EINVAL, "null argument");
+    const fe_ctx* c = p->c;
+    info->pt_bytes = (size_t)p->n_pt * (p->level + 1) * c->N * 8;
+    info->in_bytes = (size_t)p->n_in * ct_words(c, p->level) * 8;
+    info->out_bytes = (size_t)p->n_out * ct_words(c, p->level - 1) * 8;
+    // default: the whole outer stage in one chunk, unless its scratch exceeds 8 GiB
+    size_t chunk = std::max(1, p->n_outer);
+    while (chunk > 1 && plan_workspace(p, chunk) - plan_workspace(p, 1) > (8ull << 30)) chunk = (chunk + 1) / 2;
+    info->workspace_bytes = plan_workspace(p, chunk);
+    info->workspace_min_bytes = plan_workspace(p, 1);
+    info->n_in_ct = p->n_in;
+    info->n_out_ct = p->n_out;
+    info->n_pt = p->n_pt;
+    info->n_inner_rot = (uint32_t)p->inner.size();
+    info->n_outer_rot = p->n_outer;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_rotation_steps(const fe_plan* p, int32_t* steps, uint32_t max, uint32_t* n) {
+    if (!p || !n) return fail(FE_EINVAL, "null argument");
+    *n = (uint32_t)p->steps.size();
+    if (steps)
+        for (uint32_t i = 0; i < std::min<uint32_t>(max, *n); i++) steps[i] = p->steps[i];
+    return FE_OK;
+}
+
+extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host, double wmul, double w_scale,
+                                    void* pt_dev, void* stream) {
+    if (!c || !p || !W_host || !pt_dev) return fail(FE_EINVAL, "null argument");
+    if (p->n_pt == 0) return FE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = c->N, half = N / 2, nl = p->level + 1;
+    size_t wcount = p->kind == 0 ? (p->depthwise ? (size_t)p->Cin * p->K * p->K : (size_t)p->Cout * p->Cin * p->K * p->K)
+                                 : (size_t)p->F_out * p->F_in;
+    double* dW;
+    FE_CUDA_TRY(cudaMallocAsync(&dW, wcount * 8, st));
+    FE_CUDA_TRY(cudaMemcpyAsync(dW, W_host, wcount * 8, cudaMemcpyHostToDevice, st));
+    const int chunk = std::max(1, std::min(p->n_pt, (int)((64ull << 20) / ((size_t)half * 8))));
+    double* z;
+    void* descs;
+    int* dfeat = nullptr;
+    FE_CUDA_TRY(cudaMallocAsync(&z, (size_t)chunk * half * 8, st));
+    size_t dbytes = p->kind == 0 ? p->cpts.size() * sizeof(fe_plan::ConvPt) : p->fpts.size() * sizeof(fe_plan::FcPt);
+    FE_CUDA_TRY(cudaMallocAsync(&descs, std::max<size_t>(dbytes, 16), st));
+    if (p->kind == 0) {
+        FE_CUDA_TRY(cudaMemcpyAsync(descs, p->cpts.data(), dbytes, cudaMemcpyHostToDevice, st));
+    } else {
+        FE_CUDA_TRY(cudaMemcpyAsync(descs, p->fpts.data(), dbytes, cudaMemcpyHostToDevice, st));
+        FE_CUDA_TRY(cudaMallocAsync(&dfeat, p->feat.size() * sizeof(int), st));
+        FE_CUDA_TRY(cudaMemcpyAsync(dfeat, p->feat.data(), p->feat.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    int rc = FE_OK;
+    for (int s0 = 0; s0 < p->n_pt && rc == FE_OK; s0 += chunk) {
+        int cn = std::min(chunk, p->n_pt - s0);
+        if (p->kind == 0) {
+            ConvPtArgs a{(const fe_plan::ConvPt*)descs + s0, dW, wmul, (int)p->lin.S, (int)p->lin.m, (int)p->lin.BS,
+                         (int)p->lin.cpc, (int)p->lin.H, (int)p->lin.W, p->K, p->stride, p->Cin, p->Cout,
+                         p->depthwise, p->in_period};
+            k_conv_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
+        } else {
+            FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
+            k_fc_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
+        }
+        rc = encode_batch(c, z, cn, p->level, w_scale, (u64*)pt_dev + (size_t)s0 * nl * N, st);
+    }
+    cudaFreeAsync(dW, st);
+    cudaFreeAsync(z, st);
+    cudaFreeAsync(descs, st);
+    if (dfeat) cudaFreeAsync(dfeat, st);
+    FE_CUDA_TRY(cudaStreamSynchronize(st));
+    return rc;
+}
+
+extern "C" int fe_he_conv(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
+                          void* out_dev, void* ws, size_t ws_bytes, int mode, void* stream) {
+    if (!c || !evk || !p || !pt_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (p->kind != 0) return fail(FE_EINVAL, "not a conv plan");
+    return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
+                    (cudaStream_t)stream, 3);
+}
+
+extern "C" int fe_he_fc(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
+                        void* out_dev, void* ws, size_t ws_bytes, int mode, void* stream) {
+    if (!c || !evk || !p || !pt_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (p->kind != 1) return fail(FE_EINVAL, "not an fc plan");
+    return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
+                    (cudaStream_t)stream, 3);
+}

@@ -1,0 +1,399 @@
+// Element-wise and key-switching kernels.
+//
+// All kernels stream limb-major data with one thread per coefficient and
+// coalesced 8-byte accesses; products of two residues are accumulated in
+// 128 bits and reduced once (Barrett, 2^128 / q) per output word.
+#include "kernels.cuh"
+
+namespace fe {
+
+namespace {
+constexpr int kB = 256;
+
+inline dim3 grid_for(int N, int y, int z = 1) { return dim3((N + kB - 1) / kB, y, z); }
+
+// ------------------------------------------------------------------------
+// Base conversion with centred digits (see BConvTab).
+// One thread per (coefficient, polynomial).
+// ------------------------------------------------------------------------
+__global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int logN,
+                        const u64* in, size_t in_stride, int in_pos_base, u64* out,
+                        size_t out_stride, int copy_src) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u64* ip = in + blockIdx.y * in_stride;
+    u64* op = out + blockIdx.y * out_stride;
+    u64 y[8];
+    int neg = 0;
+    for (int i = 0; i < t.n_src; i++) {
+        int mi = t.src[i];
+        u64 b = mods[mi].q;
+        u64 x = ip[((size_t)(ext_pos(mi, L, level) - in_pos_base) << logN) + n];
+        if (copy_src) op[((size_t)ext_pos(mi, L, level) << logN) + n] = x;
+        u64 v = mul_shoup(x, t.inv[i], t.inv_sh[i], b);
+        y[i] = v;
+        neg += v > (b >> 1);
+    }
+    for (int d = 0; d < t.n_dst; d++) {
+        int mt = t.dst[d];
+        u128 acc = (u128)t.negB[d] * (u64)neg;
+        for (int i = 0; i < t.n_src; i++) acc += (u128)y[i] * t.mat[d * t.n_src + i];
+        op[((size_t)ext_pos(mt, L, level) << logN) + n] = reduce128(acc, mods[mt]);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Evaluation-key inner product:
+//   acc_b[p][n] = sum_j ext_j[p][n] * key_j.b[kl(p)][n],  acc_a likewise,
+// over the positions p of Q_level * P.  blockIdx.y = position, z = item.
+// ------------------------------------------------------------------------
+__global__ void k_keyip(const KsItem* items, const Modulus* mods, int L, int level, int k,
+                        int logN, int n_mod) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const KsItem it = items[blockIdx.z];
+    const int p = blockIdx.y;
+    const int np = level + 1 + k;
+    const int mi = p <= level ? p : L + 1 + (p - level - 1);
+    const int dnum = (level + 1 + k - 1) / k;
+    const Modulus m = mods[mi];
+    u128 ab = 0, aa = 0;
+    for (int j = 0; j < dnum; j++) {
+        u64 e = it.ext[((size_t)(j * np + p) << logN) + n];
+        const u64* kb = it.key + ((size_t)(j * 2 * n_mod + mi) << logN);
+        const u64* ka = kb + ((size_t)n_mod << logN);
+        ab += (u128)e * kb[n];
+        aa += (u128)e * ka[n];
+    }
+    it.acc[((size_t)p << logN) + n] = reduce128(ab, m);
+    it.acc[((size_t)(np + p) << logN) + n] = reduce128(aa, m);
+}
+
+// key-stationary form: blockIdx.z = group of items that share one key
+__global__ void k_keyip_grouped(const KsGroup* groups, const KsItem* items, const Modulus* mods,
+                                int L, int level, int k, int logN, int n_mod) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const KsGroup gr = groups[blockIdx.z];
+    const int p = blockIdx.y;
+    const int np = level + 1 + k;
+    const int mi = p <= level ? p : L + 1 + (p - level - 1);
+    const int dnum = (level + 1 + k - 1) / k;
+    const Modulus m = mods[mi];
+    u64 kb[16], ka[16];
+    for (int j = 0; j < dnum; j++) {
+        const u64* b = gr.key + ((size_t)(j * 2 * n_mod + mi) << logN);
+        kb[j] = b[n];
+        ka[j] = b[((size_t)n_mod << logN) + n];
+    }
+    for (int t = 0; t < gr.n_items; t++) {
+        const KsItem it = items[gr.item0 + t];
+        u128 ab = 0, aa = 0;
+        for (int j = 0; j < dnum; j++) {
+            u64 e = it.ext[((size_t)(j * np + p) << logN) + n];
+            ab += (u128)e * kb[j];
+            aa += (u128)e * ka[j];
+        }
+        it.acc[((size_t)p << logN) + n] = reduce128(ab, m);
+        it.acc[((size_t)(np + p) << logN) + n] = reduce128(aa, m);
+    }
+}
+
+// ------------------------------------------------------------------------
+// ModDown combine + automorphism + optional add / accumulate (see CombineItem).
+// blockIdx.y = limb i of Q_level, z = item.
+// ------------------------------------------------------------------------
+__global__ void k_combine(const CombineItem* items, const Modulus* mods, const u64* pinv,
+                          const u64* pinv_sh, int level, int k, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const CombineItem it = items[blockIdx.z];
+    const int i = blockIdx.y;
+    const int np = level + 1 + k, nq = level + 1;
+    const u64 q = mods[i].q;
+    const uint32_t src = it.galois == 1 ? (uint32_t)n : galois_perm(n, it.galois, logN);
+    const size_t so = ((size_t)i << logN) + src;
+    u64 vb = sub_mod(it.acc[so], it.conv[so], q);
+    u64 va = sub_mod(it.acc[((size_t)np << logN) + so], it.conv[((size_t)nq << logN) + so], q);
+    vb = mul_shoup(vb, pinv[i], pinv_sh[i], q);
+    va = mul_shoup(va, pinv[i], pinv_sh[i], q);
+    if (it.add0) vb = add_mod(vb, it.add0[so], q);
+    if (it.add1) va = add_mod(va, it.add1[so], q);
+    const size_t oo = ((size_t)i << logN) + n;
+    u64* o0 = it.out + oo;
+    u64* o1 = it.out + ((size_t)nq << logN) + oo;
+    if (it.accumulate) {
+        *o0 = add_mod(*o0, vb, q);
+        *o1 = add_mod(*o1, va, q);
+    } else {
+        *o0 = vb;
+        *o1 = va;
+    }
+}
+
+__global__ void k_combine_sum(const SumItem* items, const SumEntry* entries, const Modulus* mods,
+                              const u64* pinv, const u64* pinv_sh, int level, int k, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const SumItem it = items[blockIdx.z];
+    const int i = blockIdx.y;
+    const int np = level + 1 + k, nq = level + 1;
+    const u64 q = mods[i].q;
+    const size_t oo = ((size_t)i << logN) + n, oo1 = ((size_t)nq << logN) + oo;
+    u64 v0 = 0, v1 = 0;
+    if (it.base) {
+        v0 = it.base[oo];
+        v1 = it.base[oo1];
+    }
+    for (int e = 0; e < it.n_e; e++) {
+        const SumEntry en = entries[it.e0 + e];
+        const uint32_t src = galois_perm(n, en.galois, logN);
+        const size_t so = ((size_t)i << logN) + src;
+        u64 vb = sub_mod(en.acc[so], en.conv[so], q);
+        u64 va = sub_mod(en.acc[((size_t)np << logN) + so], en.conv[((size_t)nq << logN) + so], q);
+        vb = add_mod(mul_shoup(vb, pinv[i], pinv_sh[i], q), en.add0[so], q);
+        va = mul_shoup(va, pinv[i], pinv_sh[i], q);
+        v0 = add_mod(v0, vb, q);
+        v1 = add_mod(v1, va, q);
+    }
+    if (it.accumulate) {
+        v0 = add_mod(v0, it.out[oo], q);
+        v1 = add_mod(v1, it.out[oo1], q);
+    }
+    it.out[oo] = v0;
+    it.out[oo1] = v1;
+}
+
+// ------------------------------------------------------------------------
+// PMult-MAC: out[poly][i][n] = sum_terms ct[poly][i][n] * pt[i][n]
+// blockIdx.y = limb i, z = item.  Partial sums stay in 128 bits and are
+// reduced every 16 terms (products of < 2^61 residues are < 2^122).
+// ------------------------------------------------------------------------
+__global__ void k_mac(const MacItem* items, const MacTerm* terms, const Modulus* mods, int level,
+                      int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const MacItem it = items[blockIdx.z];
+    const int i = blockIdx.y, nq = level + 1;
+    const Modulus m = mods[i];
+    const size_t o0 = ((size_t)i << logN) + n, o1 = ((size_t)(nq + i) << logN) + n;
+    u128 s0 = 0, s1 = 0;
+    for (int t = 0; t < it.n_terms; t++) {
+        const MacTerm tm = terms[it.term0 + t];
+        u64 p = tm.pt[o0];
+        s0 += (u128)tm.ct[o0] * p;
+        s1 += (u128)tm.ct[o1] * p;
+        if ((t & 15) == 15) {
+            s0 = reduce128(s0, m);
+            s1 = reduce128(s1, m);
+        }
+    }
+    it.out[o0] = reduce128(s0, m);
+    it.out[o1] = reduce128(s1, m);
+}
+
+__global__ void k_rescale_combine(const u64* in, const u64* lift, u64* out, const Modulus* mods,
+                                  const u64* qlinv, const u64* qlinv_sh, int level, int L,
+                                  int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.y, poly = blockIdx.z;  // poly over n_ct * 2
+    const u64 q = mods[i].q;
+    const u64* ip = in + (size_t)poly * (level + 1) * N;
+    const u64* lp = lift + (size_t)poly * level * N;
+    u64* op = out + (size_t)poly * level * N;
+    u64 v = sub_mod(ip[((size_t)i << logN) + n], lp[((size_t)i << logN) + n], q);
+    const size_t ti = (size_t)level * (L + 1) + i;
+    op[((size_t)i << logN) + n] = mul_shoup(v, qlinv[ti], qlinv_sh[ti], q);
+}
+
+__global__ void k_add(const u64* a, const u64* b, u64* out, const Modulus* mods, int nl, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int limb = blockIdx.y;  // over the 2 (l+1) limbs of one ciphertext
+    const u64 q = mods[limb % nl].q;
+    const size_t o = ((size_t)blockIdx.z * gridDim.y + limb) * N + n;
+    out[o] = add_mod(a[o], b[o], q);
+}
+
+__global__ void k_pmult(const u64* ct, const u64* pt, u64* out, const Modulus* mods, int nl,
+                        int logN, int accumulate) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.y, ci = blockIdx.z;  // limb, ciphertext
+    const Modulus m = mods[i];
+    const u64 p = pt[((size_t)ci * nl + i) * N + n];
+    for (int poly = 0; poly < 2; poly++) {
+        const size_t o = (((size_t)ci * 2 + poly) * nl + i) * N + n;
+        u64 v = mul_mod(ct[o], p, m);
+        out[o] = accumulate ? add_mod(out[o], v, m.q) : v;
+    }
+}
+
+// (x0, x1) (x) (y0, y1) -> d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1 ([3][l+1][N] per ct)
+__global__ void k_tensor(const u64* x, const u64* y, u64* d, const Modulus* mods, int nl, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.y, ci = blockIdx.z;
+    const Modulus m = mods[i];
+    const size_t b = (size_t)ci * 2 * nl * N, o = (size_t)i * N + n, s = (size_t)nl * N;
+    u64 x0 = x[b + o], x1 = x[b + s + o], y0 = y[b + o], y1 = y[b + s + o];
+    const size_t db = (size_t)ci * 3 * nl * N;
+    d[db + o] = mul_mod(x0, y0, m);
+    d[db + s + o] = reduce128((u128)reduce128((u128)x0 * y1, m) + (u128)x1 * y0, m);
+    d[db + 2 * s + o] = mul_mod(x1, y1, m);
+}
+
+// ------------------------------------------------------------------------
+// Counter-based generator: SplitMix64 (Steele, Lea, Flood 2014).
+// word(seed, tag, n) = mix(mix(seed + (tag+1) g) + (n+1) g), g = 0x9E3779B97F4A7C15.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ u64 sm_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 stream_word(u64 seed, u64 tag, u64 n) {
+    const u64 g = 0x9E3779B97F4A7C15ull;
+    return sm_mix(sm_mix(seed + (tag + 1) * g) + (n + 1) * g);
+}
+
+__global__ void k_sample_uniform(u64 seed, u64 tag_base, u64* out, const int* mod_idx,
+                                 const Modulus* mods, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    const int mi = mod_idx[l];
+    const u64 w = stream_word(seed, tag_base + (u64)mi, (u64)n);
+    out[((size_t)l << logN) + n] = (u64)(((u128)w * mods[mi].q) >> 64);
+}
+
+// kind 0: ternary floor(3 w / 2^64) - 1; kind 1: centred binomial eta = 21
+__global__ void k_sample_signed(u64 seed, u64 tag, int kind, i64* out, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u64 w = stream_word(seed, tag, (u64)n);
+    if (kind == 0)
+        out[n] = (i64)(((u128)w * 3u) >> 64) - 1;
+    else
+        out[n] = (i64)__popcll(w & 0x1FFFFFull) - (i64)__popcll((w >> 21) & 0x1FFFFFull);
+}
+
+__global__ void k_signed_to_limbs(const i64* v, u64* out, const Modulus* mods, int first_mod,
+                                  size_t stride, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    out[(size_t)l * stride + n] = from_signed(v[n], mods[first_mod + l].q);
+}
+
+}  // namespace
+
+void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t in_stride,
+                  int in_pos_base, u64* out, size_t out_stride, int n_poly, bool copy_src,
+                  cudaStream_t st) {
+    if (n_poly == 0) return;
+    k_bconv<<<grid_for(c->N, n_poly), kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,
+                                                   in_pos_base, out, out_stride, copy_src ? 1 : 0);
+    c->cnt.launches++;
+}
+
+void launch_keyip(fe_ctx* c, const KsItem* items, int n_items, int level, cudaStream_t st) {
+    if (!n_items) return;
+    k_keyip<<<grid_for(c->N, level + 1 + c->k, n_items), kB, 0, st>>>(items, c->d_mod, c->L, level,
+                                                                     c->k, c->logN, c->n_mod);
+    c->cnt.launches++;
+}
+
+void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items, int n_groups,
+                          int level, cudaStream_t st) {
+    if (!n_groups) return;
+    k_keyip_grouped<<<grid_for(c->N, level + 1 + c->k, n_groups), kB, 0, st>>>(
+        groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod);
+    c->cnt.launches++;
+}
+
+void launch_combine(fe_ctx* c, const CombineItem* items, int n_items, int level, cudaStream_t st) {
+    if (!n_items) return;
+    k_combine<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, c->d_mod, c->d_pinv,
+                                                                c->d_pinv_sh, level, c->k, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_combine_sum(fe_ctx* c, const SumItem* items, const SumEntry* entries, int n_items,
+                        int level, cudaStream_t st) {
+    if (!n_items) return;
+    k_combine_sum<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(
+        items, entries, c->d_mod, c->d_pinv, c->d_pinv_sh, level, c->k, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int level,
+                cudaStream_t st) {
+    if (!n_items) return;
+    k_mac<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, terms, c->d_mod, level, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
+                            int level, cudaStream_t st) {
+    k_rescale_combine<<<grid_for(c->N, level, 2 * n_ct), kB, 0, st>>>(
+        in, lift, out, c->d_mod, c->d_qlinv, c->d_qlinv_sh, level, c->L, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,
+                cudaStream_t st) {
+    if (!n_ct) return;
+    k_add<<<grid_for(c->N, 2 * (level + 1), n_ct), kB, 0, st>>>(a, b, out, c->d_mod, level + 1, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_pmult(fe_ctx* c, const u64* ct, const u64* pt, u64* out, int n_ct, int level,
+                  bool accumulate, cudaStream_t st) {
+    if (!n_ct) return;
+    k_pmult<<<grid_for(c->N, level + 1, n_ct), kB, 0, st>>>(ct, pt, out, c->d_mod, level + 1, c->logN,
+                                                           accumulate ? 1 : 0);
+    c->cnt.launches++;
+}
+
+void launch_tensor(fe_ctx* c, const u64* x, const u64* y, u64* d012, int n_ct, int level,
+                   cudaStream_t st) {
+    if (!n_ct) return;
+    k_tensor<<<grid_for(c->N, level + 1, n_ct), kB, 0, st>>>(x, y, d012, c->d_mod, level + 1, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_sample_uniform_limbs(fe_ctx* c, uint64_t seed, uint64_t tag_base, u64* out, int n_limbs,
+                                 const int* mod_idx_dev, cudaStream_t st) {
+    k_sample_uniform<<<grid_for(c->N, n_limbs), kB, 0, st>>>(seed, tag_base, out, mod_idx_dev, c->d_mod,
+                                                            c->logN);
+    c->cnt.launches++;
+}
+
+void launch_sample_signed(fe_ctx* c, uint64_t seed, uint64_t tag, int kind, i64* out, cudaStream_t st) {
+    k_sample_signed<<<grid_for(c->N, 1), kB, 0, st>>>(seed, tag, kind, out, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_signed_to_limbs(fe_ctx* c, const i64* v, u64* out, int first_mod, int n_limbs,
+                            size_t out_stride_words, cudaStream_t st) {
+    k_signed_to_limbs<<<grid_for(c->N, n_limbs), kB, 0, st>>>(v, out, c->d_mod, first_mod,
+                                                             out_stride_words, c->logN);
+    c->cnt.launches++;
+}
+
+}  // namespace fe

@@ -1,0 +1,107 @@
+// Element-wise and key-switching kernels (declarations shared by the op files).
+#pragma once
+
+#include "context.h"
+
+namespace fe {
+
+// position of modulus `mi` inside a polynomial over Q_level * P
+__host__ __device__ __forceinline__ int ext_pos(int mi, int L, int level) {
+    return mi <= L ? mi : mi - (L - level);
+}
+
+// NTT-domain index of the automorphism sigma_g: NTT(sigma_g a)[n] = NTT(a)[perm(n)]
+// with 2 brv(perm(n)) + 1 = (2 brv(n) + 1) g mod 2N.
+__device__ __forceinline__ uint32_t galois_perm(uint32_t n, uint32_t g, int logN) {
+    uint32_t br = __brev(n) >> (32 - logN);
+    uint64_t e = ((2ull * br + 1ull) * g) & ((2ull << logN) - 1ull);
+    uint32_t j = (uint32_t)((e - 1) >> 1);
+    return __brev(j) >> (32 - logN);
+}
+
+// One key-switch work item: ext digits -> accumulators over Q_l * P.
+struct KsItem {
+    const u64* ext;  // [dnum_l][l+1+k][N]
+    const u64* key;  // [dnum_L][2][n_mod][N]
+    u64* acc;        // [2][l+1+k][N]
+};
+// Items sharing one key: each thread reads the key once and applies it to all of them.
+struct KsGroup {
+    const u64* key;
+    int item0, n_items;
+};
+
+// One ModDown/combine item: acc (NTT, [2][l+1+k][N]) and its converted P part
+// (conv, NTT form on Q_l, [2][l+1][N]) ->
+//   out0[n] (+)= add0[perm(n)] + (acc_b - conv_b)[perm(n)] P^-1
+//   out1[n] (+)= add1[perm(n)] + (acc_a - conv_a)[perm(n)] P^-1
+struct CombineItem {
+    const u64* acc;
+    const u64* conv;
+    const u64* add0;  // [l+1][N] or null
+    const u64* add1;  // [l+1][N] or null
+    u64* out;         // [2][l+1][N]
+    uint32_t galois;  // 1 = no automorphism
+    int accumulate;   // 1: out += result
+};
+
+// Summed combine (rotate-and-sum over diagonals): for one output ciphertext,
+//   out0[n] (+)= base0[n] + sum_e ( add0_e[perm_e(n)] + (acc_b - conv_b)_e[perm_e(n)] P^-1 )
+//   out1[n] (+)= base1[n] + sum_e (acc_a - conv_a)_e[perm_e(n)] P^-1
+struct SumEntry {
+    const u64* acc;   // [2][l+1+k][N]
+    const u64* conv;  // [2][l+1][N]
+    const u64* add0;  // [l+1][N] (c0 of the rotated ciphertext)
+    uint32_t galois;
+};
+struct SumItem {
+    u64* out;         // [2][l+1][N]
+    const u64* base;  // [2][l+1][N] or null
+    int e0, n_e;
+    int accumulate;
+};
+
+// PMult-MAC item: out = sum_t ct_t (x) pt_t over `n_terms` consecutive terms
+struct MacItem {
+    u64* out;  // [2][l+1][N]
+    int term0, n_terms;
+};
+struct MacTerm {
+    const u64* ct;  // [2][l+1][N]
+    const u64* pt;  // [l+1][N]
+};
+
+// Base conversion of n_poly polynomials: source modulus src[i] is read at position
+// ext_pos(src[i]) - in_pos_base of an input polynomial (stride in_stride words),
+// destination dst[d] is written at position ext_pos(dst[d]) of an output polynomial;
+// copy_src also copies the source limbs to their output positions.
+void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t in_stride,
+                  int in_pos_base, u64* out, size_t out_stride, int n_poly, bool copy_src,
+                  cudaStream_t st);
+void launch_keyip(fe_ctx* c, const KsItem* items_dev, int n_items, int level, cudaStream_t st);
+void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups_dev, const KsItem* items_dev,
+                          int n_groups, int level, cudaStream_t st);
+void launch_combine(fe_ctx* c, const CombineItem* items_dev, int n_items, int level,
+                    cudaStream_t st);
+void launch_combine_sum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev,
+                        int n_items, int level, cudaStream_t st);
+void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
+                int level, cudaStream_t st);
+void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
+                            int level, cudaStream_t st);
+void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,
+                cudaStream_t st);
+void launch_pmult(fe_ctx* c, const u64* ct, const u64* pt, u64* out, int n_ct, int level,
+                  bool accumulate, cudaStream_t st);
+void launch_tensor(fe_ctx* c, const u64* x, const u64* y, u64* d012, int n_ct, int level,
+                   cudaStream_t st);
+
+// sampling (counter-based SplitMix64 words)
+void launch_sample_uniform_limbs(fe_ctx* c, uint64_t seed, uint64_t tag_base, u64* out,
+                                 int n_limbs, const int* mod_idx_dev, cudaStream_t st);
+void launch_sample_signed(fe_ctx* c, uint64_t seed, uint64_t tag, int kind, i64* out,
+                          cudaStream_t st);
+void launch_signed_to_limbs(fe_ctx* c, const i64* v, u64* out, int first_mod, int n_limbs,
+                            size_t out_stride_words, cudaStream_t st);
+
+}  // namespace fe

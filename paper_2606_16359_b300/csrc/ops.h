@@ -1,0 +1,44 @@
+// Batched scheme operations used by the layer code.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace fe {
+
+// random-stream addresses of the generator: tag = kind << 56 | object << 24 | digit << 8 | limb
+enum : uint64_t { kTagSk = 1, kTagCtA = 2, kTagCtE = 3, kTagKeyA = 4, kTagKeyE = 5 };
+inline uint64_t make_tag(uint64_t kind, uint64_t obj, uint64_t digit, uint64_t limb) {
+    return (kind << 56) | (obj << 24) | (digit << 8) | limb;
+}
+
+inline int dnum_at(const fe_ctx* c, int level) { return (level + 1 + c->k - 1) / c->k; }
+inline size_t ext_words(const fe_ctx* c, int level) {
+    return (size_t)dnum_at(c, level) * (level + 1 + c->k) * c->N;
+}
+inline size_t acc_words(const fe_ctx* c, int level) { return 2 * (size_t)(level + 1 + c->k) * c->N; }
+inline size_t ct_words(const fe_ctx* c, int level) { return 2 * (size_t)(level + 1) * c->N; }
+
+// ModUp of n polynomials at `level` (each l+1 limbs, NTT form, poly stride src_stride words):
+// coef receives their inverse NTTs ([n][l+1][N]); ext receives the extended digits
+// ([n][dnum][l+1+k][N], NTT form).
+void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* coef, u64* ext,
+           cudaStream_t st);
+// ModDown preparation for n accumulators acc [n][2][l+1+k][N] (NTT form): the P limbs are
+// inverse-transformed in place, converted to Q_level into conv [n][2][l+1][N] and transformed.
+void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
+// Rescale n ciphertexts in -> out (level -> level - 1); tmp: [2n][N], lift: [2n][level][N].
+void rescale_batch(fe_ctx* c, const u64* in, int n, int level, u64* out, u64* tmp, u64* lift,
+                   cudaStream_t st);
+size_t rescale_tmp_words(const fe_ctx* c, int n, int level);
+
+const u64* evk_key(const fe_evk* evk, uint32_t galois);
+
+// upload a host vector into a device region carved from a workspace
+template <class T>
+int upload(const std::vector<T>& v, T* dst, cudaStream_t st) {
+    if (v.empty()) return FE_OK;
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return FE_OK;
+}
+
+}  // namespace fe

@@ -1,0 +1,408 @@
+// Host-side parameter generation: NTT-friendly primes, psi, NTT twiddle tables,
+// base-conversion tables, the encoder's slot maps and its double-double roots.
+#include <quadmath.h>
+#include <string.h>
+
+#include <algorithm>
+#include <thread>
+
+#include "context.h"
+
+namespace fe {
+
+static thread_local std::string g_err = "no error";
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+const char* last_error() { return g_err.c_str(); }
+
+u64 h_mulmod(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+u64 h_powmod(u64 a, u64 e, u64 q) {
+    u64 acc = 1 % q, base = a % q;
+    for (; e; e >>= 1, base = h_mulmod(base, base, q))
+        if (e & 1) acc = h_mulmod(acc, base, q);
+    return acc;
+}
+// extended Euclid on signed 128-bit integers
+u64 h_invmod(u64 a, u64 q) {
+    i128 t = 0, nt = 1, r = q, nr = a % q;
+    while (nr) {
+        i128 qq = r / nr, tmp;
+        tmp = t - qq * nt;
+        t = nt;
+        nt = tmp;
+        tmp = r - qq * nr;
+        r = nr;
+        nr = tmp;
+    }
+    if (t < 0) t += q;
+    return (u64)t;
+}
+u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+Modulus make_modulus(u64 q) {
+    // floor(2^128 / q) = floor((2^128 - 1) / q) for q not a power of two
+    u128 r = (~(u128)0) / q;
+    Modulus m;
+    m.q = q;
+    m.ratio_hi = (u64)(r >> 64);
+    m.ratio_lo = (u64)r;
+    return m;
+}
+
+// Miller-Rabin with the first twelve primes as witnesses (exact for 64-bit n).
+static bool probably_prime(u64 n) {
+    if (n < 4) return n >= 2;
+    if (!(n & 1)) return false;
+    u64 d = n - 1;
+    int r = __builtin_ctzll(d);
+    d >>= r;
+    for (u64 a : {2ULL, 3ULL, 5ULL, 7ULL, 11ULL, 13ULL, 17ULL, 19ULL, 23ULL, 29ULL, 31ULL, 37ULL}) {
+        if (a % n == 0) continue;
+        u64 x = h_powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int i = 1; i < r && witness; i++) {
+            x = h_mulmod(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+// primes p = 1 mod 2N below 2^bits, descending, skipping the given ones
+static std::vector<u64> prime_run(int logN, int bits, int count, const std::vector<u64>& skip) {
+    std::vector<u64> out;
+    u64 step = (u64)2 << logN;
+    for (u64 c = ((u64)1 << bits) + 1 - step; (int)out.size() < count && c > step; c -= step) {
+        if (std::find(skip.begin(), skip.end(), c) != skip.end()) continue;
+        if (probably_prime(c)) out.push_back(c);
+    }
+    return out;
+}
+
+// smallest primitive 2N-th root of unity: take a generator g of Z_q^*, set
+// w = g^((q-1)/2N) (a primitive 2N-th root), and minimise over its odd powers.
+static u64 min_primitive_root_2N(u64 q, int logN) {
+    u64 m = q - 1;
+    std::vector<u64> fac;
+    u64 t = m;
+    for (u64 f = 2; f * f <= t; f += (f == 2 ? 1 : 2)) {
+        if (t % f == 0) {
+            fac.push_back(f);
+            while (t % f == 0) t /= f;
+        }
+    }
+    if (t > 1) fac.push_back(t);
+    u64 g = 2;
+    for (;; g++) {
+        bool gen = true;
+        for (u64 f : fac)
+            if (h_powmod(g, m / f, q) == 1) {
+                gen = false;
+                break;
+            }
+        if (gen) break;
+    }
+    u64 twoN = (u64)2 << logN;
+    u64 w = h_powmod(g, m / twoN, q), w2 = h_mulmod(w, w, q), cur = w, best = w;
+    for (u64 i = 0; i < twoN / 2; i++) {
+        best = std::min(best, cur);
+        cur = h_mulmod(cur, w2, q);
+    }
+    return best;
+}
+
+static u64 bitrev(u64 x, int bits) {
+    u64 r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+uint32_t fe_ctx::galois(int32_t r) const {
+    int64_t half = N / 2;
+    int64_t rr = ((int64_t)r % half + half) % half;
+    return (uint32_t)h_powmod(5, (u64)rr, (u64)2 * N);
+}
+
+namespace {
+
+struct PoolBuilder {
+    std::vector<char> host;
+    size_t put(const void* src, size_t bytes) {
+        size_t off = (host.size() + 255) & ~(size_t)255;
+        host.resize(off + bytes);
+        if (bytes) memcpy(host.data() + off, src, bytes);
+        return off;
+    }
+};
+
+struct TabOffsets {
+    size_t src, dst, inv, inv_sh, mat, negB;
+    int n_src, n_dst;
+};
+
+TabOffsets build_tab(PoolBuilder& pb, const std::vector<u64>& mod, const std::vector<int>& src,
+                     const std::vector<int>& dst) {
+    TabOffsets o;
+    o.n_src = (int)src.size();
+    o.n_dst = (int)dst.size();
+    std::vector<u64> inv, inv_sh, mat, negB;
+    for (int i : src) {
+        u64 b = mod[i], bhat = 1;  // (B / b_i) mod b_i
+        for (int i2 : src)
+            if (i2 != i) bhat = h_mulmod(bhat, mod[i2] % b, b);
+        u64 iv = h_invmod(bhat, b);
+        inv.push_back(iv);
+        inv_sh.push_back(shoup_of(iv, b));
+    }
+    for (int t : dst)  // destination-major, so a table truncates to its first destinations
+        for (int i : src) {
+            u64 mt = mod[t], v = 1;
+            for (int i2 : src)
+                if (i2 != i) v = h_mulmod(v, mod[i2] % mt, mt);
+            mat.push_back(v);
+        }
+    for (int t : dst) {
+        u64 mt = mod[t], B = 1;
+        for (int i : src) B = h_mulmod(B, mod[i] % mt, mt);
+        negB.push_back((mt - B) % mt);
+    }
+    o.src = pb.put(src.data(), src.size() * sizeof(int));
+    o.dst = pb.put(dst.data(), dst.size() * sizeof(int));
+    o.inv = pb.put(inv.data(), inv.size() * 8);
+    o.inv_sh = pb.put(inv_sh.data(), inv_sh.size() * 8);
+    o.mat = pb.put(mat.data(), mat.size() * 8);
+    o.negB = pb.put(negB.data(), negB.size() * 8);
+    return o;
+}
+
+BConvTab resolve(const TabOffsets& o, char* base) {
+    BConvTab t;
+    t.n_src = o.n_src;
+    t.n_dst = o.n_dst;
+    t.src = (const int*)(base + o.src);
+    t.dst = (const int*)(base + o.dst);
+    t.inv = (const u64*)(base + o.inv);
+    t.inv_sh = (const u64*)(base + o.inv_sh);
+    t.mat = (const u64*)(base + o.mat);
+    t.negB = (const u64*)(base + o.negB);
+    return t;
+}
+
+}  // namespace
+
+extern "C" const char* fe_last_error(void) { return fe::last_error(); }
+
+extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
+    if (!p || !out) return fail(FE_EINVAL, "null argument");
+    if (p->logN < 4 || p->logN > 17 || p->n_q < 1 || p->k < 1 || p->k > 8 || p->qbits > 61 ||
+        p->pbits > 61 || p->qbits < p->logN + 2 || p->pbits < p->logN + 2)
+        return fail(FE_EINVAL, "parameter set out of range");
+    std::unique_ptr<fe_ctx> c(new fe_ctx());
+    c->prm = *p;
+    c->logN = p->logN;
+    c->N = 1 << p->logN;
+    c->L = p->n_q - 1;
+    c->k = p->k;
+    c->n_mod = p->n_q + p->k;
+    c->dnum = (p->n_q + p->k - 1) / p->k;
+    memset(&c->cnt, 0, sizeof(c->cnt));
+    c->mod = prime_run(c->logN, p->qbits, p->n_q, {});
+    if ((int)c->mod.size() != (int)p->n_q) return fail(FE_EINVAL, "not enough ciphertext primes");
+    std::vector<u64> sp = prime_run(c->logN, p->pbits, p->k, c->mod);
+    if ((int)sp.size() != (int)p->k) return fail(FE_EINVAL, "not enough special primes");
+    c->mod.insert(c->mod.end(), sp.begin(), sp.end());
+
+    int dev;
+    FE_CUDA_TRY(cudaGetDevice(&dev));
+    FE_CUDA_TRY(cudaGetDeviceProperties(&c->prop, dev));
+    c->n_sm = c->prop.multiProcessorCount;
+
+    const int N = c->N, nm = c->n_mod;
+    c->psi.resize(nm);
+    {
+        std::vector<std::thread> th;
+        for (int i = 0; i < nm; i++)
+            th.emplace_back([&, i] { c->psi[i] = min_primitive_root_2N(c->mod[i], c->logN); });
+        for (auto& t : th) t.join();
+    }
+    std::vector<u64> tw((size_t)nm * N), tw_sh((size_t)nm * N), itw((size_t)nm * N),
+        itw_sh((size_t)nm * N);
+    std::vector<u64> ninv(nm), ninv_sh(nm), pinv(nm, 0), pinv_sh(nm, 0);
+    {
+        std::vector<std::thread> th;
+        for (int i = 0; i < nm; i++)
+            th.emplace_back([&, i] {
+                u64 q = c->mod[i], w = c->psi[i], wi = h_invmod(w, q);
+                std::vector<u64> pw(N), pwi(N);
+                pw[0] = 1;
+                pwi[0] = 1;
+                for (int j = 1; j < N; j++) {
+                    pw[j] = h_mulmod(pw[j - 1], w, q);
+                    pwi[j] = h_mulmod(pwi[j - 1], wi, q);
+                }
+                for (int j = 0; j < N; j++) {
+                    u64 a = pw[bitrev(j, c->logN)], b = pwi[bitrev(j, c->logN)];
+                    tw[(size_t)i * N + j] = a;
+                    tw_sh[(size_t)i * N + j] = shoup_of(a, q);
+                    itw[(size_t)i * N + j] = b;
+                    itw_sh[(size_t)i * N + j] = shoup_of(b, q);
+                }
+                ninv[i] = h_invmod((u64)N % q, q);
+                ninv_sh[i] = shoup_of(ninv[i], q);
+            });
+        for (auto& t : th) t.join();
+    }
+    for (int i = 0; i <= c->L; i++) {
+        u64 q = c->mod[i], P = 1;
+        for (int j = 0; j < c->k; j++) P = h_mulmod(P, c->mod[c->L + 1 + j] % q, q);
+        pinv[i] = h_invmod(P, q);
+        pinv_sh[i] = shoup_of(pinv[i], q);
+    }
+    std::vector<u64> qlinv((size_t)(c->L + 1) * (c->L + 1), 0), qlinv_sh(qlinv.size(), 0);
+    for (int l = 1; l <= c->L; l++)
+        for (int i = 0; i < l; i++) {
+            u64 v = h_invmod(c->mod[l] % c->mod[i], c->mod[i]);
+            qlinv[(size_t)l * (c->L + 1) + i] = v;
+            qlinv_sh[(size_t)l * (c->L + 1) + i] = shoup_of(v, c->mod[i]);
+        }
+    // double-double table exp(-2 pi i j / 2N), j in [0, N), rounded from quad precision
+    std::vector<double> ddw((size_t)N * 4);
+    for (int j = 0; j < N; j++) {
+        __float128 ang = -4 * atanq((__float128)1) * (__float128)j / (__float128)N;
+        __float128 cr = cosq(ang), ci = sinq(ang);
+        double rh = (double)cr, ih = (double)ci;
+        ddw[4 * j + 0] = rh;
+        ddw[4 * j + 1] = (double)(cr - (__float128)rh);
+        ddw[4 * j + 2] = ih;
+        ddw[4 * j + 3] = (double)(ci - (__float128)ih);
+    }
+
+    PoolBuilder pb;
+    std::vector<Modulus> mods(nm);
+    for (int i = 0; i < nm; i++) mods[i] = make_modulus(c->mod[i]);
+    size_t o_mod = pb.put(mods.data(), nm * sizeof(Modulus));
+    size_t o_ninv = pb.put(ninv.data(), nm * 8), o_ninv_sh = pb.put(ninv_sh.data(), nm * 8);
+    size_t o_pinv = pb.put(pinv.data(), nm * 8), o_pinv_sh = pb.put(pinv_sh.data(), nm * 8);
+    size_t o_ql = pb.put(qlinv.data(), qlinv.size() * 8);
+    size_t o_ql_sh = pb.put(qlinv_sh.data(), qlinv_sh.size() * 8);
+    std::vector<int> ident(nm);
+    for (int i = 0; i < nm; i++) ident[i] = i;
+    size_t o_ident = pb.put(ident.data(), nm * sizeof(int));
+    std::vector<int> t2slot(N), slot2t(N / 2);
+    {
+        u64 e = 1, twoN = 2 * (u64)N;
+        for (int l = 0; l < N / 2; l++) {
+            t2slot[(e - 1) / 2] = l;
+            t2slot[(twoN - e - 1) / 2] = l;
+            slot2t[l] = (int)((e - 1) / 2);
+            e = e * 5 % twoN;
+        }
+    }
+    size_t o_t2s = pb.put(t2slot.data(), N * sizeof(int));
+    size_t o_s2t = pb.put(slot2t.data(), (N / 2) * sizeof(int));
+    std::vector<int> qs(c->L + 1), ps(c->k);
+    for (int i = 0; i <= c->L; i++) qs[i] = i;
+    for (int j = 0; j < c->k; j++) ps[j] = c->L + 1 + j;
+    TabOffsets md = build_tab(pb, c->mod, ps, qs);
+    struct LvOff {
+        std::vector<TabOffsets> up;
+        TabOffsets rs;
+        size_t ks;
+        std::vector<int> ks_limbs;
+    };
+    std::vector<LvOff> lvo(c->L + 1);
+    for (int l = 0; l <= c->L; l++) {
+        std::vector<int> ks;
+        for (int i = 0; i <= l; i++) ks.push_back(i);
+        for (int j = 0; j < c->k; j++) ks.push_back(c->L + 1 + j);
+        lvo[l].ks_limbs = ks;
+        lvo[l].ks = pb.put(ks.data(), ks.size() * sizeof(int));
+        int nd = (l + 1 + c->k - 1) / c->k;
+        for (int j = 0; j < nd; j++) {
+            std::vector<int> dig, oth;
+            for (int i = j * c->k; i < std::min((j + 1) * c->k, l + 1); i++) dig.push_back(i);
+            for (int t : ks)
+                if (std::find(dig.begin(), dig.end(), t) == dig.end()) oth.push_back(t);
+            lvo[l].up.push_back(build_tab(pb, c->mod, dig, oth));
+        }
+        if (l >= 1) {
+            std::vector<int> lower;
+            for (int i = 0; i < l; i++) lower.push_back(i);
+            lvo[l].rs = build_tab(pb, c->mod, {l}, lower);
+        }
+    }
+
+    char* dpool = nullptr;
+    FE_CUDA_TRY(cudaMalloc(&dpool, pb.host.size()));
+    c->pool = dpool;
+    FE_CUDA_TRY(cudaMemcpy(dpool, pb.host.data(), pb.host.size(), cudaMemcpyHostToDevice));
+    c->d_mod = (Modulus*)(dpool + o_mod);
+    c->d_ninv = (u64*)(dpool + o_ninv);
+    c->d_ninv_sh = (u64*)(dpool + o_ninv_sh);
+    c->d_pinv = (u64*)(dpool + o_pinv);
+    c->d_pinv_sh = (u64*)(dpool + o_pinv_sh);
+    c->d_qlinv = (u64*)(dpool + o_ql);
+    c->d_qlinv_sh = (u64*)(dpool + o_ql_sh);
+    c->d_identity_map = (int*)(dpool + o_ident);
+    c->d_t2slot = (int*)(dpool + o_t2s);
+    c->d_slot2t = (int*)(dpool + o_s2t);
+    c->q0inv_q1 = c->L >= 1 ? h_invmod(c->mod[0] % c->mod[1], c->mod[1]) : 0;
+    c->moddown = resolve(md, dpool);
+    c->lv.resize(c->L + 1);
+    for (int l = 0; l <= c->L; l++) {
+        for (auto& o : lvo[l].up) c->lv[l].modup.push_back(resolve(o, dpool));
+        if (l >= 1) c->lv[l].rescale = resolve(lvo[l].rs, dpool);
+        c->lv[l].ks_limbs = lvo[l].ks_limbs;
+        c->lv[l].d_ks_limbs = (const int*)(dpool + lvo[l].ks);
+    }
+    auto up = [&](u64** dst, const std::vector<u64>& v) -> int {
+        FE_CUDA_TRY(cudaMalloc(dst, v.size() * 8));
+        c->allocs.push_back(*dst);
+        FE_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice));
+        return FE_OK;
+    };
+    FE_TRY(up(&c->d_tw, tw));
+    FE_TRY(up(&c->d_tw_sh, tw_sh));
+    FE_TRY(up(&c->d_itw, itw));
+    FE_TRY(up(&c->d_itw_sh, itw_sh));
+    FE_CUDA_TRY(cudaMalloc(&c->d_dd_w, ddw.size() * sizeof(double)));
+    c->allocs.push_back(c->d_dd_w);
+    FE_CUDA_TRY(cudaMemcpy(c->d_dd_w, ddw.data(), ddw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    *out = c.release();
+    return FE_OK;
+}
+
+extern "C" void fe_ctx_destroy(fe_ctx* c) {
+    if (!c) return;
+    for (void* p : c->allocs) cudaFree(p);
+    cudaFree(c->pool);
+    delete c;
+}
+
+extern "C" int fe_ctx_moduli(const fe_ctx* c, uint64_t* out) {
+    if (!c || !out) return fail(FE_EINVAL, "null argument");
+    for (int i = 0; i < c->n_mod; i++) out[i] = c->mod[i];
+    return FE_OK;
+}
+
+extern "C" int fe_get_counters(const fe_ctx* c, fe_counters* out) {
+    if (!c || !out) return fail(FE_EINVAL, "null argument");
+    *out = c->cnt;
+    return FE_OK;
+}
+
+extern "C" int fe_counters_reset(fe_ctx* c) {
+    if (!c) return fail(FE_EINVAL, "null argument");
+    memset(&c->cnt, 0, sizeof(c->cnt));
+    return FE_OK;
+}

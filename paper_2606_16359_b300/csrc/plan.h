@@ -1,0 +1,56 @@
+// Layer plans shared by the planner (henn.cu) and the graph / layer helpers.
+#pragma once
+
+#include <vector>
+
+#include "ops.h"
+
+struct fe_plan {
+    fe_ctx* c;
+    int kind;  // 0 conv, 1 fc
+    int level;
+    int n_in, n_out;
+    fe_layout lin, lout;
+    int Cin, Cout, K, stride, depthwise, in_period;
+    int P, BS, F_in, F_out, n1, n2;
+    std::vector<int> feat;
+    struct Inner {
+        int ci;
+        int32_t step;
+    };
+    std::vector<Inner> inner;     // rotated inputs ("R slots")
+    std::vector<int> modup_cts;   // input ciphertexts that are rotated (sorted)
+    std::vector<int> modup_slot;  // [n_in] -> position in modup_cts or -1
+    struct Term {
+        int src;  // >= 0: R slot, < 0: input -(src + 1)
+        int pt;
+    };
+    struct Group {
+        int32_t step;  // 0: no rotation
+        int t0, nt;
+    };
+    struct Out {
+        std::vector<Group> groups;
+    };
+    std::vector<Term> terms;
+    std::vector<Out> outs;
+    struct ConvPt {
+        int h, up, vp, d, g, i, j;
+    };
+    std::vector<ConvPt> cpts;
+    struct FcPt {
+        int t, c, gam, beta;
+    };
+    std::vector<FcPt> fpts;
+    int n_pt = 0;
+    int n_outer = 0;
+    std::vector<int32_t> steps;
+};
+
+namespace fe {
+int layout_fill(int N, fe_layout* l);
+size_t plan_workspace(const fe_plan* p, size_t chunk);
+// phase bit 1: upload item tables; bit 2: launch kernels
+int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* in, const u64* pt, u64* out,
+             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase);
+}  // namespace fe
