@@ -1,0 +1,397 @@
+"""Python binding of libfenc (the C ABI in include/fenc.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch provides device memory (tensors are passed as raw pointers) and the
+current CUDA stream.  Ciphertexts, plaintexts and keys are int64 tensors that
+hold the uint64 residues bit for bit.
+
+Importing the package does not need a GPU; creating a Context does, and the
+library must have been built (paper_2606_16359_b300.build.build()).  There is no
+fallback path: a missing library raises.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libfenc.so")
+
+FE_OK, FE_EINVAL, FE_ENOMEM, FE_ELEVEL, FE_ESCALE, FE_EKEY, FE_ETIMEOUT, FE_ECUDA, FE_EENCODE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+
+u32, u64, i32, sz, vp, dbl = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t,
+                              ctypes.c_void_p, ctypes.c_double)
+cint = ctypes.c_int
+
+
+class FeParams(ctypes.Structure):
+    _fields_ = [("logN", u32), ("n_q", u32), ("k", u32), ("qbits", u32), ("pbits", u32)]
+
+
+class FeLayout(ctypes.Structure):
+    _fields_ = [(n, u32) for n in ("H", "W", "C", "BS", "S", "m", "M", "cpc", "groups", "n_ct")]
+
+    def describe(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class FeCounters(ctypes.Structure):
+    _fields_ = [(n, u64) for n in ("rot", "keyswitch", "ntt", "pmult", "cmult", "rescale", "launches")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class FePlanInfo(ctypes.Structure):
+    _fields_ = [("pt_bytes", sz), ("in_bytes", sz), ("out_bytes", sz), ("workspace_bytes", sz),
+                ("workspace_min_bytes", sz), ("n_in_ct", u32), ("n_out_ct", u32), ("n_pt", u32),
+                ("n_inner_rot", u32), ("n_outer_rot", u32)]
+
+
+P = ctypes.POINTER
+# name: (restype, argtypes)
+SIGNATURES = {
+    "fe_ctx_create": (cint, [P(FeParams), P(vp)]),
+    "fe_ctx_destroy": (None, [vp]),
+    "fe_ctx_moduli": (cint, [vp, P(u64)]),
+    "fe_get_counters": (cint, [vp, P(FeCounters)]),
+    "fe_counters_reset": (cint, [vp]),
+    "fe_last_error": (ctypes.c_char_p, []),
+    "fe_sk_gen": (cint, [vp, u64, vp, vp]),
+    "fe_evk_bytes": (sz, [vp, u32, cint]),
+    "fe_evk_gen": (cint, [vp, vp, u64, P(i32), u32, cint, vp, sz, vp, P(vp)]),
+    "fe_evk_destroy": (None, [vp]),
+    "fe_layout_make": (cint, [vp, P(FeLayout)]),
+    "fe_fragment_pack": (cint, [vp, P(FeLayout), vp, vp, vp]),
+    "fe_fragment_unpack": (cint, [vp, P(FeLayout), vp, vp, vp]),
+    "fe_encode": (cint, [vp, vp, u32, u32, dbl, vp, vp]),
+    "fe_encode_encrypt": (cint, [vp, vp, vp, u32, u32, dbl, u64, u64, vp, vp]),
+    "fe_decrypt_decode": (cint, [vp, vp, vp, u32, u32, dbl, vp, vp]),
+    "fe_ntt": (cint, [vp, vp, u32, u32, u32, cint, vp]),
+    "fe_rotate": (cint, [vp, vp, vp, u32, u32, i32, vp, vp]),
+    "fe_rescale": (cint, [vp, vp, u32, u32, vp, vp]),
+    "fe_pmult": (cint, [vp, vp, vp, u32, u32, vp, vp]),
+    "fe_add": (cint, [vp, vp, vp, u32, u32, vp, vp]),
+    "fe_plan_conv": (cint, [vp, P(FeLayout), u32, u32, u32, cint, u32, u32, P(FeLayout), P(vp)]),
+    "fe_plan_fc": (cint, [vp, u32, u32, u32, P(i32), u32, u32, u32, P(vp)]),
+    "fe_plan_destroy": (None, [vp]),
+    "fe_plan_query": (cint, [vp, P(FePlanInfo)]),
+    "fe_plan_rotation_steps": (cint, [vp, P(i32), u32, P(u32)]),
+    "fe_plan_load_weights": (cint, [vp, vp, vp, dbl, dbl, vp, vp]),
+    "fe_he_conv": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
+    "fe_he_fc": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
+    "fe_square_workspace_bytes": (sz, [vp, u32, u32]),
+    "fe_he_square": (cint, [vp, vp, vp, u32, u32, vp, vp, sz, vp]),
+    "fe_he_avgpool": (cint, [vp, P(FeLayout), vp, u32, vp, P(FeLayout), vp]),
+    "fe_compress_workspace_bytes": (sz, [vp, u32, u32]),
+    "fe_compress": (cint, [vp, vp, P(FeLayout), u32, vp, u32, u32, vp, vp, sz, vp]),
+    "fe_graph_capture": (cint, [vp, vp, P(vp), P(vp), u32, P(vp), vp, sz, vp, P(vp)]),
+    "fe_graph_launch": (cint, [vp, vp]),
+    "fe_graph_destroy": (None, [vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libfenc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfenc.so is not built ({LIB_PATH}); run paper_2606_16359_b300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class FencError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def check(rc):
+    if rc != FE_OK:
+        raise FencError(rc, load().fe_last_error().decode())
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+class Evk:
+    """Switching keys held in a torch buffer, with the library handle."""
+
+    def __init__(self, ctx, handle, buf, steps, relin):
+        self.ctx, self.handle, self.buf, self.steps, self.relin = ctx, handle, buf, list(steps), relin
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_evk_destroy(self.handle)
+            self.handle = None
+
+
+class Plan:
+    def __init__(self, ctx, handle, out_layout=None):
+        self.ctx, self.handle, self.out_layout = ctx, handle, out_layout
+        info = FePlanInfo()
+        check(load().fe_plan_query(handle, ctypes.byref(info)))
+        self.info = info
+        n = u32()
+        check(load().fe_plan_rotation_steps(handle, None, 0, ctypes.byref(n)))
+        arr = (i32 * max(1, n.value))()
+        check(load().fe_plan_rotation_steps(handle, arr, n.value, ctypes.byref(n)))
+        self.steps = [arr[i] for i in range(n.value)]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Graph:
+    def __init__(self, handle, keep):
+        self.handle, self._keep = handle, keep
+
+    def launch(self):
+        check(load().fe_graph_launch(self.handle, _stream()))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_graph_destroy(self.handle)
+            self.handle = None
+
+
+class Context:
+    """An RNS-CKKS parameter set on the current CUDA device."""
+
+    def __init__(self, logN, n_q, k, qbits, pbits=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        lib = load()
+        self.params = FeParams(logN, n_q, k, qbits, qbits if pbits is None else pbits)
+        h = vp()
+        check(lib.fe_ctx_create(ctypes.byref(self.params), ctypes.byref(h)))
+        self.handle = h
+        self.logN, self.N, self.L, self.k = logN, 1 << logN, n_q - 1, k
+        self.n_mod = n_q + k
+        arr = (u64 * self.n_mod)()
+        check(lib.fe_ctx_moduli(h, arr))
+        self.moduli = [int(arr[i]) for i in range(self.n_mod)]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_ctx_destroy(self.handle)
+            self.handle = None
+
+    # -- helpers --------------------------------------------------------------
+    def ct_words(self, level):
+        return 2 * (level + 1) * self.N
+
+    def empty_ct(self, n, level):
+        return _torch().empty((n, 2, level + 1, self.N), dtype=_torch().int64, device="cuda")
+
+    def counters(self):
+        c = FeCounters()
+        check(load().fe_get_counters(self.handle, ctypes.byref(c)))
+        return c.as_dict()
+
+    def reset_counters(self):
+        check(load().fe_counters_reset(self.handle))
+
+    # -- keys -------------------------------------------------------------------
+    def sk_gen(self, seed):
+        sk = _torch().empty((self.n_mod, self.N), dtype=_torch().int64, device="cuda")
+        check(load().fe_sk_gen(self.handle, seed, _ptr(sk), _stream()))
+        return sk
+
+    def evk_gen(self, sk, seed, steps, relin=False):
+        steps = sorted({int(s) for s in steps})
+        nbytes = load().fe_evk_bytes(self.handle, len(steps), 1 if relin else 0)
+        buf = _torch().empty(max(8, nbytes) // 8, dtype=_torch().int64, device="cuda")
+        arr = (i32 * max(1, len(steps)))(*steps)
+        h = vp()
+        check(load().fe_evk_gen(self.handle, _ptr(sk), seed, arr, len(steps), 1 if relin else 0, _ptr(buf),
+                                nbytes, _stream(), ctypes.byref(h)))
+        return Evk(self, h, buf, steps, relin)
+
+    # -- client side --------------------------------------------------------------
+    def layout(self, H, W, C, BS, S, m=0):
+        lay = FeLayout(H, W, C, BS, S, m, 0, 0, 0, 0)
+        check(load().fe_layout_make(self.handle, ctypes.byref(lay)))
+        return lay
+
+    def pack(self, lay, x):
+        torch = _torch()
+        x = torch.as_tensor(x, dtype=torch.float64).cuda().contiguous()
+        slots = torch.empty((lay.n_ct, self.N // 2), dtype=torch.float64, device="cuda")
+        check(load().fe_fragment_pack(self.handle, ctypes.byref(lay), _ptr(x), _ptr(slots), _stream()))
+        return slots
+
+    def unpack(self, lay, slots):
+        torch = _torch()
+        y = torch.empty((lay.BS, lay.C, lay.H, lay.W), dtype=torch.float64, device="cuda")
+        check(load().fe_fragment_unpack(self.handle, ctypes.byref(lay), _ptr(slots.contiguous()), _ptr(y), _stream()))
+        return y
+
+    def encode(self, slots, level, scale):
+        torch = _torch()
+        slots = torch.as_tensor(slots, dtype=torch.float64).cuda().contiguous()
+        n = slots.shape[0]
+        pt = torch.empty((n, level + 1, self.N), dtype=torch.int64, device="cuda")
+        check(load().fe_encode(self.handle, _ptr(slots), n, level, scale, _ptr(pt), _stream()))
+        return pt
+
+    def encrypt(self, sk, slots, level, scale, seed, ct_id0=0):
+        torch = _torch()
+        slots = torch.as_tensor(slots, dtype=torch.float64).cuda().contiguous()
+        n = slots.shape[0]
+        ct = self.empty_ct(n, level)
+        check(load().fe_encode_encrypt(self.handle, _ptr(sk), _ptr(slots), n, level, scale, seed, ct_id0,
+                                       _ptr(ct), _stream()))
+        return ct
+
+    def decrypt(self, sk, ct, level, scale):
+        torch = _torch()
+        n = ct.shape[0]
+        out = torch.empty((n, self.N // 2), dtype=torch.float64, device="cuda")
+        check(load().fe_decrypt_decode(self.handle, _ptr(sk), _ptr(ct), n, level, scale, _ptr(out), _stream()))
+        return out
+
+    # -- primitives ------------------------------------------------------------------
+    def ntt(self, data, first_mod=0, inverse=False):
+        n_poly, n_limbs = data.shape[0], data.shape[1]
+        check(load().fe_ntt(self.handle, _ptr(data), n_poly, n_limbs, first_mod, 1 if inverse else 0, _stream()))
+        return data
+
+    def rotate(self, evk, ct, level, r):
+        out = self.empty_ct(ct.shape[0], level)
+        check(load().fe_rotate(self.handle, evk.handle, _ptr(ct), ct.shape[0], level, r, _ptr(out), _stream()))
+        return out
+
+    def rescale(self, ct, level):
+        out = self.empty_ct(ct.shape[0], level - 1)
+        check(load().fe_rescale(self.handle, _ptr(ct), ct.shape[0], level, _ptr(out), _stream()))
+        return out
+
+    def pmult(self, ct, pt, level):
+        out = self.empty_ct(ct.shape[0], level)
+        check(load().fe_pmult(self.handle, _ptr(ct), _ptr(pt), ct.shape[0], level, _ptr(out), _stream()))
+        return out
+
+    def add(self, a, b, level):
+        out = self.empty_ct(a.shape[0], level)
+        check(load().fe_add(self.handle, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream()))
+        return out
+
+    # -- layers -------------------------------------------------------------------------
+    def plan_conv(self, lay, Cout, K, stride=1, depthwise=False, in_period=0, level=None):
+        level = self.L if level is None else level
+        out_lay = FeLayout()
+        h = vp()
+        check(load().fe_plan_conv(self.handle, ctypes.byref(lay), Cout, K, stride, 1 if depthwise else 0,
+                                  in_period, level, ctypes.byref(out_lay), ctypes.byref(h)))
+        p = Plan(self, h, out_lay)
+        p.level, p.in_layout = level, lay
+        return p
+
+    def plan_fc(self, n_in_ct, P, BS, feat, F_in, F_out, level):
+        feat = np.ascontiguousarray(feat, dtype=np.int32)
+        h = vp()
+        check(load().fe_plan_fc(self.handle, n_in_ct, P, BS, feat.ctypes.data_as(P_i32), F_in, F_out, level,
+                                ctypes.byref(h)))
+        p = Plan(self, h)
+        p.level = level
+        return p
+
+    def load_weights(self, plan, W, w_scale, wmul=1.0):
+        torch = _torch()
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        pt = torch.empty(max(8, plan.info.pt_bytes) // 8, dtype=torch.int64, device="cuda")
+        check(load().fe_plan_load_weights(self.handle, plan.handle, W.ctypes.data_as(vp), wmul, w_scale, _ptr(pt),
+                                          _stream()))
+        return pt
+
+    def workspace(self, nbytes):
+        return _torch().empty(max(8, (nbytes + 7) // 8), dtype=_torch().int64, device="cuda")
+
+    def he_conv(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
+        ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
+        out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        check(load().fe_he_conv(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
+                                ws.numel() * 8, mode, _stream()))
+        return out
+
+    def he_fc(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
+        ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
+        out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        check(load().fe_he_fc(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
+                              ws.numel() * 8, mode, _stream()))
+        return out
+
+    def he_square(self, evk, ct, level):
+        n = ct.shape[0]
+        ws = self.workspace(load().fe_square_workspace_bytes(self.handle, n, level))
+        out = self.empty_ct(n, level - 1)
+        check(load().fe_he_square(self.handle, evk.handle, _ptr(ct), n, level, _ptr(out), _ptr(ws), ws.numel() * 8,
+                                  _stream()))
+        return out
+
+    def he_avgpool(self, lay, ct, level):
+        out_lay = FeLayout()
+        n_out = lay.n_ct // 4
+        out = self.empty_ct(n_out, level)
+        check(load().fe_he_avgpool(self.handle, ctypes.byref(lay), _ptr(ct), level, _ptr(out),
+                                   ctypes.byref(out_lay), _stream()))
+        return out, out_lay
+
+    def compress(self, evk, lay, c_valid, ct, level):
+        n = ct.shape[0]
+        ws = self.workspace(load().fe_compress_workspace_bytes(self.handle, n, level))
+        out = self.empty_ct(n, level)
+        check(load().fe_compress(self.handle, evk.handle, ctypes.byref(lay), c_valid, _ptr(ct), n, level, _ptr(out),
+                                 _ptr(ws), ws.numel() * 8, _stream()))
+        return out
+
+    def graph_capture(self, evk, plans, pts, bufs, ws):
+        n = len(plans)
+        parr = (vp * n)(*[p.handle.value for p in plans])
+        ptarr = (vp * n)(*[t.data_ptr() for t in pts])
+        barr = (vp * (n + 1))(*[b.data_ptr() for b in bufs])
+        h = vp()
+        check(load().fe_graph_capture(self.handle, evk.handle, parr, ptarr, n, barr, _ptr(ws), ws.numel() * 8,
+                                      _stream(), ctypes.byref(h)))
+        return Graph(h, (plans, pts, bufs, ws))
+
+    # -- scale rule shared by the network code --------------------------------------------
+    def weight_scale(self, level, s_in, delta, square_follows):
+        """Scale at which a linear layer at `level` encodes its weights: after its rescale the
+        output scale is delta, or sqrt(delta q_{level-1}) when an x^2 activation follows (so
+        that the activation's rescale lands back near delta).  Evaluated in IEEE double."""
+        t = math.sqrt(delta * float(self.moduli[level - 1])) if square_follows else delta
+        return (t / s_in) * float(self.moduli[level])
+
+
+P_i32 = ctypes.POINTER(i32)
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects the library to export."""
+    return sorted(SIGNATURES)

@@ -215,6 +215,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->k = p->k;
     c->n_mod = p->n_q + p->k;
     c->dnum = (p->n_q + p->k - 1) / p->k;
+    if (c->dnum > 16) return fail(FE_EINVAL, "more than 16 key-switching digits (raise k)");
     memset(&c->cnt, 0, sizeof(c->cnt));
     c->mod = prime_run(c->logN, p->qbits, p->n_q, {});
     if ((int)c->mod.size() != (int)p->n_q) return fail(FE_EINVAL, "not enough ciphertext primes");

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Residues must be bit-exact: NTT, keys, encoding, encryption, rotation,
+rescale, PMult, the fragment convolution (plain and batched paths), FC, x^2,
+pooling and AAC, from the same seeds and seeded inputs.  Decrypted outputs are
+also checked against the FP64 definitions within 1e-3.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import _core as C
+from oracle import ckks, fragment, henn, plain
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_16359_b300 as fe  # noqa: E402
+
+
+def u64(t):
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def oracle_ct_array(cts):
+    return np.stack([c.as_array() for c in cts])
+
+
+class Pair:
+    """A parameter set instantiated on both sides."""
+
+    def __init__(self, logN, n_q, k, bits, pbits=None):
+        self.pr = ckks.Params(logN, n_q, k, bits, pbits)
+        self.g = fe.Context(logN, n_q, k, bits, pbits if pbits is not None else bits)
+        assert self.g.moduli == self.pr.moduli
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    p = W.PARAMS["tiny"]
+    return Pair(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+
+
+@pytest.fixture(scope="module")
+def ks2():
+    return Pair(7, 4, 2, 40)
+
+
+@pytest.mark.parametrize("args", [(10, 3, 1, 30, 50), (12, 4, 2, 40, 40), (13, 2, 1, 36, 60), (16, 2, 1, 36, 36),
+                                  (14, 3, 2, 40, 40)])
+def test_ntt_parity(args):
+    pr = ckks.Params(*args)
+    g = fe.Context(*args)
+    assert g.moduli == pr.moduli
+    rng = np.random.default_rng(args[0])
+    a = np.stack([rng.integers(0, q, pr.N, dtype=np.uint64) for q in pr.moduli])[None]
+    d = to_dev(a)
+    g.ntt(d)
+    want = np.stack([pr.ntt(a[0, i], i) for i in range(len(pr.moduli))])
+    assert np.array_equal(u64(d)[0], want)
+    g.ntt(d, inverse=True)
+    assert np.array_equal(u64(d)[0], a[0])
+
+
+@pytest.mark.parametrize("which", ["tiny", "ks2"])
+def test_keys_parity(which, tiny, ks2):
+    P = tiny if which == "tiny" else ks2
+    pr, g = P.pr, P.g
+    steps = [1, 5, -3]
+    keys = ckks.KeySet(pr, 77, rot_steps=steps, relin=True)
+    sk = g.sk_gen(77)
+    assert np.array_equal(u64(sk), keys.sk.ntt)
+    evk = g.evk_gen(sk, 77, steps, relin=True)
+    kb = u64(evk.buf)
+    dnum = len(pr.digits(pr.L))
+    nm = len(pr.moduli)
+    per = dnum * 2 * nm * pr.N
+    for idx, r in enumerate(sorted(steps)):
+        sw = keys.rot[pr.galois(r)]
+        got = kb[idx * per:(idx + 1) * per].reshape(dnum, 2, nm, pr.N)
+        for j in range(dnum):
+            assert np.array_equal(got[j, 0], sw.b[j]) and np.array_equal(got[j, 1], sw.a[j])
+    got = kb[len(steps) * per:(len(steps) + 1) * per].reshape(dnum, 2, nm, pr.N)
+    for j in range(dnum):
+        assert np.array_equal(got[j, 0], keys.relin.b[j]) and np.array_equal(got[j, 1], keys.relin.a[j])
+
+
+def test_encode_encrypt_decrypt_parity(tiny):
+    pr, g = tiny.pr, tiny.g
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-1, 1, (3, pr.N // 2))
+    for scale, level in [(2.0 ** 25, pr.L), (float(pr.q[-1]), 1), (2.0 ** 40 * 1.37, 2)]:
+        pt = g.encode(torch.from_numpy(z), level, scale)
+        want = np.stack([ckks.encode(pr, z[i], level, scale).m for i in range(3)])
+        assert np.array_equal(u64(pt), want)
+    keys = ckks.KeySet(pr, 5)
+    sk = g.sk_gen(5)
+    ct = g.encrypt(sk, torch.from_numpy(z), pr.L, 2.0 ** 25, seed=9, ct_id0=4)
+    want = oracle_ct_array([ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], pr.L, 2.0 ** 25), 9, 4 + i)
+                            for i in range(3)])
+    assert np.array_equal(u64(ct), want)
+    dec = g.decrypt(sk, ct, pr.L, 2.0 ** 25).cpu().numpy()
+    assert np.abs(dec - z).max() < 1e-5
+    dec0 = g.decrypt(sk, ct[:, :, :1].contiguous(), 0, 2.0 ** 25).cpu().numpy()
+    assert np.abs(dec0 - z).max() < 1e-5
+
+
+@pytest.mark.parametrize("which", ["tiny", "ks2"])
+def test_rotate_rescale_pmult_add_parity(which, tiny, ks2):
+    P = tiny if which == "tiny" else ks2
+    pr, g = P.pr, P.g
+    steps = [1, 3, -2, pr.N // 8]
+    keys = ckks.KeySet(pr, 11, rot_steps=steps)
+    sk = g.sk_gen(11)
+    evk = g.evk_gen(sk, 11, steps)
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, (2, pr.N // 2))
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], pr.L, 2.0 ** 25), 2, i) for i in range(2)]
+    ct = g.encrypt(sk, torch.from_numpy(z), pr.L, 2.0 ** 25, seed=2)
+    assert np.array_equal(u64(ct), oracle_ct_array(octs))
+    for r in steps:
+        got = g.rotate(evk, ct, pr.L, r)
+        want = oracle_ct_array([ckks.rotate(pr, keys, c, r) for c in octs])
+        assert np.array_equal(u64(got), want), r
+    w = rng.uniform(-1, 1, (2, pr.N // 2))
+    pts = g.encode(torch.from_numpy(w), pr.L, float(pr.q[pr.L]))
+    opts = [ckks.encode(pr, w[i], pr.L, float(pr.q[pr.L])) for i in range(2)]
+    pm = g.pmult(ct, pts, pr.L)
+    opm = [ckks.pmult(pr, octs[i], opts[i]) for i in range(2)]
+    assert np.array_equal(u64(pm), oracle_ct_array(opm))
+    rs = g.rescale(pm, pr.L)
+    assert np.array_equal(u64(rs), oracle_ct_array([ckks.rescale(pr, c) for c in opm]))
+    ad = g.add(ct, ct, pr.L)
+    assert np.array_equal(u64(ad), oracle_ct_array([ckks.add(pr, c, c) for c in octs]))
+
+
+def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1)):
+    pr, g = P.pr, P.g
+    BS, C, H, _ = x.shape
+    Cout = w.shape[0]
+    K = w.shape[-1]
+    olay = fragment.Layout(pr.N, H, H, C, BS, S)
+    steps = henn.conv_rotation_steps(olay, C, Cout, K, stride, depthwise)
+    keys = ckks.KeySet(pr, seed, rot_steps=steps)
+    slots = fragment.pack(olay, x)
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, delta), 17, i) for i in range(olay.n_ct)]
+    ocnt = henn.Counters()
+    oout, oolay = henn.he_conv(pr, keys, octs, olay, w, stride=stride, depthwise=depthwise, cnt=ocnt)
+    want = oracle_ct_array(oout)
+
+    lay = g.layout(H, H, C, BS, S)
+    plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L)
+    assert sorted(plan.steps) == sorted(steps)
+    assert plan.info.n_inner_rot + plan.info.n_outer_rot == ocnt.rot
+    assert plan.info.n_pt == ocnt.pmult
+    sk = g.sk_gen(seed)
+    evk = g.evk_gen(sk, seed, plan.steps)
+    xs = g.pack(lay, torch.from_numpy(x))
+    assert np.array_equal(xs.cpu().numpy(), slots)
+    ct = g.encrypt(sk, xs, pr.L, delta, seed=17)
+    pt = g.load_weights(plan, w, float(pr.q[pr.L]))
+    outs = {}
+    for mode in modes:
+        outs[mode] = g.he_conv(evk, plan, pt, ct, mode=mode)
+        assert np.array_equal(u64(outs[mode]), want), f"mode {mode}"
+    y = g.unpack(plan.out_layout, g.decrypt(sk, outs[modes[-1]], pr.L - 1, delta)).cpu().numpy()
+    ref = plain.conv2d(x, w, stride=stride, depthwise=depthwise)
+    assert np.abs(y - ref).max() < 1e-3
+    return plan, outs
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride", [
+    (8, 3, 5, 3, 2, 2, 1),
+    (8, 3, 5, 3, 1, 4, 1),
+    (9, 2, 3, 3, 2, 2, 2),
+    (6, 20, 18, 3, 1, 1, 1),
+    (7, 2, 2, 5, 1, 3, 1),
+])
+def test_conv_parity(tiny, H, C, Co, K, BS, S, stride):
+    rng = np.random.default_rng(H * 100 + C)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, (Co, C, K, K))
+    run_conv_pair(tiny, x, w, S, stride)
+
+
+def test_conv_parity_depthwise_and_two_prime_digits(ks2):
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-1, 1, (1, 4, 6, 6))
+    w = rng.normal(0, 1 / 3, (4, 1, 3, 3))
+    run_conv_pair(ks2, x, w, 1, depthwise=True)
+    w2 = rng.normal(0, 0.3, (5, 4, 1, 1))
+    run_conv_pair(ks2, x, w2, 1)
+
+
+def test_conv1_configuration_bit_exact():
+    """The single-conv configuration at full size (N = 2^13): residues bit-exact
+    to the oracle in both paths, decrypted error <= 1e-3 against Eq. 2."""
+    p = W.PARAMS["conv1"]
+    P = Pair(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+    x, w = W.conv1_workload(0)
+    plan, _ = run_conv_pair(P, x, w, 4, delta=p["delta"])
+    assert (plan.info.n_inner_rot, plan.info.n_outer_rot, plan.info.n_pt) == (48, 80, 2400)
+
+
+def test_square_pool_fc_parity():
+    pr_args = (10, 4, 1, 40, 50)
+    P = Pair(*pr_args)
+    pr, g = P.pr, P.g
+    rng = np.random.default_rng(7)
+    olay = fragment.Layout(pr.N, 4, 4, 2, 4, 2)
+    x = rng.uniform(0, 1, (4, 2, 4, 4))
+    Pp = olay.cpc * olay.m * olay.m
+    steps = henn.fc_rotation_steps(Pp, olay.BS)
+    keys = ckks.KeySet(pr, 3, rot_steps=steps, relin=True)
+    slots = fragment.pack(olay, x)
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, 2.0 ** 35), 1, i) for i in range(olay.n_ct)]
+    osq = henn.he_square(pr, keys, octs)
+    opool, opl = henn.he_avgpool2(pr, osq, olay)
+    sk = g.sk_gen(3)
+    evk = g.evk_gen(sk, 3, steps, relin=True)
+    lay = g.layout(4, 4, 2, 4, 2)
+    ct = g.encrypt(sk, torch.from_numpy(slots), pr.L, 2.0 ** 35, seed=1)
+    sq = g.he_square(evk, ct, pr.L)
+    assert np.array_equal(u64(sq), oracle_ct_array(osq))
+    pooled, pl = g.he_avgpool(lay, sq, pr.L - 1)
+    assert np.array_equal(u64(pooled), oracle_ct_array(opool))
+    wfc = rng.normal(0, 0.3, (7, 8))
+    m = opl.m
+
+    def feat(c_ct, p):
+        c_loc, k = divmod(p, m * m)
+        c = c_ct * opl.cpc + c_loc
+        bi, bj = divmod(k, m)
+        if c >= opl.C or bi >= opl.H or bj >= opl.W:
+            return -1
+        return (c * opl.H + bi) * opl.W + bj
+
+    ofc = henn.he_fc(pr, keys, opool, feat, Pp, opl.BS, wfc)
+    ftab = np.array([[feat(c, p) for p in range(Pp)] for c in range(len(opool))], dtype=np.int32)
+    plan = g.plan_fc(len(opool), Pp, opl.BS, ftab, 8, 7, pr.L - 1)
+    pt = g.load_weights(plan, wfc, float(pr.q[pr.L - 1]))
+    for mode in (0, 1):
+        out = g.he_fc(evk, plan, pt, pooled, mode=mode)
+        assert np.array_equal(u64(out), oracle_ct_array(ofc)), mode
+
+
+def test_aac_compress_parity(tiny):
+    pr, g = tiny.pr, tiny.g
+    rng = np.random.default_rng(6)
+    olay = fragment.Layout(pr.N, 8, 8, 2, 1, 1)  # cpc = 8, 2 valid channels
+    x = rng.uniform(-1, 1, (1, 2, 8, 8))
+    steps = henn.aac_rotation_steps(olay, 2)
+    keys = ckks.KeySet(pr, 4, rot_steps=steps)
+    slots = fragment.pack(olay, x)
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[0], pr.L, 2.0 ** 25), 1, 0)]
+    want = oracle_ct_array(henn.aac_compress(pr, keys, octs, olay, 2))
+    sk = g.sk_gen(4)
+    evk = g.evk_gen(sk, 4, steps)
+    lay = g.layout(8, 8, 2, 1, 1)
+    ct = g.encrypt(sk, torch.from_numpy(slots), pr.L, 2.0 ** 25, seed=1)
+    got = g.compress(evk, lay, 2, ct, pr.L)
+    assert np.array_equal(u64(got), want)
+    dec = g.decrypt(sk, got, pr.L, 2.0 ** 25).cpu().numpy()[0].reshape(8, -1)
+    for c in range(8):
+        assert np.abs(dec[c] - slots[0].reshape(8, -1)[c % 2]).max() < 1e-4
