@@ -1,0 +1,334 @@
+"""Benchmark of the encrypted-convolution hot path on B300.
+
+Workload (default): the three MobileNet-shaped blocks (depthwise 3x3 then
+pointwise) at N = 2^16, 24 x 36-bit + 4 special primes, scale 2^32, inputs
+U[-1, 1), weights N(0, 1/fan_in), fragment size S = 1, one encrypted input per
+block.  A step runs all six HE convolutions (inner rotations, PMult-MAC,
+outer rotations, rescale) with keys, plaintexts and ciphertexts resident.
+
+Reported: key switches per second (the metric's throughput form), ms per step
+and per layer, the plain per-op path beside the batched/graph path, the
+roofline fraction of the dominant kernel class, the CPU oracle timed on the
+host, an end-to-end number through host buffers, and SM clocks sampled during
+the timed region.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "he_conv layer ms & key-switches/s on 1 B300, % HBM roofline, vs plain path"
+PARAMS = dict(logN=16, n_q=24, k=4, qbits=36, pbits=36)
+DELTA = 2.0 ** 32
+WORKLOAD = "mobilenet_blocks_3x(dw3x3+pw)_N2^16_L23_k4"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, rank, world, local
+    return None, 0, 1, local
+
+
+def reduce_max(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_oracle_keyswitch(n_rot, level=22):
+    """The CPU oracle (as it stands, single-threaded) on a bounded sample: n_rot
+    rotations of one ciphertext at `level` of the same parameter set."""
+    from oracle import ckks
+    pr = ckks.Params(PARAMS["logN"], PARAMS["n_q"], PARAMS["k"], PARAMS["qbits"], PARAMS["pbits"])
+    keys = ckks.KeySet(pr, 1, rot_steps=[1])
+    rng = np.random.default_rng(0)
+    c = ckks.Ciphertext(np.stack([rng.integers(0, pr.moduli[i], pr.N, dtype=np.uint64) for i in range(level + 1)]),
+                        np.stack([rng.integers(0, pr.moduli[i], pr.N, dtype=np.uint64) for i in range(level + 1)]),
+                        level, 1.0)
+    ext = ckks.mod_up(pr, c.c1, level)  # warm caches (permutation tables)
+    t0 = time.perf_counter()
+    for _ in range(n_rot):
+        ckks.rotate(pr, keys, c, 1)
+    dt = time.perf_counter() - t0
+    del ext
+    return n_rot / dt, dt
+
+
+def run_reference(args):
+    dist, rank, world, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        v, dt = cpu_oracle_keyswitch(1)
+        if i >= args.warmup:
+            per_step.append(dt)
+    total = sum(per_step)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one CPU-oracle rotation (key switch) at level 22"},
+            "cpu_baseline": {"value": value, "unit": "keyswitch/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} rotations of one ciphertext at level 22, N=2^16"},
+            "e2e": {"value": value, "unit": "keyswitch/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--cpu-rotations", type=int, default=4)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--profile", default="auto", help="kernel class timed for the roofline, or 'auto'")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    dist, rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        return run_ours(args, dist, rank, world, local)
+
+
+def run_ours(args, dist, rank, world, local):
+    import torch
+    import paper_2606_16359_b300 as fe
+    from paper_2606_16359_b300.net import MobileNetBlocks
+
+    t_setup = time.perf_counter()
+    ctx = fe.Context(**PARAMS)
+    net = MobileNetBlocks(ctx, delta=DELTA)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    ks_per_step = net.keyswitches_per_step
+    stream = torch.cuda.current_stream()
+
+    # correctness of one step against FP64 (untimed)
+    net.run(mode=1)
+    torch.cuda.synchronize()
+    errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(len(net.blocks))]
+
+    use_graph = not args.no_graph
+    if use_graph:
+        net.capture()
+
+    def step():
+        if use_graph:
+            net.graph.launch()
+        else:
+            net.run(mode=1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist)
+
+    # ---- timed region: K steps, events on the launching stream ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(dist)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ms = reduce_max(dist, ms)
+    barrier(dist)
+    ms_step = ms / args.steps
+    value = world * ks_per_step * args.steps / (ms / 1e3)
+
+    # ---- per-layer times (batched path, events around each layer) ----
+    layer_ms = []
+    for i in range(len(net.layers)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        net.run_layer(i)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        net.run_layer(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        layer_ms.append(e0.elapsed_time(e1))
+
+    # ---- dominant kernel class and its roofline (batched path, same workload) ----
+    kinds = ["ntt", "bconv", "keyip", "combine", "mac", "rescale"]
+    per_kind = {}
+    for kd in kinds:
+        ctx.profile_begin(kd)
+        net.run(mode=1)
+        t, n, b = ctx.profile_end()
+        per_kind[kd] = (t, n, b)
+    dom = max(per_kind, key=lambda k: per_kind[k][0]) if args.profile == "auto" else args.profile
+    ctx.profile_begin(dom)
+    for _ in range(args.steps):
+        net.run(mode=1)
+    t_dom, n_dom, b_dom = ctx.profile_end()
+    peak, peak_kind = peaks()
+    achieved = (b_dom / n_dom) / (t_dom / n_dom / 1e3) / 1e9 if n_dom else 0.0
+    shares = {k: round(v[0] / sum(x[0] for x in per_kind.values()), 4) for k, v in per_kind.items()}
+
+    # ---- plain per-op path (one launch per primitive per ciphertext) ----
+    net.run(mode=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.plain_steps):
+        net.run(mode=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.plain_steps
+
+    # ---- end to end through host buffers: H2D inputs, graph step, D2H outputs ----
+    h_in = [t.cpu().pin_memory() for t in net.inputs]
+    h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in net.outputs]
+    h2d = sum(t.numel() * 8 for t in h_in)
+    d2h = sum(t.numel() * 8 for t in h_out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for d, h in zip(net.inputs, h_in):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, d in zip(h_out, net.outputs):
+            h.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(dist, e0.elapsed_time(e1)) / args.steps
+    e2e_value = world * ks_per_step / (e2e_ms / 1e3)
+
+    launches_step = None
+    ctx.reset_counters()
+    net.run(mode=1)
+    torch.cuda.synchronize()
+    cnt = ctx.counters()
+    launches_step = cnt["launches"]
+
+    cpu = None
+    if rank == 0 and args.cpu_rotations > 0:
+        v, dt = cpu_oracle_keyswitch(args.cpu_rotations)
+        cpu = {"value": v, "unit": "keyswitch/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_rotations} oracle rotations of one ciphertext at level 22 (pw layer level), "
+                         f"N=2^16, 6 digits, {dt:.1f} s single-threaded"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "blocks": net.blocks, "keyswitches_per_step": ks_per_step,
+                       "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
+                       "path": "graph" if use_graph else "batched",
+                       "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
+                       "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,
+                       "max_abs_err_vs_fp64": max(errs), "setup_s": round(t_setup, 1),
+                       "l2": "inputs (keys, plaintexts) far larger than L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "launches": n_dom, "avg_launch_us": 1e3 * t_dom / max(1, n_dom),
+                         "time_share": shares},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "keyswitch/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -264,16 +264,32 @@ int fe_compress(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uint32_t c
 
 /* ---- batched, graph-captured execution ------------------------------------- */
 
-/* Capture the batched path of n planned layers (conv or FC), run back to back,
- * into one CUDA graph (stream capture on `stream`).  pts_host[i] is layer i's
- * plaintext buffer, bufs_host[i] its input and bufs_host[i+1] its output; all
- * layers share workspace_dev.  The item tables of every layer are uploaded into
- * the workspace before capture, so the graph replays kernels only. */
+/* Capture the batched path of n planned layers (conv or FC) into one CUDA graph
+ * (stream capture on `stream`, which must not be the legacy default stream).
+ * Layer i reads ins_host[i], writes outs_host[i] and uses plaintexts pts_host[i];
+ * layers run in the order given, so a layer may read an earlier layer's output.
+ * Every layer gets its own slice of workspace_dev (the sum of the plans'
+ * workspace_bytes) and its item tables are uploaded there before capture, so the
+ * graph replays kernels only.  Counters are not advanced by graph launches. */
 int fe_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
-                     const void* const* pts_host, uint32_t n, void* const* bufs_host,
-                     void* workspace_dev, size_t workspace_bytes, void* stream, fe_graph** out);
+                     const void* const* pts_host, const void* const* ins_host,
+                     void* const* outs_host, uint32_t n, void* workspace_dev,
+                     size_t workspace_bytes, void* stream, fe_graph** out);
 int fe_graph_launch(fe_graph* graph, void* stream);
 void fe_graph_destroy(fe_graph* graph);
+
+/* ---- kernel timing ---------------------------------------------------------- */
+
+/* Time every launch of one kernel class with CUDA events recorded on the
+ * launching stream: kind is one of "ntt" (forward and inverse NTT passes),
+ * "bconv", "keyip", "combine" (ModDown combine, single and summed), "mac",
+ * "rescale", "encode".  While active, each launch of that class also adds its
+ * algorithmic bytes (words each launch must read and write once) to a total.
+ * fe_profile_end synchronises the recorded streams and returns the summed
+ * duration in ms, the launch count and the algorithmic bytes.  Not for use
+ * inside stream capture. */
+int fe_profile_begin(fe_ctx* ctx, const char* kind);
+int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes);
 
 #ifdef __cplusplus
 }

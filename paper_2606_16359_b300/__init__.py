@@ -87,9 +87,11 @@ SIGNATURES = {
     "fe_he_avgpool": (cint, [vp, P(FeLayout), vp, u32, vp, P(FeLayout), vp]),
     "fe_compress_workspace_bytes": (sz, [vp, u32, u32]),
     "fe_compress": (cint, [vp, vp, P(FeLayout), u32, vp, u32, u32, vp, vp, sz, vp]),
-    "fe_graph_capture": (cint, [vp, vp, P(vp), P(vp), u32, P(vp), vp, sz, vp, P(vp)]),
+    "fe_graph_capture": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, vp, sz, vp, P(vp)]),
     "fe_graph_launch": (cint, [vp, vp]),
     "fe_graph_destroy": (None, [vp]),
+    "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
+    "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
 }
 
 _lib = None
@@ -370,15 +372,24 @@ class Context:
                                  _ptr(ws), ws.numel() * 8, _stream()))
         return out
 
-    def graph_capture(self, evk, plans, pts, bufs, ws):
+    def graph_capture(self, evk, plans, pts, ins, outs, ws):
         n = len(plans)
         parr = (vp * n)(*[p.handle.value for p in plans])
         ptarr = (vp * n)(*[t.data_ptr() for t in pts])
-        barr = (vp * (n + 1))(*[b.data_ptr() for b in bufs])
+        iarr = (vp * n)(*[t.data_ptr() for t in ins])
+        oarr = (vp * n)(*[t.data_ptr() for t in outs])
         h = vp()
-        check(load().fe_graph_capture(self.handle, evk.handle, parr, ptarr, n, barr, _ptr(ws), ws.numel() * 8,
+        check(load().fe_graph_capture(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, _ptr(ws), ws.numel() * 8,
                                       _stream(), ctypes.byref(h)))
-        return Graph(h, (plans, pts, bufs, ws))
+        return Graph(h, (plans, pts, ins, outs, ws))
+
+    def profile_begin(self, kind):
+        check(load().fe_profile_begin(self.handle, kind.encode()))
+
+    def profile_end(self):
+        ms, n, b = dbl(), u64(), dbl()
+        check(load().fe_profile_end(self.handle, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+        return ms.value, int(n.value), b.value
 
     # -- scale rule shared by the network code --------------------------------------------
     def weight_scale(self, level, s_in, delta, square_follows):

@@ -32,7 +32,18 @@ struct LevelTabs {
     const int* d_ks_limbs;        // device copy
 };
 
+enum ProfKind { PK_NTT = 0, PK_BCONV, PK_KEYIP, PK_COMBINE, PK_MAC, PK_RESCALE, PK_ENCODE, PK_COUNT };
+
 }  // namespace fe
+
+// per-context kernel timing state (see fe_profile_begin)
+struct fe_profiler {
+    int kind = -1;
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    double bytes = 0;
+    uint64_t launches = 0;
+};
 
 struct fe_evk {
     fe_ctx* ctx;
@@ -63,6 +74,7 @@ struct fe_ctx {
     void* pool;                     // all small device tables live here
     std::vector<void*> allocs;
     fe_counters cnt;
+    fe_profiler prof;
     cudaDeviceProp prop;
     int n_sm;
 
@@ -89,6 +101,16 @@ int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st);
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
                  cudaStream_t st);
 int decode_batch(fe_ctx* c, const double* mdd, int n, double scale, double* slots, cudaStream_t st);
+
+// Records CUDA events around one launch when its kernel class is being profiled,
+// and adds the launch's algorithmic bytes.
+struct ProfScope {
+    fe_ctx* c;
+    cudaStream_t st;
+    bool on;
+    ProfScope(fe_ctx* ctx, int kind, cudaStream_t s, double bytes);
+    ~ProfScope();
+};
 
 // scratch allocation helper: carve 256-byte aligned chunks out of a caller workspace
 struct Carver {

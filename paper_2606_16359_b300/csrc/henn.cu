@@ -278,7 +278,12 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         if (!base) no_base.push_back(o);
     }
     const size_t n_base = macs.size();
+    int base_terms = 0;
+    for (size_t i = 0; i < n_base; i++) base_terms += macs[i].n_terms;
+    std::vector<int> chunk_terms;
     for (size_t k = 0; k < order.size(); k++) {
+        if (k % chunk == 0) chunk_terms.push_back(0);
+        chunk_terms.back() += p->outs[order[k].first].groups[order[k].second].nt;
         const auto& g = p->outs[order[k].first].groups[order[k].second];
         macs.push_back(MacItem{Pd + (k % chunk) * z.ctw, g.t0, g.nt});
     }
@@ -346,7 +351,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                   ext1 + i * z.extw, st);
             i = j;
         }
-        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), lv, st);
+        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)n_in_rot, lv, st);
         moddown_prepare(c, acc1, (int)n_in_rot, lv, conv1, st);
         launch_combine(c, d_in_cb, (int)n_in_rot, lv, st);
     }
@@ -362,7 +367,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                 launch_pmult(c, tm.ct, tm.pt, macs[i].out, 1, lv, t > 0, st);
             }
     } else {
-        launch_mac(c, d_mac, d_terms, (int)n_base, lv, st);
+        launch_mac(c, d_mac, d_terms, (int)n_base, base_terms, lv, st);
     }
 
     // ---- stage 3: outer rotations in chunks, summed into the totals ----
@@ -382,13 +387,13 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                 moddown_prepare(c, acc3 + s * z.accw, 1, lv, conv3 + s * z.ctw, st);
             }
             for (int si = 0; si < sum_range[ch].second; si++)
-                launch_combine_sum(c, d_sum + sum_range[ch].first + si, d_ent, 1, lv, st);
+                launch_combine_sum(c, d_sum + sum_range[ch].first + si, d_ent, 1, sums[sum_range[ch].first + si].n_e, lv, st);
         } else {
-            launch_mac(c, d_mac + n_base + c0, d_terms, cn, lv, st);
+            launch_mac(c, d_mac + n_base + c0, d_terms, cn, chunk_terms[ch], lv, st);
             modup(c, Pd + z.nlN, z.ctw, cn, lv, coef3, ext3, st);
-            launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, lv, st);
+            launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, cn, lv, st);
             moddown_prepare(c, acc3, cn, lv, conv3, st);
-            launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, sum_range[ch].second, lv, st);
+            launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, sum_range[ch].second, cn, lv, st);
         }
     }
     c->cnt.rot += order.size();

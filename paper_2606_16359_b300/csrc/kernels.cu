@@ -306,6 +306,7 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
                   int in_pos_base, u64* out, size_t out_stride, int n_poly, bool copy_src,
                   cudaStream_t st) {
     if (n_poly == 0) return;
+    ProfScope ps(c, PK_BCONV, st, 8.0 * c->N * n_poly * (t.n_src * (copy_src ? 2 : 1) + t.n_dst));
     k_bconv<<<grid_for(c->N, n_poly), kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,
                                                    in_pos_base, out, out_stride, copy_src ? 1 : 0);
     c->cnt.launches++;
@@ -313,14 +314,18 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
 
 void launch_keyip(fe_ctx* c, const KsItem* items, int n_items, int level, cudaStream_t st) {
     if (!n_items) return;
+    const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
+    ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * n_items * (3.0 * dn + 2));
     k_keyip<<<grid_for(c->N, level + 1 + c->k, n_items), kB, 0, st>>>(items, c->d_mod, c->L, level,
                                                                      c->k, c->logN, c->n_mod);
     c->cnt.launches++;
 }
 
 void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items, int n_groups,
-                          int level, cudaStream_t st) {
+                          int n_items, int level, cudaStream_t st) {
     if (!n_groups) return;
+    const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
+    ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + (double)n_items * (dn + 2)));
     k_keyip_grouped<<<grid_for(c->N, level + 1 + c->k, n_groups), kB, 0, st>>>(
         groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod);
     c->cnt.launches++;
@@ -328,28 +333,32 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
 
 void launch_combine(fe_ctx* c, const CombineItem* items, int n_items, int level, cudaStream_t st) {
     if (!n_items) return;
+    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * (level + 1) * 7.0 * n_items);
     k_combine<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, c->d_mod, c->d_pinv,
                                                                 c->d_pinv_sh, level, c->k, c->logN);
     c->cnt.launches++;
 }
 
 void launch_combine_sum(fe_ctx* c, const SumItem* items, const SumEntry* entries, int n_items,
-                        int level, cudaStream_t st) {
+                        int n_entries, int level, cudaStream_t st) {
     if (!n_items) return;
+    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * (level + 1) * (4.0 * n_items + 5.0 * n_entries));
     k_combine_sum<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(
         items, entries, c->d_mod, c->d_pinv, c->d_pinv_sh, level, c->k, c->logN);
     c->cnt.launches++;
 }
 
-void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int level,
-                cudaStream_t st) {
+void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_terms,
+                int level, cudaStream_t st) {
     if (!n_items) return;
+    ProfScope ps(c, PK_MAC, st, 8.0 * c->N * (level + 1) * (3.0 * n_terms + 2.0 * n_items));
     k_mac<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, terms, c->d_mod, level, c->logN);
     c->cnt.launches++;
 }
 
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st) {
+    ProfScope ps(c, PK_RESCALE, st, 8.0 * c->N * 2 * n_ct * (level + 1 + 2.0 * level));
     k_rescale_combine<<<grid_for(c->N, level, 2 * n_ct), kB, 0, st>>>(
         in, lift, out, c->d_mod, c->d_qlinv, c->d_qlinv_sh, level, c->L, c->logN);
     c->cnt.launches++;

@@ -80,13 +80,13 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
                   cudaStream_t st);
 void launch_keyip(fe_ctx* c, const KsItem* items_dev, int n_items, int level, cudaStream_t st);
 void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups_dev, const KsItem* items_dev,
-                          int n_groups, int level, cudaStream_t st);
+                          int n_groups, int n_items, int level, cudaStream_t st);
 void launch_combine(fe_ctx* c, const CombineItem* items_dev, int n_items, int level,
                     cudaStream_t st);
 void launch_combine_sum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev,
-                        int n_items, int level, cudaStream_t st);
+                        int n_items, int n_entries, int level, cudaStream_t st);
 void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
-                int level, cudaStream_t st);
+                int n_terms, int level, cudaStream_t st);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st);
 void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,

@@ -98,7 +98,7 @@ extern "C" int fe_he_square(fe_ctx* c, const fe_evk* evk, const void* in_dev, ui
     FE_TRY(upload(cb, dcb, st));
     launch_tensor(c, (const u64*)in_dev, (const u64*)in_dev, d012, n, level, st);
     modup(c, d012 + 2 * (size_t)nl * N, 3 * (size_t)nl * N, n, level, s.coef, s.ext, st);
-    launch_keyip_grouped(c, s.kg, s.ks, 1, level, st);
+    launch_keyip_grouped(c, s.kg, s.ks, 1, (int)n, level, st);
     moddown_prepare(c, s.acc, n, level, s.conv, st);
     launch_combine(c, dcb, n, level, st);
     rescale_batch(c, tmp, n, level, (u64*)out_dev, rs, rs + 2 * (size_t)n * N, st);
@@ -181,9 +181,9 @@ extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, u
         FE_TRY(upload(ents, dent, st));
         FE_TRY(upload(sums, dsum, st));
         modup(c, cur + (size_t)(level + 1) * c->N, ctw, n, level, ksc.coef, ksc.ext, st);
-        launch_keyip_grouped(c, ksc.kg, ksc.ks, 1, level, st);
+        launch_keyip_grouped(c, ksc.kg, ksc.ks, 1, (int)n, level, st);
         moddown_prepare(c, ksc.acc, n, level, ksc.conv, st);
-        launch_combine_sum(c, dsum, dent, n, level, st);
+        launch_combine_sum(c, dsum, dent, n, n, level, st);
         c->cnt.rot += n;
         c->cnt.keyswitch += n;
         cur = next;
@@ -195,8 +195,9 @@ extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, u
 }
 
 extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans, const void* const* pts,
-                                uint32_t n, void* const* bufs, void* ws, size_t ws_bytes, void* stream, fe_graph** out) {
-    if (!c || !evk || !plans || !pts || !bufs || !ws || !out) return fail(FE_EINVAL, "null argument");
+                                const void* const* ins, void* const* outs, uint32_t n, void* ws, size_t ws_bytes,
+                                void* stream, fe_graph** out) {
+    if (!c || !evk || !plans || !pts || !ins || !outs || !ws || !out) return fail(FE_EINVAL, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
     if (!st) return fail(FE_EINVAL, "graph capture needs a non-default stream");
     // every layer gets its own workspace slice so that its item tables survive
@@ -208,15 +209,15 @@ extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* con
     }
     if (off[n] > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the captured layers");
     for (uint32_t i = 0; i < n; i++)
-        FE_TRY(run_plan(c, evk, plans[i], (const u64*)bufs[i], (const u64*)pts[i], (u64*)bufs[i + 1],
-                        (char*)ws + off[i], off[i + 1] - off[i], 1, st, 1));
+        FE_TRY(run_plan(c, evk, plans[i], (const u64*)ins[i], (const u64*)pts[i], (u64*)outs[i], (char*)ws + off[i],
+                        off[i + 1] - off[i], 1, st, 1));
     FE_CUDA_TRY(cudaStreamSynchronize(st));
     std::unique_ptr<fe_graph> g(new fe_graph());
     FE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = FE_OK;
     for (uint32_t i = 0; i < n && rc == FE_OK; i++)
-        rc = run_plan(c, evk, plans[i], (const u64*)bufs[i], (const u64*)pts[i], (u64*)bufs[i + 1],
-                      (char*)ws + off[i], off[i + 1] - off[i], 1, st, 2);
+        rc = run_plan(c, evk, plans[i], (const u64*)ins[i], (const u64*)pts[i], (u64*)outs[i], (char*)ws + off[i],
+                      off[i + 1] - off[i], 1, st, 2);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (rc != FE_OK) {

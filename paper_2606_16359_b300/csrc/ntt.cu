@@ -190,8 +190,15 @@ void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st) {
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
     int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
     size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * N2 * 8;
-    ntt_col_pass<false><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
-    ntt_row_pass<false><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
+    const double bytes = 16.0 * limbs * N;
+    {
+        ProfScope ps(c, PK_NTT, st, bytes);
+        ntt_col_pass<false><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
+    }
+    {
+        ProfScope ps(c, PK_NTT, st, bytes);
+        ntt_row_pass<false><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
+    }
     c->cnt.ntt += limbs;
     c->cnt.launches += 2;
 }
@@ -203,8 +210,15 @@ void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st) {
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
     int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
     size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * N2 * 8;
-    ntt_row_pass<true><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
-    ntt_col_pass<true><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
+    const double bytes = 16.0 * limbs * N;
+    {
+        ProfScope ps(c, PK_NTT, st, bytes);
+        ntt_row_pass<true><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
+    }
+    {
+        ProfScope ps(c, PK_NTT, st, bytes);
+        ntt_col_pass<true><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
+    }
     c->cnt.ntt += limbs;
     c->cnt.launches += 2;
 }

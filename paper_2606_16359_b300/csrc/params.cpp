@@ -386,6 +386,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
 extern "C" void fe_ctx_destroy(fe_ctx* c) {
     if (!c) return;
     for (void* p : c->allocs) cudaFree(p);
+    for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     cudaFree(c->pool);
     delete c;
 }
@@ -399,6 +400,61 @@ extern "C" int fe_ctx_moduli(const fe_ctx* c, uint64_t* out) {
 extern "C" int fe_get_counters(const fe_ctx* c, fe_counters* out) {
     if (!c || !out) return fail(FE_EINVAL, "null argument");
     *out = c->cnt;
+    return FE_OK;
+}
+
+namespace fe {
+ProfScope::ProfScope(fe_ctx* ctx, int kind, cudaStream_t s, double bytes)
+    : c(ctx), st(s), on(ctx->prof.kind == kind) {
+    if (!on) return;
+    fe_profiler& p = c->prof;
+    while (p.used + 2 > p.ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            on = false;
+            return;
+        }
+        p.ev.push_back(e);
+    }
+    cudaEventRecord(p.ev[p.used], st);
+    p.bytes += bytes;
+    p.launches++;
+}
+ProfScope::~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(c->prof.ev[c->prof.used + 1], st);
+    c->prof.used += 2;
+}
+}  // namespace fe
+
+extern "C" int fe_profile_begin(fe_ctx* c, const char* kind) {
+    if (!c || !kind) return fail(FE_EINVAL, "null argument");
+    static const char* names[PK_COUNT] = {"ntt", "bconv", "keyip", "combine", "mac", "rescale", "encode"};
+    int k = -1;
+    for (int i = 0; i < PK_COUNT; i++)
+        if (!strcmp(kind, names[i])) k = i;
+    if (k < 0) return fail(FE_EINVAL, std::string("unknown kernel class ") + kind);
+    c->prof.kind = k;
+    c->prof.used = 0;
+    c->prof.bytes = 0;
+    c->prof.launches = 0;
+    return FE_OK;
+}
+
+extern "C" int fe_profile_end(fe_ctx* c, double* total_ms, uint64_t* launches, double* bytes) {
+    if (!c || !total_ms || !launches || !bytes) return fail(FE_EINVAL, "null argument");
+    double t = 0;
+    for (size_t i = 0; i + 1 < c->prof.used; i += 2) {
+        FE_CUDA_TRY(cudaEventSynchronize(c->prof.ev[i + 1]));
+        float ms = 0;
+        FE_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof.ev[i], c->prof.ev[i + 1]));
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = c->prof.launches;
+    *bytes = c->prof.bytes;
+    c->prof.kind = -1;
+    c->prof.used = 0;
     return FE_OK;
 }
 
