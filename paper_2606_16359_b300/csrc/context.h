@@ -59,8 +59,8 @@ struct fe_ctx {
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;
     fe::Modulus* d_mod;             // [n_mod]
-    u64 *d_tw, *d_tw_sh;            // [n_mod][N]  psi^brv(j) and Shoup companions
-    u64 *d_itw, *d_itw_sh;          // [n_mod][N]  psi^-brv(j)
+    u64* d_tw2;                     // [n_mod][N][2]  (psi^brv(j), Shoup companion)
+    u64* d_itw2;                    // [n_mod][N][2]  (psi^-brv(j), Shoup companion)
     u64 *d_ninv, *d_ninv_sh;        // [n_mod] N^-1
     u64 *d_pinv, *d_pinv_sh;        // [n_mod] P^-1 mod q_i (i <= L)
     u64 *d_qlinv, *d_qlinv_sh;      // [L+1][L+1]: q_l^-1 mod q_i at [l][i]
@@ -96,6 +96,9 @@ struct LimbSet {
 };
 void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st);
 void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st);
+// out-of-place: the first pass reads polynomials from src (poly stride src_stride words)
+void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);
+void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);
 
 int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st);
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,

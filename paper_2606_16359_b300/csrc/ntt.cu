@@ -4,12 +4,23 @@
 // in, bit-reversed order out), which computes NTT(a)[i] = a(psi^(2 brv(i) + 1)).
 // Inverse: Gentleman-Sande butterflies with psi^-brv(h + i), then N^-1.
 //
-// The transform of one limb (N = N1 * N2) runs in two passes, each staged in
-// shared memory: the stages whose butterfly distance is a multiple of N2 act
-// on the N2 columns {r + c N2} independently ("column pass"), the remaining
-// stages act on contiguous rows of N2 elements ("row pass").  A CTA loads a
-// tile of several columns (or rows) with coalesced 8-byte loads, runs its
-// stages with __syncthreads between them, and writes the tile back.
+// One limb (N = N1 * N2) is transformed in two passes.  The stages whose
+// butterfly distance is a multiple of N2 act on the N2 columns {x N2 + r}
+// independently ("column pass", lines of length N1); the remaining stages act
+// on the N1 rows of N2 contiguous elements ("row pass", lines of length N2).
+// Stage t of a line of length n with line id `lid` out of `ltot` lines uses
+// the twiddle at index (ltot + lid) * (n / 2t) + floor(x / 2t); for the column
+// pass ltot = 1, lid = 0, for the row pass ltot = N1, lid = row.
+//
+// A CTA stages a tile of lines in shared memory with coalesced loads.  The
+// stages are processed in rounds of up to three: each thread keeps 8 elements
+// of a line (stride s = the round's smallest distance) in registers, runs the
+// round's butterflies there, and writes them back; so a 256-point line needs
+// three shared-memory round trips instead of eight.  Butterflies are Harvey's
+// lazy forms with Shoup multiplication: forward values stay in [0, 4q),
+// inverse values in [0, 2q), and only the final stage reduces to [0, q)
+// (4q < 2^64 since q < 2^62).  The first pass may read a separate source
+// buffer (out-of-place); the second pass works in place.
 #include <algorithm>
 
 #include "context.h"
@@ -19,161 +30,172 @@ namespace fe {
 namespace {
 
 constexpr int kTile = 4096;  // elements per CTA tile (32 KiB)
-constexpr int kThreads = 512;
+constexpr int kE = 8;        // elements per thread per round
 
 struct NttArgs {
-    u64* base;
+    const u64* src;      // first-pass source (may equal dst)
+    size_t src_stride;   // poly stride of src
+    u64* dst;
     size_t poly_stride;
     int per_poly;
     const int* mod_map;
     const Modulus* mods;
-    const u64* tw;  // [n_mod][N]
-    const u64* tw_sh;
+    const ulonglong2* tw;  // [n_mod][N] (w, floor(w 2^64 / q))
     const u64* ninv;
     const u64* ninv_sh;
     int logN, logN2;
 };
 
-__device__ __forceinline__ u64* limb_ptr(const NttArgs& a, int limb, int& mod_idx) {
-    int poly = limb / a.per_poly, j = limb % a.per_poly;
-    mod_idx = a.mod_map[j];
-    return a.base + (size_t)poly * a.poly_stride + ((size_t)j << a.logN);
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wq, u64 q) {
+    return a * w - __umul64hi(a, wq) * q;  // in [0, 2q)
 }
 
-// Column pass: stages with distance t = tr * N2, tr = N1/2 .. 1 (forward) or
-// 1 .. N1/2 (inverse).  Tile = C columns x N1 rows, stored tile[c * C + r].
-template <bool kInverse>
-__global__ void __launch_bounds__(kThreads) ntt_col_pass(NttArgs a) {
-    extern __shared__ u64 tile[];
-    const int N = 1 << a.logN, N2 = 1 << a.logN2, N1 = N >> a.logN2;
-    const int C = min(kTile / N1, N2);
-    const int tiles_per_limb = N2 / C;
-    const int limb = blockIdx.x / tiles_per_limb;
-    const int r0 = (blockIdx.x % tiles_per_limb) * C;
-    int mi;
-    u64* d = limb_ptr(a, limb, mi);
-    const u64 q = a.mods[mi].q;
-    const u64* tw = a.tw + ((size_t)mi << a.logN);
-    const u64* tws = a.tw_sh + ((size_t)mi << a.logN);
-    const int n = N1 * C;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        int c = e / C, r = e % C;
-        tile[e] = d[(size_t)c * N2 + r0 + r];
-    }
-    __syncthreads();
-    const int nb = n / 2;
-    if (!kInverse) {
-        for (int tr = N1 / 2; tr >= 1; tr >>= 1) {
-            const int m = N1 / (2 * tr);
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                int r = b % C, bb = b / C;
-                int grp = bb / tr, pos = bb % tr;
-                int c = grp * 2 * tr + pos;
-                u64 w = tw[m + grp], ws = tws[m + grp];
-                u64 U = tile[c * C + r];
-                u64 V = mul_shoup(tile[(c + tr) * C + r], w, ws, q);
-                tile[c * C + r] = add_mod(U, V, q);
-                tile[(c + tr) * C + r] = sub_mod(U, V, q);
+// One line transform round: `lo` = log2 of the round's smallest distance (s),
+// `nst` = number of stages (distances s * 2^(nst-1) .. s), thread holds
+// v[r] = line[base + r s] for r < E (E = min(8, line length)).  The three stage
+// slots are unrolled so every register index is a compile-time constant.
+template <bool kInv>
+__device__ __forceinline__ void round_stages(u64 (&v)[kE], int base, int lo, int nst, int E, int logn,
+                                             int tw_line, const ulonglong2* __restrict__ tw, u64 q) {
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int si = 0; si < 3; si++) {
+        const int st = kInv ? si : 2 - si;  // forward: large distances first
+        if (st >= nst) continue;
+        const int d = 1 << st;
+        const int lt = lo + st;
+#pragma unroll
+        for (int r = 0; r < kE; r++) {
+            if ((r & d) || r + d >= E) continue;
+            const int x = base + (r << lo);
+            const ulonglong2 w = tw[(tw_line << (logn - 1 - lt)) + (x >> (lt + 1))];
+            if (!kInv) {
+                u64 X = v[r];
+                X = X >= q2 ? X - q2 : X;
+                const u64 T = shoup_lazy(v[r + d], w.x, w.y, q);
+                v[r] = X + T;
+                v[r + d] = X - T + q2;
+            } else {
+                const u64 X = v[r], Y = v[r + d];
+                u64 S = X + Y;
+                v[r] = S >= q2 ? S - q2 : S;
+                v[r + d] = shoup_lazy(X - Y + q2, w.x, w.y, q);
             }
-            __syncthreads();
+        }
+    }
+}
+
+// kCol: column pass (lines = columns of length N1) else row pass (lines = rows of length N2).
+template <bool kInv, bool kCol>
+__global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
+    extern __shared__ u64 tile[];
+    const int N2 = 1 << a.logN2, N1 = 1 << (a.logN - a.logN2);
+    const int logn = kCol ? a.logN - a.logN2 : a.logN2;
+    const int n = 1 << logn;
+    const int lines = kCol ? min(kTile / N1, N2) : min(kTile / N2, N1);
+    const int tiles_per_limb = (kCol ? N2 : N1) / lines;
+    const int limb = blockIdx.x / tiles_per_limb;
+    const int l0 = (blockIdx.x % tiles_per_limb) * lines;
+    const int poly = limb / a.per_poly, jl = limb % a.per_poly;
+    const int mi = a.mod_map[jl];
+    const u64 q = a.mods[mi].q;
+    const ulonglong2* tw = a.tw + ((size_t)mi << a.logN);
+    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)jl << a.logN);
+    const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)jl << a.logN) : d;
+    const int total = lines * n;
+    // coalesced load: column pass tile[x * lines + c], row pass tile[row * N2 + x]
+    // row tiles pad one word per 8 so that the strided rounds avoid bank conflicts
+    const int rs = N2 + (N2 >> 3);
+#define RIDX(ln, x) ((ln) * rs + (x) + ((x) >> 3))
+    if (kCol) {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int x = e / lines, c = e - x * lines;
+            tile[e] = s[(size_t)x * N2 + l0 + c];
         }
     } else {
+        const u64* g = s + (size_t)l0 * N2;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) tile[RIDX(e >> a.logN2, e & (N2 - 1))] = g[e];
+    }
+    __syncthreads();
+    const int E = min(kE, n);
+    const int tpl = n / E;                    // threads per line
+    const int nthr = lines * tpl;
+    const int tid = threadIdx.x;
+    const int line = kCol ? tid % lines : tid / tpl;
+    const int j = kCol ? tid / lines : tid % tpl;
+    const int tw_line = kCol ? 1 : (N1 + l0 + line);
+    // rounds: exponent chunks of 3 from the top, remainder at the bottom
+    const int nr = (logn + 2) / 3;
+    for (int rr = 0; rr < nr; rr++) {
+        const int k = kInv ? nr - 1 - rr : rr;  // chunk index from the top
+        const int hi = logn - 1 - 3 * k;        // largest exponent of the chunk
+        const int lo = max(0, hi - 2);
+        const int nst = hi - lo + 1;
+        const int sft = lo;                     // s = 2^lo
+        u64 v[kE];
+        int base = 0;
+        if (tid < nthr) {
+            // thread j of the line: block (j >> sft), offset (j & (s - 1)), block size 8 s
+            base = ((j >> sft) << (sft + 3)) + (j & ((1 << sft) - 1));
+            if (E < kE) base = 0;
+#pragma unroll
+            for (int r = 0; r < kE; r++) {
+                const int x = base + (r << sft);
+                v[r] = (r < E) ? (kCol ? tile[x * lines + line] : tile[RIDX(line, x)]) : 0;
+            }
+            round_stages<kInv>(v, base, lo, nst, E, logn, tw_line, tw, q);
+        }
+        __syncthreads();
+        if (tid < nthr) {
+#pragma unroll
+            for (int r = 0; r < kE; r++) {
+                if (r >= E) break;
+                const int x = base + (r << sft);
+                if (kCol) tile[x * lines + line] = v[r];
+                else tile[RIDX(line, x)] = v[r];
+            }
+        }
+        __syncthreads();
+    }
+    // final reduction happens in the pass that completes the transform
+    const bool last_pass = kInv ? kCol : !kCol;
+    if (last_pass) {
+        const u64 q2 = 2 * q;
         const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
-        for (int tr = 1; tr <= N1 / 2; tr <<= 1) {
-            const int h = N1 / (2 * tr);
-            const bool last = (tr == N1 / 2);
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                int r = b % C, bb = b / C;
-                int grp = bb / tr, pos = bb % tr;
-                int c = grp * 2 * tr + pos;
-                u64 w = tw[h + grp], ws = tws[h + grp];
-                u64 U = tile[c * C + r], V = tile[(c + tr) * C + r];
-                u64 s = add_mod(U, V, q);
-                u64 t = mul_shoup(sub_mod(U, V, q), w, ws, q);
-                if (last) {
-                    s = mul_shoup(s, ni, nis, q);
-                    t = mul_shoup(t, ni, nis, q);
-                }
-                tile[c * C + r] = s;
-                tile[(c + tr) * C + r] = t;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int p = kCol ? e : RIDX(e >> a.logN2, e & (N2 - 1));
+            u64 x = tile[p];
+            if (kInv) {
+                x = shoup_lazy(x, ni, nis, q);  // [0, 2q)
+            } else {
+                x = x >= q2 ? x - q2 : x;
             }
-            __syncthreads();
+            tile[p] = x >= q ? x - q : x;
         }
+        __syncthreads();
     }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        int c = e / C, r = e % C;
-        d[(size_t)c * N2 + r0 + r] = tile[e];
-    }
-}
-
-// Row pass: stages with distance t = N2/2 .. 1 (forward) or 1 .. N2/2 (inverse),
-// within rows of N2 contiguous elements.  Tile = R rows.
-template <bool kInverse>
-__global__ void __launch_bounds__(kThreads) ntt_row_pass(NttArgs a) {
-    extern __shared__ u64 tile[];
-    const int N = 1 << a.logN, N2 = 1 << a.logN2, N1 = N >> a.logN2;
-    const int R = min(kTile / N2, N1);
-    const int tiles_per_limb = N1 / R;
-    const int limb = blockIdx.x / tiles_per_limb;
-    const int row0 = (blockIdx.x % tiles_per_limb) * R;
-    int mi;
-    u64* d = limb_ptr(a, limb, mi);
-    const u64 q = a.mods[mi].q;
-    const u64* tw = a.tw + ((size_t)mi << a.logN);
-    const u64* tws = a.tw_sh + ((size_t)mi << a.logN);
-    const int n = R * N2;
-    u64* g = d + (size_t)row0 * N2;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) tile[e] = g[e];
-    __syncthreads();
-    const int nb = n / 2, half = N2 / 2;
-    if (!kInverse) {
-        for (int t = N2 / 2; t >= 1; t >>= 1) {
-            const int gpr = N2 / (2 * t);  // groups per row
-            const int m = N / (2 * t);
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                int rho = b / half, bb = b % half;
-                int grp = bb / t, pos = bb % t;
-                int x = grp * 2 * t + pos;
-                int i = (row0 + rho) * gpr + grp;
-                u64 w = tw[m + i], ws = tws[m + i];
-                int o = rho * N2 + x;
-                u64 U = tile[o];
-                u64 V = mul_shoup(tile[o + t], w, ws, q);
-                tile[o] = add_mod(U, V, q);
-                tile[o + t] = sub_mod(U, V, q);
-            }
-            __syncthreads();
+    if (kCol) {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int x = e / lines, c = e - x * lines;
+            d[(size_t)x * N2 + l0 + c] = tile[e];
         }
     } else {
-        for (int t = 1; t <= N2 / 2; t <<= 1) {
-            const int gpr = N2 / (2 * t);
-            const int h = N / (2 * t);
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                int rho = b / half, bb = b % half;
-                int grp = bb / t, pos = bb % t;
-                int x = grp * 2 * t + pos;
-                int i = (row0 + rho) * gpr + grp;
-                u64 w = tw[h + i], ws = tws[h + i];
-                int o = rho * N2 + x;
-                u64 U = tile[o], V = tile[o + t];
-                tile[o] = add_mod(U, V, q);
-                tile[o + t] = mul_shoup(sub_mod(U, V, q), w, ws, q);
-            }
-            __syncthreads();
-        }
+        u64* g = d + (size_t)l0 * N2;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) g[e] = tile[RIDX(e >> a.logN2, e & (N2 - 1))];
     }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) g[e] = tile[e];
+#undef RIDX
 }
 
-NttArgs make_args(fe_ctx* c, const LimbSet& s, bool inverse) {
+NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, bool inverse) {
     NttArgs a;
-    a.base = s.base;
+    a.src = src ? src : s.base;
+    a.src_stride = src ? src_stride : s.poly_stride;
+    a.dst = s.base;
     a.poly_stride = s.poly_stride;
     a.per_poly = s.per_poly;
     a.mod_map = s.mod_map;
     a.mods = c->d_mod;
-    a.tw = inverse ? c->d_itw : c->d_tw;
-    a.tw_sh = inverse ? c->d_itw_sh : c->d_tw_sh;
+    a.tw = (const ulonglong2*)(inverse ? c->d_itw2 : c->d_tw2);
     a.ninv = c->d_ninv;
     a.ninv_sh = c->d_ninv_sh;
     a.logN = c->logN;
@@ -181,46 +203,50 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, bool inverse) {
     return a;
 }
 
-}  // namespace
+int threads_for(int lines, int n) { return std::max(32, lines * (n / std::min(kE, n))); }
 
-void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st) {
+template <bool kInv>
+void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cudaStream_t st) {
     int limbs = s.per_poly * s.n_poly;
     if (limbs == 0) return;
-    NttArgs a = make_args(c, s, false);
+    NttArgs a = make_args(c, s, src, src_stride, kInv);
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
-    int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
-    size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * N2 * 8;
+    const int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
+    const size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
     const double bytes = 16.0 * limbs * N;
-    {
-        ProfScope ps(c, PK_NTT, st, bytes);
-        ntt_col_pass<false><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
-    }
-    {
-        ProfScope ps(c, PK_NTT, st, bytes);
-        ntt_row_pass<false><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
+    const int tc = threads_for(C, N1), tr = threads_for(R, N2);
+    if (!kInv) {
+        {
+            ProfScope ps(c, PK_NTT, st, bytes);
+            ntt_pass<false, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
+        }
+        {
+            ProfScope ps(c, PK_NTT, st, bytes);
+            ntt_pass<false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
+        }
+    } else {
+        {
+            ProfScope ps(c, PK_NTT, st, bytes);
+            ntt_pass<true, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 1);
+        }
+        {
+            ProfScope ps(c, PK_NTT, st, bytes);
+            ntt_pass<true, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 0);
+        }
     }
     c->cnt.ntt += limbs;
     c->cnt.launches += 2;
 }
 
-void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st) {
-    int limbs = s.per_poly * s.n_poly;
-    if (limbs == 0) return;
-    NttArgs a = make_args(c, s, true);
-    const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
-    int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
-    size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * N2 * 8;
-    const double bytes = 16.0 * limbs * N;
-    {
-        ProfScope ps(c, PK_NTT, st, bytes);
-        ntt_row_pass<true><<<limbs * (N1 / R), kThreads, smr, st>>>(a);
-    }
-    {
-        ProfScope ps(c, PK_NTT, st, bytes);
-        ntt_col_pass<true><<<limbs * (N2 / C), kThreads, smc, st>>>(a);
-    }
-    c->cnt.ntt += limbs;
-    c->cnt.launches += 2;
+}  // namespace
+
+void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<false>(c, s, nullptr, 0, st); }
+void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<true>(c, s, nullptr, 0, st); }
+void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st) {
+    run_ntt<false>(c, dst, src, src_stride, st);
+}
+void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st) {
+    run_ntt<true>(c, dst, src, src_stride, st);
 }
 
 }  // namespace fe

@@ -137,9 +137,7 @@ void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* 
            cudaStream_t st) {
     if (n == 0) return;
     const int N = c->N, nl = level + 1, np = level + 1 + c->k, dn = dnum_at(c, level);
-    cudaMemcpy2DAsync(coef, (size_t)nl * N * 8, src, src_stride * 8, (size_t)nl * N * 8, n,
-                      cudaMemcpyDeviceToDevice, st);
-    ntt_inverse(c, LimbSet{coef, (size_t)nl * N, nl, n, c->d_identity_map}, st);
+    ntt_inverse_from(c, src, src_stride, LimbSet{coef, (size_t)nl * N, nl, n, c->d_identity_map}, st);
     for (int j = 0; j < dn; j++)
         launch_bconv(c, c->lv[level].modup[j], level, coef, (size_t)nl * N, 0, ext + (size_t)j * np * N,
                      (size_t)dn * np * N, n, true, st);
@@ -165,9 +163,8 @@ void rescale_batch(fe_ctx* c, const u64* in, int n, int level, u64* out, u64* tm
                    cudaStream_t st) {
     if (n == 0) return;
     const int N = c->N, nl = level + 1;
-    cudaMemcpy2DAsync(tmp, (size_t)N * 8, in + (size_t)level * N, (size_t)nl * N * 8, (size_t)N * 8, 2 * n,
-                      cudaMemcpyDeviceToDevice, st);
-    ntt_inverse(c, LimbSet{tmp, (size_t)N, 1, 2 * n, c->d_identity_map + level}, st);
+    ntt_inverse_from(c, in + (size_t)level * N, (size_t)nl * N, LimbSet{tmp, (size_t)N, 1, 2 * n, c->d_identity_map + level},
+                     st);
     launch_bconv(c, c->lv[level].rescale, level, tmp, (size_t)N, level, lift, (size_t)level * N, 2 * n,
                  false, st);
     ntt_forward(c, LimbSet{lift, (size_t)level * N, level, 2 * n, c->d_identity_map}, st);

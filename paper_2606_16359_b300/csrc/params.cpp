@@ -236,8 +236,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
             th.emplace_back([&, i] { c->psi[i] = min_primitive_root_2N(c->mod[i], c->logN); });
         for (auto& t : th) t.join();
     }
-    std::vector<u64> tw((size_t)nm * N), tw_sh((size_t)nm * N), itw((size_t)nm * N),
-        itw_sh((size_t)nm * N);
+    std::vector<u64> tw2((size_t)nm * N * 2), itw2((size_t)nm * N * 2);
     std::vector<u64> ninv(nm), ninv_sh(nm), pinv(nm, 0), pinv_sh(nm, 0);
     {
         std::vector<std::thread> th;
@@ -253,10 +252,10 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
                 }
                 for (int j = 0; j < N; j++) {
                     u64 a = pw[bitrev(j, c->logN)], b = pwi[bitrev(j, c->logN)];
-                    tw[(size_t)i * N + j] = a;
-                    tw_sh[(size_t)i * N + j] = shoup_of(a, q);
-                    itw[(size_t)i * N + j] = b;
-                    itw_sh[(size_t)i * N + j] = shoup_of(b, q);
+                    tw2[2 * ((size_t)i * N + j)] = a;
+                    tw2[2 * ((size_t)i * N + j) + 1] = shoup_of(a, q);
+                    itw2[2 * ((size_t)i * N + j)] = b;
+                    itw2[2 * ((size_t)i * N + j) + 1] = shoup_of(b, q);
                 }
                 ninv[i] = h_invmod((u64)N % q, q);
                 ninv_sh[i] = shoup_of(ninv[i], q);
@@ -372,10 +371,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         FE_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice));
         return FE_OK;
     };
-    FE_TRY(up(&c->d_tw, tw));
-    FE_TRY(up(&c->d_tw_sh, tw_sh));
-    FE_TRY(up(&c->d_itw, itw));
-    FE_TRY(up(&c->d_itw_sh, itw_sh));
+    FE_TRY(up(&c->d_tw2, tw2));
+    FE_TRY(up(&c->d_itw2, itw2));
     FE_CUDA_TRY(cudaMalloc(&c->d_dd_w, ddw.size() * sizeof(double)));
     c->allocs.push_back(c->d_dd_w);
     FE_CUDA_TRY(cudaMemcpy(c->d_dd_w, ddw.data(), ddw.size() * sizeof(double), cudaMemcpyHostToDevice));
