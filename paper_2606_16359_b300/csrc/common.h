@@ -29,6 +29,12 @@ int fail(int code, const std::string& msg);
             return ::fe::fail(FE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
     } while (0)
 
+// device buffers must start on a 16-byte boundary (the kernels use 16-byte accesses)
+#define FE_ALIGNED(p)                                                                      \
+    do {                                                                                   \
+        if (((uintptr_t)(p)) & 15) return ::fe::fail(FE_EINVAL, #p " is not 16-byte aligned"); \
+    } while (0)
+
 #define FE_TRY(expr)                  \
     do {                              \
         int _rc = (expr);             \

@@ -56,6 +56,7 @@ struct fe_evk {
 struct fe_ctx {
     fe_params prm;
     int logN, N, L, k, n_mod, dnum;
+    int max_mod_bits;  // bit length of the largest modulus
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;
     fe::Modulus* d_mod;             // [n_mod]

@@ -675,6 +675,7 @@ extern "C" int fe_plan_rotation_steps(const fe_plan* p, int32_t* steps, uint32_t
 
 extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host, double wmul, double w_scale,
                                     void* pt_dev, void* stream) {
+    FE_ALIGNED(pt_dev);
     if (!c || !p || !W_host || !pt_dev) return fail(FE_EINVAL, "null argument");
     if (p->n_pt == 0) return FE_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -722,6 +723,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
 
 extern "C" int fe_he_conv(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
                           void* out_dev, void* ws, size_t ws_bytes, int mode, void* stream) {
+    FE_ALIGNED(pt_dev); FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
     if (!c || !evk || !p || !pt_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
     if (p->kind != 0) return fail(FE_EINVAL, "not a conv plan");
     return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
@@ -730,6 +732,7 @@ extern "C" int fe_he_conv(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const 
 
 extern "C" int fe_he_fc(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
                         void* out_dev, void* ws, size_t ws_bytes, int mode, void* stream) {
+    FE_ALIGNED(pt_dev); FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
     if (!c || !evk || !p || !pt_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
     if (p->kind != 1) return fail(FE_EINVAL, "not an fc plan");
     return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,

@@ -69,6 +69,7 @@ extern "C" size_t fe_square_workspace_bytes(const fe_ctx* c, uint32_t n, uint32_
 
 extern "C" int fe_he_square(fe_ctx* c, const fe_evk* evk, const void* in_dev, uint32_t n, uint32_t level,
                             void* out_dev, void* ws, size_t ws_bytes, void* stream) {
+    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
     if (!c || !evk || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
     if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "x^2 needs a level to rescale");
     if (!evk->relin) return fail(FE_EKEY, "no relinearisation key");
@@ -139,6 +140,7 @@ extern "C" size_t fe_compress_workspace_bytes(const fe_ctx* c, uint32_t n, uint3
 
 extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid, const void* in_dev,
                            uint32_t n, uint32_t level, void* out_dev, void* ws, size_t ws_bytes, void* stream) {
+    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
     if (!c || !evk || !lay || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     fe_layout L = *lay;

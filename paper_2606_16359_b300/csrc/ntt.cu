@@ -19,7 +19,8 @@
 // three shared-memory round trips instead of eight.  Butterflies are Harvey's
 // lazy forms with Shoup multiplication: forward values stay in [0, 4q),
 // inverse values in [0, 2q), and only the final stage reduces to [0, q)
-// (4q < 2^64 since q < 2^62).  The first pass may read a separate source
+// (4q < 2^64 since q < 2^62); with all moduli below 2^58 the forward
+// transform skips reductions until its last stage (see round_stages).  The first pass may read a separate source
 // buffer (out-of-place); the second pass works in place.
 #include <algorithm>
 
@@ -52,10 +53,15 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wq, u64 q) {
 
 // One line transform round: `lo` = log2 of the round's smallest distance (s),
 // `nst` = number of stages (distances s * 2^(nst-1) .. s), thread holds
-// v[r] = line[base + r s] for r < E (E = min(8, line length)).  The three stage
-// slots are unrolled so every register index is a compile-time constant.
-template <bool kInv>
-__device__ __forceinline__ void round_stages(u64 (&v)[kE], int base, int lo, int nst, int E, int logn,
+// v[r] = line[base + r s] for r < E (E = min(8, line length)), base = blk 8 s + off.
+// Stage t = s 2^st needs twiddle index (tw_line << (logn-1-lt)) + (x >> (lt+1)) with
+// lt = lo + st; for x = base + r s this is K + (r >> (st+1)), K = (tw_line << (logn-1-lt))
+// + (blk << (2-st)), so each stage loads its 8 >> (st+1) distinct twiddles once.
+// The three stage slots are unrolled so every register index is a compile-time constant.
+// kNoRed (forward only, all moduli < 2^58): no reduction inside the transform;
+// each stage adds less than 2q, so values stay below (1 + 2 * 17) q < 2^64.
+template <bool kInv, bool kNoRed>
+__device__ __forceinline__ void round_stages(u64 (&v)[kE], int blk, int lo, int nst, int E, int logn,
                                              int tw_line, const ulonglong2* __restrict__ tw, u64 q) {
     const u64 q2 = 2 * q;
 #pragma unroll
@@ -64,29 +70,34 @@ __device__ __forceinline__ void round_stages(u64 (&v)[kE], int base, int lo, int
         if (st >= nst) continue;
         const int d = 1 << st;
         const int lt = lo + st;
+        const int K = (tw_line << (logn - 1 - lt)) + (blk << (2 - st));
+        const int cnt = max(1, E >> (st + 1));
+        ulonglong2 w[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (i < (4 >> st) && i < cnt) w[i] = tw[K + i];
 #pragma unroll
         for (int r = 0; r < kE; r++) {
             if ((r & d) || r + d >= E) continue;
-            const int x = base + (r << lo);
-            const ulonglong2 w = tw[(tw_line << (logn - 1 - lt)) + (x >> (lt + 1))];
+            const ulonglong2 ww = w[r >> (st + 1)];
             if (!kInv) {
                 u64 X = v[r];
-                X = X >= q2 ? X - q2 : X;
-                const u64 T = shoup_lazy(v[r + d], w.x, w.y, q);
+                if (!kNoRed) X = X >= q2 ? X - q2 : X;
+                const u64 T = shoup_lazy(v[r + d], ww.x, ww.y, q);
                 v[r] = X + T;
                 v[r + d] = X - T + q2;
             } else {
                 const u64 X = v[r], Y = v[r + d];
                 u64 S = X + Y;
                 v[r] = S >= q2 ? S - q2 : S;
-                v[r + d] = shoup_lazy(X - Y + q2, w.x, w.y, q);
+                v[r + d] = shoup_lazy(X - Y + q2, ww.x, ww.y, q);
             }
         }
     }
 }
 
 // kCol: column pass (lines = columns of length N1) else row pass (lines = rows of length N2).
-template <bool kInv, bool kCol>
+template <bool kInv, bool kCol, bool kNoRed>
 __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     extern __shared__ u64 tile[];
     const int N2 = 1 << a.logN2, N1 = 1 << (a.logN - a.logN2);
@@ -107,14 +118,40 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     // row tiles pad one word per 8 so that the strided rounds avoid bank conflicts
     const int rs = N2 + (N2 >> 3);
 #define RIDX(ln, x) ((ln) * rs + (x) + ((x) >> 3))
-    if (kCol) {
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            const int x = e / lines, c = e - x * lines;
-            tile[e] = s[(size_t)x * N2 + l0 + c];
+    // load: each thread issues all of its 16-byte loads before storing to shared memory
+    {
+        const int pairs = total >> 1;
+        for (int e0 = 0; e0 < pairs; e0 += 4 * blockDim.x) {
+            ulonglong2 buf[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int e = e0 + threadIdx.x + k * blockDim.x;
+                if (e < pairs) {
+                    const int el = 2 * e;
+                    if (kCol) {
+                        const int x = el / lines, c = el - x * lines;
+                        buf[k] = *reinterpret_cast<const ulonglong2*>(s + (size_t)x * N2 + l0 + c);
+                    } else {
+                        buf[k] = *reinterpret_cast<const ulonglong2*>(s + (size_t)l0 * N2 + el);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int e = e0 + threadIdx.x + k * blockDim.x;
+                if (e < pairs) {
+                    const int el = 2 * e;
+                    if (kCol) {
+                        tile[el] = buf[k].x;
+                        tile[el + 1] = buf[k].y;
+                    } else {
+                        const int ln = el >> a.logN2, x = el & (N2 - 1);
+                        tile[RIDX(ln, x)] = buf[k].x;
+                        tile[RIDX(ln, x + 1)] = buf[k].y;
+                    }
+                }
+            }
         }
-    } else {
-        const u64* g = s + (size_t)l0 * N2;
-        for (int e = threadIdx.x; e < total; e += blockDim.x) tile[RIDX(e >> a.logN2, e & (N2 - 1))] = g[e];
     }
     __syncthreads();
     const int E = min(kE, n);
@@ -136,14 +173,15 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
         int base = 0;
         if (tid < nthr) {
             // thread j of the line: block (j >> sft), offset (j & (s - 1)), block size 8 s
-            base = ((j >> sft) << (sft + 3)) + (j & ((1 << sft) - 1));
-            if (E < kE) base = 0;
+            int blk = j >> sft;
+            base = (blk << (sft + 3)) + (j & ((1 << sft) - 1));
+            if (E < kE) base = blk = 0;
 #pragma unroll
             for (int r = 0; r < kE; r++) {
                 const int x = base + (r << sft);
                 v[r] = (r < E) ? (kCol ? tile[x * lines + line] : tile[RIDX(line, x)]) : 0;
             }
-            round_stages<kInv>(v, base, lo, nst, E, logn, tw_line, tw, q);
+            round_stages<kInv, kNoRed>(v, blk, lo, nst, E, logn, tw_line, tw, q);
         }
         __syncthreads();
         if (tid < nthr) {
@@ -157,31 +195,35 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
         }
         __syncthreads();
     }
-    // final reduction happens in the pass that completes the transform
+    // final reduction happens in the pass that completes the transform; fused into the store
     const bool last_pass = kInv ? kCol : !kCol;
-    if (last_pass) {
-        const u64 q2 = 2 * q;
-        const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            const int p = kCol ? e : RIDX(e >> a.logN2, e & (N2 - 1));
-            u64 x = tile[p];
-            if (kInv) {
-                x = shoup_lazy(x, ni, nis, q);  // [0, 2q)
+    const u64 q2 = 2 * q;
+    const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
+    const u64 qinv64 = a.mods[mi].ratio_hi;  // floor(2^64 / q)
+    auto fin = [&](u64 x) -> u64 {
+        if (!last_pass) return x;
+        if (kInv) x = shoup_lazy(x, ni, nis, q);      // [0, 2q)
+        else if (kNoRed) x -= __umul64hi(x, qinv64) * q;  // [0, 2q)
+        else x = x >= q2 ? x - q2 : x;
+        return x >= q ? x - q : x;
+    };
+    {
+        const int pairs = total >> 1;
+        for (int e = threadIdx.x; e < pairs; e += blockDim.x) {
+            const int el = 2 * e;
+            ulonglong2 o;
+            if (kCol) {
+                o.x = fin(tile[el]);
+                o.y = fin(tile[el + 1]);
+                const int x = el / lines, c = el - x * lines;
+                *reinterpret_cast<ulonglong2*>(d + (size_t)x * N2 + l0 + c) = o;
             } else {
-                x = x >= q2 ? x - q2 : x;
+                const int ln = el >> a.logN2, x = el & (N2 - 1);
+                o.x = fin(tile[RIDX(ln, x)]);
+                o.y = fin(tile[RIDX(ln, x + 1)]);
+                *reinterpret_cast<ulonglong2*>(d + (size_t)l0 * N2 + el) = o;
             }
-            tile[p] = x >= q ? x - q : x;
         }
-        __syncthreads();
-    }
-    if (kCol) {
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            const int x = e / lines, c = e - x * lines;
-            d[(size_t)x * N2 + l0 + c] = tile[e];
-        }
-    } else {
-        u64* g = d + (size_t)l0 * N2;
-        for (int e = threadIdx.x; e < total; e += blockDim.x) g[e] = tile[RIDX(e >> a.logN2, e & (N2 - 1))];
     }
 #undef RIDX
 }
@@ -216,22 +258,25 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const double bytes = 16.0 * limbs * N;
     const int tc = threads_for(C, N1), tr = threads_for(R, N2);
     if (!kInv) {
+        const bool nored = c->max_mod_bits <= 58;
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<false, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
+            if (nored) ntt_pass<false, true, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
+            else ntt_pass<false, true, false><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
+            if (nored) ntt_pass<false, false, true><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
+            else ntt_pass<false, false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<true, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 1);
+            ntt_pass<true, false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<true, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 0);
+            ntt_pass<true, true, false><<<limbs * (N2 / C), tc, smc, st>>>(a, 0);
         }
     }
     c->cnt.ntt += limbs;

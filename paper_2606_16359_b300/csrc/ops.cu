@@ -192,6 +192,7 @@ using namespace fe;
 // ---------------------------------------------------------------------------
 
 extern "C" int fe_sk_gen(fe_ctx* c, uint64_t seed, void* sk_dev, void* stream) {
+    FE_ALIGNED(sk_dev);
     if (!c || !sk_dev) return fail(FE_EINVAL, "null argument");
     return sk_gen(c, seed, (u64*)sk_dev, (cudaStream_t)stream);
 }
@@ -204,6 +205,7 @@ extern "C" size_t fe_evk_bytes(const fe_ctx* c, uint32_t n_steps, int relin) {
 extern "C" int fe_evk_gen(fe_ctx* c, const void* sk_dev, uint64_t seed, const int32_t* steps,
                           uint32_t n_steps, int relin, void* evk_dev, size_t evk_bytes, void* stream,
                           fe_evk** out) {
+    FE_ALIGNED(evk_dev); FE_ALIGNED(sk_dev);
     if (!c || !sk_dev || !evk_dev || !out || (n_steps && !steps)) return fail(FE_EINVAL, "null argument");
     if (evk_bytes < fe_evk_bytes(c, n_steps, relin)) return fail(FE_ENOMEM, "evk buffer too small");
     cudaStream_t st = (cudaStream_t)stream;
@@ -278,6 +280,7 @@ extern "C" void fe_evk_destroy(fe_evk* evk) { delete evk; }
 
 extern "C" int fe_encode(fe_ctx* c, const double* slots, uint32_t n, uint32_t level, double scale,
                          void* pt_dev, void* stream) {
+    FE_ALIGNED(pt_dev);
     if (!c || !slots || !pt_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     return encode_batch(c, slots, (int)n, (int)level, scale, (u64*)pt_dev, (cudaStream_t)stream);
@@ -286,6 +289,7 @@ extern "C" int fe_encode(fe_ctx* c, const double* slots, uint32_t n, uint32_t le
 extern "C" int fe_encode_encrypt(fe_ctx* c, const void* sk_dev, const double* slots, uint32_t n_ct,
                                  uint32_t level, double scale, uint64_t seed, uint64_t ct_id0, void* ct_dev,
                                  void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(sk_dev);
     if (!c || !sk_dev || !slots || !ct_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     if (ct_id0 + n_ct >= (1ull << 32)) return fail(FE_EINVAL, "ciphertext ids must stay below 2^32");
@@ -316,6 +320,7 @@ extern "C" int fe_encode_encrypt(fe_ctx* c, const void* sk_dev, const double* sl
 
 extern "C" int fe_decrypt_decode(fe_ctx* c, const void* sk_dev, const void* ct_dev, uint32_t n_ct,
                                  uint32_t level, double scale, double* slots, void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(sk_dev);
     if (!c || !sk_dev || !ct_dev || !slots) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     if (n_ct == 0) return FE_OK;
@@ -345,6 +350,7 @@ extern "C" int fe_decrypt_decode(fe_ctx* c, const void* sk_dev, const void* ct_d
 
 extern "C" int fe_ntt(fe_ctx* c, void* data, uint32_t n_poly, uint32_t n_limbs, uint32_t first_mod,
                       int inverse, void* stream) {
+    FE_ALIGNED(data);
     if (!c || !data) return fail(FE_EINVAL, "null argument");
     if ((int)(first_mod + n_limbs) > c->n_mod) return fail(FE_EINVAL, "limb range outside the moduli");
     LimbSet s{(u64*)data, (size_t)n_limbs * c->N, (int)n_limbs, (int)n_poly, c->d_identity_map + first_mod};
@@ -358,6 +364,7 @@ extern "C" int fe_ntt(fe_ctx* c, void* data, uint32_t n_poly, uint32_t n_limbs, 
 
 extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                          int32_t r, void* out_dev, void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);
     if (!c || !evk || !ct_dev || !out_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     if (n_ct == 0) return FE_OK;
@@ -409,6 +416,7 @@ extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint3
 
 extern "C" int fe_rescale(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
                           void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);
     if (!c || !ct_dev || !out_dev) return fail(FE_EINVAL, "null argument");
     if (level == 0) return fail(FE_ELEVEL, "rescale at level 0");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");

@@ -222,6 +222,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     std::vector<u64> sp = prime_run(c->logN, p->pbits, p->k, c->mod);
     if ((int)sp.size() != (int)p->k) return fail(FE_EINVAL, "not enough special primes");
     c->mod.insert(c->mod.end(), sp.begin(), sp.end());
+    c->max_mod_bits = 0;
+    for (u64 m : c->mod) c->max_mod_bits = std::max(c->max_mod_bits, 64 - __builtin_clzll(m));
 
     int dev;
     FE_CUDA_TRY(cudaGetDevice(&dev));
