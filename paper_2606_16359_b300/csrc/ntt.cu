@@ -97,35 +97,44 @@ __device__ __forceinline__ void round_stages(u64 (&v)[kE], int blk, int lo, int 
 }
 
 // kCol: column pass (lines = columns of length N1) else row pass (lines = rows of length N2).
-template <bool kInv, bool kCol, bool kNoRed>
+// kLogN > 0 fixes the ring degree at compile time so that the tile geometry, the
+// round structure and every shift fold into constants; kLogN = 0 reads it at run time.
+template <int kLogN, bool kInv, bool kCol, bool kNoRed>
 __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     extern __shared__ u64 tile[];
-    const int N2 = 1 << a.logN2, N1 = 1 << (a.logN - a.logN2);
-    const int logn = kCol ? a.logN - a.logN2 : a.logN2;
+    const int logN = kLogN ? kLogN : a.logN;
+    const int logN2 = kLogN ? kLogN / 2 : a.logN2;
+    const int N2 = 1 << logN2, N1 = 1 << (logN - logN2);
+    const int logn = kCol ? logN - logN2 : logN2;
     const int n = 1 << logn;
     const int lines = kCol ? min(kTile / N1, N2) : min(kTile / N2, N1);
     const int tiles_per_limb = (kCol ? N2 : N1) / lines;
+    const int E = min(kE, n);
+    const int tpl = n / E;  // threads per line
+    const int nthr = lines * tpl;
+    const int nthreads = kLogN ? (nthr > 32 ? nthr : 32) : (int)blockDim.x;
     const int limb = blockIdx.x / tiles_per_limb;
     const int l0 = (blockIdx.x % tiles_per_limb) * lines;
     const int poly = limb / a.per_poly, jl = limb % a.per_poly;
     const int mi = a.mod_map[jl];
     const u64 q = a.mods[mi].q;
-    const ulonglong2* tw = a.tw + ((size_t)mi << a.logN);
-    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)jl << a.logN);
-    const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)jl << a.logN) : d;
+    const ulonglong2* tw = a.tw + ((size_t)mi << logN);
+    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)jl << logN);
+    const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)jl << logN) : d;
     const int total = lines * n;
-    // coalesced load: column pass tile[x * lines + c], row pass tile[row * N2 + x]
-    // row tiles pad one word per 8 so that the strided rounds avoid bank conflicts
+    // column pass tile[x * lines + c]; row pass tile[RIDX(row, x)] with one pad word per 8
+    // so that the strided rounds avoid bank conflicts
     const int rs = N2 + (N2 >> 3);
 #define RIDX(ln, x) ((ln) * rs + (x) + ((x) >> 3))
     // load: each thread issues all of its 16-byte loads before storing to shared memory
     {
         const int pairs = total >> 1;
-        for (int e0 = 0; e0 < pairs; e0 += 4 * blockDim.x) {
+#pragma unroll 1
+        for (int e0 = 0; e0 < pairs; e0 += 4 * nthreads) {
             ulonglong2 buf[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const int e = e0 + threadIdx.x + k * blockDim.x;
+                const int e = e0 + (int)threadIdx.x + k * nthreads;
                 if (e < pairs) {
                     const int el = 2 * e;
                     if (kCol) {
@@ -138,14 +147,14 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const int e = e0 + threadIdx.x + k * blockDim.x;
+                const int e = e0 + (int)threadIdx.x + k * nthreads;
                 if (e < pairs) {
                     const int el = 2 * e;
                     if (kCol) {
                         tile[el] = buf[k].x;
                         tile[el + 1] = buf[k].y;
                     } else {
-                        const int ln = el >> a.logN2, x = el & (N2 - 1);
+                        const int ln = el >> logN2, x = el & (N2 - 1);
                         tile[RIDX(ln, x)] = buf[k].x;
                         tile[RIDX(ln, x + 1)] = buf[k].y;
                     }
@@ -154,31 +163,28 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
         }
     }
     __syncthreads();
-    const int E = min(kE, n);
-    const int tpl = n / E;                    // threads per line
-    const int nthr = lines * tpl;
     const int tid = threadIdx.x;
     const int line = kCol ? tid % lines : tid / tpl;
     const int j = kCol ? tid / lines : tid % tpl;
     const int tw_line = kCol ? 1 : (N1 + l0 + line);
     // rounds: exponent chunks of 3 from the top, remainder at the bottom
     const int nr = (logn + 2) / 3;
+#pragma unroll
     for (int rr = 0; rr < nr; rr++) {
         const int k = kInv ? nr - 1 - rr : rr;  // chunk index from the top
         const int hi = logn - 1 - 3 * k;        // largest exponent of the chunk
         const int lo = max(0, hi - 2);
         const int nst = hi - lo + 1;
-        const int sft = lo;                     // s = 2^lo
         u64 v[kE];
         int base = 0;
         if (tid < nthr) {
-            // thread j of the line: block (j >> sft), offset (j & (s - 1)), block size 8 s
-            int blk = j >> sft;
-            base = (blk << (sft + 3)) + (j & ((1 << sft) - 1));
+            // thread j of the line: block (j >> lo), offset (j & (s - 1)), block size 8 s
+            int blk = j >> lo;
+            base = (blk << (lo + 3)) + (j & ((1 << lo) - 1));
             if (E < kE) base = blk = 0;
 #pragma unroll
             for (int r = 0; r < kE; r++) {
-                const int x = base + (r << sft);
+                const int x = base + (r << lo);
                 v[r] = (r < E) ? (kCol ? tile[x * lines + line] : tile[RIDX(line, x)]) : 0;
             }
             round_stages<kInv, kNoRed>(v, blk, lo, nst, E, logn, tw_line, tw, q);
@@ -188,28 +194,29 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
 #pragma unroll
             for (int r = 0; r < kE; r++) {
                 if (r >= E) break;
-                const int x = base + (r << sft);
+                const int x = base + (r << lo);
                 if (kCol) tile[x * lines + line] = v[r];
                 else tile[RIDX(line, x)] = v[r];
             }
         }
         __syncthreads();
     }
-    // final reduction happens in the pass that completes the transform; fused into the store
+    // the pass that completes the transform reduces to [0, q), fused into the store
     const bool last_pass = kInv ? kCol : !kCol;
     const u64 q2 = 2 * q;
     const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
     const u64 qinv64 = a.mods[mi].ratio_hi;  // floor(2^64 / q)
     auto fin = [&](u64 x) -> u64 {
         if (!last_pass) return x;
-        if (kInv) x = shoup_lazy(x, ni, nis, q);      // [0, 2q)
+        if (kInv) x = shoup_lazy(x, ni, nis, q);          // [0, 2q)
         else if (kNoRed) x -= __umul64hi(x, qinv64) * q;  // [0, 2q)
         else x = x >= q2 ? x - q2 : x;
         return x >= q ? x - q : x;
     };
     {
         const int pairs = total >> 1;
-        for (int e = threadIdx.x; e < pairs; e += blockDim.x) {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < pairs; e += nthreads) {
             const int el = 2 * e;
             ulonglong2 o;
             if (kCol) {
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
                 const int x = el / lines, c = el - x * lines;
                 *reinterpret_cast<ulonglong2*>(d + (size_t)x * N2 + l0 + c) = o;
             } else {
-                const int ln = el >> a.logN2, x = el & (N2 - 1);
+                const int ln = el >> logN2, x = el & (N2 - 1);
                 o.x = fin(tile[RIDX(ln, x)]);
                 o.y = fin(tile[RIDX(ln, x + 1)]);
                 *reinterpret_cast<ulonglong2*>(d + (size_t)l0 * N2 + el) = o;
@@ -247,6 +254,30 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
 
 int threads_for(int lines, int n) { return std::max(32, lines * (n / std::min(kE, n))); }
 
+template <int kLogN, bool kInv, bool kCol>
+void launch_one(bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
+    if (nored && !kInv)
+        ntt_pass<kLogN, kInv, kCol, true><<<g, t, sm, st>>>(a, first);
+    else
+        ntt_pass<kLogN, kInv, kCol, false><<<g, t, sm, st>>>(a, first);
+}
+
+// compile-time ring degrees for the production sizes, run-time geometry otherwise
+template <bool kInv, bool kCol>
+void launch_pass(int logN, bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
+    switch (logN) {
+        case 10: launch_one<10, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 11: launch_one<11, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 12: launch_one<12, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 13: launch_one<13, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 14: launch_one<14, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 15: launch_one<15, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 16: launch_one<16, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 17: launch_one<17, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        default: launch_one<0, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+    }
+}
+
 template <bool kInv>
 void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cudaStream_t st) {
     int limbs = s.per_poly * s.n_poly;
@@ -257,26 +288,25 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
     const double bytes = 16.0 * limbs * N;
     const int tc = threads_for(C, N1), tr = threads_for(R, N2);
+    const bool nored = c->max_mod_bits <= 58;
+    const dim3 gc(limbs * (N2 / C)), gr(limbs * (N1 / R));
     if (!kInv) {
-        const bool nored = c->max_mod_bits <= 58;
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            if (nored) ntt_pass<false, true, true><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
-            else ntt_pass<false, true, false><<<limbs * (N2 / C), tc, smc, st>>>(a, 1);
+            launch_pass<false, true>(c->logN, nored, gc, tc, smc, st, a, 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            if (nored) ntt_pass<false, false, true><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
-            else ntt_pass<false, false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 0);
+            launch_pass<false, false>(c->logN, nored, gr, tr, smr, st, a, 0);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<true, false, false><<<limbs * (N1 / R), tr, smr, st>>>(a, 1);
+            launch_pass<true, false>(c->logN, false, gr, tr, smr, st, a, 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            ntt_pass<true, true, false><<<limbs * (N2 / C), tc, smc, st>>>(a, 0);
+            launch_pass<true, true>(c->logN, false, gc, tc, smc, st, a, 0);
         }
     }
     c->cnt.ntt += limbs;
