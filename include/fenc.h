@@ -172,6 +172,27 @@ int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct,
  * the centred representative.  Errors: FE_ELEVEL at level 0. */
 int fe_rescale(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
                void* stream);
+/* Rescale without allocating: same result as fe_rescale, but the scratch comes
+ * from one fixed 32 MiB array of device memory that the library holds on every
+ * GPU it is loaded on, so the call never allocates or frees device memory.  For
+ * callers that cannot allocate: a serving process whose device footprint is
+ * fixed after start-up, a host framework that owns all device memory through its
+ * own pool, or latency-critical code that cannot afford an allocation's possible
+ * device synchronisation.  There is no counterpart in the paper.
+ *  - Size limit: 16 (n_ct N + n_ct level N) bytes of scratch must fit in 32 MiB
+ *    (e.g. one ciphertext at N = 2^16 and level 23); larger requests fail with
+ *    FE_ENOMEM and a message, before any launch.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture on the device.
+ *  - Every call uses the same array.  Nothing in it needs to start at zero, and
+ *    it keeps the last call's contents.  Calls whose work overlaps on the GPU
+ *    (different streams, or host threads without ordering) race on the array;
+ *    order them on one stream.
+ *  - Kernel timing (fe_profile_begin) does not record this call.
+ * Errors: FE_EINVAL, FE_ELEVEL, FE_ENOMEM, FE_ECUDA. */
+int fe_rescale_noalloc(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                       void* out_dev, void* stream);
 /* out = ct (x) pt per limb (PMult), n_ct ciphertexts times one plaintext each. */
 int fe_pmult(fe_ctx* ctx, const void* ct_dev, const void* pt_dev, uint32_t n_ct, uint32_t level,
              void* out_dev, void* stream);

@@ -72,6 +72,7 @@ SIGNATURES = {
     "fe_ntt": (cint, [vp, vp, u32, u32, u32, cint, vp]),
     "fe_rotate": (cint, [vp, vp, vp, u32, u32, i32, vp, vp]),
     "fe_rescale": (cint, [vp, vp, u32, u32, vp, vp]),
+    "fe_rescale_noalloc": (cint, [vp, vp, u32, u32, vp, vp]),
     "fe_pmult": (cint, [vp, vp, vp, u32, u32, vp, vp]),
     "fe_add": (cint, [vp, vp, vp, u32, u32, vp, vp]),
     "fe_plan_conv": (cint, [vp, P(FeLayout), u32, u32, u32, cint, u32, u32, P(FeLayout), P(vp)]),
