@@ -30,6 +30,11 @@ struct LevelTabs {
     BConvTab rescale;             // {q_l} -> q_0..q_{l-1}
     std::vector<int> ks_limbs;    // q_0..q_l, p_0..p_{k-1}
     const int* d_ks_limbs;        // device copy
+    // extended limbs of one ciphertext's ModUp that need a forward NTT (every digit's
+    // block minus the digit's own limbs): position in the [dnum][l+1+k] block and modulus
+    int n_up_ntt;
+    const int* d_up_pos;
+    const int* d_up_mod;
 };
 
 enum ProfKind { PK_NTT = 0, PK_BCONV, PK_KEYIP, PK_COMBINE, PK_MAC, PK_RESCALE, PK_ENCODE, PK_COUNT };
@@ -93,7 +98,8 @@ struct LimbSet {
     size_t poly_stride;  // in words
     int per_poly;
     int n_poly;
-    const int* mod_map;  // device [per_poly]
+    const int* mod_map;            // device [per_poly]
+    const int* pos_map = nullptr;  // device [per_poly]: limb position inside a poly (default j)
 };
 void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st);
 void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st);

@@ -182,7 +182,7 @@ size_t plan_workspace(const fe_plan* p, size_t chunk) {
     size_t n_mu = p->modup_cts.size(), n_in_rot = p->inner.size();
     size_t persist = (n_in_rot + p->n_out) * z.ctw;
     size_t inner = n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + z.ctw);
-    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw);
+    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw) + (size_t)p->n_out * z.ctw;
     size_t rs = rescale_tmp_words(c, p->n_out, p->level);
     size_t words = persist + std::max(std::max(inner, outer), rs);
     return words * 8 + item_bytes(p, chunk) + 32 * 256;
@@ -235,6 +235,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     u64* ext3 = s3.take<u64>(chunk * z.extw);
     u64* acc3 = s3.take<u64>(chunk * z.accw);
     u64* conv3 = s3.take<u64>(chunk * z.ctw);
+    u64* csum3 = s3.take<u64>((size_t)p->n_out * z.ctw);  // per-output sums of the converted parts
     Carver s4(scratch, scratch_bytes);  // stage 4 (same region)
     u64* rs_tmp = s4.take<u64>(2 * (size_t)p->n_out * N);
     u64* rs_lift = s4.take<u64>(2 * (size_t)p->n_out * lv * N);
@@ -308,11 +309,16 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         kg_range.push_back({kg0, (int)okg.size() - kg0});
         int s0 = (int)sums.size();
         for (auto& kv : by_out) {
-            SumItem si{total + (size_t)kv.first * z.ctw, nullptr, (int)ents.size(), (int)kv.second.size(), 1};
+            // batched path: one NTT of the summed converted parts per output (convsum);
+            // plain path: each rotation's converted part is transformed and subtracted alone
+            const u64* cs = mode == 0 ? nullptr : csum3 + (size_t)(sums.size() - s0) * z.ctw;
+            SumItem si{total + (size_t)kv.first * z.ctw, nullptr, (int)ents.size(), (int)kv.second.size(), 1, cs};
             for (int k : kv.second) {
                 size_t s = k - c0;
                 const auto& g = p->outs[order[k].first].groups[order[k].second];
-                ents.push_back(SumEntry{acc3 + s * z.accw, conv3 + s * z.ctw, Pd + s * z.ctw, c->galois(g.step)});
+                const uint32_t gal = c->galois(g.step);
+                ents.push_back(SumEntry{acc3 + s * z.accw, conv3 + s * z.ctw, Pd + s * z.ctw, gal,
+                                        (uint32_t)h_invmod(gal, 2 * (u64)c->N)});
             }
             sums.push_back(si);
         }
@@ -392,8 +398,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             launch_mac(c, d_mac + n_base + c0, d_terms, cn, chunk_terms[ch], lv, st);
             modup(c, Pd + z.nlN, z.ctw, cn, lv, coef3, ext3, st);
             launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, cn, lv, st);
-            moddown_prepare(c, acc3, cn, lv, conv3, st);
-            launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, sum_range[ch].second, cn, lv, st);
+            moddown_to_coef(c, acc3, cn, lv, conv3, st);
+            const int ns = sum_range[ch].second;
+            launch_autosum(c, d_sum + sum_range[ch].first, d_ent, ns, cn, csum3, lv, st);
+            ntt_forward(c, LimbSet{csum3, (size_t)z.nlN, lv + 1, 2 * ns, c->d_identity_map}, st);
+            launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, ns, cn, lv, st);
         }
     }
     c->cnt.rot += order.size();

@@ -145,21 +145,29 @@ __global__ void k_combine_sum(const SumItem* items, const SumEntry* entries, con
     const int np = level + 1 + k, nq = level + 1;
     const u64 q = mods[i].q;
     const size_t oo = ((size_t)i << logN) + n, oo1 = ((size_t)nq << logN) + oo;
-    u64 v0 = 0, v1 = 0;
-    if (it.base) {
-        v0 = it.base[oo];
-        v1 = it.base[oo1];
-    }
+    u64 c0 = 0, ab = 0, aa = 0;  // sums of perm(c0), perm(acc_b - conv_b), perm(acc_a - conv_a)
     for (int e = 0; e < it.n_e; e++) {
         const SumEntry en = entries[it.e0 + e];
         const uint32_t src = galois_perm(n, en.galois, logN);
         const size_t so = ((size_t)i << logN) + src;
-        u64 vb = sub_mod(en.acc[so], en.conv[so], q);
-        u64 va = sub_mod(en.acc[((size_t)np << logN) + so], en.conv[((size_t)nq << logN) + so], q);
-        vb = add_mod(mul_shoup(vb, pinv[i], pinv_sh[i], q), en.add0[so], q);
-        va = mul_shoup(va, pinv[i], pinv_sh[i], q);
-        v0 = add_mod(v0, vb, q);
-        v1 = add_mod(v1, va, q);
+        u64 vb = en.acc[so], va = en.acc[((size_t)np << logN) + so];
+        if (!it.convsum) {
+            vb = sub_mod(vb, en.conv[so], q);
+            va = sub_mod(va, en.conv[((size_t)nq << logN) + so], q);
+        }
+        c0 = add_mod(c0, en.add0[so], q);
+        ab = add_mod(ab, vb, q);
+        aa = add_mod(aa, va, q);
+    }
+    if (it.convsum) {
+        ab = sub_mod(ab, it.convsum[oo], q);
+        aa = sub_mod(aa, it.convsum[oo1], q);
+    }
+    u64 v0 = add_mod(c0, mul_shoup(ab, pinv[i], pinv_sh[i], q), q);
+    u64 v1 = mul_shoup(aa, pinv[i], pinv_sh[i], q);
+    if (it.base) {
+        v0 = add_mod(v0, it.base[oo], q);
+        v1 = add_mod(v1, it.base[oo1], q);
     }
     if (it.accumulate) {
         v0 = add_mod(v0, it.out[oo], q);
@@ -167,6 +175,31 @@ __global__ void k_combine_sum(const SumItem* items, const SumEntry* entries, con
     }
     it.out[oo] = v0;
     it.out[oo1] = v1;
+}
+
+// coefficient-domain automorphism sum: (sigma_g a)[i] = a[j] if j = i g^-1 mod 2N < N,
+// else -a[j - N]
+__global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* out, const Modulus* mods,
+                          int level, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const SumItem it = items[blockIdx.z];
+    const int nq = level + 1;
+    const int pl = blockIdx.y;  // poly * nq + limb
+    const int i = pl % nq;
+    const u64 q = mods[i].q;
+    const size_t lo = (size_t)pl << logN;
+    u64 acc = 0;
+    for (int e = 0; e < it.n_e; e++) {
+        const SumEntry en = entries[it.e0 + e];
+        const uint32_t j = (uint32_t)(((uint64_t)n * en.galois_inv) & ((2ull << logN) - 1));
+        if (j < (uint32_t)N)
+            acc = add_mod(acc, en.conv[lo + j], q);
+        else
+            acc = sub_mod(acc, en.conv[lo + j - N], q);
+    }
+    out[(size_t)blockIdx.z * 2 * nq * N + lo + n] = acc;
 }
 
 // ------------------------------------------------------------------------
@@ -345,6 +378,14 @@ void launch_combine_sum(fe_ctx* c, const SumItem* items, const SumEntry* entries
     ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * (level + 1) * (4.0 * n_items + 5.0 * n_entries));
     k_combine_sum<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(
         items, entries, c->d_mod, c->d_pinv, c->d_pinv_sh, level, c->k, c->logN);
+    c->cnt.launches++;
+}
+
+void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, int n_items, int n_entries, u64* out,
+                    int level, cudaStream_t st) {
+    if (!n_items) return;
+    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * 2 * (level + 1) * ((double)n_entries + n_items));
+    k_autosum<<<grid_for(c->N, 2 * (level + 1), n_items), kB, 0, st>>>(items, entries, out, c->d_mod, level, c->logN);
     c->cnt.launches++;
 }
 

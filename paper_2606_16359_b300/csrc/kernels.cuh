@@ -48,17 +48,23 @@ struct CombineItem {
 // Summed combine (rotate-and-sum over diagonals): for one output ciphertext,
 //   out0[n] (+)= base0[n] + sum_e ( add0_e[perm_e(n)] + (acc_b - conv_b)_e[perm_e(n)] P^-1 )
 //   out1[n] (+)= base1[n] + sum_e (acc_a - conv_a)_e[perm_e(n)] P^-1
+// With convsum set, the entries' converted parts are not subtracted one by one:
+// convsum = NTT(sum_e sigma_e(conv_e)) (conv_e in coefficient form, sigma_e the
+// coefficient-domain automorphism) is subtracted once, which equals
+// sum_e perm_e(NTT(conv_e)) because the NTT and the automorphism are linear.
 struct SumEntry {
     const u64* acc;   // [2][l+1+k][N]
-    const u64* conv;  // [2][l+1][N]
+    const u64* conv;  // [2][l+1][N]: NTT form (per-entry path) or coefficient form (convsum path)
     const u64* add0;  // [l+1][N] (c0 of the rotated ciphertext)
     uint32_t galois;
+    uint32_t galois_inv;  // g^-1 mod 2N
 };
 struct SumItem {
-    u64* out;         // [2][l+1][N]
-    const u64* base;  // [2][l+1][N] or null
+    u64* out;            // [2][l+1][N]
+    const u64* base;     // [2][l+1][N] or null
     int e0, n_e;
     int accumulate;
+    const u64* convsum;  // [2][l+1][N] NTT form, or null
 };
 
 // PMult-MAC item: out = sum_t ct_t (x) pt_t over `n_terms` consecutive terms
@@ -85,6 +91,10 @@ void launch_combine(fe_ctx* c, const CombineItem* items_dev, int n_items, int le
                     cudaStream_t st);
 void launch_combine_sum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev,
                         int n_items, int n_entries, int level, cudaStream_t st);
+// convsum_i = sum over item i's entries of sigma_e(conv_e) in the coefficient domain
+// (out + i * 2 (l+1) N words)
+void launch_autosum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev, int n_items,
+                    int n_entries, u64* out, int level, cudaStream_t st);
 void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
                 int n_terms, int level, cudaStream_t st);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,

@@ -174,8 +174,10 @@ extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, u
         std::vector<SumEntry> ents(n);
         for (uint32_t i = 0; i < n; i++) {
             ks[i] = KsItem{ksc.ext + i * ext_words(c, level), key, ksc.acc + i * acc_words(c, level)};
-            ents[i] = SumEntry{ksc.acc + i * acc_words(c, level), ksc.conv + i * ctw, cur + i * ctw, c->galois(steps[si])};
-            sums[i] = SumItem{next + i * ctw, cur + i * ctw, (int)i, 1, 0};
+            const uint32_t gal = c->galois(steps[si]);
+            ents[i] = SumEntry{ksc.acc + i * acc_words(c, level), ksc.conv + i * ctw, cur + i * ctw, gal,
+                               (uint32_t)h_invmod(gal, 2 * (u64)c->N)};
+            sums[i] = SumItem{next + i * ctw, cur + i * ctw, (int)i, 1, 0, nullptr};
         }
         std::vector<KsGroup> kg{KsGroup{key, 0, (int)n}};
         FE_TRY(upload(ks, ksc.ks, st));

@@ -40,6 +40,7 @@ struct NttArgs {
     size_t poly_stride;
     int per_poly;
     const int* mod_map;
+    const int* pos_map;
     const Modulus* mods;
     const ulonglong2* tw;  // [n_mod][N] (w, floor(w 2^64 / q))
     const u64* ninv;
@@ -117,10 +118,11 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     const int l0 = (blockIdx.x % tiles_per_limb) * lines;
     const int poly = limb / a.per_poly, jl = limb % a.per_poly;
     const int mi = a.mod_map[jl];
+    const int pos = a.pos_map ? a.pos_map[jl] : jl;
     const u64 q = a.mods[mi].q;
     const ulonglong2* tw = a.tw + ((size_t)mi << logN);
-    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)jl << logN);
-    const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)jl << logN) : d;
+    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)pos << logN);
+    const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)pos << logN) : d;
     const int total = lines * n;
     // column pass tile[x * lines + c]; row pass tile[RIDX(row, x)] with one pad word per 8
     // so that the strided rounds avoid bank conflicts
@@ -243,6 +245,7 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
     a.poly_stride = s.poly_stride;
     a.per_poly = s.per_poly;
     a.mod_map = s.mod_map;
+    a.pos_map = s.pos_map;
     a.mods = c->d_mod;
     a.tw = (const ulonglong2*)(inverse ? c->d_itw2 : c->d_tw2);
     a.ninv = c->d_ninv;

@@ -138,10 +138,19 @@ void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* 
     if (n == 0) return;
     const int N = c->N, nl = level + 1, np = level + 1 + c->k, dn = dnum_at(c, level);
     ntt_inverse_from(c, src, src_stride, LimbSet{coef, (size_t)nl * N, nl, n, c->d_identity_map}, st);
+    // the converted limbs of every digit, then their forward NTT
     for (int j = 0; j < dn; j++)
         launch_bconv(c, c->lv[level].modup[j], level, coef, (size_t)nl * N, 0, ext + (size_t)j * np * N,
-                     (size_t)dn * np * N, n, true, st);
-    ntt_forward(c, LimbSet{ext, (size_t)np * N, np, n * dn, c->lv[level].d_ks_limbs}, st);
+                     (size_t)dn * np * N, n, false, st);
+    const LevelTabs& lt = c->lv[level];
+    LimbSet others{ext, (size_t)dn * np * N, lt.n_up_ntt, n, lt.d_up_mod, lt.d_up_pos};
+    ntt_forward(c, others, st);
+    // a digit's own limbs keep the input's NTT-form residues
+    for (int j = 0; j < dn; j++) {
+        const int lo = j * c->k, cnt = std::min(c->k, nl - lo);
+        cudaMemcpy2DAsync(ext + ((size_t)j * np + lo) * N, (size_t)dn * np * N * 8, src + (size_t)lo * N,
+                          src_stride * 8, (size_t)cnt * N * 8, n, cudaMemcpyDeviceToDevice, st);
+    }
 }
 
 void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st) {
@@ -153,6 +162,16 @@ void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStrea
     t.n_dst = nl;  // destination-major table: the first l+1 destinations
     launch_bconv(c, t, level, acc, (size_t)np * N, 0, conv, (size_t)nl * N, 2 * n, false, st);
     ntt_forward(c, LimbSet{conv, (size_t)nl * N, nl, 2 * n, c->d_identity_map}, st);
+}
+
+void moddown_to_coef(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st) {
+    if (n == 0) return;
+    const int N = c->N, nl = level + 1, np = level + 1 + c->k;
+    ntt_inverse(c, LimbSet{acc + (size_t)nl * N, (size_t)np * N, c->k, 2 * n, c->lv[level].d_ks_limbs + nl},
+                st);
+    BConvTab t = c->moddown;
+    t.n_dst = nl;
+    launch_bconv(c, t, level, acc, (size_t)np * N, 0, conv, (size_t)nl * N, 2 * n, false, st);
 }
 
 size_t rescale_tmp_words(const fe_ctx* c, int n, int level) {

@@ -26,6 +26,8 @@ void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* 
 // ModDown preparation for n accumulators acc [n][2][l+1+k][N] (NTT form): the P limbs are
 // inverse-transformed in place, converted to Q_level into conv [n][2][l+1][N] and transformed.
 void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
+// the same without the final NTT: conv receives the conversion in coefficient form
+void moddown_to_coef(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
 // Rescale n ciphertexts in -> out (level -> level - 1); tmp: [2n][N], lift: [2n][level][N].
 void rescale_batch(fe_ctx* c, const u64* in, int n, int level, u64* out, u64* tmp, u64* lift,
                    cudaStream_t st);

@@ -319,7 +319,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     struct LvOff {
         std::vector<TabOffsets> up;
         TabOffsets rs;
-        size_t ks;
+        size_t ks, up_pos, up_mod;
+        int n_up;
         std::vector<int> ks_limbs;
     };
     std::vector<LvOff> lvo(c->L + 1);
@@ -330,13 +331,23 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         lvo[l].ks_limbs = ks;
         lvo[l].ks = pb.put(ks.data(), ks.size() * sizeof(int));
         int nd = (l + 1 + c->k - 1) / c->k;
+        std::vector<int> up_pos, up_mod;
+        const int np = l + 1 + c->k;
         for (int j = 0; j < nd; j++) {
             std::vector<int> dig, oth;
             for (int i = j * c->k; i < std::min((j + 1) * c->k, l + 1); i++) dig.push_back(i);
             for (int t : ks)
                 if (std::find(dig.begin(), dig.end(), t) == dig.end()) oth.push_back(t);
             lvo[l].up.push_back(build_tab(pb, c->mod, dig, oth));
+            for (int pos = 0; pos < np; pos++)
+                if (std::find(dig.begin(), dig.end(), pos) == dig.end()) {  // positions of q's equal their index
+                    up_pos.push_back(j * np + pos);
+                    up_mod.push_back(ks[pos]);
+                }
         }
+        lvo[l].n_up = (int)up_pos.size();
+        lvo[l].up_pos = pb.put(up_pos.data(), up_pos.size() * sizeof(int));
+        lvo[l].up_mod = pb.put(up_mod.data(), up_mod.size() * sizeof(int));
         if (l >= 1) {
             std::vector<int> lower;
             for (int i = 0; i < l; i++) lower.push_back(i);
@@ -366,6 +377,9 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         if (l >= 1) c->lv[l].rescale = resolve(lvo[l].rs, dpool);
         c->lv[l].ks_limbs = lvo[l].ks_limbs;
         c->lv[l].d_ks_limbs = (const int*)(dpool + lvo[l].ks);
+        c->lv[l].n_up_ntt = lvo[l].n_up;
+        c->lv[l].d_up_pos = (const int*)(dpool + lvo[l].up_pos);
+        c->lv[l].d_up_mod = (const int*)(dpool + lvo[l].up_mod);
     }
     auto up = [&](u64** dst, const std::vector<u64>& v) -> int {
         FE_CUDA_TRY(cudaMalloc(dst, v.size() * 8));
