@@ -115,6 +115,24 @@ def barrier(dist):
         dist.barrier()
 
 
+def butterfly_roof(ctx, torch):
+    """Integer-pipe roof of the NTT butterfly arithmetic on this GPU, Gbutterfly/s
+    (register-resident probe of the transform's own butterflies, one full wave)."""
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    buf = torch.empty(n_sm * 8 * 256, dtype=torch.int64, device="cuda")
+    ctx.probe_butterflies(buf, 0, 40)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(3):
+        e0.record()
+        n = ctx.probe_butterflies(buf, 0, 400)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, n / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
 def cpu_oracle_keyswitch(n_rot, level=22):
     """The CPU oracle (as it stands, single-threaded) on a bounded sample: n_rot
     rotations of one ciphertext at `level` of the same parameter set."""
@@ -166,6 +184,9 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=4)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile", default="auto", help="kernel class timed for the roofline, or 'auto'")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="set up, run one warm step, then one batched step between cudaProfilerStart and "
+                         "cudaProfilerStop (for ncu --profile-from-start off), and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -190,6 +211,16 @@ def run_ours(args, dist, rank, world, local):
     t_setup = time.perf_counter() - t_setup
     ks_per_step = net.keyswitches_per_step
     stream = torch.cuda.current_stream()
+    if args.ncu_step:
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        ctx.reset_counters()
+        torch.cuda.profiler.start()
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_step": True, "launches": ctx.counters()["launches"]}), flush=True)
+        return 0
 
     # correctness of one step against FP64 (untimed)
     net.run(mode=1)
@@ -255,6 +286,20 @@ def run_ours(args, dist, rank, world, local):
     peak, peak_kind = peaks()
     achieved = (b_dom / n_dom) / (t_dom / n_dom / 1e3) / 1e9 if n_dom else 0.0
     shares = {k: round(v[0] / sum(x[0] for x in per_kind.values()), 4) for k, v in per_kind.items()}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None, "launches": n_dom,
+                "avg_launch_us": 1e3 * t_dom / max(1, n_dom), "time_share": shares}
+    if dom == "ntt":
+        # the 64-bit-word transform is bound by the integer pipes: butterflies per
+        # second against the live butterfly-probe roof; HBM figures kept beside it
+        bfly_peak = butterfly_roof(ctx, torch)
+        limb_passes = b_dom / (8.0 * ctx.N)
+        bfly = limb_passes * (ctx.N // 2) * (ctx.logN / 2)
+        bfly_rate = bfly / (t_dom / 1e3) / 1e9
+        roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": bfly_peak, "unit": "Gbutterfly/s",
+                         "frac": bfly_rate / bfly_peak, "peak_source": "butterfly probe, this run",
+                         "hbm_GBps": achieved, "hbm_peak_GBps": peak, "hbm_frac": achieved / peak,
+                         "hbm_peak_source": peak_kind})
 
     # ---- plain per-op path (one launch per primitive per ciphertext) ----
     net.run(mode=0)
@@ -314,10 +359,7 @@ def run_ours(args, dist, rank, world, local):
                        "max_abs_err_vs_fp64": max(errs), "setup_s": round(t_setup, 1),
                        "l2": "inputs (keys, plaintexts) far larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                         "launches": n_dom, "avg_launch_us": 1e3 * t_dom / max(1, n_dom),
-                         "time_share": shares},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "keyswitch/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -3,11 +3,11 @@
  *
  * The library evaluates the hot path of FEnc^2's encrypted CNN inference: the
  * homomorphic convolution under the conv-aware fragment encoding (Algorithm 1,
- * Sec. 3), with hoisted inner rotations, PMult multiply-accumulate over
+ * Sec. 4.2; the convolution of Sec. 3.1), with hoisted inner rotations, PMult multiply-accumulate over
  * fragment masks, outer rotations (Eq. 1 rotations, counted by Eq. 3 - Eq. 5),
  * one rescale, and the layers around it: x^2 activation, 2x2 average pooling,
- * fully connected layers, and Arch-aware Ciphertext Compression (Sec. 3, Fig. 6).
- * The calls follow the usage flow of the problem statement (Sec. 4): the client
+ * fully connected layers, and Arch-aware Ciphertext Compression (Sec. 4.3, Fig. 6).
+ * The calls follow the usage flow of the problem statement (Sec. 4.1): the client
  * sends shape metadata, receives the slot mapping, encodes and encrypts; the
  * server evaluates; the client decrypts.
  *
@@ -164,6 +164,17 @@ int fe_decrypt_decode(fe_ctx* ctx, const void* sk_dev, const void* ct_dev, uint3
  * in place; limb j of every polynomial uses modulus index first_mod + j. */
 int fe_ntt(fe_ctx* ctx, void* data_dev, uint32_t n_poly, uint32_t n_limbs, uint32_t first_mod,
            int inverse, void* stream);
+/* Throughput probe of the forward NTT's butterfly arithmetic (no counterpart in
+ * the paper; a measurement aid for the integer-pipe roofline of the transform).
+ * Launches `blocks` CTAs of 256 threads (blocks = 0: one full wave, i.e. the
+ * SM count times the CTAs that fit on one SM, at most 8); each thread runs
+ * `iters` x 60 lazy Shoup butterflies on register-resident residues of modulus
+ * q_0 and writes one word to out_dev (caller-owned device buffer of
+ * blocks * 256 uint64, or SMs * 8 * 256 when blocks = 0; 16-byte aligned).
+ * *butterflies (optional) receives blocks * 256 * iters * 60.  The caller
+ * times the launch on `stream`.  Errors: FE_EINVAL, FE_ECUDA. */
+int fe_probe_butterflies(fe_ctx* ctx, uint32_t blocks, uint32_t iters, void* out_dev,
+                         uint64_t* butterflies, void* stream);
 /* Left rotation of n_ct ciphertexts by r slots (Eq. 1): out = sigma_g((c0,0) + KS(c1)).
  * Errors: FE_EKEY when the key for r is missing. */
 int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
@@ -202,7 +213,7 @@ int fe_add(fe_ctx* ctx, const void* a_dev, const void* b_dev, uint32_t n_ct, uin
 
 /* ---- encrypted layers (server) -------------------------------------------- */
 
-/* Plan one HE convolution layer under the fragment encoding (Sec. 3):
+/* Plan one HE convolution layer under the fragment encoding (Sec. 3.1, Sec. 4.2):
  *   in: input layout, Cout, K, stride (1, or 2 with S even), depthwise (Cout = C,
  *   one filter per channel), in_period (0, or c_v when the input was replicated
  *   by fe_compress so that channel position c holds channel c mod c_v), level of
@@ -259,20 +270,20 @@ int fe_he_fc(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt
              const void* in_dev, void* out_dev, void* workspace_dev, size_t workspace_bytes,
              int mode, void* stream);
 
-/* x^2 activation (the a x^2 + b x + c polynomial of Sec. 4 with a = 1,
+/* x^2 activation (the a x^2 + b x + c polynomial of Sec. 5, Implementation, with a = 1,
  * b = c = 0): CMult with relinearisation, then rescale.  in: [n_ct][2][level+1][N],
  * out: [n_ct][2][level][N].  Workspace: fe_square_workspace_bytes. */
 size_t fe_square_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
 int fe_he_square(fe_ctx* ctx, const fe_evk* evk, const void* in_dev, uint32_t n_ct, uint32_t level,
                  void* out_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
-/* 2x2 average pooling by summing fragment ciphertexts (S even; Sec. 4): output
+/* 2x2 average pooling by summing fragment ciphertexts (S even; Sec. 5, Implementation): output
  * fragment (u, v) = sum of input fragments (2u + di, 2v + dj); the 1/4 is left
  * to the next layer's weights.  out_lay receives the output layout (S / 2). */
 int fe_he_avgpool(fe_ctx* ctx, const fe_layout* lay, const void* in_dev, uint32_t level,
                   void* out_dev, fe_layout* out_lay, void* stream);
 
-/* Arch-aware Ciphertext Compression (Sec. 3, Fig. 6): ciphertexts whose first
+/* Arch-aware Ciphertext Compression (Sec. 4.3, Fig. 6): ciphertexts whose first
  * c_valid channel positions hold data and whose other positions are zero are
  * filled by rotate-and-add doubling, ct += Rot(ct, -s m^2 BS) for
  * s = c_valid, 2 c_valid, ..., cpc / 2; position c then holds channel c mod c_valid.

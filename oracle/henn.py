@@ -1,4 +1,4 @@
-"""Encrypted layers under the fragment encoding: HE convolution (Sec. 3, Eq. 2
+"""Encrypted layers under the fragment encoding: HE convolution (Sec. 3.1, Eq. 2
 with inner and outer rotations), x^2 activation, 2x2 average pooling, fully
 connected layers, Arch-aware Ciphertext Compression (AAC), and the LeNet-shaped
 network built from them.
@@ -6,7 +6,7 @@ network built from them.
 Test infrastructure only (see oracle/__init__.py).
 
 HE convolution (the algorithm, in the order it is evaluated here):
- 1. Inner rotations (spatial dependency, Sec. 3 "inner rotations", Eq. 3):
+ 1. Inner rotations (spatial dependency, Sec. 3.1 inner rotations, Eq. 3):
     output pixel (h, w) = (bi S + u', bj S + v') sits in the slot of input pixel
     (h, w).  Tap (i, j) reads input pixel (h + i, w + j), which lives in input
     fragment u = (u' + i) mod S at block row bi + a, a = (u' + i) div S (same for
@@ -23,7 +23,7 @@ HE convolution (the algorithm, in the order it is evaluated here):
  4. One rescale.
 Weights are encoded at scale q_level by default, so the output scale equals the
 input scale.  Stride 2 keeps the output fragments with even (u', v') and halves S
-(Sec. 4 implementation paragraph: stride by discarding ciphertexts).
+(Sec. 5, Implementation paragraph: stride by discarding ciphertexts).
 """
 import math
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "fe_encode_encrypt": (cint, [vp, vp, vp, u32, u32, dbl, u64, u64, vp, vp]),
     "fe_decrypt_decode": (cint, [vp, vp, vp, u32, u32, dbl, vp, vp]),
     "fe_ntt": (cint, [vp, vp, u32, u32, u32, cint, vp]),
+    "fe_probe_butterflies": (cint, [vp, u32, u32, vp, P(u64), vp]),
     "fe_rotate": (cint, [vp, vp, vp, u32, u32, i32, vp, vp]),
     "fe_rescale": (cint, [vp, vp, u32, u32, vp, vp]),
     "fe_rescale_noalloc": (cint, [vp, vp, u32, u32, vp, vp]),
@@ -283,6 +284,12 @@ class Context:
         n_poly, n_limbs = data.shape[0], data.shape[1]
         check(load().fe_ntt(self.handle, _ptr(data), n_poly, n_limbs, first_mod, 1 if inverse else 0, _stream()))
         return data
+
+    def probe_butterflies(self, out, blocks, iters):
+        """Launch the butterfly-throughput probe; returns the butterflies executed."""
+        n = ctypes.c_uint64(0)
+        check(load().fe_probe_butterflies(self.handle, blocks, iters, _ptr(out), ctypes.byref(n), _stream()))
+        return n.value
 
     def rotate(self, evk, ct, level, r):
         out = self.empty_ct(ct.shape[0], level)

@@ -103,6 +103,9 @@ struct LimbSet {
 };
 void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st);
 void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st);
+// throughput probe of the transform's butterfly arithmetic (blocks x 256 threads)
+// (*blocks = 0: one full wave, set on return)
+int butterfly_probe(fe_ctx* c, uint32_t* blocks, uint32_t iters, u64* out, cudaStream_t st);
 // out-of-place: the first pass reads polynomials from src (poly stride src_stride words)
 void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);
 void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);

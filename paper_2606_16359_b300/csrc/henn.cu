@@ -1,8 +1,8 @@
 // Encrypted layers under the fragment encoding: planning and execution of the
-// HE convolution (Sec. 3) and of the fully connected layers, and fragment
+// HE convolution (Sec. 3.1) and of the fully connected layers, and fragment
 // pack / unpack.
 //
-// A conv plan follows the algorithm order of Sec. 3:
+// A conv plan follows the algorithm order of Sec. 3.1:
 //  1. inner rotations: input ciphertext (g, u, v) is rotated by (a m + b) BS
 //     for every block offset (a, b) != (0, 0) that some tap needs; one ModUp of
 //     its c1 serves all of its rotations (hoisting);

@@ -237,6 +237,31 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
 #undef RIDX
 }
 
+// Integer-pipe roof of the forward transform's arithmetic.  Every thread keeps 8
+// residues in registers and runs `iters` groups of five radix-8 rounds (15 stages,
+// 60 butterflies, the same lazy Shoup butterflies as the transform, twiddles 1..7
+// of modulus 0, which stay in L1) followed by the reduction the transform applies
+// once per element; no tile traffic.  One word per thread is written so that the
+// work is kept.  Butterflies executed = blocks * 256 * iters * 60.
+__global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __restrict__ tw, u64 q, u64 qinv64,
+                                                         int iters, u64* out) {
+    u64 v[kE];
+    const u64 seed = blockIdx.x * 256 + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < kE; r++) v[r] = (seed * 8 + r) % q;
+#pragma unroll 1
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) round_stages<false, true>(v, 0, 0, 3, kE, 3, 1, tw, q);
+#pragma unroll
+        for (int r = 0; r < kE; r++) v[r] -= __umul64hi(v[r], qinv64) * q;
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int r = 0; r < kE; r++) acc ^= v[r];
+    out[(size_t)blockIdx.x * 256 + threadIdx.x] = acc;
+}
+
 NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, bool inverse) {
     NttArgs a;
     a.src = src ? src : s.base;
@@ -289,7 +314,8 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
     const int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
     const size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
-    const double bytes = 16.0 * limbs * N;
+    // algorithmic bytes of a limb transform, 2 N w, split over its two passes
+    const double bytes = 8.0 * limbs * N;
     const int tc = threads_for(C, N1), tr = threads_for(R, N2);
     const bool nored = c->max_mod_bits <= 58;
     const dim3 gc(limbs * (N2 / C)), gr(limbs * (N1 / R));
@@ -317,6 +343,18 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
 }
 
 }  // namespace
+
+int butterfly_probe(fe_ctx* c, uint32_t* blocks, uint32_t iters, u64* out, cudaStream_t st) {
+    const Modulus m = make_modulus(c->mod[0]);
+    if (*blocks == 0) {  // one full wave: every SM holds as many CTAs as fit
+        int per_sm = 0;
+        FE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_butterfly_probe, 256, 0));
+        *blocks = (uint32_t)(std::min(per_sm, 8) * c->n_sm);
+    }
+    k_butterfly_probe<<<*blocks, 256, 0, st>>>((const ulonglong2*)c->d_tw2, m.q, m.ratio_hi, (int)iters, out);
+    c->cnt.launches += 1;
+    return cudaGetLastError() == cudaSuccess ? FE_OK : fail(FE_ECUDA, "butterfly probe launch");
+}
 
 void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<false>(c, s, nullptr, 0, st); }
 void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<true>(c, s, nullptr, 0, st); }

@@ -381,6 +381,16 @@ extern "C" int fe_ntt(fe_ctx* c, void* data, uint32_t n_poly, uint32_t n_limbs, 
     return FE_OK;
 }
 
+extern "C" int fe_probe_butterflies(fe_ctx* c, uint32_t blocks, uint32_t iters, void* out_dev,
+                                    uint64_t* butterflies, void* stream) {
+    if (!c || !out_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(out_dev);
+    if (iters == 0) return fail(FE_EINVAL, "iters must be positive");
+    FE_TRY(butterfly_probe(c, &blocks, iters, (u64*)out_dev, (cudaStream_t)stream));
+    if (butterflies) *butterflies = (uint64_t)blocks * 256 * iters * 60;
+    return FE_OK;
+}
+
 extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                          int32_t r, void* out_dev, void* stream) {
     FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);

@@ -1,0 +1,136 @@
+"""Kernel micro-benchmarks through the C ABI (one JSON line each).
+
+    python -m paper_2606_16359_b300.kbench ntt [--logN 16] [--limbs 512] [--reps 10]
+    python -m paper_2606_16359_b300.kbench alu [--iters 400]
+    python -m paper_2606_16359_b300.kbench keyswitch [--n 8] [--level 22] [--reps 5]
+
+ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
+     moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
+     write each word once), butterflies (N / 2) log2 N per limb.
+alu: the integer-pipe roof of the transform's butterfly arithmetic, from a
+     register-resident probe of the same lazy Shoup butterflies.
+keyswitch: rotations (hybrid key switch + automorphism) of n ciphertexts at one
+     level with one key; algorithmic bytes per key switch without key reuse
+     [(l+1) + 2 dnum (l+1+k) + 2 (l+1)] N w.
+
+Inputs are larger than L2 (126 MB) unless stated; times are CUDA events on the
+launching stream after warm-up.  Used for the ncu captures of single kernels,
+which need a small, self-contained case.
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_ntt(ctx, torch, args):
+    N, nm = ctx.N, ctx.n_mod
+    n_poly = max(1, (args.limbs + nm - 1) // nm)
+    limbs = n_poly * nm
+    # residues below 2^35 are valid for every modulus of 36 bits
+    d = torch.randint(0, 2 ** 35, (n_poly, nm, N), dtype=torch.int64, device="cuda")
+    out = {}
+    for inv in (False, True):
+        for _ in range(2):
+            ctx.ntt(d, inverse=inv)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(args.reps):
+            ctx.ntt(d, inverse=inv)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+        us_limb = 1e3 * ms / limbs
+        gbs = 2 * N * 8 * limbs / (ms / 1e3) / 1e9
+        bfly = (N // 2) * ctx.logN * limbs / (ms / 1e3)
+        out["inverse" if inv else "forward"] = {"ms": ms, "us_per_limb": us_limb, "GBps": gbs,
+                                                "Gbutterfly_per_s": bfly / 1e9}
+    peak, src = hbm_peak()
+    for v in out.values():
+        v["hbm_frac"] = v["GBps"] / peak
+    return {"kernel": "ntt", "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
+            "peak_GBps": peak, "peak_source": src, **out}
+
+
+def bench_alu(ctx, torch, args):
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    buf = torch.empty(n_sm * 8 * 256, dtype=torch.int64, device="cuda")
+    ctx.probe_butterflies(buf, 0, max(1, args.iters // 10))
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    n = ctx.probe_butterflies(buf, 0, args.iters)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"kernel": "butterfly_probe", "blocks": n // (256 * 60 * args.iters), "threads": 256,
+            "iters": args.iters, "butterflies": n, "ms": ms, "Gbutterfly_per_s": n / (ms / 1e3) / 1e9}
+
+
+def bench_keyswitch(ctx, torch, args):
+    lv = args.level
+    sk = ctx.sk_gen(1)
+    evk = ctx.evk_gen(sk, 1, [1])
+    slots = torch.zeros((args.n, ctx.N // 2), dtype=torch.float64, device="cuda")
+    ct = ctx.encrypt(sk, slots, lv, 2.0 ** 32, 3)
+    for _ in range(2):
+        ctx.rotate(evk, ct, lv, 1)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.reps):
+        ctx.rotate(evk, ct, lv, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    k, N = ctx.k, ctx.N
+    dnum = (lv + 1 + k - 1) // k
+    per_ks = ((lv + 1) + 2 * dnum * (lv + 1 + k) + 2 * (lv + 1)) * N * 8
+    peak, src = hbm_peak()
+    us = 1e3 * ms / args.n
+    return {"kernel": "keyswitch", "level": lv, "n_ct": args.n, "dnum": dnum, "ms": ms, "us_per_keyswitch": us,
+            "keyswitch_per_s": 1e6 / us, "bytes_per_keyswitch_no_reuse": per_ks,
+            "GBps_no_reuse": per_ks / (us / 1e6) / 1e9, "hbm_frac_no_reuse": per_ks / (us / 1e6) / 1e9 / peak,
+            "peak_GBps": peak, "peak_source": src}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch"])
+    ap.add_argument("--logN", type=int, default=16)
+    ap.add_argument("--limbs", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=400)
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--level", type=int, default=22)
+    args = ap.parse_args(argv)
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import paper_2606_16359_b300 as fe
+
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ctx = fe.Context(args.logN, 24, 4, 36, 36)
+        fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch}[args.what]
+        print(json.dumps(fn(ctx, torch, args)), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -6,7 +6,7 @@ block an independent encrypted input.  All layers' ciphertexts, plaintexts and
 keys stay resident on the device; a step runs the six HE convolutions.
 
 LeNet: conv5x5 1->6, x^2, avgpool2, conv5x5 6->16, x^2, avgpool2, FC 256->120->84->10
-at the largest slot batch (Sec. 4 implementation paragraph: x^2 activation,
+at the largest slot batch (Sec. 5, Implementation paragraph: x^2 activation,
 pooling by fragment sums, FC by diagonals with baby-step / giant-step).
 """
 import numpy as np

@@ -270,3 +270,19 @@ def test_aac_compress_parity(tiny):
     dec = g.decrypt(sk, got, pr.L, 2.0 ** 25).cpu().numpy()[0].reshape(8, -1)
     for c in range(8):
         assert np.abs(dec[c] - slots[0].reshape(8, -1)[c % 2]).max() < 1e-4
+
+
+@pytest.mark.parametrize("H,W_,C,BS,S", [(28, 28, 1, 2, 4), (7, 5, 3, 2, 2), (14, 14, 20, 1, 1), (9, 9, 5, 2, 3)])
+def test_fragment_pack_unpack_parity(tiny, H, W_, C, BS, S):
+    """Algorithm 1 slot map on the GPU equals the oracle's, element for element,
+    including ragged maps (H, W not multiples of S; C not a multiple of cpc)."""
+    rng = np.random.default_rng(H * 10 + C)
+    x = rng.uniform(-1, 1, (BS, C, H, W_))
+    lay = tiny.g.layout(H, W_, C, BS, S)
+    olay = fragment.Layout(tiny.pr.N, H, W_, C, BS, S)
+    assert (lay.m, lay.cpc, lay.n_ct) == (olay.m, olay.cpc, olay.n_ct)
+    slots = tiny.g.pack(lay, torch.from_numpy(x))
+    want = fragment.pack(olay, x)
+    assert np.array_equal(slots.cpu().numpy(), np.asarray(want))
+    back = tiny.g.unpack(lay, slots).cpu().numpy()
+    assert np.array_equal(back, x)
