@@ -82,6 +82,42 @@ typedef struct {
     uint64_t rot, keyswitch, ntt, pmult, cmult, rescale, launches;
 } fe_counters;
 
+/* ---- rotation-complexity model and fragment-size choice (host only) ------ */
+
+/* The rotation counts of the fragment encoding for one conv layer at fragment
+ * size S (Sec. 4.2): alpha = N / (2 M^2) with the padded side M = S m,
+ * Eq. 3 inner rotations (ceil(K/S)^2 - 1) Cin / alpha (0 when K <= S or S = M,
+ * the convention of Table 6), Eq. 4 outer rotations
+ * (BS/alpha)(alpha S^2/BS - 1) Cout (0 for depthwise layers), the Eq. 5 total
+ * (BS/alpha)[inner(S) Cin + (alpha S^2/BS - 1) Cout], the Eq. 7 bound
+ * sqrt(BS Cin / alpha), the Eq. 8 closed form (K^2 Cin BS / (alpha Cout))^(1/4),
+ * and the inner rotations a layer executes (every needed block offset of every
+ * input ciphertext, stride 1 or 2). */
+typedef struct {
+    uint32_t m, M, cpc;
+    double alpha, eq3_inner, eq4_outer, eq5_total, s_bound_eq7, s_star_eq8;
+    uint64_t executed_inner;
+} fe_rotation_model_t;
+/* Pure host computation (no device, no context).  Errors: FE_EINVAL (zero
+ * extent, N not a power of two, stride not 1 or 2, channel block larger than a
+ * ciphertext). */
+int fe_rotation_model(uint32_t N, uint32_t H, uint32_t W, uint32_t Cin, uint32_t Cout, uint32_t K,
+                      uint32_t S, uint32_t BS, uint32_t stride, int depthwise, fe_rotation_model_t* out);
+
+/* Analytic fragment-size choice (Theorem, Eq. 5, Eq. 7): the argmin of the
+ * Eq. 5 total over the power-of-two S <= max_S (0: 32) whose channel block fits
+ * a ciphertext (m^2 BS <= N/2) and that satisfy Eq. 7 (S = 1 always does); ties
+ * go to the smaller S.  out receives S, its layout geometry, alpha, the Eq. 5
+ * value, the Eq. 8 closed form at that alpha, and the number of admissible
+ * sizes examined.  Pure host computation.  Errors: FE_EINVAL (bad extents or no
+ * admissible S). */
+typedef struct {
+    uint32_t S, m, M, cpc, n_admissible;
+    double alpha, eq5, s_star;
+} fe_fragment_choice;
+int fe_choose_fragment(uint32_t N, uint32_t H, uint32_t W, uint32_t Cin, uint32_t Cout, uint32_t K,
+                       uint32_t BS, int depthwise, uint32_t max_S, fe_fragment_choice* out);
+
 /* ---- context ------------------------------------------------------------ */
 
 /* Create a context on the current CUDA device: generates the moduli and the

@@ -52,7 +52,25 @@ class FePlanInfo(ctypes.Structure):
 
 P = ctypes.POINTER
 # name: (restype, argtypes)
+class FeRotationModel(ctypes.Structure):
+    _fields_ = [("m", u32), ("M", u32), ("cpc", u32), ("alpha", dbl), ("eq3_inner", dbl), ("eq4_outer", dbl),
+                ("eq5_total", dbl), ("s_bound_eq7", dbl), ("s_star_eq8", dbl), ("executed_inner", u64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class FeFragmentChoice(ctypes.Structure):
+    _fields_ = [("S", u32), ("m", u32), ("M", u32), ("cpc", u32), ("n_admissible", u32), ("alpha", dbl),
+                ("eq5", dbl), ("s_star", dbl)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 SIGNATURES = {
+    "fe_rotation_model": (cint, [u32, u32, u32, u32, u32, u32, u32, u32, u32, cint, P(FeRotationModel)]),
+    "fe_choose_fragment": (cint, [u32, u32, u32, u32, u32, u32, u32, cint, u32, P(FeFragmentChoice)]),
     "fe_ctx_create": (cint, [P(FeParams), P(vp)]),
     "fe_ctx_destroy": (None, [vp]),
     "fe_ctx_moduli": (cint, [vp, P(u64)]),
@@ -409,6 +427,20 @@ class Context:
 
 
 P_i32 = ctypes.POINTER(i32)
+
+
+def rotation_model(N, H, W, Cin, Cout, K, S, BS, stride=1, depthwise=False):
+    """Eq. 3 - Eq. 8 counts of one conv layer at fragment size S (host only)."""
+    r = FeRotationModel()
+    check(load().fe_rotation_model(N, H, W, Cin, Cout, K, S, BS, stride, 1 if depthwise else 0, ctypes.byref(r)))
+    return r.as_dict()
+
+
+def choose_fragment(N, H, W, Cin, Cout, K, BS, depthwise=False, max_S=0):
+    """Analytic fragment-size choice: argmin of Eq. 5 over admissible S (host only)."""
+    r = FeFragmentChoice()
+    check(load().fe_choose_fragment(N, H, W, Cin, Cout, K, BS, 1 if depthwise else 0, max_S, ctypes.byref(r)))
+    return r.as_dict()
 
 
 def exported_symbols():

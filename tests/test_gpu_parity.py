@@ -286,3 +286,13 @@ def test_fragment_pack_unpack_parity(tiny, H, W_, C, BS, S):
     assert np.array_equal(slots.cpu().numpy(), np.asarray(want))
     back = tiny.g.unpack(lay, slots).cpu().numpy()
     assert np.array_equal(back, x)
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride", [(8, 3, 5, 3, 2, 2, 1), (9, 2, 3, 3, 2, 2, 2), (16, 4, 4, 5, 1, 4, 1),
+                                                   (6, 20, 18, 3, 1, 1, 1)])
+def test_planner_inner_count_matches_rotation_model(tiny, H, C, Co, K, BS, S, stride):
+    """The planner executes exactly the inner rotations the host model counts."""
+    lay = tiny.g.layout(H, H, C, BS, S)
+    plan = tiny.g.plan_conv(lay, Co, K, stride=stride, level=tiny.g.L)
+    r = fe.rotation_model(tiny.pr.N, H, H, C, Co, K, S, BS, stride)
+    assert plan.info.n_inner_rot == r["executed_inner"]

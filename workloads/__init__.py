@@ -76,3 +76,23 @@ def mobilenet_block(seed, H, Cin, Cout, BS=1, block=0):
     wd = normal_weight(seed, (Cin, 1, 3, 3), 1.0 / 3.0, stream=200 + block)
     wp = normal_weight(seed, (Cout, Cin, 1, 1), 1.0 / np.sqrt(Cin), stream=300 + block)
     return x, wd, wp
+
+
+def synthetic_layers(seed=0, n=200):
+    """Config "learned fragment/schedule proposer": n conv layers drawn with seed:
+    H = W log-uniform over [8, 224] (rounded to an integer), Cin and Cout
+    log-uniform over [3, 512], K in {1, 3, 5}, stride in {1, 2},
+    N in {2^14, 2^16}.  Returns a list of dicts; the first 80 % are the training
+    split, the rest the test split."""
+    rng = _rng(seed, 400)
+    out = []
+    for i in range(n):
+        H = int(round(float(np.exp(rng.uniform(np.log(8), np.log(224))))))
+        Cin = int(round(float(np.exp(rng.uniform(np.log(3), np.log(512))))))
+        Cout = int(round(float(np.exp(rng.uniform(np.log(3), np.log(512))))))
+        K = int(rng.choice([1, 3, 5]))
+        stride = int(rng.choice([1, 2]))
+        logN = int(rng.choice([14, 16]))
+        out.append(dict(id=i, H=H, W=H, Cin=Cin, Cout=Cout, K=K, stride=stride, logN=logN,
+                        split="train" if i < int(0.8 * n) else "test"))
+    return out
