@@ -56,6 +56,7 @@ typedef struct fe_ctx fe_ctx;
 typedef struct fe_evk fe_evk;
 typedef struct fe_plan fe_plan;
 typedef struct fe_graph fe_graph;
+typedef struct fe_server fe_server;
 
 /* Parameter set.  q primes: the n_q largest primes below 2^qbits with
  * q = 1 (mod 2N); special primes: the k largest primes below 2^pbits with the
@@ -157,6 +158,15 @@ int fe_evk_gen(fe_ctx* ctx, const void* sk_dev, uint64_t seed, const int32_t* st
                uint32_t n_steps, int relin, void* evk_dev, size_t evk_bytes, void* stream,
                fe_evk** out);
 void fe_evk_destroy(fe_evk* evk);
+
+/* For latency measurement only: make every step in steps[] that has no key
+ * use one of the evk's generated keys (round robin).  Rotations by those steps
+ * then compute with the wrong key (their results do not decrypt), but read
+ * and write exactly the memory a real key would, so layer timings are
+ * representative without generating and storing every key.  *n_aliased
+ * (optional) receives the number of steps added.  Errors: FE_EINVAL, FE_EKEY
+ * (the evk holds no key). */
+int fe_evk_alias(fe_ctx* ctx, fe_evk* evk, const int32_t* steps, uint32_t n_steps, uint32_t* n_aliased);
 
 /* ---- layout, packing, encode / encrypt / decrypt (client) ----------------- */
 
@@ -306,6 +316,36 @@ int fe_he_fc(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt
              const void* in_dev, void* out_dev, void* workspace_dev, size_t workspace_bytes,
              int mode, void* stream);
 
+/* Workspace bytes for running `plan` on n_req requests at once
+ * (fe_he_layer_batch); minimum = 1 gives the smallest workspace that works
+ * (outer rotations one at a time), 0 the default (all outer rotations in one
+ * chunk unless that needs more than 8 GiB of scratch).  0 on a null plan. */
+size_t fe_plan_workspace_bytes(const fe_plan* plan, uint32_t n_req, int minimum);
+/* One planned conv or FC layer (Sec. 3.1 / Sec. 5) for n_req independent
+ * requests that share the plan, its plaintexts and the keys: in_dev holds
+ * [n_req][n_in_ct] ciphertexts at the plan's level, out_dev receives
+ * [n_req][n_out_ct] at level - 1.  Items that use the same rotation key are
+ * grouped across requests, so each key is streamed once for all of them.  Each
+ * request's output residues are identical to running it alone (fe_he_conv /
+ * fe_he_fc).  ws: at least fe_plan_workspace_bytes(plan, n_req, 1) bytes.
+ * Errors as fe_he_conv. */
+int fe_he_layer_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev,
+                      const void* in_dev, void* out_dev, uint32_t n_req, void* ws, size_t ws_bytes,
+                      int mode, void* stream);
+
+/* For latency measurement only: run one conv / FC plan with its plaintexts
+ * taken cyclically from a pool (term t uses pool plaintext t mod n_pool;
+ * pt_pool_dev holds n_pool plaintexts [n_pool][level+1][N]).  The kernels,
+ * launches and memory volume are those of fe_he_conv; the result is not the
+ * layer's.  Errors as fe_he_conv. */
+int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_pool_dev,
+                       uint32_t n_pool, const void* in_dev, void* out_dev, void* ws, size_t ws_bytes,
+                       void* stream);
+/* Keep only the first max_out_ct output ciphertexts of a plan (with the terms,
+ * plaintexts and inner rotations they use); their results are unchanged.  Used
+ * to time a slice of a large layer.  Errors: FE_EINVAL. */
+int fe_plan_truncate(fe_plan* plan, uint32_t max_out_ct);
+
 /* x^2 activation (the a x^2 + b x + c polynomial of Sec. 5, Implementation, with a = 1,
  * b = c = 0): CMult with relinearisation, then rescale.  in: [n_ct][2][level+1][N],
  * out: [n_ct][2][level][N].  Workspace: fe_square_workspace_bytes. */
@@ -346,6 +386,108 @@ int fe_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans
 int fe_graph_launch(fe_graph* graph, void* stream);
 void fe_graph_destroy(fe_graph* graph);
 
+/* ---- latency model (learned fragment / schedule proposer) ------------------- */
+
+/* A small fully connected regression model in fp32 (no counterpart in the
+ * paper; it proposes a fragment size and schedule per layer from measured
+ * latencies, with the analytic choice of fe_choose_fragment as its fallback
+ * and judge): in_dim -> hidden x n_hidden (ReLU) -> 1.  Weights He-uniform
+ * from SplitMix64(seed), biases zero.  Parameters are laid out per layer as
+ * W [out][in] then b [out].  Training is full-batch Adam (beta 0.9 / 0.999,
+ * eps 1e-8, decoupled weight decay) on the mean squared error of the
+ * standardised target; features and target are standardised with the
+ * training set's statistics, which prediction reuses.  All arithmetic runs in
+ * the library's CUDA kernels. */
+typedef struct fe_mlp fe_mlp;
+int fe_mlp_create(uint32_t in_dim, uint32_t hidden, uint32_t n_hidden, uint64_t seed, fe_mlp** out);
+void fe_mlp_destroy(fe_mlp* m);
+size_t fe_mlp_param_count(const fe_mlp* m);
+/* Copy all parameters to / from host memory (fe_mlp_param_count floats). */
+int fe_mlp_get_params(const fe_mlp* m, float* host);
+int fe_mlp_set_params(fe_mlp* m, const float* host);
+/* Feature means / standard deviations (in_dim each) and the target's mean and
+ * standard deviation, as fixed by the last training call. */
+int fe_mlp_get_scaling(const fe_mlp* m, float* x_mean, float* x_std, float* y_mean_std);
+/* `steps` Adam steps on X_dev [n][in_dim], y_dev [n] (device, fp32, 16-byte
+ * aligned); *final_loss (optional) receives the standardised MSE after
+ * training.  Needs a non-default stream (one step is graph-captured).
+ * Errors: FE_EINVAL, FE_ECUDA. */
+int fe_mlp_train(fe_mlp* m, const float* X_dev, const float* y_dev, uint32_t n, uint32_t steps, float lr,
+                 float weight_decay, float* final_loss, void* stream);
+/* y_dev [n] = model(X_dev [n][in_dim]) in the target's original units. */
+int fe_mlp_predict(fe_mlp* m, const float* X_dev, uint32_t n, float* y_dev, void* stream);
+
+/* ---- request loop (serving) --------------------------------------------------- */
+
+/* A serving loop over registered models (no counterpart in the paper, which
+ * evaluates one request at a time; the usage flow of Sec. 4.1 per request):
+ * requests are batched continuously, admitted by device memory, and run with
+ * keys and plaintexts resident.  One scheduler thread per server forms launch
+ * groups of up to max_batch pending requests of one model (the model of the
+ * oldest pending request), shrunk until the group's device memory fits the
+ * budget beside the groups in flight, and runs each group on its own stream
+ * (max_inflight streams), so that groups of different models and ring sizes
+ * overlap on the device.  A request that cannot fit alone into the whole
+ * budget finishes with FE_ENOMEM.  A request's residues do not depend on the
+ * group it ran in.  The caller must not use a registered context from other
+ * threads while the server runs (its counters are not synchronised). */
+typedef struct {
+    uint32_t max_batch;        /* requests per launch group, >= 1 */
+    uint32_t max_inflight;     /* launch groups (streams) on the device at once, 1..64 */
+    size_t hbm_budget_bytes;   /* device bytes for request data; 0: free memory at creation - reserve */
+    size_t hbm_reserve_bytes;  /* kept free when hbm_budget_bytes = 0 */
+} fe_server_config;
+
+enum { FE_OP_LAYER = 0, FE_OP_SQUARE = 1, FE_OP_POOL = 2 };
+/* One operation of a model, applied to the output of the previous one:
+ * FE_OP_LAYER: a conv or FC plan with its plaintexts (fe_he_layer_batch);
+ * FE_OP_SQUARE: x^2 (fe_he_square); FE_OP_POOL: 2x2 average pooling of the
+ * fragment layout `layout` (fe_he_avgpool).  Plans and plaintexts are owned by
+ * the caller and must outlive the server. */
+typedef struct {
+    int kind;
+    const fe_plan* plan;
+    const void* pt_dev;
+    fe_layout layout;
+} fe_op;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, groups, max_group;
+    uint64_t max_inflight;  /* most groups seen with device work outstanding at once */
+    size_t peak_bytes, budget_bytes;
+    double p50_ms, p99_ms, mean_ms, wall_s;  /* latency: submit -> result in the host buffer */
+} fe_server_stats_t;
+
+/* Start a server (and its scheduler thread) on the current device.
+ * Errors: FE_EINVAL, FE_ECUDA. */
+int fe_server_create(const fe_server_config* cfg, fe_server** out);
+/* Register a model: ops[0..n_ops) on context ctx with keys evk; requests carry
+ * in_ct ciphertexts at in_level ([in_ct][2][in_level+1][N] uint64).  Checks
+ * that the levels and ciphertext counts chain.  Errors: FE_EINVAL, FE_ELEVEL,
+ * FE_EKEY. */
+int fe_server_add_model(fe_server* s, fe_ctx* ctx, const fe_evk* evk, const fe_op* ops, uint32_t n_ops,
+                        uint32_t in_ct, uint32_t in_level, uint32_t* model_id);
+/* Output shape of a model: ciphertext count, level and the byte sizes of a
+ * request's input and output buffers. */
+int fe_server_model_io(fe_server* s, uint32_t model, uint32_t* out_ct, uint32_t* out_level,
+                       size_t* in_bytes, size_t* out_bytes);
+/* Queue a request.  in_host / out_host are caller-owned host buffers of the
+ * model's input / output size and must stay valid until the request finishes
+ * (pinned memory gives asynchronous copies).  Returns at once with the id. */
+int fe_server_submit(fe_server* s, uint32_t model, const void* in_host, void* out_host, uint64_t* req_id);
+/* Pause (paused = 1) or resume (0) admission: queued requests wait, groups in
+ * flight continue (draining, maintenance, or queueing a burst to run as one
+ * batch). */
+int fe_server_pause(fe_server* s, int paused);
+/* Wait at most timeout_ms for a request; *status receives FE_OK or the
+ * request's error, *latency_ms its submit-to-result time.  Errors: FE_ETIMEOUT
+ * (not finished within the limit), FE_EINVAL (unknown id). */
+int fe_server_wait(fe_server* s, uint64_t req_id, uint32_t timeout_ms, int* status, double* latency_ms);
+/* Counters and nearest-rank latency percentiles of the completed requests. */
+int fe_server_stats(fe_server* s, fe_server_stats_t* out);
+/* Stop the scheduler, wait for the groups in flight, release the streams. */
+void fe_server_destroy(fe_server* s);
+
 /* ---- kernel timing ---------------------------------------------------------- */
 
 /* Time every launch of one kernel class with CUDA events recorded on the
@@ -353,6 +495,9 @@ void fe_graph_destroy(fe_graph* graph);
  * "bconv", "keyip", "combine" (ModDown combine, single and summed), "mac",
  * "rescale", "encode".  While active, each launch of that class also adds its
  * algorithmic bytes (words each launch must read and write once) to a total.
+ * Kinds: "ntt", "bconv", "keyip", "combine", "mac", "rescale", "encode", and
+ * the stages of a planned layer "stage_inner", "stage_base", "stage_outer",
+ * "stage_rescale" (one interval per stage and layer call).
  * fe_profile_end synchronises the recorded streams and returns the summed
  * duration in ms, the launch count and the algorithmic bytes.  Not for use
  * inside stream capture. */

@@ -68,7 +68,45 @@ class FeFragmentChoice(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class FeServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", u32), ("max_inflight", u32), ("hbm_budget_bytes", sz), ("hbm_reserve_bytes", sz)]
+
+
+class FeOp(ctypes.Structure):
+    _fields_ = [("kind", cint), ("plan", vp), ("pt_dev", vp), ("layout", FeLayout)]
+
+
+class FeServerStats(ctypes.Structure):
+    _fields_ = [("submitted", u64), ("completed", u64), ("rejected", u64), ("groups", u64), ("max_group", u64),
+                ("max_inflight", u64), ("peak_bytes", sz), ("budget_bytes", sz), ("p50_ms", dbl), ("p99_ms", dbl),
+                ("mean_ms", dbl), ("wall_s", dbl)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+OP_LAYER, OP_SQUARE, OP_POOL = 0, 1, 2
+
 SIGNATURES = {
+    "fe_mlp_create": (cint, [u32, u32, u32, u64, P(vp)]),
+    "fe_mlp_destroy": (None, [vp]),
+    "fe_mlp_param_count": (sz, [vp]),
+    "fe_mlp_get_params": (cint, [vp, P(ctypes.c_float)]),
+    "fe_mlp_set_params": (cint, [vp, P(ctypes.c_float)]),
+    "fe_mlp_get_scaling": (cint, [vp, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float)]),
+    "fe_mlp_train": (cint, [vp, vp, vp, u32, u32, ctypes.c_float, ctypes.c_float, P(ctypes.c_float), vp]),
+    "fe_mlp_predict": (cint, [vp, vp, u32, vp, vp]),
+    "fe_evk_alias": (cint, [vp, vp, P(i32), u32, P(u32)]),
+    "fe_he_layer_timing": (cint, [vp, vp, vp, vp, u32, vp, vp, vp, sz, vp]),
+    "fe_plan_truncate": (cint, [vp, u32]),
+    "fe_server_create": (cint, [P(FeServerConfig), P(vp)]),
+    "fe_server_add_model": (cint, [vp, vp, vp, P(FeOp), u32, u32, u32, P(u32)]),
+    "fe_server_model_io": (cint, [vp, u32, P(u32), P(u32), P(sz), P(sz)]),
+    "fe_server_submit": (cint, [vp, u32, vp, vp, P(u64)]),
+    "fe_server_pause": (cint, [vp, cint]),
+    "fe_server_wait": (cint, [vp, u64, u32, P(cint), P(dbl)]),
+    "fe_server_stats": (cint, [vp, P(FeServerStats)]),
+    "fe_server_destroy": (None, [vp]),
     "fe_rotation_model": (cint, [u32, u32, u32, u32, u32, u32, u32, u32, u32, cint, P(FeRotationModel)]),
     "fe_choose_fragment": (cint, [u32, u32, u32, u32, u32, u32, u32, cint, u32, P(FeFragmentChoice)]),
     "fe_ctx_create": (cint, [P(FeParams), P(vp)]),
@@ -101,6 +139,8 @@ SIGNATURES = {
     "fe_plan_rotation_steps": (cint, [vp, P(i32), u32, P(u32)]),
     "fe_plan_load_weights": (cint, [vp, vp, vp, dbl, dbl, vp, vp]),
     "fe_he_conv": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
+    "fe_plan_workspace_bytes": (sz, [vp, u32, cint]),
+    "fe_he_layer_batch": (cint, [vp, vp, vp, vp, vp, vp, u32, vp, sz, cint, vp]),
     "fe_he_fc": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
     "fe_square_workspace_bytes": (sz, [vp, u32, u32]),
     "fe_he_square": (cint, [vp, vp, vp, u32, u32, vp, vp, sz, vp]),
@@ -172,6 +212,10 @@ class Evk:
 class Plan:
     def __init__(self, ctx, handle, out_layout=None):
         self.ctx, self.handle, self.out_layout = ctx, handle, out_layout
+        self.refresh()
+
+    def refresh(self):
+        handle = self.handle
         info = FePlanInfo()
         check(load().fe_plan_query(handle, ctypes.byref(info)))
         self.info = info
@@ -367,6 +411,39 @@ class Context:
                                 ws.numel() * 8, mode, _stream()))
         return out
 
+    def workspace_bytes(self, plan, n_req=1, minimum=False):
+        return int(load().fe_plan_workspace_bytes(plan.handle, n_req, 1 if minimum else 0))
+
+    def evk_alias(self, evk, steps):
+        """Timing only: map keyless steps to generated keys (see fe_evk_alias)."""
+        arr = (i32 * max(1, len(steps)))(*steps)
+        n = u32(0)
+        check(load().fe_evk_alias(self.handle, evk.handle, arr, len(steps), ctypes.byref(n)))
+        return n.value
+
+    def plan_truncate(self, plan, max_out_ct):
+        check(load().fe_plan_truncate(plan.handle, max_out_ct))
+        plan.refresh()
+        return plan
+
+    def he_layer_timing(self, evk, plan, pt_pool, n_pool, ct, out, ws):
+        check(load().fe_he_layer_timing(self.handle, evk.handle, plan.handle, _ptr(pt_pool), n_pool, _ptr(ct),
+                                        _ptr(out), _ptr(ws), ws.numel() * ws.element_size(), _stream()))
+        return out
+
+    def he_layer_batch(self, evk, plan, pt, ct, n_req, mode=1, ws=None, out=None):
+        """One conv / FC layer for n_req requests laid out [n_req][n_in_ct] (ct: a
+        tensor [n_req * n_in_ct, 2, level+1, N]); returns [n_req * n_out_ct, ...]."""
+        info = plan.info
+        lv = plan.level
+        if out is None:
+            out = self.empty_ct(n_req * info.n_out_ct, lv - 1)
+        if ws is None:
+            ws = self.workspace(self.workspace_bytes(plan, n_req))
+        check(load().fe_he_layer_batch(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), n_req,
+                                       _ptr(ws), ws.numel() * ws.element_size(), mode, _stream()))
+        return out
+
     def he_fc(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
         ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
         out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
@@ -427,6 +504,120 @@ class Context:
 
 
 P_i32 = ctypes.POINTER(i32)
+
+
+class MLP:
+    """fp32 latency model (in_dim -> hidden x n_hidden ReLU -> 1) with CUDA
+    training (full-batch Adam) and inference kernels."""
+
+    def __init__(self, in_dim, hidden=64, n_hidden=3, seed=0):
+        h = vp()
+        check(load().fe_mlp_create(in_dim, hidden, n_hidden, seed, ctypes.byref(h)))
+        self.handle = h
+        self.in_dim, self.hidden, self.n_hidden = in_dim, hidden, n_hidden
+
+    def params(self):
+        n = load().fe_mlp_param_count(self.handle)
+        a = np.zeros(n, dtype=np.float32)
+        check(load().fe_mlp_get_params(self.handle, a.ctypes.data_as(P(ctypes.c_float))))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == load().fe_mlp_param_count(self.handle)
+        check(load().fe_mlp_set_params(self.handle, a.ctypes.data_as(P(ctypes.c_float))))
+
+    def scaling(self):
+        xm = np.zeros(self.in_dim, np.float32)
+        xs = np.zeros(self.in_dim, np.float32)
+        ys = np.zeros(2, np.float32)
+        fp = P(ctypes.c_float)
+        check(load().fe_mlp_get_scaling(self.handle, xm.ctypes.data_as(fp), xs.ctypes.data_as(fp),
+                                        ys.ctypes.data_as(fp)))
+        return xm, xs, ys
+
+    def train(self, X, y, steps=2000, lr=1e-3, weight_decay=0.0):
+        torch = _torch()
+        Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32)).cuda()
+        yd = torch.as_tensor(np.ascontiguousarray(y, np.float32)).cuda()
+        loss = ctypes.c_float(0)
+        check(load().fe_mlp_train(self.handle, _ptr(Xd), _ptr(yd), Xd.shape[0], steps, lr, weight_decay,
+                                  ctypes.byref(loss), _stream()))
+        return loss.value
+
+    def predict(self, X):
+        torch = _torch()
+        Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32)).cuda()
+        yd = torch.empty(Xd.shape[0], dtype=torch.float32, device="cuda")
+        check(load().fe_mlp_predict(self.handle, _ptr(Xd), Xd.shape[0], _ptr(yd), _stream()))
+        return yd.cpu().numpy()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_mlp_destroy(self.handle)
+            self.handle = None
+
+
+class Server:
+    """Request loop over registered models (continuous batching, admission by
+    device memory, resident keys).  Plans, plaintexts, keys and contexts passed
+    to add_model must outlive the server; host buffers passed to submit must
+    stay alive until the request finishes."""
+
+    def __init__(self, max_batch=4, max_inflight=3, hbm_budget_bytes=0, hbm_reserve_bytes=4 << 30):
+        cfg = FeServerConfig(max_batch, max_inflight, hbm_budget_bytes, hbm_reserve_bytes)
+        h = vp()
+        check(load().fe_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = []
+
+    def add_model(self, ctx, evk, ops, in_ct, in_level):
+        """ops: list of (OP_LAYER, plan, pt) / (OP_SQUARE,) / (OP_POOL, layout)."""
+        arr = (FeOp * len(ops))()
+        for i, op in enumerate(ops):
+            if op[0] == OP_LAYER:
+                arr[i] = FeOp(OP_LAYER, op[1].handle, _ptr(op[2]), FeLayout())
+            elif op[0] == OP_SQUARE:
+                arr[i] = FeOp(OP_SQUARE, None, None, FeLayout())
+            else:
+                arr[i] = FeOp(OP_POOL, None, None, op[1])
+        mid = u32(0)
+        check(load().fe_server_add_model(self.handle, ctx.handle, evk.handle, arr, len(ops), in_ct, in_level,
+                                         ctypes.byref(mid)))
+        self._keep.append((ctx, evk, ops))
+        return mid.value
+
+    def model_io(self, model):
+        oc, ol, ib, ob = u32(0), u32(0), sz(0), sz(0)
+        check(load().fe_server_model_io(self.handle, model, ctypes.byref(oc), ctypes.byref(ol), ctypes.byref(ib),
+                                        ctypes.byref(ob)))
+        return oc.value, ol.value, ib.value, ob.value
+
+    def pause(self, paused=True):
+        check(load().fe_server_pause(self.handle, 1 if paused else 0))
+
+    def submit(self, model, in_host, out_host):
+        rid = u64(0)
+        check(load().fe_server_submit(self.handle, model, _ptr(in_host), _ptr(out_host), ctypes.byref(rid)))
+        return rid.value
+
+    def wait(self, rid, timeout_ms=600000):
+        st, lat = cint(0), dbl(0)
+        check(load().fe_server_wait(self.handle, rid, timeout_ms, ctypes.byref(st), ctypes.byref(lat)))
+        return st.value, lat.value
+
+    def stats(self):
+        r = FeServerStats()
+        check(load().fe_server_stats(self.handle, ctypes.byref(r)))
+        return r.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def rotation_model(N, H, W, Cin, Cout, K, S, BS, stride=1, depthwise=False):

@@ -37,7 +37,11 @@ struct LevelTabs {
     const int* d_up_mod;
 };
 
-enum ProfKind { PK_NTT = 0, PK_BCONV, PK_KEYIP, PK_COMBINE, PK_MAC, PK_RESCALE, PK_ENCODE, PK_COUNT };
+enum ProfKind {
+    PK_NTT = 0, PK_BCONV, PK_KEYIP, PK_COMBINE, PK_MAC, PK_RESCALE, PK_ENCODE,
+    // stages of a planned layer: inner rotations, unrotated MAC, outer rotations, rescale
+    PK_STAGE_INNER, PK_STAGE_BASE, PK_STAGE_OUTER, PK_STAGE_RESCALE, PK_COUNT
+};
 
 }  // namespace fe
 

@@ -143,14 +143,15 @@ std::vector<std::pair<int, int>> outer_order(const fe_plan* p) {
     return v;
 }
 
-size_t item_bytes(const fe_plan* p, size_t chunk) {
+size_t item_bytes(const fe_plan* p, size_t chunk, size_t R) {
     size_t groups = 0;
     for (auto& o : p->outs) groups += o.groups.size();
-    size_t n_chunks = p->n_outer ? (p->n_outer + chunk - 1) / chunk : 0;
-    size_t n = p->inner.size() * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(CombineItem));
-    n += (size_t)p->n_outer * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(SumEntry));
-    n += n_chunks * p->n_out * sizeof(SumItem);
-    n += groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm);
+    const size_t n_outer = R * p->n_outer;
+    size_t n_chunks = n_outer ? (n_outer + chunk - 1) / chunk : 0;
+    size_t n = R * p->inner.size() * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(CombineItem));
+    n += n_outer * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(SumEntry));
+    n += n_chunks * R * p->n_out * sizeof(SumItem);
+    n += R * (groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm));
     return n + 16 * 256;
 }
 
@@ -176,27 +177,36 @@ int layout_fill(int N, fe_layout* l) {
     return FE_OK;
 }
 
-size_t plan_workspace(const fe_plan* p, size_t chunk) {
+size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
     const fe_ctx* c = p->c;
     Sizes z = sizes_of(c, p->level);
     size_t n_mu = p->modup_cts.size(), n_in_rot = p->inner.size();
-    size_t persist = (n_in_rot + p->n_out) * z.ctw;
-    size_t inner = n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + z.ctw);
-    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw) + (size_t)p->n_out * z.ctw;
-    size_t rs = rescale_tmp_words(c, p->n_out, p->level);
+    size_t persist = R * (n_in_rot + p->n_out) * z.ctw;
+    size_t inner = R * (n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + z.ctw));
+    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw) + R * p->n_out * z.ctw;
+    size_t rs = rescale_tmp_words(c, (int)(R * p->n_out), p->level);
     size_t words = persist + std::max(std::max(inner, outer), rs);
-    return words * 8 + item_bytes(p, chunk) + 32 * 256;
+    return words * 8 + item_bytes(p, chunk, R) + 32 * 256;
 }
 
 // Both phases derive every pointer from (plan, buffers, workspace) alone, so a
 // graph can be captured from the launch phase after an upload phase.
+// n_req requests share the plan, its plaintexts and keys: request r reads its
+// inputs at b_in + r n_in ct words and writes its outputs at b_out + r n_out
+// (level - 1) ct words.  Items that use one key are grouped across requests,
+// so a key is streamed once per launch for all of them; every request's
+// arithmetic is the same as when it runs alone.
 int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, const u64* b_pt, u64* b_out,
-             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase) {
+             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req, int pt_pool) {
     const int N = c->N, lv = p->level;
     Sizes z = sizes_of(c, lv);
-    size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, p->n_outer);
-    while (chunk > 1 && plan_workspace(p, chunk) > ws_bytes) chunk = (chunk + 1) / 2;
-    if (plan_workspace(p, chunk) > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the plan");
+    if (n_req < 1) return fail(FE_EINVAL, "n_req must be positive");
+    const size_t R = (size_t)n_req;
+    const size_t ctw_out = ct_words(c, lv - 1);
+    const size_t n_in_rot = p->inner.size(), n_mu = p->modup_cts.size(), n_terms = p->terms.size();
+    size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, R * p->n_outer);
+    while (chunk > 1 && plan_workspace(p, chunk, R) > ws_bytes) chunk = (chunk + 1) / 2;
+    if (plan_workspace(p, chunk, R) > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the plan");
     std::map<int32_t, const u64*> keys;
     for (int32_t s : p->steps) {
         const u64* k = evk_key(evk, c->galois(s));
@@ -205,88 +215,104 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     }
     // ---- carve the workspace ----
     Carver cv(ws, ws_bytes);
-    const size_t n_in_rot = p->inner.size(), n_mu = p->modup_cts.size();
-    u64* R = cv.take<u64>(n_in_rot * z.ctw);
-    u64* total = cv.take<u64>((size_t)p->n_out * z.ctw);
+    u64* Rb = cv.take<u64>(R * n_in_rot * z.ctw);
+    u64* total = cv.take<u64>(R * p->n_out * z.ctw);
     size_t n_groups_all = 0;
     for (auto& o : p->outs) n_groups_all += o.groups.size();
-    auto order = outer_order(p);
+    // rotated groups of all requests: (request, output, group), sorted by step
+    struct OuterRef {
+        int r, o, gi;
+    };
+    std::vector<OuterRef> order;
+    for (const auto& og : outer_order(p))
+        for (size_t r = 0; r < R; r++) order.push_back({(int)r, og.first, og.second});
     const size_t n_chunks = order.empty() ? 0 : (order.size() + chunk - 1) / chunk;
-    KsItem* d_in_ks = cv.take<KsItem>(std::max<size_t>(1, n_in_rot));
-    KsGroup* d_in_kg = cv.take<KsGroup>(std::max<size_t>(1, n_in_rot));
-    CombineItem* d_in_cb = cv.take<CombineItem>(std::max<size_t>(1, n_in_rot));
-    MacItem* d_mac = cv.take<MacItem>(std::max<size_t>(1, n_groups_all));
-    MacTerm* d_terms = cv.take<MacTerm>(std::max<size_t>(1, p->terms.size()));
+    KsItem* d_in_ks = cv.take<KsItem>(std::max<size_t>(1, R * n_in_rot));
+    KsGroup* d_in_kg = cv.take<KsGroup>(std::max<size_t>(1, R * n_in_rot));
+    CombineItem* d_in_cb = cv.take<CombineItem>(std::max<size_t>(1, R * n_in_rot));
+    MacItem* d_mac = cv.take<MacItem>(std::max<size_t>(1, R * n_groups_all));
+    MacTerm* d_terms = cv.take<MacTerm>(std::max<size_t>(1, R * n_terms));
     KsItem* d_out_ks = cv.take<KsItem>(std::max<size_t>(1, order.size()));
     KsGroup* d_out_kg = cv.take<KsGroup>(std::max<size_t>(1, order.size()));
     SumEntry* d_ent = cv.take<SumEntry>(std::max<size_t>(1, order.size()));
-    SumItem* d_sum = cv.take<SumItem>(std::max<size_t>(1, n_chunks * p->n_out));
+    SumItem* d_sum = cv.take<SumItem>(std::max<size_t>(1, n_chunks * R * p->n_out));
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
     char* scratch = cv.p;
     const size_t scratch_bytes = cv.left;
     Carver s1(scratch, scratch_bytes);  // stage 1
-    u64* coef1 = s1.take<u64>(n_mu * z.nlN);
-    u64* ext1 = s1.take<u64>(n_mu * z.extw);
-    u64* acc1 = s1.take<u64>(n_in_rot * z.accw);
-    u64* conv1 = s1.take<u64>(n_in_rot * z.ctw);
+    u64* coef1 = s1.take<u64>(R * n_mu * z.nlN);
+    u64* ext1 = s1.take<u64>(R * n_mu * z.extw);
+    u64* acc1 = s1.take<u64>(R * n_in_rot * z.accw);
+    u64* conv1 = s1.take<u64>(R * n_in_rot * z.ctw);
     Carver s3(scratch, scratch_bytes);  // stage 3 (same region)
     u64* Pd = s3.take<u64>(chunk * z.ctw);
     u64* coef3 = s3.take<u64>(chunk * z.nlN);
     u64* ext3 = s3.take<u64>(chunk * z.extw);
     u64* acc3 = s3.take<u64>(chunk * z.accw);
     u64* conv3 = s3.take<u64>(chunk * z.ctw);
-    u64* csum3 = s3.take<u64>((size_t)p->n_out * z.ctw);  // per-output sums of the converted parts
+    u64* csum3 = s3.take<u64>(R * p->n_out * z.ctw);  // per-output sums of the converted parts
     Carver s4(scratch, scratch_bytes);  // stage 4 (same region)
-    u64* rs_tmp = s4.take<u64>(2 * (size_t)p->n_out * N);
-    u64* rs_lift = s4.take<u64>(2 * (size_t)p->n_out * lv * N);
+    u64* rs_tmp = s4.take<u64>(2 * R * p->n_out * N);
+    u64* rs_lift = s4.take<u64>(2 * R * p->n_out * lv * N);
     if (!s1.ok || !s3.ok || !s4.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
 
-    auto src_ptr = [&](int src) -> const u64* {
-        return src >= 0 ? R + (size_t)src * z.ctw : b_in + (size_t)(-src - 1) * z.ctw;
+    auto src_ptr = [&](size_t r, int src) -> const u64* {
+        return src >= 0 ? Rb + (r * n_in_rot + src) * z.ctw : b_in + (r * p->n_in + (size_t)(-src - 1)) * z.ctw;
     };
+    // global index of the s-th converted input (request-major) and its source ciphertext
+    auto mu_ct = [&](size_t s) -> size_t { return (s / n_mu) * p->n_in + p->modup_cts[s % n_mu]; };
 
     // ---- host item tables ----
-    std::vector<int> iorder(n_in_rot);
-    for (size_t r = 0; r < n_in_rot; r++) iorder[r] = (int)r;
-    std::stable_sort(iorder.begin(), iorder.end(), [&](int x, int y) { return p->inner[x].step < p->inner[y].step; });
-    std::vector<KsItem> iks(n_in_rot);
+    std::vector<std::pair<int, int>> iorder;  // (request, R slot), sorted by step
+    for (size_t r = 0; r < R; r++)
+        for (size_t i = 0; i < n_in_rot; i++) iorder.push_back({(int)r, (int)i});
+    std::stable_sort(iorder.begin(), iorder.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+        return p->inner[x.second].step < p->inner[y.second].step;
+    });
+    std::vector<KsItem> iks(iorder.size());
     std::vector<KsGroup> ikg;
-    std::vector<CombineItem> icb(n_in_rot);
-    for (size_t q = 0; q < n_in_rot; q++) {
-        int r = iorder[q];
-        const auto& in = p->inner[r];
-        iks[q] = KsItem{ext1 + (size_t)p->modup_slot[in.ci] * z.extw, keys[in.step], acc1 + (size_t)r * z.accw};
-        if (q == 0 || in.step != p->inner[iorder[q - 1]].step) ikg.push_back(KsGroup{keys[in.step], (int)q, 0});
+    std::vector<CombineItem> icb(R * n_in_rot);
+    for (size_t q = 0; q < iorder.size(); q++) {
+        const size_t r = iorder[q].first, i = iorder[q].second;
+        const auto& in = p->inner[i];
+        iks[q] = KsItem{ext1 + (r * n_mu + p->modup_slot[in.ci]) * z.extw, keys[in.step], acc1 + (r * n_in_rot + i) * z.accw};
+        if (q == 0 || in.step != p->inner[iorder[q - 1].second].step) ikg.push_back(KsGroup{keys[in.step], (int)q, 0});
         ikg.back().n_items++;
     }
-    for (size_t r = 0; r < n_in_rot; r++) {
-        const auto& in = p->inner[r];
-        icb[r] = CombineItem{acc1 + r * z.accw, conv1 + r * z.ctw, b_in + (size_t)in.ci * z.ctw, nullptr,
-                             R + r * z.ctw, c->galois(in.step), 0};
-    }
+    for (size_t r = 0; r < R; r++)
+        for (size_t i = 0; i < n_in_rot; i++) {
+            const auto& in = p->inner[i];
+            const size_t x = r * n_in_rot + i;
+            icb[x] = CombineItem{acc1 + x * z.accw, conv1 + x * z.ctw, b_in + (r * p->n_in + in.ci) * z.ctw, nullptr,
+                                 Rb + x * z.ctw, c->galois(in.step), 0};
+        }
     std::vector<MacTerm> mterms;
-    mterms.reserve(p->terms.size());
-    for (const auto& t : p->terms) mterms.push_back(MacTerm{src_ptr(t.src), b_pt + (size_t)t.pt * z.nlN});
+    mterms.reserve(R * n_terms);
+    for (size_t r = 0; r < R; r++)
+        for (const auto& t : p->terms)
+            mterms.push_back(MacTerm{src_ptr(r, t.src), b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * z.nlN});
     std::vector<MacItem> macs;
-    std::vector<int> no_base;
-    for (int o = 0; o < p->n_out; o++) {
-        bool base = false;
-        for (const auto& g : p->outs[o].groups)
-            if (g.step == 0) {
-                macs.push_back(MacItem{total + (size_t)o * z.ctw, g.t0, g.nt});
-                base = true;
-            }
-        if (!base) no_base.push_back(o);
-    }
+    std::vector<size_t> no_base;  // request-major output index
+    for (size_t r = 0; r < R; r++)
+        for (int o = 0; o < p->n_out; o++) {
+            bool base = false;
+            for (const auto& g : p->outs[o].groups)
+                if (g.step == 0) {
+                    macs.push_back(MacItem{total + (r * p->n_out + o) * z.ctw, (int)(r * n_terms) + g.t0, g.nt});
+                    base = true;
+                }
+            if (!base) no_base.push_back(r * p->n_out + o);
+        }
     const size_t n_base = macs.size();
     int base_terms = 0;
     for (size_t i = 0; i < n_base; i++) base_terms += macs[i].n_terms;
     std::vector<int> chunk_terms;
+    auto group_of = [&](const OuterRef& x) -> const fe_plan::Group& { return p->outs[x.o].groups[x.gi]; };
     for (size_t k = 0; k < order.size(); k++) {
         if (k % chunk == 0) chunk_terms.push_back(0);
-        chunk_terms.back() += p->outs[order[k].first].groups[order[k].second].nt;
-        const auto& g = p->outs[order[k].first].groups[order[k].second];
-        macs.push_back(MacItem{Pd + (k % chunk) * z.ctw, g.t0, g.nt});
+        const auto& g = group_of(order[k]);
+        chunk_terms.back() += g.nt;
+        macs.push_back(MacItem{Pd + (k % chunk) * z.ctw, (int)(order[k].r * n_terms) + g.t0, g.nt});
     }
     std::vector<KsItem> oks(order.size());
     std::vector<KsGroup> okg;
@@ -296,15 +322,14 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
         size_t c1 = std::min(order.size(), c0 + chunk);
         int kg0 = (int)okg.size();
-        std::map<int, std::vector<int>> by_out;
+        std::map<size_t, std::vector<int>> by_out;  // request-major output -> items
         for (size_t k = c0; k < c1; k++) {
-            const auto& g = p->outs[order[k].first].groups[order[k].second];
+            const auto& g = group_of(order[k]);
             size_t s = k - c0;
             oks[k] = KsItem{ext3 + s * z.extw, keys[g.step], acc3 + s * z.accw};
-            if (k == c0 || g.step != p->outs[order[k - 1].first].groups[order[k - 1].second].step)
-                okg.push_back(KsGroup{keys[g.step], (int)k, 0});
+            if (k == c0 || g.step != group_of(order[k - 1]).step) okg.push_back(KsGroup{keys[g.step], (int)k, 0});
             okg.back().n_items++;
-            by_out[order[k].first].push_back((int)k);
+            by_out[(size_t)order[k].r * p->n_out + order[k].o].push_back((int)k);
         }
         kg_range.push_back({kg0, (int)okg.size() - kg0});
         int s0 = (int)sums.size();
@@ -312,10 +337,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             // batched path: one NTT of the summed converted parts per output (convsum);
             // plain path: each rotation's converted part is transformed and subtracted alone
             const u64* cs = mode == 0 ? nullptr : csum3 + (size_t)(sums.size() - s0) * z.ctw;
-            SumItem si{total + (size_t)kv.first * z.ctw, nullptr, (int)ents.size(), (int)kv.second.size(), 1, cs};
+            SumItem si{total + kv.first * z.ctw, nullptr, (int)ents.size(), (int)kv.second.size(), 1, cs};
             for (int k : kv.second) {
                 size_t s = k - c0;
-                const auto& g = p->outs[order[k].first].groups[order[k].second];
+                const auto& g = group_of(order[k]);
                 const uint32_t gal = c->galois(g.step);
                 ents.push_back(SumEntry{acc3 + s * z.accw, conv3 + s * z.ctw, Pd + s * z.ctw, gal,
                                         (uint32_t)h_invmod(gal, 2 * (u64)c->N)});
@@ -339,33 +364,38 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     if (!(phase & 2)) return FE_OK;
 
     // ---- stage 1: inner rotations (hoisted ModUp per input ciphertext) ----
+    const size_t n_mu_all = R * n_mu;
+    {
+    ProfScope stage(c, PK_STAGE_INNER, st, 0.0);
     if (mode == 0) {
-        for (size_t i = 0; i < n_mu; i++)
-            modup(c, b_in + (size_t)p->modup_cts[i] * z.ctw + z.nlN, z.ctw, 1, lv, coef1 + i * z.nlN,
-                  ext1 + i * z.extw, st);
-        for (size_t q = 0; q < n_in_rot; q++) {
+        for (size_t s = 0; s < n_mu_all; s++)
+            modup(c, b_in + mu_ct(s) * z.ctw + z.nlN, z.ctw, 1, lv, coef1 + s * z.nlN, ext1 + s * z.extw, st);
+        for (size_t q = 0; q < iorder.size(); q++) {
+            const size_t x = (size_t)iorder[q].first * n_in_rot + iorder[q].second;
             launch_keyip(c, d_in_ks + q, 1, lv, st);
-            moddown_prepare(c, acc1 + (size_t)iorder[q] * z.accw, 1, lv, conv1 + (size_t)iorder[q] * z.ctw, st);
+            moddown_prepare(c, acc1 + x * z.accw, 1, lv, conv1 + x * z.ctw, st);
         }
-        for (size_t r = 0; r < n_in_rot; r++) launch_combine(c, d_in_cb + r, 1, lv, st);
+        for (size_t x = 0; x < R * n_in_rot; x++) launch_combine(c, d_in_cb + x, 1, lv, st);
     } else {
         size_t i = 0;
-        while (i < n_mu) {  // consecutive runs of rotated inputs are converted together
+        while (i < n_mu_all) {  // consecutive runs of rotated inputs are converted together
             size_t j = i + 1;
-            while (j < n_mu && p->modup_cts[j] == p->modup_cts[j - 1] + 1) j++;
-            modup(c, b_in + (size_t)p->modup_cts[i] * z.ctw + z.nlN, z.ctw, (int)(j - i), lv, coef1 + i * z.nlN,
-                  ext1 + i * z.extw, st);
+            while (j < n_mu_all && mu_ct(j) == mu_ct(j - 1) + 1) j++;
+            modup(c, b_in + mu_ct(i) * z.ctw + z.nlN, z.ctw, (int)(j - i), lv, coef1 + i * z.nlN, ext1 + i * z.extw, st);
             i = j;
         }
-        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)n_in_rot, lv, st);
-        moddown_prepare(c, acc1, (int)n_in_rot, lv, conv1, st);
-        launch_combine(c, d_in_cb, (int)n_in_rot, lv, st);
+        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)iorder.size(), lv, st);
+        moddown_prepare(c, acc1, (int)(R * n_in_rot), lv, conv1, st);
+        launch_combine(c, d_in_cb, (int)(R * n_in_rot), lv, st);
     }
-    c->cnt.rot += n_in_rot;
-    c->cnt.keyswitch += n_in_rot;
+    }
+    c->cnt.rot += R * n_in_rot;
+    c->cnt.keyswitch += R * n_in_rot;
 
     // ---- stage 2: groups without rotation, straight into the totals ----
-    for (int o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + (size_t)o * z.ctw, 0, z.ctw * 8, st));
+    {
+    ProfScope stage(c, PK_STAGE_BASE, st, 0.0);
+    for (size_t o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + o * z.ctw, 0, z.ctw * 8, st));
     if (mode == 0) {
         for (size_t i = 0; i < n_base; i++)
             for (int t = 0; t < macs[i].n_terms; t++) {
@@ -375,8 +405,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     } else {
         launch_mac(c, d_mac, d_terms, (int)n_base, base_terms, lv, st);
     }
+    }
 
     // ---- stage 3: outer rotations in chunks, summed into the totals ----
+    {
+    ProfScope stage(c, PK_STAGE_OUTER, st, 0.0);
     for (size_t c0 = 0, ch = 0; c0 < order.size(); c0 += chunk, ch++) {
         size_t c1 = std::min(order.size(), c0 + chunk);
         int cn = (int)(c1 - c0);
@@ -405,17 +438,20 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             launch_combine_sum(c, d_sum + sum_range[ch].first, d_ent, ns, cn, lv, st);
         }
     }
+    }
     c->cnt.rot += order.size();
     c->cnt.keyswitch += order.size();
-    c->cnt.pmult += p->terms.size();
+    c->cnt.pmult += R * n_terms;
 
     // ---- stage 4: rescale ----
+    {
+    ProfScope stage(c, PK_STAGE_RESCALE, st, 0.0);
     if (mode == 0) {
-        for (int o = 0; o < p->n_out; o++)
-            rescale_batch(c, total + (size_t)o * z.ctw, 1, lv, b_out + (size_t)o * ct_words(c, lv - 1), rs_tmp,
-                          rs_lift, st);
+        for (size_t o = 0; o < R * p->n_out; o++)
+            rescale_batch(c, total + o * z.ctw, 1, lv, b_out + o * ctw_out, rs_tmp, rs_lift, st);
     } else {
-        rescale_batch(c, total, p->n_out, lv, b_out, rs_tmp, rs_lift, st);
+        rescale_batch(c, total, (int)(R * p->n_out), lv, b_out, rs_tmp, rs_lift, st);
+    }
     }
     FE_CUDA_TRY(cudaGetLastError());
     return FE_OK;
@@ -655,6 +691,20 @@ extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, 
 
 extern "C" void fe_plan_destroy(fe_plan* p) { delete p; }
 
+// workspace for n_req requests: the whole outer stage in one chunk, unless the
+// chunk's scratch would exceed 8 GiB
+static size_t default_workspace(const fe_plan* p, size_t n_req) {
+    size_t chunk = std::max<size_t>(1, n_req * p->n_outer);
+    while (chunk > 1 && plan_workspace(p, chunk, n_req) - plan_workspace(p, 1, n_req) > (8ull << 30))
+        chunk = (chunk + 1) / 2;
+    return plan_workspace(p, chunk, n_req);
+}
+
+extern "C" size_t fe_plan_workspace_bytes(const fe_plan* p, uint32_t n_req, int minimum) {
+    if (!p || n_req == 0) return 0;
+    return minimum ? plan_workspace(p, 1, n_req) : default_workspace(p, n_req);
+}
+
 extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     if (!p || !info) return fail(FE_EINVAL, "null argument");
     const fe_ctx* c = p->c;
@@ -662,9 +712,7 @@ extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     info->in_bytes = (size_t)p->n_in * ct_words(c, p->level) * 8;
     info->out_bytes = (size_t)p->n_out * ct_words(c, p->level - 1) * 8;
     // default: the whole outer stage in one chunk, unless its scratch exceeds 8 GiB
-    size_t chunk = std::max(1, p->n_outer);
-    while (chunk > 1 && plan_workspace(p, chunk) - plan_workspace(p, 1) > (8ull << 30)) chunk = (chunk + 1) / 2;
-    info->workspace_bytes = plan_workspace(p, chunk);
+    info->workspace_bytes = default_workspace(p, 1);
     info->workspace_min_bytes = plan_workspace(p, 1);
     info->n_in_ct = p->n_in;
     info->n_out_ct = p->n_out;
@@ -746,4 +794,54 @@ extern "C" int fe_he_fc(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const vo
     if (p->kind != 1) return fail(FE_EINVAL, "not an fc plan");
     return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
                     (cudaStream_t)stream, 3);
+}
+
+extern "C" int fe_he_layer_batch(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
+                                 void* out_dev, uint32_t n_req, void* ws, size_t ws_bytes, int mode, void* stream) {
+    FE_ALIGNED(pt_dev); FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !evk || !p || !pt_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (n_req == 0) return FE_OK;
+    return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
+                    (cudaStream_t)stream, 3, (int)n_req);
+}
+
+extern "C" int fe_he_layer_timing(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_pool_dev,
+                                  uint32_t n_pool, const void* in_dev, void* out_dev, void* ws, size_t ws_bytes,
+                                  void* stream) {
+    FE_ALIGNED(pt_pool_dev); FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !evk || !p || !pt_pool_dev || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (n_pool == 0) return fail(FE_EINVAL, "empty plaintext pool");
+    return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_pool_dev, (u64*)out_dev, ws, ws_bytes, 1,
+                    (cudaStream_t)stream, 3, 1, (int)n_pool);
+}
+
+extern "C" int fe_plan_truncate(fe_plan* p, uint32_t max_out_ct) {
+    if (!p) return fail(FE_EINVAL, "null argument");
+    if (max_out_ct == 0) return fail(FE_EINVAL, "max_out_ct must be positive");
+    if ((int)max_out_ct >= p->n_out) return FE_OK;
+    // terms (and plaintexts, one per term) are laid out in output order: the kept
+    // outputs' terms are a prefix
+    int t_keep = 0;
+    for (uint32_t o = 0; o < max_out_ct; o++)
+        for (const auto& g : p->outs[o].groups) t_keep = std::max(t_keep, g.t0 + g.nt);
+    p->terms.resize(t_keep);
+    if (p->kind == 0) p->cpts.resize(t_keep);
+    else p->fpts.resize(t_keep);
+    p->n_pt = t_keep;
+    p->outs.resize(max_out_ct);
+    p->n_out = (int)max_out_ct;
+    // drop the inner rotations that no kept term reads, renumbering the rest
+    std::vector<int> remap(p->inner.size(), -1);
+    std::vector<fe_plan::Inner> inner;
+    for (auto& t : p->terms)
+        if (t.src >= 0) {
+            if (remap[t.src] < 0) {
+                remap[t.src] = (int)inner.size();
+                inner.push_back(p->inner[t.src]);
+            }
+            t.src = remap[t.src];
+        }
+    p->inner = inner;
+    finish_plan(p);
+    return FE_OK;
 }

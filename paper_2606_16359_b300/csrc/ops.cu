@@ -293,6 +293,24 @@ extern "C" int fe_evk_gen(fe_ctx* c, const void* sk_dev, uint64_t seed, const in
 
 extern "C" void fe_evk_destroy(fe_evk* evk) { delete evk; }
 
+extern "C" int fe_evk_alias(fe_ctx* c, fe_evk* evk, const int32_t* steps, uint32_t n_steps, uint32_t* n_aliased) {
+    if (!c || !evk || (n_steps && !steps)) return fail(FE_EINVAL, "null argument");
+    std::vector<u64*> pool;
+    for (auto& kv : evk->rot) pool.push_back(kv.second);
+    if (pool.empty() && evk->relin) pool.push_back(evk->relin);
+    if (pool.empty()) return fail(FE_EKEY, "fe_evk_alias needs at least one generated key");
+    uint32_t added = 0;
+    for (uint32_t i = 0; i < n_steps; i++) {
+        if (steps[i] % (c->N / 2) == 0) continue;
+        const uint32_t g = c->galois(steps[i]);
+        if (evk->rot.count(g)) continue;
+        evk->rot[g] = pool[added % pool.size()];
+        added++;
+    }
+    if (n_aliased) *n_aliased = added;
+    return FE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI: encode / encrypt / decrypt
 // ---------------------------------------------------------------------------

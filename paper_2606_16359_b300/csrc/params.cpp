@@ -442,7 +442,8 @@ ProfScope::~ProfScope() {
 
 extern "C" int fe_profile_begin(fe_ctx* c, const char* kind) {
     if (!c || !kind) return fail(FE_EINVAL, "null argument");
-    static const char* names[PK_COUNT] = {"ntt", "bconv", "keyip", "combine", "mac", "rescale", "encode"};
+    static const char* names[PK_COUNT] = {"ntt", "bconv", "keyip", "combine", "mac", "rescale", "encode",
+                                          "stage_inner", "stage_base", "stage_outer", "stage_rescale"};
     int k = -1;
     for (int i = 0; i < PK_COUNT; i++)
         if (!strcmp(kind, names[i])) k = i;

@@ -84,6 +84,12 @@ class MobileNetBlocks:
                                             self.graph_ws)
         return self.graph
 
+    def serve_ops(self, bi):
+        """Operation chain of block bi for the request loop (dw then pw)."""
+        from . import OP_LAYER
+        dw, pw = self.layers[2 * bi], self.layers[2 * bi + 1]
+        return [(OP_LAYER, dw["plan"], dw["pt"]), (OP_LAYER, pw["plan"], pw["pt"])]
+
     def decrypt_block(self, bi):
         x, wd, wp, olay = self.ref_inputs[bi]
         slots = self.ctx.decrypt(self.sk, self.outputs[bi], self.ctx.L - 2, self.delta)
@@ -160,6 +166,13 @@ class LeNet:
         s = (s * w5) / float(q[L - 6])
         self.out_scale = s
         self.ws = ctx.workspace(max(p.info.workspace_bytes for p in (self.p1, self.p2, self.f1, self.f2, self.f3)))
+
+    def serve_ops(self):
+        """Operation chain of the whole network for the request loop."""
+        from . import OP_LAYER, OP_POOL, OP_SQUARE
+        return [(OP_LAYER, self.p1, self.pt1), (OP_SQUARE,), (OP_POOL, self.p1.out_layout),
+                (OP_LAYER, self.p2, self.pt2), (OP_SQUARE,), (OP_POOL, self.p2.out_layout),
+                (OP_LAYER, self.f1, self.ptf1), (OP_LAYER, self.f2, self.ptf2), (OP_LAYER, self.f3, self.ptf3)]
 
     def encrypt(self, x, seed=3):
         slots = self.ctx.pack(self.lay0, _torch().from_numpy(np.asarray(x, dtype=np.float64)))

@@ -296,3 +296,33 @@ def test_planner_inner_count_matches_rotation_model(tiny, H, C, Co, K, BS, S, st
     plan = tiny.g.plan_conv(lay, Co, K, stride=stride, level=tiny.g.L)
     r = fe.rotation_model(tiny.pr.N, H, H, C, Co, K, S, BS, stride)
     assert plan.info.n_inner_rot == r["executed_inner"]
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S", [(8, 3, 5, 3, 2, 2), (6, 20, 18, 3, 1, 1)])
+def test_layer_batch_each_request_equals_alone(tiny, H, C, Co, K, BS, S):
+    """Three requests through one batched launch (keys grouped across them): each
+    request's output residues equal running it alone, in both paths, and the
+    plain per-op batch equals the batched one."""
+    g, pr = tiny.g, tiny.pr
+    rng = np.random.default_rng(H + C)
+    w = rng.normal(0, 1 / K, (Co, C, K, K))
+    lay = g.layout(H, H, C, BS, S)
+    plan = g.plan_conv(lay, Co, K, level=pr.L)
+    sk = g.sk_gen(5)
+    evk = g.evk_gen(sk, 5, plan.steps)
+    pt = g.load_weights(plan, w, float(pr.q[pr.L]))
+    cts = []
+    for r in range(3):
+        x = rng.uniform(0, 1, (BS, C, H, H))
+        cts.append(g.encrypt(sk, g.pack(lay, torch.from_numpy(x)), pr.L, 2.0 ** 25, seed=30 + r))
+    alone = [u64(g.he_conv(evk, plan, pt, ct, mode=1)) for ct in cts]
+    batch_in = torch.cat(cts, 0).contiguous()
+    n_out = plan.info.n_out_ct
+    for mode in (1, 0):
+        out = u64(g.he_layer_batch(evk, plan, pt, batch_in, 3, mode=mode))
+        for r in range(3):
+            assert np.array_equal(out[r * n_out:(r + 1) * n_out], alone[r]), (mode, r)
+    # the smallest workspace (one outer rotation at a time) gives the same result
+    ws = g.workspace(g.workspace_bytes(plan, 3, minimum=True))
+    out = u64(g.he_layer_batch(evk, plan, pt, batch_in, 3, ws=ws))
+    assert np.array_equal(out, np.concatenate(alone))
