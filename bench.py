@@ -4,7 +4,10 @@ Workload (default): the three MobileNet-shaped blocks (depthwise 3x3 then
 pointwise) at N = 2^16, 24 x 36-bit + 4 special primes, scale 2^32, inputs
 U[-1, 1), weights N(0, 1/fan_in), fragment size S = 1, one encrypted input per
 block.  A step runs all six HE convolutions (inner rotations, PMult-MAC,
-outer rotations, rescale) with keys, plaintexts and ciphertexts resident.
+outer rotations, rescale) with keys, plaintexts and ciphertexts resident.  The
+outer rotations of each pointwise layer use the schedule the autotuner times
+fastest (linear or baby-step / giant-step); --schedule linear keeps one outer
+rotation per channel diagonal.
 
 Reported: key switches per second (the metric's throughput form), ms per step
 and per layer, the plain per-op path beside the batched/graph path, the
@@ -184,6 +187,8 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=4)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile", default="auto", help="kernel class timed for the roofline, or 'auto'")
+    ap.add_argument("--schedule", default="tuned",
+                    help="outer rotations of the pointwise layers: tuned (autotuner), linear, or n1")
     ap.add_argument("--ncu-step", action="store_true",
                     help="set up, run one warm step, then one batched step between cudaProfilerStart and "
                          "cudaProfilerStop (for ncu --profile-from-start off), and exit")
@@ -206,7 +211,7 @@ def run_ours(args, dist, rank, world, local):
 
     t_setup = time.perf_counter()
     ctx = fe.Context(**PARAMS)
-    net = MobileNetBlocks(ctx, delta=DELTA)
+    net = MobileNetBlocks(ctx, delta=DELTA, schedule=args.schedule)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     ks_per_step = net.keyswitches_per_step
@@ -353,6 +358,7 @@ def run_ours(args, dist, rank, world, local):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "blocks": net.blocks, "keyswitches_per_step": ks_per_step,
                        "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
+                       "pw_schedule_bsgs_n1": net.schedule, "tune_ms": net.tune_ms,
                        "path": "graph" if use_graph else "batched",
                        "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
                        "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,

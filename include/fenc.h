@@ -264,11 +264,18 @@ int fe_add(fe_ctx* ctx, const void* a_dev, const void* b_dev, uint32_t n_ct, uin
  *   one filter per channel), in_period (0, or c_v when the input was replicated
  *   by fe_compress so that channel position c holds channel c mod c_v), level of
  *   the input ciphertexts.
+ *   bsgs_n1: 0 for linear outer rotations (one per nonzero channel diagonal d,
+ *   Rot(P_d, d m^2 BS), Eq. 4); n1 > 0 for the baby-step / giant-step schedule
+ *   the paper assumes (Sec. 3.1): diagonal d = j n1 + i; every input ciphertext
+ *   is rotated by tap offset + i m^2 BS from its one hoisted ModUp, the
+ *   plaintexts of diagonal d are rotated left by i m^2 BS, and one giant
+ *   rotation by j n1 m^2 BS per output and j > 0 (n1 is clipped to cpc;
+ *   depthwise and replicated-input layers stay linear).
  * The plan records the inner rotation offsets, the nonzero diagonals, the
  * multiply-accumulate term lists and the output layout (out_lay).
  * Errors: FE_EINVAL (shape), FE_ELEVEL (level 0). */
 int fe_plan_conv(fe_ctx* ctx, const fe_layout* in_lay, uint32_t Cout, uint32_t K, uint32_t stride,
-                 int depthwise, uint32_t in_period, uint32_t level, fe_layout* out_lay,
+                 int depthwise, uint32_t in_period, uint32_t level, uint32_t bsgs_n1, fe_layout* out_lay,
                  fe_plan** out);
 /* Plan a fully connected layer y = W x on ciphertexts whose positions
  * (P = cpc m^2 per ciphertext, BS slots each) hold features:
@@ -285,6 +292,7 @@ void fe_plan_destroy(fe_plan* plan);
 typedef struct {
     size_t pt_bytes, in_bytes, out_bytes, workspace_bytes, workspace_min_bytes;
     uint32_t n_in_ct, n_out_ct, n_pt, n_inner_rot, n_outer_rot;
+    uint32_t bsgs_n1;  /* baby steps of the outer rotations actually used (0: linear) */
 } fe_plan_info;
 int fe_plan_query(const fe_plan* plan, fe_plan_info* info);
 /* Rotation steps the plan needs keys for (steps_host has room for max entries;

@@ -78,19 +78,36 @@ def conv_diagonals(lay, Cin, Cout, h, depthwise, in_period):
     return sorted(ds)
 
 
-def conv_rotation_steps(lay, Cin, Cout, K, stride=1, depthwise=False, in_period=None):
+def bsgs_split(lay, n1, depthwise=False, in_period=None):
+    """Baby-step count actually used: n1 clipped to cpc; 0 (linear outer
+    rotations) for depthwise or replicated-input layers and for cpc = 1."""
+    if not n1 or depthwise or in_period is not None or lay.cpc <= 1:
+        return 0
+    return min(n1, lay.cpc)
+
+
+def conv_rotation_steps(lay, Cin, Cout, K, stride=1, depthwise=False, in_period=None, bsgs_n1=0):
     offs = counts.inner_offsets(lay.S, K, stride)
+    G_out = lay.groups if depthwise else -(-Cout // lay.cpc)
+    n1 = bsgs_split(lay, bsgs_n1, depthwise, in_period)
+    babies = {0}
+    if n1:
+        for h in range(G_out):
+            babies |= {d % n1 for d in conv_diagonals(lay, Cin, Cout, h, depthwise, in_period)}
     steps = set()
     for u in range(lay.S):
         for v in range(lay.S):
             for a in offs[u]:
                 for b in offs[v]:
-                    if (a, b) != (0, 0):
-                        steps.add((a * lay.m + b) * lay.BS)
-    G_out = lay.groups if depthwise else -(-Cout // lay.cpc)
+                    for i in babies:
+                        if (a, b, i) != (0, 0, 0):
+                            steps.add((a * lay.m + b) * lay.BS + i * lay.blk)
     for h in range(G_out):
         for d in conv_diagonals(lay, Cin, Cout, h, depthwise, in_period):
-            if d:
+            if n1:
+                if d >= n1:
+                    steps.add((d // n1) * n1 * lay.blk)
+            elif d:
                 steps.add(d * lay.blk)
     return sorted(steps)
 
@@ -138,9 +155,14 @@ def conv_weight_slots(lay, W, h, up, vp, d, g, i, j, *, stride, depthwise, in_pe
 
 
 def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None, wmul=1.0,
-            w_scale=None, cnt=None):
+            w_scale=None, cnt=None, bsgs_n1=0):
     """Encrypted convolution of the fragment-packed input `cts` (list in (g, u, v)
-    order).  Returns (output ciphertexts in (h, u'', v'') order, output layout)."""
+    order).  Returns (output ciphertexts in (h, u'', v'') order, output layout).
+    bsgs_n1 > 0 selects the baby-step / giant-step schedule of the outer
+    rotations (he_conv_bsgs)."""
+    if bsgs_split(lay, bsgs_n1, depthwise, in_period):
+        return he_conv_bsgs(pr, keys, cts, lay, W, stride=stride, wmul=wmul, w_scale=w_scale, cnt=cnt,
+                            n1=bsgs_n1)
     cnt = cnt if cnt is not None else Counters()
     level = cts[0].level
     Cout = W.shape[0]
@@ -197,6 +219,92 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                         continue
                     if d:
                         acc = ckks.rotate(pr, keys, acc, d * lay.blk)
+                        cnt.rot += 1
+                        cnt.keyswitch += 1
+                        cnt.modup += 1
+                    total = _add(pr, total, acc)
+                res = ckks.rescale(pr, total)
+                cnt.rescale += 1
+                out[olay.ct_index(h, up // stride, vp // stride)] = res
+    return out, olay
+
+
+def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt=None, n1=4):
+    """Encrypted convolution with baby-step / giant-step outer rotations (the
+    schedule the paper assumes for the channel diagonals, Sec. 3.1).
+
+    Diagonal d = j n1 + i.  Rot(P_d, d blk) = Rot(Q, j n1 blk) with
+    Q = sum over taps of Rot(R_tap, i blk) (x) Rot(pt_d, i blk), because a slot-wise
+    product commutes with a rotation.  So:
+      1. every input ciphertext is rotated, from one hoisted ModUp, by
+         tap_step + i blk for every needed block offset and baby index i
+         (one key switch each, the inner and baby rotations together);
+      2. for each output and giant index j, Q_j = sum_{i, g, taps} of those
+         rotations times the plaintexts of diagonal j n1 + i rotated left by
+         i blk slots;
+      3. out = Q_0 + sum_{j > 0} Rot(Q_j, j n1 blk), before the one rescale."""
+    cnt = cnt if cnt is not None else Counters()
+    level = cts[0].level
+    Cout, Cin, K = W.shape[0], W.shape[1], W.shape[-1]
+    olay = out_layout_conv(lay, Cout, K, stride)
+    S, m, BS, blk, cpc = lay.S, lay.m, lay.BS, lay.blk, lay.cpc
+    n1 = min(n1, cpc)
+    n2 = -(-cpc // n1)
+    dw = float(pr.moduli[level]) if w_scale is None else w_scale
+    G_in, G_out = lay.groups, olay.groups
+    diags = {h: conv_diagonals(lay, Cin, Cout, h, False, None) for h in range(G_out)}
+    babies = sorted({0} | {d % n1 for h in diags for d in diags[h]})
+    offs = counts.inner_offsets(S, K, stride)
+
+    # 1. inner + baby rotations, hoisted per input ciphertext
+    R = {}
+    for g in range(G_in):
+        for u in range(S):
+            for v in range(S):
+                ct = cts[lay.ct_index(g, u, v)]
+                keys_needed = [(a, b, i) for a in offs[u] for b in offs[v] for i in babies]
+                ext = None
+                for (a, b, i) in keys_needed:
+                    if (a, b, i) == (0, 0, 0):
+                        R[(g, u, v, a, b, i)] = ct
+                        continue
+                    if ext is None:
+                        ext = ckks.mod_up(pr, ct.c1, ct.level)
+                        cnt.modup += 1
+                    R[(g, u, v, a, b, i)] = ckks.rotate_ext(pr, keys, ct, ext, (a * m + b) * BS + i * blk)
+                    cnt.rot += 1
+                    cnt.keyswitch += 1
+
+    # 2-4. MAC per giant step, giant rotations, rescale
+    out = [None] * olay.n_ct
+    for h in range(G_out):
+        dset = set(diags[h])
+        for up in range(0, S, stride):
+            for vp in range(0, S, stride):
+                total = None
+                for j in range(n2):
+                    acc = None
+                    for i in range(n1):
+                        d = j * n1 + i
+                        if d >= cpc or d not in dset:
+                            continue
+                        for g in range(G_in):
+                            for ti in range(K):
+                                u, a = (up + ti) % S, (up + ti) // S
+                                for tj in range(K):
+                                    v, b = (vp + tj) % S, (vp + tj) // S
+                                    z = conv_weight_slots(lay, W, h, up, vp, d, g, ti, tj, stride=stride,
+                                                          depthwise=False, in_period=None, wmul=wmul, Cout=Cout)
+                                    if not z.any():
+                                        continue
+                                    z = np.roll(z, -i * blk)  # Rot(z, i blk)[l] = z[l + i blk]
+                                    pt = ckks.encode(pr, z, level, dw)
+                                    acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b, i)], pt))
+                                    cnt.pmult += 1
+                    if acc is None:
+                        continue
+                    if j:
+                        acc = ckks.rotate(pr, keys, acc, j * n1 * blk)
                         cnt.rot += 1
                         cnt.keyswitch += 1
                         cnt.modup += 1

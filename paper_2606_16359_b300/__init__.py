@@ -47,7 +47,7 @@ class FeCounters(ctypes.Structure):
 class FePlanInfo(ctypes.Structure):
     _fields_ = [("pt_bytes", sz), ("in_bytes", sz), ("out_bytes", sz), ("workspace_bytes", sz),
                 ("workspace_min_bytes", sz), ("n_in_ct", u32), ("n_out_ct", u32), ("n_pt", u32),
-                ("n_inner_rot", u32), ("n_outer_rot", u32)]
+                ("n_inner_rot", u32), ("n_outer_rot", u32), ("bsgs_n1", u32)]
 
 
 P = ctypes.POINTER
@@ -132,7 +132,7 @@ SIGNATURES = {
     "fe_rescale_noalloc": (cint, [vp, vp, u32, u32, vp, vp]),
     "fe_pmult": (cint, [vp, vp, vp, u32, u32, vp, vp]),
     "fe_add": (cint, [vp, vp, vp, u32, u32, vp, vp]),
-    "fe_plan_conv": (cint, [vp, P(FeLayout), u32, u32, u32, cint, u32, u32, P(FeLayout), P(vp)]),
+    "fe_plan_conv": (cint, [vp, P(FeLayout), u32, u32, u32, cint, u32, u32, u32, P(FeLayout), P(vp)]),
     "fe_plan_fc": (cint, [vp, u32, u32, u32, P(i32), u32, u32, u32, P(vp)]),
     "fe_plan_destroy": (None, [vp]),
     "fe_plan_query": (cint, [vp, P(FePlanInfo)]),
@@ -374,12 +374,12 @@ class Context:
         return out
 
     # -- layers -------------------------------------------------------------------------
-    def plan_conv(self, lay, Cout, K, stride=1, depthwise=False, in_period=0, level=None):
+    def plan_conv(self, lay, Cout, K, stride=1, depthwise=False, in_period=0, level=None, bsgs_n1=0):
         level = self.L if level is None else level
         out_lay = FeLayout()
         h = vp()
         check(load().fe_plan_conv(self.handle, ctypes.byref(lay), Cout, K, stride, 1 if depthwise else 0,
-                                  in_period, level, ctypes.byref(out_lay), ctypes.byref(h)))
+                                  in_period, level, bsgs_n1, ctypes.byref(out_lay), ctypes.byref(h)))
         p = Plan(self, h, out_lay)
         p.level, p.in_layout = level, lay
         return p

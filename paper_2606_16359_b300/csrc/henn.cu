@@ -52,7 +52,9 @@ __global__ void k_conv_pt_slots(ConvPtArgs a, double* z, int slots) {
     if (l >= slots) return;
     const fe_plan::ConvPt p = a.pts[blockIdx.y];
     const int blk = a.m * a.m * a.BS;
-    const int c_loc = l / blk, rem = l % blk;
+    // a baby-step plaintext is the diagonal's slot vector rotated left by p.rot
+    const int ls = (l + p.rot) % slots;
+    const int c_loc = ls / blk, rem = ls % blk;
     const int kblk = rem / a.BS;
     const int bi = kblk / a.m, bj = kblk % a.m;
     double v = 0.0;
@@ -510,7 +512,7 @@ static void finish_plan(fe_plan* p) {
 }
 
 extern "C" int fe_plan_conv(fe_ctx* c, const fe_layout* in_lay, uint32_t Cout, uint32_t K, uint32_t stride,
-                            int depthwise, uint32_t in_period, uint32_t level, fe_layout* out_lay,
+                            int depthwise, uint32_t in_period, uint32_t level, uint32_t bsgs_n1, fe_layout* out_lay,
                             fe_plan** out) {
     if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
     if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "conv needs a level to rescale");
@@ -546,18 +548,44 @@ extern "C" int fe_plan_conv(fe_ctx* c, const fe_layout* in_lay, uint32_t Cout, u
     p->n_out = O.n_ct;
     const int S = L.S, m = L.m, BS = L.BS, cpc = L.cpc, blk = m * m * BS;
     const int G_in = in_period ? 1 : L.groups, G_out = O.groups;
+    // channel diagonals of every output group
+    std::vector<std::vector<int>> diag_of(G_out);
+    for (int h = 0; h < G_out; h++) {
+        if (depthwise) {
+            diag_of[h] = {0};
+        } else if (in_period) {
+            for (uint32_t d = 0; d < in_period; d++) diag_of[h].push_back(d);
+        } else {
+            std::set<int> ds;
+            for (uint32_t cc = 0; cc < L.C; cc++)
+                for (int ol = 0; ol < cpc; ol++)
+                    if (h * cpc + ol < (int)Cout) ds.insert((((int)(cc % cpc) - ol) % cpc + cpc) % cpc);
+            diag_of[h].assign(ds.begin(), ds.end());
+        }
+    }
+    // baby-step / giant-step split of the diagonals (0: linear outer rotations)
+    const int n1 = (bsgs_n1 && !depthwise && !in_period && cpc > 1) ? std::min<int>((int)bsgs_n1, cpc) : 0;
+    const int n2 = n1 ? (cpc + n1 - 1) / n1 : 0;
+    p->bsgs_n1 = n1;
+    std::set<int> babies{0};
+    if (n1)
+        for (auto& ds : diag_of)
+            for (int d : ds) babies.insert(d % n1);
     auto offs = inner_offsets(S, K, stride);
-    std::map<std::tuple<int, int, int>, int> rslot;  // (ci, a, b) -> R slot
+    // rotated copies of the inputs: block offset (a, b) of a tap plus baby step i,
+    // all from one hoisted ModUp per input ciphertext
+    std::map<std::tuple<int, int, int, int>, int> rslot;  // (ci, a, b, i) -> R slot
     for (int g = 0; g < G_in; g++)
         for (int u = 0; u < S; u++)
             for (int v = 0; v < S; v++) {
                 int ci = (g * S + u) * S + v;
                 for (int a : offs[u])
                     for (int bb : offs[v])
-                        if (a || bb) {
-                            rslot[std::make_tuple(ci, a, bb)] = (int)p->inner.size();
-                            p->inner.push_back({ci, (a * m + bb) * BS});
-                        }
+                        for (int i : babies)
+                            if (a || bb || i) {
+                                rslot[std::make_tuple(ci, a, bb, i)] = (int)p->inner.size();
+                                p->inner.push_back({ci, (a * m + bb) * BS + i * blk});
+                            }
             }
     auto spatial_ok = [&](int up, int extent) {
         for (int bi = 0; bi < m; bi++) {
@@ -567,52 +595,58 @@ extern "C" int fe_plan_conv(fe_ctx* c, const fe_layout* in_lay, uint32_t Cout, u
         }
         return false;
     };
+    // structurally nonzero: some channel pair of diagonal d in input group g
+    auto channels_meet = [&](int h, int d, int g) {
+        for (int cl = 0; cl < cpc; cl++) {
+            int cc = in_period ? cl % (int)in_period : g * cpc + cl;
+            if (!in_period && cc >= (int)L.C) continue;
+            int o = h * cpc + ((cl - d) % cpc + cpc) % cpc;
+            if (o >= (int)Cout) continue;
+            if (depthwise && o != cc) continue;
+            return true;
+        }
+        return false;
+    };
+    auto add_terms = [&](fe_plan::Group& grp, int h, int up, int vp, int d, int i_baby) {
+        for (int g = 0; g < G_in; g++) {
+            if (!channels_meet(h, d, g)) continue;
+            for (uint32_t ti = 0; ti < K; ti++)
+                for (uint32_t tj = 0; tj < K; tj++) {
+                    int u = (up + ti) % S, a = (up + ti) / S;
+                    int v = (vp + tj) % S, bb = (vp + tj) / S;
+                    int ci = (g * S + u) * S + v;
+                    int src = (a || bb || i_baby) ? rslot.at(std::make_tuple(ci, a, bb, i_baby)) : -(ci + 1);
+                    p->terms.push_back({src, p->n_pt});
+                    p->cpts.push_back({h, up, vp, d, g, (int)ti, (int)tj, i_baby * blk});
+                    p->n_pt++;
+                    grp.nt++;
+                }
+        }
+    };
     p->outs.resize(p->n_out);
     for (int h = 0; h < G_out; h++) {
-        std::vector<int> diags;
-        if (depthwise)
-            diags = {0};
-        else if (in_period)
-            for (uint32_t d = 0; d < in_period; d++) diags.push_back(d);
-        else {
-            std::set<int> ds;
-            for (uint32_t cc = 0; cc < L.C; cc++)
-                for (int ol = 0; ol < cpc; ol++)
-                    if (h * cpc + ol < (int)Cout) ds.insert((((int)(cc % cpc) - ol) % cpc + cpc) % cpc);
-            diags.assign(ds.begin(), ds.end());
-        }
+        const std::set<int> dset(diag_of[h].begin(), diag_of[h].end());
         for (int up = 0; up < S; up += stride)
             for (int vp = 0; vp < S; vp += stride) {
                 int oi = (h * O.S + up / stride) * O.S + vp / stride;
                 fe_plan::Out& ou = p->outs[oi];
-                bool sp = spatial_ok(up, L.H) && spatial_ok(vp, L.W);
-                for (int d : diags) {
-                    fe_plan::Group grp{d ? d * blk : 0, (int)p->terms.size(), 0};
-                    for (int g = 0; g < G_in; g++) {
-                        // structurally nonzero: some channel pair and some valid output position
-                        bool chan = false;
-                        for (int cl = 0; cl < cpc && !chan; cl++) {
-                            int cc = in_period ? cl % (int)in_period : g * cpc + cl;
-                            if (!in_period && cc >= (int)L.C) continue;
-                            int o = h * cpc + ((cl - d) % cpc + cpc) % cpc;
-                            if (o >= (int)Cout) continue;
-                            if (depthwise && o != cc) continue;
-                            chan = true;
-                        }
-                        if (!chan || !sp) continue;
-                        for (uint32_t i = 0; i < K; i++)
-                            for (uint32_t j = 0; j < K; j++) {
-                                int u = (up + i) % S, a = (up + i) / S;
-                                int v = (vp + j) % S, bb = (vp + j) / S;
-                                int ci = (g * S + u) * S + v;
-                                int src = (a || bb) ? rslot.at(std::make_tuple(ci, a, bb)) : -(ci + 1);
-                                p->terms.push_back({src, p->n_pt});
-                                p->cpts.push_back({h, up, vp, d, g, (int)i, (int)j});
-                                p->n_pt++;
-                                grp.nt++;
-                            }
+                if (!(spatial_ok(up, L.H) && spatial_ok(vp, L.W))) continue;
+                if (!n1) {
+                    for (int d : diag_of[h]) {
+                        fe_plan::Group grp{d ? d * blk : 0, (int)p->terms.size(), 0};
+                        add_terms(grp, h, up, vp, d, 0);
+                        if (grp.nt) ou.groups.push_back(grp);
                     }
-                    if (grp.nt) ou.groups.push_back(grp);
+                } else {
+                    // giant step j collects diagonals j n1 + i with plaintexts rotated by i blk
+                    for (int j = 0; j < n2; j++) {
+                        fe_plan::Group grp{j ? j * n1 * blk : 0, (int)p->terms.size(), 0};
+                        for (int i = 0; i < n1; i++) {
+                            const int d = j * n1 + i;
+                            if (d < cpc && dset.count(d)) add_terms(grp, h, up, vp, d, i);
+                        }
+                        if (grp.nt) ou.groups.push_back(grp);
+                    }
                 }
             }
     }
@@ -719,6 +753,7 @@ extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     info->n_pt = p->n_pt;
     info->n_inner_rot = (uint32_t)p->inner.size();
     info->n_outer_rot = p->n_outer;
+    info->bsgs_n1 = (uint32_t)p->bsgs_n1;
     return FE_OK;
 }
 

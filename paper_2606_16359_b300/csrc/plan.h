@@ -36,6 +36,7 @@ struct fe_plan {
     std::vector<Out> outs;
     struct ConvPt {
         int h, up, vp, d, g, i, j;
+        int rot;  // left rotation of the slot vector (baby step i: i m^2 BS)
     };
     std::vector<ConvPt> cpts;
     struct FcPt {
@@ -44,6 +45,7 @@ struct fe_plan {
     std::vector<FcPt> fpts;
     int n_pt = 0;
     int n_outer = 0;
+    int bsgs_n1 = 0;  // baby steps of the outer rotations, 0: linear
     std::vector<int32_t> steps;
 };
 

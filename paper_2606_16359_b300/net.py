@@ -22,7 +22,11 @@ def _torch():
 
 
 class MobileNetBlocks:
-    def __init__(self, ctx, blocks=None, seed=0, delta=2.0 ** 32, key_seed=101, enc_seed=202):
+    """schedule: "linear" (one outer rotation per channel diagonal, Eq. 4),
+    "tuned" (per pointwise layer, the fastest of linear and baby-step /
+    giant-step splits, timed by the autotuner), or an int n1 (baby steps)."""
+
+    def __init__(self, ctx, blocks=None, seed=0, delta=2.0 ** 32, key_seed=101, enc_seed=202, schedule="linear"):
         torch = _torch()
         self.ctx = ctx
         self.delta = delta
@@ -30,13 +34,27 @@ class MobileNetBlocks:
         L = ctx.L
         self.layers = []  # dicts: plan, pt, inp, out, level
         self.inputs, self.ref_inputs = [], []
+        self.schedule, self.tune_ms = [], []
+        tuner = None
+        if schedule == "tuned":
+            from .tune import Tuner
+            tuner = Tuner(ctx)
         plans = []
         for bi, (H, Cin, Cout) in enumerate(self.blocks):
             x, wd, wp = W.mobilenet_block(seed, H, Cin, Cout, BS=1, block=bi)
             lay = ctx.layout(H, H, Cin, 1, 1)
             pdw = ctx.plan_conv(lay, Cin, 3, depthwise=True, level=L)
-            ppw = ctx.plan_conv(pdw.out_layout, Cout, 1, level=L - 1)
+            if tuner is not None:
+                n1, times = tuner.conv_schedule(pdw.out_layout, Cout, 1, level=L - 1)
+                self.tune_ms.append({str(k): round(v, 3) for k, v in times.items()})
+            elif schedule == "linear":
+                n1 = 0
+            else:
+                n1 = int(schedule)
+            ppw = ctx.plan_conv(pdw.out_layout, Cout, 1, level=L - 1, bsgs_n1=n1)
+            self.schedule.append(ppw.info.bsgs_n1)
             plans.append((lay, pdw, ppw, x, wd, wp))
+        del tuner
         steps = sorted({s for _, a, b, *_ in plans for s in a.steps + b.steps})
         self.sk = ctx.sk_gen(key_seed)
         self.evk = ctx.evk_gen(self.sk, key_seed, steps)

@@ -6,8 +6,9 @@ module measures through the library, and proposes the fragment size S of a
 conv layer as the argmin of its predicted latency over the admissible sizes.
 The paper's analytic choice (Theorem: argmin of Eq. 5, fe_choose_fragment) is
 its fallback (no trained model, a ring degree it was not trained on) and its
-judge: a proposal whose Eq. 5 rotation count exceeds `veto` times the analytic
-choice's is replaced by the analytic choice.
+judge: the proposal stands only if the model predicts it at least `margin`
+faster than the analytic choice and its Eq. 5 rotation count is within `veto`
+times the analytic choice's; otherwise the analytic choice is taken.
 
 Measurement of one (layer, S): the full layer is planned on the host (exact
 rotation, plaintext and ciphertext counts); a slice of it is run on the GPU,
@@ -151,8 +152,15 @@ class Proposer:
     """Fragment-size proposals from the trained latency model, judged by the
     analytic choice."""
 
-    def __init__(self, mlp=None, trained_logN=(), veto=2.0):
-        self.mlp, self.trained_logN, self.veto = mlp, set(trained_logN), veto
+    def __init__(self, mlp=None, trained_logN=(), margin=0.05, veto=8.0):
+        self.mlp, self.trained_logN = mlp, set(trained_logN)
+        self.margin, self.veto = margin, veto
+
+    def predict(self, layer, counts_of):
+        """Predicted latency (ms) of every admissible S: {S: ms}."""
+        cands = candidates(layer)
+        X = np.array([features(layer, S, r, counts_of(S)) for S, r in cands], dtype=np.float32)
+        return {S: float(np.exp(v)) for (S, _), v in zip(cands, self.mlp.predict(X))}
 
     def propose(self, layer, counts_of):
         """counts_of(S) -> exact counts of the planned layer at S.
@@ -161,11 +169,11 @@ class Proposer:
         s_an = analytic_choice(layer, cands)
         if self.mlp is None or layer["logN"] not in self.trained_logN:
             return s_an, "fallback"
-        X = np.array([features(layer, S, r, counts_of(S)) for S, r in cands], dtype=np.float32)
-        pred = self.mlp.predict(X)
-        S_m, r_m = cands[int(np.argmin(pred))]
-        eq5_an = [r for S, r in cands if S == s_an][0]["eq5_total"]
-        if r_m["eq5_total"] > self.veto * max(eq5_an, 1.0):
+        pred = self.predict(layer, counts_of)
+        S_m = min(pred, key=pred.get)
+        eq5 = {S: r["eq5_total"] for S, r in cands}
+        if S_m != s_an and (pred[S_m] > (1.0 - self.margin) * pred[s_an] or
+                            eq5[S_m] > self.veto * max(eq5[s_an], 1.0)):
             return s_an, "judge"
         return S_m, "model"
 
@@ -214,15 +222,15 @@ def main(argv=None):
             cnt = {r["S"]: r["counts"] for r in lr_}
             best = min(ms, key=ms.get)
             s_an = analytic_choice(L)
-            X1 = np.array([r["x"] for r in lr_], dtype=np.float32)
-            s_model = lr_[int(np.argmin(mlp.predict(X1)))]["S"]
+            pred = prop.predict(L, lambda S: cnt[S])
+            s_model = min(pred, key=pred.get)
             s_j, src = prop.propose(L, lambda S: cnt[S])
             sources[src] += 1
             for k, s in (("model", s_model), ("analytic", s_an), ("judged", s_j)):
                 summary[k].append(ms[s] / ms[best] - 1.0)
                 hits[k] += s == best
             per_layer.append({"id": L["id"], "best": best, "model": s_model, "analytic": s_an, "judged": s_j,
-                              "ms": ms})
+                              "source": src, "ms": ms, "pred_ms": pred})
         n_test = len(per_layer)
         res = {"metric": "proposer vs analytic fragment-size choice on measured latency",
                "layers": len(layers), "train_samples": len(train), "test_layers": n_test,
@@ -235,7 +243,8 @@ def main(argv=None):
                "judged_sources": sources,
                "config": {"candidates_S": CANDIDATE_S, "mlp": "15 -> 64x3 ReLU -> 1, fp32, Adam",
                           "steps": args.steps, "seed": args.seed,
-                          "timing": "slice (1 in group, 1 out group, first output ct) extrapolated per stage"}}
+                          "timing": "slice (1 in group, 1 out group, first output ct) extrapolated per stage",
+                          "judge": {"margin": prop.margin, "veto_eq5_ratio": prop.veto}}}
         print(json.dumps(res), flush=True)
         os.makedirs(os.path.dirname(args.out), exist_ok=True)
         with open(args.out, "w") as f:

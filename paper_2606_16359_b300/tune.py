@@ -1,0 +1,85 @@
+"""Autotuner: picks, per conv layer, the outer-rotation schedule (linear, or
+baby-step / giant-step with n1 baby steps) by timing every candidate on the
+GPU, and caches the choice per layer shape.
+
+Candidates are timed through fe_he_layer_timing with plaintexts from a
+resident pool of random plaintexts and rotation keys aliased to a few
+generated ones (the kernels, launches and memory volume of the real layer,
+with a meaningless result), so no candidate needs its own keys or weight
+encoding.  The result of the chosen schedule is exact either way: every
+candidate computes the same convolution, and the residues of each schedule are
+fixed by its plan.
+
+    t = Tuner(ctx)
+    n1, times = t.conv_schedule(lay, Cout, K, level=ctx.L)
+"""
+import json
+import os
+
+_CACHE = {}
+
+
+def _key(ctx, lay, Cout, K, stride, depthwise, level):
+    return json.dumps([ctx.logN, ctx.L, level, lay.H, lay.W, lay.C, lay.BS, lay.S, lay.m, Cout, K, stride,
+                       int(depthwise)])
+
+
+class Tuner:
+    """Timing harness bound to one context: a small evk of generated keys that
+    keyless steps are aliased to, and a pool of random plaintexts."""
+
+    def __init__(self, ctx, n_keys=8, n_pts=32, cache_file=None):
+        import torch
+        self.ctx, self.torch = ctx, torch
+        sk = ctx.sk_gen(99)
+        self.evk = ctx.evk_gen(sk, 99, list(range(1, n_keys + 1)))
+        self.n_pool = n_pts
+        self.pts = torch.randint(0, 2 ** 35, (n_pts * (ctx.L + 1) * ctx.N,), dtype=torch.int64, device="cuda")
+        self.cache_file = cache_file
+        if cache_file and os.path.exists(cache_file):
+            with open(cache_file) as f:
+                _CACHE.update(json.load(f))
+
+    def time_plan(self, plan, reps=2):
+        """CUDA-event time (ms) of one call of the plan's layer, after a warm-up."""
+        torch, ctx = self.torch, self.ctx
+        i = plan.info
+        ctx.evk_alias(self.evk, plan.steps)
+        x = torch.randint(0, 2 ** 35, (i.n_in_ct, 2, plan.level + 1, ctx.N), dtype=torch.int64, device="cuda")
+        out = ctx.empty_ct(i.n_out_ct, plan.level - 1)
+        ws = ctx.workspace(i.workspace_bytes)
+        ctx.he_layer_timing(self.evk, plan, self.pts, self.n_pool, x, out, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.he_layer_timing(self.evk, plan, self.pts, self.n_pool, x, out, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def conv_schedule(self, lay, Cout, K, stride=1, depthwise=False, level=None, reps=2):
+        """Fastest outer-rotation schedule of a conv layer: returns (n1, {n1: ms}),
+        n1 = 0 for linear outer rotations."""
+        ctx = self.ctx
+        level = ctx.L if level is None else level
+        key = _key(ctx, lay, Cout, K, stride, depthwise, level)
+        if key in _CACHE:
+            c = _CACHE[key]
+            return c["n1"], {int(k): v for k, v in c["ms"].items()}
+        cands = [0]
+        if not depthwise and lay.cpc > 1:
+            n1 = 2
+            while n1 <= lay.cpc:
+                cands.append(n1)
+                n1 *= 2
+        times = {}
+        for n1 in cands:
+            plan = ctx.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=level, bsgs_n1=n1)
+            times[n1] = self.time_plan(plan, reps)
+            del plan
+        best = min(times, key=times.get)
+        _CACHE[key] = {"n1": best, "ms": times}
+        if self.cache_file:
+            with open(self.cache_file, "w") as f:
+                json.dump(_CACHE, f)
+        return best, times

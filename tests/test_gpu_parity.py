@@ -141,22 +141,23 @@ def test_rotate_rescale_pmult_add_parity(which, tiny, ks2):
     assert np.array_equal(u64(ad), oracle_ct_array([ckks.add(pr, c, c) for c in octs]))
 
 
-def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1)):
+def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1), bsgs_n1=0):
     pr, g = P.pr, P.g
     BS, C, H, _ = x.shape
     Cout = w.shape[0]
     K = w.shape[-1]
     olay = fragment.Layout(pr.N, H, H, C, BS, S)
-    steps = henn.conv_rotation_steps(olay, C, Cout, K, stride, depthwise)
+    steps = henn.conv_rotation_steps(olay, C, Cout, K, stride, depthwise, bsgs_n1=bsgs_n1)
     keys = ckks.KeySet(pr, seed, rot_steps=steps)
     slots = fragment.pack(olay, x)
     octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, delta), 17, i) for i in range(olay.n_ct)]
     ocnt = henn.Counters()
-    oout, oolay = henn.he_conv(pr, keys, octs, olay, w, stride=stride, depthwise=depthwise, cnt=ocnt)
+    oout, oolay = henn.he_conv(pr, keys, octs, olay, w, stride=stride, depthwise=depthwise, cnt=ocnt,
+                               bsgs_n1=bsgs_n1)
     want = oracle_ct_array(oout)
 
     lay = g.layout(H, H, C, BS, S)
-    plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L)
+    plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L, bsgs_n1=bsgs_n1)
     assert sorted(plan.steps) == sorted(steps)
     assert plan.info.n_inner_rot + plan.info.n_outer_rot == ocnt.rot
     assert plan.info.n_pt == ocnt.pmult
@@ -326,3 +327,20 @@ def test_layer_batch_each_request_equals_alone(tiny, H, C, Co, K, BS, S):
     ws = g.workspace(g.workspace_bytes(plan, 3, minimum=True))
     out = u64(g.he_layer_batch(evk, plan, pt, batch_in, 3, ws=ws))
     assert np.array_equal(out, np.concatenate(alone))
+
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1", [
+    (6, 20, 18, 3, 1, 1, 1, 4),
+    (4, 12, 10, 1, 2, 1, 1, 2),
+    (8, 6, 9, 3, 1, 2, 2, 4),
+    (6, 8, 8, 1, 1, 1, 1, 3),
+])
+def test_conv_parity_bsgs(tiny, H, C, Co, K, BS, S, stride, n1):
+    """Baby-step / giant-step outer rotations: residues bit-exact to the oracle's
+    schedule in both paths, decrypted within 1e-3 of FP64."""
+    rng = np.random.default_rng(H * 10 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, (Co, C, K, K))
+    plan, _ = run_conv_pair(tiny, x, w, S, stride, bsgs_n1=n1)
+    assert plan.info.bsgs_n1 == min(n1, plan.in_layout.cpc)

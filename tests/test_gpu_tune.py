@@ -1,0 +1,36 @@
+"""The schedule autotuner: every candidate is timed, the fastest is chosen and
+cached, and a network built with the tuned schedules decrypts to the FP64
+result (each schedule's residues are pinned by the BSGS parity tests)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_16359_b300 as fe  # noqa: E402
+from paper_2606_16359_b300.net import MobileNetBlocks  # noqa: E402
+from paper_2606_16359_b300.tune import Tuner  # noqa: E402
+
+
+def test_tuner_times_all_candidates_and_tuned_blocks_decrypt():
+    p = W.PARAMS["mobilenet_small"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        t = Tuner(ctx, n_keys=4, n_pts=8)
+        lay = ctx.layout(8, 8, 64, 1, 1)  # cpc = 32 at N = 2^12
+        n1, times = t.conv_schedule(lay, 64, 1, level=ctx.L - 1)
+        assert set(times) == {0, 2, 4, 8, 16, 32} and n1 in times
+        assert times[n1] == min(times.values()) and all(v > 0 for v in times.values())
+        assert t.conv_schedule(lay, 64, 1, level=ctx.L - 1)[1] == times  # cached
+        net = MobileNetBlocks(ctx, blocks=[(8, 64, 64), (6, 32, 48)], delta=p["delta"], schedule="tuned")
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(2)]
+    assert max(errs) < 1e-3, errs
+    assert len(net.schedule) == 2 and len(net.tune_ms) == 2

@@ -152,3 +152,38 @@ def test_conv1_config_end_to_end():
     y = decrypt_layout(pr, keys, olay, out)
     assert np.abs(y - plain.conv2d(x, w)).max() < 1e-3
     assert out[0].scale == p["delta"] and out[0].level == pr.L - 1
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1", [
+    (6, 20, 18, 3, 1, 1, 1, 4),    # cpc = 8: 2 giant steps of 4 diagonals
+    (4, 12, 10, 1, 2, 1, 1, 2),    # pointwise, cpc = 16, n1 = 2
+    (8, 6, 9, 3, 1, 2, 2, 4),      # stride 2, cpc = 32
+    (6, 8, 8, 1, 1, 1, 1, 3),      # n1 not dividing cpc (last giant step partial)
+])
+def test_he_conv_bsgs_matches_fp64_and_linear(tiny, H, C, Co, K, BS, S, stride, n1):
+    """Baby-step / giant-step outer rotations: the same convolution (decrypted
+    within 1e-3 of FP64 and of the linear schedule), fewer key switches when
+    there are many diagonals, and the rotation-step list covers every rotation."""
+    pr, delta = tiny
+    rng = np.random.default_rng(H * 10 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, (Co, C, K, K))
+    lay = fragment.Layout(pr.N, H, H, C, BS, S)
+    steps = henn.conv_rotation_steps(lay, C, Co, K, stride, bsgs_n1=n1)
+    keys = ckks.KeySet(pr, 3, rot_steps=steps)
+    cts = encrypt_layout(pr, keys, lay, x, pr.L, delta)
+    cnt = henn.Counters()
+    out, olay = henn.he_conv(pr, keys, cts, lay, w, stride=stride, cnt=cnt, bsgs_n1=n1)
+    y = decrypt_layout(pr, keys, olay, out)
+    assert np.abs(y - plain.conv2d(x, w, stride=stride)).max() < 1e-3
+    # key switches: (|offsets x babies| - 1) per input ciphertext + (giant steps - 1) per output
+    n1e = min(n1, lay.cpc)
+    offs = counts.inner_offsets(S, K, stride)
+    G_out = -(-Co // lay.cpc)
+    diag = {h: henn.conv_diagonals(lay, C, Co, h, False, None) for h in range(G_out)}
+    babies = {0} | {d % n1e for h in diag for d in diag[h]}
+    inner = sum(len(offs[u]) * len(offs[v]) * len(babies) - 1 for u in range(S) for v in range(S)) * lay.groups
+    giants = sum((len({d // n1e for d in diag[h]}) - 1) * (S // stride) ** 2 for h in range(G_out))
+    assert cnt.rot == inner + giants
+    assert cnt.modup == lay.groups * S * S + giants
+    assert set(steps) >= {((a * lay.m + b) * lay.BS + i * lay.blk) for a in [0] for b in [0] for i in babies if i}
