@@ -1,14 +1,17 @@
-"""Learned fragment-size proposer.
+"""Learned fragment-size and schedule proposer.
 
 A small latency model (fe_mlp_*: 3 hidden layers of 64 ReLU units, fp32, CUDA
 training and inference kernels) is trained on per-layer latencies that this
-module measures through the library, and proposes the fragment size S of a
-conv layer as the argmin of its predicted latency over the admissible sizes.
+module measures through the library, and proposes for a conv layer the
+fragment size S and the outer-rotation schedule (linear, or baby-step /
+giant-step with n1 = 2^ceil(log2(cpc) / 2) baby steps) as the argmin of its
+predicted latency over the admissible choices.
 The paper's analytic choice (Theorem: argmin of Eq. 5, fe_choose_fragment) is
-its fallback (no trained model, a ring degree it was not trained on) and its
-judge: the proposal stands only if the model predicts it at least `margin`
-faster than the analytic choice and its Eq. 5 rotation count is within `veto`
-times the analytic choice's; otherwise the analytic choice is taken.
+(with the paper's linear outer rotations) is its fallback (no trained model, a
+ring degree it was not trained on) and its judge: the proposal stands only if
+the model predicts it at least `margin` faster than the analytic choice and
+its Eq. 5 rotation count is within `veto` times the analytic choice's;
+otherwise the analytic choice is taken.
 
 Measurement of one (layer, S): the full layer is planned on the host (exact
 rotation, plaintext and ciphertext counts); a slice of it is run on the GPU,
@@ -36,7 +39,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CANDIDATE_S = (1, 2, 4, 8)
 PARAM_SET = {14: "lenet", 16: "mobilenet"}
-N_FEATURES = 15
+N_FEATURES = 16
 
 
 def _fe():
@@ -74,14 +77,28 @@ def analytic_choice(layer, cands=None):
     return min(cands, key=lambda c: (c[1]["eq5_total"], c[0]))[0]
 
 
-def features(layer, S, model, counts):
-    """Feature vector of (layer, S): shape, ring, fragment geometry and the
-    exact counts of the planned layer."""
+def schedules(model):
+    """Outer-rotation schedules tried at one fragment size: linear (0), and
+    baby-step / giant-step with n1 = 2^ceil(log2(cpc) / 2) when cpc >= 4."""
+    cpc = model["cpc"]
+    if cpc < 4:
+        return [0]
+    return [0, 1 << ((cpc.bit_length() - 1 + 1) // 2)]
+
+
+def choices(layer):
+    """All (S, n1, rotation model) the proposer chooses among."""
+    return [(S, n1, r) for S, r in candidates(layer) for n1 in schedules(r)]
+
+
+def features(layer, S, model, counts, n1=0):
+    """Feature vector of (layer, S, schedule): shape, ring, fragment geometry,
+    baby steps and the exact counts of the planned layer."""
     lg = lambda x: math.log2(1.0 + x)  # noqa: E731
     return [layer["logN"], math.log2(layer["H"]), math.log2(layer["Cin"]), math.log2(layer["Cout"]), layer["K"],
             layer["stride"], math.log2(S), math.log2(model["cpc"]), lg(counts["n_in_ct"]), lg(counts["n_out_ct"]),
             lg(counts["n_inner"]), lg(counts["n_outer"]), lg(counts["n_pt"]), lg(model["eq5_total"]),
-            counts["level"] + 1]
+            counts["level"] + 1, lg(n1)]
 
 
 class Measurer:
@@ -102,9 +119,9 @@ class Measurer:
         self.n_pool = n_pts
         self.pts = torch.randint(0, 2 ** 35, (n_pts * nl * self.ctx.N,), dtype=torch.int64, device="cuda")
 
-    def plan(self, layer, S, Cin, Cout):
+    def plan(self, layer, S, Cin, Cout, n1=0):
         lay = self.ctx.layout(layer["H"], layer["W"], Cin, 1, S)
-        return self.ctx.plan_conv(lay, Cout, layer["K"], stride=layer["stride"], level=self.level)
+        return self.ctx.plan_conv(lay, Cout, layer["K"], stride=layer["stride"], level=self.level, bsgs_n1=n1)
 
     def counts(self, plan):
         i = plan.info
@@ -129,12 +146,13 @@ class Measurer:
         del x, out, ws
         return t
 
-    def measure(self, layer, S, model):
-        """Estimated latency (ms) of the full layer at fragment size S."""
-        full = self.plan(layer, S, layer["Cin"], layer["Cout"])
+    def measure(self, layer, S, model, n1=0):
+        """Estimated latency (ms) of the full layer at fragment size S with n1
+        baby steps (0: linear outer rotations)."""
+        full = self.plan(layer, S, layer["Cin"], layer["Cout"], n1)
         cf = self.counts(full)
         cpc = model["cpc"]
-        sl = self.plan(layer, S, min(layer["Cin"], cpc), min(layer["Cout"], cpc))
+        sl = self.plan(layer, S, min(layer["Cin"], cpc), min(layer["Cout"], cpc), n1)
         self.ctx.plan_truncate(sl, 1)
         cs = self.counts(sl)
         t = self.time_slice(sl)
@@ -157,25 +175,24 @@ class Proposer:
         self.margin, self.veto = margin, veto
 
     def predict(self, layer, counts_of):
-        """Predicted latency (ms) of every admissible S: {S: ms}."""
-        cands = candidates(layer)
-        X = np.array([features(layer, S, r, counts_of(S)) for S, r in cands], dtype=np.float32)
-        return {S: float(np.exp(v)) for (S, _), v in zip(cands, self.mlp.predict(X))}
+        """Predicted latency (ms) of every choice: {(S, n1): ms}; counts_of(S, n1)
+        gives the exact counts of the planned layer."""
+        ch = choices(layer)
+        X = np.array([features(layer, S, r, counts_of(S, n1), n1) for S, n1, r in ch], dtype=np.float32)
+        return {(S, n1): float(np.exp(v)) for (S, n1, _), v in zip(ch, self.mlp.predict(X))}
 
     def propose(self, layer, counts_of):
-        """counts_of(S) -> exact counts of the planned layer at S.
-        Returns (S, source) with source 'model', 'fallback' or 'judge'."""
-        cands = candidates(layer)
-        s_an = analytic_choice(layer, cands)
+        """Returns ((S, n1), source), source 'model', 'fallback' or 'judge'."""
+        s_an = (analytic_choice(layer), 0)
         if self.mlp is None or layer["logN"] not in self.trained_logN:
             return s_an, "fallback"
         pred = self.predict(layer, counts_of)
-        S_m = min(pred, key=pred.get)
-        eq5 = {S: r["eq5_total"] for S, r in cands}
-        if S_m != s_an and (pred[S_m] > (1.0 - self.margin) * pred[s_an] or
-                            eq5[S_m] > self.veto * max(eq5[s_an], 1.0)):
+        c_m = min(pred, key=pred.get)
+        eq5 = {S: r["eq5_total"] for S, r in candidates(layer)}
+        if c_m != s_an and (pred[c_m] > (1.0 - self.margin) * pred[s_an] or
+                            eq5[c_m[0]] > self.veto * max(eq5[s_an[0]], 1.0)):
             return s_an, "judge"
-        return S_m, "model"
+        return c_m, "model"
 
 
 def main(argv=None):
@@ -199,10 +216,10 @@ def main(argv=None):
             if L["logN"] not in meas:
                 meas[L["logN"]] = Measurer(L["logN"])
             m = meas[L["logN"]]
-            for S, model in candidates(L):
-                est, cf, cs, t = m.measure(L, S, model)
-                rows.append({"layer": L, "S": S, "ms": est, "counts": cf, "slice": cs, "stage_ms": t,
-                             "eq5": model["eq5_total"], "x": features(L, S, model, cf)})
+            for S, n1, model in choices(L):
+                est, cf, cs, t = m.measure(L, S, model, n1)
+                rows.append({"layer": L, "S": S, "n1": n1, "ms": est, "counts": cf, "slice": cs, "stage_ms": t,
+                             "eq5": model["eq5_total"], "x": features(L, S, model, cf, n1)})
         t_meas = time.perf_counter() - t0
         train = [r for r in rows if r["layer"]["split"] == "train"]
         X = np.array([r["x"] for r in train], dtype=np.float32)
@@ -218,19 +235,21 @@ def main(argv=None):
             if L["split"] != "test":
                 continue
             lr_ = [r for r in rows if r["layer"]["id"] == L["id"]]
-            ms = {r["S"]: r["ms"] for r in lr_}
-            cnt = {r["S"]: r["counts"] for r in lr_}
+            ms = {(r["S"], r["n1"]): r["ms"] for r in lr_}
+            cnt = {(r["S"], r["n1"]): r["counts"] for r in lr_}
             best = min(ms, key=ms.get)
-            s_an = analytic_choice(L)
-            pred = prop.predict(L, lambda S: cnt[S])
+            s_an = (analytic_choice(L), 0)
+            pred = prop.predict(L, lambda S, n1: cnt[(S, n1)])
             s_model = min(pred, key=pred.get)
-            s_j, src = prop.propose(L, lambda S: cnt[S])
+            s_j, src = prop.propose(L, lambda S, n1: cnt[(S, n1)])
             sources[src] += 1
             for k, s in (("model", s_model), ("analytic", s_an), ("judged", s_j)):
                 summary[k].append(ms[s] / ms[best] - 1.0)
                 hits[k] += s == best
-            per_layer.append({"id": L["id"], "best": best, "model": s_model, "analytic": s_an, "judged": s_j,
-                              "source": src, "ms": ms, "pred_ms": pred})
+            key = lambda c: f"{c[0]}/{c[1]}"  # noqa: E731
+            per_layer.append({"id": L["id"], "best": key(best), "model": key(s_model), "analytic": key(s_an),
+                              "judged": key(s_j), "source": src, "ms": {key(c): v for c, v in ms.items()},
+                              "pred_ms": {key(c): v for c, v in pred.items()}})
         n_test = len(per_layer)
         res = {"metric": "proposer vs analytic fragment-size choice on measured latency",
                "layers": len(layers), "train_samples": len(train), "test_layers": n_test,
@@ -241,7 +260,8 @@ def main(argv=None):
                "total_ms_vs_best": {k: float(sum(p["ms"][p[k]] for p in per_layer) /
                                               sum(p["ms"][p["best"]] for p in per_layer)) for k in hits},
                "judged_sources": sources,
-               "config": {"candidates_S": CANDIDATE_S, "mlp": "15 -> 64x3 ReLU -> 1, fp32, Adam",
+               "config": {"candidates_S": CANDIDATE_S, "schedules": "linear, BSGS n1 = 2^ceil(log2(cpc)/2)",
+                          "mlp": "16 -> 64x3 ReLU -> 1, fp32, Adam",
                           "steps": args.steps, "seed": args.seed,
                           "timing": "slice (1 in group, 1 out group, first output ct) extrapolated per stage",
                           "judge": {"margin": prop.margin, "veto_eq5_ratio": prop.veto}}}

@@ -43,8 +43,11 @@ def test_features_and_fallback():
     L = W.synthetic_layers(0, 1)[0]
     S, r = proposer.candidates(L)[0]
     c = {"n_in_ct": 4, "n_out_ct": 4, "n_inner": 12, "n_outer": 28, "n_pt": 100, "level": 23}
-    x = proposer.features(L, S, r, c)
+    x = proposer.features(L, S, r, c, 4)
     assert len(x) == proposer.N_FEATURES and all(v == v for v in x)
     # no trained model: the analytic choice, marked as the fallback
     P = proposer.Proposer(None)
-    assert P.propose(L, lambda s: c) == (proposer.analytic_choice(L), "fallback")
+    assert P.propose(L, lambda s, n1: c) == ((proposer.analytic_choice(L), 0), "fallback")
+    # schedules: linear always, BSGS with n1 = 2^ceil(log2(cpc)/2) when cpc >= 4
+    for S, n1, r in proposer.choices(L):
+        assert n1 == 0 or (r["cpc"] >= 4 and n1 * n1 >= r["cpc"] and n1 * n1 < 4 * r["cpc"])
