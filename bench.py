@@ -258,6 +258,8 @@ def run_ours(args, dist, rank, world, local):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    if ctx.device_status():
+        raise RuntimeError("a bounded device wait expired during the timed steps")
     ms = reduce_max(dist, ms)
     barrier(dist)
     ms_step = ms / args.steps

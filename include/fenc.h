@@ -349,6 +349,10 @@ int fe_he_layer_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const
 int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_pool_dev,
                        uint32_t n_pool, const void* in_dev, void* out_dev, void* ws, size_t ws_bytes,
                        void* stream);
+/* Tile choice of the batched MAC: how many outputs whose terms read the same
+ * ciphertexts share one kernel item (1, 2 or 4; default 4).  Results do not
+ * depend on it; the autotuner picks the fastest.  Errors: FE_EINVAL. */
+int fe_plan_set_mac_ways(fe_plan* plan, uint32_t ways);
 /* Keep only the first max_out_ct output ciphertexts of a plan (with the terms,
  * plaintexts and inner rotations they use); their results are unchanged.  Used
  * to time a slice of a large layer.  Errors: FE_EINVAL. */
@@ -495,6 +499,14 @@ int fe_server_wait(fe_server* s, uint64_t req_id, uint32_t timeout_ms, int* stat
 int fe_server_stats(fe_server* s, fe_server_stats_t* out);
 /* Stop the scheduler, wait for the groups in flight, release the streams. */
 void fe_server_destroy(fe_server* s);
+
+/* ---- device status ------------------------------------------------------------ */
+
+/* Synchronise the device and read the context's device status word: bit 0 is
+ * set when a kernel's bounded wait on its own asynchronous copies expired (the
+ * kernel then skipped its work, so the results of that call are invalid and
+ * the caller should treat it as FE_ETIMEOUT).  reset = 1 clears the word. */
+int fe_device_status(fe_ctx* ctx, uint32_t* status, int reset);
 
 /* ---- kernel timing ---------------------------------------------------------- */
 

@@ -99,6 +99,8 @@ SIGNATURES = {
     "fe_evk_alias": (cint, [vp, vp, P(i32), u32, P(u32)]),
     "fe_he_layer_timing": (cint, [vp, vp, vp, vp, u32, vp, vp, vp, sz, vp]),
     "fe_plan_truncate": (cint, [vp, u32]),
+    "fe_device_status": (cint, [vp, P(u32), cint]),
+    "fe_plan_set_mac_ways": (cint, [vp, u32]),
     "fe_server_create": (cint, [P(FeServerConfig), P(vp)]),
     "fe_server_add_model": (cint, [vp, vp, vp, P(FeOp), u32, u32, u32, P(u32)]),
     "fe_server_model_io": (cint, [vp, u32, P(u32), P(u32), P(sz), P(sz)]),
@@ -420,6 +422,17 @@ class Context:
         n = u32(0)
         check(load().fe_evk_alias(self.handle, evk.handle, arr, len(steps), ctypes.byref(n)))
         return n.value
+
+    def device_status(self, reset=False):
+        """Synchronise and read the device status word (0: no bounded wait expired)."""
+        v = u32(0)
+        check(load().fe_device_status(self.handle, ctypes.byref(v), 1 if reset else 0))
+        return v.value
+
+    def plan_set_mac_ways(self, plan, ways):
+        check(load().fe_plan_set_mac_ways(plan.handle, ways))
+        plan.mac_ways = ways
+        return plan
 
     def plan_truncate(self, plan, max_out_ct):
         check(load().fe_plan_truncate(plan.handle, max_out_ct))

@@ -76,6 +76,7 @@ struct fe_ctx {
     u64 *d_qlinv, *d_qlinv_sh;      // [L+1][L+1]: q_l^-1 mod q_i at [l][i]
     double* d_dd_w;                 // [N][4]: exp(-2 pi i j / 2N) as (re_hi, re_lo, im_hi, im_lo)
     int* d_identity_map;            // [n_mod] j -> j
+    uint32_t* d_status;             // bit 0: a bounded device wait gave up (kernels skip their work)
     int* d_t2slot;                  // [N]   slot whose root is zeta^(2t+1) or its conjugate
     int* d_slot2t;                  // [N/2] (5^l mod 2N - 1) / 2
     u64 q0inv_q1;                   // q_0^-1 mod q_1 (CRT of two limbs at decryption)

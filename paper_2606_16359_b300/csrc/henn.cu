@@ -225,9 +225,20 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     struct OuterRef {
         int r, o, gi;
     };
+    // within one step: request-major, so that consecutive groups of one request
+    // (same step, other outputs) can share their ciphertext loads in the MAC
     std::vector<OuterRef> order;
-    for (const auto& og : outer_order(p))
-        for (size_t r = 0; r < R; r++) order.push_back({(int)r, og.first, og.second});
+    {
+        const auto oo = outer_order(p);
+        for (size_t a = 0; a < oo.size();) {
+            const int32_t st0 = p->outs[oo[a].first].groups[oo[a].second].step;
+            size_t b = a;
+            while (b < oo.size() && p->outs[oo[b].first].groups[oo[b].second].step == st0) b++;
+            for (size_t r = 0; r < R; r++)
+                for (size_t k = a; k < b; k++) order.push_back({(int)r, oo[k].first, oo[k].second});
+            a = b;
+        }
+    }
     const size_t n_chunks = order.empty() ? 0 : (order.size() + chunk - 1) / chunk;
     KsItem* d_in_ks = cv.take<KsItem>(std::max<size_t>(1, R * n_in_rot));
     KsGroup* d_in_kg = cv.take<KsGroup>(std::max<size_t>(1, R * n_in_rot));
@@ -293,29 +304,70 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     for (size_t r = 0; r < R; r++)
         for (const auto& t : p->terms)
             mterms.push_back(MacTerm{src_ptr(r, t.src), b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * z.nlN});
-    std::vector<MacItem> macs;
+    struct OneMac {
+        u64* out;
+        int term0, n_terms;
+    };
+    std::vector<OneMac> macs;
     std::vector<size_t> no_base;  // request-major output index
     for (size_t r = 0; r < R; r++)
         for (int o = 0; o < p->n_out; o++) {
             bool base = false;
             for (const auto& g : p->outs[o].groups)
                 if (g.step == 0) {
-                    macs.push_back(MacItem{total + (r * p->n_out + o) * z.ctw, (int)(r * n_terms) + g.t0, g.nt});
+                    macs.push_back(OneMac{total + (r * p->n_out + o) * z.ctw, (int)(r * n_terms) + g.t0, g.nt});
                     base = true;
                 }
             if (!base) no_base.push_back(r * p->n_out + o);
         }
     const size_t n_base = macs.size();
-    int base_terms = 0;
-    for (size_t i = 0; i < n_base; i++) base_terms += macs[i].n_terms;
-    std::vector<int> chunk_terms;
     auto group_of = [&](const OuterRef& x) -> const fe_plan::Group& { return p->outs[x.o].groups[x.gi]; };
     for (size_t k = 0; k < order.size(); k++) {
-        if (k % chunk == 0) chunk_terms.push_back(0);
         const auto& g = group_of(order[k]);
-        chunk_terms.back() += g.nt;
-        macs.push_back(MacItem{Pd + (k % chunk) * z.ctw, (int)(order[k].r * n_terms) + g.t0, g.nt});
+        macs.push_back(OneMac{Pd + (k % chunk) * z.ctw, (int)(order[k].r * n_terms) + g.t0, g.nt});
     }
+    // device MAC items: consecutive outputs whose terms read the same ciphertexts
+    // in the same order share one item (up to kMacWays), so each ciphertext word
+    // is loaded once for all of them
+    struct MacRange {
+        int first, count, ct_terms, pt_terms, outputs, ways;
+    };
+    const int ways = std::max(1, std::min(kMacWays, p->mac_ways));
+    std::vector<MacItem> dmacs;
+    auto same_sources = [&](const OneMac& a, const OneMac& b) {
+        if (a.n_terms != b.n_terms) return false;
+        for (int t = 0; t < a.n_terms; t++)
+            if (mterms[a.term0 + t].ct != mterms[b.term0 + t].ct) return false;
+        return true;
+    };
+    auto merge = [&](size_t b, size_t e) {
+        MacRange rg{(int)dmacs.size(), 0, 0, 0, 0, 1};
+        for (size_t i = b; i < e;) {
+            MacItem it{};
+            it.n_terms = macs[i].n_terms;
+            it.n_out = 0;
+            size_t j = i;
+            while (j < e && it.n_out < ways && (j == i || same_sources(macs[i], macs[j]))) {
+                it.out[it.n_out] = macs[j].out;
+                it.term0[it.n_out] = macs[j].term0;
+                it.n_out++;
+                j++;
+            }
+            dmacs.push_back(it);
+            rg.count++;
+            rg.ct_terms += it.n_terms;
+            rg.pt_terms += it.n_terms * it.n_out;
+            rg.outputs += it.n_out;
+            rg.ways = std::max(rg.ways, it.n_out);
+            i = j;
+        }
+        return rg;
+    };
+    const MacRange base_rg = merge(0, n_base);
+    std::vector<MacRange> chunk_rg;
+    for (size_t c0 = 0; c0 < order.size(); c0 += chunk)
+        chunk_rg.push_back(merge(n_base + c0, n_base + std::min(order.size(), c0 + chunk)));
+
     std::vector<KsItem> oks(order.size());
     std::vector<KsGroup> okg;
     std::vector<SumEntry> ents;
@@ -357,7 +409,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         FE_TRY(upload(ikg, d_in_kg, st));
         FE_TRY(upload(icb, d_in_cb, st));
         FE_TRY(upload(mterms, d_terms, st));
-        FE_TRY(upload(macs, d_mac, st));
+        FE_TRY(upload(dmacs, d_mac, st));
         FE_TRY(upload(oks, d_out_ks, st));
         FE_TRY(upload(okg, d_out_kg, st));
         FE_TRY(upload(ents, d_ent, st));
@@ -405,7 +457,8 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                 launch_pmult(c, tm.ct, tm.pt, macs[i].out, 1, lv, t > 0, st);
             }
     } else {
-        launch_mac(c, d_mac, d_terms, (int)n_base, base_terms, lv, st);
+        launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
+                   base_rg.outputs, base_rg.ways, lv, st);
     }
     }
 
@@ -417,7 +470,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         int cn = (int)(c1 - c0);
         if (mode == 0) {
             for (size_t k = c0; k < c1; k++) {
-                const MacItem& m = macs[n_base + k];
+                const OneMac& m = macs[n_base + k];
                 for (int t = 0; t < m.n_terms; t++) {
                     const MacTerm& tm = mterms[m.term0 + t];
                     launch_pmult(c, tm.ct, tm.pt, m.out, 1, lv, t > 0, st);
@@ -430,7 +483,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             for (int si = 0; si < sum_range[ch].second; si++)
                 launch_combine_sum(c, d_sum + sum_range[ch].first + si, d_ent, 1, sums[sum_range[ch].first + si].n_e, lv, st);
         } else {
-            launch_mac(c, d_mac + n_base + c0, d_terms, cn, chunk_terms[ch], lv, st);
+            const MacRange& rg = chunk_rg[ch];
+            launch_mac(c, d_mac + rg.first, d_terms, rg.count, rg.ct_terms, rg.pt_terms, rg.outputs, rg.ways, lv,
+                       st);
             modup(c, Pd + z.nlN, z.ctw, cn, lv, coef3, ext3, st);
             launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, cn, lv, st);
             moddown_to_coef(c, acc3, cn, lv, conv3, st);
@@ -878,5 +933,12 @@ extern "C" int fe_plan_truncate(fe_plan* p, uint32_t max_out_ct) {
         }
     p->inner = inner;
     finish_plan(p);
+    return FE_OK;
+}
+
+extern "C" int fe_plan_set_mac_ways(fe_plan* p, uint32_t ways) {
+    if (!p) return fail(FE_EINVAL, "null argument");
+    if (ways != 1 && ways != 2 && ways != 4) return fail(FE_EINVAL, "mac ways must be 1, 2 or 4");
+    p->mac_ways = (int)ways;
     return FE_OK;
 }

@@ -3,6 +3,8 @@
 // All kernels stream limb-major data with one thread per coefficient and
 // coalesced 8-byte accesses; products of two residues are accumulated in
 // 128 bits and reduced once (Barrett, 2^128 / q) per output word.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace fe {
@@ -207,28 +209,155 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 // blockIdx.y = limb i, z = item.  Partial sums stay in 128 bits and are
 // reduced every 16 terms (products of < 2^61 residues are < 2^122).
 // ------------------------------------------------------------------------
-__global__ void k_mac(const MacItem* items, const MacTerm* terms, const Modulus* mods, int level,
-                      int logN) {
+// PMult-MAC with the operand tiles streamed through shared memory by the bulk
+// async-copy engine.  One CTA = one item (up to W outputs sharing their
+// ciphertext terms), one limb, a tile of T coefficients (T = min(512, N),
+// T / 2 threads, two coefficients each).  For term t the CTA needs the tile of
+// c0 and c1 of the term's ciphertext and the tile of each output's plaintext,
+// (2 + n_out) T 8 bytes, copied with cp.async.bulk into stage t mod kStages and
+// signalled on that stage's mbarrier (arrive.expect_tx by the issuing thread,
+// complete_tx by the copies).  Thread 0 keeps kStages terms in flight: after
+// the CTA has consumed stage s (barrier), it issues term t + kStages into it.
+// Every wait is bounded (2 s of %globaltimer): on expiry the CTA sets bit 0 of
+// *status, stops issuing, waits (bounded) for the copies it already issued and
+// returns without writing.
+constexpr int kMacStages = 4;
+constexpr int kMacTile = 512;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait for phase `parity` of the barrier; false when the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMacTile / 2) k_mac(const MacItem* items, const MacTerm* terms,
+                                                     const Modulus* mods, int level, int logN, int T,
+                                                     uint32_t* status) {
+    extern __shared__ __align__(128) unsigned char mac_smem[];
+    uint64_t* bars = (uint64_t*)mac_smem;                      // [kMacStages]
+    u64* stage0 = (u64*)(mac_smem + 128);                      // [kMacStages][2 + W][T]
+    const size_t stage_words = (size_t)(2 + W) * T;
     const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
     const MacItem it = items[blockIdx.z];
     const int i = blockIdx.y, nq = level + 1;
     const Modulus m = mods[i];
-    const size_t o0 = ((size_t)i << logN) + n, o1 = ((size_t)(nq + i) << logN) + n;
-    u128 s0 = 0, s1 = 0;
-    for (int t = 0; t < it.n_terms; t++) {
-        const MacTerm tm = terms[it.term0 + t];
-        u64 p = tm.pt[o0];
-        s0 += (u128)tm.ct[o0] * p;
-        s1 += (u128)tm.ct[o1] * p;
-        if ((t & 15) == 15) {
-            s0 = reduce128(s0, m);
-            s1 = reduce128(s1, m);
-        }
+    const size_t base = (size_t)blockIdx.x * T;                // first coefficient of the tile
+    const size_t off0 = ((size_t)i << logN) + base, off1 = ((size_t)(nq + i) << logN) + base;
+    const uint32_t tile_bytes = (uint32_t)T * 8u;
+    const uint32_t stage_bytes = (uint32_t)(2 + it.n_out) * tile_bytes;
+    const uint64_t limit = 2000000000ull;
+    const int tid = threadIdx.x;
+    auto issue = [&](int t) {
+        const int s = t % kMacStages;
+        u64* st = stage0 + (size_t)s * stage_words;
+        const u64* ct = terms[it.term0[0] + t].ct;
+        mbar_expect_tx(&bars[s], stage_bytes);
+        bulk_g2s(st, ct + off0, tile_bytes, &bars[s]);
+        bulk_g2s(st + T, ct + off1, tile_bytes, &bars[s]);
+        for (int k = 0; k < it.n_out; k++) bulk_g2s(st + (2 + k) * T, terms[it.term0[k] + t].pt + off0, tile_bytes, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < kMacStages; s++) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    it.out[o0] = reduce128(s0, m);
-    it.out[o1] = reduce128(s1, m);
+    __syncthreads();
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < kMacStages && issued < it.n_terms; issued++) issue(issued);
+    u128 a0[W], a1[W], b0[W], b1[W];  // (coefficient 2 tid, 2 tid + 1) x (c0, c1 part)
+#pragma unroll
+    for (int k = 0; k < W; k++) a0[k] = a1[k] = b0[k] = b1[k] = 0;
+    bool ok = true;
+    int t_fail = it.n_terms;
+    for (int t = 0; t < it.n_terms; t++) {
+        const int s = t % kMacStages;
+        if (!mbar_wait(&bars[s], (uint32_t)((t / kMacStages) & 1), limit)) ok = false;
+        // all threads agree on failure before anyone touches the stage or refills it
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            t_fail = t;
+            break;
+        }
+        const u64* st = stage0 + (size_t)s * stage_words;
+        const ulonglong2 x0 = reinterpret_cast<const ulonglong2*>(st)[tid];
+        const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(st + T)[tid];
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            if (k >= it.n_out) break;
+            const ulonglong2 p = reinterpret_cast<const ulonglong2*>(st + (2 + k) * T)[tid];
+            a0[k] += (u128)x0.x * p.x;
+            a1[k] += (u128)x0.y * p.y;
+            b0[k] += (u128)x1.x * p.x;
+            b1[k] += (u128)x1.y * p.y;
+        }
+        if ((t & 15) == 15) {
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                if (k >= it.n_out) break;
+                a0[k] = reduce128(a0[k], m);
+                a1[k] = reduce128(a1[k], m);
+                b0[k] = reduce128(b0[k], m);
+                b1[k] = reduce128(b1[k], m);
+            }
+        }
+        __syncthreads();  // stage s consumed by every thread
+        if (tid == 0 && issued < it.n_terms) issue(issued++);
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(status, 1u);
+            // wait (bounded) for the copies this CTA issued and never consumed:
+            // terms t_fail .. issued - 1, one pending phase per stage
+            for (int t = t_fail; t < issued; t++)
+                mbar_wait(&bars[t % kMacStages], (uint32_t)((t / kMacStages) & 1), limit);
+        }
+        __syncthreads();
+        return;
+    }
+    (void)N;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        if (k >= it.n_out) break;
+        ulonglong2 r0, r1;
+        r0.x = reduce128(a0[k], m);
+        r0.y = reduce128(a1[k], m);
+        r1.x = reduce128(b0[k], m);
+        r1.y = reduce128(b1[k], m);
+        reinterpret_cast<ulonglong2*>(it.out[k] + off0)[tid] = r0;
+        reinterpret_cast<ulonglong2*>(it.out[k] + off1)[tid] = r1;
+    }
 }
 
 __global__ void k_rescale_combine(const u64* in, const u64* lift, u64* out, const Modulus* mods,
@@ -389,11 +518,28 @@ void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, in
     c->cnt.launches++;
 }
 
-void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_terms,
-                int level, cudaStream_t st) {
+void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
+                int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st) {
     if (!n_items) return;
-    ProfScope ps(c, PK_MAC, st, 8.0 * c->N * (level + 1) * (3.0 * n_terms + 2.0 * n_items));
-    k_mac<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, terms, c->d_mod, level, c->logN);
+    ProfScope ps(c, PK_MAC, st,
+                 8.0 * c->N * (level + 1) * (2.0 * n_ct_terms + (double)n_pt_terms + 2.0 * n_outputs));
+    const int T = std::min(kMacTile, c->N);
+    const dim3 g(c->N / T, level + 1, n_items);
+    const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
+    const size_t smem = 128 + (size_t)kMacStages * (2 + w) * T * 8;
+    if (w == 1) {
+        static bool set1 = false;
+        if (!set1) set1 = cudaFuncSetAttribute(k_mac<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 3 * kMacTile * 8) == cudaSuccess;
+        k_mac<1><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+    } else if (w == 2) {
+        static bool set2 = false;
+        if (!set2) set2 = cudaFuncSetAttribute(k_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 4 * kMacTile * 8) == cudaSuccess;
+        k_mac<2><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+    } else {
+        static bool set4 = false;
+        if (!set4) set4 = cudaFuncSetAttribute(k_mac<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 6 * kMacTile * 8) == cudaSuccess;
+        k_mac<4><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+    }
     c->cnt.launches++;
 }
 

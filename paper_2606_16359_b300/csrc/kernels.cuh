@@ -67,10 +67,15 @@ struct SumItem {
     const u64* convsum;  // [2][l+1][N] NTT form, or null
 };
 
-// PMult-MAC item: out = sum_t ct_t (x) pt_t over `n_terms` consecutive terms
+// PMult-MAC item: up to kMacWays outputs whose term lists read the same
+// ciphertexts in the same order, out[k] = sum_t ct_t (x) pt_{k,t} with
+// ct_t = terms[term0[0] + t].ct and pt_{k,t} = terms[term0[k] + t].pt, so each
+// ciphertext word is loaded once for all of them.
+constexpr int kMacWays = 4;
 struct MacItem {
-    u64* out;  // [2][l+1][N]
-    int term0, n_terms;
+    u64* out[kMacWays];  // [2][l+1][N] each
+    int term0[kMacWays];
+    int n_terms, n_out;
 };
 struct MacTerm {
     const u64* ct;  // [2][l+1][N]
@@ -95,8 +100,11 @@ void launch_combine_sum(fe_ctx* c, const SumItem* items_dev, const SumEntry* ent
 // (out + i * 2 (l+1) N words)
 void launch_autosum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev, int n_items,
                     int n_entries, u64* out, int level, cudaStream_t st);
+// n_ct_terms: ciphertext loads (sum of n_terms over items); n_pt_terms: plaintext
+// loads (sum of n_terms x n_out); n_outputs: outputs written; ways: the largest
+// n_out of the items (1, 2 or 4 selects the kernel)
 void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
-                int n_terms, int level, cudaStream_t st);
+                int n_ct_terms, int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st);
 void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,

@@ -355,6 +355,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         }
     }
 
+    const uint32_t zero_status[4] = {0, 0, 0, 0};
+    const size_t o_status = pb.put(zero_status, sizeof(zero_status));
     char* dpool = nullptr;
     FE_CUDA_TRY(cudaMalloc(&dpool, pb.host.size()));
     c->pool = dpool;
@@ -367,6 +369,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->d_qlinv = (u64*)(dpool + o_ql);
     c->d_qlinv_sh = (u64*)(dpool + o_ql_sh);
     c->d_identity_map = (int*)(dpool + o_ident);
+    c->d_status = (uint32_t*)(dpool + o_status);
     c->d_t2slot = (int*)(dpool + o_t2s);
     c->d_slot2t = (int*)(dpool + o_s2t);
     c->q0inv_q1 = c->L >= 1 ? h_invmod(c->mod[0] % c->mod[1], c->mod[1]) : 0;
@@ -475,5 +478,13 @@ extern "C" int fe_profile_end(fe_ctx* c, double* total_ms, uint64_t* launches, d
 extern "C" int fe_counters_reset(fe_ctx* c) {
     if (!c) return fail(FE_EINVAL, "null argument");
     memset(&c->cnt, 0, sizeof(c->cnt));
+    return FE_OK;
+}
+
+extern "C" int fe_device_status(fe_ctx* c, uint32_t* status, int reset) {
+    if (!c || !status) return fail(FE_EINVAL, "null argument");
+    FE_CUDA_TRY(cudaDeviceSynchronize());
+    FE_CUDA_TRY(cudaMemcpy(status, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (reset) FE_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
     return FE_OK;
 }

@@ -46,6 +46,7 @@ struct fe_plan {
     int n_pt = 0;
     int n_outer = 0;
     int bsgs_n1 = 0;  // baby steps of the outer rotations, 0: linear
+    int mac_ways = 4;  // outputs sharing one MAC item (ciphertext loads), 1, 2 or 4
     std::vector<int32_t> steps;
 };
 

@@ -52,6 +52,9 @@ class MobileNetBlocks:
             else:
                 n1 = int(schedule)
             ppw = ctx.plan_conv(pdw.out_layout, Cout, 1, level=L - 1, bsgs_n1=n1)
+            if tuner is not None:
+                ways, wt = tuner.mac_ways(ppw)
+                self.tune_ms[-1]["mac_ways"] = {str(k): round(v, 3) for k, v in wt.items()}
             self.schedule.append(ppw.info.bsgs_n1)
             plans.append((lay, pdw, ppw, x, wd, wp))
         del tuner

@@ -1,5 +1,6 @@
 """Autotuner: picks, per conv layer, the outer-rotation schedule (linear, or
-baby-step / giant-step with n1 baby steps) by timing every candidate on the
+baby-step / giant-step with n1 baby steps) and the MAC tile (how many outputs
+share one kernel item's ciphertext loads) by timing every candidate on the
 GPU, and caches the choice per layer shape.
 
 Candidates are timed through fe_he_layer_timing with plaintexts from a
@@ -79,7 +80,31 @@ class Tuner:
             del plan
         best = min(times, key=times.get)
         _CACHE[key] = {"n1": best, "ms": times}
+        self._save()
+        return best, times
+
+    def mac_ways(self, plan, reps=2):
+        """Fastest MAC tile (outputs sharing one kernel item: 1, 2 or 4) for a
+        plan; sets it on the plan and returns (ways, {ways: ms})."""
+        ctx = self.ctx
+        i = plan.info
+        key = json.dumps(["mac_ways", ctx.logN, ctx.L, plan.level, i.n_in_ct, i.n_out_ct, i.n_pt, i.n_inner_rot,
+                          i.n_outer_rot, i.bsgs_n1])
+        if key in _CACHE:
+            c = _CACHE[key]
+            ctx.plan_set_mac_ways(plan, c["ways"])
+            return c["ways"], {int(k): v for k, v in c["ms"].items()}
+        times = {}
+        for w in (1, 2, 4):
+            ctx.plan_set_mac_ways(plan, w)
+            times[w] = self.time_plan(plan, reps)
+        best = min(times, key=times.get)
+        ctx.plan_set_mac_ways(plan, best)
+        _CACHE[key] = {"ways": best, "ms": times}
+        self._save()
+        return best, times
+
+    def _save(self):
         if self.cache_file:
             with open(self.cache_file, "w") as f:
                 json.dump(_CACHE, f)
-        return best, times

@@ -344,3 +344,23 @@ def test_conv_parity_bsgs(tiny, H, C, Co, K, BS, S, stride, n1):
     w = rng.normal(0, 1 / K, (Co, C, K, K))
     plan, _ = run_conv_pair(tiny, x, w, S, stride, bsgs_n1=n1)
     assert plan.info.bsgs_n1 == min(n1, plan.in_layout.cpc)
+
+
+
+def test_mac_ways_do_not_change_residues(tiny):
+    """The MAC tile (outputs sharing ciphertext loads) is a pure schedule choice."""
+    g, pr = tiny.g, tiny.pr
+    rng = np.random.default_rng(7)
+    w = rng.normal(0, 0.3, (12, 12, 1, 1))
+    lay = g.layout(4, 4, 12, 2, 1)
+    plan = g.plan_conv(lay, 12, 1, level=pr.L, bsgs_n1=4)
+    sk = g.sk_gen(8)
+    evk = g.evk_gen(sk, 8, plan.steps)
+    pt = g.load_weights(plan, w, float(pr.q[pr.L]))
+    ct = g.encrypt(sk, g.pack(lay, torch.from_numpy(rng.uniform(0, 1, (2, 12, 4, 4)))), pr.L, 2.0 ** 25, seed=9)
+    outs = []
+    for ways in (1, 2, 4):
+        g.plan_set_mac_ways(plan, ways)
+        outs.append(u64(g.he_conv(evk, plan, pt, ct, mode=1)))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert g.device_status() == 0

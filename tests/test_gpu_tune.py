@@ -28,6 +28,9 @@ def test_tuner_times_all_candidates_and_tuned_blocks_decrypt():
         assert set(times) == {0, 2, 4, 8, 16, 32} and n1 in times
         assert times[n1] == min(times.values()) and all(v > 0 for v in times.values())
         assert t.conv_schedule(lay, 64, 1, level=ctx.L - 1)[1] == times  # cached
+        plan = ctx.plan_conv(lay, 64, 1, level=ctx.L - 1, bsgs_n1=n1)
+        ways, wt = t.mac_ways(plan)
+        assert set(wt) == {1, 2, 4} and wt[ways] == min(wt.values()) and plan.mac_ways == ways
         net = MobileNetBlocks(ctx, blocks=[(8, 64, 64), (6, 32, 48)], delta=p["delta"], schedule="tuned")
         net.run(mode=1)
         torch.cuda.synchronize()
