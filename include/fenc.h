@@ -293,6 +293,7 @@ typedef struct {
     size_t pt_bytes, in_bytes, out_bytes, workspace_bytes, workspace_min_bytes;
     uint32_t n_in_ct, n_out_ct, n_pt, n_inner_rot, n_outer_rot;
     uint32_t bsgs_n1;  /* baby steps of the outer rotations actually used (0: linear) */
+    uint32_t double_hoist;  /* 1: rotations and MAC on Q_l * P (fe_plan_set_hoisting) */
 } fe_plan_info;
 int fe_plan_query(const fe_plan* plan, fe_plan_info* info);
 /* Rotation steps the plan needs keys for (steps_host has room for max entries;
@@ -349,6 +350,16 @@ int fe_he_layer_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const
 int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_pool_dev,
                        uint32_t n_pool, const void* in_dev, void* out_dev, void* ws, size_t ws_bytes,
                        void* stream);
+/* Hoisting of a plan's inner (and baby-step) rotations.  double_hoist = 0: each
+ * rotated copy is brought back to Q_l by its own ModDown (the rotation of
+ * Eq. 1).  double_hoist = 1: the rotated copies stay on the key-switching
+ * basis Q_l * P as sigma_g((P c0, 0) + key inner product), unrotated inputs
+ * are lifted to (P c0, P c1), plaintexts are encoded on Q_l * P, and every
+ * partial sum of the MAC takes one ModDown (double hoisting; same convolution,
+ * fewer ModDowns, different rounding, its own oracle schedule).  Must be set
+ * before fe_plan_load_weights: it changes the plaintext size (pt_bytes).
+ * Errors: FE_EINVAL. */
+int fe_plan_set_hoisting(fe_plan* plan, int double_hoist);
 /* Tile choice of the batched MAC: how many outputs whose terms read the same
  * ciphertexts share one kernel item (1, 2 or 4; default 4).  Results do not
  * depend on it; the autotuner picks the fastest.  Errors: FE_EINVAL. */

@@ -327,9 +327,9 @@ def mod_down(pr, x, level):
     return out
 
 
-def key_switch_ext(pr, ext, key, level):
-    """Inner product of the extended digits with a switching key, then ModDown.
-    Returns (d0, d1) on Q_level."""
+def key_inner_product(pr, ext, key, level):
+    """Inner product of the extended digits with a switching key over
+    Q_level * P: (acc_b, acc_a) as dicts limb -> NTT residues."""
     acc_b, acc_a = {}, {}
     for t in pr.ks_limbs(level):
         mt = pr.moduli[t]
@@ -339,7 +339,76 @@ def key_switch_ext(pr, ext, key, level):
             C.vec_mac(ab, e[t], key.b[j][t], mt)
             C.vec_mac(aa, e[t], key.a[j][t], mt)
         acc_b[t], acc_a[t] = ab, aa
+    return acc_b, acc_a
+
+
+def key_switch_ext(pr, ext, key, level):
+    """Inner product of the extended digits with a switching key, then ModDown.
+    Returns (d0, d1) on Q_level."""
+    acc_b, acc_a = key_inner_product(pr, ext, key, level)
     return mod_down(pr, acc_b, level), mod_down(pr, acc_a, level)
+
+
+# ---------------------------------------------------------------------------
+# Double hoisting: rotations kept on Q_level * P until after the products
+# with plaintexts, with one ModDown per sum (instead of one per rotation).
+# ---------------------------------------------------------------------------
+
+def rotate_ext_qp(pr, keys, ct, ext, r):
+    """Rotation by r left on the key-switching basis: V = sigma_g((P c0, 0) + acc)
+    over Q_level * P (dicts limb -> NTT residues), acc the key inner product of
+    the hoisted digits.  mod_down(V) is exactly rotate_ext(ct, ext, r)."""
+    g = pr.galois(r)
+    lv = ct.level
+    acc_b, acc_a = key_inner_product(pr, ext, keys.rot[g], lv)
+    perm = pr.automorph_perm(g)
+    Vb, Va = {}, {}
+    for t in pr.ks_limbs(lv):
+        mt = pr.moduli[t]
+        b = acc_b[t]
+        if t <= lv:
+            b = C.vec_add(b, C.vec_scalar_mul(ct.c0[t], pr.P % mt, mt), mt)
+        Vb[t] = C.gather(b, perm)
+        Va[t] = C.gather(acc_a[t], perm)
+    return Vb, Va
+
+
+def lift_qp(pr, ct):
+    """(P c0, P c1) on Q_level * P: P times the ciphertext on the q limbs, zero on
+    the special limbs, so that mod_down returns ct exactly."""
+    Vb, Va = {}, {}
+    for t in pr.ks_limbs(ct.level):
+        mt = pr.moduli[t]
+        if t <= ct.level:
+            Vb[t] = C.vec_scalar_mul(ct.c0[t], pr.P % mt, mt)
+            Va[t] = C.vec_scalar_mul(ct.c1[t], pr.P % mt, mt)
+        else:
+            Vb[t] = np.zeros(pr.N, dtype=np.uint64)
+            Va[t] = np.zeros(pr.N, dtype=np.uint64)
+    return Vb, Va
+
+
+def encode_qp(pr, z, level, scale):
+    """The plaintext of encode(z, level, scale) on Q_level * P: dict limb -> NTT."""
+    m = C.encode(np.asarray(z, dtype=np.float64), pr.logN, scale)
+    return {t: pr.ntt(C.from_signed(m, pr.moduli[t]), t) for t in pr.ks_limbs(level)}
+
+
+def mac_qp(pr, level, terms):
+    """sum_t V_t (x) pt_t over Q_level * P; terms: list of ((Vb, Va), pt_qp)."""
+    ab = {t: np.zeros(pr.N, dtype=np.uint64) for t in pr.ks_limbs(level)}
+    aa = {t: np.zeros(pr.N, dtype=np.uint64) for t in pr.ks_limbs(level)}
+    for (Vb, Va), pt in terms:
+        for t in pr.ks_limbs(level):
+            mt = pr.moduli[t]
+            C.vec_mac(ab[t], Vb[t], pt[t], mt)
+            C.vec_mac(aa[t], Va[t], pt[t], mt)
+    return ab, aa
+
+
+def mod_down_ct(pr, Vb, Va, level, scale):
+    """ModDown of a pair on Q_level * P to a ciphertext on Q_level."""
+    return Ciphertext(mod_down(pr, Vb, level), mod_down(pr, Va, level), level, scale)
 
 
 def automorph_ntt(pr, poly, g, level):

@@ -43,6 +43,7 @@ class Counters:
         self.cmult = 0
         self.rescale = 0
         self.modup = 0
+        self.moddown = 0  # ModDowns of partial sums under double hoisting
 
     def as_dict(self):
         return dict(self.__dict__)
@@ -155,14 +156,19 @@ def conv_weight_slots(lay, W, h, up, vp, d, g, i, j, *, stride, depthwise, in_pe
 
 
 def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None, wmul=1.0,
-            w_scale=None, cnt=None, bsgs_n1=0):
+            w_scale=None, cnt=None, bsgs_n1=0, hoist="single"):
     """Encrypted convolution of the fragment-packed input `cts` (list in (g, u, v)
     order).  Returns (output ciphertexts in (h, u'', v'') order, output layout).
     bsgs_n1 > 0 selects the baby-step / giant-step schedule of the outer
-    rotations (he_conv_bsgs)."""
+    rotations (he_conv_bsgs).  hoist="double" keeps the inner rotations on the
+    key-switching basis Q_level * P and performs one ModDown per partial sum
+    P_d instead of one per rotation (double hoisting): P_d = ModDown(sum of
+    V (x) pt) with V = sigma((P c0, 0) + key inner product) for a rotated source
+    and V = P x for an unrotated one, plaintexts encoded on Q_level * P."""
     if bsgs_split(lay, bsgs_n1, depthwise, in_period):
         return he_conv_bsgs(pr, keys, cts, lay, W, stride=stride, wmul=wmul, w_scale=w_scale, cnt=cnt,
-                            n1=bsgs_n1)
+                            n1=bsgs_n1, hoist=hoist)
+    double = hoist == "double"
     cnt = cnt if cnt is not None else Counters()
     level = cts[0].level
     Cout = W.shape[0]
@@ -187,9 +193,10 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                     cnt.modup += 1
                 for (a, b) in pairs:
                     if (a, b) == (0, 0):
-                        R[(g, u, v, a, b)] = ct
+                        R[(g, u, v, a, b)] = ckks.lift_qp(pr, ct) if double else ct
                     else:
-                        R[(g, u, v, a, b)] = ckks.rotate_ext(pr, keys, ct, ext, (a * m + b) * BS)
+                        rot = ckks.rotate_ext_qp if double else ckks.rotate_ext
+                        R[(g, u, v, a, b)] = rot(pr, keys, ct, ext, (a * m + b) * BS)
                         cnt.rot += 1
                         cnt.keyswitch += 1
 
@@ -201,7 +208,7 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
             for vp in range(0, S, stride):
                 total = None
                 for d in diags:
-                    acc = None
+                    acc, terms = None, []
                     for g in range(G_in):
                         for i in range(K):
                             u, a = (up + i) % S, (up + i) // S
@@ -212,9 +219,16 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                                                       wmul=wmul, Cout=Cout)
                                 if not z.any():
                                     continue
-                                pt = ckks.encode(pr, z, level, dw)
-                                acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b)], pt))
+                                if double:
+                                    terms.append((R[(g, u, v, a, b)], ckks.encode_qp(pr, z, level, dw)))
+                                else:
+                                    pt = ckks.encode(pr, z, level, dw)
+                                    acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b)], pt))
                                 cnt.pmult += 1
+                    if double and terms:
+                        ab, aa = ckks.mac_qp(pr, level, terms)
+                        acc = ckks.mod_down_ct(pr, ab, aa, level, cts[0].scale * dw)
+                        cnt.moddown += 1
                     if acc is None:
                         continue
                     if d:
@@ -229,7 +243,7 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
     return out, olay
 
 
-def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt=None, n1=4):
+def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt=None, n1=4, hoist="single"):
     """Encrypted convolution with baby-step / giant-step outer rotations (the
     schedule the paper assumes for the channel diagonals, Sec. 3.1).
 
@@ -242,8 +256,11 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
       2. for each output and giant index j, Q_j = sum_{i, g, taps} of those
          rotations times the plaintexts of diagonal j n1 + i rotated left by
          i blk slots;
-      3. out = Q_0 + sum_{j > 0} Rot(Q_j, j n1 blk), before the one rescale."""
+      3. out = Q_0 + sum_{j > 0} Rot(Q_j, j n1 blk), before the one rescale.
+    hoist="double": the inner and baby rotations stay on Q_level * P and each Q_j
+    takes one ModDown (see he_conv)."""
     cnt = cnt if cnt is not None else Counters()
+    double = hoist == "double"
     level = cts[0].level
     Cout, Cin, K = W.shape[0], W.shape[1], W.shape[-1]
     olay = out_layout_conv(lay, Cout, K, stride)
@@ -266,12 +283,13 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                 ext = None
                 for (a, b, i) in keys_needed:
                     if (a, b, i) == (0, 0, 0):
-                        R[(g, u, v, a, b, i)] = ct
+                        R[(g, u, v, a, b, i)] = ckks.lift_qp(pr, ct) if double else ct
                         continue
                     if ext is None:
                         ext = ckks.mod_up(pr, ct.c1, ct.level)
                         cnt.modup += 1
-                    R[(g, u, v, a, b, i)] = ckks.rotate_ext(pr, keys, ct, ext, (a * m + b) * BS + i * blk)
+                    rot = ckks.rotate_ext_qp if double else ckks.rotate_ext
+                    R[(g, u, v, a, b, i)] = rot(pr, keys, ct, ext, (a * m + b) * BS + i * blk)
                     cnt.rot += 1
                     cnt.keyswitch += 1
 
@@ -283,7 +301,7 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
             for vp in range(0, S, stride):
                 total = None
                 for j in range(n2):
-                    acc = None
+                    acc, terms = None, []
                     for i in range(n1):
                         d = j * n1 + i
                         if d >= cpc or d not in dset:
@@ -298,9 +316,16 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                                     if not z.any():
                                         continue
                                     z = np.roll(z, -i * blk)  # Rot(z, i blk)[l] = z[l + i blk]
-                                    pt = ckks.encode(pr, z, level, dw)
-                                    acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b, i)], pt))
+                                    if double:
+                                        terms.append((R[(g, u, v, a, b, i)], ckks.encode_qp(pr, z, level, dw)))
+                                    else:
+                                        pt = ckks.encode(pr, z, level, dw)
+                                        acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b, i)], pt))
                                     cnt.pmult += 1
+                    if double and terms:
+                        ab, aa = ckks.mac_qp(pr, level, terms)
+                        acc = ckks.mod_down_ct(pr, ab, aa, level, cts[0].scale * dw)
+                        cnt.moddown += 1
                     if acc is None:
                         continue
                     if j:

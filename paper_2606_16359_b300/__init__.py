@@ -47,7 +47,7 @@ class FeCounters(ctypes.Structure):
 class FePlanInfo(ctypes.Structure):
     _fields_ = [("pt_bytes", sz), ("in_bytes", sz), ("out_bytes", sz), ("workspace_bytes", sz),
                 ("workspace_min_bytes", sz), ("n_in_ct", u32), ("n_out_ct", u32), ("n_pt", u32),
-                ("n_inner_rot", u32), ("n_outer_rot", u32), ("bsgs_n1", u32)]
+                ("n_inner_rot", u32), ("n_outer_rot", u32), ("bsgs_n1", u32), ("double_hoist", u32)]
 
 
 P = ctypes.POINTER
@@ -101,6 +101,7 @@ SIGNATURES = {
     "fe_plan_truncate": (cint, [vp, u32]),
     "fe_device_status": (cint, [vp, P(u32), cint]),
     "fe_plan_set_mac_ways": (cint, [vp, u32]),
+    "fe_plan_set_hoisting": (cint, [vp, cint]),
     "fe_server_create": (cint, [P(FeServerConfig), P(vp)]),
     "fe_server_add_model": (cint, [vp, vp, vp, P(FeOp), u32, u32, u32, P(u32)]),
     "fe_server_model_io": (cint, [vp, u32, P(u32), P(u32), P(sz), P(sz)]),
@@ -376,12 +377,15 @@ class Context:
         return out
 
     # -- layers -------------------------------------------------------------------------
-    def plan_conv(self, lay, Cout, K, stride=1, depthwise=False, in_period=0, level=None, bsgs_n1=0):
+    def plan_conv(self, lay, Cout, K, stride=1, depthwise=False, in_period=0, level=None, bsgs_n1=0,
+                  double_hoist=False):
         level = self.L if level is None else level
         out_lay = FeLayout()
         h = vp()
         check(load().fe_plan_conv(self.handle, ctypes.byref(lay), Cout, K, stride, 1 if depthwise else 0,
                                   in_period, level, bsgs_n1, ctypes.byref(out_lay), ctypes.byref(h)))
+        if double_hoist:
+            check(load().fe_plan_set_hoisting(h, 1))
         p = Plan(self, h, out_lay)
         p.level, p.in_layout = level, lay
         return p
@@ -428,6 +432,12 @@ class Context:
         v = u32(0)
         check(load().fe_device_status(self.handle, ctypes.byref(v), 1 if reset else 0))
         return v.value
+
+    def plan_set_hoisting(self, plan, double):
+        """Double hoisting of the plan's rotations (set before load_weights)."""
+        check(load().fe_plan_set_hoisting(plan.handle, 1 if double else 0))
+        plan.refresh()
+        return plan
 
     def plan_set_mac_ways(self, plan, ways):
         check(load().fe_plan_set_mac_ways(plan.handle, ways))

@@ -73,6 +73,7 @@ struct fe_ctx {
     u64* d_itw2;                    // [n_mod][N][2]  (psi^-brv(j), Shoup companion)
     u64 *d_ninv, *d_ninv_sh;        // [n_mod] N^-1
     u64 *d_pinv, *d_pinv_sh;        // [n_mod] P^-1 mod q_i (i <= L)
+    u64 *d_pmod, *d_pmod_sh;        // [n_mod] P mod q_i (i <= L)
     u64 *d_qlinv, *d_qlinv_sh;      // [L+1][L+1]: q_l^-1 mod q_i at [l][i]
     double* d_dd_w;                 // [N][4]: exp(-2 pi i j / 2N) as (re_hi, re_lo, im_hi, im_lo)
     int* d_identity_map;            // [n_mod] j -> j
@@ -116,8 +117,9 @@ void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSe
 void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);
 
 int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st);
+// qp: the plaintexts on Q_level * P (l+1+k limbs in key-switching order) instead of Q_level
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
-                 cudaStream_t st);
+                 cudaStream_t st, bool qp = false);
 int decode_batch(fe_ctx* c, const double* mdd, int n, double scale, double* slots, cudaStream_t st);
 
 // Records CUDA events around one launch when its kernel class is being profiled,

@@ -102,7 +102,7 @@ __global__ void k_fft_stage(cdd* X, const double* w, int logN, int s, int sign) 
 // m_j = round(Delta / N * Re(exp(-i pi j / N) F[j])), written as residues on
 // limbs 0..level (coefficient form) of pt[n][level+1][N].
 __global__ void k_enc_round(const cdd* F, const double* w, double scale, int logN,
-                            const Modulus* mods, int nl, u64* pt, unsigned* flags) {
+                            const Modulus* mods, const int* mod_map, int nl, u64* pt, unsigned* flags) {
     const int N = 1 << logN;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -124,7 +124,7 @@ __global__ void k_enc_round(const cdd* F, const double* w, double scale, int log
     if (fabs(d) > 0.5 - 0x1p-40 || fabs(ri) >= 0x1p62) atomicAdd(flags, 1u);
     const i64 m = (i64)ri;
     u64* o = pt + (size_t)blockIdx.y * nl * N + j;
-    for (int i = 0; i < nl; i++) o[(size_t)i * N] = from_signed(m, mods[i].q);
+    for (int i = 0; i < nl; i++) o[(size_t)i * N] = from_signed(m, mods[mod_map ? mod_map[i] : i].q);
 }
 
 // decode input: X[n][brv(j)] = m_j exp(+i pi j / N), m_j given as double-double
@@ -149,7 +149,7 @@ __global__ void k_dec_gather(const cdd* F, const int* slot2t, double inv_scale, 
 }  // namespace
 
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool qp) {
     if (n <= 0) return FE_OK;
     const int N = c->N, logN = c->logN;
     // process in chunks so that the complex double-double scratch stays bounded
@@ -159,18 +159,19 @@ int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale,
     FE_CUDA_TRY(cudaMallocAsync(&X, (size_t)chunk * N * sizeof(cdd), st));
     FE_CUDA_TRY(cudaMallocAsync(&flags, sizeof(unsigned), st));
     FE_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
-    const int nl = level + 1;
+    const int nl = qp ? level + 1 + c->k : level + 1;
+    const int* mod_map = qp ? c->lv[level].d_ks_limbs : c->d_identity_map;
     for (int s0 = 0; s0 < n; s0 += chunk) {
         int cn = std::min(chunk, n - s0);
         k_enc_scatter<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(slots + (size_t)s0 * (N / 2),
                                                                 c->d_t2slot, X, logN);
         for (int s = 1; s <= logN; s++)
             k_fft_stage<<<dim3((N / 2 + 255) / 256, cn), 256, 0, st>>>(X, c->d_dd_w, logN, s, -1);
-        k_enc_round<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(X, c->d_dd_w, scale, logN, c->d_mod, nl,
-                                                               pt + (size_t)s0 * nl * N, flags);
+        k_enc_round<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(X, c->d_dd_w, scale, logN, c->d_mod, mod_map,
+                                                               nl, pt + (size_t)s0 * nl * N, flags);
         c->cnt.launches += 2 + logN;
     }
-    ntt_forward(c, LimbSet{pt, (size_t)nl * N, nl, n, c->d_identity_map}, st);
+    ntt_forward(c, LimbSet{pt, (size_t)nl * N, nl, n, mod_map}, st);
     unsigned hflag = 0;
     FE_CUDA_TRY(cudaMemcpyAsync(&hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     FE_CUDA_TRY(cudaFreeAsync(X, st));

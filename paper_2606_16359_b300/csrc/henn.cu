@@ -154,7 +154,8 @@ size_t item_bytes(const fe_plan* p, size_t chunk, size_t R) {
     n += n_outer * (sizeof(KsItem) + sizeof(KsGroup) + sizeof(SumEntry));
     n += n_chunks * R * p->n_out * sizeof(SumItem);
     n += R * (groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm));
-    return n + 16 * 256;
+    if (p->dhoist) n += R * ((p->inner.size() + p->n_in) * sizeof(LiftItem) + groups * sizeof(CombineItem));
+    return n + 20 * 256;
 }
 
 }  // namespace
@@ -183,11 +184,15 @@ size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
     const fe_ctx* c = p->c;
     Sizes z = sizes_of(c, p->level);
     size_t n_mu = p->modup_cts.size(), n_in_rot = p->inner.size();
-    size_t persist = R * (n_in_rot + p->n_out) * z.ctw;
-    size_t inner = R * (n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + z.ctw));
-    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw) + R * p->n_out * z.ctw;
+    const bool dh = p->dhoist;
+    // double hoisting keeps the rotated copies and the lifted inputs on Q_l * P
+    size_t persist = R * (n_in_rot * (dh ? z.accw : z.ctw) + p->n_out * z.ctw + (dh ? p->n_in * z.accw : 0));
+    size_t inner = R * (n_mu * (z.nlN + z.extw) + n_in_rot * (z.accw + (dh ? 0 : z.ctw)));
+    size_t base = dh ? R * p->n_out * (z.accw + z.ctw) : 0;
+    size_t outer = chunk * (z.ctw + z.nlN + z.extw + z.accw + z.ctw + (dh ? z.accw + z.ctw : 0)) +
+                   R * p->n_out * z.ctw;
     size_t rs = rescale_tmp_words(c, (int)(R * p->n_out), p->level);
-    size_t words = persist + std::max(std::max(inner, outer), rs);
+    size_t words = persist + std::max(std::max(std::max(inner, outer), rs), base);
     return words * 8 + item_bytes(p, chunk, R) + 32 * 256;
 }
 
@@ -206,6 +211,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     const size_t R = (size_t)n_req;
     const size_t ctw_out = ct_words(c, lv - 1);
     const size_t n_in_rot = p->inner.size(), n_mu = p->modup_cts.size(), n_terms = p->terms.size();
+    // double hoisting: rotated copies, lifted inputs and plaintexts on Q_l * P
+    const bool dh = p->dhoist != 0;
+    const size_t rw = dh ? z.accw : z.ctw;                         // words of one rotated copy
+    const size_t ptw = dh ? (size_t)(lv + 1 + c->k) * N : z.nlN;  // words of one plaintext
     size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, R * p->n_outer);
     while (chunk > 1 && plan_workspace(p, chunk, R) > ws_bytes) chunk = (chunk + 1) / 2;
     if (plan_workspace(p, chunk, R) > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the plan");
@@ -217,8 +226,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     }
     // ---- carve the workspace ----
     Carver cv(ws, ws_bytes);
-    u64* Rb = cv.take<u64>(R * n_in_rot * z.ctw);
+    u64* Rb = cv.take<u64>(R * n_in_rot * rw);
     u64* total = cv.take<u64>(R * p->n_out * z.ctw);
+    u64* XP = dh ? cv.take<u64>(R * p->n_in * z.accw) : nullptr;
     size_t n_groups_all = 0;
     for (auto& o : p->outs) n_groups_all += o.groups.size();
     // rotated groups of all requests: (request, output, group), sorted by step
@@ -249,6 +259,8 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     KsGroup* d_out_kg = cv.take<KsGroup>(std::max<size_t>(1, order.size()));
     SumEntry* d_ent = cv.take<SumEntry>(std::max<size_t>(1, order.size()));
     SumItem* d_sum = cv.take<SumItem>(std::max<size_t>(1, n_chunks * R * p->n_out));
+    LiftItem* d_lift = cv.take<LiftItem>(dh ? std::max<size_t>(1, R * (n_in_rot + p->n_in)) : 1);
+    CombineItem* d_dcb = cv.take<CombineItem>(dh ? std::max<size_t>(1, R * n_groups_all) : 1);
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
     char* scratch = cv.p;
     const size_t scratch_bytes = cv.left;
@@ -256,7 +268,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     u64* coef1 = s1.take<u64>(R * n_mu * z.nlN);
     u64* ext1 = s1.take<u64>(R * n_mu * z.extw);
     u64* acc1 = s1.take<u64>(R * n_in_rot * z.accw);
-    u64* conv1 = s1.take<u64>(R * n_in_rot * z.ctw);
+    u64* conv1 = s1.take<u64>(dh ? 0 : R * n_in_rot * z.ctw);
+    Carver s2(scratch, scratch_bytes);  // stage 2 under double hoisting (same region)
+    u64* accB = s2.take<u64>(dh ? R * p->n_out * z.accw : 0);
+    u64* convB = s2.take<u64>(dh ? R * p->n_out * z.ctw : 0);
     Carver s3(scratch, scratch_bytes);  // stage 3 (same region)
     u64* Pd = s3.take<u64>(chunk * z.ctw);
     u64* coef3 = s3.take<u64>(chunk * z.nlN);
@@ -264,13 +279,17 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     u64* acc3 = s3.take<u64>(chunk * z.accw);
     u64* conv3 = s3.take<u64>(chunk * z.ctw);
     u64* csum3 = s3.take<u64>(R * p->n_out * z.ctw);  // per-output sums of the converted parts
+    u64* accO = s3.take<u64>(dh ? chunk * z.accw : 0);
+    u64* convO = s3.take<u64>(dh ? chunk * z.ctw : 0);
     Carver s4(scratch, scratch_bytes);  // stage 4 (same region)
     u64* rs_tmp = s4.take<u64>(2 * R * p->n_out * N);
     u64* rs_lift = s4.take<u64>(2 * R * p->n_out * lv * N);
-    if (!s1.ok || !s3.ok || !s4.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
+    if (!s1.ok || !s2.ok || !s3.ok || !s4.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
 
     auto src_ptr = [&](size_t r, int src) -> const u64* {
-        return src >= 0 ? Rb + (r * n_in_rot + src) * z.ctw : b_in + (r * p->n_in + (size_t)(-src - 1)) * z.ctw;
+        if (src >= 0) return Rb + (r * n_in_rot + src) * rw;
+        const size_t ci = r * p->n_in + (size_t)(-src - 1);
+        return dh ? XP + ci * z.accw : b_in + ci * z.ctw;
     };
     // global index of the s-th converted input (request-major) and its source ciphertext
     auto mu_ct = [&](size_t s) -> size_t { return (s / n_mu) * p->n_in + p->modup_cts[s % n_mu]; };
@@ -297,25 +316,45 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             const auto& in = p->inner[i];
             const size_t x = r * n_in_rot + i;
             icb[x] = CombineItem{acc1 + x * z.accw, conv1 + x * z.ctw, b_in + (r * p->n_in + in.ci) * z.ctw, nullptr,
-                                 Rb + x * z.ctw, c->galois(in.step), 0};
+                                 Rb + x * rw, c->galois(in.step), 0};
         }
+    // double hoisting: rotated copies sigma((P c0, 0) + acc) and lifted inputs (P c0, P c1)
+    std::vector<LiftItem> lifts;
+    if (dh) {
+        for (size_t r = 0; r < R; r++)
+            for (size_t i = 0; i < n_in_rot; i++) {
+                const size_t x = r * n_in_rot + i;
+                lifts.push_back(LiftItem{acc1 + x * z.accw, b_in + (r * p->n_in + p->inner[i].ci) * z.ctw,
+                                         Rb + x * rw, c->galois(p->inner[i].step)});
+            }
+        for (size_t r = 0; r < R; r++)
+            for (int ci = 0; ci < p->n_in; ci++)
+                lifts.push_back(LiftItem{nullptr, b_in + (r * p->n_in + ci) * z.ctw, XP + (r * p->n_in + ci) * z.accw, 1});
+    }
     std::vector<MacTerm> mterms;
     mterms.reserve(R * n_terms);
     for (size_t r = 0; r < R; r++)
         for (const auto& t : p->terms)
-            mterms.push_back(MacTerm{src_ptr(r, t.src), b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * z.nlN});
+            mterms.push_back(MacTerm{src_ptr(r, t.src), b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * ptw});
     struct OneMac {
         u64* out;
         int term0, n_terms;
     };
     std::vector<OneMac> macs;
     std::vector<size_t> no_base;  // request-major output index
+    std::vector<CombineItem> dcb;  // double hoisting: ModDown of every MAC output (base, then outer)
     for (size_t r = 0; r < R; r++)
         for (int o = 0; o < p->n_out; o++) {
             bool base = false;
             for (const auto& g : p->outs[o].groups)
                 if (g.step == 0) {
-                    macs.push_back(OneMac{total + (r * p->n_out + o) * z.ctw, (int)(r * n_terms) + g.t0, g.nt});
+                    u64* dst = total + (r * p->n_out + o) * z.ctw;
+                    if (dh) {
+                        const size_t b = macs.size();
+                        dcb.push_back(CombineItem{accB + b * z.accw, convB + b * z.ctw, nullptr, nullptr, dst, 1, 0});
+                        dst = accB + b * z.accw;
+                    }
+                    macs.push_back(OneMac{dst, (int)(r * n_terms) + g.t0, g.nt});
                     base = true;
                 }
             if (!base) no_base.push_back(r * p->n_out + o);
@@ -324,7 +363,13 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     auto group_of = [&](const OuterRef& x) -> const fe_plan::Group& { return p->outs[x.o].groups[x.gi]; };
     for (size_t k = 0; k < order.size(); k++) {
         const auto& g = group_of(order[k]);
-        macs.push_back(OneMac{Pd + (k % chunk) * z.ctw, (int)(order[k].r * n_terms) + g.t0, g.nt});
+        const size_t sl = k % chunk;
+        if (dh) {
+            dcb.push_back(CombineItem{accO + sl * z.accw, convO + sl * z.ctw, nullptr, nullptr, Pd + sl * z.ctw, 1, 0});
+            macs.push_back(OneMac{accO + sl * z.accw, (int)(order[k].r * n_terms) + g.t0, g.nt});
+        } else {
+            macs.push_back(OneMac{Pd + sl * z.ctw, (int)(order[k].r * n_terms) + g.t0, g.nt});
+        }
     }
     // device MAC items: consecutive outputs whose terms read the same ciphertexts
     // in the same order share one item (up to kMacWays), so each ciphertext word
@@ -332,7 +377,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     struct MacRange {
         int first, count, ct_terms, pt_terms, outputs, ways;
     };
-    const int ways = std::max(1, std::min(kMacWays, p->mac_ways));
+    const int ways = mode == 0 ? 1 : std::max(1, std::min(kMacWays, p->mac_ways));
     std::vector<MacItem> dmacs;
     auto same_sources = [&](const OneMac& a, const OneMac& b) {
         if (a.n_terms != b.n_terms) return false;
@@ -414,6 +459,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         FE_TRY(upload(okg, d_out_kg, st));
         FE_TRY(upload(ents, d_ent, st));
         FE_TRY(upload(sums, d_sum, st));
+        if (dh) {
+            FE_TRY(upload(lifts, d_lift, st));
+            FE_TRY(upload(dcb, d_dcb, st));
+        }
     }
     if (!(phase & 2)) return FE_OK;
 
@@ -427,9 +476,13 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         for (size_t q = 0; q < iorder.size(); q++) {
             const size_t x = (size_t)iorder[q].first * n_in_rot + iorder[q].second;
             launch_keyip(c, d_in_ks + q, 1, lv, st);
-            moddown_prepare(c, acc1 + x * z.accw, 1, lv, conv1 + x * z.ctw, st);
+            if (dh) launch_lift(c, d_lift + x, 1, lv, st);
+            else moddown_prepare(c, acc1 + x * z.accw, 1, lv, conv1 + x * z.ctw, st);
         }
-        for (size_t x = 0; x < R * n_in_rot; x++) launch_combine(c, d_in_cb + x, 1, lv, st);
+        if (dh)
+            for (size_t x = 0; x < R * p->n_in; x++) launch_lift(c, d_lift + R * n_in_rot + x, 1, lv, st);
+        else
+            for (size_t x = 0; x < R * n_in_rot; x++) launch_combine(c, d_in_cb + x, 1, lv, st);
     } else {
         size_t i = 0;
         while (i < n_mu_all) {  // consecutive runs of rotated inputs are converted together
@@ -439,8 +492,12 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             i = j;
         }
         launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)iorder.size(), lv, st);
-        moddown_prepare(c, acc1, (int)(R * n_in_rot), lv, conv1, st);
-        launch_combine(c, d_in_cb, (int)(R * n_in_rot), lv, st);
+        if (dh) {
+            launch_lift(c, d_lift, (int)(R * (n_in_rot + p->n_in)), lv, st);
+        } else {
+            moddown_prepare(c, acc1, (int)(R * n_in_rot), lv, conv1, st);
+            launch_combine(c, d_in_cb, (int)(R * n_in_rot), lv, st);
+        }
     }
     }
     c->cnt.rot += R * n_in_rot;
@@ -450,7 +507,14 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     {
     ProfScope stage(c, PK_STAGE_BASE, st, 0.0);
     for (size_t o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + o * z.ctw, 0, z.ctw * 8, st));
-    if (mode == 0) {
+    if (mode == 0 && dh) {
+        for (size_t i = 0; i < n_base; i++) {
+            const int nt = macs[i].n_terms;
+            launch_mac(c, d_mac + base_rg.first + i, d_terms, 1, nt, nt, 1, 1, lv, st, true);
+            moddown_prepare(c, accB + i * z.accw, 1, lv, convB + i * z.ctw, st);
+            launch_combine(c, d_dcb + i, 1, lv, st);
+        }
+    } else if (mode == 0) {
         for (size_t i = 0; i < n_base; i++)
             for (int t = 0; t < macs[i].n_terms; t++) {
                 const MacTerm& tm = mterms[macs[i].term0 + t];
@@ -458,7 +522,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             }
     } else {
         launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
-                   base_rg.outputs, base_rg.ways, lv, st);
+                   base_rg.outputs, base_rg.ways, lv, st, dh);
+        if (dh) {
+            moddown_prepare(c, accB, (int)n_base, lv, convB, st);
+            launch_combine(c, d_dcb, (int)n_base, lv, st);
+        }
     }
     }
 
@@ -471,11 +539,18 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         if (mode == 0) {
             for (size_t k = c0; k < c1; k++) {
                 const OneMac& m = macs[n_base + k];
-                for (int t = 0; t < m.n_terms; t++) {
-                    const MacTerm& tm = mterms[m.term0 + t];
-                    launch_pmult(c, tm.ct, tm.pt, m.out, 1, lv, t > 0, st);
-                }
                 size_t s = k - c0;
+                if (dh) {
+                    launch_mac(c, d_mac + chunk_rg[ch].first + (k - c0), d_terms, 1, m.n_terms, m.n_terms, 1, 1, lv,
+                               st, true);
+                    moddown_prepare(c, accO + s * z.accw, 1, lv, convO + s * z.ctw, st);
+                    launch_combine(c, d_dcb + n_base + k, 1, lv, st);
+                } else {
+                    for (int t = 0; t < m.n_terms; t++) {
+                        const MacTerm& tm = mterms[m.term0 + t];
+                        launch_pmult(c, tm.ct, tm.pt, m.out, 1, lv, t > 0, st);
+                    }
+                }
                 modup(c, Pd + s * z.ctw + z.nlN, z.ctw, 1, lv, coef3 + s * z.nlN, ext3 + s * z.extw, st);
                 launch_keyip(c, d_out_ks + k, 1, lv, st);
                 moddown_prepare(c, acc3 + s * z.accw, 1, lv, conv3 + s * z.ctw, st);
@@ -485,7 +560,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         } else {
             const MacRange& rg = chunk_rg[ch];
             launch_mac(c, d_mac + rg.first, d_terms, rg.count, rg.ct_terms, rg.pt_terms, rg.outputs, rg.ways, lv,
-                       st);
+                       st, dh);
+            if (dh) {
+                moddown_prepare(c, accO, cn, lv, convO, st);
+                launch_combine(c, d_dcb + n_base + c0, cn, lv, st);
+            }
             modup(c, Pd + z.nlN, z.ctw, cn, lv, coef3, ext3, st);
             launch_keyip_grouped(c, d_out_kg + kg_range[ch].first, d_out_ks, kg_range[ch].second, cn, lv, st);
             moddown_to_coef(c, acc3, cn, lv, conv3, st);
@@ -797,7 +876,7 @@ extern "C" size_t fe_plan_workspace_bytes(const fe_plan* p, uint32_t n_req, int 
 extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     if (!p || !info) return fail(FE_EINVAL, "null argument");
     const fe_ctx* c = p->c;
-    info->pt_bytes = (size_t)p->n_pt * (p->level + 1) * c->N * 8;
+    info->pt_bytes = (size_t)p->n_pt * (p->level + 1 + (p->dhoist ? c->k : 0)) * c->N * 8;
     info->in_bytes = (size_t)p->n_in * ct_words(c, p->level) * 8;
     info->out_bytes = (size_t)p->n_out * ct_words(c, p->level - 1) * 8;
     // default: the whole outer stage in one chunk, unless its scratch exceeds 8 GiB
@@ -809,6 +888,7 @@ extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     info->n_inner_rot = (uint32_t)p->inner.size();
     info->n_outer_rot = p->n_outer;
     info->bsgs_n1 = (uint32_t)p->bsgs_n1;
+    info->double_hoist = (uint32_t)p->dhoist;
     return FE_OK;
 }
 
@@ -826,7 +906,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     if (!c || !p || !W_host || !pt_dev) return fail(FE_EINVAL, "null argument");
     if (p->n_pt == 0) return FE_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int N = c->N, half = N / 2, nl = p->level + 1;
+    const int N = c->N, half = N / 2, nl = p->level + 1 + (p->dhoist ? c->k : 0);
     size_t wcount = p->kind == 0 ? (p->depthwise ? (size_t)p->Cin * p->K * p->K : (size_t)p->Cout * p->Cin * p->K * p->K)
                                  : (size_t)p->F_out * p->F_in;
     double* dW;
@@ -858,7 +938,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
             FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
             k_fc_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
         }
-        rc = encode_batch(c, z, cn, p->level, w_scale, (u64*)pt_dev + (size_t)s0 * nl * N, st);
+        rc = encode_batch(c, z, cn, p->level, w_scale, (u64*)pt_dev + (size_t)s0 * nl * N, st, p->dhoist != 0);
     }
     cudaFreeAsync(dW, st);
     cudaFreeAsync(z, st);
@@ -940,5 +1020,11 @@ extern "C" int fe_plan_set_mac_ways(fe_plan* p, uint32_t ways) {
     if (!p) return fail(FE_EINVAL, "null argument");
     if (ways != 1 && ways != 2 && ways != 4) return fail(FE_EINVAL, "mac ways must be 1, 2 or 4");
     p->mac_ways = (int)ways;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_set_hoisting(fe_plan* p, int double_hoist) {
+    if (!p) return fail(FE_EINVAL, "null argument");
+    p->dhoist = double_hoist ? 1 : 0;
     return FE_OK;
 }

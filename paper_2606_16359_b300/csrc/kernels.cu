@@ -137,6 +137,29 @@ __global__ void k_combine(const CombineItem* items, const Modulus* mods, const u
     }
 }
 
+__global__ void k_lift(const LiftItem* items, const Modulus* mods, const int* ks_limbs, const u64* pmod,
+                       const u64* pmod_sh, int level, int k, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const LiftItem it = items[blockIdx.z];
+    const int p = blockIdx.y, np = level + 1 + k, nq = level + 1;
+    const int mi = ks_limbs[p];
+    const u64 q = mods[mi].q;
+    const uint32_t src = it.galois == 1 ? (uint32_t)n : galois_perm(n, it.galois, logN);
+    u64 vb = 0, va = 0;
+    if (it.acc) {
+        vb = it.acc[((size_t)p << logN) + src];
+        va = it.acc[((size_t)(np + p) << logN) + src];
+    }
+    if (p < nq) {
+        vb = add_mod(vb, mul_shoup(it.ct[((size_t)p << logN) + src], pmod[p], pmod_sh[p], q), q);
+        if (!it.acc) va = mul_shoup(it.ct[((size_t)(nq + p) << logN) + src], pmod[p], pmod_sh[p], q);
+    }
+    it.out[((size_t)p << logN) + n] = vb;
+    it.out[((size_t)(np + p) << logN) + n] = va;
+}
+
 __global__ void k_combine_sum(const SumItem* items, const SumEntry* entries, const Modulus* mods,
                               const u64* pinv, const u64* pinv_sh, int level, int k, int logN) {
     const int N = 1 << logN;
@@ -211,18 +234,22 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 // ------------------------------------------------------------------------
 // PMult-MAC with the operand tiles streamed through shared memory by the bulk
 // async-copy engine.  One CTA = one item (up to W outputs sharing their
-// ciphertext terms), one limb, a tile of T coefficients (T = min(512, N),
-// T / 2 threads, two coefficients each).  For term t the CTA needs the tile of
-// c0 and c1 of the term's ciphertext and the tile of each output's plaintext,
-// (2 + n_out) T 8 bytes, copied with cp.async.bulk into stage t mod kStages and
-// signalled on that stage's mbarrier (arrive.expect_tx by the issuing thread,
-// complete_tx by the copies).  Thread 0 keeps kStages terms in flight: after
-// the CTA has consumed stage s (barrier), it issues term t + kStages into it.
-// Every wait is bounded (2 s of %globaltimer): on expiry the CTA sets bit 0 of
-// *status, stops issuing, waits (bounded) for the copies it already issued and
-// returns without writing.
-constexpr int kMacStages = 4;
+// ciphertext terms), one limb, a tile of T coefficients (T = min(512, N)):
+// T / 2 consumer threads (two coefficients each) and one producer warp.  For
+// term t the CTA needs the tiles of c0 and c1 of the term's ciphertext and of
+// each output's plaintext, (2 + n_out) T 8 bytes, copied with cp.async.bulk into
+// stage t mod S and signalled on the stage's "full" mbarrier (arrive.expect_tx
+// by the producer, complete_tx by the copies).  Each consumer warp arrives on
+// the stage's "empty" mbarrier when it has read the stage; the producer waits
+// for that before refilling it, so consumers never wait on one another.  Every
+// wait is bounded (2 s of %globaltimer): on expiry the thread sets bit 0 of
+// *status and stops; the producer then waits (bounded) for the copies it
+// issued that were never consumed, and nothing is written.
 constexpr int kMacTile = 512;
+constexpr int kMacStageBytes = 98304;  // shared memory for the stages of one CTA
+
+template <int W>
+__host__ __device__ constexpr int mac_stages() { return kMacStageBytes / ((2 + W) * kMacTile * 8); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -238,6 +265,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // bounded wait for phase `parity` of the barrier; false when the limit expired
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
@@ -262,53 +292,69 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 template <int W>
-__global__ void __launch_bounds__(kMacTile / 2) k_mac(const MacItem* items, const MacTerm* terms,
-                                                     const Modulus* mods, int level, int logN, int T,
-                                                     uint32_t* status) {
+__global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items, const MacTerm* terms,
+                                                          const Modulus* mods, const int* mod_map, int nl,
+                                                          int logN, int T, uint32_t* status) {
+    constexpr int S = mac_stages<W>();
     extern __shared__ __align__(128) unsigned char mac_smem[];
-    uint64_t* bars = (uint64_t*)mac_smem;                      // [kMacStages]
-    u64* stage0 = (u64*)(mac_smem + 128);                      // [kMacStages][2 + W][T]
+    uint64_t* full = (uint64_t*)mac_smem;  // [S]
+    uint64_t* empty = full + S;            // [S]
+    u64* stage0 = (u64*)(mac_smem + 256);  // [S][2 + W][T]
     const size_t stage_words = (size_t)(2 + W) * T;
-    const int N = 1 << logN;
     const MacItem it = items[blockIdx.z];
-    const int i = blockIdx.y, nq = level + 1;
-    const Modulus m = mods[i];
-    const size_t base = (size_t)blockIdx.x * T;                // first coefficient of the tile
-    const size_t off0 = ((size_t)i << logN) + base, off1 = ((size_t)(nq + i) << logN) + base;
+    const int i = blockIdx.y;
+    const Modulus m = mods[mod_map ? mod_map[i] : i];
+    const size_t base = (size_t)blockIdx.x * T;
+    const size_t off0 = ((size_t)i << logN) + base, off1 = ((size_t)(nl + i) << logN) + base;
     const uint32_t tile_bytes = (uint32_t)T * 8u;
-    const uint32_t stage_bytes = (uint32_t)(2 + it.n_out) * tile_bytes;
     const uint64_t limit = 2000000000ull;
     const int tid = threadIdx.x;
-    auto issue = [&](int t) {
-        const int s = t % kMacStages;
-        u64* st = stage0 + (size_t)s * stage_words;
-        const u64* ct = terms[it.term0[0] + t].ct;
-        mbar_expect_tx(&bars[s], stage_bytes);
-        bulk_g2s(st, ct + off0, tile_bytes, &bars[s]);
-        bulk_g2s(st + T, ct + off1, tile_bytes, &bars[s]);
-        for (int k = 0; k < it.n_out; k++) bulk_g2s(st + (2 + k) * T, terms[it.term0[k] + t].pt + off0, tile_bytes, &bars[s]);
-    };
+    const int n_cons = T / 2;                  // consumer threads
+    const int n_cons_warps = (n_cons + 31) / 32;
     if (tid == 0) {
-        for (int s = 0; s < kMacStages; s++) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], n_cons_warps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int issued = 0;
-    if (tid == 0)
-        for (; issued < kMacStages && issued < it.n_terms; issued++) issue(issued);
+    if (tid >= n_cons) {
+        // producer warp: lane 0 keeps up to S terms in flight
+        if (tid != n_cons) return;
+        const uint32_t stage_bytes = (uint32_t)(2 + it.n_out) * tile_bytes;
+        int issued = 0;
+        bool ok = true;
+        for (; issued < it.n_terms; issued++) {
+            const int s = issued % S;
+            if (issued >= S && !mbar_wait(&empty[s], (uint32_t)((issued / S - 1) & 1), limit)) {
+                ok = false;
+                break;
+            }
+            u64* st = stage0 + (size_t)s * stage_words;
+            const u64* ct = terms[it.term0[0] + issued].ct;
+            mbar_expect_tx(&full[s], stage_bytes);
+            bulk_g2s(st, ct + off0, tile_bytes, &full[s]);
+            bulk_g2s(st + T, ct + off1, tile_bytes, &full[s]);
+            for (int k = 0; k < it.n_out; k++)
+                bulk_g2s(st + (size_t)(2 + k) * T, terms[it.term0[k] + issued].pt + off0, tile_bytes, &full[s]);
+        }
+        if (!ok) {
+            atomicOr(status, 1u);
+            // the copies of the last S issued terms may still be in flight: wait (bounded)
+            for (int t = issued - S < 0 ? 0 : issued - S; t < issued; t++)
+                mbar_wait(&full[t % S], (uint32_t)((t / S) & 1), limit);
+        }
+        return;
+    }
     u128 a0[W], a1[W], b0[W], b1[W];  // (coefficient 2 tid, 2 tid + 1) x (c0, c1 part)
 #pragma unroll
     for (int k = 0; k < W; k++) a0[k] = a1[k] = b0[k] = b1[k] = 0;
-    bool ok = true;
-    int t_fail = it.n_terms;
     for (int t = 0; t < it.n_terms; t++) {
-        const int s = t % kMacStages;
-        if (!mbar_wait(&bars[s], (uint32_t)((t / kMacStages) & 1), limit)) ok = false;
-        // all threads agree on failure before anyone touches the stage or refills it
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            t_fail = t;
-            break;
+        const int s = t % S;
+        if (!mbar_wait(&full[s], (uint32_t)((t / S) & 1), limit)) {
+            atomicOr(status, 1u);
+            return;
         }
         const u64* st = stage0 + (size_t)s * stage_words;
         const ulonglong2 x0 = reinterpret_cast<const ulonglong2*>(st)[tid];
@@ -322,6 +368,8 @@ __global__ void __launch_bounds__(kMacTile / 2) k_mac(const MacItem* items, cons
             b0[k] += (u128)x1.x * p.x;
             b1[k] += (u128)x1.y * p.y;
         }
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
         if ((t & 15) == 15) {
 #pragma unroll
             for (int k = 0; k < W; k++) {
@@ -332,21 +380,7 @@ __global__ void __launch_bounds__(kMacTile / 2) k_mac(const MacItem* items, cons
                 b1[k] = reduce128(b1[k], m);
             }
         }
-        __syncthreads();  // stage s consumed by every thread
-        if (tid == 0 && issued < it.n_terms) issue(issued++);
     }
-    if (!ok) {
-        if (tid == 0) {
-            atomicOr(status, 1u);
-            // wait (bounded) for the copies this CTA issued and never consumed:
-            // terms t_fail .. issued - 1, one pending phase per stage
-            for (int t = t_fail; t < issued; t++)
-                mbar_wait(&bars[t % kMacStages], (uint32_t)((t / kMacStages) & 1), limit);
-        }
-        __syncthreads();
-        return;
-    }
-    (void)N;
 #pragma unroll
     for (int k = 0; k < W; k++) {
         if (k >= it.n_out) break;
@@ -501,6 +535,15 @@ void launch_combine(fe_ctx* c, const CombineItem* items, int n_items, int level,
     c->cnt.launches++;
 }
 
+void launch_lift(fe_ctx* c, const LiftItem* items, int n_items, int level, cudaStream_t st) {
+    if (!n_items) return;
+    const int np = level + 1 + c->k;
+    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * n_items * (2.0 * np + 2.0 * np + 2.0 * (level + 1)));
+    k_lift<<<grid_for(c->N, np, n_items), kB, 0, st>>>(items, c->d_mod, c->lv[level].d_ks_limbs, c->d_pmod,
+                                                       c->d_pmod_sh, level, c->k, c->logN);
+    c->cnt.launches++;
+}
+
 void launch_combine_sum(fe_ctx* c, const SumItem* items, const SumEntry* entries, int n_items,
                         int n_entries, int level, cudaStream_t st) {
     if (!n_items) return;
@@ -519,26 +562,28 @@ void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, in
 }
 
 void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
-                int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st) {
+                int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st, bool qp) {
     if (!n_items) return;
-    ProfScope ps(c, PK_MAC, st,
-                 8.0 * c->N * (level + 1) * (2.0 * n_ct_terms + (double)n_pt_terms + 2.0 * n_outputs));
+    const int nl = qp ? level + 1 + c->k : level + 1;
+    ProfScope ps(c, PK_MAC, st, 8.0 * c->N * nl * (2.0 * n_ct_terms + (double)n_pt_terms + 2.0 * n_outputs));
     const int T = std::min(kMacTile, c->N);
-    const dim3 g(c->N / T, level + 1, n_items);
+    const dim3 g(c->N / T, nl, n_items);
+    const int threads = T / 2 + 32;
     const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
-    const size_t smem = 128 + (size_t)kMacStages * (2 + w) * T * 8;
+    const size_t smem = 256 + (size_t)kMacStageBytes;
+    const int* mm = nl == level + 1 ? nullptr : c->lv[level].d_ks_limbs;
     if (w == 1) {
         static bool set1 = false;
-        if (!set1) set1 = cudaFuncSetAttribute(k_mac<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 3 * kMacTile * 8) == cudaSuccess;
-        k_mac<1><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+        if (!set1) set1 = cudaFuncSetAttribute(k_mac<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+        k_mac<1><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
     } else if (w == 2) {
         static bool set2 = false;
-        if (!set2) set2 = cudaFuncSetAttribute(k_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 4 * kMacTile * 8) == cudaSuccess;
-        k_mac<2><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+        if (!set2) set2 = cudaFuncSetAttribute(k_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+        k_mac<2><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
     } else {
         static bool set4 = false;
-        if (!set4) set4 = cudaFuncSetAttribute(k_mac<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 + kMacStages * 6 * kMacTile * 8) == cudaSuccess;
-        k_mac<4><<<g, T / 2, smem, st>>>(items, terms, c->d_mod, level, c->logN, T, c->d_status);
+        if (!set4) set4 = cudaFuncSetAttribute(k_mac<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+        k_mac<4><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
     }
     c->cnt.launches++;
 }

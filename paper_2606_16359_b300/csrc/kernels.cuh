@@ -67,6 +67,18 @@ struct SumItem {
     const u64* convsum;  // [2][l+1][N] NTT form, or null
 };
 
+// Double hoisting: a rotated copy kept on the key-switching basis Q_l * P,
+//   out = sigma_g((P c0, 0) + acc)   (acc: key inner product [2][l+1+k][N], ct: [2][l+1][N]),
+// or, with acc = null and galois = 1, the lift (P c0, P c1) of ct (zero on the
+// special limbs).  out: [2][l+1+k][N], NTT form.
+struct LiftItem {
+    const u64* acc;
+    const u64* ct;
+    u64* out;
+    uint32_t galois;
+};
+void launch_lift(fe_ctx* c, const LiftItem* items_dev, int n_items, int level, cudaStream_t st);
+
 // PMult-MAC item: up to kMacWays outputs whose term lists read the same
 // ciphertexts in the same order, out[k] = sum_t ct_t (x) pt_{k,t} with
 // ct_t = terms[term0[0] + t].ct and pt_{k,t} = terms[term0[k] + t].pt, so each
@@ -103,8 +115,11 @@ void launch_autosum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries
 // n_ct_terms: ciphertext loads (sum of n_terms over items); n_pt_terms: plaintext
 // loads (sum of n_terms x n_out); n_outputs: outputs written; ways: the largest
 // n_out of the items (1, 2 or 4 selects the kernel)
+// qp: operands on the key-switching basis Q_level * P (l+1+k limbs, ciphertext
+// polynomials [2][l+1+k][N], plaintexts [l+1+k][N]) instead of Q_level
 void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
-                int n_ct_terms, int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st);
+                int n_ct_terms, int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st,
+                bool qp = false);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st);
 void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,

@@ -239,7 +239,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         for (auto& t : th) t.join();
     }
     std::vector<u64> tw2((size_t)nm * N * 2), itw2((size_t)nm * N * 2);
-    std::vector<u64> ninv(nm), ninv_sh(nm), pinv(nm, 0), pinv_sh(nm, 0);
+    std::vector<u64> ninv(nm), ninv_sh(nm), pinv(nm, 0), pinv_sh(nm, 0), pmod(nm, 0), pmod_sh(nm, 0);
     {
         std::vector<std::thread> th;
         for (int i = 0; i < nm; i++)
@@ -269,6 +269,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         for (int j = 0; j < c->k; j++) P = h_mulmod(P, c->mod[c->L + 1 + j] % q, q);
         pinv[i] = h_invmod(P, q);
         pinv_sh[i] = shoup_of(pinv[i], q);
+        pmod[i] = P;
+        pmod_sh[i] = shoup_of(P, q);
     }
     std::vector<u64> qlinv((size_t)(c->L + 1) * (c->L + 1), 0), qlinv_sh(qlinv.size(), 0);
     for (int l = 1; l <= c->L; l++)
@@ -295,6 +297,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     size_t o_mod = pb.put(mods.data(), nm * sizeof(Modulus));
     size_t o_ninv = pb.put(ninv.data(), nm * 8), o_ninv_sh = pb.put(ninv_sh.data(), nm * 8);
     size_t o_pinv = pb.put(pinv.data(), nm * 8), o_pinv_sh = pb.put(pinv_sh.data(), nm * 8);
+    size_t o_pmod = pb.put(pmod.data(), nm * 8), o_pmod_sh = pb.put(pmod_sh.data(), nm * 8);
     size_t o_ql = pb.put(qlinv.data(), qlinv.size() * 8);
     size_t o_ql_sh = pb.put(qlinv_sh.data(), qlinv_sh.size() * 8);
     std::vector<int> ident(nm);
@@ -366,6 +369,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->d_ninv_sh = (u64*)(dpool + o_ninv_sh);
     c->d_pinv = (u64*)(dpool + o_pinv);
     c->d_pinv_sh = (u64*)(dpool + o_pinv_sh);
+    c->d_pmod = (u64*)(dpool + o_pmod);
+    c->d_pmod_sh = (u64*)(dpool + o_pmod_sh);
     c->d_qlinv = (u64*)(dpool + o_ql);
     c->d_qlinv_sh = (u64*)(dpool + o_ql_sh);
     c->d_identity_map = (int*)(dpool + o_ident);

@@ -47,6 +47,7 @@ struct fe_plan {
     int n_outer = 0;
     int bsgs_n1 = 0;  // baby steps of the outer rotations, 0: linear
     int mac_ways = 4;  // outputs sharing one MAC item (ciphertext loads), 1, 2 or 4
+    int dhoist = 0;    // 1: double hoisting (rotations and MAC on Q_l * P, one ModDown per sum)
     std::vector<int32_t> steps;
 };
 

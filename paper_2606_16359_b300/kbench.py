@@ -3,6 +3,7 @@
     python -m paper_2606_16359_b300.kbench ntt [--logN 16] [--limbs 512] [--reps 10]
     python -m paper_2606_16359_b300.kbench alu [--iters 400]
     python -m paper_2606_16359_b300.kbench keyswitch [--n 8] [--level 22] [--reps 5]
+    python -m paper_2606_16359_b300.kbench mac [--reps 5]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -109,9 +110,40 @@ def bench_keyswitch(ctx, torch, args):
             "peak_GBps": peak, "peak_source": src}
 
 
+def bench_mac(ctx, torch, args):
+    """The pointwise layer of the 14x14x512 -> 512 block (cpc = 128, 4 input and
+    4 output ciphertexts, level 22) with baby-step / giant-step n1 = 16, run in
+    timing mode (plaintexts from a pool of 48, keys aliased, smallest
+    workspace); reports the MAC launches' time and their plaintext and
+    ciphertext bytes."""
+    from paper_2606_16359_b300.tune import Tuner
+    lv = ctx.L - 1
+    t = Tuner(ctx, n_keys=4, n_pts=48)
+    lay = ctx.layout(14, 14, 512, 1, 1)
+    plan = ctx.plan_conv(lay, 512, 1, level=lv, bsgs_n1=16)
+    i = plan.info
+    ctx.evk_alias(t.evk, plan.steps)
+    x = torch.randint(0, 2 ** 35, (i.n_in_ct, 2, lv + 1, ctx.N), dtype=torch.int64, device="cuda")
+    out = ctx.empty_ct(i.n_out_ct, lv - 1)
+    ws = ctx.workspace(ctx.workspace_bytes(plan, 1, minimum=True))
+    for _ in range(2):
+        ctx.he_layer_timing(t.evk, plan, t.pts, t.n_pool, x, out, ws)
+    ctx.profile_begin("mac")
+    for _ in range(args.reps):
+        ctx.he_layer_timing(t.evk, plan, t.pts, t.n_pool, x, out, ws)
+    ms, n, b = ctx.profile_end()
+    peak, src = hbm_peak()
+    limb = ctx.N * 8
+    pt_bytes = i.n_pt * (lv + 1) * limb * args.reps
+    return {"kernel": "mac", "level": lv, "n_pt": i.n_pt, "launches": n, "ms": ms / args.reps,
+            "pt_GBps": pt_bytes / (ms / 1e3) / 1e9, "algorithmic_GBps": b / (ms / 1e3) / 1e9,
+            "hbm_frac": b / (ms / 1e3) / 1e9 / peak, "peak_GBps": peak, "peak_source": src,
+            "status": ctx.device_status()}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
@@ -127,7 +159,7 @@ def main(argv=None):
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
-        fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch}[args.what]
+        fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 

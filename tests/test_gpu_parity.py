@@ -141,7 +141,8 @@ def test_rotate_rescale_pmult_add_parity(which, tiny, ks2):
     assert np.array_equal(u64(ad), oracle_ct_array([ckks.add(pr, c, c) for c in octs]))
 
 
-def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1), bsgs_n1=0):
+def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1), bsgs_n1=0,
+                  double_hoist=False):
     pr, g = P.pr, P.g
     BS, C, H, _ = x.shape
     Cout = w.shape[0]
@@ -153,11 +154,12 @@ def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25
     octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, delta), 17, i) for i in range(olay.n_ct)]
     ocnt = henn.Counters()
     oout, oolay = henn.he_conv(pr, keys, octs, olay, w, stride=stride, depthwise=depthwise, cnt=ocnt,
-                               bsgs_n1=bsgs_n1)
+                               bsgs_n1=bsgs_n1, hoist="double" if double_hoist else "single")
     want = oracle_ct_array(oout)
 
     lay = g.layout(H, H, C, BS, S)
-    plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L, bsgs_n1=bsgs_n1)
+    plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L, bsgs_n1=bsgs_n1,
+                       double_hoist=double_hoist)
     assert sorted(plan.steps) == sorted(steps)
     assert plan.info.n_inner_rot + plan.info.n_outer_rot == ocnt.rot
     assert plan.info.n_pt == ocnt.pmult
@@ -364,3 +366,21 @@ def test_mac_ways_do_not_change_residues(tiny):
         outs.append(u64(g.he_conv(evk, plan, pt, ct, mode=1)))
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     assert g.device_status() == 0
+
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1,dw", [
+    (8, 3, 5, 3, 2, 2, 1, 0, False),
+    (6, 4, 4, 3, 1, 1, 1, 0, True),
+    (6, 20, 18, 3, 1, 1, 1, 4, False),
+    (8, 6, 9, 3, 1, 2, 2, 4, False),
+])
+def test_conv_parity_double_hoisted(tiny, H, C, Co, K, BS, S, stride, n1, dw):
+    """Double hoisting (rotations and MAC on Q P, one ModDown per partial sum):
+    residues bit-exact to the oracle's schedule in both paths, within 1e-3 of FP64."""
+    rng = np.random.default_rng(H * 7 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, ((C if dw else Co), 1 if dw else C, K, K))
+    plan, _ = run_conv_pair(tiny, x, w, S, stride, depthwise=dw, bsgs_n1=n1, double_hoist=True)
+    assert plan.info.double_hoist == 1
+    assert tiny.g.device_status() == 0

@@ -158,3 +158,29 @@ def test_pmult_rescale_and_cmult(keyed):
     assert np.abs(ckks.decrypt(pr, keys.sk, out) - z * w).max() < 1e-5
     sq = ckks.rescale(pr, ckks.cmult_relin(pr, keys, ct, ct))
     assert np.abs(ckks.decrypt(pr, keys.sk, sq) - z * z).max() < 1e-3
+
+
+def test_double_hoisted_rotation_moddown_equals_rotation(keyed):
+    """A rotation kept on Q P and brought down alone equals the rotation exactly;
+    the lifted ciphertext comes back exactly; a double-hoisted sum decrypts to
+    the sum of the products within the noise."""
+    pr, keys = keyed
+    z = np.random.default_rng(4).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 30), 2, 0)
+    ext = ckks.mod_up(pr, ct.c1, ct.level)
+    for r in (1, 5):
+        Vb, Va = ckks.rotate_ext_qp(pr, keys, ct, ext, r)
+        got = ckks.mod_down_ct(pr, Vb, Va, ct.level, ct.scale)
+        want = ckks.rotate_ext(pr, keys, ct, ext, r)
+        assert np.array_equal(got.as_array(), want.as_array())
+    Lb, La = ckks.lift_qp(pr, ct)
+    assert np.array_equal(ckks.mod_down_ct(pr, Lb, La, ct.level, ct.scale).as_array(), ct.as_array())
+    # a sum of double-hoisted products brought down once: Rot(ct,1) w1 + ct w2
+    w1 = np.random.default_rng(5).uniform(-1, 1, pr.N // 2)
+    w2 = np.random.default_rng(6).uniform(-1, 1, pr.N // 2)
+    dw = float(pr.moduli[pr.L])
+    terms = [(ckks.rotate_ext_qp(pr, keys, ct, ext, 1), ckks.encode_qp(pr, w1, pr.L, dw)),
+             (ckks.lift_qp(pr, ct), ckks.encode_qp(pr, w2, pr.L, dw))]
+    ab, aa = ckks.mac_qp(pr, pr.L, terms)
+    y = ckks.decrypt(pr, keys.sk, ckks.rescale(pr, ckks.mod_down_ct(pr, ab, aa, pr.L, ct.scale * dw)))
+    assert np.abs(y - (np.roll(z, -1) * w1 + z * w2)).max() < 1e-5

@@ -187,3 +187,32 @@ def test_he_conv_bsgs_matches_fp64_and_linear(tiny, H, C, Co, K, BS, S, stride, 
     assert cnt.rot == inner + giants
     assert cnt.modup == lay.groups * S * S + giants
     assert set(steps) >= {((a * lay.m + b) * lay.BS + i * lay.blk) for a in [0] for b in [0] for i in babies if i}
+
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1,dw", [
+    (8, 3, 5, 3, 2, 2, 1, 0, False),   # linear, K > S
+    (6, 4, 4, 3, 1, 1, 1, 0, True),    # depthwise, inner rotations only
+    (6, 20, 18, 3, 1, 1, 1, 4, False), # BSGS: baby steps double hoisted
+    (8, 6, 9, 3, 1, 2, 2, 4, False),   # BSGS with stride 2
+])
+def test_he_conv_double_hoisted_matches_fp64(tiny, H, C, Co, K, BS, S, stride, n1, dw):
+    """Double hoisting: the same convolution (within 1e-3 of FP64), the same
+    rotations and key switches, one ModDown per partial sum."""
+    pr, delta = tiny
+    rng = np.random.default_rng(H * 7 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, ((C if dw else Co), 1 if dw else C, K, K))
+    lay = fragment.Layout(pr.N, H, H, C, BS, S)
+    Cout = C if dw else Co
+    steps = henn.conv_rotation_steps(lay, C, Cout, K, stride, depthwise=dw, bsgs_n1=n1)
+    keys = ckks.KeySet(pr, 3, rot_steps=steps)
+    cts = encrypt_layout(pr, keys, lay, x, pr.L, delta)
+    c1, c2 = henn.Counters(), henn.Counters()
+    out, olay = henn.he_conv(pr, keys, cts, lay, w, stride=stride, depthwise=dw, cnt=c1, bsgs_n1=n1,
+                             hoist="double")
+    y = decrypt_layout(pr, keys, olay, out)
+    assert np.abs(y - plain.conv2d(x, w, stride=stride, depthwise=dw)).max() < 1e-3
+    out2, _ = henn.he_conv(pr, keys, cts, lay, w, stride=stride, depthwise=dw, cnt=c2, bsgs_n1=n1)
+    assert (c1.rot, c1.keyswitch, c1.pmult, c1.modup) == (c2.rot, c2.keyswitch, c2.pmult, c2.modup)
+    assert 0 < c1.moddown <= c1.pmult
