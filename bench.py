@@ -360,7 +360,7 @@ def run_ours(args, dist, rank, world, local):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "blocks": net.blocks, "keyswitches_per_step": ks_per_step,
                        "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
-                       "pw_schedule_bsgs_n1": net.schedule, "tune_ms": net.tune_ms,
+                       "schedule": net.schedule, "tune_ms": net.tune_ms,
                        "path": "graph" if use_graph else "batched",
                        "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
                        "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,

@@ -344,7 +344,8 @@ int fe_he_layer_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const
 
 /* For latency measurement only: run one conv / FC plan with its plaintexts
  * taken cyclically from a pool (term t uses pool plaintext t mod n_pool;
- * pt_pool_dev holds n_pool plaintexts [n_pool][level+1][N]).  The kernels,
+ * pt_pool_dev holds n_pool plaintexts of the plan's size, [n_pool][level+1][N],
+ * or [n_pool][level+1+k][N] under double hoisting).  The kernels,
  * launches and memory volume are those of fe_he_conv; the result is not the
  * layer's.  Errors as fe_he_conv. */
 int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_pool_dev,

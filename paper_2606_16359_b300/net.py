@@ -43,19 +43,24 @@ class MobileNetBlocks:
         for bi, (H, Cin, Cout) in enumerate(self.blocks):
             x, wd, wp = W.mobilenet_block(seed, H, Cin, Cout, BS=1, block=bi)
             lay = ctx.layout(H, H, Cin, 1, 1)
-            pdw = ctx.plan_conv(lay, Cin, 3, depthwise=True, level=L)
+            dh_dw, dh_pw = False, False
             if tuner is not None:
-                n1, times = tuner.conv_schedule(pdw.out_layout, Cout, 1, level=L - 1)
-                self.tune_ms.append({str(k): round(v, 3) for k, v in times.items()})
+                _, dh_dw, t_dw = tuner.conv_schedule(lay, Cin, 3, depthwise=True, level=L)
+            pdw = ctx.plan_conv(lay, Cin, 3, depthwise=True, level=L, double_hoist=dh_dw)
+            if tuner is not None:
+                n1, dh_pw, times = tuner.conv_schedule(pdw.out_layout, Cout, 1, level=L - 1)
+                self.tune_ms.append({"dw": {k: round(v, 3) for k, v in t_dw.items()},
+                                     "pw": {k: round(v, 3) for k, v in times.items()}})
             elif schedule == "linear":
                 n1 = 0
             else:
                 n1 = int(schedule)
-            ppw = ctx.plan_conv(pdw.out_layout, Cout, 1, level=L - 1, bsgs_n1=n1)
+            ppw = ctx.plan_conv(pdw.out_layout, Cout, 1, level=L - 1, bsgs_n1=n1, double_hoist=dh_pw)
             if tuner is not None:
                 ways, wt = tuner.mac_ways(ppw)
-                self.tune_ms[-1]["mac_ways"] = {str(k): round(v, 3) for k, v in wt.items()}
-            self.schedule.append(ppw.info.bsgs_n1)
+                self.tune_ms[-1]["pw_mac_ways"] = {str(k): round(v, 3) for k, v in wt.items()}
+            self.schedule.append({"dw_double_hoist": int(dh_dw), "pw_bsgs_n1": ppw.info.bsgs_n1,
+                                  "pw_double_hoist": int(dh_pw), "pw_mac_ways": getattr(ppw, "mac_ways", 4)})
             plans.append((lay, pdw, ppw, x, wd, wp))
         del tuner
         steps = sorted({s for _, a, b, *_ in plans for s in a.steps + b.steps})

@@ -117,7 +117,8 @@ class Measurer:
         self.evk = self.ctx.evk_gen(sk, 1, list(range(1, n_keys + 1)))
         nl = self.level + 1
         self.n_pool = n_pts
-        self.pts = torch.randint(0, 2 ** 35, (n_pts * nl * self.ctx.N,), dtype=torch.int64, device="cuda")
+        self.pts = torch.randint(0, 2 ** 35, (n_pts * (nl + self.ctx.k) * self.ctx.N,), dtype=torch.int64,
+                                 device="cuda")
 
     def plan(self, layer, S, Cin, Cout, n1=0):
         lay = self.ctx.layout(layer["H"], layer["W"], Cin, 1, S)

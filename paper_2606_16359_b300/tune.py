@@ -1,7 +1,8 @@
 """Autotuner: picks, per conv layer, the outer-rotation schedule (linear, or
-baby-step / giant-step with n1 baby steps) and the MAC tile (how many outputs
-share one kernel item's ciphertext loads) by timing every candidate on the
-GPU, and caches the choice per layer shape.
+baby-step / giant-step with n1 baby steps), the hoisting of the rotations
+(single, or double: kept on Q P with one ModDown per partial sum) and the MAC
+tile (how many outputs share one kernel item's ciphertext loads) by timing
+every candidate on the GPU, and caches the choice per layer shape.
 
 Candidates are timed through fe_he_layer_timing with plaintexts from a
 resident pool of random plaintexts and rotation keys aliased to a few
@@ -12,7 +13,7 @@ candidate computes the same convolution, and the residues of each schedule are
 fixed by its plan.
 
     t = Tuner(ctx)
-    n1, times = t.conv_schedule(lay, Cout, K, level=ctx.L)
+    n1, double, times = t.conv_schedule(lay, Cout, K, level=ctx.L)
 """
 import json
 import os
@@ -35,7 +36,9 @@ class Tuner:
         sk = ctx.sk_gen(99)
         self.evk = ctx.evk_gen(sk, 99, list(range(1, n_keys + 1)))
         self.n_pool = n_pts
-        self.pts = torch.randint(0, 2 ** 35, (n_pts * (ctx.L + 1) * ctx.N,), dtype=torch.int64, device="cuda")
+        # room for plaintexts on Q_L * P (double hoisting) at any level
+        self.pts = torch.randint(0, 2 ** 35, (n_pts * (ctx.L + 1 + ctx.k) * ctx.N,), dtype=torch.int64,
+                                 device="cuda")
         self.cache_file = cache_file
         if cache_file and os.path.exists(cache_file):
             with open(cache_file) as f:
@@ -59,29 +62,35 @@ class Tuner:
         return e0.elapsed_time(e1) / reps
 
     def conv_schedule(self, lay, Cout, K, stride=1, depthwise=False, level=None, reps=2):
-        """Fastest outer-rotation schedule of a conv layer: returns (n1, {n1: ms}),
-        n1 = 0 for linear outer rotations."""
+        """Fastest schedule of a conv layer: outer rotations (n1 baby steps, 0 =
+        linear) and hoisting (double = True: rotations and MAC on Q P).
+        Returns (n1, double, {"n1/double": ms})."""
         ctx = self.ctx
         level = ctx.L if level is None else level
         key = _key(ctx, lay, Cout, K, stride, depthwise, level)
         if key in _CACHE:
             c = _CACHE[key]
-            return c["n1"], {int(k): v for k, v in c["ms"].items()}
-        cands = [0]
+            return c["n1"], c["double"], dict(c["ms"])
+        n1s = [0]
         if not depthwise and lay.cpc > 1:
             n1 = 2
             while n1 <= lay.cpc:
-                cands.append(n1)
+                n1s.append(n1)
                 n1 *= 2
         times = {}
-        for n1 in cands:
-            plan = ctx.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=level, bsgs_n1=n1)
-            times[n1] = self.time_plan(plan, reps)
-            del plan
+        for n1 in n1s:
+            for dh in (False, True):
+                plan = ctx.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=level, bsgs_n1=n1,
+                                     double_hoist=dh)
+                if plan.info.n_inner_rot == 0 and dh:
+                    continue  # nothing to hoist
+                times[f"{n1}/{int(dh)}"] = self.time_plan(plan, reps)
+                del plan
         best = min(times, key=times.get)
-        _CACHE[key] = {"n1": best, "ms": times}
+        n1, dh = (int(v) for v in best.split("/"))
+        _CACHE[key] = {"n1": n1, "double": bool(dh), "ms": times}
         self._save()
-        return best, times
+        return n1, bool(dh), times
 
     def mac_ways(self, plan, reps=2):
         """Fastest MAC tile (outputs sharing one kernel item: 1, 2 or 4) for a
@@ -89,7 +98,7 @@ class Tuner:
         ctx = self.ctx
         i = plan.info
         key = json.dumps(["mac_ways", ctx.logN, ctx.L, plan.level, i.n_in_ct, i.n_out_ct, i.n_pt, i.n_inner_rot,
-                          i.n_outer_rot, i.bsgs_n1])
+                          i.n_outer_rot, i.bsgs_n1, i.double_hoist])
         if key in _CACHE:
             c = _CACHE[key]
             ctx.plan_set_mac_ways(plan, c["ways"])

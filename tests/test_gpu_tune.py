@@ -24,11 +24,11 @@ def test_tuner_times_all_candidates_and_tuned_blocks_decrypt():
         ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
         t = Tuner(ctx, n_keys=4, n_pts=8)
         lay = ctx.layout(8, 8, 64, 1, 1)  # cpc = 32 at N = 2^12
-        n1, times = t.conv_schedule(lay, 64, 1, level=ctx.L - 1)
-        assert set(times) == {0, 2, 4, 8, 16, 32} and n1 in times
-        assert times[n1] == min(times.values()) and all(v > 0 for v in times.values())
-        assert t.conv_schedule(lay, 64, 1, level=ctx.L - 1)[1] == times  # cached
-        plan = ctx.plan_conv(lay, 64, 1, level=ctx.L - 1, bsgs_n1=n1)
+        n1, dh, times = t.conv_schedule(lay, 64, 1, level=ctx.L - 1)
+        assert {int(k.split("/")[0]) for k in times} == {0, 2, 4, 8, 16, 32}
+        assert times[f"{n1}/{int(dh)}"] == min(times.values()) and all(v > 0 for v in times.values())
+        assert t.conv_schedule(lay, 64, 1, level=ctx.L - 1)[2] == times  # cached
+        plan = ctx.plan_conv(lay, 64, 1, level=ctx.L - 1, bsgs_n1=n1, double_hoist=dh)
         ways, wt = t.mac_ways(plan)
         assert set(wt) == {1, 2, 4} and wt[ways] == min(wt.values()) and plan.mac_ways == ways
         net = MobileNetBlocks(ctx, blocks=[(8, 64, 64), (6, 32, 48)], delta=p["delta"], schedule="tuned")
