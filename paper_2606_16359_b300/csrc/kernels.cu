@@ -18,6 +18,8 @@ inline dim3 grid_for(int N, int y, int z = 1) { return dim3((N + kB - 1) / kB, y
 // Base conversion with centred digits (see BConvTab).
 // One thread per (coefficient, polynomial).
 // ------------------------------------------------------------------------
+// kS = number of source moduli (compile time, so that the digits stay in registers)
+template <int kS>
 __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int logN,
                         const u64* in, size_t in_stride, int in_pos_base, u64* out,
                         size_t out_stride, int copy_src) {
@@ -26,9 +28,10 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
     if (n >= N) return;
     const u64* ip = in + blockIdx.y * in_stride;
     u64* op = out + blockIdx.y * out_stride;
-    u64 y[8];
+    u64 y[kS];
     int neg = 0;
-    for (int i = 0; i < t.n_src; i++) {
+#pragma unroll
+    for (int i = 0; i < kS; i++) {
         int mi = t.src[i];
         u64 b = mods[mi].q;
         u64 x = ip[((size_t)(ext_pos(mi, L, level) - in_pos_base) << logN) + n];
@@ -40,7 +43,9 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
     for (int d = 0; d < t.n_dst; d++) {
         int mt = t.dst[d];
         u128 acc = (u128)t.negB[d] * (u64)neg;
-        for (int i = 0; i < t.n_src; i++) acc += (u128)y[i] * t.mat[d * t.n_src + i];
+        const u64* row = t.mat + d * kS;
+#pragma unroll
+        for (int i = 0; i < kS; i++) acc += (u128)y[i] * row[i];
         op[((size_t)ext_pos(mt, L, level) << logN) + n] = reduce128(acc, mods[mt]);
     }
 }
@@ -73,34 +78,45 @@ __global__ void k_keyip(const KsItem* items, const Modulus* mods, int L, int lev
     it.acc[((size_t)(np + p) << logN) + n] = reduce128(aa, m);
 }
 
-// key-stationary form: blockIdx.z = group of items that share one key
-__global__ void k_keyip_grouped(const KsGroup* groups, const KsItem* items, const Modulus* mods,
-                                int L, int level, int k, int logN, int n_mod) {
+// key-stationary form: blockIdx.z = group of items that share one key; kD =
+// number of digits (compile time, so that the key words stay in registers).
+// Each thread handles two consecutive coefficients with 16-byte accesses.
+template <int kD>
+__global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups, const KsItem* items,
+                                                          const Modulus* mods, int L, int level, int k,
+                                                          int logN, int n_mod) {
     const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (n >= N) return;
     const KsGroup gr = groups[blockIdx.z];
     const int p = blockIdx.y;
     const int np = level + 1 + k;
     const int mi = p <= level ? p : L + 1 + (p - level - 1);
-    const int dnum = (level + 1 + k - 1) / k;
     const Modulus m = mods[mi];
-    u64 kb[16], ka[16];
-    for (int j = 0; j < dnum; j++) {
+    ulonglong2 kb[kD], ka[kD];
+#pragma unroll
+    for (int j = 0; j < kD; j++) {
         const u64* b = gr.key + ((size_t)(j * 2 * n_mod + mi) << logN);
-        kb[j] = b[n];
-        ka[j] = b[((size_t)n_mod << logN) + n];
+        kb[j] = *reinterpret_cast<const ulonglong2*>(b + n);
+        ka[j] = *reinterpret_cast<const ulonglong2*>(b + ((size_t)n_mod << logN) + n);
     }
+    const size_t ob = ((size_t)p << logN) + n, oa = ((size_t)(np + p) << logN) + n;
     for (int t = 0; t < gr.n_items; t++) {
         const KsItem it = items[gr.item0 + t];
-        u128 ab = 0, aa = 0;
-        for (int j = 0; j < dnum; j++) {
-            u64 e = it.ext[((size_t)(j * np + p) << logN) + n];
-            ab += (u128)e * kb[j];
-            aa += (u128)e * ka[j];
+        ulonglong2 e[kD];
+#pragma unroll
+        for (int j = 0; j < kD; j++)
+            e[j] = *reinterpret_cast<const ulonglong2*>(it.ext + ((size_t)(j * np + p) << logN) + n);
+        u128 bx = 0, by = 0, ax = 0, ay = 0;
+#pragma unroll
+        for (int j = 0; j < kD; j++) {
+            bx += (u128)e[j].x * kb[j].x;
+            by += (u128)e[j].y * kb[j].y;
+            ax += (u128)e[j].x * ka[j].x;
+            ay += (u128)e[j].y * ka[j].y;
         }
-        it.acc[((size_t)p << logN) + n] = reduce128(ab, m);
-        it.acc[((size_t)(np + p) << logN) + n] = reduce128(aa, m);
+        *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce128(bx, m), reduce128(by, m));
+        *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce128(ax, m), reduce128(ay, m));
     }
 }
 
@@ -503,8 +519,18 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
                   cudaStream_t st) {
     if (n_poly == 0) return;
     ProfScope ps(c, PK_BCONV, st, 8.0 * c->N * n_poly * (t.n_src * (copy_src ? 2 : 1) + t.n_dst));
-    k_bconv<<<grid_for(c->N, n_poly), kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,
-                                                   in_pos_base, out, out_stride, copy_src ? 1 : 0);
+    const dim3 g = grid_for(c->N, n_poly);
+    const int cs = copy_src ? 1 : 0;
+#define FE_BCONV(S)                                                                                   \
+    case S:                                                                                           \
+        k_bconv<S><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride, in_pos_base, out, \
+                                     out_stride, cs);                                                 \
+        break;
+    switch (t.n_src) {
+        FE_BCONV(1) FE_BCONV(2) FE_BCONV(3) FE_BCONV(4) FE_BCONV(5) FE_BCONV(6) FE_BCONV(7) FE_BCONV(8)
+        default: break;  // n_src <= k <= 8 (checked at context creation)
+    }
+#undef FE_BCONV
     c->cnt.launches++;
 }
 
@@ -522,8 +548,17 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
     if (!n_groups) return;
     const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
     ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + (double)n_items * (dn + 2)));
-    k_keyip_grouped<<<grid_for(c->N, level + 1 + c->k, n_groups), kB, 0, st>>>(
-        groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod);
+    const dim3 g((c->N / 2 + kB - 1) / kB, level + 1 + c->k, n_groups);  // two coefficients per thread
+#define FE_KEYIP(D)                                                                                   \
+    case D:                                                                                           \
+        k_keyip_grouped<D><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod); \
+        break;
+    switch (dn) {
+        FE_KEYIP(1) FE_KEYIP(2) FE_KEYIP(3) FE_KEYIP(4) FE_KEYIP(5) FE_KEYIP(6) FE_KEYIP(7) FE_KEYIP(8)
+        FE_KEYIP(9) FE_KEYIP(10) FE_KEYIP(11) FE_KEYIP(12) FE_KEYIP(13) FE_KEYIP(14) FE_KEYIP(15) FE_KEYIP(16)
+        default: break;  // dnum <= 16 (checked at context creation)
+    }
+#undef FE_KEYIP
     c->cnt.launches++;
 }
 
