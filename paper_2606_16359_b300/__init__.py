@@ -115,6 +115,7 @@ SIGNATURES = {
     "fe_ctx_create": (cint, [P(FeParams), P(vp)]),
     "fe_ctx_destroy": (None, [vp]),
     "fe_ctx_moduli": (cint, [vp, P(u64)]),
+    "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -343,6 +344,9 @@ class Context:
         out = torch.empty((n, self.N // 2), dtype=torch.float64, device="cuda")
         check(load().fe_decrypt_decode(self.handle, _ptr(sk), _ptr(ct), n, level, scale, _ptr(out), _stream()))
         return out
+
+    def set_ntt_radix(self, radix):
+        check(load().fe_ctx_set_ntt_radix(self.handle, radix))
 
     # -- primitives ------------------------------------------------------------------
     def ntt(self, data, first_mod=0, inverse=False):

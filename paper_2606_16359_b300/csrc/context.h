@@ -66,6 +66,7 @@ struct fe_ctx {
     fe_params prm;
     int logN, N, L, k, n_mod, dnum;
     int max_mod_bits;  // bit length of the largest modulus
+    int ntt_radix = 8;  // elements per thread per NTT round (8 or 16; 16 compiled for N = 2^14, 2^16)
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;
     fe::Modulus* d_mod;             // [n_mod]

@@ -31,7 +31,7 @@ namespace fe {
 namespace {
 
 constexpr int kTile = 4096;  // elements per CTA tile (32 KiB)
-constexpr int kE = 8;        // elements per thread per round
+constexpr int kE = 8;        // elements per thread per round (radix 8; radix 16: 2 kE)
 
 struct NttArgs {
     const u64* src;      // first-pass source (may equal dst)
@@ -61,24 +61,26 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wq, u64 q) {
 // The three stage slots are unrolled so every register index is a compile-time constant.
 // kNoRed (forward only, all moduli < 2^58): no reduction inside the transform;
 // each stage adds less than 2q, so values stay below (1 + 2 * 17) q < 2^64.
-template <bool kInv, bool kNoRed>
-__device__ __forceinline__ void round_stages(u64 (&v)[kE], int blk, int lo, int nst, int E, int logn,
+// kLE = log2 of the elements a thread holds per round (3: radix 8, 4: radix 16).
+template <bool kInv, bool kNoRed, int kLE>
+__device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo, int nst, int E, int logn,
                                              int tw_line, const ulonglong2* __restrict__ tw, u64 q) {
+    constexpr int kEE = 1 << kLE, kHalf = kEE / 2;
     const u64 q2 = 2 * q;
 #pragma unroll
-    for (int si = 0; si < 3; si++) {
-        const int st = kInv ? si : 2 - si;  // forward: large distances first
+    for (int si = 0; si < kLE; si++) {
+        const int st = kInv ? si : kLE - 1 - si;  // forward: large distances first
         if (st >= nst) continue;
         const int d = 1 << st;
         const int lt = lo + st;
-        const int K = (tw_line << (logn - 1 - lt)) + (blk << (2 - st));
+        const int K = (tw_line << (logn - 1 - lt)) + (blk << (kLE - 1 - st));
         const int cnt = max(1, E >> (st + 1));
-        ulonglong2 w[4];
+        ulonglong2 w[kHalf];
 #pragma unroll
-        for (int i = 0; i < 4; i++)
-            if (i < (4 >> st) && i < cnt) w[i] = tw[K + i];
+        for (int i = 0; i < kHalf; i++)
+            if (i < (kHalf >> st) && i < cnt) w[i] = tw[K + i];
 #pragma unroll
-        for (int r = 0; r < kE; r++) {
+        for (int r = 0; r < kEE; r++) {
             if ((r & d) || r + d >= E) continue;
             const ulonglong2 ww = w[r >> (st + 1)];
             if (!kInv) {
@@ -100,8 +102,9 @@ __device__ __forceinline__ void round_stages(u64 (&v)[kE], int blk, int lo, int 
 // kCol: column pass (lines = columns of length N1) else row pass (lines = rows of length N2).
 // kLogN > 0 fixes the ring degree at compile time so that the tile geometry, the
 // round structure and every shift fold into constants; kLogN = 0 reads it at run time.
-template <int kLogN, bool kInv, bool kCol, bool kNoRed>
+template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE>
 __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
+    constexpr int kEE = 1 << kLE;
     extern __shared__ u64 tile[];
     const int logN = kLogN ? kLogN : a.logN;
     const int logN2 = kLogN ? kLogN / 2 : a.logN2;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     const int n = 1 << logn;
     const int lines = kCol ? min(kTile / N1, N2) : min(kTile / N2, N1);
     const int tiles_per_limb = (kCol ? N2 : N1) / lines;
-    const int E = min(kE, n);
+    const int E = min(kEE, n);
     const int tpl = n / E;  // threads per line
     const int nthr = lines * tpl;
     const int nthreads = kLogN ? (nthr > 32 ? nthr : 32) : (int)blockDim.x;
@@ -169,32 +172,32 @@ __global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
     const int line = kCol ? tid % lines : tid / tpl;
     const int j = kCol ? tid / lines : tid % tpl;
     const int tw_line = kCol ? 1 : (N1 + l0 + line);
-    // rounds: exponent chunks of 3 from the top, remainder at the bottom
-    const int nr = (logn + 2) / 3;
+    // rounds: exponent chunks of kLE from the top, remainder at the bottom
+    const int nr = (logn + kLE - 1) / kLE;
 #pragma unroll
     for (int rr = 0; rr < nr; rr++) {
         const int k = kInv ? nr - 1 - rr : rr;  // chunk index from the top
-        const int hi = logn - 1 - 3 * k;        // largest exponent of the chunk
-        const int lo = max(0, hi - 2);
+        const int hi = logn - 1 - kLE * k;      // largest exponent of the chunk
+        const int lo = max(0, hi - (kLE - 1));
         const int nst = hi - lo + 1;
-        u64 v[kE];
+        u64 v[kEE];
         int base = 0;
         if (tid < nthr) {
-            // thread j of the line: block (j >> lo), offset (j & (s - 1)), block size 8 s
+            // thread j of the line: block (j >> lo), offset (j & (s - 1)), block size kEE s
             int blk = j >> lo;
-            base = (blk << (lo + 3)) + (j & ((1 << lo) - 1));
-            if (E < kE) base = blk = 0;
+            base = (blk << (lo + kLE)) + (j & ((1 << lo) - 1));
+            if (E < kEE) base = blk = 0;
 #pragma unroll
-            for (int r = 0; r < kE; r++) {
+            for (int r = 0; r < kEE; r++) {
                 const int x = base + (r << lo);
                 v[r] = (r < E) ? (kCol ? tile[x * lines + line] : tile[RIDX(line, x)]) : 0;
             }
-            round_stages<kInv, kNoRed>(v, blk, lo, nst, E, logn, tw_line, tw, q);
+            round_stages<kInv, kNoRed, kLE>(v, blk, lo, nst, E, logn, tw_line, tw, q);
         }
         __syncthreads();
         if (tid < nthr) {
 #pragma unroll
-            for (int r = 0; r < kE; r++) {
+            for (int r = 0; r < kEE; r++) {
                 if (r >= E) break;
                 const int x = base + (r << lo);
                 if (kCol) tile[x * lines + line] = v[r];
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __res
 #pragma unroll 1
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int k = 0; k < 5; k++) round_stages<false, true>(v, 0, 0, 3, kE, 3, 1, tw, q);
+        for (int k = 0; k < 5; k++) round_stages<false, true, 3>(v, 0, 0, 3, kE, 3, 1, tw, q);
 #pragma unroll
         for (int r = 0; r < kE; r++) v[r] -= __umul64hi(v[r], qinv64) * q;
     }
@@ -280,19 +283,23 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
     return a;
 }
 
-int threads_for(int lines, int n) { return std::max(32, lines * (n / std::min(kE, n))); }
+int threads_for(int lines, int n, int E) { return std::max(32, lines * (n / std::min(E, n))); }
 
-template <int kLogN, bool kInv, bool kCol>
+template <int kLogN, bool kInv, bool kCol, int kLE = 3>
 void launch_one(bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
     if (nored && !kInv)
-        ntt_pass<kLogN, kInv, kCol, true><<<g, t, sm, st>>>(a, first);
+        ntt_pass<kLogN, kInv, kCol, true, kLE><<<g, t, sm, st>>>(a, first);
     else
-        ntt_pass<kLogN, kInv, kCol, false><<<g, t, sm, st>>>(a, first);
+        ntt_pass<kLogN, kInv, kCol, false, kLE><<<g, t, sm, st>>>(a, first);
 }
 
 // compile-time ring degrees for the production sizes, run-time geometry otherwise
+// radix 16 (le = 4) is compiled for the production ring degrees 2^14 and 2^16
 template <bool kInv, bool kCol>
-void launch_pass(int logN, bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
+void launch_pass(int logN, bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first,
+                 int le) {
+    if (le == 4 && logN == 16) return launch_one<16, kInv, kCol, 4>(nored, g, t, sm, st, a, first);
+    if (le == 4 && logN == 14) return launch_one<14, kInv, kCol, 4>(nored, g, t, sm, st, a, first);
     switch (logN) {
         case 10: launch_one<10, kInv, kCol>(nored, g, t, sm, st, a, first); break;
         case 11: launch_one<11, kInv, kCol>(nored, g, t, sm, st, a, first); break;
@@ -316,26 +323,27 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
     // algorithmic bytes of a limb transform, 2 N w, split over its two passes
     const double bytes = 8.0 * limbs * N;
-    const int tc = threads_for(C, N1), tr = threads_for(R, N2);
+    const int le = (c->ntt_radix == 16 && (c->logN == 14 || c->logN == 16)) ? 4 : 3;
+    const int tc = threads_for(C, N1, 1 << le), tr = threads_for(R, N2, 1 << le);
     const bool nored = c->max_mod_bits <= 58;
     const dim3 gc(limbs * (N2 / C)), gr(limbs * (N1 / R));
     if (!kInv) {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, true>(c->logN, nored, gc, tc, smc, st, a, 1);
+            launch_pass<false, true>(c->logN, nored, gc, tc, smc, st, a, 1, le);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, false>(c->logN, nored, gr, tr, smr, st, a, 0);
+            launch_pass<false, false>(c->logN, nored, gr, tr, smr, st, a, 0, le);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, false>(c->logN, false, gr, tr, smr, st, a, 1);
+            launch_pass<true, false>(c->logN, false, gr, tr, smr, st, a, 1, le);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, true>(c->logN, false, gc, tc, smc, st, a, 0);
+            launch_pass<true, true>(c->logN, false, gc, tc, smc, st, a, 0, le);
         }
     }
     c->cnt.ntt += limbs;
@@ -366,3 +374,10 @@ void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSe
 }
 
 }  // namespace fe
+
+extern "C" int fe_ctx_set_ntt_radix(fe_ctx* c, int radix) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (radix != 8 && radix != 16) return fe::fail(FE_EINVAL, "NTT radix must be 8 or 16");
+    c->ntt_radix = radix;
+    return FE_OK;
+}

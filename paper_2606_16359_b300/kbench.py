@@ -4,6 +4,7 @@
     python -m paper_2606_16359_b300.kbench alu [--iters 400]
     python -m paper_2606_16359_b300.kbench keyswitch [--n 8] [--level 22] [--reps 5]
     python -m paper_2606_16359_b300.kbench mac [--reps 5]
+    python -m paper_2606_16359_b300.kbench aac [--reps 5]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -39,6 +40,7 @@ def _events(torch):
 
 
 def bench_ntt(ctx, torch, args):
+    ctx.set_ntt_radix(args.radix)
     N, nm = ctx.N, ctx.n_mod
     n_poly = max(1, (args.limbs + nm - 1) // nm)
     limbs = n_poly * nm
@@ -64,7 +66,7 @@ def bench_ntt(ctx, torch, args):
     peak, src = hbm_peak()
     for v in out.values():
         v["hbm_frac"] = v["GBps"] / peak
-    return {"kernel": "ntt", "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
+    return {"kernel": "ntt", "radix": args.radix, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
             "peak_GBps": peak, "peak_source": src, **out}
 
 
@@ -141,15 +143,62 @@ def bench_mac(ctx, torch, args):
             "status": ctx.device_status()}
 
 
+def bench_aac(ctx, torch, args):
+    """Arch-aware Ciphertext Compression on the residual-shortcut shapes of
+    Table 7 (8 valid channels after a channel-reducing layer, N = 2^16, level
+    22): the compression (log2(cpc / 8) rotate-and-adds per ciphertext) against
+    the next 1x1 conv 8 -> Nout with the replicated input (8 diagonals) and
+    without compression (every diagonal of the sparse input).  The convs run
+    in timing mode (plaintext pool, aliased keys); the compression with real
+    keys.  Overhead = compression / (compression + conv with AAC)."""
+    from paper_2606_16359_b300.tune import Tuner
+    lv = ctx.L - 1
+    t = Tuner(ctx, n_keys=4, n_pts=32)
+    sk = ctx.sk_gen(3)
+    rows = []
+    for nin, nout, H in ((64, 128, 56), (128, 256, 28), (256, 512, 14), (512, 512, 7)):
+        lay = ctx.layout(H, H, 8, 1, 1)
+        cpc = lay.cpc
+        steps = []
+        s = 8
+        while s < cpc:
+            steps.append(-s * lay.m * lay.m * lay.BS)
+            s *= 2
+        evk = ctx.evk_gen(sk, 3, steps) if steps else None
+        ct = torch.randint(0, 2 ** 35, (lay.n_ct, 2, lv + 1, ctx.N), dtype=torch.int64, device="cuda")
+        t_cmp = 0.0
+        if evk is not None:
+            ctx.compress(evk, lay, 8, ct, lv)
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch)
+            e0.record()
+            for _ in range(args.reps):
+                ctx.compress(evk, lay, 8, ct, lv)
+            e1.record()
+            torch.cuda.synchronize()
+            t_cmp = e0.elapsed_time(e1) / args.reps
+        p_aac = ctx.plan_conv(lay, nout, 1, level=lv, in_period=8 if cpc > 8 else 0)
+        p_raw = ctx.plan_conv(lay, nout, 1, level=lv)
+        t_aac = t.time_plan(p_aac, args.reps)
+        t_raw = t.time_plan(p_raw, args.reps)
+        rows.append({"shape": [nin, 8, nout, H], "cpc": cpc, "util_without": min(1.0, 8 / cpc), "util_with": 1.0,
+                     "compress_ms": t_cmp, "conv_with_aac_ms": t_aac, "conv_without_ms": t_raw,
+                     "outer_rot_with": p_aac.info.n_outer_rot, "outer_rot_without": p_raw.info.n_outer_rot,
+                     "overhead_pct": 100 * t_cmp / max(1e-9, t_cmp + t_aac),
+                     "speedup": t_raw / max(1e-9, t_cmp + t_aac)})
+    return {"kernel": "aac", "level": lv, "rows": rows, "status": ctx.device_status()}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "aac"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--iters", type=int, default=400)
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--level", type=int, default=22)
+    ap.add_argument("--radix", type=int, default=8, help="NTT elements per thread per round (8 or 16)")
     args = ap.parse_args(argv)
     import torch
 
@@ -159,7 +208,8 @@ def main(argv=None):
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
-        fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac}[args.what]
+        fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
+              "aac": bench_aac}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 
