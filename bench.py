@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--cpu-rotations", type=int, default=4)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile", default="auto", help="kernel class timed for the roofline, or 'auto'")
+    ap.add_argument("--batch", type=int, default=1, help="independent encrypted inputs per block per step")
     ap.add_argument("--schedule", default="tuned",
                     help="outer rotations of the pointwise layers: tuned (autotuner), linear, or n1")
     ap.add_argument("--ncu-step", action="store_true",
@@ -211,7 +212,7 @@ def run_ours(args, dist, rank, world, local):
 
     t_setup = time.perf_counter()
     ctx = fe.Context(**PARAMS)
-    net = MobileNetBlocks(ctx, delta=DELTA, schedule=args.schedule)
+    net = MobileNetBlocks(ctx, delta=DELTA, schedule=args.schedule, batch=args.batch)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     ks_per_step = net.keyswitches_per_step
@@ -230,7 +231,8 @@ def run_ours(args, dist, rank, world, local):
     # correctness of one step against FP64 (untimed)
     net.run(mode=1)
     torch.cuda.synchronize()
-    errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(len(net.blocks))]
+    errs = [float(np.abs(net.decrypt_block(b, r) - net.reference_block(b, r)).max())
+            for b in range(len(net.blocks)) for r in range(net.batch)]
 
     use_graph = not args.no_graph
     if use_graph:
@@ -358,7 +360,8 @@ def run_ours(args, dist, rank, world, local):
             "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "blocks": net.blocks, "keyswitches_per_step": ks_per_step,
+            "config": {"workload": WORKLOAD, "blocks": net.blocks, "inputs_per_block": net.batch,
+                       "ms_per_input": ms_step / net.batch, "keyswitches_per_step": ks_per_step,
                        "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
                        "schedule": net.schedule, "tune_ms": net.tune_ms,
                        "path": "graph" if use_graph else "batched",

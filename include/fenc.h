@@ -405,13 +405,23 @@ int fe_compress(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uint32_t c
  * (stream capture on `stream`, which must not be the legacy default stream).
  * Layer i reads ins_host[i], writes outs_host[i] and uses plaintexts pts_host[i];
  * layers run in the order given, so a layer may read an earlier layer's output.
- * Every layer gets its own slice of workspace_dev (the sum of the plans'
- * workspace_bytes) and its item tables are uploaded there before capture, so the
- * graph replays kernels only.  Counters are not advanced by graph launches. */
+ * Every layer's item tables are uploaded into workspace_dev before capture (its
+ * size: fe_graph_workspace_bytes(plans, n, 1)), so the graph replays kernels
+ * only.  Counters are not advanced by graph launches. */
 int fe_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
                      const void* const* pts_host, const void* const* ins_host,
                      void* const* outs_host, uint32_t n, void* workspace_dev,
                      size_t workspace_bytes, void* stream, fe_graph** out);
+/* The same for n_req requests per layer (fe_he_layer_batch layout: layer i reads
+ * [n_req][n_in_ct] ciphertexts at ins_host[i] and writes [n_req][n_out_ct] at
+ * outs_host[i]).  The workspace holds every layer's item tables and one data
+ * region (rotated copies, partial sums, scratch) that the layers share, since
+ * they run in order; its size is fe_graph_workspace_bytes(plans, n, n_req). */
+size_t fe_graph_workspace_bytes(const fe_plan* const* plans_host, uint32_t n, uint32_t n_req);
+int fe_graph_capture_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
+                           const void* const* pts_host, const void* const* ins_host,
+                           void* const* outs_host, uint32_t n, uint32_t n_req, void* workspace_dev,
+                           size_t workspace_bytes, void* stream, fe_graph** out);
 int fe_graph_launch(fe_graph* graph, void* stream);
 void fe_graph_destroy(fe_graph* graph);
 

@@ -152,6 +152,8 @@ SIGNATURES = {
     "fe_compress_workspace_bytes": (sz, [vp, u32, u32]),
     "fe_compress": (cint, [vp, vp, P(FeLayout), u32, vp, u32, u32, vp, vp, sz, vp]),
     "fe_graph_capture": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, vp, sz, vp, P(vp)]),
+    "fe_graph_capture_batch": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, u32, vp, sz, vp, P(vp)]),
+    "fe_graph_workspace_bytes": (sz, [P(vp), u32, u32]),
     "fe_graph_launch": (cint, [vp, vp]),
     "fe_graph_destroy": (None, [vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
@@ -502,15 +504,20 @@ class Context:
                                  _ptr(ws), ws.numel() * 8, _stream()))
         return out
 
-    def graph_capture(self, evk, plans, pts, ins, outs, ws):
+    def graph_workspace_bytes(self, plans, n_req=1):
+        n = len(plans)
+        parr = (vp * n)(*[p.handle.value for p in plans])
+        return int(load().fe_graph_workspace_bytes(parr, n, n_req))
+
+    def graph_capture(self, evk, plans, pts, ins, outs, ws, n_req=1):
         n = len(plans)
         parr = (vp * n)(*[p.handle.value for p in plans])
         ptarr = (vp * n)(*[t.data_ptr() for t in pts])
         iarr = (vp * n)(*[t.data_ptr() for t in ins])
         oarr = (vp * n)(*[t.data_ptr() for t in outs])
         h = vp()
-        check(load().fe_graph_capture(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, _ptr(ws), ws.numel() * 8,
-                                      _stream(), ctypes.byref(h)))
+        check(load().fe_graph_capture_batch(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, n_req, _ptr(ws),
+                                            ws.numel() * 8, _stream(), ctypes.byref(h)))
         return Graph(h, (plans, pts, ins, outs, ws))
 
     def profile_begin(self, kind):

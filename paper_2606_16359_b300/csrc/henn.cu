@@ -180,7 +180,7 @@ int layout_fill(int N, fe_layout* l) {
     return FE_OK;
 }
 
-size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
+size_t plan_data_bytes(const fe_plan* p, size_t chunk, size_t R) {
     const fe_ctx* c = p->c;
     Sizes z = sizes_of(c, p->level);
     size_t n_mu = p->modup_cts.size(), n_in_rot = p->inner.size();
@@ -193,7 +193,21 @@ size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
                    R * p->n_out * z.ctw;
     size_t rs = rescale_tmp_words(c, (int)(R * p->n_out), p->level);
     size_t words = persist + std::max(std::max(std::max(inner, outer), rs), base);
-    return words * 8 + item_bytes(p, chunk, R) + 32 * 256;
+    return words * 8 + 24 * 256;
+}
+
+size_t plan_table_bytes(const fe_plan* p, size_t chunk, size_t R) { return item_bytes(p, chunk, R); }
+
+size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
+    return plan_data_bytes(p, chunk, R) + plan_table_bytes(p, chunk, R);
+}
+
+// the outer-rotation chunk run_plan takes: as large as the data region allows
+size_t plan_chunk(const fe_plan* p, size_t R, int mode, size_t data_bytes, bool data_only) {
+    size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, R * p->n_outer);
+    auto need = [&](size_t ch) { return data_only ? plan_data_bytes(p, ch, R) : plan_workspace(p, ch, R); };
+    while (chunk > 1 && need(chunk) > data_bytes) chunk = (chunk + 1) / 2;
+    return chunk;
 }
 
 // Both phases derive every pointer from (plan, buffers, workspace) alone, so a
@@ -204,7 +218,8 @@ size_t plan_workspace(const fe_plan* p, size_t chunk, size_t R) {
 // so a key is streamed once per launch for all of them; every request's
 // arithmetic is the same as when it runs alone.
 int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, const u64* b_pt, u64* b_out,
-             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req, int pt_pool) {
+             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req, int pt_pool,
+             void* data_ws, size_t data_ws_bytes) {
     const int N = c->N, lv = p->level;
     Sizes z = sizes_of(c, lv);
     if (n_req < 1) return fail(FE_EINVAL, "n_req must be positive");
@@ -215,20 +230,20 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     const bool dh = p->dhoist != 0;
     const size_t rw = dh ? z.accw : z.ctw;                         // words of one rotated copy
     const size_t ptw = dh ? (size_t)(lv + 1 + c->k) * N : z.nlN;  // words of one plaintext
-    size_t chunk = mode == 0 ? 1 : std::max<size_t>(1, R * p->n_outer);
-    while (chunk > 1 && plan_workspace(p, chunk, R) > ws_bytes) chunk = (chunk + 1) / 2;
-    if (plan_workspace(p, chunk, R) > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the plan");
+    // item tables in ws; data (rotated copies, sums, scratch) after them, or in
+    // data_ws when given (graph capture: one data region shared by all layers)
+    const size_t chunk = data_ws ? plan_chunk(p, R, mode, data_ws_bytes, true) : plan_chunk(p, R, mode, ws_bytes, false);
+    if (data_ws ? (plan_data_bytes(p, chunk, R) > data_ws_bytes || plan_table_bytes(p, chunk, R) > ws_bytes)
+                : plan_workspace(p, chunk, R) > ws_bytes)
+        return fail(FE_ENOMEM, "workspace too small for the plan");
     std::map<int32_t, const u64*> keys;
     for (int32_t s : p->steps) {
         const u64* k = evk_key(evk, c->galois(s));
         if (!k) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(s));
         keys[s] = k;
     }
-    // ---- carve the workspace ----
+    // ---- carve the workspace: item tables first ----
     Carver cv(ws, ws_bytes);
-    u64* Rb = cv.take<u64>(R * n_in_rot * rw);
-    u64* total = cv.take<u64>(R * p->n_out * z.ctw);
-    u64* XP = dh ? cv.take<u64>(R * p->n_in * z.accw) : nullptr;
     size_t n_groups_all = 0;
     for (auto& o : p->outs) n_groups_all += o.groups.size();
     // rotated groups of all requests: (request, output, group), sorted by step
@@ -262,8 +277,13 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     LiftItem* d_lift = cv.take<LiftItem>(dh ? std::max<size_t>(1, R * (n_in_rot + p->n_in)) : 1);
     CombineItem* d_dcb = cv.take<CombineItem>(dh ? std::max<size_t>(1, R * n_groups_all) : 1);
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
-    char* scratch = cv.p;
-    const size_t scratch_bytes = cv.left;
+    Carver cd(data_ws ? (char*)data_ws : cv.p, data_ws ? data_ws_bytes : cv.left);
+    u64* Rb = cd.take<u64>(R * n_in_rot * rw);
+    u64* total = cd.take<u64>(R * p->n_out * z.ctw);
+    u64* XP = dh ? cd.take<u64>(R * p->n_in * z.accw) : nullptr;
+    if (!cd.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
+    char* scratch = cd.p;
+    const size_t scratch_bytes = cd.left;
     Carver s1(scratch, scratch_bytes);  // stage 1
     u64* coef1 = s1.take<u64>(R * n_mu * z.nlN);
     u64* ext1 = s1.take<u64>(R * n_mu * z.extw);

@@ -198,30 +198,60 @@ extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, u
     return FE_OK;
 }
 
-extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans, const void* const* pts,
-                                const void* const* ins, void* const* outs, uint32_t n, void* ws, size_t ws_bytes,
-                                void* stream, fe_graph** out) {
+namespace {
+// shared data region of a captured sequence: the largest default data region
+// of its layers
+size_t graph_data_bytes(const fe_plan* const* plans, uint32_t n, uint32_t n_req) {
+    size_t data = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const size_t def = fe_plan_workspace_bytes(plans[i], n_req, 0);
+        const size_t ch = plan_chunk(plans[i], n_req, 1, def, false);
+        data = std::max(data, plan_data_bytes(plans[i], ch, n_req));
+    }
+    return (data + 255) & ~(size_t)255;
+}
+}  // namespace
+
+extern "C" size_t fe_graph_workspace_bytes(const fe_plan* const* plans, uint32_t n, uint32_t n_req) {
+    if (!plans || n_req == 0) return 0;
+    for (uint32_t i = 0; i < n; i++)
+        if (!plans[i]) return 0;
+    const size_t data = graph_data_bytes(plans, n, n_req);
+    size_t tables = 0;
+    for (uint32_t i = 0; i < n; i++)
+        tables += (plan_table_bytes(plans[i], plan_chunk(plans[i], n_req, 1, data, true), n_req) + 255) & ~(size_t)255;
+    return tables + data;
+}
+
+extern "C" int fe_graph_capture_batch(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans,
+                                      const void* const* pts, const void* const* ins, void* const* outs, uint32_t n,
+                                      uint32_t n_req, void* ws, size_t ws_bytes, void* stream, fe_graph** out) {
     if (!c || !evk || !plans || !pts || !ins || !outs || !ws || !out) return fail(FE_EINVAL, "null argument");
+    if (n_req == 0) return fail(FE_EINVAL, "n_req must be positive");
     cudaStream_t st = (cudaStream_t)stream;
     if (!st) return fail(FE_EINVAL, "graph capture needs a non-default stream");
-    // every layer gets its own workspace slice so that its item tables survive
+    for (uint32_t i = 0; i < n; i++)
+        if (!plans[i]) return fail(FE_EINVAL, "null plan");
+    // every layer keeps its own item tables (they must survive until replay);
+    // the data region (rotated copies, sums, scratch) is shared, layers run in order
+    const size_t data = graph_data_bytes(plans, n, n_req);
     std::vector<size_t> off(n + 1, 0);
     for (uint32_t i = 0; i < n; i++) {
-        fe_plan_info info;
-        FE_TRY(fe_plan_query(plans[i], &info));
-        off[i + 1] = off[i] + ((info.workspace_bytes + 255) & ~(size_t)255);
+        const size_t ch = plan_chunk(plans[i], n_req, 1, data, true);
+        off[i + 1] = off[i] + ((plan_table_bytes(plans[i], ch, n_req) + 255) & ~(size_t)255);
     }
-    if (off[n] > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the captured layers");
+    if (off[n] + data > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the captured layers");
+    char* shared = (char*)ws + off[n];
     for (uint32_t i = 0; i < n; i++)
         FE_TRY(run_plan(c, evk, plans[i], (const u64*)ins[i], (const u64*)pts[i], (u64*)outs[i], (char*)ws + off[i],
-                        off[i + 1] - off[i], 1, st, 1));
+                        off[i + 1] - off[i], 1, st, 1, (int)n_req, 0, shared, data));
     FE_CUDA_TRY(cudaStreamSynchronize(st));
     std::unique_ptr<fe_graph> g(new fe_graph());
     FE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = FE_OK;
     for (uint32_t i = 0; i < n && rc == FE_OK; i++)
         rc = run_plan(c, evk, plans[i], (const u64*)ins[i], (const u64*)pts[i], (u64*)outs[i], (char*)ws + off[i],
-                      off[i + 1] - off[i], 1, st, 2);
+                      off[i + 1] - off[i], 1, st, 2, (int)n_req, 0, shared, data);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (rc != FE_OK) {
@@ -233,6 +263,12 @@ extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* con
     FE_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
     *out = g.release();
     return FE_OK;
+}
+
+extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans, const void* const* pts,
+                                const void* const* ins, void* const* outs, uint32_t n, void* ws, size_t ws_bytes,
+                                void* stream, fe_graph** out) {
+    return fe_graph_capture_batch(c, evk, plans, pts, ins, outs, n, 1, ws, ws_bytes, stream, out);
 }
 
 extern "C" int fe_graph_launch(fe_graph* g, void* stream) {

@@ -54,8 +54,12 @@ struct fe_plan {
 namespace fe {
 int layout_fill(int N, fe_layout* l);
 size_t plan_workspace(const fe_plan* p, size_t chunk, size_t n_req = 1);
+size_t plan_data_bytes(const fe_plan* p, size_t chunk, size_t n_req);
+size_t plan_table_bytes(const fe_plan* p, size_t chunk, size_t n_req);
+size_t plan_chunk(const fe_plan* p, size_t n_req, int mode, size_t data_bytes, bool data_only);
 // phase bit 1: upload item tables; bit 2: launch kernels.  n_req requests laid
 // out contiguously (inputs [n_req][n_in] ct, outputs [n_req][n_out] ct).
 int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* in, const u64* pt, u64* out,
-             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req = 1, int pt_pool = 0);
+             void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req = 1, int pt_pool = 0,
+             void* data_ws = nullptr, size_t data_ws_bytes = 0);
 }  // namespace fe

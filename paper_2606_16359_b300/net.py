@@ -23,10 +23,12 @@ def _torch():
 
 class MobileNetBlocks:
     """schedule: "linear" (one outer rotation per channel diagonal, Eq. 4),
-    "tuned" (per pointwise layer, the fastest of linear and baby-step /
-    giant-step splits, timed by the autotuner), or an int n1 (baby steps)."""
+    "tuned" (per layer, the fastest outer-rotation split, hoisting and MAC tile
+    timed by the autotuner), or an int n1 (baby steps).  batch: independent
+    encrypted inputs per block, run together (keys shared across them)."""
 
-    def __init__(self, ctx, blocks=None, seed=0, delta=2.0 ** 32, key_seed=101, enc_seed=202, schedule="linear"):
+    def __init__(self, ctx, blocks=None, seed=0, delta=2.0 ** 32, key_seed=101, enc_seed=202, schedule="linear",
+                 batch=1):
         torch = _torch()
         self.ctx = ctx
         self.delta = delta
@@ -35,6 +37,7 @@ class MobileNetBlocks:
         self.layers = []  # dicts: plan, pt, inp, out, level
         self.inputs, self.ref_inputs = [], []
         self.schedule, self.tune_ms = [], []
+        self.batch = B = int(batch)
         tuner = None
         if schedule == "tuned":
             from .tune import Tuner
@@ -69,45 +72,52 @@ class MobileNetBlocks:
         self.n_keys = len(steps)
         ct_id = 0
         for bi, (lay, pdw, ppw, x, wd, wp) in enumerate(plans):
-            slots = ctx.pack(lay, torch.from_numpy(x))
-            ct = ctx.encrypt(self.sk, slots, L, delta, enc_seed, ct_id0=ct_id)
-            ct_id += lay.n_ct
+            xs = [x] + [W.mobilenet_block(seed + 1000 * b, *self.blocks[bi], BS=1, block=bi)[0] for b in range(1, B)]
+            cts = []
+            for xb in xs:
+                slots = ctx.pack(lay, torch.from_numpy(xb))
+                cts.append(ctx.encrypt(self.sk, slots, L, delta, enc_seed, ct_id0=ct_id))
+                ct_id += lay.n_ct
+            ct = torch.cat(cts, 0).contiguous() if B > 1 else cts[0]
             pt_dw = ctx.load_weights(pdw, wd, float(ctx.moduli[L]))
             pt_pw = ctx.load_weights(ppw, wp, float(ctx.moduli[L - 1]))
-            mid = ctx.empty_ct(pdw.info.n_out_ct, L - 1)
-            out = ctx.empty_ct(ppw.info.n_out_ct, L - 2)
+            mid = ctx.empty_ct(B * pdw.info.n_out_ct, L - 1)
+            out = ctx.empty_ct(B * ppw.info.n_out_ct, L - 2)
             self.layers.append(dict(plan=pdw, pt=pt_dw, inp=ct, out=mid, level=L, name=f"b{bi}_dw"))
             self.layers.append(dict(plan=ppw, pt=pt_pw, inp=mid, out=out, level=L - 1, name=f"b{bi}_pw"))
             self.inputs.append(ct)
-            self.ref_inputs.append((x, wd, wp, ppw.out_layout))
+            self.ref_inputs.append((xs, wd, wp, ppw.out_layout))
         self.outputs = [self.layers[2 * i + 1]["out"] for i in range(len(self.blocks))]
-        self.ws_bytes = max(l_["plan"].info.workspace_bytes for l_ in self.layers)
+        self.ws_bytes = max(ctx.workspace_bytes(l_["plan"], B) for l_ in self.layers)
         self.ws = ctx.workspace(self.ws_bytes)
         self.graph = None
 
     @property
     def keyswitches_per_step(self):
-        return sum(l_["plan"].info.n_inner_rot + l_["plan"].info.n_outer_rot for l_ in self.layers)
+        return self.batch * sum(l_["plan"].info.n_inner_rot + l_["plan"].info.n_outer_rot for l_ in self.layers)
 
     @property
     def pmults_per_step(self):
-        return sum(l_["plan"].info.n_pt for l_ in self.layers)
+        return self.batch * sum(l_["plan"].info.n_pt for l_ in self.layers)
 
     def run(self, mode=1):
-        for l_ in self.layers:
-            self.ctx.he_conv(self.evk, l_["plan"], l_["pt"], l_["inp"], mode=mode, ws=self.ws, out=l_["out"])
+        for i in range(len(self.layers)):
+            self.run_layer(i, mode)
 
     def run_layer(self, i, mode=1):
         l_ = self.layers[i]
-        self.ctx.he_conv(self.evk, l_["plan"], l_["pt"], l_["inp"], mode=mode, ws=self.ws, out=l_["out"])
+        if self.batch == 1:
+            self.ctx.he_conv(self.evk, l_["plan"], l_["pt"], l_["inp"], mode=mode, ws=self.ws, out=l_["out"])
+        else:
+            self.ctx.he_layer_batch(self.evk, l_["plan"], l_["pt"], l_["inp"], self.batch, mode=mode, ws=self.ws,
+                                    out=l_["out"])
 
     def capture(self):
         plans = [l_["plan"] for l_ in self.layers]
-        total = sum((p.info.workspace_bytes + 255) // 256 * 256 for p in plans)
-        self.graph_ws = self.ctx.workspace(total)
+        self.graph_ws = self.ctx.workspace(self.ctx.graph_workspace_bytes(plans, self.batch))
         self.graph = self.ctx.graph_capture(self.evk, plans, [l_["pt"] for l_ in self.layers],
                                             [l_["inp"] for l_ in self.layers], [l_["out"] for l_ in self.layers],
-                                            self.graph_ws)
+                                            self.graph_ws, n_req=self.batch)
         return self.graph
 
     def serve_ops(self, bi):
@@ -116,14 +126,16 @@ class MobileNetBlocks:
         dw, pw = self.layers[2 * bi], self.layers[2 * bi + 1]
         return [(OP_LAYER, dw["plan"], dw["pt"]), (OP_LAYER, pw["plan"], pw["pt"])]
 
-    def decrypt_block(self, bi):
-        x, wd, wp, olay = self.ref_inputs[bi]
-        slots = self.ctx.decrypt(self.sk, self.outputs[bi], self.ctx.L - 2, self.delta)
+    def decrypt_block(self, bi, b=0):
+        xs, wd, wp, olay = self.ref_inputs[bi]
+        n = self.outputs[bi].shape[0] // self.batch
+        slots = self.ctx.decrypt(self.sk, self.outputs[bi][b * n:(b + 1) * n], self.ctx.L - 2, self.delta)
         return self.ctx.unpack(olay, slots).cpu().numpy()
 
-    def reference_block(self, bi):
-        """FP64 plaintext result of block bi (valid convolutions)."""
-        x, wd, wp, _ = self.ref_inputs[bi]
+    def reference_block(self, bi, b=0):
+        """FP64 plaintext result of block bi for input b (valid convolutions)."""
+        xs, wd, wp, _ = self.ref_inputs[bi]
+        x = xs[b]
         from .plainref import conv2d
         return conv2d(conv2d(x, wd, depthwise=True), wp)
 

@@ -37,3 +37,25 @@ def test_tuner_times_all_candidates_and_tuned_blocks_decrypt():
         errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(2)]
     assert max(errs) < 1e-3, errs
     assert len(net.schedule) == 2 and len(net.tune_ms) == 2
+
+
+
+def test_batched_blocks_graph_decrypt_every_input():
+    """Three inputs per block in one graph-captured step: every input decrypts to
+    its FP64 result, and equals the same input run alone bit for bit."""
+    p = W.PARAMS["mobilenet_small"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        net = MobileNetBlocks(ctx, blocks=[(8, 64, 64)], delta=p["delta"], schedule=4, batch=3)
+        net.capture()
+        net.graph.launch()
+        torch.cuda.synchronize()
+        errs = [float(np.abs(net.decrypt_block(0, b) - net.reference_block(0, b)).max()) for b in range(3)]
+        out = net.outputs[0].cpu().numpy()
+        single = MobileNetBlocks(ctx, blocks=[(8, 64, 64)], delta=p["delta"], schedule=4, batch=1)
+        single.run()
+        torch.cuda.synchronize()
+        one = single.outputs[0].cpu().numpy()
+    assert max(errs) < 1e-3, errs
+    assert np.array_equal(out[:one.shape[0]], one)
