@@ -30,7 +30,7 @@ namespace fe {
 
 namespace {
 
-constexpr int kTile = 4096;  // elements per CTA tile (32 KiB)
+constexpr int kTile = 1024;  // elements per CTA tile (8 KiB)
 constexpr int kE = 8;        // elements per thread per round (radix 8; radix 16: 2 kE)
 
 struct NttArgs {
@@ -102,8 +102,9 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
 // kCol: column pass (lines = columns of length N1) else row pass (lines = rows of length N2).
 // kLogN > 0 fixes the ring degree at compile time so that the tile geometry, the
 // round structure and every shift fold into constants; kLogN = 0 reads it at run time.
+// CTAs of kTile / 2^kLE threads; the bound lets 9 radix-8 CTAs (36 warps) share an SM
 template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE>
-__global__ void __launch_bounds__(512) ntt_pass(NttArgs a, int first) {
+__global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttArgs a, int first) {
     constexpr int kEE = 1 << kLE;
     extern __shared__ u64 tile[];
     const int logN = kLogN ? kLogN : a.logN;
