@@ -86,10 +86,12 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
                                                           const Modulus* mods, int L, int level, int k,
                                                           int logN, int n_mod) {
     const int N = 1 << logN;
-    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    // blockIdx.x = group (fastest), so that the CTAs of all keys of one
+    // (coefficient tile, limb) run together and the digits they share hit L2
+    const int n = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
     if (n >= N) return;
-    const KsGroup gr = groups[blockIdx.z];
-    const int p = blockIdx.y;
+    const KsGroup gr = groups[blockIdx.x];
+    const int p = blockIdx.z;
     const int np = level + 1 + k;
     const int mi = p <= level ? p : L + 1 + (p - level - 1);
     const Modulus m = mods[mi];
@@ -317,10 +319,12 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
     uint64_t* empty = full + S;            // [S]
     u64* stage0 = (u64*)(mac_smem + 256);  // [S][2 + W][T]
     const size_t stage_words = (size_t)(2 + W) * T;
-    const MacItem it = items[blockIdx.z];
-    const int i = blockIdx.y;
+    // blockIdx.x = item (fastest): the items of one (tile, limb) run together and
+    // the ciphertext tiles they share are read from L2
+    const MacItem it = items[blockIdx.x];
+    const int i = blockIdx.z;
     const Modulus m = mods[mod_map ? mod_map[i] : i];
-    const size_t base = (size_t)blockIdx.x * T;
+    const size_t base = (size_t)blockIdx.y * T;
     const size_t off0 = ((size_t)i << logN) + base, off1 = ((size_t)(nl + i) << logN) + base;
     const uint32_t tile_bytes = (uint32_t)T * 8u;
     const uint64_t limit = 2000000000ull;
@@ -548,7 +552,7 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
     if (!n_groups) return;
     const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
     ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + (double)n_items * (dn + 2)));
-    const dim3 g((c->N / 2 + kB - 1) / kB, level + 1 + c->k, n_groups);  // two coefficients per thread
+    const dim3 g(n_groups, (c->N / 2 + kB - 1) / kB, level + 1 + c->k);  // two coefficients per thread
 #define FE_KEYIP(D)                                                                                   \
     case D:                                                                                           \
         k_keyip_grouped<D><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod); \
@@ -602,7 +606,7 @@ void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_ite
     const int nl = qp ? level + 1 + c->k : level + 1;
     ProfScope ps(c, PK_MAC, st, 8.0 * c->N * nl * (2.0 * n_ct_terms + (double)n_pt_terms + 2.0 * n_outputs));
     const int T = std::min(kMacTile, c->N);
-    const dim3 g(c->N / T, nl, n_items);
+    const dim3 g(n_items, c->N / T, nl);
     const int threads = T / 2 + 32;
     const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
     const size_t smem = 256 + (size_t)kMacStageBytes;

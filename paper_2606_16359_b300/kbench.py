@@ -5,6 +5,7 @@
     python -m paper_2606_16359_b300.kbench keyswitch [--n 8] [--level 22] [--reps 5]
     python -m paper_2606_16359_b300.kbench mac [--reps 5]
     python -m paper_2606_16359_b300.kbench aac [--reps 5]
+    python -m paper_2606_16359_b300.kbench configs [--reps 5]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -189,9 +190,62 @@ def bench_aac(ctx, torch, args):
     return {"kernel": "aac", "level": lv, "rows": rows, "status": ctx.device_status()}
 
 
+def bench_configs(ctx_unused, torch, args):
+    """The two small configurations end to end on the GPU: the single 5x5 conv
+    1 -> 6 at N = 2^13 (S = 4) and the LeNet-shaped network at N = 2^14
+    (128 images), batched and per-op paths, with the max error against FP64."""
+    import numpy as np
+    import workloads as W
+    from paper_2606_16359_b300 import plainref
+    from paper_2606_16359_b300.net import LeNet
+    import paper_2606_16359_b300 as fe
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"kernel": "configs"}
+    p = W.PARAMS["conv1"]
+    c1 = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+    x, w = W.conv1_workload(0)
+    lay = c1.layout(28, 28, 1, 1, 4)
+    plan = c1.plan_conv(lay, 6, 5, level=c1.L)
+    sk = c1.sk_gen(1)
+    evk = c1.evk_gen(sk, 1, plan.steps)
+    ct = c1.encrypt(sk, c1.pack(lay, torch.from_numpy(x)), c1.L, p["delta"], 2)
+    pt = c1.load_weights(plan, w, float(c1.moduli[c1.L]))
+    ws = c1.workspace(plan.info.workspace_bytes)
+    res = {}
+    for mode in (1, 0):
+        res[mode] = timed(lambda: c1.he_conv(evk, plan, pt, ct, mode=mode, ws=ws), args.reps)
+    y = c1.unpack(plan.out_layout, c1.decrypt(sk, c1.he_conv(evk, plan, pt, ct, ws=ws), c1.L - 1, p["delta"]))
+    out["conv1"] = {"batched_ms": res[1], "per_op_ms": res[0], "rotations": plan.info.n_inner_rot + plan.info.n_outer_rot,
+                    "pmults": plan.info.n_pt, "max_abs_err": float(np.abs(y.cpu().numpy() - plainref.conv2d(x, w)).max())}
+    p = W.PARAMS["lenet"]
+    c2 = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+    wts = W.lenet_weights(0)
+    net = LeNet(c2, p["delta"], wts)
+    xs = W.lenet_input(0, net.BS)
+    ct2 = net.encrypt(xs)
+    for mode in (1, 0):
+        res[mode] = timed(lambda: net.forward(ct2, mode=mode), args.reps)
+    yl = net.decode_logits(net.forward(ct2))
+    out["lenet"] = {"images": net.BS, "batched_ms": res[1], "per_op_ms": res[0], "ms_per_image": res[1] / net.BS,
+                    "max_abs_err": float(np.abs(yl - plainref.lenet(xs, wts)).max())}
+    out["status"] = c1.device_status() | c2.device_status()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "aac"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "aac", "configs"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
@@ -209,7 +263,7 @@ def main(argv=None):
     with torch.cuda.stream(side):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
-              "aac": bench_aac}[args.what]
+              "aac": bench_aac, "configs": bench_configs}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 

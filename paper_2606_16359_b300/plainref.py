@@ -11,3 +11,19 @@ def conv2d(x, w, stride=1, depthwise=False):
     wt = torch.from_numpy(np.asarray(w, dtype=np.float64))
     y = F.conv2d(xt, wt, stride=stride, groups=xt.shape[1] if depthwise else 1)
     return y.numpy()
+
+
+def lenet(x, weights):
+    """The LeNet-5-shaped network in the clear (float64): two 5x5 valid convs,
+    each followed by x^2 and 2x2 average pooling, then FC 256 -> 120 -> 84 -> 10
+    with no activation between the FC layers."""
+    import torch
+    import torch.nn.functional as F
+    t = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float64))
+    h = t(x)
+    for name in ("conv1", "conv2"):
+        h = F.avg_pool2d(F.conv2d(h, t(weights[name])) ** 2, 2)
+    h = h.flatten(1)
+    for name in ("fc1", "fc2", "fc3"):
+        h = F.linear(h, t(weights[name]))
+    return h.numpy()
