@@ -312,7 +312,15 @@ int fe_plan_rotation_steps(const fe_plan* plan, int32_t* steps_host, uint32_t ma
  * (Cout, Cin, K, K) or (C, 1, K, K) when depthwise; FC (F_out, F_in).  Every
  * weight is multiplied by wmul first (a folded 1/4 of a preceding pooling).
  * Zero weights at invalid output positions make the plaintexts the fragment
- * masks of Fig. 2. */
+ * masks of Fig. 2.
+ * Layout (opaque to callers, but fixed): plaintexts one after another, each
+ * [level+1] limbs (level+1+k under double hoisting) in NTT form; a limb is
+ * N / T tiles of T = min(512, N) consecutive residues, and a tile is the low 32
+ * bits of its T residues (uint32) followed by their high bits, hb bytes each
+ * (hb = 1 when every modulus of the context is below 2^40, 2 below 2^48, else
+ * 4), (4 + hb) T bytes in all.  The residues are the same
+ * as those of fe_encode; only their storage is narrower, so the PMult-MAC reads
+ * (4 + hb) / 8 of the bytes. */
 int fe_plan_load_weights(fe_ctx* ctx, fe_plan* plan, const double* weights_host, double wmul,
                          double w_scale, void* pt_dev, void* stream);
 
@@ -349,8 +357,8 @@ int fe_he_layer_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const
 
 /* For latency measurement only: run one conv / FC plan with its plaintexts
  * taken cyclically from a pool (term t uses pool plaintext t mod n_pool;
- * pt_pool_dev holds n_pool plaintexts of the plan's size, [n_pool][level+1][N],
- * or [n_pool][level+1+k][N] under double hoisting).  The kernels,
+ * pt_pool_dev holds n_pool plaintexts in the layout of fe_plan_load_weights,
+ * pt_bytes / n_pt bytes each; any bytes will do).  The kernels,
  * launches and memory volume are those of fe_he_conv; the result is not the
  * layer's.  Errors as fe_he_conv. */
 int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_pool_dev,

@@ -229,7 +229,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     // double hoisting: rotated copies, lifted inputs and plaintexts on Q_l * P
     const bool dh = p->dhoist != 0;
     const size_t rw = dh ? z.accw : z.ctw;                         // words of one rotated copy
-    const size_t ptw = dh ? (size_t)(lv + 1 + c->k) * N : z.nlN;  // words of one plaintext
+    const size_t ptb = (size_t)(dh ? lv + 1 + c->k : lv + 1) * pt_limb_bytes(c);  // bytes of one plaintext
     // item tables in ws; data (rotated copies, sums, scratch) after them, or in
     // data_ws when given (graph capture: one data region shared by all layers)
     const size_t chunk = data_ws ? plan_chunk(p, R, mode, data_ws_bytes, true) : plan_chunk(p, R, mode, ws_bytes, false);
@@ -355,7 +355,8 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     mterms.reserve(R * n_terms);
     for (size_t r = 0; r < R; r++)
         for (const auto& t : p->terms)
-            mterms.push_back(MacTerm{src_ptr(r, t.src), b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * ptw});
+            mterms.push_back(MacTerm{src_ptr(r, t.src),
+                                     (const uint8_t*)b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * ptb});
     struct OneMac {
         u64* out;
         int term0, n_terms;
@@ -538,7 +539,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         for (size_t i = 0; i < n_base; i++)
             for (int t = 0; t < macs[i].n_terms; t++) {
                 const MacTerm& tm = mterms[macs[i].term0 + t];
-                launch_pmult(c, tm.ct, tm.pt, macs[i].out, 1, lv, t > 0, st);
+                launch_pmult_compact(c, tm.ct, tm.pt, macs[i].out, lv, t > 0, st);
             }
     } else {
         launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
@@ -568,7 +569,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                 } else {
                     for (int t = 0; t < m.n_terms; t++) {
                         const MacTerm& tm = mterms[m.term0 + t];
-                        launch_pmult(c, tm.ct, tm.pt, m.out, 1, lv, t > 0, st);
+                        launch_pmult_compact(c, tm.ct, tm.pt, m.out, lv, t > 0, st);
                     }
                 }
                 modup(c, Pd + s * z.ctw + z.nlN, z.ctw, 1, lv, coef3 + s * z.nlN, ext3 + s * z.extw, st);
@@ -896,7 +897,7 @@ extern "C" size_t fe_plan_workspace_bytes(const fe_plan* p, uint32_t n_req, int 
 extern "C" int fe_plan_query(const fe_plan* p, fe_plan_info* info) {
     if (!p || !info) return fail(FE_EINVAL, "null argument");
     const fe_ctx* c = p->c;
-    info->pt_bytes = (size_t)p->n_pt * (p->level + 1 + (p->dhoist ? c->k : 0)) * c->N * 8;
+    info->pt_bytes = (size_t)p->n_pt * (p->level + 1 + (p->dhoist ? c->k : 0)) * pt_limb_bytes(c);
     info->in_bytes = (size_t)p->n_in * ct_words(c, p->level) * 8;
     info->out_bytes = (size_t)p->n_out * ct_words(c, p->level - 1) * 8;
     // default: the whole outer stage in one chunk, unless its scratch exceeds 8 GiB
@@ -932,11 +933,16 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     double* dW;
     FE_CUDA_TRY(cudaMallocAsync(&dW, wcount * 8, st));
     FE_CUDA_TRY(cudaMemcpyAsync(dW, W_host, wcount * 8, cudaMemcpyHostToDevice, st));
-    const int chunk = std::max(1, std::min(p->n_pt, (int)((64ull << 20) / ((size_t)half * 8))));
+    // chunks of plaintexts: slot vectors (<= 64 MiB) and 64-bit limbs (<= 1 GiB)
+    // before they are compacted into pt_dev
+    const int chunk = std::max(1, std::min({p->n_pt, (int)((64ull << 20) / ((size_t)half * 8)),
+                                            (int)((1ull << 30) / ((size_t)nl * N * 8))}));
     double* z;
+    u64* limbs;
     void* descs;
     int* dfeat = nullptr;
     FE_CUDA_TRY(cudaMallocAsync(&z, (size_t)chunk * half * 8, st));
+    FE_CUDA_TRY(cudaMallocAsync(&limbs, (size_t)chunk * nl * N * 8, st));
     size_t dbytes = p->kind == 0 ? p->cpts.size() * sizeof(fe_plan::ConvPt) : p->fpts.size() * sizeof(fe_plan::FcPt);
     FE_CUDA_TRY(cudaMallocAsync(&descs, std::max<size_t>(dbytes, 16), st));
     if (p->kind == 0) {
@@ -958,10 +964,13 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
             FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
             k_fc_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
         }
-        rc = encode_batch(c, z, cn, p->level, w_scale, (u64*)pt_dev + (size_t)s0 * nl * N, st, p->dhoist != 0);
+        rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, p->dhoist != 0);
+        if (rc == FE_OK)
+            launch_pt_compact(c, limbs, (uint8_t*)pt_dev + (size_t)s0 * nl * pt_limb_bytes(c), cn * nl, st);
     }
     cudaFreeAsync(dW, st);
     cudaFreeAsync(z, st);
+    cudaFreeAsync(limbs, st);
     cudaFreeAsync(descs, st);
     if (dfeat) cudaFreeAsync(dfeat, st);
     FE_CUDA_TRY(cudaStreamSynchronize(st));

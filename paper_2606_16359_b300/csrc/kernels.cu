@@ -254,8 +254,9 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 // async-copy engine.  One CTA = one item (up to W outputs sharing their
 // ciphertext terms), one limb, a tile of T coefficients (T = min(512, N)):
 // T / 2 consumer threads (two coefficients each) and one producer warp.  For
-// term t the CTA needs the tiles of c0 and c1 of the term's ciphertext and of
-// each output's plaintext, (2 + n_out) T 8 bytes, copied with cp.async.bulk into
+// term t the CTA needs the tiles of c0 and c1 of the term's ciphertext (2 T 8
+// bytes) and of each output's compact plaintext (a low-word tile of T 4 bytes
+// and a high-bit tile of T HB bytes), copied with cp.async.bulk into
 // stage t mod S and signalled on the stage's "full" mbarrier (arrive.expect_tx
 // by the producer, complete_tx by the copies).  Each consumer warp arrives on
 // the stage's "empty" mbarrier when it has read the stage; the producer waits
@@ -266,8 +267,10 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 constexpr int kMacTile = 512;
 constexpr int kMacStageBytes = 98304;  // shared memory for the stages of one CTA
 
-template <int W>
-__host__ __device__ constexpr int mac_stages() { return kMacStageBytes / ((2 + W) * kMacTile * 8); }
+template <int W, int HB>
+__host__ __device__ constexpr int mac_stage_bytes() { return (16 + W * (4 + HB)) * kMacTile; }
+template <int W, int HB>
+__host__ __device__ constexpr int mac_stages() { return kMacStageBytes / mac_stage_bytes<W, HB>(); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -309,16 +312,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-template <int W>
-__global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items, const MacTerm* terms,
+template <int W, int HB>
+__global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* items, const MacTerm* terms,
                                                           const Modulus* mods, const int* mod_map, int nl,
                                                           int logN, int T, uint32_t* status) {
-    constexpr int S = mac_stages<W>();
+    constexpr int S = mac_stages<W, HB>();
     extern __shared__ __align__(128) unsigned char mac_smem[];
     uint64_t* full = (uint64_t*)mac_smem;  // [S]
     uint64_t* empty = full + S;            // [S]
-    u64* stage0 = (u64*)(mac_smem + 256);  // [S][2 + W][T]
-    const size_t stage_words = (size_t)(2 + W) * T;
+    unsigned char* stage0 = mac_smem + 256;  // [S] x (c0 | c1 | W x (low | high))
+    const size_t stage_stride = (size_t)(16 + W * (4 + HB)) * T;
     // blockIdx.x = item (fastest): the items of one (tile, limb) run together and
     // the ciphertext tiles they share are read from L2
     const MacItem it = items[blockIdx.x];
@@ -326,7 +329,10 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
     const Modulus m = mods[mod_map ? mod_map[i] : i];
     const size_t base = (size_t)blockIdx.y * T;
     const size_t off0 = ((size_t)i << logN) + base, off1 = ((size_t)(nl + i) << logN) + base;
-    const uint32_t tile_bytes = (uint32_t)T * 8u;
+    // compact plaintext limb i, tile blockIdx.y: T low words then T high parts,
+    // (4 + HB) T contiguous bytes
+    const size_t pt_off = ((size_t)i << logN) * (4 + HB) + base * (4 + HB);
+    const uint32_t ct_tile = (uint32_t)T * 8u, lo_tile = (uint32_t)T * 4u, hi_tile = (uint32_t)T * HB;
     const uint64_t limit = 2000000000ull;
     const int tid = threadIdx.x;
     const int n_cons = T / 2;                  // consumer threads
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
     if (tid >= n_cons) {
         // producer warp: lane 0 keeps up to S terms in flight
         if (tid != n_cons) return;
-        const uint32_t stage_bytes = (uint32_t)(2 + it.n_out) * tile_bytes;
+        const uint32_t stage_bytes = 2 * ct_tile + (uint32_t)it.n_out * (lo_tile + hi_tile);
         int issued = 0;
         bool ok = true;
         for (; issued < it.n_terms; issued++) {
@@ -351,13 +357,15 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
                 ok = false;
                 break;
             }
-            u64* st = stage0 + (size_t)s * stage_words;
+            unsigned char* st = stage0 + (size_t)s * stage_stride;
             const u64* ct = terms[it.term0[0] + issued].ct;
             mbar_expect_tx(&full[s], stage_bytes);
-            bulk_g2s(st, ct + off0, tile_bytes, &full[s]);
-            bulk_g2s(st + T, ct + off1, tile_bytes, &full[s]);
-            for (int k = 0; k < it.n_out; k++)
-                bulk_g2s(st + (size_t)(2 + k) * T, terms[it.term0[k] + issued].pt + off0, tile_bytes, &full[s]);
+            bulk_g2s(st, ct + off0, ct_tile, &full[s]);
+            bulk_g2s(st + ct_tile, ct + off1, ct_tile, &full[s]);
+            for (int k = 0; k < it.n_out; k++) {
+                bulk_g2s(st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile), terms[it.term0[k] + issued].pt + pt_off,
+                         lo_tile + hi_tile, &full[s]);
+            }
         }
         if (!ok) {
             atomicOr(status, 1u);
@@ -376,17 +384,30 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
             atomicOr(status, 1u);
             return;
         }
-        const u64* st = stage0 + (size_t)s * stage_words;
+        const unsigned char* st = stage0 + (size_t)s * stage_stride;
         const ulonglong2 x0 = reinterpret_cast<const ulonglong2*>(st)[tid];
-        const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(st + T)[tid];
+        const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(st + ct_tile)[tid];
 #pragma unroll
         for (int k = 0; k < W; k++) {
             if (k >= it.n_out) break;
-            const ulonglong2 p = reinterpret_cast<const ulonglong2*>(st + (2 + k) * T)[tid];
-            a0[k] += (u128)x0.x * p.x;
-            a1[k] += (u128)x0.y * p.y;
-            b0[k] += (u128)x1.x * p.x;
-            b1[k] += (u128)x1.y * p.y;
+            const unsigned char* pk = st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile);
+            const uint2 lo = reinterpret_cast<const uint2*>(pk)[tid];
+            u64 hx, hy;
+            if (HB == 1) {
+                const uchar2 h = reinterpret_cast<const uchar2*>(pk + lo_tile)[tid];
+                hx = h.x, hy = h.y;
+            } else if (HB == 2) {
+                const ushort2 h = reinterpret_cast<const ushort2*>(pk + lo_tile)[tid];
+                hx = h.x, hy = h.y;
+            } else {
+                const uint2 h = reinterpret_cast<const uint2*>(pk + lo_tile)[tid];
+                hx = h.x, hy = h.y;
+            }
+            const u64 px = (u64)lo.x | (hx << 32), py = (u64)lo.y | (hy << 32);
+            a0[k] += (u128)x0.x * px;
+            a1[k] += (u128)x0.y * py;
+            b0[k] += (u128)x1.x * px;
+            b1[k] += (u128)x1.y * py;
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);
@@ -411,6 +432,48 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32) k_mac(const MacItem* items,
         r1.y = reduce128(b1[k], m);
         reinterpret_cast<ulonglong2*>(it.out[k] + off0)[tid] = r0;
         reinterpret_cast<ulonglong2*>(it.out[k] + off1)[tid] = r1;
+    }
+}
+
+// byte offset of the tile holding residue n inside a compact limb, and n's index in it
+__device__ __forceinline__ size_t pt_tile_at(int n, int T, int hb, int& r) {
+    r = n % T;
+    return (size_t)(n / T) * (4 + hb) * T;
+}
+
+// 64-bit limbs -> compact limbs (tiles of T residues: T low words, then T high parts)
+__global__ void k_pt_compact(const u64* in, uint8_t* out, int hb, int T, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t j = blockIdx.y;
+    const u64 v = in[(j << logN) + n];
+    int r;
+    uint8_t* tile = out + j * (4 + hb) * (size_t)N + pt_tile_at(n, T, hb, r);
+    reinterpret_cast<uint32_t*>(tile)[r] = (uint32_t)v;
+    uint8_t* hi = tile + 4 * (size_t)T;
+    if (hb == 1) hi[r] = (uint8_t)(v >> 32);
+    else if (hb == 2) reinterpret_cast<uint16_t*>(hi)[r] = (uint16_t)(v >> 32);
+    else reinterpret_cast<uint32_t*>(hi)[r] = (uint32_t)(v >> 32);
+}
+
+__global__ void k_pmult_compact(const u64* ct, const uint8_t* pt, u64* out, const Modulus* mods, int nl, int hb,
+                                int T, int logN, int accumulate) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.y;  // limb
+    const Modulus m = mods[i];
+    int r;
+    const uint8_t* tile = pt + (size_t)i * (4 + hb) * N + pt_tile_at(n, T, hb, r);
+    const uint8_t* hi = tile + 4 * (size_t)T;
+    const u64 h = hb == 1 ? (u64)hi[r] : (hb == 2 ? (u64)reinterpret_cast<const uint16_t*>(hi)[r]
+                                                  : (u64)reinterpret_cast<const uint32_t*>(hi)[r]);
+    const u64 p = (u64)reinterpret_cast<const uint32_t*>(tile)[r] | (h << 32);
+    for (int poly = 0; poly < 2; poly++) {
+        const size_t o = ((size_t)poly * nl + i) * N + n;
+        u64 v = mul_mod(ct[o], p, m);
+        out[o] = accumulate ? add_mod(out[o], v, m.q) : v;
     }
 }
 
@@ -600,30 +663,54 @@ void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, in
     c->cnt.launches++;
 }
 
+template <int W, int HB>
+static void mac_launch(dim3 g, int threads, size_t smem, cudaStream_t st, const MacItem* items, const MacTerm* terms,
+                       const Modulus* mods, const int* mm, int nl, int logN, int T, uint32_t* status) {
+    static bool set = false;
+    if (!set) set = cudaFuncSetAttribute(k_mac<W, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    k_mac<W, HB><<<g, threads, smem, st>>>(items, terms, mods, mm, nl, logN, T, status);
+}
+
 void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
                 int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st, bool qp) {
     if (!n_items) return;
     const int nl = qp ? level + 1 + c->k : level + 1;
-    ProfScope ps(c, PK_MAC, st, 8.0 * c->N * nl * (2.0 * n_ct_terms + (double)n_pt_terms + 2.0 * n_outputs));
-    const int T = std::min(kMacTile, c->N);
+    ProfScope ps(c, PK_MAC, st, (double)c->N * nl * (8.0 * (2.0 * n_ct_terms + 2.0 * n_outputs) +
+                                                     (4.0 + c->pt_hb) * n_pt_terms));
+    const int T = pt_tile(c);
     const dim3 g(n_items, c->N / T, nl);
     const int threads = T / 2 + 32;
     const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
     const size_t smem = 256 + (size_t)kMacStageBytes;
     const int* mm = nl == level + 1 ? nullptr : c->lv[level].d_ks_limbs;
-    if (w == 1) {
-        static bool set1 = false;
-        if (!set1) set1 = cudaFuncSetAttribute(k_mac<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-        k_mac<1><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
-    } else if (w == 2) {
-        static bool set2 = false;
-        if (!set2) set2 = cudaFuncSetAttribute(k_mac<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-        k_mac<2><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
+#define FE_MAC(W, HB) mac_launch<W, HB>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
+    if (c->pt_hb == 1) {
+        if (w == 1) FE_MAC(1, 1);
+        else if (w == 2) FE_MAC(2, 1);
+        else FE_MAC(4, 1);
+    } else if (c->pt_hb == 2) {
+        if (w == 1) FE_MAC(1, 2);
+        else if (w == 2) FE_MAC(2, 2);
+        else FE_MAC(4, 2);
     } else {
-        static bool set4 = false;
-        if (!set4) set4 = cudaFuncSetAttribute(k_mac<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-        k_mac<4><<<g, threads, smem, st>>>(items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status);
+        if (w == 1) FE_MAC(1, 4);
+        else if (w == 2) FE_MAC(2, 4);
+        else FE_MAC(4, 4);
     }
+#undef FE_MAC
+    c->cnt.launches++;
+}
+
+void launch_pt_compact(fe_ctx* c, const u64* in, uint8_t* out, int n_limbs, cudaStream_t st) {
+    if (n_limbs <= 0) return;
+    k_pt_compact<<<grid_for(c->N, n_limbs), kB, 0, st>>>(in, out, c->pt_hb, pt_tile(c), c->logN);
+    c->cnt.launches++;
+}
+
+void launch_pmult_compact(fe_ctx* c, const u64* ct, const uint8_t* pt, u64* out, int level, bool accumulate,
+                          cudaStream_t st) {
+    k_pmult_compact<<<grid_for(c->N, level + 1), kB, 0, st>>>(ct, pt, out, c->d_mod, level + 1, c->pt_hb,
+                                                             pt_tile(c), c->logN, accumulate ? 1 : 0);
     c->cnt.launches++;
 }
 

@@ -89,10 +89,21 @@ struct MacItem {
     int term0[kMacWays];
     int n_terms, n_out;
 };
+// Plan plaintexts are stored compactly, limb by limb, each limb as N / T tiles
+// of T = pt_tile(c) residues: the T low 32-bit words, then the T high parts of
+// c->pt_hb bytes each, so one limb takes (4 + pt_hb) N bytes and the PMult-MAC
+// fetches a tile with one bulk copy.
 struct MacTerm {
-    const u64* ct;  // [2][l+1][N]
-    const u64* pt;  // [l+1][N]
+    const u64* ct;      // [2][l+1][N]
+    const uint8_t* pt;  // compact plaintext, l+1 limbs
 };
+inline size_t pt_limb_bytes(const fe_ctx* c) { return (size_t)(4 + c->pt_hb) * c->N; }
+inline int pt_tile(const fe_ctx* c) { return c->N < 512 ? c->N : 512; }
+// n_limbs 64-bit limbs [n_limbs][N] -> compact limbs
+void launch_pt_compact(fe_ctx* c, const u64* in, uint8_t* out, int n_limbs, cudaStream_t st);
+// out (+)= ct (x) pt for one ciphertext at `level` and a compact plaintext
+void launch_pmult_compact(fe_ctx* c, const u64* ct, const uint8_t* pt, u64* out, int level, bool accumulate,
+                          cudaStream_t st);
 
 // Base conversion of n_poly polynomials: source modulus src[i] is read at position
 // ext_pos(src[i]) - in_pos_base of an input polynomial (stride in_stride words),

@@ -224,6 +224,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->mod.insert(c->mod.end(), sp.begin(), sp.end());
     c->max_mod_bits = 0;
     for (u64 m : c->mod) c->max_mod_bits = std::max(c->max_mod_bits, 64 - __builtin_clzll(m));
+    c->pt_hb = c->max_mod_bits <= 40 ? 1 : (c->max_mod_bits <= 48 ? 2 : 4);
 
     int dev;
     FE_CUDA_TRY(cudaGetDevice(&dev));

@@ -136,8 +136,7 @@ def bench_mac(ctx, torch, args):
         ctx.he_layer_timing(t.evk, plan, t.pts, t.n_pool, x, out, ws)
     ms, n, b = ctx.profile_end()
     peak, src = hbm_peak()
-    limb = ctx.N * 8
-    pt_bytes = i.n_pt * (lv + 1) * limb * args.reps
+    pt_bytes = i.pt_bytes * args.reps
     return {"kernel": "mac", "level": lv, "n_pt": i.n_pt, "launches": n, "ms": ms / args.reps,
             "pt_GBps": pt_bytes / (ms / 1e3) / 1e9, "algorithmic_GBps": b / (ms / 1e3) / 1e9,
             "hbm_frac": b / (ms / 1e3) / 1e9 / peak, "peak_GBps": peak, "peak_source": src,

@@ -387,6 +387,23 @@ def test_conv_parity_double_hoisted(tiny, H, C, Co, K, BS, S, stride, n1, dw):
 
 
 
+@pytest.mark.parametrize("pbits,hb", [(36, 1), (45, 2), (52, 4)])
+def test_compact_plaintext_widths(pbits, hb):
+    """Plan plaintexts are stored as a 32-bit low plane plus a 1-, 2- or 4-byte
+    high plane, chosen by the widest modulus; every width gives the oracle's
+    residues in both paths, with plaintexts on Q (single hoisting) and on Q P
+    (double hoisting, where the special primes set the width)."""
+    P = Pair(10, 3, 1, 30, pbits)
+    rng = np.random.default_rng(pbits)
+    x = rng.uniform(0, 1, (1, 6, 6, 6))
+    w = rng.normal(0, 1 / 3, (5, 6, 3, 3))
+    for dh in (False, True):
+        plan, _ = run_conv_pair(P, x, w, 1, bsgs_n1=2, double_hoist=dh)
+        nl = P.pr.L + 1 + (P.pr.k if dh else 0)
+        assert plan.info.pt_bytes == plan.info.n_pt * nl * (4 + hb) * P.pr.N
+    assert P.g.device_status() == 0
+
+
 @pytest.mark.parametrize("logN", [14, 16])
 def test_ntt_radix16_equals_radix8_and_oracle(logN):
     """The radix-16 round variant of the NTT gives the same residues."""
