@@ -411,7 +411,10 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);
-        if ((t & 15) == 15) {
+        // a product is below 2^80 when every modulus is below 2^40 (HB = 1) and
+        // below 2^96 below 2^48 (HB = 2), so 2^31 terms fit the 128-bit sums;
+        // wider moduli (products below 2^120) fold every 16 terms
+        if (HB == 4 && (t & 15) == 15) {
 #pragma unroll
             for (int k = 0; k < W; k++) {
                 if (k >= it.n_out) break;

@@ -29,8 +29,10 @@ def models():
         xs = [W.lenet_input(i, lenet.BS) for i in range(3)]
         l_in = [lenet.encrypt(x, seed=40 + i).cpu().pin_memory() for i, x in enumerate(xs)]
         p = W.PARAMS["mobilenet_small"]
-        c_mb = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])   # N = 2^12
-        mb = MobileNetBlocks(c_mb, blocks=[(8, 16, 16)], delta=p["delta"])
+        # N = 2^14: a block request keeps the device busy for milliseconds, longer
+        # than the host takes to enqueue a LeNet group, so overlap is observable
+        c_mb = fe.Context(14, p["n_q"], p["k"], p["bits"], p["pbits"])
+        mb = MobileNetBlocks(c_mb, blocks=[(32, 32, 32)], delta=p["delta"])
         m_in = [mb.inputs[0].cpu().pin_memory()]
         torch.cuda.synchronize()
     return dict(lenet=lenet, xs=xs, wts=wts, l_in=l_in, mb=mb, m_in=m_in, stream=s)
@@ -50,8 +52,9 @@ def _out_buf(srv, model):
 
 
 def _workload(M):
-    # 10 requests: LeNet inputs 0, 1, 2 and the MobileNet-shaped block, interleaved
-    kinds = ["l0", "m", "l1", "l2", "m", "l0", "l1", "m", "l2", "l0"]
+    # 10 requests: LeNet inputs 0, 1, 2 and the MobileNet-shaped block, interleaved;
+    # the block's group is formed first, the LeNet groups run beside it
+    kinds = ["m", "l0", "l1", "m", "l2", "l0", "m", "l1", "l2", "l0"]
     return kinds
 
 
