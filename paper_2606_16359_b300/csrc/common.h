@@ -47,7 +47,8 @@ int fail(int code, const std::string& msg);
 // ---------------------------------------------------------------------------
 struct Modulus {
     u64 q;
-    u64 ratio_hi, ratio_lo;
+    u64 ratio_hi, ratio_lo;  // floor(2^128 / q)
+    u64 mu88;                // floor(2^88 / q) (q > 2^24), for reduce_narrow
 };
 
 #if defined(__CUDACC__)
@@ -82,6 +83,16 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const Modulus& m) {
 }
 __device__ __forceinline__ u64 reduce128(u128 x, const Modulus& m) {
     return reduce128((u64)(x >> 64), (u64)x, m);
+}
+// x mod q for x < 2^84 and 2^25 <= q < 2^62 (sums of up to 16 products of
+// residues below 2^40).  qhat = floor(floor(x / 2^24) mu88 / 2^64) is at most
+// x / q and misses it by less than x / 2^88 + 2^24 / q < 1 (the two floors), so
+// it is floor(x / q) or one less and one conditional subtraction finishes: one
+// 64x64 high product and one low product instead of reduce128's four and one.
+__device__ __forceinline__ u64 reduce_narrow(u128 x, const Modulus& m) {
+    const u64 qhat = __umul64hi((u64)(x >> 24), m.mu88);
+    const u64 r = (u64)x - qhat * m.q;
+    return r >= m.q ? r - m.q : r;
 }
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
     return reduce128((u128)a * b, m);

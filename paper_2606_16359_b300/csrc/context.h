@@ -69,6 +69,9 @@ struct fe_ctx {
     // compact plan plaintexts: bytes of the high-bit plane per residue (1 when
     // every modulus is below 2^40, 2 below 2^48, else 4)
     int pt_hb;
+    // every modulus in [2^25, 2^40], dnum <= 15 and k <= 15: the base conversion
+    // and key inner product sums (< 16 products) reduce with reduce_narrow
+    int narrow;
     int ntt_radix = 8;  // elements per thread per NTT round (8 or 16; 16 compiled for N = 2^14, 2^16)
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;

@@ -19,7 +19,7 @@ inline dim3 grid_for(int N, int y, int z = 1) { return dim3((N + kB - 1) / kB, y
 // One thread per (coefficient, polynomial).
 // ------------------------------------------------------------------------
 // kS = number of source moduli (compile time, so that the digits stay in registers)
-template <int kS>
+template <int kS, bool kNarrow>
 __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int logN,
                         const u64* in, size_t in_stride, int in_pos_base, u64* out,
                         size_t out_stride, int copy_src) {
@@ -46,7 +46,7 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
         const u64* row = t.mat + d * kS;
 #pragma unroll
         for (int i = 0; i < kS; i++) acc += (u128)y[i] * row[i];
-        op[((size_t)ext_pos(mt, L, level) << logN) + n] = reduce128(acc, mods[mt]);
+        op[((size_t)ext_pos(mt, L, level) << logN) + n] = kNarrow ? reduce_narrow(acc, mods[mt]) : reduce128(acc, mods[mt]);
     }
 }
 
@@ -56,7 +56,7 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
 // over the positions p of Q_level * P.  blockIdx.y = position, z = item.
 // ------------------------------------------------------------------------
 __global__ void k_keyip(const KsItem* items, const Modulus* mods, int L, int level, int k,
-                        int logN, int n_mod) {
+                        int logN, int n_mod, int narrow) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -74,14 +74,14 @@ __global__ void k_keyip(const KsItem* items, const Modulus* mods, int L, int lev
         ab += (u128)e * kb[n];
         aa += (u128)e * ka[n];
     }
-    it.acc[((size_t)p << logN) + n] = reduce128(ab, m);
-    it.acc[((size_t)(np + p) << logN) + n] = reduce128(aa, m);
+    it.acc[((size_t)p << logN) + n] = narrow ? reduce_narrow(ab, m) : reduce128(ab, m);
+    it.acc[((size_t)(np + p) << logN) + n] = narrow ? reduce_narrow(aa, m) : reduce128(aa, m);
 }
 
 // key-stationary form: blockIdx.z = group of items that share one key; kD =
 // number of digits (compile time, so that the key words stay in registers).
 // Each thread handles two consecutive coefficients with 16-byte accesses.
-template <int kD>
+template <int kD, bool kNarrow>
 __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups, const KsItem* items,
                                                           const Modulus* mods, int L, int level, int k,
                                                           int logN, int n_mod) {
@@ -117,8 +117,13 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
             ax += (u128)e[j].x * ka[j].x;
             ay += (u128)e[j].y * ka[j].y;
         }
-        *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce128(bx, m), reduce128(by, m));
-        *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce128(ax, m), reduce128(ay, m));
+        if (kNarrow) {
+            *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce_narrow(bx, m), reduce_narrow(by, m));
+            *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce_narrow(ax, m), reduce_narrow(ay, m));
+        } else {
+            *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce128(bx, m), reduce128(by, m));
+            *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce128(ax, m), reduce128(ay, m));
+        }
     }
 }
 
@@ -593,8 +598,12 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
     const int cs = copy_src ? 1 : 0;
 #define FE_BCONV(S)                                                                                   \
     case S:                                                                                           \
-        k_bconv<S><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride, in_pos_base, out, \
-                                     out_stride, cs);                                                 \
+        if (c->narrow)                                                                                \
+            k_bconv<S, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,      \
+                                               in_pos_base, out, out_stride, cs);                     \
+        else                                                                                          \
+            k_bconv<S, false><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,     \
+                                                in_pos_base, out, out_stride, cs);                    \
         break;
     switch (t.n_src) {
         FE_BCONV(1) FE_BCONV(2) FE_BCONV(3) FE_BCONV(4) FE_BCONV(5) FE_BCONV(6) FE_BCONV(7) FE_BCONV(8)
@@ -609,7 +618,7 @@ void launch_keyip(fe_ctx* c, const KsItem* items, int n_items, int level, cudaSt
     const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
     ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * n_items * (3.0 * dn + 2));
     k_keyip<<<grid_for(c->N, level + 1 + c->k, n_items), kB, 0, st>>>(items, c->d_mod, c->L, level,
-                                                                     c->k, c->logN, c->n_mod);
+                                                                     c->k, c->logN, c->n_mod, c->narrow);
     c->cnt.launches++;
 }
 
@@ -619,15 +628,28 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
     const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
     ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + (double)n_items * (dn + 2)));
     const dim3 g(n_groups, (c->N / 2 + kB - 1) / kB, level + 1 + c->k);  // two coefficients per thread
+    // narrow reductions for up to 8 digits (the sums stay below 2^84)
+#define FE_KEYIP_N(D)                                                                                 \
+    case D:                                                                                           \
+        if (c->narrow)                                                                                \
+            k_keyip_grouped<D, true><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
+                                                       c->n_mod);                                     \
+        else                                                                                          \
+            k_keyip_grouped<D, false><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
+                                                        c->n_mod);                                    \
+        break;
 #define FE_KEYIP(D)                                                                                   \
     case D:                                                                                           \
-        k_keyip_grouped<D><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod); \
+        k_keyip_grouped<D, false><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
+                                                    c->n_mod);                                        \
         break;
     switch (dn) {
-        FE_KEYIP(1) FE_KEYIP(2) FE_KEYIP(3) FE_KEYIP(4) FE_KEYIP(5) FE_KEYIP(6) FE_KEYIP(7) FE_KEYIP(8)
-        FE_KEYIP(9) FE_KEYIP(10) FE_KEYIP(11) FE_KEYIP(12) FE_KEYIP(13) FE_KEYIP(14) FE_KEYIP(15) FE_KEYIP(16)
+        FE_KEYIP_N(1) FE_KEYIP_N(2) FE_KEYIP_N(3) FE_KEYIP_N(4) FE_KEYIP_N(5) FE_KEYIP_N(6) FE_KEYIP_N(7)
+        FE_KEYIP_N(8) FE_KEYIP(9) FE_KEYIP(10) FE_KEYIP(11) FE_KEYIP(12) FE_KEYIP(13) FE_KEYIP(14)
+        FE_KEYIP(15) FE_KEYIP(16)
         default: break;  // dnum <= 16 (checked at context creation)
     }
+#undef FE_KEYIP_N
 #undef FE_KEYIP
     c->cnt.launches++;
 }

@@ -50,6 +50,7 @@ Modulus make_modulus(u64 q) {
     m.q = q;
     m.ratio_hi = (u64)(r >> 64);
     m.ratio_lo = (u64)r;
+    m.mu88 = q > (1ull << 24) ? (u64)(((u128)1 << 88) / q) : 0;
     return m;
 }
 
@@ -225,6 +226,12 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->max_mod_bits = 0;
     for (u64 m : c->mod) c->max_mod_bits = std::max(c->max_mod_bits, 64 - __builtin_clzll(m));
     c->pt_hb = c->max_mod_bits <= 40 ? 1 : (c->max_mod_bits <= 48 ? 2 : 4);
+    {
+        int min_bits = 64;
+        for (u64 m : c->mod) min_bits = std::min(min_bits, 64 - __builtin_clzll(m));
+        // sums of up to 16 products of residues below 2^40 stay below 2^84
+        c->narrow = c->max_mod_bits <= 40 && min_bits >= 26 && c->dnum <= 15 && c->k <= 15 ? 1 : 0;
+    }
 
     int dev;
     FE_CUDA_TRY(cudaGetDevice(&dev));
