@@ -112,13 +112,53 @@ class MobileNetBlocks:
             self.ctx.he_layer_batch(self.evk, l_["plan"], l_["pt"], l_["inp"], self.batch, mode=mode, ws=self.ws,
                                     out=l_["out"])
 
-    def capture(self):
-        plans = [l_["plan"] for l_ in self.layers]
-        self.graph_ws = self.ctx.workspace(self.ctx.graph_workspace_bytes(plans, self.batch))
-        self.graph = self.ctx.graph_capture(self.evk, plans, [l_["pt"] for l_ in self.layers],
-                                            [l_["inp"] for l_ in self.layers], [l_["out"] for l_ in self.layers],
-                                            self.graph_ws, n_req=self.batch)
-        return self.graph
+    def capture(self, concurrent=True):
+        """CUDA graph(s) of one step.  concurrent: the blocks are independent, so
+        each gets its own graph, workspace and stream and launch() runs them side
+        by side (one block's kernels and copies overlap another's); otherwise one
+        graph runs all layers in order in one shared workspace."""
+        torch = _torch()
+        groups = ([self.layers[2 * b:2 * b + 2] for b in range(len(self.blocks))] if concurrent
+                  else [self.layers])
+        self.graphs, self.graph_ws, self.streams = [], [], []
+        for ls in groups:
+            plans = [l_["plan"] for l_ in ls]
+            ws = self.ctx.workspace(self.ctx.graph_workspace_bytes(plans, self.batch))
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                g = self.ctx.graph_capture(self.evk, plans, [l_["pt"] for l_ in ls], [l_["inp"] for l_ in ls],
+                                           [l_["out"] for l_ in ls], ws, n_req=self.batch)
+            torch.cuda.current_stream().wait_stream(s)
+            self.graphs.append(g)
+            self.graph_ws.append(ws)
+            self.streams.append(s)
+        self.graph = self.graphs[0] if len(self.graphs) == 1 else None
+        self._fork = torch.cuda.Event()
+        self._join = [torch.cuda.Event() for _ in self.graphs]
+        return self.graphs
+
+    def launch(self, h_in=None, h_out=None):
+        """One step through the captured graph(s) on the current stream: fork to
+        the per-graph streams, optionally copy each block's input from pinned host
+        memory first (h_in) and its output back after (h_out), join."""
+        torch = _torch()
+        main = torch.cuda.current_stream()
+        self._fork.record(main)
+        per = len(self.blocks) // len(self.graphs)
+        for i, (g, s) in enumerate(zip(self.graphs, self.streams)):
+            s.wait_event(self._fork)
+            with torch.cuda.stream(s):
+                blocks = range(i * per, (i + 1) * per)
+                if h_in is not None:
+                    for b in blocks:
+                        self.inputs[b].copy_(h_in[b], non_blocking=True)
+                g.launch()
+                if h_out is not None:
+                    for b in blocks:
+                        h_out[b].copy_(self.outputs[b], non_blocking=True)
+            self._join[i].record(s)
+            main.wait_event(self._join[i])
 
     def serve_ops(self, bi):
         """Operation chain of block bi for the request loop (dw then pw)."""

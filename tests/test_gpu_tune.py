@@ -59,3 +59,28 @@ def test_batched_blocks_graph_decrypt_every_input():
         one = single.outputs[0].cpu().numpy()
     assert max(errs) < 1e-3, errs
     assert np.array_equal(out[:one.shape[0]], one)
+
+
+def test_concurrent_block_graphs_equal_sequential():
+    """One graph per independent block, launched side by side on their own
+    streams with the host copies in and out inside each stream: the outputs
+    copied back equal the residues of the layers run one after another."""
+    p = W.PARAMS["mobilenet_small"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        net = MobileNetBlocks(ctx, blocks=[(8, 16, 16), (8, 32, 32), (4, 64, 64)], delta=p["delta"], schedule=4)
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        want = [o.cpu().numpy() for o in net.outputs]
+        net.capture(concurrent=True)
+        assert len(net.graphs) == 3
+        h_in = [t.cpu().pin_memory() for t in net.inputs]
+        h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in net.outputs]
+        for t in net.inputs + net.outputs:
+            t.zero_()
+        for _ in range(2):
+            net.launch(h_in, h_out)
+        torch.cuda.synchronize()
+    for w_, h in zip(want, h_out):
+        assert np.array_equal(h.numpy(), w_)
