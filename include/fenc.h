@@ -328,7 +328,12 @@ int fe_plan_load_weights(fe_ctx* ctx, fe_plan* plan, const double* weights_host,
  * [n_out_ct][2][level][N] (rescaled once).  mode 0 = plain path (one launch per
  * primitive per ciphertext), mode 1 = batched path (all ciphertexts of a stage
  * in one launch per primitive, key-stationary inner products, summed
- * rotate-and-add).  Both produce identical residues.
+ * rotate-and-add).  Both produce identical residues.  mode 2 = the layer
+ * composed from single-ciphertext operations as a per-operation HE library
+ * runs it: every rotation a full key switch of its own (no hoisting), one
+ * PMult per term, one rotation and addition per partial sum, one rescale per
+ * output; it gives the residues of single hoisting (also for a plan set to
+ * double hoisting, whose Q*P plaintexts it reads on Q) and is not captured.
  * Errors: FE_EKEY, FE_ENOMEM (workspace too small). */
 int fe_he_conv(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev,
                const void* in_dev, void* out_dev, void* workspace_dev, size_t workspace_bytes,

@@ -210,6 +210,98 @@ size_t plan_chunk(const fe_plan* p, size_t R, int mode, size_t data_bytes, bool 
     return chunk;
 }
 
+// The layer composed from single-ciphertext operations, as a client of a
+// per-operation HE library writes it (mode 2): every rotation, inner or outer,
+// is a full key switch of its own (ModUp, key inner product, ModDown,
+// automorphism: no hoisting, no key reuse across ciphertexts); every term is one
+// PMult accumulated into its sum; each rotated partial sum is added to its
+// output; each output is rescaled alone.  Same plan, rotations and plaintexts
+// (the Q limbs of Q*P plaintexts under double hoisting); the residues are those
+// of single hoisting.  One request at a time; nothing is captured.
+int run_plan_per_op(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, const u64* b_pt, u64* b_out,
+                    void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int lv = p->level;
+    const Sizes z = sizes_of(c, lv);
+    const size_t ctw_out = ct_words(c, lv - 1);
+    const size_t ptb = (size_t)(p->dhoist ? lv + 1 + c->k : lv + 1) * pt_limb_bytes(c);
+    std::map<int32_t, const u64*> keys;
+    for (int32_t s : p->steps) {
+        const u64* k = evk_key(evk, c->galois(s));
+        if (!k) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(s));
+        keys[s] = k;
+    }
+    size_t n_rot = p->inner.size();
+    for (const auto& o : p->outs)
+        for (const auto& g : o.groups) n_rot += g.step != 0;
+    Carver cv(ws, ws_bytes);
+    KsItem* d_ks = cv.take<KsItem>(std::max<size_t>(1, n_rot));
+    CombineItem* d_cb = cv.take<CombineItem>(std::max<size_t>(1, n_rot));
+    u64* Rb = cv.take<u64>(p->inner.size() * z.ctw);
+    u64* total = cv.take<u64>((size_t)p->n_out * z.ctw);
+    u64* Pd = cv.take<u64>(z.ctw);
+    u64* T = cv.take<u64>(z.ctw);
+    u64* coef = cv.take<u64>(z.nlN);
+    u64* ext = cv.take<u64>(z.extw);
+    u64* acc = cv.take<u64>(z.accw);
+    u64* conv = cv.take<u64>(z.ctw);
+    u64* rs = cv.take<u64>(rescale_tmp_words(c, 1, lv));
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
+    // one key-switch item and one combine item per rotation, in execution order
+    std::vector<KsItem> ks;
+    std::vector<CombineItem> cb;
+    for (size_t i = 0; i < p->inner.size(); i++) {
+        const auto& in = p->inner[i];
+        ks.push_back(KsItem{ext, keys[in.step], acc});
+        cb.push_back(CombineItem{acc, conv, b_in + (size_t)in.ci * z.ctw, nullptr, Rb + i * z.ctw,
+                                 c->galois(in.step), 0});
+    }
+    for (const auto& o : p->outs)
+        for (const auto& g : o.groups)
+            if (g.step) {
+                ks.push_back(KsItem{ext, keys[g.step], acc});
+                cb.push_back(CombineItem{acc, conv, Pd, nullptr, T, c->galois(g.step), 0});
+            }
+    FE_TRY(upload(ks, d_ks, st));
+    FE_TRY(upload(cb, d_cb, st));
+    auto rotate = [&](const u64* src, size_t item) {
+        modup(c, src + z.nlN, z.ctw, 1, lv, coef, ext, st);
+        launch_keyip(c, d_ks + item, 1, lv, st);
+        moddown_prepare(c, acc, 1, lv, conv, st);
+        launch_combine(c, d_cb + item, 1, lv, st);
+    };
+    auto pmults = [&](const fe_plan::Group& g, u64* dst) {
+        for (int t = 0; t < g.nt; t++) {
+            const fe_plan::Term& tm = p->terms[g.t0 + t];
+            const u64* src = tm.src >= 0 ? Rb + (size_t)tm.src * z.ctw : b_in + (size_t)(-tm.src - 1) * z.ctw;
+            launch_pmult_compact(c, src, (const uint8_t*)b_pt + (size_t)tm.pt * ptb, dst, lv, t > 0, st);
+        }
+    };
+    for (size_t i = 0; i < p->inner.size(); i++) rotate(b_in + (size_t)p->inner[i].ci * z.ctw, i);
+    size_t item = p->inner.size();
+    for (int o = 0; o < p->n_out; o++) {
+        u64* out = total + (size_t)o * z.ctw;
+        bool started = false;
+        for (const auto& g : p->outs[o].groups)
+            if (!g.step) {
+                pmults(g, out);
+                started = g.nt > 0;
+            }
+        if (!started) FE_CUDA_TRY(cudaMemsetAsync(out, 0, z.ctw * 8, st));
+        for (const auto& g : p->outs[o].groups)
+            if (g.step) {
+                pmults(g, Pd);
+                rotate(Pd, item++);
+                launch_add(c, out, T, out, 1, lv, st);
+            }
+        rescale_batch(c, out, 1, lv, b_out + (size_t)o * ctw_out, rs, rs + 2 * (size_t)c->N, st);
+    }
+    c->cnt.rot += n_rot;
+    c->cnt.keyswitch += n_rot;
+    c->cnt.pmult += p->terms.size();
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
 // Both phases derive every pointer from (plan, buffers, workspace) alone, so a
 // graph can be captured from the launch phase after an upload phase.
 // n_req requests share the plan, its plaintexts and keys: request r reads its
@@ -220,6 +312,15 @@ size_t plan_chunk(const fe_plan* p, size_t R, int mode, size_t data_bytes, bool 
 int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, const u64* b_pt, u64* b_out,
              void* ws, size_t ws_bytes, int mode, cudaStream_t st, int phase, int n_req, int pt_pool,
              void* data_ws, size_t data_ws_bytes) {
+    if (mode == 2) {  // the per-operation composition, request by request
+        if (!(phase & 2)) return FE_OK;
+        if (pt_pool || data_ws) return fail(FE_EINVAL, "mode 2 runs only real plaintexts, uncaptured");
+        for (int r = 0; r < n_req; r++)
+            FE_TRY(run_plan_per_op(c, evk, p, b_in + (size_t)r * p->n_in * ct_words(c, p->level), b_pt,
+                                   b_out + (size_t)r * p->n_out * ct_words(c, p->level - 1), ws, ws_bytes, st));
+        return FE_OK;
+    }
+    if (mode != 0 && mode != 1) return fail(FE_EINVAL, "mode must be 0, 1 or 2");
     const int N = c->N, lv = p->level;
     Sizes z = sizes_of(c, lv);
     if (n_req < 1) return fail(FE_EINVAL, "n_req must be positive");

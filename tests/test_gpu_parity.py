@@ -387,6 +387,28 @@ def test_conv_parity_double_hoisted(tiny, H, C, Co, K, BS, S, stride, n1, dw):
 
 
 
+@pytest.mark.parametrize("n1", [0, 4])
+def test_per_operation_path(tiny, n1):
+    """Mode 2 composes the layer from single-ciphertext operations (every
+    rotation a key switch of its own, one PMult per term, one rescale per
+    output): residues equal to the oracle's single-hoisted schedule, and on a
+    plan whose plaintexts are encoded on Q P (double hoisting) equal to the
+    single-hoisted plan's."""
+    rng = np.random.default_rng(11 + n1)
+    x = rng.uniform(0, 1, (1, 20, 6, 6))
+    w = rng.normal(0, 1 / 3, (18, 20, 3, 3))
+    plan, outs = run_conv_pair(tiny, x, w, 1, bsgs_n1=n1, modes=(1, 2))
+    g = tiny.g
+    lay = g.layout(6, 6, 20, 1, 1)
+    dplan = g.plan_conv(lay, 18, 3, level=tiny.pr.L, bsgs_n1=n1, double_hoist=True)
+    sk = g.sk_gen(3)
+    evk = g.evk_gen(sk, 3, dplan.steps)
+    ct = g.encrypt(sk, g.pack(lay, torch.from_numpy(x)), tiny.pr.L, 2.0 ** 25, seed=17)
+    pt = g.load_weights(dplan, w, float(tiny.pr.q[tiny.pr.L]))
+    assert np.array_equal(u64(g.he_conv(evk, dplan, pt, ct, mode=2)), u64(outs[2]))
+    assert g.device_status() == 0
+
+
 @pytest.mark.parametrize("pbits,hb", [(36, 1), (45, 2), (52, 4)])
 def test_compact_plaintext_widths(pbits, hb):
     """Plan plaintexts are stored as a 32-bit low plane plus a 1-, 2- or 4-byte
