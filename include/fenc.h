@@ -132,6 +132,22 @@ void fe_ctx_destroy(fe_ctx* ctx);
  * 2^16, other ring degrees stay at 8).  Results do not depend on it.
  * Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
+/* Generator behind every sampler of the context (secret key, encryption
+ * randomness and errors, evaluation keys).  Each sample is drawn from word n of
+ * a stream addressed by (seed, tag):
+ *   FE_GEN_SPLITMIX64 (default): SplitMix64 (Steele, Lea, Flood 2014),
+ *     word = mix(mix(seed + (tag + 1) g) + (n + 1) g), g = 0x9E3779B97F4A7C15;
+ *   FE_GEN_CHACHA20: the ChaCha20 block function of RFC 8439 with key =
+ *     (seed low, seed high, key_material[0..5]) as eight 32-bit words, nonce =
+ *     (tag low, tag high, 0) and block counter n / 8; the word is output words
+ *     2 (n mod 8) and 2 (n mod 8) + 1 of that block, low word first.
+ * key_material: six 32-bit words (host), required for ChaCha20, ignored for
+ * SplitMix64.  Samplers: uniform mod q = floor(word q / 2^64); ternary =
+ * floor(3 word / 2^64) - 1; error = popcount(word bits 0..20) - popcount(bits
+ * 21..41).  Errors: FE_EINVAL. */
+#define FE_GEN_SPLITMIX64 0
+#define FE_GEN_CHACHA20 1
+int fe_ctx_set_generator(fe_ctx* ctx, int kind, const uint32_t* key_material);
 /* Copy the n_q + k moduli (q_0..q_L, p_0..p_{k-1}) to moduli_host. */
 int fe_ctx_moduli(const fe_ctx* ctx, uint64_t* moduli_host);
 /* Read / reset the operation counters of the context. */

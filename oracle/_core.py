@@ -37,6 +37,9 @@ _sig = {
     "or_vec_gather": (None, [P, P, P, ctypes.c_int]),
     "or_mix64": (u64, [u64]),
     "or_word": (u64, [u64, u64, u64]),
+    "or_chacha_quarter": (None, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "or_chacha20_block": (None, [P, ctypes.c_uint32, P, P]),
+    "or_set_generator": (None, [ctypes.c_int, P]),
     "or_sample_uniform": (None, [u64, u64, u64, P, ctypes.c_int]),
     "or_sample_ternary": (None, [u64, u64, P, ctypes.c_int]),
     "or_sample_cbd21": (None, [u64, u64, P, ctypes.c_int]),
@@ -181,6 +184,27 @@ def mix64(z):
 
 def word(master, tag, n):
     return int(_lib.or_word(master, tag, n))
+
+
+def chacha_quarter(a, b, c, d):
+    s = np.array([a, b, c, d], dtype=np.uint32)
+    _lib.or_chacha_quarter(_p(s), 0, 1, 2, 3)
+    return tuple(int(v) for v in s)
+
+
+def chacha20_block(key8, counter, nonce3):
+    k = np.ascontiguousarray(key8, dtype=np.uint32)
+    nc = np.ascontiguousarray(nonce3, dtype=np.uint32)
+    out = np.empty(16, dtype=np.uint32)
+    _lib.or_chacha20_block(_p(k), counter, _p(nc), _p(out))
+    return out
+
+
+def set_generator(kind, key6=None):
+    """Generator of every sampler: "splitmix64" (default) or "chacha20" keyed by
+    (master seed, key6: six 32-bit words of key material)."""
+    k = np.ascontiguousarray(key6 if key6 is not None else np.zeros(6), dtype=np.uint32)
+    _lib.or_set_generator({"splitmix64": 0, "chacha20": 1}[kind], _p(k))
 
 
 def sample_uniform(master, tag, q, n):

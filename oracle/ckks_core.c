@@ -247,9 +247,67 @@ u64 or_mix64(u64 z) {
     return z ^ (z >> 31);
 }
 
-/* SplitMix64 output number (n+1) of the stream whose seed is output number
- * (tag+1) of the generator seeded with `master`. */
+/* ChaCha20 (RFC 8439, Sec. 2.1-2.3).  The quarter round on four 32-bit
+ * words: add, xor, rotate left by 16, 12, 8 and 7. */
+static uint32_t rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+void or_chacha_quarter(uint32_t *s, int a, int b, int c, int d) {
+    s[a] += s[b]; s[d] ^= s[a]; s[d] = rotl32(s[d], 16);
+    s[c] += s[d]; s[b] ^= s[c]; s[b] = rotl32(s[b], 12);
+    s[a] += s[b]; s[d] ^= s[a]; s[d] = rotl32(s[d], 8);
+    s[c] += s[d]; s[b] ^= s[c]; s[b] = rotl32(s[b], 7);
+}
+
+/* Block function: state = the four constants "expand 32-byte k", the eight
+ * key words, the block counter and the three nonce words; ten double rounds
+ * (four column quarter rounds, then four diagonal ones); the output is the
+ * final state plus the initial state, word by word. */
+void or_chacha20_block(const uint32_t key[8], uint32_t counter, const uint32_t nonce[3], uint32_t out[16]) {
+    uint32_t init[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u};
+    for (int i = 0; i < 8; i++) init[4 + i] = key[i];
+    init[12] = counter;
+    for (int i = 0; i < 3; i++) init[13 + i] = nonce[i];
+    uint32_t x[16];
+    memcpy(x, init, sizeof x);
+    for (int round = 0; round < 10; round++) {
+        or_chacha_quarter(x, 0, 4, 8, 12);
+        or_chacha_quarter(x, 1, 5, 9, 13);
+        or_chacha_quarter(x, 2, 6, 10, 14);
+        or_chacha_quarter(x, 3, 7, 11, 15);
+        or_chacha_quarter(x, 0, 5, 10, 15);
+        or_chacha_quarter(x, 1, 6, 11, 12);
+        or_chacha_quarter(x, 2, 7, 8, 13);
+        or_chacha_quarter(x, 3, 4, 9, 14);
+    }
+    for (int i = 0; i < 16; i++) out[i] = x[i] + init[i];
+}
+
+/* Generator of the samplers: 0 = SplitMix64 (default), 1 = ChaCha20 keyed by
+ * (master seed, 192 bits of key material). */
+static int g_gen = 0;
+static uint32_t g_key6[6];
+
+void or_set_generator(int kind, const uint32_t *key6) {
+    g_gen = kind;
+    for (int i = 0; i < 6; i++) g_key6[i] = key6 ? key6[i] : 0;
+}
+
+/* Word n of stream `tag`:
+ *   SplitMix64: output number (n+1) of the stream whose seed is output number
+ *   (tag+1) of the generator seeded with `master`;
+ *   ChaCha20: key = (master low, master high, key material), nonce = (tag low,
+ *   tag high, 0), block counter n / 8; the word is output words 2 (n mod 8) and
+ *   2 (n mod 8) + 1 of that block, low word first. */
 u64 or_word(u64 master, u64 tag, u64 n) {
+    if (g_gen == 1) {
+        uint32_t key[8] = {(uint32_t)master, (uint32_t)(master >> 32)};
+        for (int i = 0; i < 6; i++) key[2 + i] = g_key6[i];
+        const uint32_t nonce[3] = {(uint32_t)tag, (uint32_t)(tag >> 32), 0};
+        uint32_t blk[16];
+        or_chacha20_block(key, (uint32_t)(n >> 3), nonce, blk);
+        const int j = 2 * (int)(n & 7);
+        return (u64)blk[j] | ((u64)blk[j + 1] << 32);
+    }
     u64 s = or_mix64(master + (tag + 1) * GOLDEN_GAMMA);
     return or_mix64(s + (n + 1) * GOLDEN_GAMMA);
 }

@@ -115,6 +115,7 @@ SIGNATURES = {
     "fe_ctx_create": (cint, [P(FeParams), P(vp)]),
     "fe_ctx_destroy": (None, [vp]),
     "fe_ctx_moduli": (cint, [vp, P(u64)]),
+    "fe_ctx_set_generator": (cint, [vp, cint, P(u32)]),
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
@@ -346,6 +347,13 @@ class Context:
         out = torch.empty((n, self.N // 2), dtype=torch.float64, device="cuda")
         check(load().fe_decrypt_decode(self.handle, _ptr(sk), _ptr(ct), n, level, scale, _ptr(out), _stream()))
         return out
+
+    def set_generator(self, kind, key_material=None):
+        """Generator of every sampler: "splitmix64" (default) or "chacha20" keyed by
+        (seed, key_material: six 32-bit words) (see fe_ctx_set_generator)."""
+        code = {"splitmix64": 0, "chacha20": 1}[kind]
+        arr = (u32 * 6)(*[int(v) & 0xFFFFFFFF for v in (key_material if key_material is not None else [0] * 6)])
+        check(load().fe_ctx_set_generator(self.handle, code, arr))
 
     def set_ntt_radix(self, radix):
         check(load().fe_ctx_set_ntt_radix(self.handle, radix))

@@ -45,6 +45,13 @@ int fail(int code, const std::string& msg);
 // A modulus with the constants its reductions need.
 //   ratio = floor(2^128 / q) as (hi, lo) words, for 128-bit Barrett reduction.
 // ---------------------------------------------------------------------------
+// Generator of the samplers (see prng.cuh): kind and ChaCha20 key material.
+enum : int { kGenSplitMix64 = 0, kGenChaCha20 = 1 };
+struct GenKey {
+    int kind;
+    uint32_t k[6];
+};
+
 struct Modulus {
     u64 q;
     u64 ratio_hi, ratio_lo;  // floor(2^128 / q)

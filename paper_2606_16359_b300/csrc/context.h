@@ -69,6 +69,7 @@ struct fe_ctx {
     // compact plan plaintexts: bytes of the high-bit plane per residue (1 when
     // every modulus is below 2^40, 2 below 2^48, else 4)
     int pt_hb;
+    fe::GenKey gen{};  // generator of the samplers (SplitMix64 unless set to ChaCha20)
     // every modulus in [2^25, 2^40], dnum <= 15 and k <= 15: the base conversion
     // and key inner product sums (< 16 products) reduce with reduce_narrow
     int narrow;

@@ -541,37 +541,23 @@ __global__ void k_tensor(const u64* x, const u64* y, u64* d, const Modulus* mods
     d[db + 2 * s + o] = mul_mod(x1, y1, m);
 }
 
-// ------------------------------------------------------------------------
-// Counter-based generator: SplitMix64 (Steele, Lea, Flood 2014).
-// word(seed, tag, n) = mix(mix(seed + (tag+1) g) + (n+1) g), g = 0x9E3779B97F4A7C15.
-// ------------------------------------------------------------------------
-__device__ __forceinline__ u64 sm_mix(u64 z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ u64 stream_word(u64 seed, u64 tag, u64 n) {
-    const u64 g = 0x9E3779B97F4A7C15ull;
-    return sm_mix(sm_mix(seed + (tag + 1) * g) + (n + 1) * g);
-}
-
-__global__ void k_sample_uniform(u64 seed, u64 tag_base, u64* out, const int* mod_idx,
+__global__ void k_sample_uniform(GenKey gk, u64 seed, u64 tag_base, u64* out, const int* mod_idx,
                                  const Modulus* mods, int logN) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int l = blockIdx.y;
     const int mi = mod_idx[l];
-    const u64 w = stream_word(seed, tag_base + (u64)mi, (u64)n);
+    const u64 w = gen_word(gk, seed, tag_base + (u64)mi, (u64)n);
     out[((size_t)l << logN) + n] = (u64)(((u128)w * mods[mi].q) >> 64);
 }
 
 // kind 0: ternary floor(3 w / 2^64) - 1; kind 1: centred binomial eta = 21
-__global__ void k_sample_signed(u64 seed, u64 tag, int kind, i64* out, int logN) {
+__global__ void k_sample_signed(GenKey gk, u64 seed, u64 tag, int kind, i64* out, int logN) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const u64 w = stream_word(seed, tag, (u64)n);
+    const u64 w = gen_word(gk, seed, tag, (u64)n);
     if (kind == 0)
         out[n] = (i64)(((u128)w * 3u) >> 64) - 1;
     else
@@ -771,13 +757,13 @@ void launch_tensor(fe_ctx* c, const u64* x, const u64* y, u64* d012, int n_ct, i
 
 void launch_sample_uniform_limbs(fe_ctx* c, uint64_t seed, uint64_t tag_base, u64* out, int n_limbs,
                                  const int* mod_idx_dev, cudaStream_t st) {
-    k_sample_uniform<<<grid_for(c->N, n_limbs), kB, 0, st>>>(seed, tag_base, out, mod_idx_dev, c->d_mod,
+    k_sample_uniform<<<grid_for(c->N, n_limbs), kB, 0, st>>>(c->gen, seed, tag_base, out, mod_idx_dev, c->d_mod,
                                                             c->logN);
     c->cnt.launches++;
 }
 
 void launch_sample_signed(fe_ctx* c, uint64_t seed, uint64_t tag, int kind, i64* out, cudaStream_t st) {
-    k_sample_signed<<<grid_for(c->N, 1), kB, 0, st>>>(seed, tag, kind, out, c->logN);
+    k_sample_signed<<<grid_for(c->N, 1), kB, 0, st>>>(c->gen, seed, tag, kind, out, c->logN);
     c->cnt.launches++;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "context.h"
+#include "prng.cuh"
 
 namespace fe {
 

@@ -12,15 +12,6 @@ namespace {
 constexpr int kB = 256;
 inline dim3 grid_for(int N, int y, int z = 1) { return dim3((N + kB - 1) / kB, y, z); }
 
-__device__ __forceinline__ u64 sm_mix(u64 z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ u64 stream_word(u64 seed, u64 tag, u64 n) {
-    const u64 g = 0x9E3779B97F4A7C15ull;
-    return sm_mix(sm_mix(seed + (tag + 1) * g) + (n + 1) * g);
-}
 __device__ __forceinline__ i64 cbd21(u64 w) {
     return (i64)__popcll(w & 0x1FFFFFull) - (i64)__popcll((w >> 21) & 0x1FFFFFull);
 }
@@ -51,16 +42,17 @@ __global__ void k_square_limbs(const u64* s, u64* out, const Modulus* mods, int 
 }
 
 // ciphertext z: c1[t] = uniform (tag CtA(id0 + z, limb t)); e (tag CtE(id0 + z)) signed
-__global__ void k_enc_sample(u64 seed, u64 id0, u64* ct, i64* e, const Modulus* mods, int nl, int logN) {
+__global__ void k_enc_sample(GenKey gk, u64 seed, u64 id0, u64* ct, i64* e, const Modulus* mods, int nl,
+                             int logN) {
     const int N = 1 << logN;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const u64 id = id0 + blockIdx.z;
     const int t = blockIdx.y;
     u64* c1 = ct + ((size_t)blockIdx.z * 2 + 1) * nl * N;
-    const u64 w = stream_word(seed, (kTagCtA << 56) | (id << 24) | (u64)t, (u64)n);
+    const u64 w = gen_word(gk, seed, (kTagCtA << 56) | (id << 24) | (u64)t, (u64)n);
     c1[((size_t)t << logN) + n] = (u64)(((u128)w * mods[t].q) >> 64);
-    if (t == 0) e[(size_t)blockIdx.z * N + n] = cbd21(stream_word(seed, (kTagCtE << 56) | (id << 24), (u64)n));
+    if (t == 0) e[(size_t)blockIdx.z * N + n] = cbd21(gen_word(gk, seed, (kTagCtE << 56) | (id << 24), (u64)n));
 }
 
 // c0 = m + e - a s  (m, e NTT form)
@@ -341,7 +333,7 @@ extern "C" int fe_encode_encrypt(fe_ctx* c, const void* sk_dev, const double* sl
     int rc = encode_batch(c, slots, (int)n_ct, (int)level, scale, m, st);
     if (rc == FE_OK) {
         u64* ct = (u64*)ct_dev;
-        k_enc_sample<<<grid_for(N, nl, n_ct), kB, 0, st>>>(seed, ct_id0, ct, e, c->d_mod, nl, c->logN);
+        k_enc_sample<<<grid_for(N, nl, n_ct), kB, 0, st>>>(c->gen, seed, ct_id0, ct, e, c->d_mod, nl, c->logN);
         k_signed_rows_to_limbs<<<grid_for(N, nl, n_ct), kB, 0, st>>>(e, en, c->d_mod, nl, c->logN);
         ntt_forward(c, LimbSet{en, (size_t)nl * N, nl, (int)n_ct, c->d_identity_map}, st);
         k_enc_c0<<<grid_for(N, nl, n_ct), kB, 0, st>>>(ct, m, en, (const u64*)sk_dev, c->d_mod, nl, c->logN);

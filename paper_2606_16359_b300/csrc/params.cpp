@@ -501,3 +501,12 @@ extern "C" int fe_device_status(fe_ctx* c, uint32_t* status, int reset) {
     if (reset) FE_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
     return FE_OK;
 }
+
+extern "C" int fe_ctx_set_generator(fe_ctx* c, int kind, const uint32_t* key_material) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (kind != FE_GEN_SPLITMIX64 && kind != FE_GEN_CHACHA20) return fe::fail(FE_EINVAL, "unknown generator");
+    if (kind == FE_GEN_CHACHA20 && !key_material) return fe::fail(FE_EINVAL, "ChaCha20 needs key material");
+    c->gen.kind = kind == FE_GEN_CHACHA20 ? fe::kGenChaCha20 : fe::kGenSplitMix64;
+    for (int i = 0; i < 6; i++) c->gen.k[i] = kind == FE_GEN_CHACHA20 ? key_material[i] : 0;
+    return FE_OK;
+}

@@ -92,6 +92,44 @@ def test_keys_parity(which, tiny, ks2):
         assert np.array_equal(got[j, 0], keys.relin.b[j]) and np.array_equal(got[j, 1], keys.relin.a[j])
 
 
+def test_chacha20_generator_parity():
+    """ChaCha20 (RFC 8439) as the generator on both sides: the secret key, the
+    evaluation keys (b and a of every digit), fresh ciphertexts and a rotation
+    are bit-exact to the oracle's, and differ from the SplitMix64 ones."""
+    key6 = [0x01234567, 0x89abcdef, 0x0badf00d, 0xdeadbeef, 0x13579bdf, 0x2468ace0]
+    P = Pair(10, 3, 1, 30, 50)
+    pr, g = P.pr, P.g
+    g.set_generator("chacha20", key6)
+    C.set_generator("chacha20", np.array(key6, dtype=np.uint32))
+    try:
+        steps = [1, -3]
+        keys = ckks.KeySet(pr, 5, rot_steps=steps, relin=True)
+        sk = g.sk_gen(5)
+        assert np.array_equal(u64(sk), keys.sk.ntt)
+        evk = g.evk_gen(sk, 5, steps, relin=True)
+        kb = u64(evk.buf)
+        dnum, nm = len(pr.digits(pr.L)), len(pr.moduli)
+        per = dnum * 2 * nm * pr.N
+        for idx, r in enumerate(sorted(steps)):
+            got = kb[idx * per:(idx + 1) * per].reshape(dnum, 2, nm, pr.N)
+            sw = keys.rot[pr.galois(r)]
+            for j in range(dnum):
+                assert np.array_equal(got[j, 0], sw.b[j]) and np.array_equal(got[j, 1], sw.a[j])
+        z = np.random.default_rng(8).uniform(-1, 1, (2, pr.N // 2))
+        octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], pr.L, 2.0 ** 25), 2, i) for i in range(2)]
+        ct = g.encrypt(sk, torch.from_numpy(z), pr.L, 2.0 ** 25, seed=2)
+        assert np.array_equal(u64(ct), oracle_ct_array(octs))
+        for r in steps:
+            want = oracle_ct_array([ckks.rotate(pr, keys, c, r) for c in octs])
+            assert np.array_equal(u64(g.rotate(evk, ct, pr.L, r)), want), r
+        y = g.decrypt(sk, g.rotate(evk, ct, pr.L, 1), pr.L, 2.0 ** 25).cpu().numpy()
+        assert np.abs(y - np.roll(z, -1, axis=1)).max() < 1e-3
+    finally:
+        C.set_generator("splitmix64")
+    g2 = fe.Context(10, 3, 1, 30, 50)
+    assert not np.array_equal(u64(g2.sk_gen(5)), u64(sk))
+
+
 def test_encode_encrypt_decrypt_parity(tiny):
     pr, g = tiny.pr, tiny.g
     rng = np.random.default_rng(3)
