@@ -128,10 +128,13 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
     u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)pos << logN);
     const u64* s = first ? a.src + (size_t)poly * a.src_stride + ((size_t)pos << logN) : d;
     const int total = lines * n;
-    // column pass tile[x * lines + c]; row pass tile[RIDX(row, x)] with one pad word per 8
-    // so that the strided rounds avoid bank conflicts
+    // column pass tile[CIDX(x, c)]: element x of the `lines` columns side by side,
+    // with a pad row after every 8 rows; row pass tile[RIDX(row, x)] with one pad
+    // word per 8.  The pads spread the strided rounds over the banks: without the
+    // column pass's, its unit-stride round put 8 threads of a warp on one bank.
     const int rs = N2 + (N2 >> 3);
 #define RIDX(ln, x) ((ln) * rs + (x) + ((x) >> 3))
+#define CIDX(x, c) (((x) + ((x) >> 3)) * lines + (c))
     // load: each thread issues all of its 16-byte loads before storing to shared memory
     {
         const int pairs = total >> 1;
@@ -157,8 +160,10 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
                 if (e < pairs) {
                     const int el = 2 * e;
                     if (kCol) {
-                        tile[el] = buf[k].x;
-                        tile[el + 1] = buf[k].y;
+                        const int x = el / lines, c = el - x * lines;
+                        const int x1 = (el + 1) / lines, c1 = el + 1 - x1 * lines;
+                        tile[CIDX(x, c)] = buf[k].x;
+                        tile[CIDX(x1, c1)] = buf[k].y;
                     } else {
                         const int ln = el >> logN2, x = el & (N2 - 1);
                         tile[RIDX(ln, x)] = buf[k].x;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
 #pragma unroll
             for (int r = 0; r < kEE; r++) {
                 const int x = base + (r << lo);
-                v[r] = (r < E) ? (kCol ? tile[x * lines + line] : tile[RIDX(line, x)]) : 0;
+                v[r] = (r < E) ? (kCol ? tile[CIDX(x, line)] : tile[RIDX(line, x)]) : 0;
             }
             round_stages<kInv, kNoRed, kLE>(v, blk, lo, nst, E, logn, tw_line, tw, q);
         }
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
             for (int r = 0; r < kEE; r++) {
                 if (r >= E) break;
                 const int x = base + (r << lo);
-                if (kCol) tile[x * lines + line] = v[r];
+                if (kCol) tile[CIDX(x, line)] = v[r];
                 else tile[RIDX(line, x)] = v[r];
             }
         }
@@ -226,9 +231,10 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
             const int el = 2 * e;
             ulonglong2 o;
             if (kCol) {
-                o.x = fin(tile[el]);
-                o.y = fin(tile[el + 1]);
                 const int x = el / lines, c = el - x * lines;
+                const int x1 = (el + 1) / lines, c1 = el + 1 - x1 * lines;
+                o.x = fin(tile[CIDX(x, c)]);
+                o.y = fin(tile[CIDX(x1, c1)]);
                 *reinterpret_cast<ulonglong2*>(d + (size_t)x * N2 + l0 + c) = o;
             } else {
                 const int ln = el >> logN2, x = el & (N2 - 1);
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
         }
     }
 #undef RIDX
+#undef CIDX
 }
 
 // Integer-pipe roof of the forward transform's arithmetic.  Every thread keeps 8
@@ -321,7 +328,7 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     NttArgs a = make_args(c, s, src, src_stride, kInv);
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
     const int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
-    const size_t smc = (size_t)N1 * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
+    const size_t smc = (size_t)(N1 + (N1 >> 3) + 1) * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
     // algorithmic bytes of a limb transform, 2 N w, split over its two passes
     const double bytes = 8.0 * limbs * N;
     const int le = (c->ntt_radix == 16 && (c->logN == 14 || c->logN == 16)) ? 4 : 3;

@@ -69,7 +69,7 @@ struct Group {
     std::vector<const void*> in_host;  // copied from the requests: launch runs without the lock
     std::vector<void*> out_host;
     cudaStream_t stream;
-    cudaEvent_t done;
+    cudaEvent_t start = nullptr, done = nullptr;  // timing events: the group's interval on the device
     void* mem;
     size_t bytes;
 };
@@ -91,6 +91,10 @@ struct fe_server {
     size_t in_use = 0, peak_use = 0;
     uint64_t submitted = 0, completed = 0, rejected = 0, groups = 0, max_group = 0, max_inflight_seen = 0;
     std::vector<double> lat_ms;
+    // device intervals (ms after `epoch`) of finished groups: from the moment the
+    // group's stream starts its work (input copies) to its completion
+    std::vector<std::pair<float, float>> intervals;
+    cudaEvent_t epoch = nullptr;
     Clock::time_point t0;
     bool stop = false;
     bool paused = false;
@@ -127,6 +131,7 @@ int fe_server::launch(Group& g, const Model& m) {
     char* ws = base + 2 * buf;
     const size_t ws_bytes = g.bytes - 2 * buf;
     cudaStream_t st = g.stream;
+    FE_CUDA_TRY(cudaEventRecord(g.start, st));
     for (uint32_t r = 0; r < R; r++)
         FE_CUDA_TRY(cudaMemcpyAsync(bufs[0] + r * m.in_bytes, g.in_host[r], m.in_bytes, cudaMemcpyHostToDevice, st));
     int cur = 0;
@@ -175,7 +180,19 @@ void fe_server::loop() {
                     lat_ms.push_back(std::chrono::duration<double, std::milli>(now - q.t_submit).count());
                 }
             }
+            float t_s = 0, t_e = 0;
+            if (e == cudaSuccess && cudaEventElapsedTime(&t_s, epoch, g.start) == cudaSuccess &&
+                cudaEventElapsedTime(&t_e, epoch, g.done) == cudaSuccess) {
+                intervals.push_back({t_s, t_e});
+                // groups whose device intervals overlapped this one's
+                uint64_t over = 1;
+                for (const auto& iv : intervals)
+                    if (&iv != &intervals.back() && iv.first < t_e && t_s < iv.second) over++;
+                max_inflight_seen = std::max(max_inflight_seen, over);
+                if (intervals.size() > 4096) intervals.erase(intervals.begin(), intervals.begin() + 2048);
+            }
             cudaFreeAsync(g.mem, g.stream);
+            cudaEventDestroy(g.start);
             cudaEventDestroy(g.done);
             in_use -= g.bytes;
             free_streams.push_back(g.stream);
@@ -222,7 +239,8 @@ void fe_server::loop() {
             lk.unlock();
             int rc = FE_OK;
             if (cudaMallocAsync(&g.mem, g.bytes, g.stream) != cudaSuccess) rc = FE_ENOMEM;
-            if (rc == FE_OK && cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) rc = FE_ECUDA;
+            if (rc == FE_OK && (cudaEventCreate(&g.start) != cudaSuccess || cudaEventCreate(&g.done) != cudaSuccess))
+                rc = FE_ECUDA;
             if (rc == FE_OK) rc = launch(g, models[mid]);
             lk.lock();
             if (rc != FE_OK) {
@@ -234,16 +252,14 @@ void fe_server::loop() {
                     rejected++;
                 }
                 if (g.mem) cudaFreeAsync(g.mem, g.stream);
+                if (g.start) cudaEventDestroy(g.start);
+                if (g.done) cudaEventDestroy(g.done);
                 cv_done.notify_all();
                 continue;
             }
             peak_use = std::max(peak_use, in_use);
             groups++;
             max_group = std::max<uint64_t>(max_group, R);
-            // groups whose work is still on the device next to this one
-            uint64_t running = 1;
-            for (const Group& o : inflight) running += cudaEventQuery(o.done) == cudaErrorNotReady;
-            max_inflight_seen = std::max<uint64_t>(max_inflight_seen, running);
             inflight.push_back(g);
         }
         cv_work.wait_for(lk, std::chrono::microseconds(inflight.empty() ? 2000 : 100));
@@ -270,6 +286,9 @@ extern "C" int fe_server_create(const fe_server_config* cfg, fe_server** out) {
         s->all_streams.push_back(st);
         s->free_streams.push_back(st);
     }
+    FE_CUDA_TRY(cudaEventCreate(&s->epoch));
+    FE_CUDA_TRY(cudaEventRecord(s->epoch, s->all_streams[0]));
+    FE_CUDA_TRY(cudaEventSynchronize(s->epoch));
     s->t0 = Clock::now();
     fe_server* raw = s.get();
     s->worker = std::thread([raw] { raw->loop(); });
@@ -418,8 +437,10 @@ extern "C" void fe_server_destroy(fe_server* s) {
     for (auto& g : s->inflight) {
         cudaEventSynchronize(g.done);
         cudaFreeAsync(g.mem, g.stream);
+        cudaEventDestroy(g.start);
         cudaEventDestroy(g.done);
     }
+    if (s->epoch) cudaEventDestroy(s->epoch);
     for (cudaStream_t st : s->all_streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);

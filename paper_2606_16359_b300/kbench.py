@@ -4,6 +4,7 @@
     python -m paper_2606_16359_b300.kbench alu [--iters 400]
     python -m paper_2606_16359_b300.kbench keyswitch [--n 8] [--level 22] [--reps 5]
     python -m paper_2606_16359_b300.kbench mac [--reps 5]
+    python -m paper_2606_16359_b300.kbench layer [--channels 128] [--hw 14] [--dw] [--reps 5]
     python -m paper_2606_16359_b300.kbench aac [--reps 5]
     python -m paper_2606_16359_b300.kbench configs [--reps 5]
 
@@ -143,6 +144,54 @@ def bench_mac(ctx, torch, args):
             "status": ctx.device_status()}
 
 
+def bench_layer(ctx, torch, args):
+    """One real layer on resident operands (no pool, no aliasing) at level 22,
+    N = 2^16, double hoisting, real keys and encoded weights: pointwise
+    HxHxC -> C with baby-step / giant-step n1 = 16, or with --dw the depthwise
+    3x3 conv HxHxC (H = --hw, C = --channels; the defaults keep every operand a
+    few GB, larger than L2).  For ncu captures of the MAC, key inner product,
+    base conversion and lift kernels with DRAM traffic as in the bench step.
+    Reports the layer's CUDA-event time and the per-kernel-class times and
+    algorithmic bytes."""
+    import numpy as np
+    lv = ctx.L - 1
+    C, H = args.channels, args.hw
+    lay = ctx.layout(H, H, C, 1, 1)
+    if args.dw:
+        plan = ctx.plan_conv(lay, C, 3, depthwise=True, level=lv, double_hoist=True)
+        w = np.random.default_rng(0).normal(0, 1 / 3, (C, 1, 3, 3))
+    else:
+        plan = ctx.plan_conv(lay, C, 1, level=lv, bsgs_n1=16, double_hoist=True)
+        w = np.random.default_rng(0).normal(0, 1 / np.sqrt(C), (C, C, 1, 1))
+    i = plan.info
+    sk = ctx.sk_gen(5)
+    evk = ctx.evk_gen(sk, 5, plan.steps)
+    pt = ctx.load_weights(plan, w, float(ctx.moduli[lv]))
+    x = ctx.encrypt(sk, ctx.pack(lay, torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, (1, C, H, H)))),
+                    lv, 2.0 ** 32, seed=3)
+    out = ctx.empty_ct(i.n_out_ct, lv - 1)
+    ws = ctx.workspace(i.workspace_bytes)
+    for _ in range(2):
+        ctx.he_conv(evk, plan, pt, x, ws=ws, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.reps):
+        ctx.he_conv(evk, plan, pt, x, ws=ws, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    kinds = {}
+    for kind in ("mac", "keyip", "bconv", "ntt", "combine"):
+        ctx.profile_begin(kind)
+        ctx.he_conv(evk, plan, pt, x, ws=ws, out=out)
+        kms, n, b = ctx.profile_end()
+        kinds[kind] = {"ms": kms, "launches": n, "GB": b / 1e9, "GBps": b / (kms / 1e3) / 1e9 if kms else 0.0}
+    return {"kernel": "layer", "depthwise": bool(args.dw), "hw": H, "channels": C, "level": lv, "n_pt": i.n_pt, "pt_GB": i.pt_bytes / 1e9,
+            "n_inner_rot": i.n_inner_rot, "n_outer_rot": i.n_outer_rot, "ms": ms, "kinds": kinds,
+            "status": ctx.device_status()}
+
+
 def bench_aac(ctx, torch, args):
     """Arch-aware Ciphertext Compression on the residual-shortcut shapes of
     Table 7 (8 valid channels after a channel-reducing layer, N = 2^16, level
@@ -244,7 +293,7 @@ def bench_configs(ctx_unused, torch, args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "aac", "configs"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
@@ -252,6 +301,9 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--level", type=int, default=22)
     ap.add_argument("--radix", type=int, default=8, help="NTT elements per thread per round (8 or 16)")
+    ap.add_argument("--channels", type=int, default=128, help="channels of the layer case")
+    ap.add_argument("--hw", type=int, default=14, help="map height = width of the layer case")
+    ap.add_argument("--dw", action="store_true", help="layer case: depthwise 3x3 instead of pointwise")
     args = ap.parse_args(argv)
     import torch
 
@@ -262,7 +314,7 @@ def main(argv=None):
     with torch.cuda.stream(side):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
-              "aac": bench_aac, "configs": bench_configs}[args.what]
+              "layer": bench_layer, "aac": bench_aac, "configs": bench_configs}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 
