@@ -124,6 +124,25 @@ def barrier(dist):
         dist.barrier()
 
 
+def ntt_traffic_per_limb_pass():
+    """DRAM bytes (read + write) of one limb-pass of the NTT as ncu measured
+    them (profiles/ntt_pass_forward_N65536_532limbs.txt), or None when the
+    NTT source changed since that capture (its SHA-256 is recorded beside
+    the figure)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_2606_16359_b300", "csrc", "ntt.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, "profiles", "ntt_pass_forward_N65536_532limbs.txt")) as f:
+            for line in f:
+                w = line.split()
+                if len(w) == 4 and w[0] == "traffic_bytes_per_limb_pass" and w[2] == "ntt_source_sha256":
+                    return float(w[1]) if w[3] == sha else None
+    except OSError:
+        pass
+    return None
+
+
 def butterfly_roof(ctx, torch):
     """Integer-pipe roof of the NTT butterfly arithmetic on this GPU, Gbutterfly/s
     (register-resident probe of the transform's own butterflies, one full wave)."""
@@ -313,6 +332,9 @@ def run_ours(args, dist, rank, world, local):
         limb_passes = b_dom / (8.0 * ctx.N)
         bfly = limb_passes * (ctx.N // 2) * (ctx.logN / 2)
         bfly_rate = bfly / (t_dom / 1e3) / 1e9
+        tpl = ntt_traffic_per_limb_pass()
+        roofline["traffic"] = tpl * limb_passes / n_dom if tpl else None
+        roofline["traffic_unit"] = "bytes per launch (ncu dram read + write; algorithmic: %.0f)" % (b_dom / n_dom)
         roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": bfly_peak, "unit": "Gbutterfly/s",
                          "frac": bfly_rate / bfly_peak, "peak_source": "butterfly probe, this run",
                          "hbm_GBps": achieved, "hbm_peak_GBps": peak, "hbm_frac": achieved / peak,
