@@ -10,7 +10,9 @@ fastest (linear or baby-step / giant-step); --schedule linear keeps one outer
 rotation per channel diagonal.  The blocks are independent, so a step
 launches one captured graph per block on its own stream (--one-stream: one
 graph over the six layers in order); the end-to-end run copies each block's
-input in and output out inside that block's stream.
+input in and output out inside that block's stream.  The per-block streams are
+joined only at the end of a timed region: one block's next step queues behind
+its own previous step while the other blocks are still busy.
 
 Reported: key switches per second (the metric's throughput form), ms per step
 and per layer, beside the batched/graph path two per-op paths (mode 0: one
@@ -266,13 +268,20 @@ def run_ours(args, dist, rank, world, local):
         net.capture(concurrent=not args.one_stream)
 
     def step():
+        # per-block streams run ahead across steps (each block's next step queues
+        # behind its own previous one); the timed region joins them at its end
         if use_graph:
-            net.launch()
+            net.launch(join=args.one_stream)
         else:
             net.run(mode=1)
 
+    def join():
+        if use_graph:
+            net.join()
+
     for _ in range(args.warmup):
         step()
+    join()
     torch.cuda.synchronize()
     barrier(dist)
 
@@ -284,6 +293,7 @@ def run_ours(args, dist, rank, world, local):
         ev0.record(stream)
         for _ in range(args.steps):
             step()
+        join()
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -372,13 +382,15 @@ def run_ours(args, dist, rank, world, local):
     e0.record(stream)
     for _ in range(args.steps):
         if use_graph:
-            net.launch(h_in, h_out)  # each block's copies in its own stream, beside the others' kernels
+            # each block's copies in its own stream, beside the other blocks' kernels
+            net.launch(h_in, h_out, join=args.one_stream)
         else:
             for d, h in zip(net.inputs, h_in):
                 d.copy_(h, non_blocking=True)
             step()
             for h, d in zip(h_out, net.outputs):
                 h.copy_(d, non_blocking=True)
+    join()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = reduce_max(dist, e0.elapsed_time(e1)) / args.steps

@@ -138,10 +138,14 @@ class MobileNetBlocks:
         self._join = [torch.cuda.Event() for _ in self.graphs]
         return self.graphs
 
-    def launch(self, h_in=None, h_out=None):
-        """One step through the captured graph(s) on the current stream: fork to
-        the per-graph streams, optionally copy each block's input from pinned host
-        memory first (h_in) and its output back after (h_out), join."""
+    def launch(self, h_in=None, h_out=None, join=True):
+        """One step through the captured graph(s): fork from the current stream
+        to the per-graph streams, optionally copy each block's input from pinned
+        host memory first (h_in) and its output back after (h_out), and join
+        back.  join=False leaves the per-block streams running ahead: the next
+        step's work of one block queues behind its own previous step (same
+        stream, same buffers) while the other blocks are still busy; join()
+        waits for all of them."""
         torch = _torch()
         main = torch.cuda.current_stream()
         self._fork.record(main)
@@ -157,6 +161,14 @@ class MobileNetBlocks:
                 if h_out is not None:
                     for b in blocks:
                         h_out[b].copy_(self.outputs[b], non_blocking=True)
+        if join:
+            self.join()
+
+    def join(self):
+        """Make the current stream wait for every per-block stream."""
+        torch = _torch()
+        main = torch.cuda.current_stream()
+        for i, s in enumerate(self.streams):
             self._join[i].record(s)
             main.wait_event(self._join[i])
 
