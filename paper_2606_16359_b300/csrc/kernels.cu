@@ -131,56 +131,102 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
 // ModDown combine + automorphism + optional add / accumulate (see CombineItem).
 // blockIdx.y = limb i of Q_level, z = item.
 // ------------------------------------------------------------------------
+// Two coefficients per thread (n even, n + 1), 16-byte accesses: the
+// automorphism maps the pair onto a pair (see k_lift).
 __global__ void k_combine(const CombineItem* items, const Modulus* mods, const u64* pinv,
                           const u64* pinv_sh, int level, int k, int logN) {
     const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (n >= N) return;
     const CombineItem it = items[blockIdx.z];
     const int i = blockIdx.y;
     const int np = level + 1 + k, nq = level + 1;
     const u64 q = mods[i].q;
     const uint32_t src = it.galois == 1 ? (uint32_t)n : galois_perm(n, it.galois, logN);
-    const size_t so = ((size_t)i << logN) + src;
-    u64 vb = sub_mod(it.acc[so], it.conv[so], q);
-    u64 va = sub_mod(it.acc[((size_t)np << logN) + so], it.conv[((size_t)nq << logN) + so], q);
-    vb = mul_shoup(vb, pinv[i], pinv_sh[i], q);
-    va = mul_shoup(va, pinv[i], pinv_sh[i], q);
-    if (it.add0) vb = add_mod(vb, it.add0[so], q);
-    if (it.add1) va = add_mod(va, it.add1[so], q);
-    const size_t oo = ((size_t)i << logN) + n;
-    u64* o0 = it.out + oo;
-    u64* o1 = it.out + ((size_t)nq << logN) + oo;
-    if (it.accumulate) {
-        *o0 = add_mod(*o0, vb, q);
-        *o1 = add_mod(*o1, va, q);
-    } else {
-        *o0 = vb;
-        *o1 = va;
+    const size_t so = ((size_t)i << logN) + (src & ~1u);
+    const bool swap = src & 1u;
+    auto load2 = [&](const u64* p) -> ulonglong2 {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+        if (swap) {
+            const u64 t = v.x;
+            v.x = v.y;
+            v.y = t;
+        }
+        return v;
+    };
+    const ulonglong2 ab = load2(it.acc + so), cb = load2(it.conv + so);
+    const ulonglong2 aa = load2(it.acc + ((size_t)np << logN) + so), ca = load2(it.conv + ((size_t)nq << logN) + so);
+    ulonglong2 vb, va;
+    vb.x = mul_shoup(sub_mod(ab.x, cb.x, q), pinv[i], pinv_sh[i], q);
+    vb.y = mul_shoup(sub_mod(ab.y, cb.y, q), pinv[i], pinv_sh[i], q);
+    va.x = mul_shoup(sub_mod(aa.x, ca.x, q), pinv[i], pinv_sh[i], q);
+    va.y = mul_shoup(sub_mod(aa.y, ca.y, q), pinv[i], pinv_sh[i], q);
+    if (it.add0) {
+        const ulonglong2 a0 = load2(it.add0 + so);
+        vb.x = add_mod(vb.x, a0.x, q);
+        vb.y = add_mod(vb.y, a0.y, q);
     }
+    if (it.add1) {
+        const ulonglong2 a1 = load2(it.add1 + so);
+        va.x = add_mod(va.x, a1.x, q);
+        va.y = add_mod(va.y, a1.y, q);
+    }
+    const size_t oo = ((size_t)i << logN) + n;
+    ulonglong2* o0 = reinterpret_cast<ulonglong2*>(it.out + oo);
+    ulonglong2* o1 = reinterpret_cast<ulonglong2*>(it.out + ((size_t)nq << logN) + oo);
+    if (it.accumulate) {
+        const ulonglong2 p0 = *o0, p1 = *o1;
+        vb.x = add_mod(p0.x, vb.x, q);
+        vb.y = add_mod(p0.y, vb.y, q);
+        va.x = add_mod(p1.x, va.x, q);
+        va.y = add_mod(p1.y, va.y, q);
+    }
+    *o0 = vb;
+    *o1 = va;
 }
 
+// Two coefficients per thread (n even, n + 1): the automorphism maps the pair
+// onto the pair perm(n) & ~1 (perm(n + 1) = perm(n) ^ 1, since 2 brv(n + 1) + 1
+// = 2 brv(n) + 1 + N and N g = N mod 2N flips only the top bit), so every
+// access is a 16-byte load or store.
 __global__ void k_lift(const LiftItem* items, const Modulus* mods, const int* ks_limbs, const u64* pmod,
                        const u64* pmod_sh, int level, int k, int logN) {
     const int N = 1 << logN;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (n >= N) return;
     const LiftItem it = items[blockIdx.z];
     const int p = blockIdx.y, np = level + 1 + k, nq = level + 1;
     const int mi = ks_limbs[p];
     const u64 q = mods[mi].q;
     const uint32_t src = it.galois == 1 ? (uint32_t)n : galois_perm(n, it.galois, logN);
-    u64 vb = 0, va = 0;
+    const uint32_t pair = src & ~1u;
+    const bool swap = src & 1u;
+    auto load2 = [&](const u64* base) -> ulonglong2 {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + pair);
+        if (swap) {
+            const u64 t = v.x;
+            v.x = v.y;
+            v.y = t;
+        }
+        return v;
+    };
+    ulonglong2 vb = make_ulonglong2(0, 0), va = make_ulonglong2(0, 0);
     if (it.acc) {
-        vb = it.acc[((size_t)p << logN) + src];
-        va = it.acc[((size_t)(np + p) << logN) + src];
+        vb = load2(it.acc + ((size_t)p << logN));
+        va = load2(it.acc + ((size_t)(np + p) << logN));
     }
     if (p < nq) {
-        vb = add_mod(vb, mul_shoup(it.ct[((size_t)p << logN) + src], pmod[p], pmod_sh[p], q), q);
-        if (!it.acc) va = mul_shoup(it.ct[((size_t)(nq + p) << logN) + src], pmod[p], pmod_sh[p], q);
+        const ulonglong2 c0 = load2(it.ct + ((size_t)p << logN));
+        vb.x = add_mod(vb.x, mul_shoup(c0.x, pmod[p], pmod_sh[p], q), q);
+        vb.y = add_mod(vb.y, mul_shoup(c0.y, pmod[p], pmod_sh[p], q), q);
+        if (!it.acc) {
+            const ulonglong2 c1 = load2(it.ct + ((size_t)(nq + p) << logN));
+            va.x = mul_shoup(c1.x, pmod[p], pmod_sh[p], q);
+            va.y = mul_shoup(c1.y, pmod[p], pmod_sh[p], q);
+        }
     }
-    it.out[((size_t)p << logN) + n] = vb;
-    it.out[((size_t)(np + p) << logN) + n] = va;
+    *reinterpret_cast<ulonglong2*>(it.out + ((size_t)p << logN) + n) = vb;
+    *reinterpret_cast<ulonglong2*>(it.out + ((size_t)(np + p) << logN) + n) = va;
 }
 
 __global__ void k_combine_sum(const SumItem* items, const SumEntry* entries, const Modulus* mods,
@@ -643,7 +689,7 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
 void launch_combine(fe_ctx* c, const CombineItem* items, int n_items, int level, cudaStream_t st) {
     if (!n_items) return;
     ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * (level + 1) * 7.0 * n_items);
-    k_combine<<<grid_for(c->N, level + 1, n_items), kB, 0, st>>>(items, c->d_mod, c->d_pinv,
+    k_combine<<<grid_for(c->N / 2, level + 1, n_items), kB, 0, st>>>(items, c->d_mod, c->d_pinv,
                                                                 c->d_pinv_sh, level, c->k, c->logN);
     c->cnt.launches++;
 }
@@ -652,8 +698,8 @@ void launch_lift(fe_ctx* c, const LiftItem* items, int n_items, int level, cudaS
     if (!n_items) return;
     const int np = level + 1 + c->k;
     ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * n_items * (2.0 * np + 2.0 * np + 2.0 * (level + 1)));
-    k_lift<<<grid_for(c->N, np, n_items), kB, 0, st>>>(items, c->d_mod, c->lv[level].d_ks_limbs, c->d_pmod,
-                                                       c->d_pmod_sh, level, c->k, c->logN);
+    k_lift<<<grid_for(c->N / 2, np, n_items), kB, 0, st>>>(items, c->d_mod, c->lv[level].d_ks_limbs, c->d_pmod,
+                                                           c->d_pmod_sh, level, c->k, c->logN);
     c->cnt.launches++;
 }
 
