@@ -3,7 +3,8 @@ pool, FC x3) on the GPU against the oracle at a reduced ring (bit-exact output
 residues), and at the full LeNet parameter set (N = 2^14, 8 x 40-bit primes,
 BS = 128) against the FP64 network (decrypted logits within 1e-3).  Also the
 MobileNet-shaped blocks at N = 2^16 against FP64, and one sampled output
-ciphertext of the smallest block's depthwise layer against the oracle."""
+ciphertext of the smallest block's depthwise layer against the oracle, both in
+the default schedule and in the benchmark's own launch configuration."""
 import numpy as np
 import pytest
 
@@ -93,4 +94,57 @@ def test_mobilenet_blocks_decrypt_to_fp64_and_sampled_oracle_ct():
     # group 0 only: channels 0..cpc-1 live in input ciphertext 0
     sub = fragment.Layout(pr.N, H, H, olay.cpc, 1, 1)
     oout, _ = henn.he_conv(pr, keys, [oct0], sub, wd[:olay.cpc], depthwise=True)
+    assert np.array_equal(got[0], oout[0].as_array())
+
+
+def test_mobilenet_blocks_in_the_bench_launch_configuration():
+    """The benchmark's own configuration at full size (N = 2^16, 24 x 36-bit +
+    4 special primes): schedules picked by the autotuner, one captured graph per
+    block launched side by side on its own stream with the host copies inside,
+    the streams left running ahead across steps.  Every block's output decrypts
+    to the FP64 result within 1e-3; the copied-back residues equal the eager
+    batched path and the per-op path bit for bit; and ciphertext 0 of the
+    smallest block's depthwise layer, in the hoisting the tuner chose, equals
+    the oracle's."""
+    p = W.PARAMS["mobilenet"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        net = MobileNetBlocks(ctx, delta=p["delta"], schedule="tuned")
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        eager = [u64(o) for o in net.outputs]
+        net.run(mode=0)
+        torch.cuda.synchronize()
+        per_op = [u64(o) for o in net.outputs]
+        net.capture(concurrent=True)
+        h_in = [t.cpu().pin_memory() for t in net.inputs]
+        h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in net.outputs]
+        for t in net.inputs + net.outputs:
+            t.zero_()
+        for _ in range(2):
+            net.launch(h_in, h_out, join=False)
+        net.join()
+        torch.cuda.synchronize()
+        for o, h in zip(net.outputs, h_out):
+            o.copy_(h)
+        errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(3)]
+        dw3 = net.layers[4]
+        got = u64(dw3["out"][0:1])
+        dh = bool(dw3["plan"].info.double_hoist)
+        assert ctx.device_status() == 0
+    assert max(errs) < 1e-3, errs
+    for b in range(3):
+        graph_out = h_out[b].numpy().view(np.uint64)
+        assert np.array_equal(graph_out, eager[b]) and np.array_equal(graph_out, per_op[b]), b
+    H, Cin, Cout = W.MOBILENET_BLOCKS[2]
+    x, wd, wp = W.mobilenet_block(0, H, Cin, Cout, BS=1, block=2)
+    pr = ckks.Params(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+    olay = fragment.Layout(pr.N, H, H, Cin, 1, 1)
+    keys = ckks.KeySet(pr, 101, rot_steps=henn.conv_rotation_steps(olay, Cin, Cin, 3, depthwise=True))
+    slots = fragment.pack(olay, x)
+    oct0 = ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[0], pr.L, p["delta"]), 202, 16 + 16)
+    sub = fragment.Layout(pr.N, H, H, olay.cpc, 1, 1)
+    oout, _ = henn.he_conv(pr, keys, [oct0], sub, wd[:olay.cpc], depthwise=True,
+                           hoist="double" if dh else "single")
     assert np.array_equal(got[0], oout[0].as_array())
