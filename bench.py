@@ -332,9 +332,17 @@ def run_ours(args, dist, rank, world, local):
     peak, peak_kind = peaks()
     achieved = (b_dom / n_dom) / (t_dom / n_dom / 1e3) / 1e9 if n_dom else 0.0
     shares = {k: round(v[0] / sum(x[0] for x in per_kind.values()), 4) for k, v in per_kind.items()}
+    # every class beside the dominant one: CUDA-event time over one step and its
+    # algorithmic bytes per second against the measured HBM copy rate (the NTT
+    # and base conversion are bound by the integer pipes, so their fraction is
+    # low by construction; the bytes of the key inner product, lift and MAC
+    # count operand re-reads that hit L2)
+    by_class = {k: {"ms": round(t, 3), "launches": n, "algorithmic_GBps": round(b / (t / 1e3) / 1e9, 1) if t else 0.0,
+                    "hbm_frac": round(b / (t / 1e3) / 1e9 / peak, 3) if t else 0.0}
+                for k, (t, n, b) in per_kind.items()}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": None, "launches": n_dom,
-                "avg_launch_us": 1e3 * t_dom / max(1, n_dom), "time_share": shares}
+                "avg_launch_us": 1e3 * t_dom / max(1, n_dom), "time_share": shares, "by_class": by_class}
     if dom == "ntt":
         # the 64-bit-word transform is bound by the integer pipes: butterflies per
         # second against the live butterfly-probe roof; HBM figures kept beside it
