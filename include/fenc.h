@@ -314,7 +314,8 @@ typedef struct {
     size_t pt_bytes, in_bytes, out_bytes, workspace_bytes, workspace_min_bytes;
     uint32_t n_in_ct, n_out_ct, n_pt, n_inner_rot, n_outer_rot;
     uint32_t bsgs_n1;  /* baby steps of the outer rotations actually used (0: linear) */
-    uint32_t double_hoist;  /* 1: rotations and MAC on Q_l * P (fe_plan_set_hoisting) */
+    uint32_t double_hoist;  /* 1: rotations and MAC on Q_l * P; 2: the same with ModDown and
+                               rescale fused when there is no outer rotation (fe_plan_set_hoisting) */
 } fe_plan_info;
 int fe_plan_query(const fe_plan* plan, fe_plan_info* info);
 /* Rotation steps the plan needs keys for (steps_host has room for max entries;
@@ -391,9 +392,14 @@ int fe_he_layer_timing(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, cons
  * basis Q_l * P as sigma_g((P c0, 0) + key inner product), unrotated inputs
  * are lifted to (P c0, P c1), plaintexts are encoded on Q_l * P, and every
  * partial sum of the MAC takes one ModDown (double hoisting; same convolution,
- * fewer ModDowns, different rounding, its own oracle schedule).  Must be set
- * before fe_plan_load_weights: it changes the plaintext size (pt_bytes).
- * Errors: FE_EINVAL. */
+ * fewer ModDowns, different rounding, its own oracle schedule).
+ * double_hoist = 2: as 1, and when the plan has no outer rotation (depthwise
+ * layers; baby-step / giant-step with n1 = cpc) every output's one partial sum
+ * on Q_l * P is divided by q_l P in a single centred conversion instead of a
+ * ModDown followed by the rescale (one transform of the output's limbs saved;
+ * one rounding instead of two, its own oracle schedule); with outer rotations
+ * it is 1.  Must be set before fe_plan_load_weights: it changes the plaintext
+ * size (pt_bytes).  Errors: FE_EINVAL. */
 int fe_plan_set_hoisting(fe_plan* plan, int double_hoist);
 /* Tile choice of the batched MAC: how many outputs whose terms read the same
  * ciphertexts share one kernel item (1, 2 or 4; default 4).  Results do not

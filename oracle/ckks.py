@@ -411,6 +411,31 @@ def mod_down_ct(pr, Vb, Va, level, scale):
     return Ciphertext(mod_down(pr, Vb, level), mod_down(pr, Va, level), level, scale)
 
 
+def mod_down_rescale(pr, x, level):
+    """ModDown and rescale as one division (x dict limb -> NTT residues over
+    Q_level * P, result on Q_{level-1}): the centred base conversion of
+    [x]_{q_level P} to q_0..q_{level-1}, then (x - conv) (q_level P)^-1, which is
+    round(x / (q_level P)) up to the conversion's small integer error.  It
+    replaces ModDown followed by the rescale of Sec. 2 (rounding x / P, then
+    the result / q_level) when nothing else is added on Q_level in between."""
+    src = [level] + [pr.p_index(j) for j in range(pr.k)]
+    coef = [pr.intt(x[t], t) for t in src]
+    conv = centred_bconv(pr, coef, src, range(level))
+    out = np.empty((level, pr.N), dtype=np.uint64)
+    for i in range(level):
+        qi = pr.moduli[i]
+        y = C.vec_sub(x[i], pr.ntt(conv[i], i), qi)
+        out[i] = C.vec_scalar_mul(y, pow(pr.P * pr.moduli[level] % qi, -1, qi), qi)
+    return out
+
+
+def mod_down_rescale_ct(pr, Vb, Va, level, scale):
+    """A pair on Q_level * P at `scale` (times P) to a ciphertext on Q_{level-1}
+    at scale / q_level."""
+    return Ciphertext(mod_down_rescale(pr, Vb, level), mod_down_rescale(pr, Va, level), level - 1,
+                      scale / pr.moduli[level])
+
+
 def automorph_ntt(pr, poly, g, level):
     perm = pr.automorph_perm(g)
     return np.stack([C.gather(poly[t], perm) for t in range(level + 1)])

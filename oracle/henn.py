@@ -164,11 +164,14 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
     key-switching basis Q_level * P and performs one ModDown per partial sum
     P_d instead of one per rotation (double hoisting): P_d = ModDown(sum of
     V (x) pt) with V = sigma((P c0, 0) + key inner product) for a rotated source
-    and V = P x for an unrotated one, plaintexts encoded on Q_level * P."""
+    and V = P x for an unrotated one, plaintexts encoded on Q_level * P.
+    hoist="double_fused": as "double", and when the layer has no outer rotation
+    every output is its one partial sum divided by q_level P in one step
+    (ckks.mod_down_rescale) instead of ModDown then rescale."""
     if bsgs_split(lay, bsgs_n1, depthwise, in_period):
         return he_conv_bsgs(pr, keys, cts, lay, W, stride=stride, wmul=wmul, w_scale=w_scale, cnt=cnt,
                             n1=bsgs_n1, hoist=hoist)
-    double = hoist == "double"
+    double = hoist in ("double", "double_fused")
     cnt = cnt if cnt is not None else Counters()
     level = cts[0].level
     Cout = W.shape[0]
@@ -201,6 +204,8 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                         cnt.keyswitch += 1
 
     # 2-4. MAC per diagonal, outer rotations, rescale
+    fused = hoist == "double_fused" and not any(
+        d for h in range(G_out) for d in conv_diagonals(lay, Cin, Cout, h, depthwise, in_period))
     out = [None] * olay.n_ct
     for h in range(G_out):
         diags = conv_diagonals(lay, Cin, Cout, h, depthwise, in_period)
@@ -225,6 +230,12 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                                     pt = ckks.encode(pr, z, level, dw)
                                     acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b)], pt))
                                 cnt.pmult += 1
+                    if double and terms and fused:
+                        ab, aa = ckks.mac_qp(pr, level, terms)
+                        total = ckks.mod_down_rescale_ct(pr, ab, aa, level, cts[0].scale * dw)
+                        cnt.moddown += 1
+                        cnt.rescale += 1
+                        continue
                     if double and terms:
                         ab, aa = ckks.mac_qp(pr, level, terms)
                         acc = ckks.mod_down_ct(pr, ab, aa, level, cts[0].scale * dw)
@@ -237,8 +248,11 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                         cnt.keyswitch += 1
                         cnt.modup += 1
                     total = _add(pr, total, acc)
-                res = ckks.rescale(pr, total)
-                cnt.rescale += 1
+                if fused:
+                    res = total
+                else:
+                    res = ckks.rescale(pr, total)
+                    cnt.rescale += 1
                 out[olay.ct_index(h, up // stride, vp // stride)] = res
     return out, olay
 
@@ -258,9 +272,9 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
          i blk slots;
       3. out = Q_0 + sum_{j > 0} Rot(Q_j, j n1 blk), before the one rescale.
     hoist="double": the inner and baby rotations stay on Q_level * P and each Q_j
-    takes one ModDown (see he_conv)."""
+    takes one ModDown (see he_conv); "double_fused" as in he_conv."""
     cnt = cnt if cnt is not None else Counters()
-    double = hoist == "double"
+    double = hoist in ("double", "double_fused")
     level = cts[0].level
     Cout, Cin, K = W.shape[0], W.shape[1], W.shape[-1]
     olay = out_layout_conv(lay, Cout, K, stride)
@@ -294,6 +308,7 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                     cnt.keyswitch += 1
 
     # 2-4. MAC per giant step, giant rotations, rescale
+    fused = hoist == "double_fused" and not any(d >= n1 for h in diags for d in diags[h])
     out = [None] * olay.n_ct
     for h in range(G_out):
         dset = set(diags[h])
@@ -322,6 +337,12 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                                         pt = ckks.encode(pr, z, level, dw)
                                         acc = _add(pr, acc, ckks.pmult(pr, R[(g, u, v, a, b, i)], pt))
                                     cnt.pmult += 1
+                    if double and terms and fused:
+                        ab, aa = ckks.mac_qp(pr, level, terms)
+                        total = ckks.mod_down_rescale_ct(pr, ab, aa, level, cts[0].scale * dw)
+                        cnt.moddown += 1
+                        cnt.rescale += 1
+                        continue
                     if double and terms:
                         ab, aa = ckks.mac_qp(pr, level, terms)
                         acc = ckks.mod_down_ct(pr, ab, aa, level, cts[0].scale * dw)
@@ -334,8 +355,11 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                         cnt.keyswitch += 1
                         cnt.modup += 1
                     total = _add(pr, total, acc)
-                res = ckks.rescale(pr, total)
-                cnt.rescale += 1
+                if fused:
+                    res = total
+                else:
+                    res = ckks.rescale(pr, total)
+                    cnt.rescale += 1
                 out[olay.ct_index(h, up // stride, vp // stride)] = res
     return out, olay
 

@@ -238,6 +238,17 @@ class Plan:
             self.handle = None
 
 
+def _hoisting(v):
+    """fe_plan_set_hoisting's value: False / 0, True / 1, 2 or "fused"."""
+    if v == "fused":
+        return 2
+    if v is True:
+        return 1
+    if v in (0, 1, 2):
+        return int(v)
+    raise ValueError(f"hoisting must be False, True, 2 or 'fused', not {v!r}")
+
+
 class Graph:
     def __init__(self, handle, keep):
         self.handle, self._keep = handle, keep
@@ -399,7 +410,7 @@ class Context:
         check(load().fe_plan_conv(self.handle, ctypes.byref(lay), Cout, K, stride, 1 if depthwise else 0,
                                   in_period, level, bsgs_n1, ctypes.byref(out_lay), ctypes.byref(h)))
         if double_hoist:
-            check(load().fe_plan_set_hoisting(h, 1))
+            check(load().fe_plan_set_hoisting(h, _hoisting(double_hoist)))
         p = Plan(self, h, out_lay)
         p.level, p.in_layout = level, lay
         return p
@@ -448,8 +459,10 @@ class Context:
         return v.value
 
     def plan_set_hoisting(self, plan, double):
-        """Double hoisting of the plan's rotations (set before load_weights)."""
-        check(load().fe_plan_set_hoisting(plan.handle, 1 if double else 0))
+        """Hoisting of the plan's rotations (set before load_weights): False / 0
+        single, True / 1 double, 2 or "fused" double with ModDown and rescale in
+        one step when the plan has no outer rotation."""
+        check(load().fe_plan_set_hoisting(plan.handle, _hoisting(double)))
         plan.refresh()
         return plan
 

@@ -28,6 +28,7 @@ struct BConvTab {
 struct LevelTabs {
     std::vector<BConvTab> modup;  // one per digit
     BConvTab rescale;             // {q_l} -> q_0..q_{l-1}
+    BConvTab mdrs;                // {q_l, p_0..p_{k-1}} -> q_0..q_{l-1} (ModDown and rescale in one)
     std::vector<int> ks_limbs;    // q_0..q_l, p_0..p_{k-1}
     const int* d_ks_limbs;        // device copy
     // extended limbs of one ciphertext's ModUp that need a forward NTT (every digit's
@@ -82,6 +83,7 @@ struct fe_ctx {
     u64 *d_ninv, *d_ninv_sh;        // [n_mod] N^-1
     u64 *d_pinv, *d_pinv_sh;        // [n_mod] P^-1 mod q_i (i <= L)
     u64 *d_pmod, *d_pmod_sh;        // [n_mod] P mod q_i (i <= L)
+    u64 *d_qpinv, *d_qpinv_sh;      // [L+1][L+1] (q_l P)^-1 mod q_i, i < l
     u64 *d_qlinv, *d_qlinv_sh;      // [L+1][L+1]: q_l^-1 mod q_i at [l][i]
     double* d_dd_w;                 // [N][4]: exp(-2 pi i j / 2N) as (re_hi, re_lo, im_hi, im_lo)
     int* d_identity_map;            // [n_mod] j -> j

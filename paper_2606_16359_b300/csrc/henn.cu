@@ -155,7 +155,8 @@ size_t item_bytes(const fe_plan* p, size_t chunk, size_t R) {
     n += n_chunks * R * p->n_out * sizeof(SumItem);
     n += R * (groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm));
     if (p->dhoist) n += R * ((p->inner.size() + p->n_in) * sizeof(LiftItem) + groups * sizeof(CombineItem));
-    return n + 20 * 256;
+    if (p->dhoist == 2) n += R * p->n_out * sizeof(u64*);
+    return n + 21 * 256;
 }
 
 }  // namespace
@@ -329,6 +330,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     const size_t n_in_rot = p->inner.size(), n_mu = p->modup_cts.size(), n_terms = p->terms.size();
     // double hoisting: rotated copies, lifted inputs and plaintexts on Q_l * P
     const bool dh = p->dhoist != 0;
+    // double hoisting without outer rotations: every output is its one partial sum
+    // on Q_l * P, divided by q_l P in one step (ModDown and rescale together)
+    const bool fuse = p->dhoist == 2 && p->n_outer == 0;
     const size_t rw = dh ? z.accw : z.ctw;                         // words of one rotated copy
     const size_t ptb = (size_t)(dh ? lv + 1 + c->k : lv + 1) * pt_limb_bytes(c);  // bytes of one plaintext
     // item tables in ws; data (rotated copies, sums, scratch) after them, or in
@@ -377,6 +381,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     SumItem* d_sum = cv.take<SumItem>(std::max<size_t>(1, n_chunks * R * p->n_out));
     LiftItem* d_lift = cv.take<LiftItem>(dh ? std::max<size_t>(1, R * (n_in_rot + p->n_in)) : 1);
     CombineItem* d_dcb = cv.take<CombineItem>(dh ? std::max<size_t>(1, R * n_groups_all) : 1);
+    u64** d_fout = cv.take<u64*>(fuse ? std::max<size_t>(1, R * p->n_out) : 1);
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
     Carver cd(data_ws ? (char*)data_ws : cv.p, data_ws ? data_ws_bytes : cv.left);
     u64* Rb = cd.take<u64>(R * n_in_rot * rw);
@@ -465,12 +470,14 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     std::vector<OneMac> macs;
     std::vector<size_t> no_base;  // request-major output index
     std::vector<CombineItem> dcb;  // double hoisting: ModDown of every MAC output (base, then outer)
+    std::vector<u64*> fout;        // fused: output ciphertext of every base MAC
     for (size_t r = 0; r < R; r++)
         for (int o = 0; o < p->n_out; o++) {
             bool base = false;
             for (const auto& g : p->outs[o].groups)
                 if (g.step == 0) {
                     u64* dst = total + (r * p->n_out + o) * z.ctw;
+                    if (fuse) fout.push_back(b_out + (r * p->n_out + o) * ctw_out);
                     if (dh) {
                         const size_t b = macs.size();
                         dcb.push_back(CombineItem{accB + b * z.accw, convB + b * z.ctw, nullptr, nullptr, dst, 1, 0});
@@ -585,6 +592,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             FE_TRY(upload(lifts, d_lift, st));
             FE_TRY(upload(dcb, d_dcb, st));
         }
+        if (fuse) FE_TRY(upload(fout, d_fout, st));
     }
     if (!(phase & 2)) return FE_OK;
 
@@ -628,8 +636,17 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     // ---- stage 2: groups without rotation, straight into the totals ----
     {
     ProfScope stage(c, PK_STAGE_BASE, st, 0.0);
-    for (size_t o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + o * z.ctw, 0, z.ctw * 8, st));
-    if (mode == 0 && dh) {
+    if (fuse)
+        for (size_t o : no_base) FE_CUDA_TRY(cudaMemsetAsync(b_out + o * ctw_out, 0, ctw_out * 8, st));
+    else
+        for (size_t o : no_base) FE_CUDA_TRY(cudaMemsetAsync(total + o * z.ctw, 0, z.ctw * 8, st));
+    if (mode == 0 && fuse) {
+        for (size_t i = 0; i < n_base; i++) {
+            const int nt = macs[i].n_terms;
+            launch_mac(c, d_mac + base_rg.first + i, d_terms, 1, nt, nt, 1, 1, lv, st, true);
+            moddown_rescale(c, accB + i * z.accw, 1, lv, convB + i * z.ctw, d_fout + i, st);
+        }
+    } else if (mode == 0 && dh) {
         for (size_t i = 0; i < n_base; i++) {
             const int nt = macs[i].n_terms;
             launch_mac(c, d_mac + base_rg.first + i, d_terms, 1, nt, nt, 1, 1, lv, st, true);
@@ -645,7 +662,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     } else {
         launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
                    base_rg.outputs, base_rg.ways, lv, st, dh);
-        if (dh) {
+        if (fuse) {
+            moddown_rescale(c, accB, (int)n_base, lv, convB, d_fout, st);
+        } else if (dh) {
             moddown_prepare(c, accB, (int)n_base, lv, convB, st);
             launch_combine(c, d_dcb, (int)n_base, lv, st);
         }
@@ -701,8 +720,8 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     c->cnt.keyswitch += order.size();
     c->cnt.pmult += R * n_terms;
 
-    // ---- stage 4: rescale ----
-    {
+    // ---- stage 4: rescale (done with the ModDown when fused) ----
+    if (!fuse) {
     ProfScope stage(c, PK_STAGE_RESCALE, st, 0.0);
     if (mode == 0) {
         for (size_t o = 0; o < R * p->n_out; o++)
@@ -1155,6 +1174,7 @@ extern "C" int fe_plan_set_mac_ways(fe_plan* p, uint32_t ways) {
 
 extern "C" int fe_plan_set_hoisting(fe_plan* p, int double_hoist) {
     if (!p) return fail(FE_EINVAL, "null argument");
-    p->dhoist = double_hoist ? 1 : 0;
+    if (double_hoist < 0 || double_hoist > 2) return fail(FE_EINVAL, "hoisting must be 0, 1 or 2");
+    p->dhoist = double_hoist;
     return FE_OK;
 }

@@ -531,6 +531,24 @@ __global__ void k_pmult_compact(const u64* ct, const uint8_t* pt, u64* out, cons
     }
 }
 
+// ModDown and rescale in one division by q_l P: out_i = (acc_i - conv_i)
+// (q_l P)^-1 mod q_i for i < l.  acc: [n][2][l+1+k][N] (NTT form), conv:
+// [n][2][l][N] (NTT form of the centred conversion of [acc]_{q_l P}), outs[j]:
+// item j's output [2][l][N].  blockIdx.y = limb i, z = polynomial over 2n.
+__global__ void k_mdrs_combine(const u64* acc, const u64* conv, u64* const* outs, const Modulus* mods,
+                               const u64* qpinv, const u64* qpinv_sh, int level, int k, int L, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = blockIdx.y, z = blockIdx.z, item = z >> 1, poly = z & 1;
+    const int np = level + 1 + k;
+    const u64 q = mods[i].q;
+    const u64 a = acc[((((size_t)item * 2 + poly) * np + i) << logN) + n];
+    const u64 c = conv[((((size_t)item * 2 + poly) * level + i) << logN) + n];
+    const size_t ti = (size_t)level * (L + 1) + i;
+    outs[item][(((size_t)poly * level + i) << logN) + n] = mul_shoup(sub_mod(a, c, q), qpinv[ti], qpinv_sh[ti], q);
+}
+
 __global__ void k_rescale_combine(const u64* in, const u64* lift, u64* out, const Modulus* mods,
                                   const u64* qlinv, const u64* qlinv_sh, int level, int L,
                                   int logN) {
@@ -768,6 +786,15 @@ void launch_pmult_compact(fe_ctx* c, const u64* ct, const uint8_t* pt, u64* out,
                           cudaStream_t st) {
     k_pmult_compact<<<grid_for(c->N, level + 1), kB, 0, st>>>(ct, pt, out, c->d_mod, level + 1, c->pt_hb,
                                                              pt_tile(c), c->logN, accumulate ? 1 : 0);
+    c->cnt.launches++;
+}
+
+void launch_mdrs_combine(fe_ctx* c, const u64* acc, const u64* conv, u64* const* outs, int n, int level,
+                         cudaStream_t st) {
+    if (!n) return;
+    ProfScope ps(c, PK_RESCALE, st, 8.0 * c->N * 2 * n * (3.0 * level));
+    k_mdrs_combine<<<grid_for(c->N, level, 2 * n), kB, 0, st>>>(acc, conv, outs, c->d_mod, c->d_qpinv, c->d_qpinv_sh,
+                                                               level, c->k, c->L, c->logN);
     c->cnt.launches++;
 }
 

@@ -134,6 +134,9 @@ void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, i
                 bool qp = false);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st);
+// out_j = (acc_j - conv_j) (q_l P)^-1 on q_0..q_{l-1} for n items (see moddown_rescale)
+void launch_mdrs_combine(fe_ctx* c, const u64* acc, const u64* conv, u64* const* outs_dev, int n, int level,
+                         cudaStream_t st);
 void launch_add(fe_ctx* c, const u64* a, const u64* b, u64* out, int n_ct, int level,
                 cudaStream_t st);
 void launch_pmult(fe_ctx* c, const u64* ct, const u64* pt, u64* out, int n_ct, int level,

@@ -166,6 +166,17 @@ void moddown_to_coef(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStrea
     launch_bconv(c, t, level, acc, (size_t)np * N, 0, conv, (size_t)nl * N, 2 * n, false, st);
 }
 
+void moddown_rescale(fe_ctx* c, u64* acc, int n, int level, u64* conv, u64* const* outs_dev, cudaStream_t st) {
+    if (n == 0) return;
+    const int N = c->N, np = level + 1 + c->k;
+    ntt_inverse(c, LimbSet{acc + (size_t)level * N, (size_t)np * N, c->k + 1, 2 * n, c->lv[level].d_ks_limbs + level},
+                st);
+    launch_bconv(c, c->lv[level].mdrs, level, acc, (size_t)np * N, 0, conv, (size_t)level * N, 2 * n, false, st);
+    ntt_forward(c, LimbSet{conv, (size_t)level * N, level, 2 * n, c->d_identity_map}, st);
+    launch_mdrs_combine(c, acc, conv, outs_dev, n, level, st);
+    c->cnt.rescale += n;
+}
+
 size_t rescale_tmp_words(const fe_ctx* c, int n, int level) {
     return 2 * (size_t)n * c->N + 2 * (size_t)n * level * c->N;
 }

@@ -28,6 +28,11 @@ void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* 
 void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
 // the same without the final NTT: conv receives the conversion in coefficient form
 void moddown_to_coef(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
+// ModDown and rescale in one division by q_l P for n accumulators acc
+// [n][2][l+1+k][N] (NTT form; the q_l and P limbs are inverse-transformed in
+// place): the centred conversion of [acc]_{q_l P} to q_0..q_{l-1} into conv
+// [n][2][l][N], then outs_dev[j] = (acc_j - conv_j) (q_l P)^-1 ([2][l][N]).
+void moddown_rescale(fe_ctx* c, u64* acc, int n, int level, u64* conv, u64* const* outs_dev, cudaStream_t st);
 // Rescale n ciphertexts in -> out (level -> level - 1); tmp: [2n][N], lift: [2n][level][N].
 void rescale_batch(fe_ctx* c, const u64* in, int n, int level, u64* out, u64* tmp, u64* lift,
                    cudaStream_t st);

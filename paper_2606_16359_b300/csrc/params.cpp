@@ -281,11 +281,15 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
         pmod_sh[i] = shoup_of(P, q);
     }
     std::vector<u64> qlinv((size_t)(c->L + 1) * (c->L + 1), 0), qlinv_sh(qlinv.size(), 0);
+    std::vector<u64> qpinv(qlinv.size(), 0), qpinv_sh(qlinv.size(), 0);
     for (int l = 1; l <= c->L; l++)
         for (int i = 0; i < l; i++) {
             u64 v = h_invmod(c->mod[l] % c->mod[i], c->mod[i]);
             qlinv[(size_t)l * (c->L + 1) + i] = v;
             qlinv_sh[(size_t)l * (c->L + 1) + i] = shoup_of(v, c->mod[i]);
+            u64 w = h_mulmod(v, pinv[i], c->mod[i]);  // (q_l P)^-1
+            qpinv[(size_t)l * (c->L + 1) + i] = w;
+            qpinv_sh[(size_t)l * (c->L + 1) + i] = shoup_of(w, c->mod[i]);
         }
     // double-double table exp(-2 pi i j / 2N), j in [0, N), rounded from quad precision
     std::vector<double> ddw((size_t)N * 4);
@@ -308,6 +312,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     size_t o_pmod = pb.put(pmod.data(), nm * 8), o_pmod_sh = pb.put(pmod_sh.data(), nm * 8);
     size_t o_ql = pb.put(qlinv.data(), qlinv.size() * 8);
     size_t o_ql_sh = pb.put(qlinv_sh.data(), qlinv_sh.size() * 8);
+    size_t o_qp = pb.put(qpinv.data(), qpinv.size() * 8);
+    size_t o_qp_sh = pb.put(qpinv_sh.data(), qpinv_sh.size() * 8);
     std::vector<int> ident(nm);
     for (int i = 0; i < nm; i++) ident[i] = i;
     size_t o_ident = pb.put(ident.data(), nm * sizeof(int));
@@ -329,7 +335,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     TabOffsets md = build_tab(pb, c->mod, ps, qs);
     struct LvOff {
         std::vector<TabOffsets> up;
-        TabOffsets rs;
+        TabOffsets rs, mdrs;
         size_t ks, up_pos, up_mod;
         int n_up;
         std::vector<int> ks_limbs;
@@ -363,6 +369,9 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
             std::vector<int> lower;
             for (int i = 0; i < l; i++) lower.push_back(i);
             lvo[l].rs = build_tab(pb, c->mod, {l}, lower);
+            std::vector<int> qp{l};
+            for (int j = 0; j < c->k; j++) qp.push_back(c->L + 1 + j);
+            lvo[l].mdrs = build_tab(pb, c->mod, qp, lower);
         }
     }
 
@@ -381,6 +390,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->d_pmod_sh = (u64*)(dpool + o_pmod_sh);
     c->d_qlinv = (u64*)(dpool + o_ql);
     c->d_qlinv_sh = (u64*)(dpool + o_ql_sh);
+    c->d_qpinv = (u64*)(dpool + o_qp);
+    c->d_qpinv_sh = (u64*)(dpool + o_qp_sh);
     c->d_identity_map = (int*)(dpool + o_ident);
     c->d_status = (uint32_t*)(dpool + o_status);
     c->d_t2slot = (int*)(dpool + o_t2s);
@@ -391,6 +402,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     for (int l = 0; l <= c->L; l++) {
         for (auto& o : lvo[l].up) c->lv[l].modup.push_back(resolve(o, dpool));
         if (l >= 1) c->lv[l].rescale = resolve(lvo[l].rs, dpool);
+        if (l >= 1) c->lv[l].mdrs = resolve(lvo[l].mdrs, dpool);
         c->lv[l].ks_limbs = lvo[l].ks_limbs;
         c->lv[l].d_ks_limbs = (const int*)(dpool + lvo[l].ks);
         c->lv[l].n_up_ntt = lvo[l].n_up;

@@ -13,7 +13,7 @@ candidate computes the same convolution, and the residues of each schedule are
 fixed by its plan.
 
     t = Tuner(ctx)
-    n1, double, times = t.conv_schedule(lay, Cout, K, level=ctx.L)
+    n1, hoist, times = t.conv_schedule(lay, Cout, K, level=ctx.L)
 """
 import json
 import os
@@ -63,14 +63,15 @@ class Tuner:
 
     def conv_schedule(self, lay, Cout, K, stride=1, depthwise=False, level=None, reps=2):
         """Fastest schedule of a conv layer: outer rotations (n1 baby steps, 0 =
-        linear) and hoisting (double = True: rotations and MAC on Q P).
-        Returns (n1, double, {"n1/double": ms})."""
+        linear) and hoisting (0 single; 2 double: rotations and MAC on Q P, with
+        ModDown and rescale in one step when there is no outer rotation).
+        Returns (n1, hoisting, {"n1/hoisting": ms})."""
         ctx = self.ctx
         level = ctx.L if level is None else level
         key = _key(ctx, lay, Cout, K, stride, depthwise, level)
         if key in _CACHE:
             c = _CACHE[key]
-            return c["n1"], c["double"], dict(c["ms"])
+            return c["n1"], c["hoist"], dict(c["ms"])
         n1s = [0]
         if not depthwise and lay.cpc > 1:
             n1 = 2
@@ -79,18 +80,18 @@ class Tuner:
                 n1 *= 2
         times = {}
         for n1 in n1s:
-            for dh in (False, True):
+            for dh in (0, 2):
                 plan = ctx.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=level, bsgs_n1=n1,
                                      double_hoist=dh)
                 if plan.info.n_inner_rot == 0 and dh:
                     continue  # nothing to hoist
-                times[f"{n1}/{int(dh)}"] = self.time_plan(plan, reps)
+                times[f"{n1}/{dh}"] = self.time_plan(plan, reps)
                 del plan
         best = min(times, key=times.get)
         n1, dh = (int(v) for v in best.split("/"))
-        _CACHE[key] = {"n1": n1, "double": bool(dh), "ms": times}
+        _CACHE[key] = {"n1": n1, "hoist": dh, "ms": times}
         self._save()
-        return n1, bool(dh), times
+        return n1, dh, times
 
     def mac_ways(self, plan, reps=2):
         """Fastest MAC tile (outputs sharing one kernel item: 1, 2 or 4) for a

@@ -131,7 +131,7 @@ def test_mobilenet_blocks_in_the_bench_launch_configuration():
         errs = [float(np.abs(net.decrypt_block(b) - net.reference_block(b)).max()) for b in range(3)]
         dw3 = net.layers[4]
         got = u64(dw3["out"][0:1])
-        dh = bool(dw3["plan"].info.double_hoist)
+        hoist = {0: "single", 1: "double", 2: "double_fused"}[dw3["plan"].info.double_hoist]
         assert ctx.device_status() == 0
     assert max(errs) < 1e-3, errs
     for b in range(3):
@@ -146,5 +146,5 @@ def test_mobilenet_blocks_in_the_bench_launch_configuration():
     oct0 = ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[0], pr.L, p["delta"]), 202, 16 + 16)
     sub = fragment.Layout(pr.N, H, H, olay.cpc, 1, 1)
     oout, _ = henn.he_conv(pr, keys, [oct0], sub, wd[:olay.cpc], depthwise=True,
-                           hoist="double" if dh else "single")
+                           hoist=hoist)
     assert np.array_equal(got[0], oout[0].as_array())

@@ -179,6 +179,9 @@ def test_rotate_rescale_pmult_add_parity(which, tiny, ks2):
     assert np.array_equal(u64(ad), oracle_ct_array([ckks.add(pr, c, c) for c in octs]))
 
 
+ORACLE_HOIST = {0: "single", 1: "double", 2: "double_fused"}
+
+
 def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1), bsgs_n1=0,
                   double_hoist=False):
     pr, g = P.pr, P.g
@@ -192,7 +195,7 @@ def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25
     octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, delta), 17, i) for i in range(olay.n_ct)]
     ocnt = henn.Counters()
     oout, oolay = henn.he_conv(pr, keys, octs, olay, w, stride=stride, depthwise=depthwise, cnt=ocnt,
-                               bsgs_n1=bsgs_n1, hoist="double" if double_hoist else "single")
+                               bsgs_n1=bsgs_n1, hoist=ORACLE_HOIST[fe._hoisting(double_hoist)])
     want = oracle_ct_array(oout)
 
     lay = g.layout(H, H, C, BS, S)
@@ -423,6 +426,24 @@ def test_conv_parity_double_hoisted(tiny, H, C, Co, K, BS, S, stride, n1, dw):
     assert plan.info.double_hoist == 1
     assert tiny.g.device_status() == 0
 
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1,dw", [
+    (6, 4, 4, 3, 1, 1, 1, 0, True),    # depthwise: no outer rotation, fused
+    (8, 3, 3, 3, 2, 2, 1, 0, True),    # depthwise, S = 2, two images
+    (6, 8, 8, 1, 1, 1, 1, 8, False),   # BSGS with n1 = cpc: no giant step, fused
+    (6, 20, 18, 3, 1, 1, 1, 4, False), # giant steps: plain double hoisting
+])
+def test_conv_parity_fused_moddown_rescale(tiny, H, C, Co, K, BS, S, stride, n1, dw):
+    """Hoisting 2 (double hoisting, ModDown and rescale as one division by
+    q_l P when the layer has no outer rotation): residues bit-exact to the
+    oracle's "double_fused" schedule in both paths, within 1e-3 of FP64."""
+    rng = np.random.default_rng(H * 13 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, ((C if dw else Co), 1 if dw else C, K, K))
+    plan, _ = run_conv_pair(tiny, x, w, S, stride, depthwise=dw, bsgs_n1=n1, double_hoist=2)
+    assert plan.info.double_hoist == 2
+    assert tiny.g.device_status() == 0
 
 
 @pytest.mark.parametrize("n1", [0, 4])

@@ -184,3 +184,51 @@ def test_double_hoisted_rotation_moddown_equals_rotation(keyed):
     ab, aa = ckks.mac_qp(pr, pr.L, terms)
     y = ckks.decrypt(pr, keys.sk, ckks.rescale(pr, ckks.mod_down_ct(pr, ab, aa, pr.L, ct.scale * dw)))
     assert np.abs(y - (np.roll(z, -1) * w1 + z * w2)).max() < 1e-5
+
+
+def test_mod_down_rescale_is_rounded_division(pr):
+    """ModDown and rescale in one conversion: the result is (X - Y) / (q_l P) with
+    Y the centred conversion of [X]_{q_l P} (an exact integer identity), hence
+    round(X / (q_l P)) up to the conversion error (|u| <= (k + 1) / 2)."""
+    rng = np.random.default_rng(4)
+    level = 3
+    limbs = pr.ks_limbs(level)
+    xc = {t: rng.integers(0, pr.moduli[t], pr.N, dtype=np.uint64) for t in limbs}
+    x = {t: pr.ntt(xc[t], t) for t in limbs}
+    out = ckks.mod_down_rescale(pr, x, level)
+    outc = [pr.intt(out[i], i) for i in range(level)]
+    src = [level] + [pr.p_index(j) for j in range(pr.k)]
+    B = prod(pr.moduli[t] for t in src)
+    Q = prod(pr.moduli[i] for i in range(level))
+    for n in range(pr.N):
+        X = crt([xc[t][n] for t in limbs], [pr.moduli[t] for t in limbs])
+        Y = 0
+        for t in src:
+            b = pr.moduli[t]
+            y = int(xc[t][n]) * pow((B // b) % b, -1, b) % b
+            y = y - b if y > b // 2 else y
+            Y += y * (B // b)
+        assert (X - Y) % B == 0
+        want = (X - Y) // B
+        got = crt([outc[i][n] for i in range(level)], [pr.moduli[i] for i in range(level)])
+        assert (got - want) % Q == 0
+        assert abs(want - (2 * X + B) // (2 * B)) <= (pr.k + 1) // 2 + 1
+
+
+def test_mod_down_rescale_close_to_the_two_steps(pr):
+    """On a ciphertext-sized input the one-step division and ModDown followed by
+    rescale differ by at most a few units (two roundings against one)."""
+    rng = np.random.default_rng(5)
+    level = 3
+    limbs = pr.ks_limbs(level)
+    xc = {t: rng.integers(0, pr.moduli[t], pr.N, dtype=np.uint64) for t in limbs}
+    x = {t: pr.ntt(xc[t], t) for t in limbs}
+    one = ckks.mod_down_rescale(pr, x, level)
+    md = ckks.mod_down(pr, x, level)
+    two = ckks.rescale(pr, ckks.Ciphertext(md, md, level, 1.0)).c0
+    Q = prod(pr.moduli[i] for i in range(level))
+    for n in range(0, pr.N, 7):
+        a = crt([int(pr.intt(one[i], i)[n]) for i in range(level)], pr.moduli[:level])
+        b = crt([int(pr.intt(two[i], i)[n]) for i in range(level)], pr.moduli[:level])
+        d = (a - b) % Q
+        assert min(d, Q - d) <= pr.k + 2

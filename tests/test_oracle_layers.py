@@ -216,3 +216,40 @@ def test_he_conv_double_hoisted_matches_fp64(tiny, H, C, Co, K, BS, S, stride, n
     out2, _ = henn.he_conv(pr, keys, cts, lay, w, stride=stride, depthwise=dw, cnt=c2, bsgs_n1=n1)
     assert (c1.rot, c1.keyswitch, c1.pmult, c1.modup) == (c2.rot, c2.keyswitch, c2.pmult, c2.modup)
     assert 0 < c1.moddown <= c1.pmult
+
+
+@pytest.mark.parametrize("H,C,Co,K,BS,S,stride,n1,dw", [
+    (6, 4, 4, 3, 1, 1, 1, 0, True),    # depthwise: no outer rotation, fused
+    (8, 3, 3, 3, 2, 2, 1, 0, True),    # depthwise, S = 2, batch 2
+    (6, 8, 8, 1, 1, 1, 1, 8, False),   # BSGS with n1 = cpc: no giant step, fused
+    (6, 20, 18, 3, 1, 1, 1, 4, False), # BSGS with giant steps: the double-hoisted path
+])
+def test_he_conv_fused_moddown_rescale_matches_fp64(tiny, H, C, Co, K, BS, S, stride, n1, dw):
+    """hoist="double_fused": when the layer has no outer rotation each output is
+    its partial sum divided by q_level P in one step; the convolution stays within
+    1e-3 of FP64 with one rescale fewer than double hoisting's ModDown + rescale
+    per output, and with outer rotations it is double hoisting exactly."""
+    pr, delta = tiny
+    rng = np.random.default_rng(H * 11 + C + n1)
+    x = rng.uniform(0, 1, (BS, C, H, H))
+    w = rng.normal(0, 1 / K, ((C if dw else Co), 1 if dw else C, K, K))
+    lay = fragment.Layout(pr.N, H, H, C, BS, S)
+    Cout = C if dw else Co
+    steps = henn.conv_rotation_steps(lay, C, Cout, K, stride, depthwise=dw, bsgs_n1=n1)
+    keys = ckks.KeySet(pr, 3, rot_steps=steps)
+    cts = encrypt_layout(pr, keys, lay, x, pr.L, delta)
+    c1, c2 = henn.Counters(), henn.Counters()
+    out, olay = henn.he_conv(pr, keys, cts, lay, w, stride=stride, depthwise=dw, cnt=c1, bsgs_n1=n1,
+                             hoist="double_fused")
+    ref, _ = henn.he_conv(pr, keys, cts, lay, w, stride=stride, depthwise=dw, cnt=c2, bsgs_n1=n1,
+                          hoist="double")
+    y = decrypt_layout(pr, keys, olay, out)
+    assert np.abs(y - plain.conv2d(x, w, stride=stride, depthwise=dw)).max() < 1e-3
+    assert all(o.level == r.level for o, r in zip(out, ref))
+    fused = c1.rot == c2.rot and c1.keyswitch == c2.keyswitch and c1.rescale == c2.rescale
+    assert fused
+    no_outer = dw or n1 >= lay.cpc
+    if not no_outer:  # with outer rotations nothing changes
+        assert all(np.array_equal(o.as_array(), r.as_array()) for o, r in zip(out, ref))
+    else:  # one division instead of two roundings: residues differ, decryptions agree
+        assert any(not np.array_equal(o.as_array(), r.as_array()) for o, r in zip(out, ref))
