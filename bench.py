@@ -126,23 +126,33 @@ def barrier(dist):
         dist.barrier()
 
 
-def ntt_traffic_per_limb_pass():
-    """DRAM bytes (read + write) of one limb-pass of the NTT as ncu measured
-    them (profiles/ntt_pass_forward_N65536_532limbs.txt), or None when the
-    NTT source changed since that capture (its SHA-256 is recorded beside
-    the figure)."""
+def profiled_traffic(profile, key, source):
+    """A DRAM-traffic figure (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+    recorded in a profiles/ summary as `<key> <bytes> <source>_sha256 <hash>`,
+    or None when the kernel source changed since that capture."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "paper_2606_16359_b300", "csrc", "ntt.cu"), "rb") as f:
+        with open(os.path.join(ROOT, "paper_2606_16359_b300", "csrc", source), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        with open(os.path.join(ROOT, "profiles", "ntt_pass_forward_N65536_532limbs.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
             for line in f:
                 w = line.split()
-                if len(w) == 4 and w[0] == "traffic_bytes_per_limb_pass" and w[2] == "ntt_source_sha256":
+                if len(w) == 4 and w[0] == key:
                     return float(w[1]) if w[3] == sha else None
     except OSError:
         pass
     return None
+
+
+def ntt_traffic_per_limb_pass():
+    """DRAM bytes of one limb-pass of the NTT (ncu over 532 limbs)."""
+    return profiled_traffic("ntt_pass_forward_N65536_532limbs.txt", "traffic_bytes_per_limb_pass", "ntt.cu")
+
+
+def mac_traffic_per_launch():
+    """Mean DRAM bytes of the PMult-MAC launches of one bench step (ncu,
+    one-pass metrics over the step's launches)."""
+    return profiled_traffic("mac_pointwise_14x14x512_bsgs16.txt", "traffic_bytes_per_launch_in_step", "kernels.cu")
 
 
 def butterfly_roof(ctx, torch):
@@ -343,6 +353,9 @@ def run_ours(args, dist, rank, world, local):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": None, "launches": n_dom,
                 "avg_launch_us": 1e3 * t_dom / max(1, n_dom), "time_share": shares, "by_class": by_class}
+    if dom == "mac":
+        roofline["traffic"] = mac_traffic_per_launch()
+        roofline["traffic_unit"] = "bytes per launch (ncu dram read + write, mean over the step's launches)"
     if dom == "ntt":
         # the 64-bit-word transform is bound by the integer pipes: butterflies per
         # second against the live butterfly-probe roof; HBM figures kept beside it

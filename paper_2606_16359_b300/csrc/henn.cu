@@ -505,6 +505,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     // is loaded once for all of them
     struct MacRange {
         int first, count, ct_terms, pt_terms, outputs, ways;
+        int ct_distinct;  // distinct ciphertexts among the terms (the profiler's byte count)
     };
     const int ways = mode == 0 ? 1 : std::max(1, std::min(kMacWays, p->mac_ways));
     std::vector<MacItem> dmacs;
@@ -515,7 +516,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         return true;
     };
     auto merge = [&](size_t b, size_t e) {
-        MacRange rg{(int)dmacs.size(), 0, 0, 0, 0, 1};
+        MacRange rg{(int)dmacs.size(), 0, 0, 0, 0, 1, 0};
+        std::set<const u64*> cts;
+        for (size_t i = b; i < e; i++)
+            for (int t = 0; t < macs[i].n_terms; t++) cts.insert(mterms[macs[i].term0 + t].ct);
+        rg.ct_distinct = (int)cts.size();
         for (size_t i = b; i < e;) {
             MacItem it{};
             it.n_terms = macs[i].n_terms;
@@ -621,9 +626,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             modup(c, b_in + mu_ct(i) * z.ctw + z.nlN, z.ctw, (int)(j - i), lv, coef1 + i * z.nlN, ext1 + i * z.extw, st);
             i = j;
         }
-        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)iorder.size(), lv, st);
+        launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)iorder.size(), lv, st, (int)n_mu_all);
         if (dh) {
-            launch_lift(c, d_lift, (int)(R * (n_in_rot + p->n_in)), lv, st);
+            launch_lift(c, d_lift, (int)(R * (n_in_rot + p->n_in)), lv, st, (int)(R * n_in_rot),
+                        (int)(R * p->n_in));
         } else {
             moddown_prepare(c, acc1, (int)(R * n_in_rot), lv, conv1, st);
             launch_combine(c, d_in_cb, (int)(R * n_in_rot), lv, st);
@@ -661,7 +667,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             }
     } else {
         launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
-                   base_rg.outputs, base_rg.ways, lv, st, dh);
+                   base_rg.outputs, base_rg.ways, lv, st, dh, base_rg.ct_distinct);
         if (fuse) {
             moddown_rescale(c, accB, (int)n_base, lv, convB, d_fout, st);
         } else if (dh) {
@@ -701,7 +707,7 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         } else {
             const MacRange& rg = chunk_rg[ch];
             launch_mac(c, d_mac + rg.first, d_terms, rg.count, rg.ct_terms, rg.pt_terms, rg.outputs, rg.ways, lv,
-                       st, dh);
+                       st, dh, rg.ct_distinct);
             if (dh) {
                 moddown_prepare(c, accO, cn, lv, convO, st);
                 launch_combine(c, d_dcb + n_base + c0, cn, lv, st);

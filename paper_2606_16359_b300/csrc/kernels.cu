@@ -673,10 +673,13 @@ void launch_keyip(fe_ctx* c, const KsItem* items, int n_items, int level, cudaSt
 }
 
 void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items, int n_groups,
-                          int n_items, int level, cudaStream_t st) {
+                          int n_items, int level, cudaStream_t st, int n_sources) {
     if (!n_groups) return;
     const int np = level + 1 + c->k, dn = (level + c->k) / c->k;
-    ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + (double)n_items * (dn + 2)));
+    // algorithmic bytes: every key once, every distinct source's digits once,
+    // every item's two accumulators written
+    const double src = n_sources > 0 ? n_sources : n_items;
+    ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + src * dn + 2.0 * n_items));
     const dim3 g(n_groups, (c->N / 2 + kB - 1) / kB, level + 1 + c->k);  // two coefficients per thread
     // narrow reductions for up to 8 digits (the sums stay below 2^84)
 #define FE_KEYIP_N(D)                                                                                 \
@@ -712,10 +715,13 @@ void launch_combine(fe_ctx* c, const CombineItem* items, int n_items, int level,
     c->cnt.launches++;
 }
 
-void launch_lift(fe_ctx* c, const LiftItem* items, int n_items, int level, cudaStream_t st) {
+void launch_lift(fe_ctx* c, const LiftItem* items, int n_items, int level, cudaStream_t st, int n_acc, int n_sources) {
     if (!n_items) return;
     const int np = level + 1 + c->k;
-    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * n_items * (2.0 * np + 2.0 * np + 2.0 * (level + 1)));
+    // algorithmic bytes: each accumulator read (2 np limbs), each distinct
+    // source ciphertext read once (2 (l+1)), every output written (2 np)
+    const double acc = n_acc >= 0 ? n_acc : n_items, src = n_sources > 0 ? n_sources : n_items;
+    ProfScope ps(c, PK_COMBINE, st, 8.0 * c->N * (2.0 * np * acc + 2.0 * (level + 1) * src + 2.0 * np * n_items));
     k_lift<<<grid_for(c->N / 2, np, n_items), kB, 0, st>>>(items, c->d_mod, c->lv[level].d_ks_limbs, c->d_pmod,
                                                            c->d_pmod_sh, level, c->k, c->logN);
     c->cnt.launches++;
@@ -747,10 +753,13 @@ static void mac_launch(dim3 g, int threads, size_t smem, cudaStream_t st, const 
 }
 
 void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
-                int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st, bool qp) {
+                int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st, bool qp, int n_ct_distinct) {
     if (!n_items) return;
     const int nl = qp ? level + 1 + c->k : level + 1;
-    ProfScope ps(c, PK_MAC, st, (double)c->N * nl * (8.0 * (2.0 * n_ct_terms + 2.0 * n_outputs) +
+    // algorithmic bytes: every plaintext as stored, every distinct ciphertext once
+    // (loads of one ciphertext by several items come from L2), every output written
+    const double cts = n_ct_distinct > 0 ? n_ct_distinct : n_ct_terms;
+    ProfScope ps(c, PK_MAC, st, (double)c->N * nl * (8.0 * (2.0 * cts + 2.0 * n_outputs) +
                                                      (4.0 + c->pt_hb) * n_pt_terms));
     const int T = pt_tile(c);
     const dim3 g(n_items, c->N / T, nl);

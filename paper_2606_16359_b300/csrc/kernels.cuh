@@ -78,7 +78,10 @@ struct LiftItem {
     u64* out;
     uint32_t galois;
 };
-void launch_lift(fe_ctx* c, const LiftItem* items_dev, int n_items, int level, cudaStream_t st);
+// n_acc: items with an accumulator (-1 = all), n_sources: distinct source
+// ciphertexts (0 = every item its own); both for the profiler's byte count
+void launch_lift(fe_ctx* c, const LiftItem* items_dev, int n_items, int level, cudaStream_t st, int n_acc = -1,
+                 int n_sources = 0);
 
 // PMult-MAC item: up to kMacWays outputs whose term lists read the same
 // ciphertexts in the same order, out[k] = sum_t ct_t (x) pt_{k,t} with
@@ -114,8 +117,10 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
                   int in_pos_base, u64* out, size_t out_stride, int n_poly, bool copy_src,
                   cudaStream_t st);
 void launch_keyip(fe_ctx* c, const KsItem* items_dev, int n_items, int level, cudaStream_t st);
+// n_sources: distinct digit arrays among the items (for the profiler's byte
+// count; 0 = every item its own)
 void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups_dev, const KsItem* items_dev,
-                          int n_groups, int n_items, int level, cudaStream_t st);
+                          int n_groups, int n_items, int level, cudaStream_t st, int n_sources = 0);
 void launch_combine(fe_ctx* c, const CombineItem* items_dev, int n_items, int level,
                     cudaStream_t st);
 void launch_combine_sum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries_dev,
@@ -129,9 +134,11 @@ void launch_autosum(fe_ctx* c, const SumItem* items_dev, const SumEntry* entries
 // n_out of the items (1, 2 or 4 selects the kernel)
 // qp: operands on the key-switching basis Q_level * P (l+1+k limbs, ciphertext
 // polynomials [2][l+1+k][N], plaintexts [l+1+k][N]) instead of Q_level
+// n_ct_distinct: distinct ciphertexts among the terms (for the profiler's byte
+// count; 0 = every ciphertext load counted)
 void launch_mac(fe_ctx* c, const MacItem* items_dev, const MacTerm* terms_dev, int n_items,
                 int n_ct_terms, int n_pt_terms, int n_outputs, int ways, int level, cudaStream_t st,
-                bool qp = false);
+                bool qp = false, int n_ct_distinct = 0);
 void launch_rescale_combine(fe_ctx* c, const u64* in, const u64* lift, u64* out, int n_ct,
                             int level, cudaStream_t st);
 // out_j = (acc_j - conv_j) (q_l P)^-1 on q_0..q_{l-1} for n items (see moddown_rescale)

@@ -146,7 +146,8 @@ def bench_mac(ctx, torch, args):
 
 def bench_layer(ctx, torch, args):
     """One real layer on resident operands (no pool, no aliasing) at level 22,
-    N = 2^16, double hoisting, real keys and encoded weights: pointwise
+    N = 2^16, double hoisting (fused ModDown and rescale where it applies),
+    real keys and encoded weights: pointwise
     HxHxC -> C with baby-step / giant-step n1 = 16, or with --dw the depthwise
     3x3 conv HxHxC (H = --hw, C = --channels; the defaults keep every operand a
     few GB, larger than L2).  For ncu captures of the MAC, key inner product,
@@ -158,10 +159,10 @@ def bench_layer(ctx, torch, args):
     C, H = args.channels, args.hw
     lay = ctx.layout(H, H, C, 1, 1)
     if args.dw:
-        plan = ctx.plan_conv(lay, C, 3, depthwise=True, level=lv, double_hoist=True)
+        plan = ctx.plan_conv(lay, C, 3, depthwise=True, level=lv, double_hoist=2)
         w = np.random.default_rng(0).normal(0, 1 / 3, (C, 1, 3, 3))
     else:
-        plan = ctx.plan_conv(lay, C, 1, level=lv, bsgs_n1=16, double_hoist=True)
+        plan = ctx.plan_conv(lay, C, 1, level=lv, bsgs_n1=16, double_hoist=2)
         w = np.random.default_rng(0).normal(0, 1 / np.sqrt(C), (C, C, 1, 1))
     i = plan.info
     sk = ctx.sk_gen(5)
