@@ -158,9 +158,9 @@ const char* fe_last_error(void);
 
 /* ---- keys (client) ------------------------------------------------------- */
 
-/* Secret key: ternary s sampled from the counter-based generator (SplitMix64
- * words addressed by seed and stream), written in NTT form on every modulus:
- * sk_dev holds [n_q + k][N] uint64. */
+/* Secret key: ternary s sampled from the context's counter-based generator
+ * (fe_ctx_set_generator; words addressed by seed and stream), written in NTT
+ * form on every modulus: sk_dev holds [n_q + k][N] uint64. */
 int fe_sk_gen(fe_ctx* ctx, uint64_t seed, void* sk_dev, void* stream);
 
 /* Bytes of the switching keys for n_steps rotations (+1 relinearisation key if
@@ -178,6 +178,16 @@ size_t fe_evk_bytes(const fe_ctx* ctx, uint32_t n_steps, int relin);
 int fe_evk_gen(fe_ctx* ctx, const void* sk_dev, uint64_t seed, const int32_t* steps_host,
                uint32_t n_steps, int relin, void* evk_dev, size_t evk_bytes, void* stream,
                fe_evk** out);
+/* Server side: index switching keys that a client generated (fe_evk_gen on
+ * its own device, then copied to host memory), so that the secret key never
+ * reaches the evaluating party.  evk_host holds fe_evk_bytes(ctx, n_steps,
+ * relin) bytes in fe_evk_gen's layout for the same steps in the same order
+ * (the relinearisation key last); they are copied into the device buffer
+ * evk_dev (caller-owned, at least that size), which must outlive the handle.
+ * Errors: FE_EINVAL (short host bytes, bad or duplicate steps), FE_ENOMEM. */
+int fe_evk_upload(fe_ctx* ctx, const void* evk_host, size_t evk_host_bytes, const int32_t* steps_host,
+                  uint32_t n_steps, int relin, void* evk_dev, size_t evk_dev_bytes, void* stream,
+                  fe_evk** out);
 void fe_evk_destroy(fe_evk* evk);
 
 /* For latency measurement only: make every step in steps[] that has no key

@@ -116,6 +116,7 @@ SIGNATURES = {
     "fe_ctx_destroy": (None, [vp]),
     "fe_ctx_moduli": (cint, [vp, P(u64)]),
     "fe_ctx_set_generator": (cint, [vp, cint, P(u32)]),
+    "fe_evk_upload": (cint, [vp, vp, sz, P(i32), u32, cint, vp, sz, vp, P(vp)]),
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
@@ -314,6 +315,20 @@ class Context:
         h = vp()
         check(load().fe_evk_gen(self.handle, _ptr(sk), seed, arr, len(steps), 1 if relin else 0, _ptr(buf),
                                 nbytes, _stream(), ctypes.byref(h)))
+        return Evk(self, h, buf, steps, relin)
+
+    def evk_upload(self, host, steps, relin=False):
+        """Index switching keys produced elsewhere (host: an int64 CPU tensor in
+        evk_gen's layout for `steps` in the given order), on this device."""
+        torch = _torch()
+        steps = [int(s) for s in steps]
+        nbytes = load().fe_evk_bytes(self.handle, len(steps), 1 if relin else 0)
+        host = host.contiguous()
+        buf = torch.empty(max(8, nbytes) // 8, dtype=torch.int64, device="cuda")
+        arr = (i32 * max(1, len(steps)))(*steps)
+        h = vp()
+        check(load().fe_evk_upload(self.handle, ctypes.c_void_p(host.data_ptr()), host.numel() * 8, arr, len(steps),
+                                   1 if relin else 0, _ptr(buf), nbytes, _stream(), ctypes.byref(h)))
         return Evk(self, h, buf, steps, relin)
 
     # -- client side --------------------------------------------------------------

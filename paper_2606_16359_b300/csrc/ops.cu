@@ -294,6 +294,36 @@ extern "C" int fe_evk_gen(fe_ctx* c, const void* sk_dev, uint64_t seed, const in
     return FE_OK;
 }
 
+extern "C" int fe_evk_upload(fe_ctx* c, const void* evk_host, size_t evk_host_bytes, const int32_t* steps,
+                             uint32_t n_steps, int relin, void* evk_dev, size_t evk_dev_bytes, void* stream,
+                             fe_evk** out) {
+    FE_ALIGNED(evk_dev);
+    if (!c || !evk_host || !evk_dev || !out || (n_steps && !steps)) return fail(FE_EINVAL, "null argument");
+    const size_t need = fe_evk_bytes(c, n_steps, relin);
+    if (evk_host_bytes < need) return fail(FE_EINVAL, "host key bytes shorter than the keys of the steps");
+    if (evk_dev_bytes < need) return fail(FE_ENOMEM, "evk buffer too small");
+    const int N = c->N;
+    std::set<uint32_t> seen;
+    for (uint32_t i = 0; i < n_steps; i++) {
+        if (steps[i] % (N / 2) == 0) return fail(FE_EINVAL, "rotation step is a multiple of N/2");
+        if (!seen.insert(c->galois(steps[i])).second) return fail(FE_EINVAL, "duplicate rotation step");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    FE_CUDA_TRY(cudaMemcpyAsync(evk_dev, evk_host, need, cudaMemcpyHostToDevice, st));
+    FE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::unique_ptr<fe_evk> h(new fe_evk());
+    h->ctx = c;
+    h->base = (u64*)evk_dev;
+    const size_t key_words = (size_t)c->dnum * 2 * c->n_mod * N;
+    for (uint32_t i = 0; i < n_steps; i++) {
+        h->rot[c->galois(steps[i])] = h->base + (size_t)i * key_words;
+        h->steps.push_back(steps[i]);
+    }
+    h->relin = relin ? h->base + (size_t)n_steps * key_words : nullptr;
+    *out = h.release();
+    return FE_OK;
+}
+
 extern "C" void fe_evk_destroy(fe_evk* evk) { delete evk; }
 
 extern "C" int fe_evk_alias(fe_ctx* c, fe_evk* evk, const int32_t* steps, uint32_t n_steps, uint32_t* n_aliased) {

@@ -92,6 +92,25 @@ def test_keys_parity(which, tiny, ks2):
         assert np.array_equal(got[j, 0], keys.relin.b[j]) and np.array_equal(got[j, 1], keys.relin.a[j])
 
 
+def test_evk_upload_from_host_equals_generated(tiny):
+    """Keys generated on one side and indexed from their host bytes on the
+    other (fe_evk_upload) give the same rotations and relinearisations bit for
+    bit; host bytes shorter than the keys are rejected."""
+    pr, g = tiny.pr, tiny.g
+    sk = g.sk_gen(21)
+    steps = [-2, 1, 5]
+    evk = g.evk_gen(sk, 21, steps, relin=True)
+    host = evk.buf.cpu()
+    evk2 = g.evk_upload(host, evk.steps, relin=True)
+    z = np.random.default_rng(21).uniform(-1, 1, (2, pr.N // 2))
+    ct = g.encrypt(sk, torch.from_numpy(z), pr.L, 2.0 ** 25, seed=3)
+    for r in steps:
+        assert np.array_equal(u64(g.rotate(evk, ct, pr.L, r)), u64(g.rotate(evk2, ct, pr.L, r))), r
+    assert np.array_equal(u64(g.he_square(evk, ct, pr.L)), u64(g.he_square(evk2, ct, pr.L)))
+    with pytest.raises(fe.FencError):
+        g.evk_upload(host[:16], evk.steps, relin=True)
+
+
 def test_chacha20_generator_parity():
     """ChaCha20 (RFC 8439) as the generator on both sides: the secret key, the
     evaluation keys (b and a of every digit), fresh ciphertexts and a rotation
