@@ -298,16 +298,18 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 
 // ------------------------------------------------------------------------
 // PMult-MAC: out[poly][i][n] = sum_terms ct[poly][i][n] * pt[i][n]
-// blockIdx.y = limb i, z = item.  Partial sums stay in 128 bits and are
-// reduced every 16 terms (products of < 2^61 residues are < 2^122).
+// blockIdx.x = item, y = coefficient tile, z = limb i.  Partial sums stay in
+// 128 bits; with moduli below 2^48 (HB <= 2) a product is below 2^96 and the
+// sums are reduced once at the end, wider moduli fold every 16 terms
+// (products below 2^122).
 // ------------------------------------------------------------------------
 // PMult-MAC with the operand tiles streamed through shared memory by the bulk
 // async-copy engine.  One CTA = one item (up to W outputs sharing their
 // ciphertext terms), one limb, a tile of T coefficients (T = min(512, N)):
 // T / 2 consumer threads (two coefficients each) and one producer warp.  For
 // term t the CTA needs the tiles of c0 and c1 of the term's ciphertext (2 T 8
-// bytes) and of each output's compact plaintext (a low-word tile of T 4 bytes
-// and a high-bit tile of T HB bytes), copied with cp.async.bulk into
+// bytes) and of each output's compact plaintext (T low words and T high parts
+// of HB bytes, (4 + HB) T contiguous bytes), copied with cp.async.bulk into
 // stage t mod S and signalled on the stage's "full" mbarrier (arrive.expect_tx
 // by the producer, complete_tx by the copies).  Each consumer warp arrives on
 // the stage's "empty" mbarrier when it has read the stage; the producer waits
