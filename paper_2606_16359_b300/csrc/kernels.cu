@@ -78,13 +78,28 @@ __global__ void k_keyip(const KsItem* items, const Modulus* mods, int L, int lev
     it.acc[((size_t)(np + p) << logN) + n] = narrow ? reduce_narrow(aa, m) : reduce128(aa, m);
 }
 
-// key-stationary form: blockIdx.z = group of items that share one key; kD =
+// key-stationary form: blockIdx.x = group of items that share one key; kD =
 // number of digits (compile time, so that the key words stay in registers).
-// Each thread handles two consecutive coefficients with 16-byte accesses.
+// Each thread handles two consecutive coefficients with 16-byte accesses.  The
+// digits of the next item are fetched into shared memory by cp.async while
+// the current item is computed (double buffer); every thread copies and reads
+// only its own slots, so waiting on its own copies is enough (no barrier).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPending) : "memory");
+}
+
 template <int kD, bool kNarrow>
 __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups, const KsItem* items,
                                                           const Modulus* mods, int L, int level, int k,
                                                           int logN, int n_mod) {
+    extern __shared__ ulonglong2 ext_sm[];  // [2 buffers][kD][blockDim.x]
     const int N = 1 << logN;
     // blockIdx.x = group (fastest), so that the CTAs of all keys of one
     // (coefficient tile, limb) run together and the digits they share hit L2
@@ -95,6 +110,15 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
     const int np = level + 1 + k;
     const int mi = p <= level ? p : L + 1 + (p - level - 1);
     const Modulus m = mods[mi];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto fetch = [&](int t, int buf) {
+        const u64* ext = items[gr.item0 + t].ext;
+#pragma unroll
+        for (int j = 0; j < kD; j++)
+            cp_async16(&ext_sm[(buf * kD + j) * nt + tid], ext + ((size_t)(j * np + p) << logN) + n);
+        cp_async_commit();
+    };
+    fetch(0, 0);
     ulonglong2 kb[kD], ka[kD];
 #pragma unroll
     for (int j = 0; j < kD; j++) {
@@ -104,25 +128,29 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
     }
     const size_t ob = ((size_t)p << logN) + n, oa = ((size_t)(np + p) << logN) + n;
     for (int t = 0; t < gr.n_items; t++) {
-        const KsItem it = items[gr.item0 + t];
-        ulonglong2 e[kD];
-#pragma unroll
-        for (int j = 0; j < kD; j++)
-            e[j] = *reinterpret_cast<const ulonglong2*>(it.ext + ((size_t)(j * np + p) << logN) + n);
+        const int buf = t & 1;
+        if (t + 1 < gr.n_items) {
+            fetch(t + 1, buf ^ 1);
+            cp_async_wait<1>();  // item t's copies are complete, item t + 1's may be in flight
+        } else {
+            cp_async_wait<0>();
+        }
+        u64* acc = items[gr.item0 + t].acc;
         u128 bx = 0, by = 0, ax = 0, ay = 0;
 #pragma unroll
         for (int j = 0; j < kD; j++) {
-            bx += (u128)e[j].x * kb[j].x;
-            by += (u128)e[j].y * kb[j].y;
-            ax += (u128)e[j].x * ka[j].x;
-            ay += (u128)e[j].y * ka[j].y;
+            const ulonglong2 e = ext_sm[(buf * kD + j) * nt + tid];
+            bx += (u128)e.x * kb[j].x;
+            by += (u128)e.y * kb[j].y;
+            ax += (u128)e.x * ka[j].x;
+            ay += (u128)e.y * ka[j].y;
         }
         if (kNarrow) {
-            *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce_narrow(bx, m), reduce_narrow(by, m));
-            *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce_narrow(ax, m), reduce_narrow(ay, m));
+            *reinterpret_cast<ulonglong2*>(acc + ob) = make_ulonglong2(reduce_narrow(bx, m), reduce_narrow(by, m));
+            *reinterpret_cast<ulonglong2*>(acc + oa) = make_ulonglong2(reduce_narrow(ax, m), reduce_narrow(ay, m));
         } else {
-            *reinterpret_cast<ulonglong2*>(it.acc + ob) = make_ulonglong2(reduce128(bx, m), reduce128(by, m));
-            *reinterpret_cast<ulonglong2*>(it.acc + oa) = make_ulonglong2(reduce128(ax, m), reduce128(ay, m));
+            *reinterpret_cast<ulonglong2*>(acc + ob) = make_ulonglong2(reduce128(bx, m), reduce128(by, m));
+            *reinterpret_cast<ulonglong2*>(acc + oa) = make_ulonglong2(reduce128(ax, m), reduce128(ay, m));
         }
     }
 }
@@ -674,6 +702,16 @@ void launch_keyip(fe_ctx* c, const KsItem* items, int n_items, int level, cudaSt
     c->cnt.launches++;
 }
 
+template <int D, bool kNarrow>
+static void keyip_launch(dim3 g, size_t esm, cudaStream_t st, const KsGroup* groups, const KsItem* items, fe_ctx* c,
+                         int level) {
+    static bool set = false;  // more than 48 KiB of digit buffers when D > 6
+    if (!set && esm > (48u << 10))
+        set = cudaFuncSetAttribute(k_keyip_grouped<D, kNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)esm) == cudaSuccess;
+    k_keyip_grouped<D, kNarrow><<<g, kB, esm, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, c->n_mod);
+}
+
 void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items, int n_groups,
                           int n_items, int level, cudaStream_t st, int n_sources) {
     if (!n_groups) return;
@@ -683,20 +721,18 @@ void launch_keyip_grouped(fe_ctx* c, const KsGroup* groups, const KsItem* items,
     const double src = n_sources > 0 ? n_sources : n_items;
     ProfScope ps(c, PK_KEYIP, st, 8.0 * c->N * np * (2.0 * dn * n_groups + src * dn + 2.0 * n_items));
     const dim3 g(n_groups, (c->N / 2 + kB - 1) / kB, level + 1 + c->k);  // two coefficients per thread
+    const size_t esm = (size_t)2 * dn * kB * 16;                          // double-buffered digits
     // narrow reductions for up to 8 digits (the sums stay below 2^84)
 #define FE_KEYIP_N(D)                                                                                 \
     case D:                                                                                           \
         if (c->narrow)                                                                                \
-            k_keyip_grouped<D, true><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
-                                                       c->n_mod);                                     \
+            keyip_launch<D, true>(g, esm, st, groups, items, c, level);                              \
         else                                                                                          \
-            k_keyip_grouped<D, false><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
-                                                        c->n_mod);                                    \
+            keyip_launch<D, false>(g, esm, st, groups, items, c, level);                             \
         break;
 #define FE_KEYIP(D)                                                                                   \
     case D:                                                                                           \
-        k_keyip_grouped<D, false><<<g, kB, 0, st>>>(groups, items, c->d_mod, c->L, level, c->k, c->logN, \
-                                                    c->n_mod);                                        \
+        keyip_launch<D, false>(g, esm, st, groups, items, c, level);                                 \
         break;
     switch (dn) {
         FE_KEYIP_N(1) FE_KEYIP_N(2) FE_KEYIP_N(3) FE_KEYIP_N(4) FE_KEYIP_N(5) FE_KEYIP_N(6) FE_KEYIP_N(7)
