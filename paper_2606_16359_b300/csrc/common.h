@@ -101,6 +101,32 @@ __device__ __forceinline__ u64 reduce_narrow(u128 x, const Modulus& m) {
     const u64 r = (u64)x - qhat * m.q;
     return r >= m.q ? r - m.q : r;
 }
+// Exact sum of products x y of operands below 2^40, in three 32-bit words
+// (w2, w1, w0).  With the halves x = x1 2^32 + x0, y = y1 2^32 + y0 (x1, y1 <
+// 2^8), x y = x0 y0 + (x0 y1 + x1 y0) 2^32 + x1 y1 2^64; each partial product
+// is added to its words by 32-bit multiply-adds with carries: seven per term,
+// against the 64x64-bit high and low products and the 128-bit addition of a
+// u128 sum.  A term adds at most 2^16 + 2^9 + 3 to w2 (x1 y1 < 2^16, the high
+// words of the cross products below 2^8, three carries), so 2^15 terms fit.
+struct Acc40 {
+    uint32_t w0, w1, w2;
+};
+__device__ __forceinline__ void acc40_zero(Acc40& a) { a.w0 = a.w1 = a.w2 = 0; }
+__device__ __forceinline__ void acc40_mad(Acc40& a, u64 x, u64 y) {
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32), y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "madc.lo.u32 %2, %5, %6, %2;\n\t"
+        "mad.lo.cc.u32 %1, %3, %6, %1;\n\t"
+        "madc.hi.u32 %2, %3, %6, %2;\n\t"
+        "mad.lo.cc.u32 %1, %5, %4, %1;\n\t"
+        "madc.hi.u32 %2, %5, %4, %2;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2)
+        : "r"(x0), "r"(y0), "r"(x1), "r"(y1));
+}
+__device__ __forceinline__ u128 acc40_value(const Acc40& a) {
+    return ((u128)a.w2 << 64) | ((u64)a.w1 << 32) | a.w0;
+}
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
     return reduce128((u128)a * b, m);
 }

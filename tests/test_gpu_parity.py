@@ -487,6 +487,37 @@ def test_per_operation_path(tiny, n1):
     assert g.device_status() == 0
 
 
+@pytest.fixture(scope="module")
+def narrow():
+    """Every modulus in [2^26, 2^40): the MAC keeps its sums in three 32-bit
+    words (Acc40); base conversion and the key inner product use the narrow
+    reduction."""
+    return Pair(10, 3, 1, 30, 36)
+
+
+@pytest.mark.parametrize("dh", [False, 2])
+def test_split_sums_below_2_40_bit_exact(narrow, dh):
+    """With every modulus below 2^40 the MAC uses the three-word sums and the
+    key-switching kernels the narrow reduction; depthwise and pointwise (BSGS)
+    layers give the oracle's residues in both paths, and MAC items of 1, 2 and
+    4 outputs agree."""
+    rng = np.random.default_rng(40 + int(dh))
+    x = rng.uniform(0, 1, (1, 12, 6, 6))
+    run_conv_pair(narrow, x, rng.normal(0, 1 / 3, (12, 1, 3, 3)), 1, depthwise=True, double_hoist=dh)
+    w = rng.normal(0, 0.3, (12, 12, 1, 1))
+    plan, outs = run_conv_pair(narrow, x, w, 1, bsgs_n1=4, double_hoist=dh)
+    g, pr = narrow.g, narrow.pr
+    lay = g.layout(6, 6, 12, 1, 1)
+    sk = g.sk_gen(3)
+    evk = g.evk_gen(sk, 3, plan.steps)
+    ct = g.encrypt(sk, g.pack(lay, torch.from_numpy(x)), pr.L, 2.0 ** 25, seed=17)
+    pt = g.load_weights(plan, w, float(pr.q[pr.L]))
+    for ways in (1, 2, 4):
+        g.plan_set_mac_ways(plan, ways)
+        assert np.array_equal(u64(g.he_conv(evk, plan, pt, ct, mode=1)), u64(outs[1])), f"ways {ways}"
+    assert g.device_status() == 0
+
+
 @pytest.mark.parametrize("pbits,hb", [(36, 1), (45, 2), (52, 4)])
 def test_compact_plaintext_widths(pbits, hb):
     """Plan plaintexts are stored as a 32-bit low plane plus a 1-, 2- or 4-byte
