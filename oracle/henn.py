@@ -20,6 +20,9 @@ HE convolution (the algorithm, in the order it is evaluated here):
     position that is not a valid output of the (strided) valid convolution.
  3. Outer rotations (channel dependency, Eq. 4): out = P_0 + sum_{d != 0}
     Rot(P_d, d m^2 BS), before any rescale; all-zero diagonals are skipped.
+    An output with no nonzero term at all (its fragment holds no valid output
+    position, or every weight it reads is zero) is an empty sum: the zero
+    ciphertext.
  4. One rescale.
 Weights are encoded at scale q_level by default, so the output scale equals the
 input scale.  Stride 2 keeps the output fragments with even (u', v') and halves S
@@ -53,6 +56,15 @@ def _add(pr, acc, x):
     if acc is None:
         return x.copy()
     return ckks.add(pr, acc, x)
+
+
+def _empty_sum(pr, level, scale):
+    """An output ciphertext none of whose terms has a nonzero plaintext (its
+    fragment holds no valid output position, or every weight it reads is zero):
+    the sum of step 3 is empty, so the output is the zero ciphertext, at the
+    level and scale that the rescaled sum would have had."""
+    z = np.zeros((level, pr.N), dtype=np.uint64)
+    return ckks.Ciphertext(z, z.copy(), level - 1, scale / pr.moduli[level])
 
 
 def out_layout_conv(lay, Cout, K, stride):
@@ -248,7 +260,9 @@ def he_conv(pr, keys, cts, lay, W, *, stride=1, depthwise=False, in_period=None,
                         cnt.keyswitch += 1
                         cnt.modup += 1
                     total = _add(pr, total, acc)
-                if fused:
+                if total is None:
+                    res = _empty_sum(pr, level, cts[0].scale * dw)
+                elif fused:
                     res = total
                 else:
                     res = ckks.rescale(pr, total)
@@ -355,7 +369,9 @@ def he_conv_bsgs(pr, keys, cts, lay, W, *, stride=1, wmul=1.0, w_scale=None, cnt
                         cnt.keyswitch += 1
                         cnt.modup += 1
                     total = _add(pr, total, acc)
-                if fused:
+                if total is None:
+                    res = _empty_sum(pr, level, cts[0].scale * dw)
+                elif fused:
                     res = total
                 else:
                     res = ckks.rescale(pr, total)

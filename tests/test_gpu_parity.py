@@ -202,7 +202,7 @@ ORACLE_HOIST = {0: "single", 1: "double", 2: "double_fused"}
 
 
 def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25, modes=(0, 1), bsgs_n1=0,
-                  double_hoist=False):
+                  double_hoist=False, check_counts=True):
     pr, g = P.pr, P.g
     BS, C, H, _ = x.shape
     Cout = w.shape[0]
@@ -221,8 +221,9 @@ def run_conv_pair(P, x, w, S, stride=1, depthwise=False, seed=3, delta=2.0 ** 25
     plan = g.plan_conv(lay, Cout, K, stride=stride, depthwise=depthwise, level=pr.L, bsgs_n1=bsgs_n1,
                        double_hoist=double_hoist)
     assert sorted(plan.steps) == sorted(steps)
-    assert plan.info.n_inner_rot + plan.info.n_outer_rot == ocnt.rot
-    assert plan.info.n_pt == ocnt.pmult
+    if check_counts:  # the plan is structural; the oracle also drops plaintexts that are zero by value
+        assert plan.info.n_inner_rot + plan.info.n_outer_rot == ocnt.rot
+        assert plan.info.n_pt == ocnt.pmult
     sk = g.sk_gen(seed)
     evk = g.evk_gen(sk, seed, plan.steps)
     xs = g.pack(lay, torch.from_numpy(x))
@@ -251,6 +252,37 @@ def test_conv_parity(tiny, H, C, Co, K, BS, S, stride):
     x = rng.uniform(0, 1, (BS, C, H, H))
     w = rng.normal(0, 1 / K, (Co, C, K, K))
     run_conv_pair(tiny, x, w, S, stride)
+
+
+@pytest.mark.parametrize("n1,dh", [(0, False), (2, False), (0, 2)])
+def test_conv_parity_empty_sums(tiny, n1, dh):
+    """Outputs with no nonzero term are the zero ciphertext on both sides: with
+    H = 6, K = 5, S = 4 the fragments u', v' > H - K hold no valid output (12 of
+    16 outputs), and all-zero weights empty every output; single hoisting with
+    linear and baby-step / giant-step outer rotations, and fused double hoisting."""
+    rng = np.random.default_rng(70 + n1)
+    x = rng.uniform(0, 1, (1, 2, 6, 6))
+    plan, outs = run_conv_pair(tiny, x, rng.normal(0, 1 / 5, (3, 2, 5, 5)), 4, bsgs_n1=n1, double_hoist=dh)
+    res = u64(outs[1]).reshape(plan.info.n_out_ct, -1)
+    assert int((~res.any(axis=1)).sum()) == 12
+    plan, outs = run_conv_pair(tiny, x, np.zeros((3, 2, 5, 5)), 4, bsgs_n1=n1, double_hoist=dh,
+                               check_counts=False)
+    assert not u64(outs[1]).any() and not u64(outs[0]).any()
+    assert tiny.g.device_status() == 0
+
+
+@pytest.mark.parametrize("H,C,Co,K,S", [
+    (6, 1, 1, 1, 1),   # one channel, 1x1 kernel: no rotation at all
+    (5, 2, 3, 5, 1),   # kernel as large as the map: one valid output per channel
+    (5, 3, 2, 5, 2),   # the same with S = 2: three of the four output fragments are empty
+])
+def test_conv_parity_degenerate_shapes(tiny, H, C, Co, K, S):
+    rng = np.random.default_rng(H * 31 + C + K)
+    x = rng.uniform(0, 1, (1, C, H, H))
+    plan, _ = run_conv_pair(tiny, x, rng.normal(0, 1 / K, (Co, C, K, K)), S)
+    if K == 1 and C == 1:
+        assert plan.info.n_inner_rot == 0 and plan.info.n_outer_rot == 0 and not plan.steps
+    assert tiny.g.device_status() == 0
 
 
 def test_conv_parity_depthwise_and_two_prime_digits(ks2):

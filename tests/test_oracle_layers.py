@@ -57,6 +57,37 @@ def test_he_conv_matches_fp64(tiny, H, C, Co, K, BS, S, stride):
     assert np.abs(full[~mask]).max() < 1e-3
 
 
+@pytest.mark.parametrize("n1,hoist", [(0, "single"), (2, "single"), (0, "double_fused")])
+def test_he_conv_empty_sums_are_zero_ciphertexts(tiny, n1, hoist):
+    """Outputs none of whose terms has a nonzero plaintext: with H = 6, K = 5,
+    S = 4 the valid outputs (h, w <= H - K = 1) lie only in fragments u', v' <= 1,
+    so 12 of the 16 output ciphertexts are empty sums; with all-zero weights every
+    output is.  An empty sum is the zero ciphertext (every residue 0) at the
+    output level and scale, and the decrypted layer equals the FP64 convolution."""
+    pr, delta = tiny
+    rng = np.random.default_rng(66 + n1)
+    H, C, Co, K, S = 6, 2, 3, 5, 4
+    x = rng.uniform(0, 1, (1, C, H, H))
+    for w in (rng.normal(0, 1 / K, (Co, C, K, K)), np.zeros((Co, C, K, K))):
+        lay = fragment.Layout(pr.N, H, H, C, 1, S)
+        keys = ckks.KeySet(pr, 3, rot_steps=henn.conv_rotation_steps(lay, C, Co, K, bsgs_n1=n1))
+        cts = encrypt_layout(pr, keys, lay, x, pr.L, delta)
+        cnt = henn.Counters()
+        out, olay = henn.he_conv(pr, keys, cts, lay, w, cnt=cnt, bsgs_n1=n1, hoist=hoist)
+        assert np.abs(decrypt_layout(pr, keys, olay, out) - plain.conv2d(x, w)).max() < 1e-3
+        nonzero_w = bool(w.any())
+        for h in range(olay.groups):
+            for up in range(S):
+                for vp in range(S):
+                    c = out[olay.ct_index(h, up, vp)]
+                    assert c.level == pr.L - 1 and c.scale == delta
+                    empty = not nonzero_w or up > H - K or vp > H - K
+                    assert (not c.as_array().any()) == empty
+        assert cnt.rescale == (4 * olay.groups if nonzero_w else 0)
+        if not nonzero_w:
+            assert cnt.pmult == 0
+
+
 def test_he_conv_depthwise(tiny):
     pr, delta = tiny
     rng = np.random.default_rng(5)
