@@ -529,6 +529,9 @@ def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None):
                 cnt.keyswitch += 1
                 cnt.modup += 1
             total = _add(pr, total, acc)
+        if total is None:  # every weight of these outputs is zero: an empty sum
+            out.append(_empty_sum(pr, level, cts[0].scale * dw))
+            continue
         out.append(ckks.rescale(pr, total))
         cnt.rescale += 1
     return out

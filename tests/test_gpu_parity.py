@@ -344,6 +344,17 @@ def test_square_pool_fc_parity():
     for mode in (0, 1):
         out = g.he_fc(evk, plan, pt, pooled, mode=mode)
         assert np.array_equal(u64(out), oracle_ct_array(ofc)), mode
+    # outputs Pp .. Pp + 2 with all-zero weights: their ciphertext is the zero
+    # ciphertext on both sides (an empty sum in the oracle)
+    wz = np.zeros((Pp + 3, 8))
+    wz[:7] = wfc
+    ofz = henn.he_fc(pr, keys, opool, feat, Pp, opl.BS, wz)
+    planz = g.plan_fc(len(opool), Pp, opl.BS, ftab, 8, Pp + 3, pr.L - 1)
+    ptz = g.load_weights(planz, wz, float(pr.q[pr.L - 1]))
+    for mode in (0, 1):
+        out = u64(g.he_fc(evk, planz, ptz, pooled, mode=mode))
+        assert np.array_equal(out, oracle_ct_array(ofz)), mode
+        assert not out[1].any()
 
 
 def test_aac_compress_parity(tiny):

@@ -165,6 +165,15 @@ def test_square_pool_fc(tiny):
     y = henn.lenet_decode_logits(dec, P, pl.BS, 7)
     ref_fc = plain.fc(ref.reshape(4, -1), wfc)
     assert np.abs(y - ref_fc).max() < 1e-3
+    # outputs P .. P + 2 have all-zero weights, so their ciphertext is an empty
+    # sum: the zero ciphertext at the output level and scale; the first one is
+    # unchanged (its extra rows are zero too)
+    wz = np.zeros((P + 3, wfc.shape[1]))
+    wz[:7] = wfc
+    out2 = henn.he_fc(pr, keys, pooled, feat, P, pl.BS, wz)
+    assert len(out2) == 2 and np.array_equal(out2[0].as_array(), out[0].as_array())
+    assert not out2[1].as_array().any()
+    assert (out2[1].level, out2[1].scale) == (out[0].level, out[0].scale)
 
 
 @pytest.mark.slow
