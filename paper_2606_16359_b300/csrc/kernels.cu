@@ -116,14 +116,18 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
     const int mi = p <= level ? p : L + 1 + (p - level - 1);
     const Modulus m = mods[mi];
     const int tid = threadIdx.x, nt = blockDim.x;
-    auto fetch = [&](int t, int buf) {
-        const u64* ext = items[gr.item0 + t].ext;
+    // the item pointers are loaded one item ahead of their use (item t + 2's
+    // digits while item t is computed), so their global loads stay off the
+    // path between two items
+    const KsItem* its = items + gr.item0;
+    auto fetch = [&](const u64* ext, int buf) {
 #pragma unroll
         for (int j = 0; j < kD; j++)
             cp_async16(&ext_sm[(buf * kD + j) * nt + tid], ext + ((size_t)(j * np + p) << logN) + n);
         cp_async_commit();
     };
-    fetch(0, 0);
+    fetch(its[0].ext, 0);
+    const u64* ext_next = gr.n_items > 1 ? its[1].ext : nullptr;
     ulonglong2 kb[kD], ka[kD];
 #pragma unroll
     for (int j = 0; j < kD; j++) {
@@ -134,13 +138,14 @@ __global__ void __launch_bounds__(256, 2) k_keyip_grouped(const KsGroup* groups,
     const size_t ob = ((size_t)p << logN) + n, oa = ((size_t)(np + p) << logN) + n;
     for (int t = 0; t < gr.n_items; t++) {
         const int buf = t & 1;
+        u64* acc = its[t].acc;
         if (t + 1 < gr.n_items) {
-            fetch(t + 1, buf ^ 1);
+            fetch(ext_next, buf ^ 1);
+            ext_next = t + 2 < gr.n_items ? its[t + 2].ext : nullptr;
             cp_async_wait<1>();  // item t's copies are complete, item t + 1's may be in flight
         } else {
             cp_async_wait<0>();
         }
-        u64* acc = items[gr.item0 + t].acc;
         u128 bx = 0, by = 0, ax = 0, ay = 0;
 #pragma unroll
         for (int j = 0; j < kD; j++) {
@@ -410,7 +415,10 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
     const size_t stage_stride = (size_t)(16 + W * (4 + HB)) * T;
     // blockIdx.x = item (fastest): the items of one (tile, limb) run together and
     // the ciphertext tiles they share are read from L2
-    const MacItem it = items[blockIdx.x];
+    // the item stays in global memory (cached): its counts are kept in
+    // registers, its pointers and term indices are read where they are used
+    const MacItem* itp = items + blockIdx.x;
+    const int n_terms = itp->n_terms, n_out = itp->n_out;
     const int i = blockIdx.z;
     const Modulus m = mods[mod_map ? mod_map[i] : i];
     const size_t base = (size_t)blockIdx.y * T;
@@ -432,26 +440,39 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
     }
     __syncthreads();
     if (tid >= n_cons) {
-        // producer warp: lane 0 keeps up to S terms in flight
+        // producer warp: lane 0 keeps up to S terms in flight.  The operand
+        // pointers of the next term are loaded as soon as the current term's
+        // copies are issued, so their global loads complete during the wait
+        // for a free stage; the loops over the outputs are unrolled over W so
+        // that the item stays in registers.
         if (tid != n_cons) return;
-        const uint32_t stage_bytes = 2 * ct_tile + (uint32_t)it.n_out * (lo_tile + hi_tile);
+        const uint32_t stage_bytes = 2 * ct_tile + (uint32_t)n_out * (lo_tile + hi_tile);
+        const u64* ct = nullptr;
+        const uint8_t* pt[W];
+        auto load_pointers = [&](int t) {
+            ct = terms[itp->term0[0] + t].ct;
+#pragma unroll
+            for (int k = 0; k < W; k++) pt[k] = k < n_out ? terms[itp->term0[k] + t].pt : nullptr;
+        };
+        if (n_terms > 0) load_pointers(0);
         int issued = 0;
         bool ok = true;
-        for (; issued < it.n_terms; issued++) {
+        for (; issued < n_terms; issued++) {
             const int s = issued % S;
             if (issued >= S && !mbar_wait(&empty[s], (uint32_t)((issued / S - 1) & 1), limit)) {
                 ok = false;
                 break;
             }
             unsigned char* st = stage0 + (size_t)s * stage_stride;
-            const u64* ct = terms[it.term0[0] + issued].ct;
             mbar_expect_tx(&full[s], stage_bytes);
             bulk_g2s(st, ct + off0, ct_tile, &full[s]);
             bulk_g2s(st + ct_tile, ct + off1, ct_tile, &full[s]);
-            for (int k = 0; k < it.n_out; k++) {
-                bulk_g2s(st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile), terms[it.term0[k] + issued].pt + pt_off,
-                         lo_tile + hi_tile, &full[s]);
-            }
+#pragma unroll
+            for (int k = 0; k < W; k++)
+                if (k < n_out)
+                    bulk_g2s(st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile), pt[k] + pt_off, lo_tile + hi_tile,
+                             &full[s]);
+            if (issued + 1 < n_terms) load_pointers(issued + 1);
         }
         if (!ok) {
             atomicOr(status, 1u);
@@ -482,7 +503,7 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
         zero(b0[k]);
         zero(b1[k]);
     }
-    for (int t = 0; t < it.n_terms; t++) {
+    for (int t = 0; t < n_terms; t++) {
         const int s = t % S;
         if (!mbar_wait(&full[s], (uint32_t)((t / S) & 1), limit)) {
             atomicOr(status, 1u);
@@ -493,7 +514,7 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
         const ulonglong2 x1 = reinterpret_cast<const ulonglong2*>(st + ct_tile)[tid];
 #pragma unroll
         for (int k = 0; k < W; k++) {
-            if (k >= it.n_out) break;
+            if (k >= n_out) break;
             const unsigned char* pk = st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile);
             const uint2 lo = reinterpret_cast<const uint2*>(pk)[tid];
             u64 hx, hy;
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
             };
 #pragma unroll
             for (int k = 0; k < W; k++) {
-                if (k >= it.n_out) break;
+                if (k >= n_out) break;
                 fold(a0[k]);
                 fold(a1[k]);
                 fold(b0[k]);
@@ -537,14 +558,14 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
     }
 #pragma unroll
     for (int k = 0; k < W; k++) {
-        if (k >= it.n_out) break;
+        if (k >= n_out) break;
         ulonglong2 r0, r1;
         r0.x = reduce128(value(a0[k]), m);
         r0.y = reduce128(value(a1[k]), m);
         r1.x = reduce128(value(b0[k]), m);
         r1.y = reduce128(value(b1[k]), m);
-        reinterpret_cast<ulonglong2*>(it.out[k] + off0)[tid] = r0;
-        reinterpret_cast<ulonglong2*>(it.out[k] + off1)[tid] = r1;
+        reinterpret_cast<ulonglong2*>(itp->out[k] + off0)[tid] = r0;
+        reinterpret_cast<ulonglong2*>(itp->out[k] + off1)[tid] = r1;
     }
 }
 
