@@ -55,6 +55,67 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
     }
 }
 
+// Two coefficients per thread (n, n + 1) with 16-byte accesses: the table
+// words are read once for both, and with every modulus below 2^40 each
+// destination keeps two independent three-word sums (Acc40).  Needs 16-byte
+// aligned bases and even strides (checked by the launcher).
+template <int kS, bool kNarrow>
+__global__ void k_bconv2(BConvTab t, const Modulus* mods, int L, int level, int logN,
+                         const u64* in, size_t in_stride, int in_pos_base, u64* out,
+                         size_t out_stride, int copy_src) {
+    const int N = 1 << logN;
+    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (n >= N) return;
+    const u64* ip = in + blockIdx.y * in_stride;
+    u64* op = out + blockIdx.y * out_stride;
+    u64 y0[kS], y1[kS];
+    int neg0 = 0, neg1 = 0;
+#pragma unroll
+    for (int i = 0; i < kS; i++) {
+        const int mi = t.src[i];
+        const u64 b = mods[mi].q;
+        const ulonglong2 x =
+            *reinterpret_cast<const ulonglong2*>(ip + ((size_t)(ext_pos(mi, L, level) - in_pos_base) << logN) + n);
+        if (copy_src) *reinterpret_cast<ulonglong2*>(op + ((size_t)ext_pos(mi, L, level) << logN) + n) = x;
+        y0[i] = mul_shoup(x.x, t.inv[i], t.inv_sh[i], b);
+        y1[i] = mul_shoup(x.y, t.inv[i], t.inv_sh[i], b);
+        neg0 += y0[i] > (b >> 1);
+        neg1 += y1[i] > (b >> 1);
+    }
+    for (int d = 0; d < t.n_dst; d++) {
+        const int mt = t.dst[d];
+        const u64* row = t.mat + d * kS;
+        const u64 nb = t.negB[d];
+        ulonglong2 r;
+        if constexpr (kNarrow) {
+            Acc40 a0, a1;
+            acc40_zero(a0);
+            acc40_zero(a1);
+            acc40_mad(a0, nb, (u64)neg0);
+            acc40_mad(a1, nb, (u64)neg1);
+#pragma unroll
+            for (int i = 0; i < kS; i++) {
+                const u64 w = row[i];
+                acc40_mad(a0, y0[i], w);
+                acc40_mad(a1, y1[i], w);
+            }
+            r.x = reduce_narrow(acc40_value(a0), mods[mt]);
+            r.y = reduce_narrow(acc40_value(a1), mods[mt]);
+        } else {
+            u128 a0 = (u128)nb * (u64)neg0, a1 = (u128)nb * (u64)neg1;
+#pragma unroll
+            for (int i = 0; i < kS; i++) {
+                const u64 w = row[i];
+                a0 += (u128)y0[i] * w;
+                a1 += (u128)y1[i] * w;
+            }
+            r.x = reduce128(a0, mods[mt]);
+            r.y = reduce128(a1, mods[mt]);
+        }
+        *reinterpret_cast<ulonglong2*>(op + ((size_t)ext_pos(mt, L, level) << logN) + n) = r;
+    }
+}
+
 // ------------------------------------------------------------------------
 // Evaluation-key inner product:
 //   acc_b[p][n] = sum_j ext_j[p][n] * key_j.b[kl(p)][n],  acc_a likewise,
@@ -730,11 +791,20 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
                   cudaStream_t st) {
     if (n_poly == 0) return;
     ProfScope ps(c, PK_BCONV, st, 8.0 * c->N * n_poly * (t.n_src * (copy_src ? 2 : 1) + t.n_dst));
-    const dim3 g = grid_for(c->N, n_poly);
     const int cs = copy_src ? 1 : 0;
+    // two coefficients per thread when every 16-byte access is aligned
+    const bool pair = c->N >= 2 && !(((uintptr_t)in | (uintptr_t)out) & 15) && !(in_stride & 1) &&
+                      !(out_stride & 1) && !(c->N & 1);
+    const dim3 g = pair ? grid_for(c->N / 2, n_poly) : grid_for(c->N, n_poly);
 #define FE_BCONV(S)                                                                                   \
     case S:                                                                                           \
-        if (c->narrow)                                                                                \
+        if (pair && c->narrow)                                                                        \
+            k_bconv2<S, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,     \
+                                                in_pos_base, out, out_stride, cs);                    \
+        else if (pair)                                                                                \
+            k_bconv2<S, false><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,    \
+                                                 in_pos_base, out, out_stride, cs);                   \
+        else if (c->narrow)                                                                           \
             k_bconv<S, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,      \
                                                in_pos_base, out, out_stride, cs);                     \
         else                                                                                          \
