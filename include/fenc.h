@@ -18,7 +18,9 @@
  *    without a bound.
  *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors);
  *    *_host are host pointers.  Device buffers passed in are owned by the
- *    caller; the library never frees them.  Library objects (fe_ctx, fe_evk,
+ *    caller; the library never frees them.  Every device buffer must start on a
+ *    16-byte boundary (cudaMalloc and torch allocations do; kernels use 16-byte
+ *    accesses); a misaligned one is rejected with FE_EINVAL before any launch.  Library objects (fe_ctx, fe_evk,
  *    fe_plan, fe_graph) are opaque handles released with their *_destroy call.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Calls enqueue work and return without synchronising unless stated.

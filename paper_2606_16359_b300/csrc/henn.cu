@@ -756,6 +756,8 @@ extern "C" int fe_layout_make(const fe_ctx* c, fe_layout* l) {
 extern "C" int fe_fragment_pack(const fe_ctx* c, const fe_layout* lay, const double* x, double* slots,
                                 void* stream) {
     if (!c || !lay || !x || !slots) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(x);
+    FE_ALIGNED(slots);
     fe_layout L = *lay;
     FE_TRY(layout_fill(c->N, &L));
     k_pack<<<dim3((c->N / 2 + kB - 1) / kB, L.n_ct), kB, 0, (cudaStream_t)stream>>>(x, slots, L, c->N);
@@ -766,6 +768,8 @@ extern "C" int fe_fragment_pack(const fe_ctx* c, const fe_layout* lay, const dou
 extern "C" int fe_fragment_unpack(const fe_ctx* c, const fe_layout* lay, const double* slots, double* y,
                                   void* stream) {
     if (!c || !lay || !slots || !y) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(slots);
+    FE_ALIGNED(y);
     fe_layout L = *lay;
     FE_TRY(layout_fill(c->N, &L));
     size_t total = (size_t)L.BS * L.C * L.H * L.W;

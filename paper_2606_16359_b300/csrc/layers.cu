@@ -112,6 +112,8 @@ extern "C" int fe_he_square(fe_ctx* c, const fe_evk* evk, const void* in_dev, ui
 extern "C" int fe_he_avgpool(fe_ctx* c, const fe_layout* lay, const void* in_dev, uint32_t level, void* out_dev,
                              fe_layout* out_lay, void* stream) {
     if (!c || !lay || !in_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(in_dev);
+    FE_ALIGNED(out_dev);
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     fe_layout L = *lay;
     FE_TRY(layout_fill(c->N, &L));
@@ -230,8 +232,13 @@ extern "C" int fe_graph_capture_batch(fe_ctx* c, const fe_evk* evk, const fe_pla
     if (n_req == 0) return fail(FE_EINVAL, "n_req must be positive");
     cudaStream_t st = (cudaStream_t)stream;
     if (!st) return fail(FE_EINVAL, "graph capture needs a non-default stream");
-    for (uint32_t i = 0; i < n; i++)
+    FE_ALIGNED(ws);
+    for (uint32_t i = 0; i < n; i++) {
         if (!plans[i]) return fail(FE_EINVAL, "null plan");
+        FE_ALIGNED(pts[i]);
+        FE_ALIGNED(ins[i]);
+        FE_ALIGNED(outs[i]);
+    }
     // every layer keeps its own item tables (they must survive until replay);
     // the data region (rotated copies, sums, scratch) is shared, layers run in order
     const size_t data = graph_data_bytes(plans, n, n_req);

@@ -350,6 +350,7 @@ extern "C" int fe_evk_alias(fe_ctx* c, fe_evk* evk, const int32_t* steps, uint32
 
 extern "C" int fe_encode(fe_ctx* c, const double* slots, uint32_t n, uint32_t level, double scale,
                          void* pt_dev, void* stream) {
+    FE_ALIGNED(slots);
     FE_ALIGNED(pt_dev);
     if (!c || !slots || !pt_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
@@ -359,6 +360,7 @@ extern "C" int fe_encode(fe_ctx* c, const double* slots, uint32_t n, uint32_t le
 extern "C" int fe_encode_encrypt(fe_ctx* c, const void* sk_dev, const double* slots, uint32_t n_ct,
                                  uint32_t level, double scale, uint64_t seed, uint64_t ct_id0, void* ct_dev,
                                  void* stream) {
+    FE_ALIGNED(slots);
     FE_ALIGNED(ct_dev); FE_ALIGNED(sk_dev);
     if (!c || !sk_dev || !slots || !ct_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
@@ -390,6 +392,7 @@ extern "C" int fe_encode_encrypt(fe_ctx* c, const void* sk_dev, const double* sl
 
 extern "C" int fe_decrypt_decode(fe_ctx* c, const void* sk_dev, const void* ct_dev, uint32_t n_ct,
                                  uint32_t level, double scale, double* slots, void* stream) {
+    FE_ALIGNED(slots);
     FE_ALIGNED(ct_dev); FE_ALIGNED(sk_dev);
     if (!c || !sk_dev || !ct_dev || !slots) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
@@ -514,6 +517,9 @@ extern "C" int fe_rescale(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t
 extern "C" int fe_pmult(fe_ctx* c, const void* ct_dev, const void* pt_dev, uint32_t n_ct, uint32_t level,
                         void* out_dev, void* stream) {
     if (!c || !ct_dev || !pt_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(ct_dev);
+    FE_ALIGNED(pt_dev);
+    FE_ALIGNED(out_dev);
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     launch_pmult(c, (const u64*)ct_dev, (const u64*)pt_dev, (u64*)out_dev, n_ct, level, false,
                  (cudaStream_t)stream);
@@ -525,6 +531,9 @@ extern "C" int fe_pmult(fe_ctx* c, const void* ct_dev, const void* pt_dev, uint3
 extern "C" int fe_add(fe_ctx* c, const void* a, const void* b, uint32_t n_ct, uint32_t level, void* out,
                       void* stream) {
     if (!c || !a || !b || !out) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(a);
+    FE_ALIGNED(b);
+    FE_ALIGNED(out);
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     launch_add(c, (const u64*)a, (const u64*)b, (u64*)out, n_ct, level, (cudaStream_t)stream);
     FE_CUDA_TRY(cudaGetLastError());

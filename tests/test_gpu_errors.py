@@ -76,6 +76,26 @@ def test_rejected_calls_return_their_status_and_leave_the_context_usable(g, keys
         ("no-alloc rescale at level 0", lambda: lib.fe_rescale_noalloc(g.handle, P(ct), 1, 0, P(out), s),
          fe.FE_ELEVEL),
     ]
+    # every call that takes device buffers rejects a misaligned one before launching
+    slots = torch.zeros((2, g.N // 2), dtype=torch.float64, device="cuda")
+    bad_slots = ctypes.c_void_p(slots.data_ptr() + 8)
+    lay = g.layout(4, 4, 1, 1, 2)
+    out_lay = fe.FeLayout()
+    cases += [
+        ("misaligned pmult", lambda: lib.fe_pmult(g.handle, misaligned, P(ct), 1, g.L, P(out), s), fe.FE_EINVAL),
+        ("misaligned add", lambda: lib.fe_add(g.handle, P(ct), misaligned, 1, g.L, P(out), s), fe.FE_EINVAL),
+        ("misaligned encode", lambda: lib.fe_encode(g.handle, bad_slots, 1, g.L, 2.0 ** 25, P(out), s), fe.FE_EINVAL),
+        ("misaligned encrypt", lambda: lib.fe_encode_encrypt(g.handle, P(sk), bad_slots, 1, g.L, 2.0 ** 25, 5, 0,
+                                                             P(out), s), fe.FE_EINVAL),
+        ("misaligned decrypt", lambda: lib.fe_decrypt_decode(g.handle, P(sk), P(ct), 1, g.L, 2.0 ** 25, bad_slots, s),
+         fe.FE_EINVAL),
+        ("misaligned pack", lambda: lib.fe_fragment_pack(g.handle, ctypes.byref(lay), bad_slots, P(slots), s),
+         fe.FE_EINVAL),
+        ("misaligned unpack", lambda: lib.fe_fragment_unpack(g.handle, ctypes.byref(lay), bad_slots, P(slots), s),
+         fe.FE_EINVAL),
+        ("misaligned pool", lambda: lib.fe_he_avgpool(g.handle, ctypes.byref(lay), misaligned, g.L, P(out),
+                                                      ctypes.byref(out_lay), s), fe.FE_EINVAL),
+    ]
     for name, call, code in cases:
         assert call() == code, name
         assert lib.fe_last_error(), name
