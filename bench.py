@@ -155,6 +155,27 @@ def mac_traffic_per_launch():
     return profiled_traffic("mac_pointwise_14x14x512_bsgs16.txt", "traffic_bytes_per_launch_in_step", "kernels.cu")
 
 
+# Warp instructions per lazy Shoup butterfly, counted by ncu on the register-
+# resident probe (profiles/ntt_pass_forward_N65536_532limbs.txt).
+BUTTERFLY_WARP_INSTRUCTIONS = 23.2
+
+
+def butterfly_issue_roof(torch):
+    """Butterflies per second at the issue limit, Gbutterfly/s: every SM's four
+    schedulers issue one warp instruction per clock at the maximum SM clock, and
+    a warp completes 32 butterflies per BUTTERFLY_WARP_INSTRUCTIONS."""
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz") or 0) or None
+    except (OSError, ValueError):
+        pass
+    if mhz is None:
+        mhz = 2032.0  # B300 maximum SM clock
+    return n_sm * 4 * mhz * 1e6 * 32 / BUTTERFLY_WARP_INSTRUCTIONS / 1e9, n_sm, mhz
+
+
 def butterfly_roof(ctx, torch):
     """Integer-pipe roof of the NTT butterfly arithmetic on this GPU, Gbutterfly/s
     (register-resident probe of the transform's own butterflies, one full wave)."""
@@ -366,8 +387,14 @@ def run_ours(args, dist, rank, world, local):
         tpl = ntt_traffic_per_limb_pass()
         roofline["traffic"] = tpl * limb_passes / n_dom if tpl else None
         roofline["traffic_unit"] = "bytes per launch (ncu dram read + write; algorithmic: %.0f)" % (b_dom / n_dom)
-        roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": bfly_peak, "unit": "Gbutterfly/s",
-                         "frac": bfly_rate / bfly_peak, "peak_source": "butterfly probe, this run",
+        issue_peak, n_sm, mhz = butterfly_issue_roof(torch)
+        roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": issue_peak, "unit": "Gbutterfly/s",
+                         "frac": bfly_rate / issue_peak,
+                         "peak_source": "issue limit: %d SMs x 4 warp instructions per clock x %.0f MHz x 32 lanes"
+                                        " / %.1f warp instructions per butterfly" % (n_sm, mhz,
+                                                                                     BUTTERFLY_WARP_INSTRUCTIONS),
+                         "probe_peak": bfly_peak, "frac_of_probe": bfly_rate / bfly_peak,
+                         "probe_source": "butterfly probe, this run (register-resident, one full wave)",
                          "hbm_GBps": achieved, "hbm_peak_GBps": peak, "hbm_frac": achieved / peak,
                          "hbm_peak_source": peak_kind})
 
