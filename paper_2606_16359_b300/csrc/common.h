@@ -127,6 +127,38 @@ __device__ __forceinline__ void acc40_mad(Acc40& a, u64 x, u64 y) {
 __device__ __forceinline__ u128 acc40_value(const Acc40& a) {
     return ((u128)a.w2 << 64) | ((u64)a.w1 << 32) | a.w0;
 }
+// Exact sum of products x y of operands below 2^36, as a + b 2^24.  With
+// x = x0 + x1 2^32 (x1 < 2^4) and y = yl + yh 2^24 (yl < 2^24, yh < 2^12):
+//   a += x yl = x0 yl + (x1 yl) 2^32   (below 2^60: one widening and one 32-bit multiply-add)
+//   b += x yh = x0 yh + (x1 yh) 2^32   (below 2^48: the same)
+// so a product costs two widening and two 32-bit multiply-adds with no carry
+// chain.  Sixteen terms fit a; acc36_fold moves a's high part into b (every 16
+// terms), after which 2^15 more terms fit b.
+struct Acc36 {
+    u64 a, b;
+};
+__device__ __forceinline__ void acc36_zero(Acc36& s) { s.a = s.b = 0; }
+__device__ __forceinline__ void acc36_mad(Acc36& s, u64 x, uint32_t yl, uint32_t yh) {
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    asm("{ .reg .u32 lo, hi;\n\t"
+        "mad.wide.u32 %0, %2, %3, %0;\n\t"
+        "mov.b64 {lo, hi}, %0;\n\t"
+        "mad.lo.u32 hi, %4, %3, hi;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t"
+        "mad.wide.u32 %1, %2, %5, %1;\n\t"
+        "mov.b64 {lo, hi}, %1;\n\t"
+        "mad.lo.u32 hi, %4, %5, hi;\n\t"
+        "mov.b64 %1, {lo, hi}; }"
+        : "+l"(s.a), "+l"(s.b)
+        : "r"(x0), "r"(yl), "r"(x1), "r"(yh));
+}
+__device__ __forceinline__ void acc36_fold(Acc36& s) {
+    s.b += s.a >> 24;
+    s.a &= (1ull << 24) - 1;
+}
+__device__ __forceinline__ u128 acc36_value(const Acc36& s) { return ((u128)s.b << 24) + s.a; }
+__device__ __forceinline__ uint32_t split24_lo(u64 y) { return (uint32_t)y & ((1u << 24) - 1); }
+__device__ __forceinline__ uint32_t split24_hi(u64 y) { return (uint32_t)(y >> 24); }
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
     return reduce128((u128)a * b, m);
 }

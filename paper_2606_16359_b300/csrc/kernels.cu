@@ -59,7 +59,7 @@ __global__ void k_bconv(BConvTab t, const Modulus* mods, int L, int level, int l
 // words are read once for both, and with every modulus below 2^40 each
 // destination keeps two independent three-word sums (Acc40).  Needs 16-byte
 // aligned bases and even strides (checked by the launcher).
-template <int kS, bool kNarrow>
+template <int kS, bool kNarrow, bool kM36>
 __global__ void k_bconv2(BConvTab t, const Modulus* mods, int L, int level, int logN,
                          const u64* in, size_t in_stride, int in_pos_base, u64* out,
                          size_t out_stride, int copy_src) {
@@ -87,7 +87,23 @@ __global__ void k_bconv2(BConvTab t, const Modulus* mods, int L, int level, int 
         const u64* row = t.mat + d * kS;
         const u64 nb = t.negB[d];
         ulonglong2 r;
-        if constexpr (kNarrow) {
+        if constexpr (kM36) {  // every modulus below 2^36; at most 9 terms
+            Acc36 a0, a1;
+            acc36_zero(a0);
+            acc36_zero(a1);
+            const uint32_t nl = split24_lo(nb), nh = split24_hi(nb);
+            acc36_mad(a0, (u64)neg0, nl, nh);
+            acc36_mad(a1, (u64)neg1, nl, nh);
+#pragma unroll
+            for (int i = 0; i < kS; i++) {
+                const u64 w = row[i];
+                const uint32_t wl = split24_lo(w), wh = split24_hi(w);
+                acc36_mad(a0, y0[i], wl, wh);
+                acc36_mad(a1, y1[i], wl, wh);
+            }
+            r.x = reduce_narrow(acc36_value(a0), mods[mt]);
+            r.y = reduce_narrow(acc36_value(a1), mods[mt]);
+        } else if constexpr (kNarrow) {
             Acc40 a0, a1;
             acc40_zero(a0);
             acc40_zero(a1);
@@ -470,7 +486,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-template <int W, int HB>
+template <int W, int HB, bool kM36>
 __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* items, const MacTerm* terms,
                                                           const Modulus* mods, const int* mod_map, int nl,
                                                           int logN, int T, uint32_t* status) {
@@ -551,17 +567,21 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
     }
     // (coefficient 2 tid, 2 tid + 1) x (c0, c1 part); with 1-byte high planes
     // (every modulus below 2^40) the sums are kept as Acc40, else in 128 bits
+    // (every modulus below 2^36: Acc36, two widening and two 32-bit
+    // multiply-adds per product, folded every 16 terms)
     constexpr bool kSplit = HB == 1;
-    using Acc = typename std::conditional<kSplit, Acc40, u128>::type;
+    using Acc = typename std::conditional<kM36, Acc36, typename std::conditional<kSplit, Acc40, u128>::type>::type;
     Acc a0[W], a1[W], b0[W], b1[W];
     auto zero = [](Acc& a) {
-        if constexpr (kSplit) acc40_zero(a); else a = 0;
+        if constexpr (kM36) acc36_zero(a); else if constexpr (kSplit) acc40_zero(a); else a = 0;
     };
     auto mad = [](Acc& a, u64 x, u64 y) {
-        if constexpr (kSplit) acc40_mad(a, x, y); else a += (u128)x * y;
+        if constexpr (kM36) acc36_mad(a, x, split24_lo(y), split24_hi(y));
+        else if constexpr (kSplit) acc40_mad(a, x, y);
+        else a += (u128)x * y;
     };
     auto value = [](const Acc& a) -> u128 {
-        if constexpr (kSplit) return acc40_value(a); else return a;
+        if constexpr (kM36) return acc36_value(a); else if constexpr (kSplit) return acc40_value(a); else return a;
     };
 #pragma unroll
     for (int k = 0; k < W; k++) {
@@ -596,10 +616,18 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
                 hx = h.x, hy = h.y;
             }
             const u64 px = (u64)lo.x | (hx << 32), py = (u64)lo.y | (hy << 32);
-            mad(a0[k], x0.x, px);
-            mad(a1[k], x0.y, py);
-            mad(b0[k], x1.x, px);
-            mad(b1[k], x1.y, py);
+            if constexpr (kM36) {
+                const uint32_t lx = split24_lo(px), hx = split24_hi(px), ly = split24_lo(py), hy = split24_hi(py);
+                acc36_mad(a0[k], x0.x, lx, hx);
+                acc36_mad(a1[k], x0.y, ly, hy);
+                acc36_mad(b0[k], x1.x, lx, hx);
+                acc36_mad(b1[k], x1.y, ly, hy);
+            } else {
+                mad(a0[k], x0.x, px);
+                mad(a1[k], x0.y, py);
+                mad(b0[k], x1.x, px);
+                mad(b1[k], x1.y, py);
+            }
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);
@@ -607,6 +635,18 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
         // every modulus is below 2^48 (HB = 2), so 2^31 terms fit the 128-bit
         // sums; wider moduli (products below 2^120) fold every 16 terms.  A fold
         // replaces a sum by its residue, which leaves the final residue unchanged.
+        if constexpr (kM36) {
+            if ((t & 15) == 15) {
+#pragma unroll
+                for (int k = 0; k < W; k++) {
+                    if (k >= n_out) break;
+                    acc36_fold(a0[k]);
+                    acc36_fold(a1[k]);
+                    acc36_fold(b0[k]);
+                    acc36_fold(b1[k]);
+                }
+            }
+        }
         if ((kSplit && (t & 0x3FFF) == 0x3FFF) || (HB == 4 && (t & 15) == 15)) {
             auto fold = [&](Acc& a) {
                 const u64 r = reduce128(value(a), m);
@@ -798,12 +838,15 @@ void launch_bconv(fe_ctx* c, const BConvTab& t, int level, const u64* in, size_t
     const dim3 g = pair ? grid_for(c->N / 2, n_poly) : grid_for(c->N, n_poly);
 #define FE_BCONV(S)                                                                                   \
     case S:                                                                                           \
-        if (pair && c->narrow)                                                                        \
-            k_bconv2<S, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,     \
-                                                in_pos_base, out, out_stride, cs);                    \
+        if (pair && c->narrow && c->max_mod_bits <= 36)                                               \
+            k_bconv2<S, true, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride, \
+                                                      in_pos_base, out, out_stride, cs);              \
+        else if (pair && c->narrow)                                                                   \
+            k_bconv2<S, true, false><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in,         \
+                                                       in_stride, in_pos_base, out, out_stride, cs);  \
         else if (pair)                                                                                \
-            k_bconv2<S, false><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,    \
-                                                 in_pos_base, out, out_stride, cs);                   \
+            k_bconv2<S, false, false><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in,        \
+                                                        in_stride, in_pos_base, out, out_stride, cs); \
         else if (c->narrow)                                                                           \
             k_bconv<S, true><<<g, kB, 0, st>>>(t, c->d_mod, c->L, level, c->logN, in, in_stride,      \
                                                in_pos_base, out, out_stride, cs);                     \
@@ -908,12 +951,14 @@ void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, in
     c->cnt.launches++;
 }
 
-template <int W, int HB>
+template <int W, int HB, bool kM36>
 static void mac_launch(dim3 g, int threads, size_t smem, cudaStream_t st, const MacItem* items, const MacTerm* terms,
                        const Modulus* mods, const int* mm, int nl, int logN, int T, uint32_t* status) {
     static bool set = false;
-    if (!set) set = cudaFuncSetAttribute(k_mac<W, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-    k_mac<W, HB><<<g, threads, smem, st>>>(items, terms, mods, mm, nl, logN, T, status);
+    if (!set)
+        set = cudaFuncSetAttribute(k_mac<W, HB, kM36>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+              cudaSuccess;
+    k_mac<W, HB, kM36><<<g, threads, smem, st>>>(items, terms, mods, mm, nl, logN, T, status);
 }
 
 void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
@@ -931,8 +976,13 @@ void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_ite
     const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
     const size_t smem = 256 + (size_t)kMacStageBytes;
     const int* mm = nl == level + 1 ? nullptr : c->lv[level].d_ks_limbs;
-#define FE_MAC(W, HB) mac_launch<W, HB>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
-    if (c->pt_hb == 1) {
+#define FE_MAC(W, HB) mac_launch<W, HB, false>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
+#define FE_MAC36(W) mac_launch<W, 1, true>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
+    if (c->pt_hb == 1 && c->max_mod_bits <= 36) {
+        if (w == 1) FE_MAC36(1);
+        else if (w == 2) FE_MAC36(2);
+        else FE_MAC36(4);
+    } else if (c->pt_hb == 1) {
         if (w == 1) FE_MAC(1, 1);
         else if (w == 2) FE_MAC(2, 1);
         else FE_MAC(4, 1);
@@ -946,6 +996,7 @@ void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_ite
         else FE_MAC(4, 4);
     }
 #undef FE_MAC
+#undef FE_MAC36
     c->cnt.launches++;
 }
 

@@ -530,20 +530,21 @@ def test_per_operation_path(tiny, n1):
     assert g.device_status() == 0
 
 
-@pytest.fixture(scope="module")
-def narrow():
-    """Every modulus in [2^26, 2^40): the MAC keeps its sums in three 32-bit
-    words (Acc40); base conversion and the key inner product use the narrow
-    reduction."""
-    return Pair(10, 3, 1, 30, 36)
+@pytest.fixture(scope="module", params=[36, 40])
+def narrow(request):
+    """Every modulus in [2^26, 2^40) (narrow reductions).  With a 36-bit special
+    prime every modulus is below 2^36: the MAC and base conversion split their
+    products at bit 24 (Acc36); with a 40-bit one the MAC keeps three 32-bit
+    words (Acc40)."""
+    return Pair(10, 3, 1, 30, request.param)
 
 
 @pytest.mark.parametrize("dh", [False, 2])
 def test_split_sums_below_2_40_bit_exact(narrow, dh):
-    """With every modulus below 2^40 the MAC uses the three-word sums and the
-    key-switching kernels the narrow reduction; depthwise and pointwise (BSGS)
-    layers give the oracle's residues in both paths, and MAC items of 1, 2 and
-    4 outputs agree."""
+    """With every modulus below 2^40 the MAC and base conversion use split sums
+    (Acc36 below 2^36, Acc40 up to 2^40) and the key inner product the narrow
+    reduction; depthwise and pointwise (BSGS) layers give the oracle's residues
+    in both paths, and MAC items of 1, 2 and 4 outputs agree."""
     rng = np.random.default_rng(40 + int(dh))
     x = rng.uniform(0, 1, (1, 12, 6, 6))
     run_conv_pair(narrow, x, rng.normal(0, 1 / 3, (12, 1, 3, 3)), 1, depthwise=True, double_hoist=dh)
