@@ -121,3 +121,61 @@ def test_executed_inner_rotation_counts():
         assert counts.executed_inner(1, K, 1) == K * K - 1
     # K <= S: edge rotations only; S=4, K=3 executes 1.25 per ciphertext on average
     assert counts.executed_inner(4, 3, 1) / 16 == 1.25
+
+
+def _edge_fragments(S):
+    """Brute-force count of the fragments of an S x S fragment grid that lie on
+    its border (first or last fragment row or column)."""
+    return sum(1 for u in range(S) for v in range(S) if u in (0, S - 1) or v in (0, S - 1))
+
+
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 8, 16])
+def test_eq3_case2_is_the_border_of_the_fragment_grid(S):
+    """Eq. 3, case K <= S < M (Sec. 4.2, inner-rotation complexity): only the
+    edge computations rotate, up to 4(S - 1) rotations per S x S set of fragment
+    ciphertexts.  With N_in / alpha = S^2 ciphertexts (one full fragment set),
+    the per-layer value must equal the enumerated border fragments."""
+    alpha_ = 2.0
+    n_in = alpha_ * S * S
+    assert counts.inner_eq3_case2(n_in, S, alpha_) == pytest.approx(_edge_fragments(S))
+    # linear in the ciphertext count N_in / alpha
+    assert counts.inner_eq3_case2(3 * n_in, S, alpha_) == pytest.approx(3 * _edge_fragments(S))
+
+
+def test_eq6_equals_eq3_per_regime_and_falls_with_S():
+    """Eq. 6 (Sec. 4.2, large batch): with no outer rotations left, the cost is
+    the inner-rotation cost of Eq. 3 alone, in both regimes, and it does not
+    grow as S grows from 2 on (the statement after Eq. 6; at S = 1 the case
+    K <= S is the 1x1 kernel, which needs no rotation at all).  Its S < K regime at S = 1 is
+    the (K^2 - 1) rotations per ciphertext that the enumerated inner offsets
+    give (every tap but the centre needs its own rotation)."""
+    for K in (1, 2, 3, 5, 7):
+        for n_in, a in ((16, 1.0), (64, 4.0), (512, 8.0)):
+            prev = None
+            for S in (1, 2, 4, 8, 16, 32):
+                v = counts.amortized_eq6(n_in, K, S, a)
+                if S < K:
+                    assert v == counts.inner_eq3(n_in, K, S, a)
+                else:
+                    assert v == counts.inner_eq3_case2(n_in, S, a)
+                # non-increasing from S = 2 on, and from S = 1 whenever K > 1
+                if prev is not None and (S > 2 or K > 1):
+                    assert v <= prev + 1e-12
+                prev = v
+            if K > 1:
+                # S = 1: one ciphertext per channel block, K^2 - 1 executed rotations each
+                per_ct = counts.executed_inner(1, K, 1)
+                assert counts.amortized_eq6(n_in, K, 1, a) == per_ct * n_in / a
+
+
+def test_eq5_printed_first_case_is_eq3_case2_plus_eq4():
+    """The first case of Eq. 5 as printed, (BS/alpha)(4(S-1)/S^2 N_in +
+    (alpha S^2/BS - 1) N_out), is BS times Eq. 3 case 2 plus Eq. 4, and both
+    cases of Eq. 5 reduce to the Table 6 total (inner term 0 for K <= S)
+    minus or plus exactly that edge term."""
+    for (ni, no, K, BS, H, S) in [(64, 64, 3, 4, 32, 4), (128, 32, 3, 8, 32, 8), (32, 128, 3, 8, 32, 4)]:
+        a = counts.alpha(2 ** 15, H)
+        printed = (BS / a) * (4 * (S - 1) / (S * S) * ni + (a * S * S / BS - 1) * no)
+        assert printed == pytest.approx(BS * counts.inner_eq3_case2(ni, S, a) + counts.outer_eq4(no, S, BS, a))
+        assert printed - counts.total_eq5(ni, no, K, S, BS, a) == pytest.approx(
+            BS * counts.inner_eq3_case2(ni, S, a))
