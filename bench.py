@@ -58,10 +58,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="fenc_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -97,6 +98,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -194,42 +199,131 @@ def butterfly_roof(ctx, torch):
     return best
 
 
-def cpu_oracle_keyswitch(n_rot, level=22):
-    """The CPU oracle (as it stands, single-threaded) on a bounded sample: n_rot
-    rotations of one ciphertext at `level` of the same parameter set."""
+_ORACLE = {}
+
+
+def _oracle_setup(level=22):
+    """Per-process oracle state: the parameter set, one rotation key and a random
+    ciphertext at `level` (the level of the pointwise layers)."""
     from oracle import ckks
     pr = ckks.Params(PARAMS["logN"], PARAMS["n_q"], PARAMS["k"], PARAMS["qbits"], PARAMS["pbits"])
     keys = ckks.KeySet(pr, 1, rot_steps=[1])
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(os.getpid())
     c = ckks.Ciphertext(np.stack([rng.integers(0, pr.moduli[i], pr.N, dtype=np.uint64) for i in range(level + 1)]),
                         np.stack([rng.integers(0, pr.moduli[i], pr.N, dtype=np.uint64) for i in range(level + 1)]),
                         level, 1.0)
-    ext = ckks.mod_up(pr, c.c1, level)  # warm caches (permutation tables)
+    _ORACLE.update(ckks=ckks, pr=pr, keys=keys, c=c)
+
+
+def _oracle_rotations(n_rot):
+    """n_rot oracle rotations (key switches) in this process; returns seconds."""
+    if not _ORACLE:
+        _oracle_setup()
+    o = _ORACLE
     t0 = time.perf_counter()
     for _ in range(n_rot):
-        ckks.rotate(pr, keys, c, 1)
-    dt = time.perf_counter() - t0
-    del ext
+        o["ckks"].rotate(o["pr"], o["keys"], o["c"], 1)
+    return time.perf_counter() - t0
+
+
+def host_cpu():
+    """(usable host cores, CPU model)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return n, model
+
+
+class OraclePool:
+    """The CPU oracle as it stands, run in `workers` single-threaded processes
+    (spawned, so they share no state with a CUDA context of the parent); each
+    process holds its own parameter set, key and ciphertext."""
+
+    def __init__(self, workers):
+        import multiprocessing as mp
+        self.workers = workers
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_setup)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, n_rot_each):
+        """Every process runs n_rot_each rotations; returns (rotations, wall seconds)."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_rotations, [n_rot_each] * self.workers, chunksize=1)
+        return n_rot_each * self.workers, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_keyswitch(n_rot):
+    """The CPU oracle (as it stands, single-threaded, in this process) on a
+    bounded sample: n_rot rotations of one ciphertext at level 22 of the same
+    parameter set (set-up and a first rotation untimed)."""
+    _oracle_setup()
+    _oracle_rotations(1)
+    dt = _oracle_rotations(n_rot)
     return n_rot / dt, dt
+
+
+def cpu_oracle_all_cores(n_rot_each, max_workers=64):
+    """The same oracle rotation on every usable host core (one process each, at
+    most max_workers, about 0.5 GB of host memory apiece)."""
+    cores, model = host_cpu()
+    workers = max(1, min(cores, max_workers))
+    pool = OraclePool(workers)
+    try:
+        pool.run(1)  # set-up and one warm rotation per process
+        n, dt = pool.run(n_rot_each)
+    finally:
+        pool.close()
+    return n / dt, dt, workers, cores, model
 
 
 def run_reference(args):
     dist, rank, world, local = dist_setup(args)
     if rank != 0:
         return 0
+    cores, model = host_cpu()
+    workers = max(1, min(cores, 64))
+    pool = OraclePool(workers)
     per_step = []
-    for i in range(args.warmup + args.steps):
-        v, dt = cpu_oracle_keyswitch(1)
-        if i >= args.warmup:
-            per_step.append(dt)
+    try:
+        for i in range(args.warmup + args.steps):
+            n, dt = pool.run(1)
+            if i >= args.warmup:
+                per_step.append(dt)
+    finally:
+        pool.close()
     total = sum(per_step)
-    value = args.steps / total
+    value = args.steps * workers / total
+    sample = (f"each step: one oracle rotation of a level-22 ciphertext (N=2^16, 6 digits) in each of {workers} "
+              f"single-threaded processes, one per host core ({cores} usable, {model})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one CPU-oracle rotation (key switch) at level 22"},
-            "cpu_baseline": {"value": value, "unit": "keyswitch/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} rotations of one ciphertext at level 22, N=2^16"},
+            "config": {"workload": WORKLOAD, "step": f"{workers} CPU-oracle rotations (key switches) at level 22, "
+                                                     f"one per process"},
+            "cpu_baseline": {"value": value, "unit": "keyswitch/s", "cores": workers, "kind": "oracle",
+                             "sample": sample, "cpu_model": model},
             "e2e": {"value": value, "unit": "keyswitch/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -250,6 +344,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="independent encrypted inputs per block per step")
     ap.add_argument("--schedule", default="tuned",
                     help="outer rotations of the pointwise layers: tuned (autotuner), linear, or n1")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="also time the one-graph form and 4 and 16 inputs per block (context fields)")
     ap.add_argument("--ncu-step", action="store_true",
                     help="set up, run one warm step, then one batched step between cudaProfilerStart and "
                          "cudaProfilerStop (for ncu --profile-from-start off), and exit")
@@ -388,13 +484,14 @@ def run_ours(args, dist, rank, world, local):
         roofline["traffic"] = tpl * limb_passes / n_dom if tpl else None
         roofline["traffic_unit"] = "bytes per launch (ncu dram read + write; algorithmic: %.0f)" % (b_dom / n_dom)
         issue_peak, n_sm, mhz = butterfly_issue_roof(torch)
-        roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": issue_peak, "unit": "Gbutterfly/s",
-                         "frac": bfly_rate / issue_peak,
-                         "peak_source": "issue limit: %d SMs x 4 warp instructions per clock x %.0f MHz x 32 lanes"
-                                        " / %.1f warp instructions per butterfly" % (n_sm, mhz,
-                                                                                     BUTTERFLY_WARP_INSTRUCTIONS),
-                         "probe_peak": bfly_peak, "frac_of_probe": bfly_rate / bfly_peak,
-                         "probe_source": "butterfly probe, this run (register-resident, one full wave)",
+        roofline.update({"bound": "alu", "achieved": bfly_rate, "peak": bfly_peak, "unit": "Gbutterfly/s",
+                         "frac": bfly_rate / bfly_peak,
+                         "peak_source": "measured in this run: the butterfly probe (the transform's own lazy Shoup "
+                                        "butterflies on register-resident residues, one full wave of CTAs)",
+                         "issue_limit_context": issue_peak,
+                         "issue_limit_source": "derived, context only: %d SMs x 4 warp instructions per clock x "
+                                               "%.0f MHz x 32 lanes / %.1f warp instructions per butterfly"
+                                               % (n_sm, mhz, BUTTERFLY_WARP_INSTRUCTIONS),
                          "hbm_GBps": achieved, "hbm_peak_GBps": peak, "hbm_frac": achieved / peak,
                          "hbm_peak_source": peak_kind})
 
@@ -451,12 +548,69 @@ def run_ours(args, dist, rank, world, local):
     cnt = ctx.counters()
     launches_step = cnt["launches"]
 
+    config = {"workload": WORKLOAD, "blocks": net.blocks, "inputs_per_block": net.batch,
+              "ms_per_input": ms_step / net.batch, "keyswitches_per_step": ks_per_step,
+              "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
+              "schedule": net.schedule, "tune_ms": net.tune_ms,
+              "path": (("one graph, one stream" if args.one_stream else
+                        f"graph per block x{len(net.graphs)} streams") if use_graph else "batched"),
+              "e2e_path": ("fe_graph_launch_host per graph (host copies in, replay, host copies out)"
+                           if use_graph else "torch copies around the batched layers"),
+              "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
+              "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,
+              "per_op_library_ms_per_step": per_op_ms, "speedup_vs_per_op_library": per_op_ms / ms_step,
+              "max_abs_err_vs_fp64": max(errs), "setup_s": round(t_setup, 1),
+              "l2": "inputs (keys, plaintexts) far larger than L2; no flush",
+              "parallelism": f"replicas x{world}"}
+
+    # ---- variants (context for the headline, not separate bench lines): the whole
+    # step as one graph on one stream, and B independent inputs per block ----
+    variants = {}
+    if use_graph and args.variants:
+        def timed(net_, concurrent, steps):
+            net_.capture(concurrent=concurrent)
+            for _ in range(3):
+                net_.launch(join=not concurrent)
+            net_.join()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                net_.launch(join=not concurrent)
+            net_.join()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if ctx.device_status():
+                raise RuntimeError("a bounded device wait expired in a variant")
+            t = a.elapsed_time(b) / steps
+            return {"ms_per_step": round(t, 3), "keyswitches_per_step": net_.keyswitches_per_step,
+                    "keyswitch_per_s": net_.keyswitches_per_step / (t / 1e3),
+                    "ms_per_input": round(t / net_.batch, 3), "steps": steps, "warmup": 3}
+        if not args.one_stream:
+            variants["one_graph_one_stream"] = timed(net, False, args.steps)
+        schedule = net.schedule
+        del net
+        torch.cuda.empty_cache()
+        for B in (4, 16):
+            if B == args.batch:
+                continue
+            nb = MobileNetBlocks(ctx, delta=DELTA, schedule=schedule, batch=B)
+            variants[f"batch_{B}"] = timed(nb, True, max(3, min(args.steps, 5)))
+            del nb
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and args.cpu_rotations > 0:
-        v, dt = cpu_oracle_keyswitch(args.cpu_rotations)
-        cpu = {"value": v, "unit": "keyswitch/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_rotations} oracle rotations of one ciphertext at level 22 (pw layer level), "
-                         f"N=2^16, 6 digits, {dt:.1f} s single-threaded"}
+        v1, dt1 = cpu_oracle_keyswitch(args.cpu_rotations)
+        va, dta, workers, cores, model = cpu_oracle_all_cores(max(1, args.cpu_rotations // 2))
+        cpu = {"value": va, "unit": "keyswitch/s", "cores": workers, "kind": "oracle",
+               "sample": f"{max(1, args.cpu_rotations // 2)} oracle rotations of a level-22 ciphertext (the pointwise "
+                         f"layers' level; N=2^16, 6 digits) in each of {workers} single-threaded processes, "
+                         f"{dta:.1f} s wall",
+               "cpu_model": model, "host_cores": cores,
+               "single_thread": {"value": v1, "unit": "keyswitch/s", "cores": 1,
+                                 "sample": f"{args.cpu_rotations} oracle rotations of one level-22 ciphertext, "
+                                           f"{dt1:.1f} s"}}
 
     if rank == 0:
         clocks = clk.summary()
@@ -464,18 +618,7 @@ def run_ours(args, dist, rank, world, local):
             "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "blocks": net.blocks, "inputs_per_block": net.batch,
-                       "ms_per_input": ms_step / net.batch, "keyswitches_per_step": ks_per_step,
-                       "pmults_per_step": net.pmults_per_step, "rotation_keys": net.n_keys,
-                       "schedule": net.schedule, "tune_ms": net.tune_ms,
-                       "path": ("graph" if args.one_stream else f"graph per block x{len(net.graphs)} streams")
-                       if use_graph else "batched",
-                       "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
-                       "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,
-                       "per_op_library_ms_per_step": per_op_ms, "speedup_vs_per_op_library": per_op_ms / ms_step,
-                       "max_abs_err_vs_fp64": max(errs), "setup_s": round(t_setup, 1),
-                       "l2": "inputs (keys, plaintexts) far larger than L2; no flush",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(config, variants=variants),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "keyswitch/s", "h2d_bytes_per_step": h2d,

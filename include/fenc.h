@@ -263,8 +263,12 @@ int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct,
 int fe_rescale(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
                void* stream);
 /* Rescale without allocating: same result as fe_rescale, but the scratch comes
- * from one fixed 32 MiB array of device memory that the library holds on every
- * GPU it is loaded on, so the call never allocates or frees device memory.  For
+ * from one fixed 32 MiB array of device memory (a static device variable of the
+ * library), so the call never allocates or frees device memory.  The array is
+ * reserved on a device when the library's module holding it loads there: under
+ * CUDA's lazy module loading (the default) that is the first fe_rescale_noalloc
+ * call on that device, so a caller planning a fixed footprint should make one
+ * call at start-up; the 32 MiB then stay reserved until the process exits.  For
  * callers that cannot allocate: a serving process whose device footprint is
  * fixed after start-up, a host framework that owns all device memory through its
  * own pool, or latency-critical code that cannot afford an allocation's possible
@@ -272,9 +276,9 @@ int fe_rescale(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level, v
  *  - Size limit: 16 (n_ct N + n_ct level N) bytes of scratch must fit in 32 MiB
  *    (e.g. one ciphertext at N = 2^16 and level 23); larger requests fail with
  *    FE_ENOMEM and a message, before any launch.
- *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any stream
- *    capture on the device.
+ *  - The current device must be the context's device (else FE_EINVAL).  The
+ *    first call on a device looks up the array's device address (once per
+ *    device); make that first call before any stream capture on the device.
  *  - Every call uses the same array.  Nothing in it needs to start at zero, and
  *    it keeps the last call's contents.  Calls whose work overlaps on the GPU
  *    (different streams, or host threads without ordering) race on the array;
@@ -470,6 +474,20 @@ int fe_graph_capture_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const*
                            void* const* outs_host, uint32_t n, uint32_t n_req, void* workspace_dev,
                            size_t workspace_bytes, void* stream, fe_graph** out);
 int fe_graph_launch(fe_graph* graph, void* stream);
+/* The captured sequence's host-visible ends: its external inputs (layer inputs
+ * that no earlier layer of the graph writes) and final outputs (layer outputs
+ * that no later layer reads), each counted once, in layer order, with their
+ * sizes in bytes (n_req x ciphertexts x [2][level+1][N] uint64).  in_bytes /
+ * out_bytes may be NULL (counts only); otherwise they have room for the counts.
+ * Errors: FE_EINVAL. */
+int fe_graph_io(const fe_graph* graph, uint32_t* n_in, size_t* in_bytes, uint32_t* n_out, size_t* out_bytes);
+/* One end-to-end step of a captured graph through host memory: on `stream`,
+ * copy in_host[i] (fe_graph_io's in_bytes[i] bytes) into external input i,
+ * replay the graph, and copy final output j into out_host[j].  Enqueued only:
+ * the host buffers must stay valid until the stream reaches the copies (page-
+ * locked buffers make the copies asynchronous; pageable ones are staged by the
+ * driver).  The caller owns the host buffers.  Errors: FE_EINVAL, FE_ECUDA. */
+int fe_graph_launch_host(fe_graph* graph, const void* const* in_host, void* const* out_host, void* stream);
 void fe_graph_destroy(fe_graph* graph);
 
 /* ---- latency model (learned fragment / schedule proposer) ------------------- */
@@ -577,6 +595,18 @@ int fe_server_stats(fe_server* s, fe_server_stats_t* out);
 void fe_server_destroy(fe_server* s);
 
 /* ---- device status ------------------------------------------------------------ */
+
+/* Bounded waits of the PMult-MAC kernel (its mbarrier waits on the bulk copies
+ * that stage its operands, and on the consumers that free a stage): limit_ns is
+ * the longest a thread waits (default 2 s) before it sets bit 0 of the status
+ * word (fe_device_status) and stops.  unfed_term >= 0 exists to test that expiry
+ * path: every MAC item then announces the bytes of its term `unfed_term` but
+ * issues no copy for it, so that stage never fills, its consumers give up after
+ * limit_ns, and the launch's results are invalid; -1 (the default) turns it
+ * off.  Applies to launches (and graph captures) made after the call.  No
+ * counterpart in the paper.  Errors: FE_EINVAL (limit 0 or above 60 s,
+ * unfed_term below -1). */
+int fe_ctx_set_mac_wait(fe_ctx* ctx, uint64_t limit_ns, int32_t unfed_term);
 
 /* Synchronise the device and read the context's device status word: bit 0 is
  * set when a kernel's bounded wait on its own asynchronous copies expired (the

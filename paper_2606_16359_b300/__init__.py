@@ -100,6 +100,7 @@ SIGNATURES = {
     "fe_he_layer_timing": (cint, [vp, vp, vp, vp, u32, vp, vp, vp, sz, vp]),
     "fe_plan_truncate": (cint, [vp, u32]),
     "fe_device_status": (cint, [vp, P(u32), cint]),
+    "fe_ctx_set_mac_wait": (cint, [vp, u64, i32]),
     "fe_plan_set_mac_ways": (cint, [vp, u32]),
     "fe_plan_set_hoisting": (cint, [vp, cint]),
     "fe_server_create": (cint, [P(FeServerConfig), P(vp)]),
@@ -157,6 +158,8 @@ SIGNATURES = {
     "fe_graph_capture_batch": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, u32, vp, sz, vp, P(vp)]),
     "fe_graph_workspace_bytes": (sz, [P(vp), u32, u32]),
     "fe_graph_launch": (cint, [vp, vp]),
+    "fe_graph_io": (cint, [vp, P(u32), P(sz), P(u32), P(sz)]),
+    "fe_graph_launch_host": (cint, [vp, P(vp), P(vp), vp]),
     "fe_graph_destroy": (None, [vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
     "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
@@ -256,6 +259,25 @@ class Graph:
 
     def launch(self):
         check(load().fe_graph_launch(self.handle, _stream()))
+
+    def io(self):
+        """(input byte sizes, output byte sizes) of the graph's host-visible ends."""
+        ni, no = u32(0), u32(0)
+        check(load().fe_graph_io(self.handle, ctypes.byref(ni), None, ctypes.byref(no), None))
+        ib, ob = (sz * max(1, ni.value))(), (sz * max(1, no.value))()
+        check(load().fe_graph_io(self.handle, ctypes.byref(ni), ib, ctypes.byref(no), ob))
+        return list(ib)[:ni.value], list(ob)[:no.value]
+
+    def launch_host(self, in_host, out_host):
+        """One step through host memory (copies in, replay, copies out) on the current stream.
+        in_host / out_host: host tensors (pinned for asynchronous copies) of io()'s sizes."""
+        ib, ob = self.io()
+        assert len(in_host) == len(ib) and len(out_host) == len(ob)
+        for t, b in zip(list(in_host) + list(out_host), ib + ob):
+            assert not t.is_cuda and t.numel() * t.element_size() == b
+        ins = (vp * max(1, len(ib)))(*[t.data_ptr() for t in in_host])
+        outs = (vp * max(1, len(ob)))(*[t.data_ptr() for t in out_host])
+        check(load().fe_graph_launch_host(self.handle, ins, outs, _stream()))
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -472,6 +494,9 @@ class Context:
         v = u32(0)
         check(load().fe_device_status(self.handle, ctypes.byref(v), 1 if reset else 0))
         return v.value
+
+    def set_mac_wait(self, limit_ns=2_000_000_000, unfed_term=-1):
+        check(load().fe_ctx_set_mac_wait(self.handle, int(limit_ns), int(unfed_term)))
 
     def plan_set_hoisting(self, plan, double):
         """Hoisting of the plan's rotations (set before load_weights): False / 0

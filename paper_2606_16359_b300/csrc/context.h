@@ -99,6 +99,11 @@ struct fe_ctx {
     fe_profiler prof;
     cudaDeviceProp prop;
     int n_sm;
+    int device;  // CUDA device the context was created on (its tables live there)
+    // bounded waits of the PMult-MAC's mbarriers: the limit, and (for tests of the
+    // expiry path only; -1 otherwise) a term whose copies the producer never issues
+    uint64_t mac_wait_ns = 2000000000ull;
+    int mac_unfed_term = -1;
 
     int slot_count() const { return N / 2; }
     size_t limb_bytes() const { return (size_t)N * sizeof(u64); }

@@ -429,9 +429,14 @@ __global__ void k_autosum(const SumItem* items, const SumEntry* entries, u64* ou
 // by the producer, complete_tx by the copies).  Each consumer warp arrives on
 // the stage's "empty" mbarrier when it has read the stage; the producer waits
 // for that before refilling it, so consumers never wait on one another.  Every
-// wait is bounded (2 s of %globaltimer): on expiry the thread sets bit 0 of
-// *status and stops; the producer then waits (bounded) for the copies it
-// issued that were never consumed, and nothing is written.
+// wait is bounded (`limit` ns of %globaltimer, 2 s unless fe_ctx_set_mac_wait
+// changed it): on expiry the thread sets bit 0 of *status and stops without
+// writing its outputs.  Before it exits, the producer waits (bounded) until the
+// copies of the last S terms it issued have landed, on the normal path as on
+// expiry, so no copy is still writing into the CTA's shared memory when it
+// ends.  unfed_term >= 0 (tests of the expiry path only) makes the producer
+// announce that term's bytes without issuing its copies: its stage never fills
+// and the consumers' wait runs out.
 constexpr int kMacTile = 512;
 constexpr int kMacStageBytes = 98304;  // shared memory for the stages of one CTA
 
@@ -489,7 +494,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 template <int W, int HB, bool kM36>
 __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* items, const MacTerm* terms,
                                                           const Modulus* mods, const int* mod_map, int nl,
-                                                          int logN, int T, uint32_t* status) {
+                                                          int logN, int T, uint32_t* status, uint64_t limit,
+                                                          int unfed_term) {
     constexpr int S = mac_stages<W, HB>();
     extern __shared__ __align__(128) unsigned char mac_smem[];
     uint64_t* full = (uint64_t*)mac_smem;  // [S]
@@ -510,7 +516,6 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
     // (4 + HB) T contiguous bytes
     const size_t pt_off = ((size_t)i << logN) * (4 + HB) + base * (4 + HB);
     const uint32_t ct_tile = (uint32_t)T * 8u, lo_tile = (uint32_t)T * 4u, hi_tile = (uint32_t)T * HB;
-    const uint64_t limit = 2000000000ull;
     const int tid = threadIdx.x;
     const int n_cons = T / 2;                  // consumer threads
     const int n_cons_warps = (n_cons + 31) / 32;
@@ -548,21 +553,24 @@ __global__ void __launch_bounds__(kMacTile / 2 + 32, 2) k_mac(const MacItem* ite
             }
             unsigned char* st = stage0 + (size_t)s * stage_stride;
             mbar_expect_tx(&full[s], stage_bytes);
-            bulk_g2s(st, ct + off0, ct_tile, &full[s]);
-            bulk_g2s(st + ct_tile, ct + off1, ct_tile, &full[s]);
+            if (issued != unfed_term) {  // an unfed term (expiry tests only) never fills its stage
+                bulk_g2s(st, ct + off0, ct_tile, &full[s]);
+                bulk_g2s(st + ct_tile, ct + off1, ct_tile, &full[s]);
 #pragma unroll
-            for (int k = 0; k < W; k++)
-                if (k < n_out)
-                    bulk_g2s(st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile), pt[k] + pt_off, lo_tile + hi_tile,
-                             &full[s]);
+                for (int k = 0; k < W; k++)
+                    if (k < n_out)
+                        bulk_g2s(st + 2 * ct_tile + (size_t)k * (lo_tile + hi_tile), pt[k] + pt_off,
+                                 lo_tile + hi_tile, &full[s]);
+            }
             if (issued + 1 < n_terms) load_pointers(issued + 1);
         }
-        if (!ok) {
-            atomicOr(status, 1u);
-            // the copies of the last S issued terms may still be in flight: wait (bounded)
-            for (int t = issued - S < 0 ? 0 : issued - S; t < issued; t++)
-                mbar_wait(&full[t % S], (uint32_t)((t / S) & 1), limit);
-        }
+        if (!ok) atomicOr(status, 1u);
+        // Before this thread exits, the copies of the last S issued terms must have
+        // landed: consumers that gave up early no longer keep the CTA (and its
+        // shared memory) alive.  On the normal path these phases complete as the
+        // copies arrive, independently of the consumers.  Bounded like every wait.
+        for (int t = issued - S < 0 ? 0 : issued - S; t < issued; t++)
+            if (t != unfed_term && !mbar_wait(&full[t % S], (uint32_t)((t / S) & 1), limit)) atomicOr(status, 1u);
         return;
     }
     // (coefficient 2 tid, 2 tid + 1) x (c0, c1 part); with 1-byte high planes
@@ -953,12 +961,13 @@ void launch_autosum(fe_ctx* c, const SumItem* items, const SumEntry* entries, in
 
 template <int W, int HB, bool kM36>
 static void mac_launch(dim3 g, int threads, size_t smem, cudaStream_t st, const MacItem* items, const MacTerm* terms,
-                       const Modulus* mods, const int* mm, int nl, int logN, int T, uint32_t* status) {
+                       const Modulus* mods, const int* mm, int nl, int logN, int T, uint32_t* status,
+                       uint64_t limit, int unfed_term) {
     static bool set = false;
     if (!set)
         set = cudaFuncSetAttribute(k_mac<W, HB, kM36>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
               cudaSuccess;
-    k_mac<W, HB, kM36><<<g, threads, smem, st>>>(items, terms, mods, mm, nl, logN, T, status);
+    k_mac<W, HB, kM36><<<g, threads, smem, st>>>(items, terms, mods, mm, nl, logN, T, status, limit, unfed_term);
 }
 
 void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_items, int n_ct_terms,
@@ -976,8 +985,12 @@ void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_ite
     const int w = ways <= 1 ? 1 : (ways == 2 ? 2 : 4);
     const size_t smem = 256 + (size_t)kMacStageBytes;
     const int* mm = nl == level + 1 ? nullptr : c->lv[level].d_ks_limbs;
-#define FE_MAC(W, HB) mac_launch<W, HB, false>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
-#define FE_MAC36(W) mac_launch<W, 1, true>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status)
+#define FE_MAC(W, HB)                                                                                    \
+    mac_launch<W, HB, false>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status, \
+                             c->mac_wait_ns, c->mac_unfed_term)
+#define FE_MAC36(W)                                                                                    \
+    mac_launch<W, 1, true>(g, threads, smem, st, items, terms, c->d_mod, mm, nl, c->logN, T, c->d_status, \
+                           c->mac_wait_ns, c->mac_unfed_term)
     if (c->pt_hb == 1 && c->max_mod_bits <= 36) {
         if (w == 1) FE_MAC36(1);
         else if (w == 2) FE_MAC36(2);

@@ -10,6 +10,13 @@
 struct fe_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    // the captured sequence's external inputs (layer inputs no earlier layer writes)
+    // and final outputs (layer outputs no later layer reads), in layer order
+    struct Io {
+        void* dev;
+        size_t bytes;
+    };
+    std::vector<Io> in, out;
 };
 
 namespace fe {
@@ -268,6 +275,21 @@ extern "C" int fe_graph_capture_batch(fe_ctx* c, const fe_evk* evk, const fe_pla
     if (e != cudaSuccess) return fail(FE_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
     g->graph = graph;
     FE_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
+    for (uint32_t i = 0; i < n; i++) {
+        const fe_plan* p = plans[i];
+        bool external = true;
+        for (uint32_t j = 0; j < i; j++) external = external && outs[j] != ins[i];
+        bool dup = false;
+        for (const auto& e : g->in) dup = dup || e.dev == ins[i];
+        if (external && !dup)
+            g->in.push_back({const_cast<void*>(ins[i]), (size_t)n_req * p->n_in * 2 * (p->level + 1) * c->limb_bytes()});
+    }
+    for (uint32_t j = 0; j < n; j++) {
+        bool read_later = false;
+        for (uint32_t i = j + 1; i < n; i++) read_later = read_later || ins[i] == outs[j];
+        if (!read_later)
+            g->out.push_back({outs[j], (size_t)n_req * plans[j]->n_out * 2 * plans[j]->level * c->limb_bytes()});
+    }
     *out = g.release();
     return FE_OK;
 }
@@ -281,6 +303,33 @@ extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* con
 extern "C" int fe_graph_launch(fe_graph* g, void* stream) {
     if (!g) return fail(FE_EINVAL, "null argument");
     FE_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return FE_OK;
+}
+
+extern "C" int fe_graph_io(const fe_graph* g, uint32_t* n_in, size_t* in_bytes, uint32_t* n_out,
+                           size_t* out_bytes) {
+    if (!g || !n_in || !n_out) return fail(FE_EINVAL, "null argument");
+    if (in_bytes)
+        for (size_t i = 0; i < g->in.size(); i++) in_bytes[i] = g->in[i].bytes;
+    if (out_bytes)
+        for (size_t i = 0; i < g->out.size(); i++) out_bytes[i] = g->out[i].bytes;
+    *n_in = (uint32_t)g->in.size();
+    *n_out = (uint32_t)g->out.size();
+    return FE_OK;
+}
+
+extern "C" int fe_graph_launch_host(fe_graph* g, const void* const* in_host, void* const* out_host, void* stream) {
+    if (!g || (!g->in.empty() && !in_host) || (!g->out.empty() && !out_host)) return fail(FE_EINVAL, "null argument");
+    for (size_t i = 0; i < g->in.size(); i++)
+        if (!in_host[i]) return fail(FE_EINVAL, "null host input buffer");
+    for (size_t i = 0; i < g->out.size(); i++)
+        if (!out_host[i]) return fail(FE_EINVAL, "null host output buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (size_t i = 0; i < g->in.size(); i++)
+        FE_CUDA_TRY(cudaMemcpyAsync(g->in[i].dev, in_host[i], g->in[i].bytes, cudaMemcpyHostToDevice, st));
+    FE_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    for (size_t i = 0; i < g->out.size(); i++)
+        FE_CUDA_TRY(cudaMemcpyAsync(out_host[i], g->out[i].dev, g->out[i].bytes, cudaMemcpyDeviceToHost, st));
     return FE_OK;
 }
 

@@ -11,7 +11,10 @@
 //
 // Host code cannot use the array's name as a device address (on the host it is
 // only a stand-in symbol); the device address is looked up once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current.
+// cudaGetSymbolAddress, on the first call for a context of that device (which
+// must be the current device).  Under lazy module loading (the CUDA default) the
+// array is only reserved on a device when this file's module first loads there,
+// which is that first call.
 #include <mutex>
 
 #include "ops.h"
@@ -19,7 +22,7 @@
 namespace fe {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 32ull << 20;  // 32 MiB, held by every GPU that loads the library
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;  // 32 MiB per device, from the module's first load there
 constexpr size_t kNoAllocScratchWords = kNoAllocScratchBytes / sizeof(u64);
 constexpr int kMaxDevices = 64;
 
@@ -28,10 +31,17 @@ static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchWords];
 std::mutex g_scratch_mu;
 u64* g_scratch_addr[kMaxDevices] = {};
 
-// device address of g_noalloc_scratch on the current device (looked up once per device)
-int scratch_address(u64** out) {
+// device address of g_noalloc_scratch on the context's device (looked up once per
+// device).  The context's tables, the caller's buffers and the stream belong to the
+// device the context was created on, so that device must be the current one: the
+// symbol's address is per device, and another device's array must never reach
+// these kernels.
+int scratch_address(const fe_ctx* c, u64** out) {
     int dev = 0;
     FE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(FE_EINVAL, "fe_rescale_noalloc: the current device (" + std::to_string(dev) +
+                                   ") is not the context's device (" + std::to_string(c->device) + ")");
     if (dev < 0 || dev >= kMaxDevices) return fail(FE_EINVAL, "device index above the supported maximum");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
@@ -65,7 +75,7 @@ extern "C" int fe_rescale_noalloc(fe_ctx* c, const void* ct_dev, uint32_t n_ct, 
                                    " bytes of scratch, above the fixed " + std::to_string(kNoAllocScratchBytes) +
                                    "-byte static buffer; split the batch or use fe_rescale");
     u64* scratch = nullptr;
-    FE_TRY(scratch_address(&scratch));
+    FE_TRY(scratch_address(c, &scratch));
     // profiling would create CUDA events; keep this path free of allocations
     const int saved_kind = c->prof.kind;
     c->prof.kind = -1;

@@ -237,6 +237,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     FE_CUDA_TRY(cudaGetDevice(&dev));
     FE_CUDA_TRY(cudaGetDeviceProperties(&c->prop, dev));
     c->n_sm = c->prop.multiProcessorCount;
+    c->device = dev;
 
     const int N = c->N, nm = c->n_mod;
     c->psi.resize(nm);
@@ -511,6 +512,15 @@ extern "C" int fe_device_status(fe_ctx* c, uint32_t* status, int reset) {
     FE_CUDA_TRY(cudaDeviceSynchronize());
     FE_CUDA_TRY(cudaMemcpy(status, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (reset) FE_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+    return FE_OK;
+}
+
+extern "C" int fe_ctx_set_mac_wait(fe_ctx* c, uint64_t limit_ns, int32_t unfed_term) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (limit_ns == 0 || limit_ns > 60000000000ull) return fe::fail(FE_EINVAL, "wait limit outside (0, 60 s]");
+    if (unfed_term < -1) return fe::fail(FE_EINVAL, "unfed_term must be -1 or a term index");
+    c->mac_wait_ns = limit_ns;
+    c->mac_unfed_term = unfed_term;
     return FE_OK;
 }
 

@@ -24,8 +24,10 @@ def _torch():
 class MobileNetBlocks:
     """schedule: "linear" (one outer rotation per channel diagonal, Eq. 4),
     "tuned" (per layer, the fastest outer-rotation split, hoisting and MAC tile
-    timed by the autotuner), or an int n1 (baby steps).  batch: independent
-    encrypted inputs per block, run together (keys shared across them)."""
+    timed by the autotuner), an int n1 (baby steps), or the list of per-block
+    schedule dicts a tuned instance reports in `.schedule` (reused without
+    tuning again).  batch: independent encrypted inputs per block, run
+    together (keys shared across them)."""
 
     def __init__(self, ctx, blocks=None, seed=0, delta=2.0 ** 32, key_seed=101, enc_seed=202, schedule="linear",
                  batch=1):
@@ -43,17 +45,22 @@ class MobileNetBlocks:
             from .tune import Tuner
             tuner = Tuner(ctx)
         plans = []
+        given = schedule if isinstance(schedule, (list, tuple)) else None
         for bi, (H, Cin, Cout) in enumerate(self.blocks):
             x, wd, wp = W.mobilenet_block(seed, H, Cin, Cout, BS=1, block=bi)
             lay = ctx.layout(H, H, Cin, 1, 1)
             dh_dw, dh_pw = False, False
             if tuner is not None:
                 _, dh_dw, t_dw = tuner.conv_schedule(lay, Cin, 3, depthwise=True, level=L)
+            elif given is not None:
+                dh_dw = given[bi]["dw_double_hoist"]
             pdw = ctx.plan_conv(lay, Cin, 3, depthwise=True, level=L, double_hoist=dh_dw)
             if tuner is not None:
                 n1, dh_pw, times = tuner.conv_schedule(pdw.out_layout, Cout, 1, level=L - 1)
                 self.tune_ms.append({"dw": {k: round(v, 3) for k, v in t_dw.items()},
                                      "pw": {k: round(v, 3) for k, v in times.items()}})
+            elif given is not None:
+                n1, dh_pw = given[bi]["pw_bsgs_n1"], given[bi]["pw_double_hoist"]
             elif schedule == "linear":
                 n1 = 0
             else:
@@ -62,6 +69,8 @@ class MobileNetBlocks:
             if tuner is not None:
                 ways, wt = tuner.mac_ways(ppw)
                 self.tune_ms[-1]["pw_mac_ways"] = {str(k): round(v, 3) for k, v in wt.items()}
+            elif given is not None:
+                ctx.plan_set_mac_ways(ppw, given[bi]["pw_mac_ways"])
             self.schedule.append({"dw_double_hoist": int(dh_dw), "pw_bsgs_n1": ppw.info.bsgs_n1,
                                   "pw_double_hoist": int(dh_pw), "pw_mac_ways": getattr(ppw, "mac_ways", 4)})
             plans.append((lay, pdw, ppw, x, wd, wp))
@@ -154,6 +163,10 @@ class MobileNetBlocks:
             s.wait_event(self._fork)
             with torch.cuda.stream(s):
                 blocks = range(i * per, (i + 1) * per)
+                if h_in is not None and h_out is not None:
+                    # through the C ABI: host copies in, replay, host copies out (fe_graph_launch_host)
+                    g.launch_host([h_in[b] for b in blocks], [h_out[b] for b in blocks])
+                    continue
                 if h_in is not None:
                     for b in blocks:
                         self.inputs[b].copy_(h_in[b], non_blocking=True)

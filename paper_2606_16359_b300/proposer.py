@@ -201,7 +201,8 @@ def main(argv=None):
     ap.add_argument("--layers", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out", "proposer_config4.json"))
+    ap.add_argument("--out", default="proposer_config4.json",
+                    help="report file (JSON), relative to the working directory")
     args = ap.parse_args(argv)
     import torch
     import workloads as W

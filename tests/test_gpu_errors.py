@@ -144,3 +144,42 @@ def test_layer_planning_and_evaluation_errors(g, keys):
     y = g.unpack(plan.out_layout, g.decrypt(sk, g.he_conv(full, plan, pt, ct), g.L - 1, 2.0 ** 25)).cpu().numpy()
     x = np.random.default_rng(4).uniform(0, 1, (1, 2, 6, 6))
     assert np.abs(y - plain.conv2d(x, w)).max() < 1e-3
+
+
+def test_mac_wait_expiry_sets_the_status_and_leaves_the_context_usable(g, keys):
+    """The PMult-MAC's bounded waits, made to run out on purpose: every MAC item
+    announces the bytes of its first term but no copy for it is issued, so that
+    stage never fills.  With a 1 ms limit the consumers give up, set bit 0 of the
+    status word and stop; the producer waits (bounded) for the copies it did
+    issue.  Afterwards, with the default limit back, the same layer on the same
+    context and stream gives the residues of a clean run, and a rotation
+    decrypts correctly."""
+    sk, evk = keys
+    lay = g.layout(6, 6, 2, 1, 2)
+    plan = g.plan_conv(lay, 3, 3)
+    w = np.random.default_rng(5).normal(0, 0.3, (3, 2, 3, 3))
+    pt = g.load_weights(plan, w, float(g.moduli[g.L]))
+    x = np.random.default_rng(6).uniform(0, 1, (1, 2, 6, 6))
+    ct = g.encrypt(sk, g.pack(lay, torch.from_numpy(x)), g.L, 2.0 ** 25, seed=4)
+    full = g.evk_gen(sk, 22, plan.steps)
+    clean = g.he_conv(full, plan, pt, ct).cpu().numpy().view(np.uint64).copy()
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    try:
+        g.set_mac_wait(1_000_000, 0)
+        g.he_conv(full, plan, pt, ct)
+        assert g.device_status(reset=True) & 1 == 1
+    finally:
+        g.set_mac_wait()
+    assert g.device_status() == 0
+    again = g.he_conv(full, plan, pt, ct).cpu().numpy().view(np.uint64)
+    assert np.array_equal(again, clean)
+    y = g.unpack(plan.out_layout, g.decrypt(sk, g.he_conv(full, plan, pt, ct), g.L - 1, 2.0 ** 25)).cpu().numpy()
+    assert np.abs(y - plain.conv2d(x, w)).max() < 1e-3
+    z = _slots(g, 1, 9)
+    zc = g.encrypt(sk, z, g.L, 2.0 ** 25, seed=8)
+    yr = g.decrypt(sk, g.rotate(evk, zc, g.L, 1), g.L, 2.0 ** 25).cpu().numpy()
+    assert np.abs(yr - np.roll(z.numpy(), -1, axis=1)).max() < 1e-3
+    assert g.device_status() == 0
+    with pytest.raises(fe.FencError):
+        g.set_mac_wait(0, -1)

@@ -5,8 +5,13 @@ device footprint, a host framework that owns all device memory, latency-critical
 code that cannot afford an allocation -- use fe_rescale_noalloc, whose scratch is
 a fixed static device array.  This test calls it through the C ABI twice in a
 row (the second call reuses the array left over from the first) and requires the
-same residues as fe_rescale, bit for bit.  It lives in its own file, collected
-last, and creates its own context so that it passes alone or after other tests.
+same residues as fe_rescale, bit for bit.  Around a warmed-up call it also
+checks the property the entry point exists for: the device's stream-ordered
+memory pool (which fe_rescale draws on) sees no allocation -- its used-memory
+high watermark stays at the current use -- and PyTorch's allocator makes none
+either; fe_rescale, under the same watch, does raise the watermark.  It lives
+in its own file, collected last, and creates its own context so that it passes
+alone or after other tests.
 """
 import ctypes
 
@@ -22,12 +27,44 @@ if not torch.cuda.is_available():
 import paper_2606_16359_b300 as fe  # noqa: E402
 
 
+class PoolWatch:
+    """Used-memory high watermark of the current device's default stream-ordered
+    pool (cudaMallocAsync draws on it), reset to the current use on entry."""
+
+    def __init__(self):
+        from cuda.bindings import driver, runtime
+        self.rt, self.drv = runtime, driver
+        err, self.pool = runtime.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+        assert err == runtime.cudaError_t.cudaSuccess
+
+    def _get(self, attr):
+        err, v = self.rt.cudaMemPoolGetAttribute(self.pool, attr)
+        assert err == self.rt.cudaError_t.cudaSuccess
+        return int(v)
+
+    def __enter__(self):
+        A = self.rt.cudaMemPoolAttr
+        torch.cuda.synchronize()
+        self.used0 = self._get(A.cudaMemPoolAttrUsedMemCurrent)
+        err, = self.rt.cudaMemPoolSetAttribute(self.pool, A.cudaMemPoolAttrUsedMemHigh, self.drv.cuuint64_t(0))
+        assert err == self.rt.cudaError_t.cudaSuccess
+        self.torch0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        return self
+
+    def __exit__(self, *exc):
+        torch.cuda.synchronize()
+        A = self.rt.cudaMemPoolAttr
+        self.high = self._get(A.cudaMemPoolAttrUsedMemHigh)
+        self.torch_allocs = torch.cuda.memory_stats().get("allocation.all.allocated", 0) - self.torch0
+        return False
+
+
 def _u64(t):
     return t.detach().cpu().numpy().view(np.uint64)
 
 
-def _noalloc(ctx, ct, level):
-    out = ctx.empty_ct(ct.shape[0], level - 1)
+def _noalloc(ctx, ct, level, out=None):
+    out = ctx.empty_ct(ct.shape[0], level - 1) if out is None else out
     rc = fe.load().fe_rescale_noalloc(ctx.handle, ctypes.c_void_p(ct.data_ptr()), ct.shape[0], level,
                                       ctypes.c_void_p(out.data_ptr()), fe._stream())
     fe.check(rc)
@@ -51,6 +88,16 @@ def test_rescale_noalloc_matches_rescale_on_two_calls(args, n_ct, level):
             assert np.array_equal(got, want), f"call {call}"
             outs.append(got)
         assert not np.array_equal(outs[0], outs[1])
+        # a warmed-up call allocates nothing; the regular rescale does, under the same watch
+        out = ctx.empty_ct(n_ct, level - 1)
+        with PoolWatch() as w:
+            _noalloc(ctx, ct, level, out)
+        assert w.high == w.used0 and w.torch_allocs == 0
+        assert np.array_equal(_u64(out), outs[1])
+        with PoolWatch() as w:
+            fe.check(fe.load().fe_rescale(ctx.handle, ctypes.c_void_p(ct.data_ptr()), n_ct, level,
+                                          ctypes.c_void_p(out.data_ptr()), fe._stream()))
+        assert w.high > w.used0
 
 
 def test_rescale_noalloc_rejects_oversized_requests():
