@@ -154,10 +154,12 @@ def ntt_traffic_per_limb_pass():
     return profiled_traffic("ntt_pass_forward_N65536_532limbs.txt", "traffic_bytes_per_limb_pass", "ntt.cu")
 
 
-def mac_traffic_per_launch():
-    """Mean DRAM bytes of the PMult-MAC launches of one bench step (ncu,
-    one-pass metrics over the step's launches)."""
-    return profiled_traffic("mac_pointwise_14x14x512_bsgs16.txt", "traffic_bytes_per_launch_in_step", "kernels.cu")
+def mac_traffic_ratio():
+    """DRAM bytes / algorithmic bytes of the PMult-MAC, from ncu on a small
+    pointwise layer (one kernel, two launches, a few GB resident); the MAC
+    streams each operand once, so its traffic scales with its algorithmic
+    bytes."""
+    return profiled_traffic("mac_traffic_pointwise_14x14x128_layer.txt", "traffic_ratio_to_algorithmic", "kernels.cu")
 
 
 # Warp instructions per lazy Shoup butterfly, counted by ncu on the register-
@@ -471,8 +473,10 @@ def run_ours(args, dist, rank, world, local):
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": None, "launches": n_dom,
                 "avg_launch_us": 1e3 * t_dom / max(1, n_dom), "time_share": shares, "by_class": by_class}
     if dom == "mac":
-        roofline["traffic"] = mac_traffic_per_launch()
-        roofline["traffic_unit"] = "bytes per launch (ncu dram read + write, mean over the step's launches)"
+        ratio = mac_traffic_ratio()
+        roofline["traffic"] = ratio * (b_dom / n_dom) if ratio and n_dom else None
+        roofline["traffic_unit"] = ("bytes per launch: ncu dram read + write over algorithmic bytes on a small "
+                                    "pointwise layer (%s), times this launch's algorithmic bytes" % ratio)
     if dom == "ntt":
         # the 64-bit-word transform is bound by the integer pipes: butterflies per
         # second against the live butterfly-probe roof; HBM figures kept beside it
@@ -588,15 +592,30 @@ def run_ours(args, dist, rank, world, local):
                     "ms_per_input": round(t / net_.batch, 3), "steps": steps, "warmup": 3}
         if not args.one_stream:
             variants["one_graph_one_stream"] = timed(net, False, args.steps)
+        import gc
         schedule = net.schedule
         del net
+        gc.collect()
         torch.cuda.empty_cache()
         for B in (4, 16):
             if B == args.batch:
                 continue
             nb = MobileNetBlocks(ctx, delta=DELTA, schedule=schedule, batch=B)
-            variants[f"batch_{B}"] = timed(nb, True, max(3, min(args.steps, 5)))
-            del nb
+            # B = 16 shares one data region across the six layers (one graph): the hoisted
+            # rotated copies of 16 inputs per block are tens of GB
+            concurrent = B <= 4
+            plans = [l_["plan"] for l_ in nb.layers]
+            need = (sum(ctx.graph_workspace_bytes(plans[2 * b:2 * b + 2], B) for b in range(len(nb.blocks)))
+                    if concurrent else ctx.graph_workspace_bytes(plans, B))
+            free = torch.cuda.mem_get_info()[0]
+            if need > free - (4 << 30):
+                variants[f"batch_{B}"] = {"skipped": f"graph workspace {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free"}
+            else:
+                variants[f"batch_{B}"] = dict(timed(nb, concurrent, max(3, min(args.steps, 5))),
+                                              path="graph per block, 3 streams" if concurrent
+                                              else "one graph, one stream")
+            del nb, plans
+            gc.collect()
             torch.cuda.empty_cache()
 
     cpu = None

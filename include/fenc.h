@@ -321,6 +321,22 @@ int fe_plan_conv(fe_ctx* ctx, const fe_layout* in_lay, uint32_t Cout, uint32_t K
  * giant-step split n1 = 2^ceil(log2(P)/2), n2 = P / n1. */
 int fe_plan_fc(fe_ctx* ctx, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat_host,
                uint32_t F_in, uint32_t F_out, uint32_t level, fe_plan** out);
+/* Plan the first fully connected layer on a fragment-packed map (the flatten
+ * step of a CNN, Sec. 5 Implementation: FC by diagonals with baby-step /
+ * giant-step): feature (c, h, w) of the (C, H, W) map in layout in_lay is input
+ * feature (c H + h) W + w (row-major flattening), read from the slot that
+ * Algorithm 1 gives it; F_in = C H W.  Same plan as fe_plan_fc with that table.
+ * Errors as fe_plan_fc. */
+int fe_plan_fc_layout(fe_ctx* ctx, const fe_layout* in_lay, uint32_t F_out, uint32_t level, fe_plan** out);
+/* Plan a fully connected layer that reads the output of the fully connected plan
+ * `prev` (neuron n of prev at position n mod P of ciphertext n / P), with
+ * F_in = prev's F_out.  Errors as fe_plan_fc; FE_EINVAL when prev is not FC. */
+int fe_plan_fc_next(fe_ctx* ctx, const fe_plan* prev, uint32_t F_out, uint32_t level, fe_plan** out);
+/* Read a fully connected plan's decrypted output slots back as outputs:
+ * y_dev[b][n] (BS x F_out, float64) = slots_dev[n / P][(n mod P) BS + b]
+ * (slots_dev: the plan's n_out_ct decoded slot vectors of N/2 doubles).
+ * Errors: FE_EINVAL. */
+int fe_fc_unpack(const fe_ctx* ctx, const fe_plan* plan, const double* slots_dev, double* y_dev, void* stream);
 void fe_plan_destroy(fe_plan* plan);
 
 /* Sizes of a plan's buffers: encoded weight plaintexts, input / output
@@ -356,6 +372,18 @@ int fe_plan_rotation_steps(const fe_plan* plan, int32_t* steps_host, uint32_t ma
  * (4 + hb) / 8 of the bytes. */
 int fe_plan_load_weights(fe_ctx* ctx, fe_plan* plan, const double* weights_host, double wmul,
                          double w_scale, void* pt_dev, void* stream);
+/* The scale rule for a chain of layers (the weights' scale of Sec. 4.3 / Sec. 5):
+ * a linear layer at `level` with input scale s_in encodes its weights at
+ *   *w_scale = (t / s_in) q_level,
+ * so that its output after the rescale by q_level has scale t: t = delta, or,
+ * when an activation with leading coefficient act_a != 0 follows (x^2: 1),
+ * t = sqrt(delta q_{level-1} |act_a|), which that activation's rescale brings
+ * back to delta (fe_poly_act_scale).  IEEE double, in the order written.
+ * Errors: FE_ELEVEL (level 0 or above L), FE_EINVAL. */
+int fe_weight_scale(const fe_ctx* ctx, uint32_t level, double s_in, double delta, double act_a, double* w_scale);
+/* Output scale of a conv or FC plan whose weights were loaded at w_scale:
+ * (in_scale w_scale) / q_level.  Errors: FE_EINVAL (weights not loaded). */
+int fe_plan_out_scale(const fe_plan* plan, double in_scale, double* out_scale);
 
 /* Run a planned HE convolution: in_dev [n_in_ct][2][level+1][N] -> out_dev
  * [n_out_ct][2][level][N] (rescaled once).  mode 0 = plain path (one launch per
@@ -426,12 +454,32 @@ int fe_plan_set_mac_ways(fe_plan* plan, uint32_t ways);
  * to time a slice of a large layer.  Errors: FE_EINVAL. */
 int fe_plan_truncate(fe_plan* plan, uint32_t max_out_ct);
 
-/* x^2 activation (the a x^2 + b x + c polynomial of Sec. 5, Implementation, with a = 1,
- * b = c = 0): CMult with relinearisation, then rescale.  in: [n_ct][2][level+1][N],
+/* x^2 activation (fe_he_poly_act with a = 1, b = c = 0; same residues):
+ * CMult with relinearisation, then rescale.  in: [n_ct][2][level+1][N],
  * out: [n_ct][2][level][N].  Workspace: fe_square_workspace_bytes. */
 size_t fe_square_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
 int fe_he_square(fe_ctx* ctx, const fe_evk* evk, const void* in_dev, uint32_t n_ct, uint32_t level,
                  void* out_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* The activation a x^2 + b x + c that replaces ReLU (Sec. 5, Implementation),
+ * on n_ct ciphertexts at `level` with scale in_scale, in one level:
+ *   a != 0: a x^2 + b x + c = a [(x + beta)^2 + gamma], beta = b / (2a),
+ *     gamma = c / a - beta^2: add K1 = nearest(beta s) to the constant term,
+ *     CMult with relinearisation, multiply by sign(a) and add
+ *     K2 = sign(a) nearest(gamma s s), rescale by q_level; the output decrypts
+ *     to a x^2 + b x + c at scale (s s) / (q_level |a|);
+ *   a == 0: multiply by nearest(b q_level), add nearest(c (s q_level)), rescale:
+ *     scale s.
+ * nearest() is the nearest integer of the IEEE double, ties away from zero.
+ * With a = 1, b = c = 0 the residues are fe_he_square's.  out: [n_ct][2][level][N];
+ * *out_scale (optional) receives the output scale.  Workspace:
+ * fe_poly_act_workspace_bytes.  Errors: FE_ELEVEL, FE_EKEY (no relinearisation
+ * key when a != 0), FE_ENOMEM, FE_EINVAL (non-finite coefficient or scale). */
+size_t fe_poly_act_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
+int fe_poly_act_scale(const fe_ctx* ctx, uint32_t level, double in_scale, double a, double* out_scale);
+int fe_he_poly_act(fe_ctx* ctx, const fe_evk* evk, double a, double b, double c, const void* in_dev, uint32_t n_ct,
+                   uint32_t level, double in_scale, void* out_dev, double* out_scale, void* workspace_dev,
+                   size_t workspace_bytes, void* stream);
 
 /* 2x2 average pooling by summing fragment ciphertexts (S even; Sec. 5, Implementation): output
  * fragment (u, v) = sum of input fragments (2u + di, 2v + dj); the 1/4 is left
@@ -449,6 +497,22 @@ size_t fe_compress_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t le
 int fe_compress(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid,
                 const void* in_dev, uint32_t n_ct, uint32_t level, void* out_dev,
                 void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* AAC with its plaintext mask (Sec. 4.3, last paragraph), for inputs whose empty
+ * channel blocks are not zero (e.g. after an activation with c != 0): every
+ * ciphertext is multiplied by the 0/1 mask of the valid blocks (slots below
+ * c_valid m^2 BS), encoded at scale mask_scale (Delta_2), and then replicated
+ * as by fe_compress.  No rescale: the output stays at `level` with scale
+ * in_scale mask_scale (*out_scale, optional), and the next layer's weights take
+ * Delta_1 = q_level t / (in_scale Delta_2) from fe_weight_scale, so one rescale
+ * follows both multiplications.  The mask's encoding error is about
+ * sqrt(N / 12) / Delta_2 of the values: choose Delta_2 well above sqrt(N).
+ * Workspace: fe_compress_masked_workspace_bytes.  Errors as fe_compress,
+ * FE_EINVAL (mask_scale below 1). */
+size_t fe_compress_masked_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct, uint32_t level);
+int fe_compress_masked(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid, double mask_scale,
+                       const void* in_dev, uint32_t n_ct, uint32_t level, double in_scale, void* out_dev,
+                       double* out_scale, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* ---- batched, graph-captured execution ------------------------------------- */
 

@@ -491,3 +491,34 @@ def cmult_relin(pr, keys, x, y):
     c0 = np.stack([C.vec_add(d0[t], e0[t], pr.moduli[t]) for t in range(lv + 1)])
     c1 = np.stack([C.vec_add(d1[t], e1[t], pr.moduli[t]) for t in range(lv + 1)])
     return Ciphertext(c0, c1, lv, x.scale * y.scale)
+
+
+# ---------------------------------------------------------------------------
+# Constants and integer scalars (the affine parts of a polynomial activation)
+# ---------------------------------------------------------------------------
+
+def nearest_int(x):
+    """The integer nearest to the IEEE double x, ties away from zero (exact)."""
+    from fractions import Fraction
+    f = Fraction(float(x))
+    n = abs(f.numerator) // f.denominator
+    if abs(f) - n >= Fraction(1, 2):
+        n += 1
+    return n if f >= 0 else -n
+
+
+def add_int(pr, ct, K):
+    """Add the integer K to the constant coefficient of the message: the constant
+    polynomial K has the value K at every NTT position, so K mod q_t is added to
+    every residue of c0.  The scale is unchanged."""
+    c0 = np.stack([C.vec_add(ct.c0[t], np.full(pr.N, K % pr.moduli[t], dtype=np.uint64), pr.moduli[t])
+                   for t in range(ct.level + 1)])
+    return Ciphertext(c0, ct.c1.copy(), ct.level, ct.scale)
+
+
+def mul_int(pr, ct, K):
+    """Multiply both polynomials by the integer K (mod each q_t).  The message is
+    multiplied by K; the caller decides what that does to the scale."""
+    c0 = np.stack([C.vec_scalar_mul(ct.c0[t], K % pr.moduli[t], pr.moduli[t]) for t in range(ct.level + 1)])
+    c1 = np.stack([C.vec_scalar_mul(ct.c1[t], K % pr.moduli[t], pr.moduli[t]) for t in range(ct.level + 1)])
+    return Ciphertext(c0, c1, ct.level, ct.scale)

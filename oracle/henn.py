@@ -538,15 +538,98 @@ def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None):
 
 
 # ---------------------------------------------------------------------------
+# Polynomial activation a x^2 + b x + c (Sec. 5, Implementation paragraph)
+# ---------------------------------------------------------------------------
+
+def poly_act_constants(s, a, b, c):
+    """The integer constants of he_poly_act for input scale s and a != 0:
+    (K1, sign, K2) with beta = b / (2a), gamma = c / a - beta^2,
+    K1 = nearest(beta s), sign = sign(a), K2 = sign nearest(gamma (s s)).
+    Every quotient and product is one IEEE double operation in the order
+    written; nearest() rounds to the nearest integer, ties away from zero."""
+    if a == 0:
+        raise ValueError("a == 0 has no square term")
+    beta = b / (2.0 * a)
+    gamma = c / a - beta * beta
+    sign = 1 if a > 0 else -1
+    return ckks.nearest_int(beta * s), sign, sign * ckks.nearest_int(gamma * (s * s))
+
+
+def he_poly_act(pr, keys, cts, a, b, c, cnt=None):
+    """The activation a x^2 + b x + c that replaces ReLU (Sec. 5, Implementation),
+    in one level, as the library computes it.
+
+    a != 0 (completing the square): a x^2 + b x + c = a [(x + beta)^2 + gamma],
+      1. u = ct + K1, K1 = nearest(beta s)          (scale s)
+      2. w = relin(u (x) u)                          (scale s^2)
+      3. v = sign(a) w + K2, K2 = sign(a) nearest(gamma s^2)
+      4. rescale by q_l: the output decrypts to sign(a) [(x+beta)^2 + gamma]
+         at scale s^2 / q_l, i.e. to a x^2 + b x + c at scale s^2 / (q_l |a|).
+    a == 0 (affine): v = ct B + K with B = nearest(b q_l), K = nearest(c s q_l)
+      (scale s q_l), rescaled by q_l to scale s.
+    With a = 1, b = c = 0 every step is the identity but the square and the
+    rescale, so the residues are those of he_square."""
+    cnt = cnt if cnt is not None else Counters()
+    out = []
+    for ct in cts:
+        lv, s = ct.level, ct.scale
+        ql = float(pr.moduli[lv])
+        if a != 0:
+            K1, sign, K2 = poly_act_constants(s, a, b, c)
+            u = ckks.add_int(pr, ct, K1)
+            w = ckks.cmult_relin(pr, keys, u, u)
+            cnt.cmult += 1
+            cnt.keyswitch += 1
+            v = ckks.add_int(pr, ckks.mul_int(pr, w, sign), K2)
+            r = ckks.rescale(pr, v)
+            r.scale = (s * s) / (ql * abs(a))
+        else:
+            B = ckks.nearest_int(b * ql)
+            K = ckks.nearest_int(c * (s * ql))
+            r = ckks.rescale(pr, ckks.add_int(pr, ckks.mul_int(pr, ct, B), K))
+            r.scale = s
+        cnt.rescale += 1
+        out.append(r)
+    return out
+
+
+def aac_mask_slots(lay, c_valid):
+    """0/1 slot vector of the valid channel blocks: 1 where c_loc < c_valid."""
+    mask = np.zeros(lay.N // 2)
+    per = lay.m * lay.m * lay.BS
+    mask[:c_valid * per] = 1.0
+    return mask
+
+
+def aac_compress_masked(pr, keys, cts, lay, c_valid, mask_scale, cnt=None):
+    """AAC with its plaintext mask (Sec. 4.3, last paragraph): the 0/1 mask of the
+    valid channel blocks, encoded at scale Delta_2 = mask_scale, zeroes whatever
+    the empty blocks hold (e.g. the constant of an activation with c != 0); the
+    rotate-and-add replication follows on the masked ciphertexts.  No rescale
+    here: the output scale is s Delta_2, and the next layer's weights are
+    encoded at Delta_1 = q_l t / (s Delta_2), so that one rescale follows both
+    multiplications (Delta_1 Delta_2 = q_l t / s)."""
+    cnt = cnt if cnt is not None else Counters()
+    mask = ckks.encode(pr, aac_mask_slots(lay, c_valid), cts[0].level, mask_scale)
+    masked = []
+    for ct in cts:
+        masked.append(ckks.pmult(pr, ct, mask))
+        cnt.pmult += 1
+    return aac_compress(pr, keys, masked, lay, c_valid, cnt)
+
+
+# ---------------------------------------------------------------------------
 # Scale rule for a chain of layers and the LeNet-shaped network
 # ---------------------------------------------------------------------------
 
-def weight_scale(pr, level, s_in, delta, square_follows):
+def weight_scale(pr, level, s_in, delta, act_a):
     """Scale at which a linear layer at `level` encodes its weights: the output
-    scale after its rescale is delta, or sqrt(delta q_{level-1}) when an x^2
-    activation follows (so that the activation's rescale lands back near delta).
+    scale after its rescale is delta, or sqrt(delta q_{level-1} |a|) when an
+    activation with leading coefficient a follows (x^2: a = 1; a bool True
+    counts as 1), so that the activation's rescale (scale s^2 / (q_{level-1} |a|),
+    he_poly_act) lands back on delta.  act_a = 0 / False: no activation follows.
     Evaluated as written, in IEEE double arithmetic."""
-    t = math.sqrt(delta * float(pr.moduli[level - 1])) if square_follows else delta
+    t = math.sqrt(delta * float(pr.moduli[level - 1]) * abs(act_a)) if act_a else delta
     return (t / s_in) * float(pr.moduli[level])
 
 
@@ -567,19 +650,25 @@ def lenet_rotation_steps(N, BS, S=4):
     return sorted(steps)
 
 
-def he_lenet(pr, keys, cts, lay, weights, delta, cnt=None):
-    """conv5x5 1->6, x^2, avgpool2, conv5x5 6->16, x^2, avgpool2, FC 256->120->84->10.
+def he_lenet(pr, keys, cts, lay, weights, delta, cnt=None, act=None):
+    """conv5x5 1->6, act, avgpool2, conv5x5 6->16, act, avgpool2, FC 256->120->84->10,
+    act = x^2 (he_square) or, given act = (a, b, c), a x^2 + b x + c (he_poly_act).
     Returns the output ciphertexts (neuron n at position n of the FC layout)."""
     cnt = cnt if cnt is not None else Counters()
+    a = 1.0 if act is None else act[0]
+
+    def activation(h):
+        return he_square(pr, keys, h, cnt) if act is None else he_poly_act(pr, keys, h, *act, cnt=cnt)
+
     lv = cts[0].level
     h, l1 = he_conv(pr, keys, cts, lay, weights["conv1"],
-                    w_scale=weight_scale(pr, lv, cts[0].scale, delta, True), cnt=cnt)
-    h = he_square(pr, keys, h, cnt)
+                    w_scale=weight_scale(pr, lv, cts[0].scale, delta, a), cnt=cnt)
+    h = activation(h)
     h, l1 = he_avgpool2(pr, h, l1)
     lv = h[0].level
     h, l2 = he_conv(pr, keys, h, l1, weights["conv2"], wmul=0.25,
-                    w_scale=weight_scale(pr, lv, h[0].scale, delta, True), cnt=cnt)
-    h = he_square(pr, keys, h, cnt)
+                    w_scale=weight_scale(pr, lv, h[0].scale, delta, a), cnt=cnt)
+    h = activation(h)
     h, l2 = he_avgpool2(pr, h, l2)
     assert l2.S == 1
     P = l2.cpc * l2.m * l2.m

@@ -45,10 +45,11 @@ def fc(x, w):
     return x @ w.T
 
 
-def lenet(x, weights):
-    """conv5x5 1->6, x^2, avgpool2, conv5x5 6->16, x^2, avgpool2, FC 256->120->84->10."""
-    h = avgpool2(poly_act(conv2d(x, weights["conv1"])))
-    h = avgpool2(poly_act(conv2d(h, weights["conv2"])))
+def lenet(x, weights, act=(1.0, 0.0, 0.0)):
+    """conv5x5 1->6, act, avgpool2, conv5x5 6->16, act, avgpool2, FC 256->120->84->10;
+    act = (a, b, c) of a x^2 + b x + c (x^2 by default)."""
+    h = avgpool2(poly_act(conv2d(x, weights["conv1"]), *act))
+    h = avgpool2(poly_act(conv2d(h, weights["conv2"]), *act))
     h = h.reshape(h.shape[0], -1)
     h = fc(h, weights["fc1"])
     h = fc(h, weights["fc2"])

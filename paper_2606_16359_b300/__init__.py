@@ -10,7 +10,6 @@ library must have been built (paper_2606_16359_b300.build.build()).  There is no
 fallback path: a missing library raises.
 """
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -142,6 +141,16 @@ SIGNATURES = {
     "fe_plan_conv": (cint, [vp, P(FeLayout), u32, u32, u32, cint, u32, u32, u32, P(FeLayout), P(vp)]),
     "fe_plan_fc": (cint, [vp, u32, u32, u32, P(i32), u32, u32, u32, P(vp)]),
     "fe_plan_destroy": (None, [vp]),
+    "fe_plan_fc_layout": (cint, [vp, P(FeLayout), u32, u32, P(vp)]),
+    "fe_plan_fc_next": (cint, [vp, vp, u32, u32, P(vp)]),
+    "fe_fc_unpack": (cint, [vp, vp, vp, vp, vp]),
+    "fe_weight_scale": (cint, [vp, u32, dbl, dbl, dbl, P(dbl)]),
+    "fe_plan_out_scale": (cint, [vp, dbl, P(dbl)]),
+    "fe_poly_act_workspace_bytes": (sz, [vp, u32, u32]),
+    "fe_poly_act_scale": (cint, [vp, u32, dbl, dbl, P(dbl)]),
+    "fe_he_poly_act": (cint, [vp, vp, dbl, dbl, dbl, vp, u32, u32, dbl, vp, P(dbl), vp, sz, vp]),
+    "fe_compress_masked_workspace_bytes": (sz, [vp, u32, u32]),
+    "fe_compress_masked": (cint, [vp, vp, P(FeLayout), u32, dbl, vp, u32, u32, dbl, vp, P(dbl), vp, sz, vp]),
     "fe_plan_query": (cint, [vp, P(FePlanInfo)]),
     "fe_plan_rotation_steps": (cint, [vp, P(i32), u32, P(u32)]),
     "fe_plan_load_weights": (cint, [vp, vp, vp, dbl, dbl, vp, vp]),
@@ -590,12 +599,66 @@ class Context:
         return ms.value, int(n.value), b.value
 
     # -- scale rule shared by the network code --------------------------------------------
-    def weight_scale(self, level, s_in, delta, square_follows):
-        """Scale at which a linear layer at `level` encodes its weights: after its rescale the
-        output scale is delta, or sqrt(delta q_{level-1}) when an x^2 activation follows (so
-        that the activation's rescale lands back near delta).  Evaluated in IEEE double."""
-        t = math.sqrt(delta * float(self.moduli[level - 1])) if square_follows else delta
-        return (t / s_in) * float(self.moduli[level])
+    def weight_scale(self, level, s_in, delta, act_a=0.0):
+        """fe_weight_scale: the weights' scale of a linear layer at `level` with input scale
+        s_in (act_a: leading coefficient of the activation that follows, 0 for none)."""
+        r = dbl()
+        check(load().fe_weight_scale(self.handle, level, float(s_in), float(delta), float(act_a), ctypes.byref(r)))
+        return r.value
+
+    def plan_out_scale(self, plan, in_scale):
+        """fe_plan_out_scale: output scale of a plan with loaded weights."""
+        r = dbl()
+        check(load().fe_plan_out_scale(plan.handle, float(in_scale), ctypes.byref(r)))
+        return r.value
+
+    def poly_act_scale(self, level, in_scale, a):
+        r = dbl()
+        check(load().fe_poly_act_scale(self.handle, level, float(in_scale), float(a), ctypes.byref(r)))
+        return r.value
+
+    def he_poly_act(self, evk, ct, level, in_scale, a, b, c):
+        """a x^2 + b x + c on ciphertexts at `level` with scale in_scale; returns (out, out_scale)."""
+        n = ct.shape[0]
+        ws = self.workspace(load().fe_poly_act_workspace_bytes(self.handle, n, level))
+        out = self.empty_ct(n, level - 1)
+        sc = dbl()
+        check(load().fe_he_poly_act(self.handle, evk.handle if evk is not None else None, float(a), float(b),
+                                    float(c), _ptr(ct), n, level, float(in_scale), _ptr(out), ctypes.byref(sc),
+                                    _ptr(ws), ws.numel() * 8, _stream()))
+        return out, sc.value
+
+    def compress_masked(self, evk, lay, c_valid, mask_scale, ct, level, in_scale):
+        """AAC with its 0/1 mask at mask_scale; returns (out, out_scale)."""
+        n = ct.shape[0]
+        ws = self.workspace(load().fe_compress_masked_workspace_bytes(self.handle, n, level))
+        out = self.empty_ct(n, level)
+        sc = dbl()
+        check(load().fe_compress_masked(self.handle, evk.handle, ctypes.byref(lay), c_valid, float(mask_scale),
+                                        _ptr(ct), n, level, float(in_scale), _ptr(out), ctypes.byref(sc), _ptr(ws),
+                                        ws.numel() * 8, _stream()))
+        return out, sc.value
+
+    def plan_fc_layout(self, lay, F_out, level):
+        h = vp()
+        check(load().fe_plan_fc_layout(self.handle, ctypes.byref(lay), F_out, level, ctypes.byref(h)))
+        p = Plan(self, h)
+        p.level = level
+        return p
+
+    def plan_fc_next(self, prev, F_out, level):
+        h = vp()
+        check(load().fe_plan_fc_next(self.handle, prev.handle, F_out, level, ctypes.byref(h)))
+        p = Plan(self, h)
+        p.level = level
+        return p
+
+    def fc_unpack(self, plan, slots, BS, F_out):
+        """fe_fc_unpack: decoded output slots of an FC plan -> (BS, F_out) outputs."""
+        torch = _torch()
+        y = torch.empty((BS, F_out), dtype=torch.float64, device="cuda")
+        check(load().fe_fc_unpack(self.handle, plan.handle, _ptr(slots.contiguous()), _ptr(y), _stream()))
+        return y
 
 
 P_i32 = ctypes.POINTER(i32)

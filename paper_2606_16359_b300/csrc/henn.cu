@@ -1008,6 +1008,67 @@ extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, 
     return FE_OK;
 }
 
+extern "C" int fe_plan_fc_layout(fe_ctx* c, const fe_layout* in_lay, uint32_t F_out, uint32_t level,
+                                 fe_plan** out) {
+    if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
+    fe_layout L = *in_lay;
+    FE_TRY(layout_fill(c->N, &L));
+    // feature (c, h, w) -> (c H + h) W + w, the row-major flattening of a (C, H, W) map
+    const uint32_t P = L.cpc * L.m * L.m;
+    std::vector<int32_t> feat((size_t)L.n_ct * P, -1);
+    for (uint32_t ci = 0; ci < L.n_ct; ci++) {
+        const uint32_t g = ci / (L.S * L.S), u = (ci / L.S) % L.S, v = ci % L.S;
+        for (uint32_t p = 0; p < P; p++) {
+            const uint32_t c_loc = p / (L.m * L.m), k = p % (L.m * L.m);
+            const uint32_t ch = g * L.cpc + c_loc, h = (k / L.m) * L.S + u, w = (k % L.m) * L.S + v;
+            if (ch < L.C && h < L.H && w < L.W) feat[(size_t)ci * P + p] = (int32_t)((ch * L.H + h) * L.W + w);
+        }
+    }
+    return fe_plan_fc(c, L.n_ct, P, L.BS, feat.data(), L.C * L.H * L.W, F_out, level, out);
+}
+
+extern "C" int fe_plan_fc_next(fe_ctx* c, const fe_plan* prev, uint32_t F_out, uint32_t level, fe_plan** out) {
+    if (!c || !prev || !out) return fail(FE_EINVAL, "null argument");
+    if (prev->kind != 1) return fail(FE_EINVAL, "fe_plan_fc_next continues a fully connected plan");
+    const uint32_t P = (uint32_t)prev->P, n_in = (uint32_t)prev->n_out, F_in = (uint32_t)prev->F_out;
+    std::vector<int32_t> feat((size_t)n_in * P);
+    for (size_t i = 0; i < feat.size(); i++) feat[i] = i < F_in ? (int32_t)i : -1;
+    return fe_plan_fc(c, n_in, P, (uint32_t)prev->BS, feat.data(), F_in, F_out, level, out);
+}
+
+namespace fe {
+namespace {
+// logits y[b][n] = slot (n mod P) BS + b of ciphertext n / P
+__global__ void k_fc_unpack(const double* slots, double* y, int P, int BS, int F, int half) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // i = b F + n
+    if (i >= BS * F) return;
+    const int b = i / F, n = i % F;
+    y[i] = slots[(size_t)(n / P) * half + (size_t)(n % P) * BS + b];
+}
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_fc_unpack(const fe_ctx* c, const fe_plan* p, const double* slots_dev, double* y_dev,
+                            void* stream) {
+    if (!c || !p || !slots_dev || !y_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(slots_dev);
+    FE_ALIGNED(y_dev);
+    if (p->kind != 1) return fail(FE_EINVAL, "not a fully connected plan");
+    const int total = p->BS * p->F_out;
+    k_fc_unpack<<<(total + kB - 1) / kB, kB, 0, (cudaStream_t)stream>>>(slots_dev, y_dev, p->P, p->BS, p->F_out,
+                                                                        c->N / 2);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_plan_out_scale(const fe_plan* p, double in_scale, double* out_scale) {
+    if (!p || !out_scale) return fail(FE_EINVAL, "null argument");
+    if (p->w_scale == 0) return fail(FE_EINVAL, "the plan's weights are not loaded");
+    if (!(in_scale > 0)) return fail(FE_EINVAL, "scale must be positive");
+    *out_scale = (in_scale * p->w_scale) / (double)p->c->mod[p->level];
+    return FE_OK;
+}
+
 extern "C" void fe_plan_destroy(fe_plan* p) { delete p; }
 
 // workspace for n_req requests: the whole outer stage in one chunk, unless the
@@ -1104,6 +1165,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     cudaFreeAsync(descs, st);
     if (dfeat) cudaFreeAsync(dfeat, st);
     FE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rc == FE_OK) p->w_scale = w_scale;
     return rc;
 }
 

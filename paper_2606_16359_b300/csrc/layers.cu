@@ -3,6 +3,7 @@
 // Compression (rotate-and-add replication), and CUDA-graph capture of a
 // sequence of planned layers.
 #include <algorithm>
+#include <cmath>
 #include <memory>
 
 #include "plan.h"
@@ -63,6 +64,88 @@ bool carve_ks(Carver& cv, const fe_ctx* c, int n, int level, KsScratch* s) {
     return cv.ok;
 }
 
+// Per-limb constants of an affine map of ciphertexts (polynomial activation).
+constexpr int kMaxAffineLimbs = 64;
+struct AffineConsts {
+    u64 mul[kMaxAffineLimbs];  // factor per limb (both polynomials)
+    u64 add[kMaxAffineLimbs];  // constant per limb (c0 only: a constant message term)
+};
+
+// out = in * mul_i (+ add_i on c0), limb i of each of n ciphertexts [2][nl][N]
+__global__ void k_affine(const u64* in, u64* out, const Modulus* mods, AffineConsts k, int nl, int logN,
+                         int do_mul) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int limb = blockIdx.y, ci = blockIdx.z;  // limb over 2 nl
+    const int i = limb % nl;
+    const Modulus m = mods[i];
+    const size_t o = ((size_t)ci * 2 * nl + limb) * N + n;
+    u64 v = in[o];
+    if (do_mul) v = mul_mod(v, k.mul[i], m);
+    if (limb < nl) v = add_mod(v, k.add[i], m.q);
+    out[o] = v;
+}
+
+// the integer nearest to x, ties away from zero, reduced mod q (any finite x)
+u64 nearest_mod(double x, u64 q) {
+    double t = std::trunc(x);
+    if (std::fabs(x - t) >= 0.5) t += x > 0 ? 1.0 : -1.0;
+    const bool neg = t < 0;
+    const double mag = std::fabs(t);
+    int e = 0;
+    const double fr = std::frexp(mag, &e);  // mag = fr 2^e, fr in [1/2, 1)
+    u64 r;
+    if (e <= 63) {
+        r = (u64)mag % q;
+    } else {  // mag = M 2^(e - 53) with the 53-bit integer M
+        const u64 M = (u64)std::ldexp(fr, 53);
+        r = h_mulmod(M % q, h_powmod(2, (u64)(e - 53), q), q);
+    }
+    return neg && r ? q - r : r;
+}
+
+int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const AffineConsts& k, bool do_mul,
+                  cudaStream_t st) {
+    if (level + 1 > kMaxAffineLimbs) return fail(FE_EINVAL, "more limbs than the affine kernel holds");
+    if (!n) return FE_OK;
+    k_affine<<<dim3((c->N + kB - 1) / kB, 2 * (level + 1), n), kB, 0, st>>>(in, out, c->d_mod, k, level + 1, c->logN,
+                                                                           do_mul ? 1 : 0);
+    c->cnt.launches++;
+    return FE_OK;
+}
+
+// d = relin(in (x) in) on Q_level for n ciphertexts, no rescale (CMult + relinearisation)
+int square_relin(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, u64* d, Carver& cv,
+                 cudaStream_t st) {
+    const int N = c->N, nl = level + 1;
+    KsScratch s;
+    carve_ks(cv, c, n, level, &s);
+    CombineItem* dcb = cv.take<CombineItem>(n);
+    u64* d012 = cv.take<u64>((size_t)n * 3 * nl * N);
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
+    std::vector<KsItem> ks(n);
+    std::vector<CombineItem> cb(n);
+    for (int i = 0; i < n; i++) {
+        ks[i] = KsItem{s.ext + i * ext_words(c, level), evk->relin, s.acc + i * acc_words(c, level)};
+        const u64* dd = d012 + (size_t)i * 3 * nl * N;
+        cb[i] = CombineItem{s.acc + i * acc_words(c, level), s.conv + i * ct_words(c, level), dd, dd + (size_t)nl * N,
+                            d + i * ct_words(c, level), 1, 0};
+    }
+    std::vector<KsGroup> kg{KsGroup{evk->relin, 0, n}};
+    FE_TRY(upload(ks, s.ks, st));
+    FE_TRY(upload(kg, s.kg, st));
+    FE_TRY(upload(cb, dcb, st));
+    launch_tensor(c, in, in, d012, n, level, st);
+    modup(c, d012 + 2 * (size_t)nl * N, 3 * (size_t)nl * N, n, level, s.coef, s.ext, st);
+    launch_keyip_grouped(c, s.kg, s.ks, 1, n, level, st);
+    moddown_prepare(c, s.acc, n, level, s.conv, st);
+    launch_combine(c, dcb, n, level, st);
+    c->cnt.cmult += n;
+    c->cnt.keyswitch += n;
+    return FE_OK;
+}
+
 }  // namespace
 }  // namespace fe
 
@@ -83,36 +166,89 @@ extern "C" int fe_he_square(fe_ctx* c, const fe_evk* evk, const void* in_dev, ui
     if (ws_bytes < fe_square_workspace_bytes(c, n, level)) return fail(FE_ENOMEM, "workspace too small");
     if (n == 0) return FE_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int N = c->N, nl = level + 1;
+    const int N = c->N;
     Carver cv(ws, ws_bytes);
-    KsScratch s;
-    carve_ks(cv, c, n, level, &s);
-    CombineItem* dcb = cv.take<CombineItem>(n);
-    u64* d012 = cv.take<u64>((size_t)n * 3 * nl * N);
-    u64* tmp = cv.take<u64>((size_t)n * 2 * nl * N);
+    u64* tmp = cv.take<u64>((size_t)n * ct_words(c, level));
     u64* rs = cv.take<u64>(rescale_tmp_words(c, n, level));
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
-    std::vector<KsItem> ks(n);
-    std::vector<CombineItem> cb(n);
-    for (uint32_t i = 0; i < n; i++) {
-        ks[i] = KsItem{s.ext + i * ext_words(c, level), evk->relin, s.acc + i * acc_words(c, level)};
-        const u64* d = d012 + (size_t)i * 3 * nl * N;
-        cb[i] = CombineItem{s.acc + i * acc_words(c, level), s.conv + i * ct_words(c, level), d, d + (size_t)nl * N,
-                            tmp + i * ct_words(c, level), 1, 0};
-    }
-    std::vector<KsGroup> kg{KsGroup{evk->relin, 0, (int)n}};
-    FE_TRY(upload(ks, s.ks, st));
-    FE_TRY(upload(kg, s.kg, st));
-    FE_TRY(upload(cb, dcb, st));
-    launch_tensor(c, (const u64*)in_dev, (const u64*)in_dev, d012, n, level, st);
-    modup(c, d012 + 2 * (size_t)nl * N, 3 * (size_t)nl * N, n, level, s.coef, s.ext, st);
-    launch_keyip_grouped(c, s.kg, s.ks, 1, (int)n, level, st);
-    moddown_prepare(c, s.acc, n, level, s.conv, st);
-    launch_combine(c, dcb, n, level, st);
+    FE_TRY(square_relin(c, evk, (const u64*)in_dev, (int)n, (int)level, tmp, cv, st));
     rescale_batch(c, tmp, n, level, (u64*)out_dev, rs, rs + 2 * (size_t)n * N, st);
-    c->cnt.cmult += n;
-    c->cnt.keyswitch += n;
     FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" size_t fe_poly_act_workspace_bytes(const fe_ctx* c, uint32_t n, uint32_t level) {
+    if (!c) return 0;
+    return fe_square_workspace_bytes(c, n, level) + (size_t)n * ct_words(c, level) * 8 + 256;
+}
+
+extern "C" int fe_poly_act_scale(const fe_ctx* c, uint32_t level, double in_scale, double a, double* out_scale) {
+    if (!c || !out_scale) return fail(FE_EINVAL, "null argument");
+    if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "the activation needs a level to rescale");
+    if (!(in_scale > 0) || !std::isfinite(a)) return fail(FE_EINVAL, "bad scale or coefficient");
+    const double ql = (double)c->mod[level];
+    *out_scale = a != 0 ? (in_scale * in_scale) / (ql * std::fabs(a)) : in_scale;
+    return FE_OK;
+}
+
+extern "C" int fe_he_poly_act(fe_ctx* c, const fe_evk* evk, double a, double b, double cc, const void* in_dev,
+                              uint32_t n, uint32_t level, double in_scale, void* out_dev, double* out_scale, void* ws,
+                              size_t ws_bytes, void* stream) {
+    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(cc)) return fail(FE_EINVAL, "coefficient not finite");
+    double sc = 0;
+    FE_TRY(fe_poly_act_scale(c, level, in_scale, a, &sc));
+    if (a != 0 && (!evk || !evk->relin)) return fail(FE_EKEY, "no relinearisation key");
+    if (ws_bytes < fe_poly_act_workspace_bytes(c, n, level)) return fail(FE_ENOMEM, "workspace too small");
+    if (out_scale) *out_scale = sc;
+    if (n == 0) return FE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nl = level + 1;
+    const double s = in_scale, ql = (double)c->mod[level];
+    Carver cv(ws, ws_bytes);
+    u64* u = cv.take<u64>((size_t)n * ct_words(c, level));
+    u64* v = cv.take<u64>((size_t)n * ct_words(c, level));
+    u64* rs = cv.take<u64>(rescale_tmp_words(c, n, level));
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
+    AffineConsts k{};
+    if (a != 0) {
+        // a x^2 + b x + c = a [(x + beta)^2 + gamma]: shift, square, scale by sign(a) and add
+        const double beta = b / (2.0 * a);
+        const double gamma = cc / a - beta * beta;
+        const bool neg = a < 0;
+        for (int i = 0; i < nl; i++) {
+            k.mul[i] = 1;
+            k.add[i] = nearest_mod(beta * s, c->mod[i]);
+        }
+        FE_TRY(launch_affine(c, (const u64*)in_dev, u, n, level, k, false, st));
+        FE_TRY(square_relin(c, evk, u, (int)n, (int)level, v, cv, st));
+        for (int i = 0; i < nl; i++) {
+            const u64 q = c->mod[i], g = nearest_mod(gamma * (s * s), q);
+            k.mul[i] = neg ? q - 1 : 1;
+            k.add[i] = neg && g ? q - g : g;
+        }
+        FE_TRY(launch_affine(c, v, v, n, level, k, neg, st));
+    } else {
+        // b x + c: times the integer nearest b q_l, plus the integer nearest c s q_l
+        for (int i = 0; i < nl; i++) {
+            k.mul[i] = nearest_mod(b * ql, c->mod[i]);
+            k.add[i] = nearest_mod(cc * (s * ql), c->mod[i]);
+        }
+        FE_TRY(launch_affine(c, (const u64*)in_dev, v, n, level, k, true, st));
+    }
+    rescale_batch(c, v, n, level, (u64*)out_dev, rs, rs + 2 * (size_t)n * c->N, st);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_weight_scale(const fe_ctx* c, uint32_t level, double s_in, double delta, double act_a,
+                               double* w_scale) {
+    if (!c || !w_scale) return fail(FE_EINVAL, "null argument");
+    if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "a linear layer needs a level to rescale");
+    if (!(s_in > 0) || !(delta > 0) || !std::isfinite(act_a)) return fail(FE_EINVAL, "bad scale");
+    const double t = act_a != 0 ? std::sqrt(delta * (double)c->mod[level - 1] * std::fabs(act_a)) : delta;
+    *w_scale = (t / s_in) * (double)c->mod[level];
     return FE_OK;
 }
 
@@ -147,16 +283,12 @@ extern "C" size_t fe_compress_workspace_bytes(const fe_ctx* c, uint32_t n, uint3
     return ks_scratch_bytes(c, n, level) + 2 * (size_t)n * ct_words(c, level) * 8 + 8 * 256;
 }
 
-extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid, const void* in_dev,
-                           uint32_t n, uint32_t level, void* out_dev, void* ws, size_t ws_bytes, void* stream) {
-    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
-    if (!c || !evk || !lay || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
-    if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
-    fe_layout L = *lay;
-    FE_TRY(layout_fill(c->N, &L));
-    if (c_valid == 0 || L.cpc % c_valid) return fail(FE_EINVAL, "c_valid must divide cpc");
-    if (ws_bytes < fe_compress_workspace_bytes(c, n, level)) return fail(FE_ENOMEM, "workspace too small");
-    cudaStream_t st = (cudaStream_t)stream;
+namespace fe {
+namespace {
+// rotate-and-add replication of the c_valid valid channel blocks (Fig. 6) on n
+// ciphertexts at `level`; the layout L is filled and validated by the caller
+int compress_core(fe_ctx* c, const fe_evk* evk, const fe_layout& L, uint32_t c_valid, const void* in_dev, uint32_t n,
+                  uint32_t level, void* out_dev, void* ws, size_t ws_bytes, cudaStream_t st) {
     const size_t ctw = ct_words(c, level);
     if (n == 0) return FE_OK;
     std::vector<int32_t> steps;
@@ -206,6 +338,68 @@ extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, u
     FE_CUDA_TRY(cudaGetLastError());
     return FE_OK;
 }
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_compress(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid, const void* in_dev,
+                           uint32_t n, uint32_t level, void* out_dev, void* ws, size_t ws_bytes, void* stream) {
+    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !evk || !lay || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
+    fe_layout L = *lay;
+    FE_TRY(layout_fill(c->N, &L));
+    if (c_valid == 0 || L.cpc % c_valid) return fail(FE_EINVAL, "c_valid must divide cpc");
+    if (ws_bytes < fe_compress_workspace_bytes(c, n, level)) return fail(FE_ENOMEM, "workspace too small");
+    return compress_core(c, evk, L, c_valid, in_dev, n, level, out_dev, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+namespace fe {
+namespace {
+// 0/1 slot vector of the valid channel blocks: slot < c_valid m^2 BS
+__global__ void k_aac_mask(double* slots, int n_one, int half) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < half) slots[i] = i < n_one ? 1.0 : 0.0;
+}
+}  // namespace
+}  // namespace fe
+
+extern "C" size_t fe_compress_masked_workspace_bytes(const fe_ctx* c, uint32_t n, uint32_t level) {
+    if (!c) return 0;
+    return fe_compress_workspace_bytes(c, n, level) + (size_t)n * ct_words(c, level) * 8 +
+           (size_t)(level + 1) * c->N * 8 + (size_t)c->N / 2 * 8 + 4 * 256;
+}
+
+extern "C" int fe_compress_masked(fe_ctx* c, const fe_evk* evk, const fe_layout* lay, uint32_t c_valid,
+                                  double mask_scale, const void* in_dev, uint32_t n, uint32_t level, double in_scale,
+                                  void* out_dev, double* out_scale, void* ws, size_t ws_bytes, void* stream) {
+    FE_ALIGNED(in_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !evk || !lay || !in_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
+    if (!(mask_scale >= 1) || !(in_scale > 0)) return fail(FE_EINVAL, "bad scale");
+    fe_layout L = *lay;
+    FE_TRY(layout_fill(c->N, &L));
+    if (c_valid == 0 || L.cpc % c_valid) return fail(FE_EINVAL, "c_valid must divide cpc");
+    if (ws_bytes < fe_compress_masked_workspace_bytes(c, n, level)) return fail(FE_ENOMEM, "workspace too small");
+    if (out_scale) *out_scale = in_scale * mask_scale;
+    if (n == 0) return FE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ctw = ct_words(c, level);
+    Carver cv(ws, ws_bytes);
+    u64* masked = cv.take<u64>((size_t)n * ctw);
+    u64* pt = cv.take<u64>((size_t)(level + 1) * c->N);
+    double* slots = cv.take<double>((size_t)c->N / 2);
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
+    const int half = c->N / 2;
+    k_aac_mask<<<(half + kB - 1) / kB, kB, 0, st>>>(slots, (int)(c_valid * L.m * L.m * L.BS), half);
+    c->cnt.launches++;
+    FE_TRY(encode_batch(c, slots, 1, (int)level, mask_scale, pt, st));
+    for (uint32_t i = 0; i < n; i++)
+        launch_pmult(c, (const u64*)in_dev + i * ctw, pt, masked + i * ctw, 1, (int)level, false, st);
+    c->cnt.pmult += n;
+    return compress_core(c, evk, L, c_valid, masked, n, level, out_dev, (char*)ws + (ws_bytes - cv.left),
+                         cv.left, st);
+}
+
 
 namespace {
 // shared data region of a captured sequence: the largest default data region

@@ -49,6 +49,7 @@ struct fe_plan {
     int mac_ways = 4;  // outputs sharing one MAC item (ciphertext loads), 1, 2 or 4
     int dhoist = 0;    // 1: double hoisting (rotations and MAC on Q_l * P, one ModDown per sum)
     std::vector<int32_t> steps;
+    double w_scale = 0;  // scale of the loaded weights (0 until fe_plan_load_weights)
 };
 
 namespace fe {

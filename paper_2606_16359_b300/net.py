@@ -207,18 +207,21 @@ class MobileNetBlocks:
 
 class LeNet:
     """LeNet-5-shaped encrypted network at the largest slot batch for S = 4
-    (BS = N / 2 / 64).  Scales are tracked in IEEE double exactly as the layers
-    change them: PMult multiplies by the weight scale, CMult squares, rescale
-    divides by the dropped prime."""
+    (BS = N / 2 / 64): conv, act, pool, conv, act, pool, FC x3.  The activation
+    is a x^2 + b x + c (act = (a, b, c); x^2 by default).  The library fixes
+    every scale: each linear layer's weight scale (fe_weight_scale, with the
+    next activation's a), the scale after it (fe_plan_out_scale) and after the
+    activation (fe_poly_act_scale); this class only passes them along."""
 
-    def __init__(self, ctx, delta, weights, S=4, key_seed=7):
+    def __init__(self, ctx, delta, weights, S=4, key_seed=7, act=(1.0, 0.0, 0.0)):
         self.ctx, self.delta, self.S = ctx, delta, S
+        self.act = tuple(float(v) for v in act)
+        a = self.act[0]
         self.BS = ctx.N // 2 // 64
         L = ctx.L
         if L < 7:
             raise ValueError("the network needs 7 levels")
         self.lay0 = ctx.layout(28, 28, 1, self.BS, S)
-        q = ctx.moduli
         # plans
         self.p1 = ctx.plan_conv(self.lay0, 6, 5, level=L)
         l1 = self.p1.out_layout
@@ -226,53 +229,35 @@ class LeNet:
         self.p2 = ctx.plan_conv(lp1, 16, 5, level=L - 2)
         l2 = self.p2.out_layout
         lp2 = ctx.layout(l2.H // 2, l2.W // 2, l2.C, l2.BS, l2.S // 2, l2.m)
-        assert lp2.S == 1
-        self.P = P = lp2.cpc * lp2.m * lp2.m
-        m = lp2.m
-        feat1 = np.full((lp2.n_ct, P), -1, dtype=np.int32)
-        for cc in range(lp2.n_ct):
-            for p in range(P):
-                c_loc, kk = divmod(p, m * m)
-                c = cc * lp2.cpc + c_loc
-                bi, bj = divmod(kk, m)
-                if c < lp2.C and bi < lp2.H and bj < lp2.W:
-                    feat1[cc, p] = (c * lp2.H + bi) * lp2.W + bj
-        self.f1 = ctx.plan_fc(lp2.n_ct, P, self.BS, feat1, 256, 120, L - 4)
-        n1 = self.f1.info.n_out_ct
-        feat2 = np.array([[c * P + p if c * P + p < 120 else -1 for p in range(P)] for c in range(n1)], np.int32)
-        self.f2 = ctx.plan_fc(n1, P, self.BS, feat2, 120, 84, L - 5)
-        n2 = self.f2.info.n_out_ct
-        feat3 = np.array([[c * P + p if c * P + p < 84 else -1 for p in range(P)] for c in range(n2)], np.int32)
-        self.f3 = ctx.plan_fc(n2, P, self.BS, feat3, 84, 10, L - 6)
+        self.f1 = ctx.plan_fc_layout(lp2, 120, L - 4)
+        self.f2 = ctx.plan_fc_next(self.f1, 84, L - 5)
+        self.f3 = ctx.plan_fc_next(self.f2, 10, L - 6)
         self.lp1, self.lp2 = lp1, lp2
         steps = sorted({s for p in (self.p1, self.p2, self.f1, self.f2, self.f3) for s in p.steps})
         self.sk = ctx.sk_gen(key_seed)
-        self.evk = ctx.evk_gen(self.sk, key_seed, steps, relin=True)
+        self.evk = ctx.evk_gen(self.sk, key_seed, steps, relin=a != 0)
         # weights and scales (input scale delta at level L)
-        s = delta
-        w1 = ctx.weight_scale(L, s, delta, True)
-        self.pt1 = ctx.load_weights(self.p1, weights["conv1"], w1)
-        s = (s * w1) / float(q[L])          # conv1
-        s = (s * s) / float(q[L - 1])       # x^2
-        w2 = ctx.weight_scale(L - 2, s, delta, True)
-        self.pt2 = ctx.load_weights(self.p2, weights["conv2"], w2, wmul=0.25)
-        s = (s * w2) / float(q[L - 2])      # conv2
-        s = (s * s) / float(q[L - 3])       # x^2
-        w3 = ctx.weight_scale(L - 4, s, delta, False)
-        self.ptf1 = ctx.load_weights(self.f1, weights["fc1"], w3, wmul=0.25)
-        s = (s * w3) / float(q[L - 4])
-        w4 = ctx.weight_scale(L - 5, s, delta, False)
-        self.ptf2 = ctx.load_weights(self.f2, weights["fc2"], w4)
-        s = (s * w4) / float(q[L - 5])
-        w5 = ctx.weight_scale(L - 6, s, delta, False)
-        self.ptf3 = ctx.load_weights(self.f3, weights["fc3"], w5)
-        s = (s * w5) / float(q[L - 6])
-        self.out_scale = s
+        s = self.in_scale = delta
+        self.pt1 = ctx.load_weights(self.p1, weights["conv1"], ctx.weight_scale(L, s, delta, a))
+        s = ctx.plan_out_scale(self.p1, s)
+        self.s_act1 = s
+        s = ctx.poly_act_scale(L - 1, s, a)
+        self.pt2 = ctx.load_weights(self.p2, weights["conv2"], ctx.weight_scale(L - 2, s, delta, a), wmul=0.25)
+        s = ctx.plan_out_scale(self.p2, s)
+        self.s_act2 = s
+        s = ctx.poly_act_scale(L - 3, s, a)
+        self.ptf1 = ctx.load_weights(self.f1, weights["fc1"], ctx.weight_scale(L - 4, s, delta), wmul=0.25)
+        s = ctx.plan_out_scale(self.f1, s)
+        self.ptf2 = ctx.load_weights(self.f2, weights["fc2"], ctx.weight_scale(L - 5, s, delta))
+        s = ctx.plan_out_scale(self.f2, s)
+        self.ptf3 = ctx.load_weights(self.f3, weights["fc3"], ctx.weight_scale(L - 6, s, delta))
+        self.out_scale = ctx.plan_out_scale(self.f3, s)
         self.ws = ctx.workspace(max(p.info.workspace_bytes for p in (self.p1, self.p2, self.f1, self.f2, self.f3)))
 
     def serve_ops(self):
-        """Operation chain of the whole network for the request loop."""
+        """Operation chain of the whole network for the request loop (x^2 activation)."""
         from . import OP_LAYER, OP_POOL, OP_SQUARE
+        assert self.act == (1.0, 0.0, 0.0), "the request loop runs the x^2 activation"
         return [(OP_LAYER, self.p1, self.pt1), (OP_SQUARE,), (OP_POOL, self.p1.out_layout),
                 (OP_LAYER, self.p2, self.pt2), (OP_SQUARE,), (OP_POOL, self.p2.out_layout),
                 (OP_LAYER, self.f1, self.ptf1), (OP_LAYER, self.f2, self.ptf2), (OP_LAYER, self.f3, self.ptf3)]
@@ -284,19 +269,15 @@ class LeNet:
     def forward(self, ct, mode=1):
         c, L = self.ctx, self.ctx.L
         h = c.he_conv(self.evk, self.p1, self.pt1, ct, mode=mode, ws=self.ws)
-        h = c.he_square(self.evk, h, L - 1)
+        h, _ = c.he_poly_act(self.evk, h, L - 1, self.s_act1, *self.act)
         h, _ = c.he_avgpool(self.p1.out_layout, h, L - 2)
         h = c.he_conv(self.evk, self.p2, self.pt2, h, mode=mode, ws=self.ws)
-        h = c.he_square(self.evk, h, L - 3)
+        h, _ = c.he_poly_act(self.evk, h, L - 3, self.s_act2, *self.act)
         h, _ = c.he_avgpool(self.p2.out_layout, h, L - 4)
         h = c.he_fc(self.evk, self.f1, self.ptf1, h, mode=mode, ws=self.ws)
         h = c.he_fc(self.evk, self.f2, self.ptf2, h, mode=mode, ws=self.ws)
         return c.he_fc(self.evk, self.f3, self.ptf3, h, mode=mode, ws=self.ws)
 
     def decode_logits(self, out_ct):
-        slots = self.ctx.decrypt(self.sk, out_ct, self.ctx.L - 7, self.out_scale).cpu().numpy()
-        y = np.zeros((self.BS, 10))
-        for n in range(10):
-            t, p = divmod(n, self.P)
-            y[:, n] = slots[t][p * self.BS:(p + 1) * self.BS]
-        return y
+        slots = self.ctx.decrypt(self.sk, out_ct, self.ctx.L - 7, self.out_scale)
+        return self.ctx.fc_unpack(self.f3, slots, self.BS, 10).cpu().numpy()
