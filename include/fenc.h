@@ -134,6 +134,15 @@ void fe_ctx_destroy(fe_ctx* ctx);
  * 2^16, other ring degrees stay at 8).  Results do not depend on it.
  * Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
+/* Butterfly product of the inverse NTT when every modulus is below 2^36:
+ * enable = 1 (default) takes Shoup's product in 32-bit pieces with the quotient
+ * against floor(w 2^63 / q) (ten 32-bit multiply instructions, exact for inputs
+ * below 2^42); 0 takes the general 64-bit form everywhere.  The forward
+ * transform keeps the general form (it measured faster there).  Results do not
+ * depend on it; other moduli always take the general form.  enable = 2 is as 1
+ * and makes the butterfly probe (fe_probe_butterflies) run the 32-bit-piece
+ * form instead of the forward transform's.  Errors: FE_EINVAL. */
+int fe_ctx_set_ntt_q36(fe_ctx* ctx, int enable);
 /* Generator behind every sampler of the context (secret key, encryption
  * randomness and errors, evaluation keys).  Each sample is drawn from word n of
  * a stream addressed by (seed, tag):

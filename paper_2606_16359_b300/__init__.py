@@ -118,6 +118,7 @@ SIGNATURES = {
     "fe_ctx_set_generator": (cint, [vp, cint, P(u32)]),
     "fe_evk_upload": (cint, [vp, vp, sz, P(i32), u32, cint, vp, sz, vp, P(vp)]),
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
+    "fe_ctx_set_ntt_q36": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -414,6 +415,9 @@ class Context:
 
     def set_ntt_radix(self, radix):
         check(load().fe_ctx_set_ntt_radix(self.handle, radix))
+
+    def set_ntt_q36(self, enable):
+        check(load().fe_ctx_set_ntt_q36(self.handle, int(enable)))
 
     # -- primitives ------------------------------------------------------------------
     def ntt(self, data, first_mod=0, inverse=False):

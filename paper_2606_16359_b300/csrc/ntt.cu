@@ -52,6 +52,51 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wq, u64 q) {
     return a * w - __umul64hi(a, wq) * q;  // in [0, 2q)
 }
 
+// Shoup's product (Shoup; lazy form of Harvey, "Faster arithmetic for
+// number-theoretic transforms", 2014) for moduli below 2^36 and inputs
+// a < 2^42, from 32-bit multiply-adds only:
+//   quotient  Q = floor(a wq63 / 2^63), wq63 = floor(w 2^63 / q) = wq >> 1;
+//   result    T = a w - Q q  (mod 2^64), in [0, 2q) since a < 2^63.
+// With a = a1 2^32 + a0 (a1 < 2^10) and wq63 = h 2^32 + l (h < 2^31):
+//   Z = a0 h + a1 l + floor(a0 l / 2^32) < 2^63 + 2^43 (no 64-bit overflow),
+//   Q = 2 a1 h + floor(Z / 2^31)   (exact: the dropped a0 l mod 2^32 term
+//   cannot carry past a multiple of 2^31 in Z 2^32 + (a0 l mod 2^32)),
+// and T = a w + Q (2^64 - q) mod 2^64 takes two widening multiply-adds for its
+// low 64 bits and four 32-bit multiply-adds for the cross terms of its high
+// word.  Ten integer multiply instructions against the general form's
+// 64 x 64 high product and two 64-bit low products.
+__device__ __forceinline__ u64 shoup36(u64 a, u64 w, u64 wq, u64 nq) {
+    u64 T;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, l, h, h2, t, w0, w1, n0, n1, q0, q1, tl, th;\n\t"
+        ".reg .u64 Z, W63;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "shr.u64 W63, %3, 1;\n\t"
+        "mov.b64 {l, h}, W63;\n\t"
+        "shl.b32 h2, h, 1;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.hi.u32 t, a0, l;\n\t"
+        "cvt.u64.u32 Z, t;\n\t"
+        "mad.wide.u32 Z, a0, h, Z;\n\t"
+        "mad.wide.u32 Z, a1, l, Z;\n\t"
+        "shr.u64 Z, Z, 31;\n\t"
+        "mad.wide.u32 Z, a1, h2, Z;\n\t"
+        "mov.b64 {q0, q1}, Z;\n\t"
+        "mul.wide.u32 %0, a0, w0;\n\t"
+        "mad.wide.u32 %0, q0, n0, %0;\n\t"
+        "mov.b64 {tl, th}, %0;\n\t"
+        "mad.lo.u32 th, a0, w1, th;\n\t"
+        "mad.lo.u32 th, a1, w0, th;\n\t"
+        "mad.lo.u32 th, q0, n1, th;\n\t"
+        "mad.lo.u32 th, q1, n0, th;\n\t"
+        "mov.b64 %0, {tl, th};\n\t"
+        "}"
+        : "=l"(T)
+        : "l"(a), "l"(w), "l"(wq), "l"(nq));
+    return T;
+}
+
 // One line transform round: `lo` = log2 of the round's smallest distance (s),
 // `nst` = number of stages (distances s * 2^(nst-1) .. s), thread holds
 // v[r] = line[base + r s] for r < E (E = min(8, line length)), base = blk 8 s + off.
@@ -62,11 +107,15 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wq, u64 q) {
 // kNoRed (forward only, all moduli < 2^58): no reduction inside the transform;
 // each stage adds less than 2q, so values stay below (1 + 2 * 17) q < 2^64.
 // kLE = log2 of the elements a thread holds per round (3: radix 8, 4: radix 16).
-template <bool kInv, bool kNoRed, int kLE>
+template <bool kInv, bool kNoRed, int kLE, bool kQ36 = false>
 __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo, int nst, int E, int logn,
                                              int tw_line, const ulonglong2* __restrict__ tw, u64 q) {
     constexpr int kEE = 1 << kLE, kHalf = kEE / 2;
-    const u64 q2 = 2 * q;
+    const u64 q2 = 2 * q, nq = 0 - q;
+    auto mulw = [&](u64 a, const ulonglong2& ww) -> u64 {
+        if constexpr (kQ36) return shoup36(a, ww.x, ww.y, nq);
+        else return shoup_lazy(a, ww.x, ww.y, q);
+    };
 #pragma unroll
     for (int si = 0; si < kLE; si++) {
         const int st = kInv ? si : kLE - 1 - si;  // forward: large distances first
@@ -86,14 +135,14 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
             if (!kInv) {
                 u64 X = v[r];
                 if (!kNoRed) X = X >= q2 ? X - q2 : X;
-                const u64 T = shoup_lazy(v[r + d], ww.x, ww.y, q);
+                const u64 T = mulw(v[r + d], ww);
                 v[r] = X + T;
                 v[r + d] = X - T + q2;
             } else {
                 const u64 X = v[r], Y = v[r + d];
                 u64 S = X + Y;
                 v[r] = S >= q2 ? S - q2 : S;
-                v[r + d] = shoup_lazy(X - Y + q2, ww.x, ww.y, q);
+                v[r + d] = mulw(X - Y + q2, ww);
             }
         }
     }
@@ -103,7 +152,7 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
 // kLogN > 0 fixes the ring degree at compile time so that the tile geometry, the
 // round structure and every shift fold into constants; kLogN = 0 reads it at run time.
 // CTAs of kTile / 2^kLE threads; the bound lets 9 radix-8 CTAs (36 warps) share an SM
-template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE>
+template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE, bool kQ36>
 __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttArgs a, int first) {
     constexpr int kEE = 1 << kLE;
     extern __shared__ u64 tile[];
@@ -198,7 +247,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
                 const int x = base + (r << lo);
                 v[r] = (r < E) ? (kCol ? tile[CIDX(x, line)] : tile[RIDX(line, x)]) : 0;
             }
-            round_stages<kInv, kNoRed, kLE>(v, blk, lo, nst, E, logn, tw_line, tw, q);
+            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q);
         }
         __syncthreads();
         if (tid < nthr) {
@@ -219,7 +268,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
     const u64 qinv64 = a.mods[mi].ratio_hi;  // floor(2^64 / q)
     auto fin = [&](u64 x) -> u64 {
         if (!last_pass) return x;
-        if (kInv) x = shoup_lazy(x, ni, nis, q);          // [0, 2q)
+        if (kInv) x = kQ36 ? shoup36(x, ni, nis, 0 - q) : shoup_lazy(x, ni, nis, q);  // [0, 2q)
         else if (kNoRed) x -= __umul64hi(x, qinv64) * q;  // [0, 2q)
         else x = x >= q2 ? x - q2 : x;
         return x >= q ? x - q : x;
@@ -254,6 +303,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttAr
 // of modulus 0, which stay in L1) followed by the reduction the transform applies
 // once per element; no tile traffic.  One word per thread is written so that the
 // work is kept.  Butterflies executed = blocks * 256 * iters * 60.
+template <bool kQ36>
 __global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __restrict__ tw, u64 q, u64 qinv64,
                                                          int iters, u64* out) {
     u64 v[kE];
@@ -263,7 +313,7 @@ __global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __res
 #pragma unroll 1
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int k = 0; k < 5; k++) round_stages<false, true, 3>(v, 0, 0, 3, kE, 3, 1, tw, q);
+        for (int k = 0; k < 5; k++) round_stages<false, true, 3, kQ36>(v, 0, 0, 3, kE, 3, 1, tw, q);
 #pragma unroll
         for (int r = 0; r < kE; r++) v[r] -= __umul64hi(v[r], qinv64) * q;
     }
@@ -294,30 +344,36 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
 int threads_for(int lines, int n, int E) { return std::max(32, lines * (n / std::min(E, n))); }
 
 template <int kLogN, bool kInv, bool kCol, int kLE = 3>
-void launch_one(bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
-    if (nored && !kInv)
-        ntt_pass<kLogN, kInv, kCol, true, kLE><<<g, t, sm, st>>>(a, first);
-    else
-        ntt_pass<kLogN, kInv, kCol, false, kLE><<<g, t, sm, st>>>(a, first);
+void launch_one(bool nored, bool q36, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
+    if (q36) {
+        if (nored && !kInv)
+            ntt_pass<kLogN, kInv, kCol, true, kLE, true><<<g, t, sm, st>>>(a, first);
+        else
+            ntt_pass<kLogN, kInv, kCol, false, kLE, true><<<g, t, sm, st>>>(a, first);
+    } else if (nored && !kInv) {
+        ntt_pass<kLogN, kInv, kCol, true, kLE, false><<<g, t, sm, st>>>(a, first);
+    } else {
+        ntt_pass<kLogN, kInv, kCol, false, kLE, false><<<g, t, sm, st>>>(a, first);
+    }
 }
 
 // compile-time ring degrees for the production sizes, run-time geometry otherwise
 // radix 16 (le = 4) is compiled for the production ring degrees 2^14 and 2^16
 template <bool kInv, bool kCol>
-void launch_pass(int logN, bool nored, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first,
-                 int le) {
-    if (le == 4 && logN == 16) return launch_one<16, kInv, kCol, 4>(nored, g, t, sm, st, a, first);
-    if (le == 4 && logN == 14) return launch_one<14, kInv, kCol, 4>(nored, g, t, sm, st, a, first);
+void launch_pass(int logN, bool nored, bool q36, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a,
+                 int first, int le) {
+    if (le == 4 && logN == 16) return launch_one<16, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
+    if (le == 4 && logN == 14) return launch_one<14, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
     switch (logN) {
-        case 10: launch_one<10, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 11: launch_one<11, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 12: launch_one<12, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 13: launch_one<13, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 14: launch_one<14, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 15: launch_one<15, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 16: launch_one<16, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        case 17: launch_one<17, kInv, kCol>(nored, g, t, sm, st, a, first); break;
-        default: launch_one<0, kInv, kCol>(nored, g, t, sm, st, a, first); break;
+        case 10: launch_one<10, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 11: launch_one<11, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 12: launch_one<12, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 13: launch_one<13, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 14: launch_one<14, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 15: launch_one<15, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 16: launch_one<16, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        case 17: launch_one<17, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
+        default: launch_one<0, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
     }
 }
 
@@ -334,24 +390,28 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const int le = (c->ntt_radix == 16 && (c->logN == 14 || c->logN == 16)) ? 4 : 3;
     const int tc = threads_for(C, N1, 1 << le), tr = threads_for(R, N2, 1 << le);
     const bool nored = c->max_mod_bits <= 58;
+    // every modulus below 2^36: the 36-bit Shoup product in the inverse passes (inputs below
+    // 4 q, within its 2^42 bound).  Measured on B300 (N = 2^16, 532 limbs): inverse 0.932 ->
+    // 0.908 us per limb; the forward passes were 1.6 % slower with it and keep the general form.
+    const bool q36 = kInv && c->max_mod_bits <= 36 && c->ntt_q36;
     const dim3 gc(limbs * (N2 / C)), gr(limbs * (N1 / R));
     if (!kInv) {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, true>(c->logN, nored, gc, tc, smc, st, a, 1, le);
+            launch_pass<false, true>(c->logN, nored, q36, gc, tc, smc, st, a, 1, le);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, false>(c->logN, nored, gr, tr, smr, st, a, 0, le);
+            launch_pass<false, false>(c->logN, nored, q36, gr, tr, smr, st, a, 0, le);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, false>(c->logN, false, gr, tr, smr, st, a, 1, le);
+            launch_pass<true, false>(c->logN, false, q36, gr, tr, smr, st, a, 1, le);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, true>(c->logN, false, gc, tc, smc, st, a, 0, le);
+            launch_pass<true, true>(c->logN, false, q36, gc, tc, smc, st, a, 0, le);
         }
     }
     c->cnt.ntt += limbs;
@@ -364,10 +424,15 @@ int butterfly_probe(fe_ctx* c, uint32_t* blocks, uint32_t iters, u64* out, cudaS
     const Modulus m = make_modulus(c->mod[0]);
     if (*blocks == 0) {  // one full wave: every SM holds as many CTAs as fit
         int per_sm = 0;
-        FE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_butterfly_probe, 256, 0));
+        FE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_butterfly_probe<false>, 256, 0));
         *blocks = (uint32_t)(std::min(per_sm, 8) * c->n_sm);
     }
-    k_butterfly_probe<<<*blocks, 256, 0, st>>>((const ulonglong2*)c->d_tw2, m.q, m.ratio_hi, (int)iters, out);
+    // the forward transform's butterfly (the general form; fe_ctx_set_ntt_q36(ctx, 2) probes
+    // the 36-bit form the inverse passes use)
+    if (c->max_mod_bits <= 36 && c->ntt_q36 == 2)
+        k_butterfly_probe<true><<<*blocks, 256, 0, st>>>((const ulonglong2*)c->d_tw2, m.q, m.ratio_hi, (int)iters, out);
+    else
+        k_butterfly_probe<false><<<*blocks, 256, 0, st>>>((const ulonglong2*)c->d_tw2, m.q, m.ratio_hi, (int)iters, out);
     c->cnt.launches += 1;
     return cudaGetLastError() == cudaSuccess ? FE_OK : fail(FE_ECUDA, "butterfly probe launch");
 }
@@ -382,6 +447,13 @@ void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSe
 }
 
 }  // namespace fe
+
+extern "C" int fe_ctx_set_ntt_q36(fe_ctx* c, int enable) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (enable < 0 || enable > 2) return fe::fail(FE_EINVAL, "enable must be 0, 1 or 2");
+    c->ntt_q36 = enable;
+    return FE_OK;
+}
 
 extern "C" int fe_ctx_set_ntt_radix(fe_ctx* c, int radix) {
     if (!c) return fe::fail(FE_EINVAL, "null argument");

@@ -43,6 +43,7 @@ def _events(torch):
 
 def bench_ntt(ctx, torch, args):
     ctx.set_ntt_radix(args.radix)
+    ctx.set_ntt_q36(args.q36)
     N, nm = ctx.N, ctx.n_mod
     n_poly = max(1, (args.limbs + nm - 1) // nm)
     limbs = n_poly * nm
@@ -68,11 +69,12 @@ def bench_ntt(ctx, torch, args):
     peak, src = hbm_peak()
     for v in out.values():
         v["hbm_frac"] = v["GBps"] / peak
-    return {"kernel": "ntt", "radix": args.radix, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
+    return {"kernel": "ntt", "radix": args.radix, "q36": args.q36, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
             "peak_GBps": peak, "peak_source": src, **out}
 
 
 def bench_alu(ctx, torch, args):
+    ctx.set_ntt_q36(args.q36)
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     buf = torch.empty(n_sm * 8 * 256, dtype=torch.int64, device="cuda")
     ctx.probe_butterflies(buf, 0, max(1, args.iters // 10))
@@ -83,7 +85,7 @@ def bench_alu(ctx, torch, args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    return {"kernel": "butterfly_probe", "blocks": n // (256 * 60 * args.iters), "threads": 256,
+    return {"kernel": "butterfly_probe", "q36": args.q36, "blocks": n // (256 * 60 * args.iters), "threads": 256,
             "iters": args.iters, "butterflies": n, "ms": ms, "Gbutterfly_per_s": n / (ms / 1e3) / 1e9}
 
 
@@ -302,6 +304,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--level", type=int, default=22)
     ap.add_argument("--radix", type=int, default=8, help="NTT elements per thread per round (8 or 16)")
+    ap.add_argument("--q36", type=int, default=1, help="36-bit Shoup product in the inverse NTT (1, default), nowhere (0), or also in the probe (2)")
     ap.add_argument("--channels", type=int, default=128, help="channels of the layer case")
     ap.add_argument("--hw", type=int, default=14, help="map height = width of the layer case")
     ap.add_argument("--dw", action="store_true", help="layer case: depthwise 3x3 instead of pointwise")

@@ -598,3 +598,32 @@ def test_ntt_radix16_equals_radix8_and_oracle(logN):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[1][1], a)
     for t in range(pr.n_mod if hasattr(pr, "n_mod") else len(pr.moduli)):
         assert np.array_equal(outs[1][0][t], pr.ntt(a[t], t))
+
+
+@pytest.mark.parametrize("logN,radix", [(11, 8), (14, 16), (16, 8), (16, 16)])
+def test_ntt_36bit_shoup_form_equals_general_form_and_oracle(logN, radix):
+    """With every modulus below 2^36 the transforms take the Shoup product in
+    32-bit pieces (fe_ctx_set_ntt_q36); it gives the residues of the general
+    64-bit form and of the oracle, forward and inverse, including inputs at
+    q - 1 everywhere (the largest values the forward transform's lazy stages
+    build up)."""
+    g = fe.Context(logN, 3, 2, 36, 36)
+    pr = ckks.Params(logN, 3, 2, 36, 36)
+    rng = np.random.default_rng(logN + radix)
+    rnd = np.stack([rng.integers(0, q, pr.N, dtype=np.uint64) for q in pr.moduli])
+    top = np.stack([np.full(pr.N, q - 1, dtype=np.uint64) for q in pr.moduli])
+    g.set_ntt_radix(radix)
+    for a in (rnd, top):
+        res = []
+        for q36 in (True, False):
+            g.set_ntt_q36(q36)
+            d = to_dev(a[None])
+            g.ntt(d)
+            fwd = u64(d)[0]
+            g.ntt(d, inverse=True)
+            res.append((fwd, u64(d)[0]))
+        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], a) and np.array_equal(res[1][1], a)
+        for t in range(len(pr.moduli)):
+            assert np.array_equal(res[0][0][t], pr.ntt(a[t], t))
+    g.set_ntt_q36(True)
+    g.set_ntt_radix(8)
