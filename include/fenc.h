@@ -341,6 +341,25 @@ int fe_plan_fc_layout(fe_ctx* ctx, const fe_layout* in_lay, uint32_t F_out, uint
  * `prev` (neuron n of prev at position n mod P of ciphertext n / P), with
  * F_in = prev's F_out.  Errors as fe_plan_fc; FE_EINVAL when prev is not FC. */
 int fe_plan_fc_next(fe_ctx* ctx, const fe_plan* prev, uint32_t F_out, uint32_t level, fe_plan** out);
+/* Fragment-size change between layers (Sec. 5, Implementation: a later layer
+ * whose best block size S differs gets its input re-encoded by rot-mask-add).
+ * Plans the re-encoding of ciphertexts in layout `from` into layout `to`
+ * (the same BS x C x H x W map; any S and block grid m on either side) at
+ * `level`: target ciphertext t = sum over source ciphertexts s and position
+ * shifts d of Rot(ct_s, d BS) (x) M_{t,s,d}, M the 0/1 mask of the target
+ * positions whose element sits d positions further in s -- the diagonal method
+ * of the permutation matrix, with baby-step / giant-step rotations whose n1 (a
+ * power of two) minimises the distinct nonzero baby steps per source plus giant
+ * steps per target.  It is an FC-kind plan: fe_plan_load_weights with
+ * weights_host = NULL writes the masks (at w_scale, normally q_level so the
+ * scale is kept), and fe_he_repack (or fe_he_fc, fe_he_layer_batch, graph
+ * capture) runs it; one level is consumed.  Cost grows with the distinct
+ * shifts, i.e. with how far elements move: cheap for small maps and large
+ * batches, costly for large maps at BS = 1.  Errors: FE_EINVAL (layouts of
+ * different maps), FE_ELEVEL. */
+int fe_plan_repack(fe_ctx* ctx, const fe_layout* from, const fe_layout* to, uint32_t level, fe_plan** out);
+int fe_he_repack(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev, const void* in_dev,
+                 void* out_dev, void* workspace_dev, size_t workspace_bytes, int mode, void* stream);
 /* Read a fully connected plan's decrypted output slots back as outputs:
  * y_dev[b][n] (BS x F_out, float64) = slots_dev[n / P][(n mod P) BS + b]
  * (slots_dev: the plan's n_out_ct decoded slot vectors of N/2 doubles).

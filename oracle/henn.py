@@ -463,16 +463,19 @@ def fc_rotation_steps(P, BS):
     return sorted({b * BS for b in range(1, n1)} | {n1 * g * BS for g in range(1, n2)})
 
 
-def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None):
+def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None, n1=None):
     """y = Wfc x.  cts: input ciphertexts; feat_of(c, p) -> feature index or -1 for
     position p of input ciphertext c.  Output neuron n sits in ciphertext n // P at
-    position n % P (for every batch slot)."""
+    position n % P (for every batch slot).  n1: baby steps (default fc_bsgs_split)."""
     cnt = cnt if cnt is not None else Counters()
     level = cts[0].level
     dw = float(pr.moduli[level]) if w_scale is None else w_scale
     F_out = Wfc.shape[0]
     T = -(-F_out // P)
-    n1, n2 = fc_bsgs_split(P)
+    if n1 is None:
+        n1, n2 = fc_bsgs_split(P)
+    else:
+        n2 = P // n1
 
     def diag(t, c, delta):
         z = np.zeros(P)
@@ -535,6 +538,106 @@ def he_fc(pr, keys, cts, feat_of, P, BS, Wfc, *, w_scale=None, cnt=None):
         out.append(ckks.rescale(pr, total))
         cnt.rescale += 1
     return out
+
+
+# ---------------------------------------------------------------------------
+# Fragment-size change between layers (Sec. 5, Implementation paragraph: the
+# rot-mask-add adjustment of the block size S when a later layer's optimal S
+# differs)
+# ---------------------------------------------------------------------------
+
+def element_id(lay, c, h, w):
+    return (c * lay.H + h) * lay.W + w
+
+
+def layout_position(lay, c, h, w):
+    """(ciphertext, position) of element (c, h, w) under Algorithm 1's slot map;
+    the element's BS batch entries occupy slots position * BS + b."""
+    g, c_loc = divmod(c, lay.cpc)
+    ct = lay.ct_index(g, h % lay.S, w % lay.S)
+    return ct, (c_loc * lay.m + h // lay.S) * lay.m + w // lay.S
+
+
+def repack_map(la, lb):
+    """Source (ct, position) under layout la and target (ct, position) under lb
+    of every element (c, h, w) of the map both layouts describe."""
+    assert (la.C, la.H, la.W, la.BS, la.N) == (lb.C, lb.H, lb.W, lb.BS, lb.N)
+    out = []
+    for c in range(la.C):
+        for h in range(la.H):
+            for w in range(la.W):
+                out.append((layout_position(la, c, h, w), layout_position(lb, c, h, w)))
+    return out
+
+
+def repack_shifts(la, lb):
+    """{(target ct, source ct): set of position shifts d = source - target mod P}."""
+    P = la.cpc * la.m * la.m
+    sh = {}
+    for (cs, ps), (ct, pt) in repack_map(la, lb):
+        sh.setdefault((ct, cs), set()).add((ps - pt) % P)
+    return sh
+
+
+def repack_bsgs_n1(la, lb):
+    """Baby-step count of the repack: the power of two n1 <= P that minimises the
+    rotations of the diagonal method, sum over source ciphertexts of their
+    distinct nonzero baby steps (d mod n1) plus sum over target ciphertexts of
+    their distinct nonzero giant steps (d div n1); ties to the smaller n1."""
+    P = la.cpc * la.m * la.m
+    sh = repack_shifts(la, lb)
+    best = None
+    n1 = 1
+    while n1 <= P:
+        baby, giant = {}, {}
+        for (ct, cs), ds in sh.items():
+            for d in ds:
+                if d % n1:
+                    baby.setdefault(cs, set()).add(d % n1)
+                if d // n1:
+                    giant.setdefault(ct, set()).add(d // n1)
+        cost = sum(map(len, baby.values())) + sum(map(len, giant.values()))
+        if best is None or cost < best[1]:
+            best = (n1, cost)
+        n1 *= 2
+    return best[0]
+
+
+def he_repack(pr, keys, cts, la, lb, cnt=None):
+    """Re-encode ciphertexts from fragment layout la to layout lb (same map, other
+    S or block grid): each target position receives its element from its
+    source position, target_t = sum_{source s} sum_d Rot(ct_s, d BS) (x) M_{t,s,d},
+    M_{t,s,d} the 0/1 mask of the target positions whose element sits d positions
+    further in source s -- the diagonal method of a permutation matrix, with
+    baby-step / giant-step rotations (repack_bsgs_n1) and the masks at scale
+    q_level, so one rescale follows and the scale is kept.  Written as the FC
+    layer whose weight matrix is that permutation."""
+    P = la.cpc * la.m * la.m
+    n_out = lb.n_ct
+    F_in = la.C * la.H * la.W
+    W = np.zeros((n_out * P, F_in))
+    feat = {}
+    for (c, h, w), ((cs, ps), (ct, pt)) in zip(
+            ((c, h, w) for c in range(la.C) for h in range(la.H) for w in range(la.W)), repack_map(la, lb)):
+        f = element_id(la, c, h, w)
+        feat[(cs, ps)] = f
+        W[ct * P + pt, f] = 1.0
+    return he_fc(pr, keys, cts, lambda c, p: feat.get((c, p), -1), P, la.BS, W, cnt=cnt,
+                 n1=repack_bsgs_n1(la, lb))
+
+
+def repack_rotation_steps(la, lb):
+    """Rotation steps (slots) the repack needs keys for."""
+    P = la.cpc * la.m * la.m
+    n1 = repack_bsgs_n1(la, lb)
+    steps = set()
+    for (ct, cs), ds in repack_shifts(la, lb).items():
+        for d in ds:
+            if d % n1:
+                steps.add((d % n1) * la.BS)
+            if d // n1:
+                steps.add((d // n1) * n1 * la.BS)
+    return sorted(steps)
 
 
 # ---------------------------------------------------------------------------

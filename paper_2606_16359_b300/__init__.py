@@ -144,6 +144,8 @@ SIGNATURES = {
     "fe_plan_destroy": (None, [vp]),
     "fe_plan_fc_layout": (cint, [vp, P(FeLayout), u32, u32, P(vp)]),
     "fe_plan_fc_next": (cint, [vp, vp, u32, u32, P(vp)]),
+    "fe_plan_repack": (cint, [vp, P(FeLayout), P(FeLayout), u32, P(vp)]),
+    "fe_he_repack": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
     "fe_fc_unpack": (cint, [vp, vp, vp, vp, vp]),
     "fe_weight_scale": (cint, [vp, u32, dbl, dbl, dbl, P(dbl)]),
     "fe_plan_out_scale": (cint, [vp, dbl, P(dbl)]),
@@ -649,6 +651,30 @@ class Context:
         p = Plan(self, h)
         p.level = level
         return p
+
+    def plan_repack(self, lay_from, lay_to, level):
+        """fe_plan_repack: re-encoding from one fragment layout to another (one level)."""
+        h = vp()
+        check(load().fe_plan_repack(self.handle, ctypes.byref(lay_from), ctypes.byref(lay_to), level,
+                                    ctypes.byref(h)))
+        p = Plan(self, h, lay_to)
+        p.level, p.in_layout = level, lay_from
+        return p
+
+    def load_repack_masks(self, plan, w_scale=None):
+        """Encode a repack plan's masks (at q_level unless given)."""
+        torch = _torch()
+        w_scale = float(self.moduli[plan.level]) if w_scale is None else w_scale
+        pt = torch.empty(max(8, plan.info.pt_bytes) // 8, dtype=torch.int64, device="cuda")
+        check(load().fe_plan_load_weights(self.handle, plan.handle, None, 1.0, w_scale, _ptr(pt), _stream()))
+        return pt
+
+    def he_repack(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
+        ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
+        out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        check(load().fe_he_repack(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
+                                  ws.numel() * 8, mode, _stream()))
+        return out
 
     def plan_fc_next(self, prev, F_out, level):
         h = vp()

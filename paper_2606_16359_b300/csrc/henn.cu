@@ -14,6 +14,7 @@
 // An FC plan has the same shape: baby-step rotations of the inputs (1), MAC of
 // the rotated diagonals (2), giant-step rotate-and-sum (3), rescale (4).
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <memory>
 #include <set>
@@ -93,6 +94,33 @@ __global__ void k_fc_pt_slots(FcPtArgs a, double* z, int slots) {
     const int f = a.feat[(size_t)q.c * a.P + (p + q.beta) % a.P];
     double v = 0.0;
     if (n < a.F_out && f >= 0) v = a.W[(size_t)n * a.F_in + f] * a.wmul;
+    z[(size_t)blockIdx.y * slots + l] = v;
+}
+
+// repack mask, rotated for the giant step: z[p BS + b] = 1 when the element at
+// source position (p + beta) mod P of ciphertext c has target (t, (p - n1 gam) mod P)
+struct RepackPtArgs {
+    const fe_plan::FcPt* pts;
+    const int* feat;  // [n_in][P] source element ids
+    fe_layout B;      // target layout
+    int P, BS, n1;
+};
+__global__ void k_repack_pt_slots(RepackPtArgs a, double* z, int slots) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= slots) return;
+    const fe_plan::FcPt q = a.pts[blockIdx.y];
+    const int p = l / a.BS;
+    const int p0 = ((p - a.n1 * q.gam) % a.P + a.P) % a.P;
+    const int f = a.feat[(size_t)q.c * a.P + (p + q.beta) % a.P];
+    double v = 0.0;
+    if (f >= 0) {
+        const fe_layout& B = a.B;
+        const int w = f % (int)B.W, h = (f / (int)B.W) % (int)B.H, ch = f / ((int)B.W * (int)B.H);
+        const int g = ch / (int)B.cpc, c_loc = ch % (int)B.cpc;
+        const int ct = (g * (int)B.S + h % (int)B.S) * (int)B.S + w % (int)B.S;
+        const int pos = (c_loc * (int)B.m + h / (int)B.S) * (int)B.m + w / (int)B.S;
+        if (ct == q.t && pos == p0) v = 1.0;
+    }
     z[(size_t)blockIdx.y * slots + l] = v;
 }
 
@@ -941,13 +969,36 @@ extern "C" int fe_plan_conv(fe_ctx* c, const fe_layout* in_lay, uint32_t Cout, u
     return FE_OK;
 }
 
+namespace fe {
+namespace {
+// FC planner core: diagonal method with baby-step / giant-step over P positions.
+// `sparse` (optional) decides which (t, c, gam, beta) diagonals are nonzero; by
+// default every diagonal with a valid (neuron, feature) pair is planned (dense W).
+// n1 = 0 takes the default split 2^ceil(log2(P) / 2).
+int plan_fc_core(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat, uint32_t F_in,
+                 uint32_t F_out, uint32_t level, const std::function<bool(int, int, int, int)>* sparse,
+                 int n1_req, std::unique_ptr<fe_plan>& p);
+}  // namespace
+}  // namespace fe
+
 extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat,
                           uint32_t F_in, uint32_t F_out, uint32_t level, fe_plan** out) {
     if (!c || !feat || !out) return fail(FE_EINVAL, "null argument");
+    std::unique_ptr<fe_plan> p;
+    FE_TRY(plan_fc_core(c, n_in_ct, P, BS, feat, F_in, F_out, level, nullptr, 0, p));
+    *out = p.release();
+    return FE_OK;
+}
+
+namespace fe {
+namespace {
+int plan_fc_core(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat, uint32_t F_in,
+                 uint32_t F_out, uint32_t level, const std::function<bool(int, int, int, int)>* sparse,
+                 int n1_req, std::unique_ptr<fe_plan>& p) {
     if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "fc needs a level to rescale");
     if ((uint64_t)P * BS != (uint64_t)c->N / 2 || (P & (P - 1)) || !n_in_ct || !F_out)
         return fail(FE_EINVAL, "fc needs P BS = N/2 with P a power of two");
-    std::unique_ptr<fe_plan> p(new fe_plan());
+    p.reset(new fe_plan());
     p->c = c;
     p->kind = 1;
     p->level = level;
@@ -960,12 +1011,14 @@ extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, 
     p->feat.assign(feat, feat + (size_t)n_in_ct * P);
     int kbits = 0;
     while ((1u << kbits) < P) kbits++;
-    p->n1 = 1 << ((kbits + 1) / 2);
+    p->n1 = n1_req > 0 ? n1_req : 1 << ((kbits + 1) / 2);
+    if (p->n1 > (int)P || (p->n1 & (p->n1 - 1))) return fail(FE_EINVAL, "n1 must be a power of two <= P");
     p->n2 = P / p->n1;
     p->n_in = n_in_ct;
     const int T = (F_out + P - 1) / P;
     p->n_out = T;
     auto present = [&](int t, int cc, int gam, int beta) {
+        if (sparse) return (*sparse)(t, cc, gam, beta);
         for (uint32_t q = 0; q < P; q++) {
             int p0 = (((int)q - p->n1 * gam) % (int)P + (int)P) % (int)P;
             int n = t * P + p0;
@@ -1004,16 +1057,12 @@ extern "C" int fe_plan_fc(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, 
         }
     }
     finish_plan(p.get());
-    *out = p.release();
     return FE_OK;
 }
 
-extern "C" int fe_plan_fc_layout(fe_ctx* c, const fe_layout* in_lay, uint32_t F_out, uint32_t level,
-                                 fe_plan** out) {
-    if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
-    fe_layout L = *in_lay;
-    FE_TRY(layout_fill(c->N, &L));
-    // feature (c, h, w) -> (c H + h) W + w, the row-major flattening of a (C, H, W) map
+// feature table of a fragment layout: position p of ciphertext ci holds element
+// (ch, h, w) = (c H + h) W + w, or -1 (padding)
+std::vector<int32_t> layout_features(const fe_layout& L) {
     const uint32_t P = L.cpc * L.m * L.m;
     std::vector<int32_t> feat((size_t)L.n_ct * P, -1);
     for (uint32_t ci = 0; ci < L.n_ct; ci++) {
@@ -1024,7 +1073,81 @@ extern "C" int fe_plan_fc_layout(fe_ctx* c, const fe_layout* in_lay, uint32_t F_
             if (ch < L.C && h < L.H && w < L.W) feat[(size_t)ci * P + p] = (int32_t)((ch * L.H + h) * L.W + w);
         }
     }
-    return fe_plan_fc(c, L.n_ct, P, L.BS, feat.data(), L.C * L.H * L.W, F_out, level, out);
+    return feat;
+}
+
+// (ciphertext, position) of element (ch, h, w) under a fragment layout (Algorithm 1)
+inline void layout_position(const fe_layout& L, uint32_t ch, uint32_t h, uint32_t w, uint32_t* ct, uint32_t* pos) {
+    const uint32_t g = ch / L.cpc, c_loc = ch % L.cpc;
+    *ct = (g * L.S + h % L.S) * L.S + w % L.S;
+    *pos = (c_loc * L.m + h / L.S) * L.m + w / L.S;
+}
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_plan_repack(fe_ctx* c, const fe_layout* from, const fe_layout* to, uint32_t level,
+                              fe_plan** out) {
+    if (!c || !from || !to || !out) return fail(FE_EINVAL, "null argument");
+    if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "the repack needs a level to rescale");
+    fe_layout A = *from, B = *to;
+    FE_TRY(layout_fill(c->N, &A));
+    FE_TRY(layout_fill(c->N, &B));
+    if (A.C != B.C || A.H != B.H || A.W != B.W || A.BS != B.BS)
+        return fail(FE_EINVAL, "both layouts must describe the same (BS, C, H, W) map");
+    const uint32_t P = A.cpc * A.m * A.m;
+    // every element's source and target (ciphertext, position), and the shift d = source - target
+    struct Move {
+        uint32_t cs, ct, d;
+    };
+    std::vector<Move> moves;
+    moves.reserve((size_t)A.C * A.H * A.W);
+    for (uint32_t ch = 0; ch < A.C; ch++)
+        for (uint32_t h = 0; h < A.H; h++)
+            for (uint32_t w = 0; w < A.W; w++) {
+                uint32_t cs, ps, ct, pt;
+                layout_position(A, ch, h, w, &cs, &ps);
+                layout_position(B, ch, h, w, &ct, &pt);
+                moves.push_back({cs, ct, (ps + P - pt) % P});
+            }
+    // baby steps n1: the power of two that minimises distinct nonzero baby steps per
+    // source plus distinct nonzero giant steps per target (ties to the smaller n1)
+    int best_n1 = 1;
+    size_t best = SIZE_MAX;
+    for (uint32_t n1 = 1; n1 <= P; n1 *= 2) {
+        std::set<std::pair<uint32_t, uint32_t>> baby, giant;
+        for (const Move& mv : moves) {
+            if (mv.d % n1) baby.insert({mv.cs, mv.d % n1});
+            if (mv.d / n1) giant.insert({mv.ct, mv.d / n1});
+        }
+        if (baby.size() + giant.size() < best) {
+            best = baby.size() + giant.size();
+            best_n1 = (int)n1;
+        }
+    }
+    std::set<std::tuple<int, int, int, int>> nz;
+    for (const Move& mv : moves)
+        nz.insert({(int)mv.ct, (int)mv.cs, (int)(mv.d / best_n1), (int)(mv.d % best_n1)});
+    std::function<bool(int, int, int, int)> sparse = [&](int t, int cc, int gam, int beta) {
+        return nz.count({t, cc, gam, beta}) != 0;
+    };
+    const std::vector<int32_t> feat = layout_features(A);
+    std::unique_ptr<fe_plan> p;
+    FE_TRY(plan_fc_core(c, A.n_ct, P, A.BS, feat.data(), A.C * A.H * A.W, B.n_ct * P, level, &sparse, best_n1, p));
+    p->repack = 1;
+    p->lin = A;
+    p->lout = B;
+    *out = p.release();
+    return FE_OK;
+}
+
+extern "C" int fe_plan_fc_layout(fe_ctx* c, const fe_layout* in_lay, uint32_t F_out, uint32_t level,
+                                 fe_plan** out) {
+    if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
+    fe_layout L = *in_lay;
+    FE_TRY(layout_fill(c->N, &L));
+    // feature (c, h, w) -> (c H + h) W + w, the row-major flattening of a (C, H, W) map
+    const std::vector<int32_t> feat = layout_features(L);
+    return fe_plan_fc(c, L.n_ct, L.cpc * L.m * L.m, L.BS, feat.data(), L.C * L.H * L.W, F_out, level, out);
 }
 
 extern "C" int fe_plan_fc_next(fe_ctx* c, const fe_plan* prev, uint32_t F_out, uint32_t level, fe_plan** out) {
@@ -1115,15 +1238,20 @@ extern "C" int fe_plan_rotation_steps(const fe_plan* p, int32_t* steps, uint32_t
 extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host, double wmul, double w_scale,
                                     void* pt_dev, void* stream) {
     FE_ALIGNED(pt_dev);
-    if (!c || !p || !W_host || !pt_dev) return fail(FE_EINVAL, "null argument");
-    if (p->n_pt == 0) return FE_OK;
+    if (!c || !p || (!W_host && !p->repack) || !pt_dev) return fail(FE_EINVAL, "null argument");
+    if (p->n_pt == 0) {
+        p->w_scale = w_scale;
+        return FE_OK;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const int N = c->N, half = N / 2, nl = p->level + 1 + (p->dhoist ? c->k : 0);
-    size_t wcount = p->kind == 0 ? (p->depthwise ? (size_t)p->Cin * p->K * p->K : (size_t)p->Cout * p->Cin * p->K * p->K)
-                                 : (size_t)p->F_out * p->F_in;
+    size_t wcount = p->repack ? 1
+                    : p->kind == 0 ? (p->depthwise ? (size_t)p->Cin * p->K * p->K
+                                                   : (size_t)p->Cout * p->Cin * p->K * p->K)
+                                   : (size_t)p->F_out * p->F_in;
     double* dW;
     FE_CUDA_TRY(cudaMallocAsync(&dW, wcount * 8, st));
-    FE_CUDA_TRY(cudaMemcpyAsync(dW, W_host, wcount * 8, cudaMemcpyHostToDevice, st));
+    if (!p->repack) FE_CUDA_TRY(cudaMemcpyAsync(dW, W_host, wcount * 8, cudaMemcpyHostToDevice, st));
     // chunks of plaintexts: slot vectors (<= 64 MiB) and 64-bit limbs (<= 1 GiB)
     // before they are compacted into pt_dev
     const int chunk = std::max(1, std::min({p->n_pt, (int)((64ull << 20) / ((size_t)half * 8)),
@@ -1151,6 +1279,9 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
                          (int)p->lin.cpc, (int)p->lin.H, (int)p->lin.W, p->K, p->stride, p->Cin, p->Cout,
                          p->depthwise, p->in_period};
             k_conv_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
+        } else if (p->repack) {
+            RepackPtArgs a{(const fe_plan::FcPt*)descs + s0, dfeat, p->lout, p->P, p->BS, p->n1};
+            k_repack_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
         } else {
             FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
             k_fc_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
@@ -1185,6 +1316,12 @@ extern "C" int fe_he_fc(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const vo
     if (p->kind != 1) return fail(FE_EINVAL, "not an fc plan");
     return run_plan(c, evk, p, (const u64*)in_dev, (const u64*)pt_dev, (u64*)out_dev, ws, ws_bytes, mode,
                     (cudaStream_t)stream, 3);
+}
+
+extern "C" int fe_he_repack(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,
+                            void* out_dev, void* ws, size_t ws_bytes, int mode, void* stream) {
+    if (p && !p->repack) return fail(FE_EINVAL, "not a repack plan");
+    return fe_he_fc(c, evk, p, pt_dev, in_dev, out_dev, ws, ws_bytes, mode, stream);
 }
 
 extern "C" int fe_he_layer_batch(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const void* pt_dev, const void* in_dev,

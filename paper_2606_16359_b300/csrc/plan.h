@@ -50,6 +50,7 @@ struct fe_plan {
     int dhoist = 0;    // 1: double hoisting (rotations and MAC on Q_l * P, one ModDown per sum)
     std::vector<int32_t> steps;
     double w_scale = 0;  // scale of the loaded weights (0 until fe_plan_load_weights)
+    int repack = 0;      // 1: an FC-kind plan whose weights are the permutation from lin to lout
 };
 
 namespace fe {
