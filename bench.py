@@ -509,6 +509,13 @@ def run_ours(args, dist, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / args.plain_steps
+    # where the per-primitive path spends its time, by kernel class (CUDA events)
+    plain_by_class = {}
+    for kd in kinds:
+        ctx.profile_begin(kd)
+        net.run(mode=0)
+        t, n, b = ctx.profile_end()
+        plain_by_class[kd] = {"ms": round(t, 3), "launches": n, "algorithmic_GB": round(b / 1e9, 2)}
 
     # ---- the layers composed from single-ciphertext operations (mode 2): every
     # rotation its own key switch, one PMult per term, as a per-op HE library ----
@@ -562,6 +569,9 @@ def run_ours(args, dist, rank, world, local):
                            if use_graph else "torch copies around the batched layers"),
               "layer_ms": {l_["name"]: round(t, 3) for l_, t in zip(net.layers, layer_ms)},
               "plain_path_ms_per_step": plain_ms, "speedup_vs_plain": plain_ms / ms_step,
+              "plain_path_by_class": plain_by_class,
+              "batched_path_by_class": {k: {"ms": round(v[0], 3), "launches": v[1], "algorithmic_GB": round(v[2] / 1e9, 2)}
+                                        for k, v in per_kind.items()},
               "per_op_library_ms_per_step": per_op_ms, "speedup_vs_per_op_library": per_op_ms / ms_step,
               "max_abs_err_vs_fp64": max(errs), "setup_s": round(t_setup, 1),
               "l2": "inputs (keys, plaintexts) far larger than L2; no flush",

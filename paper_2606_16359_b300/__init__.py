@@ -487,9 +487,22 @@ class Context:
     def workspace(self, nbytes):
         return _torch().empty(max(8, (nbytes + 7) // 8), dtype=_torch().int64, device="cuda")
 
+    def _check_layer_buffers(self, plan, pt, ct, out, n_req=1):
+        """The device buffers a planned layer reads and writes must have the sizes its
+        plan implies (the C ABI takes raw pointers and cannot see their extents)."""
+        i = plan.info
+        if ct.numel() != n_req * i.n_in_ct * self.ct_words(plan.level):
+            raise ValueError(f"input holds {ct.numel()} words, the plan reads "
+                             f"{n_req * i.n_in_ct} ciphertexts at level {plan.level}")
+        if out.numel() != n_req * i.n_out_ct * self.ct_words(plan.level - 1):
+            raise ValueError("output buffer does not match the plan")
+        if pt.numel() * pt.element_size() < i.pt_bytes:
+            raise ValueError("plaintext buffer smaller than the plan's pt_bytes")
+
     def he_conv(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
         ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
         out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        self._check_layer_buffers(plan, pt, ct, out)
         check(load().fe_he_conv(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
                                 ws.numel() * 8, mode, _stream()))
         return out
@@ -545,6 +558,7 @@ class Context:
             out = self.empty_ct(n_req * info.n_out_ct, lv - 1)
         if ws is None:
             ws = self.workspace(self.workspace_bytes(plan, n_req))
+        self._check_layer_buffers(plan, pt, ct, out, n_req)
         check(load().fe_he_layer_batch(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), n_req,
                                        _ptr(ws), ws.numel() * ws.element_size(), mode, _stream()))
         return out
@@ -552,6 +566,7 @@ class Context:
     def he_fc(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
         ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
         out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        self._check_layer_buffers(plan, pt, ct, out)
         check(load().fe_he_fc(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
                               ws.numel() * 8, mode, _stream()))
         return out
@@ -672,6 +687,7 @@ class Context:
     def he_repack(self, evk, plan, pt, ct, mode=1, ws=None, out=None):
         ws = self.workspace(plan.info.workspace_bytes) if ws is None else ws
         out = self.empty_ct(plan.info.n_out_ct, plan.level - 1) if out is None else out
+        self._check_layer_buffers(plan, pt, ct, out)
         check(load().fe_he_repack(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), _ptr(ws),
                                   ws.numel() * 8, mode, _stream()))
         return out

@@ -5,8 +5,6 @@ after decryption the target layout unpacks to the input tensor.  Then a
 MobileNet-shaped block at a reduced ring that runs its depthwise 3x3 layer at
 S = 2 and its pointwise layer at S = 1 with the re-encoding between them,
 bit-exact to the oracle's chain and within 1e-3 of the FP64 block."""
-import time
-
 import numpy as np
 import pytest
 
@@ -98,15 +96,18 @@ def test_block_with_depthwise_at_s2_and_pointwise_at_s1():
         pt_rp = g.load_repack_masks(prp)
         pt_pw = g.load_weights(ppw, wp, float(g.moduli[L - 2]))
         ct = g.encrypt(sk, g.pack(ga, torch.from_numpy(x)), L, delta, 4, ct_id0=0)
-        h = g.he_conv(evk, pdw, pt_dw, ct)
-        h = g.he_repack(evk, prp, pt_rp, h)
-        out = g.he_conv(evk, ppw, pt_pw, h)
+        h_dw = g.he_conv(evk, pdw, pt_dw, ct)
+        assert h_dw.shape[0] == prp.info.n_in_ct
+        h_rp = g.he_repack(evk, prp, pt_rp, h_dw)
+        assert h_rp.shape[0] == ppw.info.n_in_ct
+        out = g.he_conv(evk, ppw, pt_pw, h_rp)
         got = u64(out)
         y = g.unpack(ppw.out_layout, g.decrypt(sk, out, L - 3, delta)).cpu().numpy()
-        # share of the re-encoding in the block (CUDA events, warm)
+        # share of the re-encoding in the block (CUDA events, warm); each layer reads
+        # the output of the one before it, of the size its plan expects
         for name, fn in (("dw", lambda: g.he_conv(evk, pdw, pt_dw, ct)),
-                         ("repack", lambda: g.he_repack(evk, prp, pt_rp, h)),
-                         ("pw", lambda: g.he_conv(evk, ppw, pt_pw, h))):
+                         ("repack", lambda: g.he_repack(evk, prp, pt_rp, h_dw)),
+                         ("pw", lambda: g.he_conv(evk, ppw, pt_pw, h_rp))):
             fn()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
