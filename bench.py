@@ -151,7 +151,7 @@ def profiled_traffic(profile, key, source):
 
 def ntt_traffic_per_limb_pass():
     """DRAM bytes of one limb-pass of the NTT (ncu over 532 limbs)."""
-    return profiled_traffic("ntt_pass_forward_N65536_532limbs.txt", "traffic_bytes_per_limb_pass", "ntt.cu")
+    return profiled_traffic("ntt_pass_N65536_532limbs.txt", "traffic_bytes_per_limb_pass", "ntt.cu")
 
 
 def mac_traffic_ratio():
@@ -163,7 +163,7 @@ def mac_traffic_ratio():
 
 
 # Warp instructions per lazy Shoup butterfly, counted by ncu on the register-
-# resident probe (profiles/ntt_pass_forward_N65536_532limbs.txt).
+# resident probe (profiles/ntt_pass_N65536_532limbs.txt).
 BUTTERFLY_WARP_INSTRUCTIONS = 23.2
 
 
