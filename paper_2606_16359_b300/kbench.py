@@ -7,6 +7,7 @@
     python -m paper_2606_16359_b300.kbench layer [--channels 128] [--hw 14] [--dw] [--reps 5]
     python -m paper_2606_16359_b300.kbench aac [--reps 5]
     python -m paper_2606_16359_b300.kbench configs [--reps 5]
+    python -m paper_2606_16359_b300.kbench repack
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -241,6 +242,33 @@ def bench_aac(ctx, torch, args):
     return {"kernel": "aac", "level": lv, "rows": rows, "status": ctx.device_status()}
 
 
+def bench_repack(ctx, torch, args):
+    """Cost of running each MobileNet-shaped block's depthwise layer at S = 2 and
+    its pointwise layer at S = 1 (N = 2^16, level 23): the rotations the
+    depthwise layer saves at S = 2, against the rotations, masks and mask bytes
+    of the S = 2 -> 1 re-encoding between the layers (plans only; nothing is
+    encoded or run at this size)."""
+    import workloads as W
+    out = []
+    L = ctx.L
+    for H, Cin, Cout in W.MOBILENET_BLOCKS:
+        row = {"block": [H, Cin, Cout]}
+        for S in (1, 2):
+            lay = ctx.layout(H, H, Cin, 1, S)
+            pdw = ctx.plan_conv(lay, Cin, 3, depthwise=True, level=L)
+            row[f"dw_S{S}_rotations"] = pdw.info.n_inner_rot
+            if S == 2:
+                lo = pdw.out_layout
+                tgt = ctx.layout(lo.H, lo.W, Cin, 1, 1)
+                prp = ctx.plan_repack(lo, tgt, L - 1)
+                i = prp.info
+                row.update(repack_rotations=i.n_inner_rot + i.n_outer_rot, repack_masks=i.n_pt,
+                           repack_mask_GB=round(i.pt_bytes / 1e9, 1), repack_bsgs_n1=i.bsgs_n1)
+        row["rotations_saved_by_S2"] = row["dw_S1_rotations"] - row["dw_S2_rotations"]
+        out.append(row)
+    return {"kernel": "repack_plans", "logN": ctx.logN, "level": L, "blocks": out}
+
+
 def bench_configs(ctx_unused, torch, args):
     """The two small configurations end to end on the GPU: the single 5x5 conv
     1 -> 6 at N = 2^13 (S = 4) and the LeNet-shaped network at N = 2^14
@@ -296,7 +324,7 @@ def bench_configs(ctx_unused, torch, args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs", "repack"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
@@ -318,7 +346,8 @@ def main(argv=None):
     with torch.cuda.stream(side):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
-              "layer": bench_layer, "aac": bench_aac, "configs": bench_configs}[args.what]
+              "layer": bench_layer, "aac": bench_aac, "configs": bench_configs,
+              "repack": bench_repack}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 
