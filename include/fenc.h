@@ -360,6 +360,44 @@ int fe_plan_fc_next(fe_ctx* ctx, const fe_plan* prev, uint32_t F_out, uint32_t l
 int fe_plan_repack(fe_ctx* ctx, const fe_layout* from, const fe_layout* to, uint32_t level, fe_plan** out);
 int fe_he_repack(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev, const void* in_dev,
                  void* out_dev, void* workspace_dev, size_t workspace_bytes, int mode, void* stream);
+/* ---- transformer extension (Sec. 7): fragmented token embeddings ---------- */
+
+/* n_tok tokens with embedding dimension E, split into fragments of size S:
+ * element e = f S + s of token t sits in ciphertext s at position f, slot
+ * f n_tok + t, so each of the S ciphertexts holds ceil(E / S) = F elements of
+ * every token and an embedding-wise sum spans F positions instead of E.
+ * Filled by fe_token_layout_make: P = N / (2 n_tok) positions per ciphertext,
+ * F, n_ct = S.  Errors: FE_EINVAL (n_tok does not divide N/2, F > P). */
+typedef struct {
+    uint32_t n_tok, E, S;
+    uint32_t P, F, n_ct;
+} fe_token_layout;
+int fe_token_layout_make(const fe_ctx* ctx, fe_token_layout* lay);
+/* x_dev float64 (n_tok, E) -> slots_dev float64 [S][N/2] (zero padded), and back. */
+int fe_token_pack(const fe_ctx* ctx, const fe_token_layout* lay, const double* x_dev, double* slots_dev,
+                  void* stream);
+int fe_token_unpack(const fe_ctx* ctx, const fe_token_layout* lay, const double* slots_dev, double* x_dev,
+                    void* stream);
+/* Plan Y = X W^T (W: E_out x E, row-major) on fragmented tokens (the
+ * projections and FFN layers of an encoder block): the FC plan of Sec. 5
+ * (diagonals with baby-step / giant-step over the P positions, tokens in the
+ * batch slots) on the fragment feature table, with output element
+ * k = f' S + s' at ciphertext s' position f' (out_lay: the same S and n_tok,
+ * E = E_out).  Weights through fe_plan_load_weights (weights_host: W), run by
+ * fe_he_fc.  The attention products (ciphertext by ciphertext) are not part of
+ * this library.  Errors as fe_plan_fc, FE_EINVAL (layouts). */
+int fe_plan_token_linear(fe_ctx* ctx, const fe_token_layout* in_lay, uint32_t E_out, uint32_t level,
+                         fe_token_layout* out_lay, fe_plan** out);
+/* The block-size choice of Sec. 7: the rotation complexity gamma E / S + 2 n S
+ * (FFN and projections: embedding aggregation over E / S positions, gamma the
+ * FFN's expansion; attention: token-wise aggregation over S times more tokens
+ * per ciphertext) taken as a count, minimised over the power-of-two S <= max_S
+ * (0: 64) that divide E, ties to the smaller S; *rotations (optional) receives
+ * its value, *s_star (optional) the continuous optimum sqrt(gamma E / (2 n)).
+ * Pure host computation.  Errors: FE_EINVAL. */
+int fe_choose_token_fragment(uint32_t E, uint32_t n_tok, double gamma, uint32_t max_S, uint32_t* S,
+                             double* rotations, double* s_star);
+
 /* Read a fully connected plan's decrypted output slots back as outputs:
  * y_dev[b][n] (BS x F_out, float64) = slots_dev[n / P][(n mod P) BS + b]
  * (slots_dev: the plan's n_out_ct decoded slot vectors of N/2 doubles).

@@ -108,3 +108,33 @@ def executed_inner(S, K, n_groups, stride=1):
         for v in range(S):
             total += sum(1 for a in offs[u] for b in offs[v] if (a, b) != (0, 0))
     return total * n_groups
+
+
+# ---------------------------------------------------------------------------
+# Transformer extension (Sec. 7): token embeddings split into fragments of size
+# S; embedding-wise rotations fall as E / S, token-wise ones grow as S.
+# ---------------------------------------------------------------------------
+
+def transformer_rotations(E, n, gamma, S):
+    """The rotation complexity of Sec. 7 taken as a count: gamma E / S for the
+    FFN and projections (embedding aggregation over E / S positions) plus 2 n S
+    for the token-wise aggregation of the attention products."""
+    return gamma * E / S + 2 * n * S
+
+
+def choose_S_transformer(E, n, gamma, candidates=(1, 2, 4, 8, 16, 32, 64)):
+    """Argmin of transformer_rotations over the candidate S that divide E
+    (ties to the smaller S)."""
+    best = None
+    for S in candidates:
+        if E % S:
+            continue
+        cost = transformer_rotations(E, n, gamma, S)
+        if best is None or cost < best[1]:
+            best = (S, cost)
+    return best
+
+
+def s_star_transformer(E, n, gamma):
+    """Continuous optimum of gamma E / S + 2 n S: S* = sqrt(gamma E / (2 n))."""
+    return math.sqrt(gamma * E / (2 * n))

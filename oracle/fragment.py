@@ -131,3 +131,44 @@ def slot_map(lay):
                     ct[b, c, h, w] = lay.ct_index(g, u, v)
                     sl[b, c, h, w] = lay.slot(c_loc, bi, bj, b)
     return ct, sl
+
+
+class TokenLayout:
+    """Fragmented token-embedding layout (Sec. 7): n_tok tokens with embedding
+    dimension E; element e = f S + s of token t sits in ciphertext s at
+    position f, slot f n_tok + t (tokens innermost, like the batch of
+    Algorithm 1).  Each ciphertext holds E / S elements of every token, so an
+    embedding-wise sum needs rotations over E / S positions, and P = N / (2
+    n_tok) positions must hold them."""
+
+    def __init__(self, N, n_tok, E, S):
+        if (N // 2) % n_tok:
+            raise ValueError("n_tok must divide N / 2")
+        self.N, self.n_tok, self.E, self.S = N, n_tok, E, S
+        self.P = N // 2 // n_tok
+        self.F = -(-E // S)  # positions used
+        if self.F > self.P:
+            raise ValueError("E / S positions do not fit a ciphertext")
+        self.n_ct = S
+
+    def feature(self, c, p):
+        """Embedding index held at position p of ciphertext c, or -1."""
+        e = p * self.S + c
+        return e if p < self.F and e < self.E else -1
+
+
+def pack_tokens(tl, x):
+    """x: (n_tok, E) -> (S, N/2) slot vectors."""
+    out = np.zeros((tl.n_ct, tl.N // 2))
+    for e in range(tl.E):
+        f, s = divmod(e, tl.S)
+        out[s, f * tl.n_tok:(f + 1) * tl.n_tok] = x[:, e]
+    return out
+
+
+def unpack_tokens(tl, slots):
+    x = np.zeros((tl.n_tok, tl.E))
+    for e in range(tl.E):
+        f, s = divmod(e, tl.S)
+        x[:, e] = slots[s, f * tl.n_tok:(f + 1) * tl.n_tok]
+    return x

@@ -35,7 +35,7 @@ import numpy as np
 from . import _core as C
 from . import ckks
 from . import counts
-from .fragment import Layout
+from .fragment import Layout, TokenLayout
 
 
 class Counters:
@@ -638,6 +638,27 @@ def repack_rotation_steps(la, lb):
             if d // n1:
                 steps.add((d // n1) * n1 * la.BS)
     return sorted(steps)
+
+
+# ---------------------------------------------------------------------------
+# Transformer extension (Sec. 7): a linear layer on fragmented token embeddings
+# ---------------------------------------------------------------------------
+
+def he_token_linear(pr, keys, cts, tl, W, *, w_scale=None, cnt=None):
+    """Y = X W^T for the tokens of layout tl (W: E_out x E), output in the
+    fragmented layout of E_out with the same S and token count: output element
+    k = f' S + s' of every token sits in ciphertext s' at position f'.  It is
+    the FC layer of Sec. 5 (diagonals with baby-step / giant-step) on the
+    fragment feature table, with its output neuron s' P + f' taking row k of W."""
+    E_out = W.shape[0]
+    tlo = TokenLayout(tl.N, tl.n_tok, E_out, tl.S)
+    P = tl.P
+    Wfc = np.zeros((tl.S * P, tl.E))
+    for k in range(E_out):
+        f, s = divmod(k, tl.S)
+        Wfc[s * P + f] = W[k]
+    out = he_fc(pr, keys, cts, tl.feature, P, tl.n_tok, Wfc, w_scale=w_scale, cnt=cnt)
+    return out, tlo
 
 
 # ---------------------------------------------------------------------------

@@ -67,6 +67,10 @@ class FeFragmentChoice(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class FeTokenLayout(ctypes.Structure):
+    _fields_ = [("n_tok", u32), ("E", u32), ("S", u32), ("P", u32), ("F", u32), ("n_ct", u32)]
+
+
 class FeServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", u32), ("max_inflight", u32), ("hbm_budget_bytes", sz), ("hbm_reserve_bytes", sz)]
 
@@ -145,6 +149,11 @@ SIGNATURES = {
     "fe_plan_fc_layout": (cint, [vp, P(FeLayout), u32, u32, P(vp)]),
     "fe_plan_fc_next": (cint, [vp, vp, u32, u32, P(vp)]),
     "fe_plan_repack": (cint, [vp, P(FeLayout), P(FeLayout), u32, P(vp)]),
+    "fe_token_layout_make": (cint, [vp, P(FeTokenLayout)]),
+    "fe_token_pack": (cint, [vp, P(FeTokenLayout), vp, vp, vp]),
+    "fe_token_unpack": (cint, [vp, P(FeTokenLayout), vp, vp, vp]),
+    "fe_plan_token_linear": (cint, [vp, P(FeTokenLayout), u32, u32, P(FeTokenLayout), P(vp)]),
+    "fe_choose_token_fragment": (cint, [u32, u32, dbl, u32, P(u32), P(dbl), P(dbl)]),
     "fe_he_repack": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
     "fe_fc_unpack": (cint, [vp, vp, vp, vp, vp]),
     "fe_weight_scale": (cint, [vp, u32, dbl, dbl, dbl, P(dbl)]),
@@ -692,6 +701,33 @@ class Context:
                                   ws.numel() * 8, mode, _stream()))
         return out
 
+    def token_layout(self, n_tok, E, S):
+        lay = FeTokenLayout(n_tok, E, S, 0, 0, 0)
+        check(load().fe_token_layout_make(self.handle, ctypes.byref(lay)))
+        return lay
+
+    def token_pack(self, lay, x):
+        torch = _torch()
+        x = torch.as_tensor(x, dtype=torch.float64).cuda().contiguous()
+        slots = torch.empty((lay.n_ct, self.N // 2), dtype=torch.float64, device="cuda")
+        check(load().fe_token_pack(self.handle, ctypes.byref(lay), _ptr(x), _ptr(slots), _stream()))
+        return slots
+
+    def token_unpack(self, lay, slots):
+        torch = _torch()
+        x = torch.zeros((lay.n_tok, lay.E), dtype=torch.float64, device="cuda")
+        check(load().fe_token_unpack(self.handle, ctypes.byref(lay), _ptr(slots.contiguous()), _ptr(x), _stream()))
+        return x
+
+    def plan_token_linear(self, lay, E_out, level):
+        out_lay = FeTokenLayout()
+        h = vp()
+        check(load().fe_plan_token_linear(self.handle, ctypes.byref(lay), E_out, level, ctypes.byref(out_lay),
+                                          ctypes.byref(h)))
+        p = Plan(self, h)
+        p.level, p.token_out = level, out_lay
+        return p
+
     def plan_fc_next(self, prev, F_out, level):
         h = vp()
         check(load().fe_plan_fc_next(self.handle, prev.handle, F_out, level, ctypes.byref(h)))
@@ -836,6 +872,14 @@ def choose_fragment(N, H, W, Cin, Cout, K, BS, depthwise=False, max_S=0):
     r = FeFragmentChoice()
     check(load().fe_choose_fragment(N, H, W, Cin, Cout, K, BS, 1 if depthwise else 0, max_S, ctypes.byref(r)))
     return r.as_dict()
+
+
+def choose_token_fragment(E, n_tok, gamma, max_S=0):
+    """Block size of the transformer extension: argmin of gamma E / S + 2 n S (host only)."""
+    S, r, st = u32(0), dbl(), dbl()
+    check(load().fe_choose_token_fragment(E, n_tok, float(gamma), max_S, ctypes.byref(S), ctypes.byref(r),
+                                          ctypes.byref(st)))
+    return {"S": S.value, "rotations": r.value, "s_star": st.value}
 
 
 def exported_symbols():

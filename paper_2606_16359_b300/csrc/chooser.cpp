@@ -119,3 +119,29 @@ extern "C" int fe_choose_fragment(uint32_t N, uint32_t H, uint32_t W, uint32_t C
     if (!found) return fe::fail(FE_EINVAL, "fe_choose_fragment: no admissible fragment size (the map does not fit)");
     return FE_OK;
 }
+
+// Transformer extension (Sec. 7): the rotation complexity gamma E / S + 2 n S
+// (embedding-wise aggregation over E / S positions in the FFN and projections,
+// token-wise aggregation over S times more tokens per ciphertext in the
+// attention products), taken as a count, and its argmin over the power-of-two
+// S <= max_S that divide E (ties to the smaller S).
+extern "C" int fe_choose_token_fragment(uint32_t E, uint32_t n_tok, double gamma, uint32_t max_S, uint32_t* S_out,
+                                        double* rotations, double* s_star) {
+    if (!S_out || !E || !n_tok || !(gamma > 0)) return fe::fail(FE_EINVAL, "fe_choose_token_fragment: bad argument");
+    if (max_S == 0) max_S = 64;
+    bool found = false;
+    double best = 0;
+    for (uint32_t S = 1; S <= max_S; S *= 2) {
+        if (E % S) continue;
+        const double r = gamma * E / S + 2.0 * n_tok * S;
+        if (!found || r < best) {
+            found = true;
+            best = r;
+            *S_out = S;
+        }
+    }
+    if (!found) return fe::fail(FE_EINVAL, "fe_choose_token_fragment: no candidate S divides E");
+    if (rotations) *rotations = best;
+    if (s_star) *s_star = std::sqrt(gamma * E / (2.0 * n_tok));
+    return FE_OK;
+}

@@ -78,7 +78,8 @@ __global__ void k_conv_pt_slots(ConvPtArgs a, double* z, int slots) {
 struct FcPtArgs {
     const fe_plan::FcPt* pts;
     const double* W;
-    const int* feat;  // [n_in][P]
+    const int* feat;    // [n_in][P]
+    const int* rowmap;  // [F_out] neuron -> row of W (-1: zero), or null (row = neuron)
     double wmul;
     int P, BS, n1, F_in, F_out;
 };
@@ -93,7 +94,8 @@ __global__ void k_fc_pt_slots(FcPtArgs a, double* z, int slots) {
     const int n = q.t * a.P + p0;
     const int f = a.feat[(size_t)q.c * a.P + (p + q.beta) % a.P];
     double v = 0.0;
-    if (n < a.F_out && f >= 0) v = a.W[(size_t)n * a.F_in + f] * a.wmul;
+    const int row = n < a.F_out ? (a.rowmap ? a.rowmap[n] : n) : -1;
+    if (row >= 0 && f >= 0) v = a.W[(size_t)row * a.F_in + f] * a.wmul;
     z[(size_t)blockIdx.y * slots + l] = v;
 }
 
@@ -977,7 +979,7 @@ namespace {
 // n1 = 0 takes the default split 2^ceil(log2(P) / 2).
 int plan_fc_core(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat, uint32_t F_in,
                  uint32_t F_out, uint32_t level, const std::function<bool(int, int, int, int)>* sparse,
-                 int n1_req, std::unique_ptr<fe_plan>& p);
+                 int n1_req, std::unique_ptr<fe_plan>& p, const std::vector<int>* rowmap = nullptr);
 }  // namespace
 }  // namespace fe
 
@@ -994,7 +996,7 @@ namespace fe {
 namespace {
 int plan_fc_core(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int32_t* feat, uint32_t F_in,
                  uint32_t F_out, uint32_t level, const std::function<bool(int, int, int, int)>* sparse,
-                 int n1_req, std::unique_ptr<fe_plan>& p) {
+                 int n1_req, std::unique_ptr<fe_plan>& p, const std::vector<int>* rowmap) {
     if (level == 0 || (int)level > c->L) return fail(FE_ELEVEL, "fc needs a level to rescale");
     if ((uint64_t)P * BS != (uint64_t)c->N / 2 || (P & (P - 1)) || !n_in_ct || !F_out)
         return fail(FE_EINVAL, "fc needs P BS = N/2 with P a power of two");
@@ -1023,7 +1025,7 @@ int plan_fc_core(fe_ctx* c, uint32_t n_in_ct, uint32_t P, uint32_t BS, const int
             int p0 = (((int)q - p->n1 * gam) % (int)P + (int)P) % (int)P;
             int n = t * P + p0;
             int f = p->feat[(size_t)cc * P + (q + beta) % P];
-            if (n < (int)F_out && f >= 0) return true;
+            if (n < (int)F_out && f >= 0 && (!rowmap || (*rowmap)[n] >= 0)) return true;
         }
         return false;
     };
@@ -1140,6 +1142,96 @@ extern "C" int fe_plan_repack(fe_ctx* c, const fe_layout* from, const fe_layout*
     return FE_OK;
 }
 
+namespace fe {
+namespace {
+int token_layout_fill(int N, fe_token_layout* t) {
+    if (!t->n_tok || !t->E || !t->S) return fail(FE_EINVAL, "token layout: zero extent");
+    if ((N / 2) % t->n_tok) return fail(FE_EINVAL, "token layout: n_tok must divide N / 2");
+    t->P = (uint32_t)(N / 2) / t->n_tok;
+    t->F = (t->E + t->S - 1) / t->S;
+    if (t->F > t->P) return fail(FE_EINVAL, "token layout: E / S positions do not fit a ciphertext");
+    t->n_ct = t->S;
+    return FE_OK;
+}
+
+// slots[s][f n_tok + t] = x[t][f S + s], zero outside the embedding
+__global__ void k_token_pack(const double* x, double* slots, fe_token_layout T, int half) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= half) return;
+    const int s = blockIdx.y;
+    const int f = l / (int)T.n_tok, t = l % (int)T.n_tok;
+    const int e = f * (int)T.S + s;
+    slots[(size_t)s * half + l] = f < (int)T.F && e < (int)T.E ? x[(size_t)t * T.E + e] : 0.0;
+}
+
+// the reverse: x[t][f S + s] = slots[s][f n_tok + t]
+__global__ void k_token_unpack(const double* slots, double* x, fe_token_layout T, int half) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= half) return;
+    const int s = blockIdx.y;
+    const int f = l / (int)T.n_tok, t = l % (int)T.n_tok;
+    const int e = f * (int)T.S + s;
+    if (f < (int)T.F && e < (int)T.E) x[(size_t)t * T.E + e] = slots[(size_t)s * half + l];
+}
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_token_layout_make(const fe_ctx* c, fe_token_layout* t) {
+    if (!c || !t) return fail(FE_EINVAL, "null argument");
+    return token_layout_fill(c->N, t);
+}
+
+extern "C" int fe_token_pack(const fe_ctx* c, const fe_token_layout* lay, const double* x_dev, double* slots_dev,
+                             void* stream) {
+    if (!c || !lay || !x_dev || !slots_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(x_dev);
+    FE_ALIGNED(slots_dev);
+    fe_token_layout T = *lay;
+    FE_TRY(token_layout_fill(c->N, &T));
+    const int half = c->N / 2;
+    k_token_pack<<<dim3((half + kB - 1) / kB, T.n_ct), kB, 0, (cudaStream_t)stream>>>(x_dev, slots_dev, T, half);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_token_unpack(const fe_ctx* c, const fe_token_layout* lay, const double* slots_dev, double* x_dev,
+                               void* stream) {
+    if (!c || !lay || !x_dev || !slots_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(x_dev);
+    FE_ALIGNED(slots_dev);
+    fe_token_layout T = *lay;
+    FE_TRY(token_layout_fill(c->N, &T));
+    const int half = c->N / 2;
+    k_token_unpack<<<dim3((half + kB - 1) / kB, T.n_ct), kB, 0, (cudaStream_t)stream>>>(slots_dev, x_dev, T, half);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_plan_token_linear(fe_ctx* c, const fe_token_layout* in_lay, uint32_t E_out, uint32_t level,
+                                    fe_token_layout* out_lay, fe_plan** out) {
+    if (!c || !in_lay || !out || !E_out) return fail(FE_EINVAL, "null argument or E_out = 0");
+    fe_token_layout A = *in_lay;
+    FE_TRY(token_layout_fill(c->N, &A));
+    fe_token_layout B{A.n_tok, E_out, A.S, 0, 0, 0};
+    FE_TRY(token_layout_fill(c->N, &B));
+    const uint32_t P = A.P;
+    // input feature of position p of ciphertext s: element p S + s; output neuron
+    // s' P + f' carries output element f' S + s' (row f' S + s' of the caller's W)
+    std::vector<int32_t> feat((size_t)A.n_ct * P, -1);
+    for (uint32_t s2 = 0; s2 < A.n_ct; s2++)
+        for (uint32_t p = 0; p < A.F; p++)
+            if (p * A.S + s2 < A.E) feat[(size_t)s2 * P + p] = (int32_t)(p * A.S + s2);
+    std::vector<int> rowmap((size_t)B.n_ct * P, -1);
+    for (uint32_t k = 0; k < E_out; k++) rowmap[(size_t)(k % B.S) * P + k / B.S] = (int)k;
+    std::unique_ptr<fe_plan> p;
+    FE_TRY(plan_fc_core(c, A.n_ct, P, A.n_tok, feat.data(), A.E, B.n_ct * P, level, nullptr, 0, p, &rowmap));
+    p->rowmap = std::move(rowmap);
+    p->w_rows = (int)E_out;
+    if (out_lay) *out_lay = B;
+    *out = p.release();
+    return FE_OK;
+}
+
 extern "C" int fe_plan_fc_layout(fe_ctx* c, const fe_layout* in_lay, uint32_t F_out, uint32_t level,
                                  fe_plan** out) {
     if (!c || !in_lay || !out) return fail(FE_EINVAL, "null argument");
@@ -1248,7 +1340,8 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     size_t wcount = p->repack ? 1
                     : p->kind == 0 ? (p->depthwise ? (size_t)p->Cin * p->K * p->K
                                                    : (size_t)p->Cout * p->Cin * p->K * p->K)
-                                   : (size_t)p->F_out * p->F_in;
+                    : !p->rowmap.empty() ? (size_t)p->w_rows * p->F_in
+                                         : (size_t)p->F_out * p->F_in;
     double* dW;
     FE_CUDA_TRY(cudaMallocAsync(&dW, wcount * 8, st));
     if (!p->repack) FE_CUDA_TRY(cudaMemcpyAsync(dW, W_host, wcount * 8, cudaMemcpyHostToDevice, st));
@@ -1260,6 +1353,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     u64* limbs;
     void* descs;
     int* dfeat = nullptr;
+    int* drow = nullptr;
     FE_CUDA_TRY(cudaMallocAsync(&z, (size_t)chunk * half * 8, st));
     FE_CUDA_TRY(cudaMallocAsync(&limbs, (size_t)chunk * nl * N * 8, st));
     size_t dbytes = p->kind == 0 ? p->cpts.size() * sizeof(fe_plan::ConvPt) : p->fpts.size() * sizeof(fe_plan::FcPt);
@@ -1270,6 +1364,11 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
         FE_CUDA_TRY(cudaMemcpyAsync(descs, p->fpts.data(), dbytes, cudaMemcpyHostToDevice, st));
         FE_CUDA_TRY(cudaMallocAsync(&dfeat, p->feat.size() * sizeof(int), st));
         FE_CUDA_TRY(cudaMemcpyAsync(dfeat, p->feat.data(), p->feat.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (!p->rowmap.empty()) {
+            FE_CUDA_TRY(cudaMallocAsync(&drow, p->rowmap.size() * sizeof(int), st));
+            FE_CUDA_TRY(cudaMemcpyAsync(drow, p->rowmap.data(), p->rowmap.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                        st));
+        }
     }
     int rc = FE_OK;
     for (int s0 = 0; s0 < p->n_pt && rc == FE_OK; s0 += chunk) {
@@ -1283,7 +1382,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
             RepackPtArgs a{(const fe_plan::FcPt*)descs + s0, dfeat, p->lout, p->P, p->BS, p->n1};
             k_repack_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
         } else {
-            FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
+            FcPtArgs a{(const fe_plan::FcPt*)descs + s0, dW, dfeat, drow, wmul, p->P, p->BS, p->n1, p->F_in, p->F_out};
             k_fc_pt_slots<<<dim3((half + kB - 1) / kB, cn), kB, 0, st>>>(a, z, half);
         }
         rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, p->dhoist != 0);
@@ -1295,6 +1394,7 @@ extern "C" int fe_plan_load_weights(fe_ctx* c, fe_plan* p, const double* W_host,
     cudaFreeAsync(limbs, st);
     cudaFreeAsync(descs, st);
     if (dfeat) cudaFreeAsync(dfeat, st);
+    if (drow) cudaFreeAsync(drow, st);
     FE_CUDA_TRY(cudaStreamSynchronize(st));
     if (rc == FE_OK) p->w_scale = w_scale;
     return rc;

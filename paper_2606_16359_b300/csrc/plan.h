@@ -51,6 +51,8 @@ struct fe_plan {
     std::vector<int32_t> steps;
     double w_scale = 0;  // scale of the loaded weights (0 until fe_plan_load_weights)
     int repack = 0;      // 1: an FC-kind plan whose weights are the permutation from lin to lout
+    std::vector<int> rowmap;  // FC-kind: output neuron -> row of the caller's weight matrix (-1: none)
+    int w_rows = 0;           // rows of the caller's weight matrix when rowmap is used
 };
 
 namespace fe {

@@ -90,3 +90,21 @@ def test_rejects_bad_arguments():
         fe.rotation_model(2 ** 10, 224, 224, 3, 3, 3, 1, 1)   # block does not fit
     with pytest.raises(fe.FencError):
         fe.choose_fragment(1000, 8, 8, 3, 3, 3, 1)            # N not a power of two
+
+
+def test_token_fragment_choice_matches_the_oracle_and_the_paper():
+    """Sec. 7: the block size of fragmented token embeddings minimises
+    gamma E / S + 2 n S; for BERT-base (E = 768, n = 128, gamma about 6) the
+    paper's encoder block is fastest at S = 4."""
+    import paper_2606_16359_b300 as fe
+    from oracle import counts
+    r = fe.choose_token_fragment(768, 128, 6.0)
+    assert r["S"] == 4 and r["rotations"] == counts.transformer_rotations(768, 128, 6, 4)
+    assert abs(r["s_star"] - counts.s_star_transformer(768, 128, 6)) < 1e-12
+    import random
+    rng = random.Random(3)
+    for _ in range(200):
+        E = rng.choice([64, 96, 128, 192, 256, 384, 512, 768, 1024])
+        n = rng.choice([8, 16, 32, 64, 128, 256, 512])
+        g = rng.choice([1.0, 2.0, 4.0, 6.0, 8.0])
+        assert fe.choose_token_fragment(E, n, g)["S"] == counts.choose_S_transformer(E, n, g)[0]
