@@ -661,6 +661,115 @@ def he_token_linear(pr, keys, cts, tl, W, *, w_scale=None, cnt=None):
     return out, tlo
 
 
+def drop_level(ct):
+    """The same ciphertext modulo Q_{l-1}: its first l limbs (exact; scale kept)."""
+    return ckks.Ciphertext(ct.c0[:ct.level].copy(), ct.c1[:ct.level].copy(), ct.level - 1, ct.scale)
+
+
+def mask_scale_pow2(pr, level):
+    """Scale of the 0/1 token masks: the power of two 2^floor(log2 q_level).  The
+    masks are periodic in the slots, so their coefficients are rationals with
+    denominators dividing N; at an odd scale (a prime) some land exactly on a
+    rounding tie, at 2^k >= N none does."""
+    return 2.0 ** (int(pr.moduli[level]).bit_length() - 1)
+
+
+def token_masks(tl, r):
+    """0/1 slot vectors of the tokens t < n - r and t >= n - r, in every position
+    block of n_tok slots (the two halves of a token-wise rotation by r)."""
+    n = tl.n_tok
+    lo = np.tile((np.arange(n) < n - r).astype(float), tl.P)
+    return lo, 1.0 - lo
+
+
+def token_rotate(pr, keys, ct, tl, r, mask_scale):
+    """Rotation of every position block of n_tok token slots by r tokens, t <- t + r
+    mod n: M_lo (x) Rot(ct, r) + M_hi (x) Rot(ct, r - n) with the masks at
+    mask_scale (a power of two), then one rescale: scale (s mask_scale) / q_l.
+    r = 0: the ciphertext times the integer mask_scale, rescaled, which gives
+    the same level and scale as the rotated ones."""
+    if r == 0:
+        x = ckks.mul_int(pr, ct, int(mask_scale))
+        x.scale = ct.scale * mask_scale
+        return ckks.rescale(pr, x)
+    lo, hi = token_masks(tl, r)
+    a = ckks.pmult(pr, ckks.rotate(pr, keys, ct, r), ckks.encode(pr, lo, ct.level, mask_scale))
+    b = ckks.pmult(pr, ckks.rotate(pr, keys, ct, r - tl.n_tok), ckks.encode(pr, hi, ct.level, mask_scale))
+    return ckks.rescale(pr, ckks.add(pr, a, b))  # scale (s mask_scale) / q_l
+
+
+def position_sum(pr, keys, ct, tl):
+    """Sum over the P positions of a ciphertext, replicated into every position:
+    ct += Rot(ct, 2^k n_tok) for k = 0 .. log2(P) - 1."""
+    acc = ct
+    step = tl.n_tok
+    while step < tl.N // 2:
+        acc = ckks.add(pr, acc, ckks.rotate(pr, keys, acc, step))
+        step *= 2
+    return acc
+
+
+def attention_rotation_steps(tl):
+    """Rotation steps (slots) of the attention products."""
+    n = tl.n_tok
+    steps = set()
+    for r in range(1, n):
+        steps |= {r, r - n}
+    step = n
+    while step < tl.N // 2:
+        steps.add(step)
+        step *= 2
+    return sorted(steps)
+
+
+def he_attention_scores(pr, keys, q_cts, k_cts, tl, mask_scale=None):
+    """A = Q K^T of the tokens of the fragmented layout tl (Sec. 7: token-wise
+    aggregation for the attention products), as its n diagonals:
+    D_r[i] = A[i][(i + r) mod n] = sum_e Q[i][e] K[(i + r) mod n][e], r < n.
+    For each r: K's fragment ciphertexts rotated token-wise by r (token_rotate,
+    one level), each multiplied by Q's matching fragment (one level dropped to
+    meet them) with relinearisation, summed over the S fragments, rescaled, and
+    summed over the positions (position_sum), so D_r holds A[i][(i + r) mod n]
+    at slot f n + i of every position f.  Two levels; the output scale is
+    s_q s_k' / q_{l-1}, s_k' the rotated K's scale."""
+    level = q_cts[0].level
+    ms = mask_scale_pow2(pr, level) if mask_scale is None else mask_scale
+    qd = [drop_level(q) for q in q_cts]
+    out = []
+    for r in range(tl.n_tok):
+        acc = None
+        for s, (q, k) in enumerate(zip(qd, k_cts)):
+            acc = _add(pr, acc, ckks.cmult_relin(pr, keys, q, token_rotate(pr, keys, k, tl, r, ms)))
+        d = ckks.rescale(pr, acc)
+        out.append(position_sum(pr, keys, d, tl))
+    return out
+
+
+def he_attention_apply(pr, keys, d_cts, v_cts, tl, mask_scale=None):
+    """O = A V from the n diagonals of A (as he_attention_scores leaves them,
+    replicated over positions) and V in the fragmented layout tl:
+    O[i][e] = sum_r D_r[i] V[(i + r) mod n][e].  For each fragment ciphertext of V
+    and each r: V rotated token-wise by r (one level), multiplied by D_r with
+    relinearisation after the higher of the two has limbs dropped to meet the
+    other; the sum over r is rescaled once.  Output in V's layout, one level
+    below the lower of V's rotated copies and D's."""
+    level = v_cts[0].level
+    ms = mask_scale_pow2(pr, level) if mask_scale is None else mask_scale
+    out = []
+    for v in v_cts:
+        acc = None
+        for r, d in enumerate(d_cts):
+            vr = token_rotate(pr, keys, v, tl, r, ms)
+            dr = d
+            while dr.level > vr.level:
+                dr = drop_level(dr)
+            while vr.level > dr.level:
+                vr = drop_level(vr)
+            acc = _add(pr, acc, ckks.cmult_relin(pr, keys, dr, vr))
+        out.append(ckks.rescale(pr, acc))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Polynomial activation a x^2 + b x + c (Sec. 5, Implementation paragraph)
 # ---------------------------------------------------------------------------

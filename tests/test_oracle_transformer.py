@@ -52,3 +52,49 @@ def test_token_linear_decrypts_to_xwt(E, E_out, S):
     assert len(out) == S and tlo.E == E_out
     y = fragment.unpack_tokens(tlo, np.stack([ckks.decrypt(pr, keys.sk, c) for c in out]))
     assert np.abs(y - x @ w.T).max() < 1e-3
+
+
+def _attn_setup(n=4, E=16, S=2, seed=1):
+    pr = ckks.Params(10, 6, 1, 40, 40)
+    delta = 2.0 ** 35
+    tl = fragment.TokenLayout(pr.N, n, E, S)
+    rng = np.random.default_rng(seed)
+    Q, K, V = (rng.uniform(-1, 1, (n, E)) for _ in range(3))
+    keys = ckks.KeySet(pr, 2, rot_steps=henn.attention_rotation_steps(tl), relin=True)
+
+    def enc(X, sd):
+        sl = fragment.pack_tokens(tl, X)
+        return [ckks.encrypt(pr, keys.sk, ckks.encode(pr, sl[i], pr.L, delta), sd, i) for i in range(S)]
+    return pr, keys, tl, Q, K, V, enc(Q, 3), enc(K, 4), enc(V, 5)
+
+
+def test_drop_level_and_token_rotation():
+    """Dropping the last limb keeps the message and the scale; a token-wise
+    rotation by r moves token (t + r) mod n into token t in every position."""
+    pr, keys, tl, Q, K, V, q, k, v = _attn_setup()
+    d = henn.drop_level(q[0])
+    assert d.level == pr.L - 1 and d.scale == q[0].scale
+    assert np.abs(ckks.decrypt(pr, keys.sk, d) - ckks.decrypt(pr, keys.sk, q[0])).max() < 1e-6
+    ms = henn.mask_scale_pow2(pr, pr.L)
+    want = fragment.pack_tokens(tl, Q)[1]
+    for r in range(tl.n_tok):
+        y = ckks.decrypt(pr, keys.sk, henn.token_rotate(pr, keys, q[1], tl, r, ms))
+        rolled = np.concatenate([np.roll(want[f * tl.n_tok:(f + 1) * tl.n_tok], -r) for f in range(tl.P)])
+        assert np.abs(y - rolled).max() < 1e-4
+
+
+def test_attention_scores_and_apply_match_fp64():
+    """Sec. 7's attention products on fragmented tokens: the n diagonals of
+    Q K^T (replicated over positions) and then (Q K^T) V, against FP64."""
+    pr, keys, tl, Q, K, V, q, k, v = _attn_setup()
+    D = henn.he_attention_scores(pr, keys, q, k, tl)
+    A = Q @ K.T
+    n = tl.n_tok
+    for r, d in enumerate(D):
+        z = ckks.decrypt(pr, keys.sk, d).reshape(tl.P, n)
+        want = np.array([A[i][(i + r) % n] for i in range(n)])
+        assert np.abs(z - want[None, :]).max() < 1e-3
+    assert len({d.scale for d in D}) == 1 and D[0].level == pr.L - 2
+    O = henn.he_attention_apply(pr, keys, D, v, tl)
+    y = fragment.unpack_tokens(tl, np.stack([ckks.decrypt(pr, keys.sk, o) for o in O]))
+    assert np.abs(y - A @ V).max() < 1e-3
