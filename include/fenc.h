@@ -384,10 +384,40 @@ int fe_token_unpack(const fe_ctx* ctx, const fe_token_layout* lay, const double*
  * batch slots) on the fragment feature table, with output element
  * k = f' S + s' at ciphertext s' position f' (out_lay: the same S and n_tok,
  * E = E_out).  Weights through fe_plan_load_weights (weights_host: W), run by
- * fe_he_fc.  The attention products (ciphertext by ciphertext) are not part of
- * this library.  Errors as fe_plan_fc, FE_EINVAL (layouts). */
+ * fe_he_fc (the attention products: fe_he_attention_scores / _apply).
+ * Errors as fe_plan_fc, FE_EINVAL (layouts). */
 int fe_plan_token_linear(fe_ctx* ctx, const fe_token_layout* in_lay, uint32_t E_out, uint32_t level,
                          fe_token_layout* out_lay, fe_plan** out);
+/* Attention products on fragmented tokens (Sec. 7: the token-wise aggregation
+ * of Q K^T and A V).  A token-wise rotation by r rotates every position block
+ * of n_tok slots by r tokens: M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n), the
+ * 0/1 masks of the tokens t < n - r and t >= n - r encoded at the power of two
+ * ms = 2^floor(log2 q_level), then one rescale (r = 0: x times the integer ms,
+ * rescaled); scale (s ms) / q_level.  Keys: fe_attention_rotation_steps, plus
+ * the relinearisation key.
+ * fe_he_attention_scores: Q and K ([S][2][level+1][N] each, scales q_scale,
+ * k_scale) -> the n_tok diagonals D_r[i] = A[i][(i + r) mod n] of A = Q K^T
+ * (out_dev: [n_tok][2][level-1][N] at level - 2): for each r, the sum over the
+ * S fragments of relin(Q' (x) K_r) (Q' = Q with one limb dropped, K_r K rotated
+ * token-wise by r), rescaled, then summed over the P positions (acc +=
+ * Rot(acc, 2^k n)), so D_r holds A[i][(i + r) mod n] at slot f n + i of every
+ * position f.  *out_scale = (q_scale ((k_scale ms) / q_l)) / q_{l-1}.
+ * fe_he_attention_apply: D (n_tok ciphertexts at d_level, scale d_scale) and V
+ * ([S] at v_level) -> O = A V in V's layout: for each fragment of V,
+ * sum over r of relin(D_r (x) V_r), V_r V rotated token-wise by r, the higher
+ * of the two with limbs dropped to meet the other (level m = min(v_level - 1,
+ * d_level)), rescaled once: *out_level = m - 1, *out_scale = (d_scale
+ * ((v_scale ms) / q_{v_level})) / q_m.  Softmax and other non-linear parts of
+ * attention are not included.  Composed from the library's primitives with
+ * stream-ordered scratch.  Errors: FE_EKEY, FE_ELEVEL, FE_EINVAL, FE_ENOMEM. */
+int fe_attention_rotation_steps(const fe_ctx* ctx, const fe_token_layout* lay, int32_t* steps, uint32_t max,
+                                uint32_t* n_steps);
+int fe_he_attention_scores(fe_ctx* ctx, const fe_evk* evk, const fe_token_layout* lay, const void* q_dev,
+                           const void* k_dev, uint32_t level, double q_scale, double k_scale, void* out_dev,
+                           double* out_scale, void* stream);
+int fe_he_attention_apply(fe_ctx* ctx, const fe_evk* evk, const fe_token_layout* lay, const void* d_dev,
+                          uint32_t d_level, double d_scale, const void* v_dev, uint32_t v_level, double v_scale,
+                          void* out_dev, uint32_t* out_level, double* out_scale, void* stream);
 /* The block-size choice of Sec. 7: the rotation complexity gamma E / S + 2 n S
  * (FFN and projections: embedding aggregation over E / S positions, gamma the
  * FFN's expansion; attention: token-wise aggregation over S times more tokens

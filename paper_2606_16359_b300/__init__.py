@@ -154,6 +154,9 @@ SIGNATURES = {
     "fe_token_unpack": (cint, [vp, P(FeTokenLayout), vp, vp, vp]),
     "fe_plan_token_linear": (cint, [vp, P(FeTokenLayout), u32, u32, P(FeTokenLayout), P(vp)]),
     "fe_choose_token_fragment": (cint, [u32, u32, dbl, u32, P(u32), P(dbl), P(dbl)]),
+    "fe_attention_rotation_steps": (cint, [vp, P(FeTokenLayout), P(i32), u32, P(u32)]),
+    "fe_he_attention_scores": (cint, [vp, vp, P(FeTokenLayout), vp, vp, u32, dbl, dbl, vp, P(dbl), vp]),
+    "fe_he_attention_apply": (cint, [vp, vp, P(FeTokenLayout), vp, u32, dbl, vp, u32, dbl, vp, P(u32), P(dbl), vp]),
     "fe_he_repack": (cint, [vp, vp, vp, vp, vp, vp, vp, sz, cint, vp]),
     "fe_fc_unpack": (cint, [vp, vp, vp, vp, vp]),
     "fe_weight_scale": (cint, [vp, u32, dbl, dbl, dbl, P(dbl)]),
@@ -727,6 +730,36 @@ class Context:
         p = Plan(self, h)
         p.level, p.token_out = level, out_lay
         return p
+
+    def attention_rotation_steps(self, lay):
+        n = u32()
+        check(load().fe_attention_rotation_steps(self.handle, ctypes.byref(lay), None, 0, ctypes.byref(n)))
+        arr = (i32 * max(1, n.value))()
+        check(load().fe_attention_rotation_steps(self.handle, ctypes.byref(lay), arr, n.value, ctypes.byref(n)))
+        return [arr[i] for i in range(n.value)]
+
+    def he_attention_scores(self, evk, lay, q, k, level, q_scale, k_scale):
+        """Diagonals of Q K^T: returns (out [n_tok, 2, level-1, N], out_scale)."""
+        for t in (q, k):
+            if t.numel() != lay.n_ct * self.ct_words(level):
+                raise ValueError("Q and K must hold S ciphertexts at `level`")
+        out = self.empty_ct(lay.n_tok, level - 2)
+        sc = dbl()
+        check(load().fe_he_attention_scores(self.handle, evk.handle, ctypes.byref(lay), _ptr(q), _ptr(k), level,
+                                            float(q_scale), float(k_scale), _ptr(out), ctypes.byref(sc), _stream()))
+        return out, sc.value
+
+    def he_attention_apply(self, evk, lay, d, d_level, d_scale, v, v_level, v_scale):
+        """(Q K^T) V from the score diagonals: returns (out, out_level, out_scale)."""
+        if d.numel() != lay.n_tok * self.ct_words(d_level) or v.numel() != lay.n_ct * self.ct_words(v_level):
+            raise ValueError("D must hold n_tok ciphertexts at d_level, V S at v_level")
+        ml = min(v_level - 1, d_level)
+        out = self.empty_ct(lay.n_ct, ml - 1)
+        lv, sc = u32(), dbl()
+        check(load().fe_he_attention_apply(self.handle, evk.handle, ctypes.byref(lay), _ptr(d), d_level,
+                                           float(d_scale), _ptr(v), v_level, float(v_scale), _ptr(out),
+                                           ctypes.byref(lv), ctypes.byref(sc), _stream()))
+        return out, lv.value, sc.value
 
     def plan_fc_next(self, prev, F_out, level):
         h = vp()

@@ -1,0 +1,284 @@
+// Attention products of the transformer extension (Sec. 7) on fragmented
+// token embeddings (fe_token_layout: element f S + s of token t in ciphertext s,
+// slot f n + t).  The token-wise aggregation the paper names for Q K^T and A V
+// is done with token-wise rotations: every position block of n token slots is
+// rotated by r tokens as M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n), the masks
+// selecting the tokens t < n - r and t >= n - r, encoded at a power of two
+// (their coefficients are rationals with denominators dividing N: at 2^k >= N
+// none falls on a rounding tie, as one can at a prime scale).
+//
+// These layers are composed from the library's primitives (rotation, PMult,
+// addition, CMult with relinearisation, rescale) in a fixed order, so that
+// their residues equal the oracle's step for step; their scratch comes from the
+// stream-ordered allocator.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ops.h"
+
+extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                         int32_t r, void* out_dev, void* stream);
+extern "C" int fe_encode(fe_ctx* c, const double* slots_dev, uint32_t n, uint32_t level, double scale, void* pt_dev,
+                         void* stream);
+extern "C" int fe_pmult(fe_ctx* c, const void* ct_dev, const void* pt_dev, uint32_t n_ct, uint32_t level,
+                        void* out_dev, void* stream);
+extern "C" int fe_add(fe_ctx* c, const void* a_dev, const void* b_dev, uint32_t n_ct, uint32_t level, void* out_dev,
+                      void* stream);
+extern "C" int fe_rescale(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
+                          void* stream);
+extern "C" int fe_token_layout_make(const fe_ctx* c, fe_token_layout* t);
+
+namespace fe {
+namespace {
+constexpr int kB = 256;
+
+// slot l -> 1 when its token (l mod n) is below n - r (lo) / at or above it (hi)
+__global__ void k_token_mask(double* lo, double* hi, int n, int r, int half) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= half) return;
+    const bool below = (l % n) < n - r;
+    lo[l] = below ? 1.0 : 0.0;
+    hi[l] = below ? 0.0 : 1.0;
+}
+
+// out = in times the per-limb constant k[i] (both polynomials), n ciphertexts at `level`
+__global__ void k_mul_const(const u64* in, u64* out, const Modulus* mods, const u64* k, int nl, int logN) {
+    const int N = 1 << logN;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int limb = blockIdx.y, ci = blockIdx.z;  // limb over 2 nl
+    const int i = limb % nl;
+    const size_t o = ((size_t)ci * 2 * nl + limb) * N + x;
+    out[o] = mul_mod(in[o], k[i], mods[i]);
+}
+
+// first l limbs of each polynomial of n ciphertexts at level l (modulus dropped to Q_{l-1})
+__global__ void k_drop_limb(const u64* in, u64* out, int nl_in, int logN) {
+    const int N = 1 << logN;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int nl_out = nl_in - 1;
+    const int limb = blockIdx.y, ci = blockIdx.z;  // limb over 2 nl_out
+    const int poly = limb / nl_out, i = limb % nl_out;
+    out[(((size_t)ci * 2 + poly) * nl_out + i) * N + x] = in[(((size_t)ci * 2 + poly) * nl_in + i) * N + x];
+}
+
+struct Dev {
+    void* p = nullptr;
+    cudaStream_t st;
+    explicit Dev(cudaStream_t s) : st(s) {}
+    ~Dev() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    template <class T>
+    T* get(size_t count) {
+        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) return nullptr;
+        return (T*)p;
+    }
+};
+
+double mask_scale_pow2(const fe_ctx* c, int level) {
+    return std::ldexp(1.0, 63 - __builtin_clzll(c->mod[level]));
+}
+
+// out = x with its last limb dropped (n ciphertexts at `level`)
+int drop_limb(fe_ctx* c, const u64* x, int n, int level, u64* out, cudaStream_t st) {
+    k_drop_limb<<<dim3((c->N + kB - 1) / kB, 2 * level, n), kB, 0, st>>>(x, out, level + 1, c->logN);
+    c->cnt.launches++;
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+// token-wise rotation of one ciphertext at `level` by r tokens (one level):
+// out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n)), masks at ms;
+// r = 0: rescale(x times the integer ms)
+int token_rotate(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int level, int r, double ms,
+                 u64* out, cudaStream_t st) {
+    const size_t ctw = ct_words(c, level);
+    Dev buf(st);
+    u64* tmp = buf.get<u64>(2 * ctw);
+    if (!tmp) return fail(FE_ENOMEM, "token rotation scratch");
+    if (r == 0) {
+        Dev kb(st);
+        u64* k = kb.get<u64>(level + 1);
+        if (!k) return fail(FE_ENOMEM, "token rotation scratch");
+        std::vector<u64> kh(level + 1);
+        const u64 m = (u64)ms;  // a power of two below the modulus
+        for (int i = 0; i <= level; i++) kh[i] = m % c->mod[i];
+        FE_CUDA_TRY(cudaMemcpyAsync(k, kh.data(), kh.size() * 8, cudaMemcpyHostToDevice, st));
+        k_mul_const<<<dim3((c->N + kB - 1) / kB, 2 * (level + 1), 1), kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1,
+                                                                                 c->logN);
+        c->cnt.launches++;
+        FE_CUDA_TRY(cudaGetLastError());
+        return fe_rescale(c, tmp, 1, level, out, st);
+    }
+    const int half = c->N / 2, n = (int)T.n_tok;
+    Dev sb(st), pb(st);
+    double* slots = sb.get<double>(2 * (size_t)half);
+    u64* pts = pb.get<u64>(2 * (size_t)(level + 1) * c->N);
+    if (!slots || !pts) return fail(FE_ENOMEM, "token rotation scratch");
+    k_token_mask<<<(half + kB - 1) / kB, kB, 0, st>>>(slots, slots + half, n, r, half);
+    c->cnt.launches++;
+    FE_TRY(fe_encode(c, slots, 2, level, ms, pts, st));
+    u64* a = tmp;
+    u64* b = tmp + ctw;
+    FE_TRY(fe_rotate(c, evk, x, 1, level, r, a, st));
+    FE_TRY(fe_rotate(c, evk, x, 1, level, r - n, b, st));
+    FE_TRY(fe_pmult(c, a, pts, 1, level, a, st));
+    FE_TRY(fe_pmult(c, b, pts + (size_t)(level + 1) * c->N, 1, level, b, st));
+    FE_TRY(fe_add(c, a, b, 1, level, a, st));
+    return fe_rescale(c, a, 1, level, out, st);
+}
+
+// acc += Rot(acc, 2^k n) for k = 0 .. log2(P) - 1 (one ciphertext at `level`)
+int position_sum(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, u64* acc, int level, cudaStream_t st) {
+    Dev rb(st);
+    u64* rot = rb.get<u64>(ct_words(c, level));
+    if (!rot) return fail(FE_ENOMEM, "position sum scratch");
+    for (uint32_t step = T.n_tok; step < (uint32_t)c->N / 2; step *= 2) {
+        FE_TRY(fe_rotate(c, evk, acc, 1, level, (int32_t)step, rot, st));
+        FE_TRY(fe_add(c, acc, rot, 1, level, acc, st));
+    }
+    return FE_OK;
+}
+
+// d = relin(x (x) y) at `level` (one pair)
+int cmult_one(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int level, u64* d, cudaStream_t st) {
+    const size_t bytes = cmult_relin_bytes(c, 1, level);
+    Dev wb(st);
+    char* ws = wb.get<char>(bytes);
+    if (!ws) return fail(FE_ENOMEM, "CMult scratch");
+    Carver cv(ws, bytes);
+    return cmult_relin(c, evk, x, y, 1, level, d, cv, st);
+}
+
+int check_common(fe_ctx* c, const fe_evk* evk, const fe_token_layout* lay, fe_token_layout* T) {
+    if (!c || !evk || !lay) return fail(FE_EINVAL, "null argument");
+    if (!evk->relin) return fail(FE_EKEY, "no relinearisation key");
+    *T = *lay;
+    FE_TRY(fe_token_layout_make(c, T));
+    for (uint32_t r = 1; r < T->n_tok; r++)
+        for (int32_t s : {(int32_t)r, (int32_t)r - (int32_t)T->n_tok})
+            if (!evk_key(evk, c->galois(s))) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(s));
+    for (uint32_t step = T->n_tok; step < (uint32_t)c->N / 2; step *= 2)
+        if (!evk_key(evk, c->galois((int32_t)step)))
+            return fail(FE_EKEY, "missing rotation key for step " + std::to_string(step));
+    return FE_OK;
+}
+}  // namespace
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" int fe_attention_rotation_steps(const fe_ctx* c, const fe_token_layout* lay, int32_t* steps, uint32_t max,
+                                           uint32_t* n_steps) {
+    if (!c || !lay || !n_steps) return fail(FE_EINVAL, "null argument");
+    fe_token_layout T = *lay;
+    FE_TRY(fe_token_layout_make(c, &T));
+    std::vector<int32_t> v;
+    for (int32_t r = 1; r < (int32_t)T.n_tok; r++) {
+        v.push_back(r - (int32_t)T.n_tok);
+        v.push_back(r);
+    }
+    for (uint32_t step = T.n_tok; step < (uint32_t)c->N / 2; step *= 2) v.push_back((int32_t)step);
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    *n_steps = (uint32_t)v.size();
+    if (steps)
+        for (size_t i = 0; i < v.size() && i < max; i++) steps[i] = v[i];
+    return FE_OK;
+}
+
+extern "C" int fe_he_attention_scores(fe_ctx* c, const fe_evk* evk, const fe_token_layout* lay, const void* q_dev,
+                                      const void* k_dev, uint32_t level, double q_scale, double k_scale,
+                                      void* out_dev, double* out_scale, void* stream) {
+    fe_token_layout T;
+    FE_TRY(check_common(c, evk, lay, &T));
+    if (!q_dev || !k_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(q_dev);
+    FE_ALIGNED(k_dev);
+    FE_ALIGNED(out_dev);
+    if (level < 2 || (int)level > c->L) return fail(FE_ELEVEL, "the attention scores need two levels");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int lv = (int)level;
+    const double ms = mask_scale_pow2(c, lv);
+    const size_t ctw = ct_words(c, lv), ctw1 = ct_words(c, lv - 1), ctw2 = ct_words(c, lv - 2);
+    Dev qb(st), wb(st);
+    u64* qd = qb.get<u64>(T.n_ct * ctw1);          // Q with one limb dropped
+    u64* work = wb.get<u64>(3 * ctw1);              // rotated K, product, running sum
+    if (!qd || !work) return fail(FE_ENOMEM, "attention scratch");
+    FE_TRY(drop_limb(c, (const u64*)q_dev, (int)T.n_ct, lv, qd, st));
+    u64 *kr = work, *prod = work + ctw1, *acc = work + 2 * ctw1;
+    for (uint32_t r = 0; r < T.n_tok; r++) {
+        for (uint32_t s = 0; s < T.n_ct; s++) {
+            FE_TRY(token_rotate(c, evk, T, (const u64*)k_dev + s * ctw, lv, (int)r, ms, kr, st));
+            FE_TRY(cmult_one(c, evk, qd + s * ctw1, kr, lv - 1, s == 0 ? acc : prod, st));
+            if (s) FE_TRY(fe_add(c, acc, prod, 1, lv - 1, acc, st));
+        }
+        u64* d = (u64*)out_dev + r * ctw2;
+        FE_TRY(fe_rescale(c, acc, 1, lv - 1, d, st));
+        FE_TRY(position_sum(c, evk, T, d, lv - 2, st));
+    }
+    // scales as the operations change them: K rotated (k ms) / q_l, product q (.),
+    // rescale by q_{l-1}
+    const double kr_scale = (k_scale * ms) / (double)c->mod[lv];
+    if (out_scale) *out_scale = (q_scale * kr_scale) / (double)c->mod[lv - 1];
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_token_layout* lay, const void* d_dev,
+                                     uint32_t d_level, double d_scale, const void* v_dev, uint32_t v_level,
+                                     double v_scale, void* out_dev, uint32_t* out_level, double* out_scale,
+                                     void* stream) {
+    fe_token_layout T;
+    FE_TRY(check_common(c, evk, lay, &T));
+    if (!d_dev || !v_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    FE_ALIGNED(d_dev);
+    FE_ALIGNED(v_dev);
+    FE_ALIGNED(out_dev);
+    if (v_level < 1 || (int)v_level > c->L || d_level < 1 || (int)d_level > c->L)
+        return fail(FE_ELEVEL, "level out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int vl = (int)v_level, dl = (int)d_level;
+    const int ml = std::min(vl - 1, dl);  // level of the products
+    if (ml < 1) return fail(FE_ELEVEL, "the attention output needs a level to rescale");
+    const double ms = mask_scale_pow2(c, vl);
+    const size_t ctwv = ct_words(c, vl), ctwd = ct_words(c, dl), ctwm = ct_words(c, ml);
+    Dev wb(st), tb(st);
+    u64* work = wb.get<u64>(3 * ct_words(c, vl - 1));
+    u64* tmp = tb.get<u64>(2 * ct_words(c, std::max(vl - 1, dl)));
+    if (!work || !tmp) return fail(FE_ENOMEM, "attention scratch");
+    u64 *vr = work, *prod = work + ct_words(c, vl - 1), *acc = work + 2 * ct_words(c, vl - 1);
+    for (uint32_t s = 0; s < T.n_ct; s++) {
+        for (uint32_t r = 0; r < T.n_tok; r++) {
+            FE_TRY(token_rotate(c, evk, T, (const u64*)v_dev + s * ctwv, vl, (int)r, ms, vr, st));
+            // drop the higher of the two to the products' level, one limb at a time
+            const u64* x = (const u64*)d_dev + r * ctwd;
+            const u64* y = vr;
+            u64* bx = tmp;
+            u64* by = tmp + ct_words(c, std::max(vl - 1, dl));
+            for (int l = dl; l > ml; l--) {
+                u64* dst = (x == bx) ? by : bx;
+                FE_TRY(drop_limb(c, x, 1, l, dst, st));
+                x = dst;
+            }
+            for (int l = vl - 1; l > ml; l--) {
+                u64* dst = (y == bx || x == bx) ? by : bx;
+                FE_TRY(drop_limb(c, y, 1, l, dst, st));
+                y = dst;
+            }
+            FE_TRY(cmult_one(c, evk, x, y, ml, r == 0 ? acc : prod, st));
+            if (r) FE_TRY(fe_add(c, acc, prod, 1, ml, acc, st));
+        }
+        FE_TRY(fe_rescale(c, acc, 1, ml, (u64*)out_dev + s * ct_words(c, ml - 1), st));
+    }
+    (void)ctwm;
+    const double vr_scale = (v_scale * ms) / (double)c->mod[vl];
+    if (out_level) *out_level = (uint32_t)(ml - 1);
+    if (out_scale) *out_scale = (d_scale * vr_scale) / (double)c->mod[ml];
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}

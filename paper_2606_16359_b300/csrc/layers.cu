@@ -115,9 +115,11 @@ int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const Af
     return FE_OK;
 }
 
-// d = relin(in (x) in) on Q_level for n ciphertexts, no rescale (CMult + relinearisation)
-int square_relin(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, u64* d, Carver& cv,
-                 cudaStream_t st) {
+}  // namespace
+
+// d = relin(x (x) y) on Q_level for n pairs of ciphertexts, no rescale (CMult + relinearisation)
+int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,
+                cudaStream_t st) {
     const int N = c->N, nl = level + 1;
     KsScratch s;
     carve_ks(cv, c, n, level, &s);
@@ -136,7 +138,7 @@ int square_relin(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, 
     FE_TRY(upload(ks, s.ks, st));
     FE_TRY(upload(kg, s.kg, st));
     FE_TRY(upload(cb, dcb, st));
-    launch_tensor(c, in, in, d012, n, level, st);
+    launch_tensor(c, x, y, d012, n, level, st);
     modup(c, d012 + 2 * (size_t)nl * N, 3 * (size_t)nl * N, n, level, s.coef, s.ext, st);
     launch_keyip_grouped(c, s.kg, s.ks, 1, n, level, st);
     moddown_prepare(c, s.acc, n, level, s.conv, st);
@@ -144,6 +146,17 @@ int square_relin(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, 
     c->cnt.cmult += n;
     c->cnt.keyswitch += n;
     return FE_OK;
+}
+
+size_t cmult_relin_bytes(const fe_ctx* c, int n, int level) {
+    return ks_scratch_bytes(c, n, level) + (size_t)n * (3 * (level + 1)) * c->N * 8 +
+           (size_t)n * sizeof(CombineItem) + 4 * 256;
+}
+
+namespace {
+int square_relin(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, u64* d, Carver& cv,
+                 cudaStream_t st) {
+    return cmult_relin(c, evk, in, in, n, level, d, cv, st);
 }
 
 }  // namespace

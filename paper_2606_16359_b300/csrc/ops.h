@@ -40,6 +40,12 @@ size_t rescale_tmp_words(const fe_ctx* c, int n, int level);
 
 const u64* evk_key(const fe_evk* evk, uint32_t galois);
 
+// d = relin(x (x) y) for n pairs of ciphertexts at `level` (CMult with
+// relinearisation, no rescale); scratch carved from cv (cmult_relin_bytes).
+int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,
+                cudaStream_t st);
+size_t cmult_relin_bytes(const fe_ctx* c, int n, int level);
+
 // upload a host vector into a device region carved from a workspace
 template <class T>
 int upload(const std::vector<T>& v, T* dst, cudaStream_t st) {

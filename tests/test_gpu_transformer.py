@@ -102,3 +102,45 @@ def test_ffn_chain_bit_exact_and_fp64():
     assert sc2 == oout[0].scale
     t = x @ w1.T
     assert np.abs(y - (a * t * t + b * t + c) @ w2.T).max() < 1e-3
+
+
+def test_attention_products_bit_exact_and_fp64():
+    """Q K^T diagonals and (Q K^T) V on fragmented tokens (4 tokens, E = 16,
+    S = 2, N = 2^10 with 40-bit primes): residues and scales equal the
+    oracle's, decryption equals FP64 within 1e-3."""
+    args = (10, 6, 1, 40, 40)
+    delta = 2.0 ** 35
+    n, E, S = 4, 16, 2
+    pr = ckks.Params(*args)
+    tl = fragment.TokenLayout(pr.N, n, E, S)
+    rng = np.random.default_rng(1)
+    Q, K, V = (rng.uniform(-1, 1, (n, E)) for _ in range(3))
+    steps = henn.attention_rotation_steps(tl)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = fe.Context(*args)
+        L = g.L
+        lay = g.token_layout(n, E, S)
+        assert g.attention_rotation_steps(lay) == steps
+        sk = g.sk_gen(2)
+        evk = g.evk_gen(sk, 2, steps, relin=True)
+        enc = [g.encrypt(sk, g.token_pack(lay, torch.from_numpy(X)), L, delta, sd, ct_id0=0)
+               for X, sd in ((Q, 3), (K, 4), (V, 5))]
+        D, d_scale = g.he_attention_scores(evk, lay, enc[0], enc[1], L, delta, delta)
+        got_d = u64(D)
+        O, o_level, o_scale = g.he_attention_apply(evk, lay, D, L - 2, d_scale, enc[2], L, delta)
+        got_o = u64(O)
+        y = g.token_unpack(lay, g.decrypt(sk, O, o_level, o_scale)).cpu().numpy()
+        assert g.device_status() == 0
+    keys = ckks.KeySet(pr, 2, rot_steps=steps, relin=True)
+
+    def oenc(X, sd):
+        sl = fragment.pack_tokens(tl, X)
+        return [ckks.encrypt(pr, keys.sk, ckks.encode(pr, sl[i], pr.L, delta), sd, i) for i in range(S)]
+    od = henn.he_attention_scores(pr, keys, oenc(Q, 3), oenc(K, 4), tl)
+    assert np.array_equal(got_d, np.stack([d.as_array() for d in od]))
+    assert d_scale == od[0].scale
+    oo = henn.he_attention_apply(pr, keys, od, oenc(V, 5), tl)
+    assert np.array_equal(got_o, np.stack([o.as_array() for o in oo]))
+    assert o_scale == oo[0].scale and o_level == oo[0].level
+    assert np.abs(y - (Q @ K.T) @ V).max() < 1e-3
