@@ -183,3 +183,53 @@ def test_mac_wait_expiry_sets_the_status_and_leaves_the_context_usable(g, keys):
     assert g.device_status() == 0
     with pytest.raises(fe.FencError):
         g.set_mac_wait(0, -1)
+
+
+def test_error_contract_of_the_layers_added_around_the_convolution(g, keys):
+    """The activation, masked AAC, scale rule, block-size change, token layout
+    and attention calls return their status before any launch, and the
+    context stays usable."""
+    sk, evk = keys
+    lib, s = fe.load(), fe._stream()
+    ct = g.encrypt(sk, _slots(g, 1, 12), g.L, 2.0 ** 25, seed=12)
+    out = g.empty_ct(1, g.L)
+    ws = g.workspace(1 << 20)
+    sc = ctypes.c_double()
+    # activation: level 0, non-finite coefficient, a != 0 without a relinearisation key
+    assert lib.fe_he_poly_act(g.handle, evk.handle, 1.0, 0.0, 0.0, P(ct), 1, 0, 2.0 ** 25, P(out), ctypes.byref(sc),
+                              P(ws), ws.numel() * 8, s) == fe.FE_ELEVEL
+    assert lib.fe_he_poly_act(g.handle, evk.handle, float("nan"), 0.0, 0.0, P(ct), 1, g.L, 2.0 ** 25, P(out),
+                              ctypes.byref(sc), P(ws), ws.numel() * 8, s) == fe.FE_EINVAL
+    assert lib.fe_he_poly_act(g.handle, evk.handle, 1.0, 0.0, 0.0, P(ct), 1, g.L, 2.0 ** 25, P(out),
+                              ctypes.byref(sc), P(ws), ws.numel() * 8, s) == fe.FE_EKEY
+    # masked AAC: a mask scale below 1
+    lay = g.layout(4, 4, 1, 1, 1)
+    assert lib.fe_compress_masked(g.handle, evk.handle, ctypes.byref(lay), 1, 0.5, P(ct), 1, g.L, 2.0 ** 25, P(out),
+                                  ctypes.byref(sc), P(ws), ws.numel() * 8, s) == fe.FE_EINVAL
+    # scale rule and plan scales
+    assert lib.fe_weight_scale(g.handle, 0, 1.0, 1.0, 0.0, ctypes.byref(sc)) == fe.FE_ELEVEL
+    assert lib.fe_poly_act_scale(g.handle, g.L, -1.0, 1.0, ctypes.byref(sc)) == fe.FE_EINVAL
+    plan = g.plan_conv(g.layout(6, 6, 2, 1, 2), 3, 3)
+    assert lib.fe_plan_out_scale(plan.handle, 1.0, ctypes.byref(sc)) == fe.FE_EINVAL  # weights not loaded
+    # block-size change between layouts of different maps
+    h = ctypes.c_void_p()
+    la, lb = g.layout(6, 6, 2, 1, 2), g.layout(6, 6, 3, 1, 1)
+    assert lib.fe_plan_repack(g.handle, ctypes.byref(la), ctypes.byref(lb), g.L, ctypes.byref(h)) == fe.FE_EINVAL
+    # token layout that does not fit, attention without its keys
+    bad = fe.FeTokenLayout(4, 4000, 2, 0, 0, 0)
+    assert lib.fe_token_layout_make(g.handle, ctypes.byref(bad)) == fe.FE_EINVAL
+    tl = g.token_layout(4, 16, 2)
+    relin_only = g.evk_gen(sk, 21, [1], relin=True)
+    assert lib.fe_he_attention_scores(g.handle, relin_only.handle, ctypes.byref(tl), P(ct), P(ct), g.L, 1.0, 1.0,
+                                      P(out), ctypes.byref(sc), s) == fe.FE_EKEY
+    # wait limits out of range
+    assert lib.fe_ctx_set_mac_wait(g.handle, 0, -1) == fe.FE_EINVAL
+    assert lib.fe_ctx_set_mac_wait(g.handle, 1000, -2) == fe.FE_EINVAL
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    # still usable: the affine case a = 0 needs no relinearisation key
+    z = _slots(g, 1, 13)
+    c2 = g.encrypt(sk, z, g.L, 2.0 ** 25, seed=13)
+    o, osc = g.he_poly_act(evk, c2, g.L, 2.0 ** 25, 0.0, 0.5, 0.25)
+    y = g.decrypt(sk, o, g.L - 1, osc).cpu().numpy()
+    assert np.abs(y - (0.5 * z.numpy() + 0.25)).max() < 1e-3
