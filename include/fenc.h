@@ -633,6 +633,19 @@ int fe_graph_capture_batch(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const*
                            const void* const* pts_host, const void* const* ins_host,
                            void* const* outs_host, uint32_t n, uint32_t n_req, void* workspace_dev,
                            size_t workspace_bytes, void* stream, fe_graph** out);
+/* As fe_graph_capture_batch, with the requests of every layer taken req_chunk
+ * at a time (the last chunk may be smaller): each chunk's kernels run in
+ * order over one data region sized for req_chunk requests, so the workspace
+ * (fe_graph_workspace_bytes_chunked) grows with n_req only through the item
+ * tables.  Residues are the same as with one chunk.  For request counts whose
+ * hoisted rotated copies do not fit the device at once.  Errors as
+ * fe_graph_capture_batch. */
+size_t fe_graph_workspace_bytes_chunked(const fe_plan* const* plans_host, uint32_t n, uint32_t n_req,
+                                        uint32_t req_chunk);
+int fe_graph_capture_chunked(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
+                             const void* const* pts_host, const void* const* ins_host, void* const* outs_host,
+                             uint32_t n, uint32_t n_req, uint32_t req_chunk, void* workspace_dev,
+                             size_t workspace_bytes, void* stream, fe_graph** out);
 int fe_graph_launch(fe_graph* graph, void* stream);
 /* The captured sequence's host-visible ends: its external inputs (layer inputs
  * that no earlier layer of the graph writes) and final outputs (layer outputs

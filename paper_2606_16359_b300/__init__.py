@@ -181,6 +181,8 @@ SIGNATURES = {
     "fe_graph_capture": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, vp, sz, vp, P(vp)]),
     "fe_graph_capture_batch": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, u32, vp, sz, vp, P(vp)]),
     "fe_graph_workspace_bytes": (sz, [P(vp), u32, u32]),
+    "fe_graph_workspace_bytes_chunked": (sz, [P(vp), u32, u32, u32]),
+    "fe_graph_capture_chunked": (cint, [vp, vp, P(vp), P(vp), P(vp), P(vp), u32, u32, u32, vp, sz, vp, P(vp)]),
     "fe_graph_launch": (cint, [vp, vp]),
     "fe_graph_io": (cint, [vp, P(u32), P(sz), P(u32), P(sz)]),
     "fe_graph_launch_host": (cint, [vp, P(vp), P(vp), vp]),
@@ -612,15 +614,24 @@ class Context:
         parr = (vp * n)(*[p.handle.value for p in plans])
         return int(load().fe_graph_workspace_bytes(parr, n, n_req))
 
-    def graph_capture(self, evk, plans, pts, ins, outs, ws, n_req=1):
+    def graph_workspace_bytes_chunked(self, plans, n_req, req_chunk):
+        n = len(plans)
+        parr = (vp * n)(*[p.handle.value for p in plans])
+        return int(load().fe_graph_workspace_bytes_chunked(parr, n, n_req, req_chunk))
+
+    def graph_capture(self, evk, plans, pts, ins, outs, ws, n_req=1, req_chunk=None):
         n = len(plans)
         parr = (vp * n)(*[p.handle.value for p in plans])
         ptarr = (vp * n)(*[t.data_ptr() for t in pts])
         iarr = (vp * n)(*[t.data_ptr() for t in ins])
         oarr = (vp * n)(*[t.data_ptr() for t in outs])
         h = vp()
-        check(load().fe_graph_capture_batch(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, n_req, _ptr(ws),
-                                            ws.numel() * 8, _stream(), ctypes.byref(h)))
+        if req_chunk is None:
+            check(load().fe_graph_capture_batch(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, n_req, _ptr(ws),
+                                                ws.numel() * 8, _stream(), ctypes.byref(h)))
+        else:
+            check(load().fe_graph_capture_chunked(self.handle, evk.handle, parr, ptarr, iarr, oarr, n, n_req,
+                                                  req_chunk, _ptr(ws), ws.numel() * 8, _stream(), ctypes.byref(h)))
         return Graph(h, (plans, pts, ins, outs, ws))
 
     def profile_begin(self, kind):

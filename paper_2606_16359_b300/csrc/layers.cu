@@ -501,6 +501,102 @@ extern "C" int fe_graph_capture_batch(fe_ctx* c, const fe_evk* evk, const fe_pla
     return FE_OK;
 }
 
+extern "C" size_t fe_graph_workspace_bytes_chunked(const fe_plan* const* plans, uint32_t n, uint32_t n_req,
+                                                   uint32_t req_chunk) {
+    if (!plans || n_req == 0 || req_chunk == 0) return 0;
+    for (uint32_t i = 0; i < n; i++)
+        if (!plans[i]) return 0;
+    const uint32_t rc = std::min(req_chunk, n_req);
+    const size_t data = graph_data_bytes(plans, n, rc);
+    size_t tables = 0;
+    for (uint32_t i = 0; i < n; i++)
+        for (uint32_t r0 = 0; r0 < n_req; r0 += rc) {
+            const uint32_t nr = std::min(rc, n_req - r0);
+            tables += (plan_table_bytes(plans[i], plan_chunk(plans[i], nr, 1, data, true), nr) + 255) & ~(size_t)255;
+        }
+    return tables + data;
+}
+
+extern "C" int fe_graph_capture_chunked(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans,
+                                        const void* const* pts, const void* const* ins, void* const* outs, uint32_t n,
+                                        uint32_t n_req, uint32_t req_chunk, void* ws, size_t ws_bytes, void* stream,
+                                        fe_graph** out) {
+    if (!c || !evk || !plans || !pts || !ins || !outs || !ws || !out) return fail(FE_EINVAL, "null argument");
+    if (n_req == 0 || req_chunk == 0) return fail(FE_EINVAL, "n_req and req_chunk must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!st) return fail(FE_EINVAL, "graph capture needs a non-default stream");
+    FE_ALIGNED(ws);
+    for (uint32_t i = 0; i < n; i++) {
+        if (!plans[i]) return fail(FE_EINVAL, "null plan");
+        FE_ALIGNED(pts[i]);
+        FE_ALIGNED(ins[i]);
+        FE_ALIGNED(outs[i]);
+    }
+    const uint32_t rc = std::min(req_chunk, n_req);
+    const size_t data = graph_data_bytes(plans, n, rc);
+    // item tables per (layer, request chunk), in capture order; one shared data region
+    struct Piece {
+        uint32_t layer, r0, nr;
+        size_t off, bytes;
+    };
+    std::vector<Piece> pieces;
+    size_t off = 0;
+    for (uint32_t i = 0; i < n; i++)
+        for (uint32_t r0 = 0; r0 < n_req; r0 += rc) {
+            const uint32_t nr = std::min(rc, n_req - r0);
+            const size_t b = (plan_table_bytes(plans[i], plan_chunk(plans[i], nr, 1, data, true), nr) + 255) &
+                             ~(size_t)255;
+            pieces.push_back({i, r0, nr, off, b});
+            off += b;
+        }
+    if (off + data > ws_bytes) return fail(FE_ENOMEM, "workspace too small for the captured layers");
+    char* shared = (char*)ws + off;
+    auto in_at = [&](const Piece& q) {
+        return (const u64*)ins[q.layer] + (size_t)q.r0 * plans[q.layer]->n_in * ct_words(c, plans[q.layer]->level);
+    };
+    auto out_at = [&](const Piece& q) {
+        return (u64*)outs[q.layer] + (size_t)q.r0 * plans[q.layer]->n_out * ct_words(c, plans[q.layer]->level - 1);
+    };
+    for (const Piece& q : pieces)
+        FE_TRY(run_plan(c, evk, plans[q.layer], in_at(q), (const u64*)pts[q.layer], out_at(q), (char*)ws + q.off,
+                        q.bytes, 1, st, 1, (int)q.nr, 0, shared, data));
+    FE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::unique_ptr<fe_graph> g(new fe_graph());
+    FE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc_ = FE_OK;
+    for (size_t k = 0; k < pieces.size() && rc_ == FE_OK; k++) {
+        const Piece& q = pieces[k];
+        rc_ = run_plan(c, evk, plans[q.layer], in_at(q), (const u64*)pts[q.layer], out_at(q), (char*)ws + q.off,
+                       q.bytes, 1, st, 2, (int)q.nr, 0, shared, data);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc_ != FE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc_;
+    }
+    if (e != cudaSuccess) return fail(FE_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    g->graph = graph;
+    FE_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
+    for (uint32_t i = 0; i < n; i++) {
+        bool external = true;
+        for (uint32_t j = 0; j < i; j++) external = external && outs[j] != ins[i];
+        bool dup = false;
+        for (const auto& e2 : g->in) dup = dup || e2.dev == ins[i];
+        if (external && !dup)
+            g->in.push_back({const_cast<void*>(ins[i]),
+                             (size_t)n_req * plans[i]->n_in * 2 * (plans[i]->level + 1) * c->limb_bytes()});
+    }
+    for (uint32_t j = 0; j < n; j++) {
+        bool read_later = false;
+        for (uint32_t i = j + 1; i < n; i++) read_later = read_later || ins[i] == outs[j];
+        if (!read_later)
+            g->out.push_back({outs[j], (size_t)n_req * plans[j]->n_out * 2 * plans[j]->level * c->limb_bytes()});
+    }
+    *out = g.release();
+    return FE_OK;
+}
+
 extern "C" int fe_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_plan* const* plans, const void* const* pts,
                                 const void* const* ins, void* const* outs, uint32_t n, void* ws, size_t ws_bytes,
                                 void* stream, fe_graph** out) {

@@ -121,23 +121,28 @@ class MobileNetBlocks:
             self.ctx.he_layer_batch(self.evk, l_["plan"], l_["pt"], l_["inp"], self.batch, mode=mode, ws=self.ws,
                                     out=l_["out"])
 
-    def capture(self, concurrent=True):
+    def capture(self, concurrent=True, req_chunk=None):
         """CUDA graph(s) of one step.  concurrent: the blocks are independent, so
         each gets its own graph, workspace and stream and launch() runs them side
         by side (one block's kernels and copies overlap another's); otherwise one
-        graph runs all layers in order in one shared workspace."""
+        graph runs all layers in order in one shared workspace.  req_chunk: take
+        the batch's requests that many at a time inside each graph (one data
+        region per graph sized for req_chunk requests)."""
         torch = _torch()
         groups = ([self.layers[2 * b:2 * b + 2] for b in range(len(self.blocks))] if concurrent
                   else [self.layers])
         self.graphs, self.graph_ws, self.streams = [], [], []
         for ls in groups:
             plans = [l_["plan"] for l_ in ls]
-            ws = self.ctx.workspace(self.ctx.graph_workspace_bytes(plans, self.batch))
+            if req_chunk is None:
+                ws = self.ctx.workspace(self.ctx.graph_workspace_bytes(plans, self.batch))
+            else:
+                ws = self.ctx.workspace(self.ctx.graph_workspace_bytes_chunked(plans, self.batch, req_chunk))
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
                 g = self.ctx.graph_capture(self.evk, plans, [l_["pt"] for l_ in ls], [l_["inp"] for l_ in ls],
-                                           [l_["out"] for l_ in ls], ws, n_req=self.batch)
+                                           [l_["out"] for l_ in ls], ws, n_req=self.batch, req_chunk=req_chunk)
             torch.cuda.current_stream().wait_stream(s)
             self.graphs.append(g)
             self.graph_ws.append(ws)

@@ -84,3 +84,33 @@ def test_concurrent_block_graphs_equal_sequential():
         torch.cuda.synchronize()
     for w_, h in zip(want, h_out):
         assert np.array_equal(h.numpy(), w_)
+
+
+def test_request_chunked_graph_equals_one_chunk():
+    """Five inputs per block captured with the requests taken two at a time
+    (fe_graph_capture_chunked: chunks of 2, 2, 1 over one data region per
+    graph, a smaller workspace) give the residues of the unchunked capture,
+    and every input decrypts to its FP64 result."""
+    p = W.PARAMS["mobilenet_small"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        net = MobileNetBlocks(ctx, blocks=[(8, 32, 32), (4, 64, 64)], delta=p["delta"], schedule=4, batch=5)
+        plans = [l_["plan"] for l_ in net.layers[:2]]
+        assert ctx.graph_workspace_bytes_chunked(plans, 5, 2) < ctx.graph_workspace_bytes(plans, 5)
+        net.capture(concurrent=True)
+        net.launch()
+        torch.cuda.synchronize()
+        want = [o.cpu().numpy() for o in net.outputs]
+        for o in net.outputs:
+            o.zero_()
+        net.capture(concurrent=True, req_chunk=2)
+        net.launch()
+        torch.cuda.synchronize()
+        got = [o.cpu().numpy() for o in net.outputs]
+        errs = [float(np.abs(net.decrypt_block(b, r) - net.reference_block(b, r)).max())
+                for b in range(2) for r in range(5)]
+        assert ctx.device_status() == 0
+    for w_, g_ in zip(want, got):
+        assert np.array_equal(g_, w_)
+    assert max(errs) < 1e-3, errs
