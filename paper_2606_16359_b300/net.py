@@ -98,8 +98,14 @@ class MobileNetBlocks:
             self.ref_inputs.append((xs, wd, wp, ppw.out_layout))
         self.outputs = [self.layers[2 * i + 1]["out"] for i in range(len(self.blocks))]
         self.ws_bytes = max(ctx.workspace_bytes(l_["plan"], B) for l_ in self.layers)
-        self.ws = ctx.workspace(self.ws_bytes)
+        self._ws = None  # the eager path's workspace, allocated on first use (graphs bring their own)
         self.graph = None
+
+    @property
+    def ws(self):
+        if self._ws is None:
+            self._ws = self.ctx.workspace(self.ws_bytes)
+        return self._ws
 
     @property
     def keyswitches_per_step(self):
