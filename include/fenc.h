@@ -129,9 +129,10 @@ int fe_choose_fragment(uint32_t N, uint32_t H, uint32_t W, uint32_t Cin, uint32_
  * [1,8], primes above 61 bits), FE_ECUDA. */
 int fe_ctx_create(const fe_params* params, fe_ctx** out);
 void fe_ctx_destroy(fe_ctx* ctx);
-/* Tile choice of the NTT: elements a thread holds per round, 8 (default) or 16
- * (fewer shared-memory round trips, more registers; compiled for N = 2^14 and
- * 2^16, other ring degrees stay at 8).  Results do not depend on it.
+/* Tile choice of the NTT: elements a thread holds per round, 8 (default), 16
+ * (fewer shared-memory round trips, more registers) or 4 (more rounds, fewer
+ * registers, more resident warps); 4 and 16 are compiled for N = 2^14 and
+ * 2^16, other ring degrees stay at 8.  Results do not depend on it.
  * Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
 /* Butterfly product of the inverse NTT when every modulus is below 2^36:

@@ -153,7 +153,7 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
 // round structure and every shift fold into constants; kLogN = 0 reads it at run time.
 // CTAs of kTile / 2^kLE threads; the bound lets 9 radix-8 CTAs (36 warps) share an SM
 template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE, bool kQ36>
-__global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : 8) ntt_pass(NttArgs a, int first) {
+__global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6)) ntt_pass(NttArgs a, int first) {
     constexpr int kEE = 1 << kLE;
     extern __shared__ u64 tile[];
     const int logN = kLogN ? kLogN : a.logN;
@@ -364,6 +364,8 @@ void launch_pass(int logN, bool nored, bool q36, dim3 g, int t, size_t sm, cudaS
                  int first, int le) {
     if (le == 4 && logN == 16) return launch_one<16, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
     if (le == 4 && logN == 14) return launch_one<14, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
+    if (le == 2 && logN == 16) return launch_one<16, kInv, kCol, 2>(nored, q36, g, t, sm, st, a, first);
+    if (le == 2 && logN == 14) return launch_one<14, kInv, kCol, 2>(nored, q36, g, t, sm, st, a, first);
     switch (logN) {
         case 10: launch_one<10, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
         case 11: launch_one<11, kInv, kCol>(nored, q36, g, t, sm, st, a, first); break;
@@ -387,7 +389,8 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const size_t smc = (size_t)(N1 + (N1 >> 3) + 1) * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
     // algorithmic bytes of a limb transform, 2 N w, split over its two passes
     const double bytes = 8.0 * limbs * N;
-    const int le = (c->ntt_radix == 16 && (c->logN == 14 || c->logN == 16)) ? 4 : 3;
+    const bool big = c->logN == 14 || c->logN == 16;
+    const int le = big && c->ntt_radix == 16 ? 4 : (big && c->ntt_radix == 4 ? 2 : 3);
     const int tc = threads_for(C, N1, 1 << le), tr = threads_for(R, N2, 1 << le);
     const bool nored = c->max_mod_bits <= 58;
     // every modulus below 2^36: the 36-bit Shoup product in the inverse passes (inputs below
@@ -457,7 +460,7 @@ extern "C" int fe_ctx_set_ntt_q36(fe_ctx* c, int enable) {
 
 extern "C" int fe_ctx_set_ntt_radix(fe_ctx* c, int radix) {
     if (!c) return fe::fail(FE_EINVAL, "null argument");
-    if (radix != 8 && radix != 16) return fe::fail(FE_EINVAL, "NTT radix must be 8 or 16");
+    if (radix != 4 && radix != 8 && radix != 16) return fe::fail(FE_EINVAL, "NTT radix must be 4, 8 or 16");
     c->ntt_radix = radix;
     return FE_OK;
 }
