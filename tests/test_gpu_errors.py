@@ -52,6 +52,13 @@ def test_empty_batches_succeed_and_touch_nothing(g, keys):
     assert lib.fe_add(g.handle, P(src), P(src), 0, g.L, P(out), s) == fe.FE_OK
     assert lib.fe_encode_encrypt(g.handle, P(sk), P(slots), 0, g.L, 2.0 ** 25, 5, 0, P(out), s) == fe.FE_OK
     assert lib.fe_decrypt_decode(g.handle, P(sk), P(src), 0, g.L, 2.0 ** 25, P(slots), s) == fe.FE_OK
+    ws = g.workspace(1 << 16)
+    sc = ctypes.c_double()
+    assert lib.fe_he_poly_act(g.handle, evk.handle, 0.0, 0.5, 0.25, P(src), 0, g.L, 2.0 ** 25, P(out),
+                              ctypes.byref(sc), P(ws), ws.numel() * 8, s) == fe.FE_OK
+    lay = g.layout(4, 4, 1, 1, 1)
+    assert lib.fe_compress_masked(g.handle, evk.handle, ctypes.byref(lay), 1, 2.0 ** 20, P(src), 0, g.L, 2.0 ** 25,
+                                  P(out), ctypes.byref(sc), P(ws), ws.numel() * 8, s) == fe.FE_OK
     torch.cuda.synchronize()
     assert bool((out == 7).all()) and bool((slots == 3.0).all())
     assert g.device_status() == 0
