@@ -662,6 +662,14 @@ int fe_graph_io(const fe_graph* graph, uint32_t* n_in, size_t* in_bytes, uint32_
  * locked buffers make the copies asynchronous; pageable ones are staged by the
  * driver).  The caller owns the host buffers.  Errors: FE_EINVAL, FE_ECUDA. */
 int fe_graph_launch_host(fe_graph* graph, const void* const* in_host, void* const* out_host, void* stream);
+/* Level at which fe_graph_launch_host hands the final outputs to the host:
+ * the first level + 1 limbs of every polynomial, i.e. the same ciphertexts
+ * modulo q_0 .. q_level (an exact modulus drop, the usual step before a
+ * result leaves the server; the client decrypts them at that level and the
+ * same scale).  fe_graph_io's out_bytes follow it.  UINT32_MAX (the default)
+ * copies the outputs at their own level.  Errors: FE_EINVAL, FE_ELEVEL (above
+ * an output's level). */
+int fe_graph_set_host_output_level(fe_graph* graph, uint32_t level);
 void fe_graph_destroy(fe_graph* graph);
 
 /* ---- latency model (learned fragment / schedule proposer) ------------------- */

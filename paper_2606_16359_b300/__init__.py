@@ -186,6 +186,7 @@ SIGNATURES = {
     "fe_graph_launch": (cint, [vp, vp]),
     "fe_graph_io": (cint, [vp, P(u32), P(sz), P(u32), P(sz)]),
     "fe_graph_launch_host": (cint, [vp, P(vp), P(vp), vp]),
+    "fe_graph_set_host_output_level": (cint, [vp, u32]),
     "fe_graph_destroy": (None, [vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
     "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
@@ -293,6 +294,10 @@ class Graph:
         ib, ob = (sz * max(1, ni.value))(), (sz * max(1, no.value))()
         check(load().fe_graph_io(self.handle, ctypes.byref(ni), ib, ctypes.byref(no), ob))
         return list(ib)[:ni.value], list(ob)[:no.value]
+
+    def set_host_output_level(self, level=None):
+        """Final outputs reach the host at `level` (exact modulus drop); None: their own level."""
+        check(load().fe_graph_set_host_output_level(self.handle, 0xFFFFFFFF if level is None else int(level)))
 
     def launch_host(self, in_host, out_host):
         """One step through host memory (copies in, replay, copies out) on the current stream.

@@ -3,6 +3,8 @@
 // Compression (rotate-and-add replication), and CUDA-graph capture of a
 // sequence of planned layers.
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <cmath>
 #include <memory>
 
@@ -18,6 +20,9 @@ struct fe_graph {
         size_t bytes;
     };
     std::vector<Io> in, out;
+    std::vector<uint32_t> out_level;  // level of each final output ciphertext array
+    uint32_t host_out_level = UINT32_MAX;  // outputs copied to the host at this level (UINT32_MAX: their own)
+    size_t N = 0;
 };
 
 namespace fe {
@@ -494,9 +499,12 @@ extern "C" int fe_graph_capture_batch(fe_ctx* c, const fe_evk* evk, const fe_pla
     for (uint32_t j = 0; j < n; j++) {
         bool read_later = false;
         for (uint32_t i = j + 1; i < n; i++) read_later = read_later || ins[i] == outs[j];
-        if (!read_later)
+        if (!read_later) {
             g->out.push_back({outs[j], (size_t)n_req * plans[j]->n_out * 2 * plans[j]->level * c->limb_bytes()});
+            g->out_level.push_back((uint32_t)plans[j]->level - 1);
+        }
     }
+    g->N = (size_t)c->N;
     *out = g.release();
     return FE_OK;
 }
@@ -590,9 +598,12 @@ extern "C" int fe_graph_capture_chunked(fe_ctx* c, const fe_evk* evk, const fe_p
     for (uint32_t j = 0; j < n; j++) {
         bool read_later = false;
         for (uint32_t i = j + 1; i < n; i++) read_later = read_later || ins[i] == outs[j];
-        if (!read_later)
+        if (!read_later) {
             g->out.push_back({outs[j], (size_t)n_req * plans[j]->n_out * 2 * plans[j]->level * c->limb_bytes()});
+            g->out_level.push_back((uint32_t)plans[j]->level - 1);
+        }
     }
+    g->N = (size_t)c->N;
     *out = g.release();
     return FE_OK;
 }
@@ -609,13 +620,32 @@ extern "C" int fe_graph_launch(fe_graph* g, void* stream) {
     return FE_OK;
 }
 
+namespace {
+// host-side bytes of final output i: its ciphertexts at the host output level
+size_t host_out_bytes(const fe_graph* g, size_t i) {
+    const uint32_t lv = g->out_level[i];
+    if (g->host_out_level >= lv) return g->out[i].bytes;
+    const size_t per_ct_full = 2 * (size_t)(lv + 1) * g->N * 8;
+    return g->out[i].bytes / per_ct_full * 2 * (size_t)(g->host_out_level + 1) * g->N * 8;
+}
+}  // namespace
+
+extern "C" int fe_graph_set_host_output_level(fe_graph* g, uint32_t level) {
+    if (!g) return fail(FE_EINVAL, "null argument");
+    if (level != UINT32_MAX)
+        for (uint32_t lv : g->out_level)
+            if (level > lv) return fail(FE_ELEVEL, "host output level above an output's level");
+    g->host_out_level = level;
+    return FE_OK;
+}
+
 extern "C" int fe_graph_io(const fe_graph* g, uint32_t* n_in, size_t* in_bytes, uint32_t* n_out,
                            size_t* out_bytes) {
     if (!g || !n_in || !n_out) return fail(FE_EINVAL, "null argument");
     if (in_bytes)
         for (size_t i = 0; i < g->in.size(); i++) in_bytes[i] = g->in[i].bytes;
     if (out_bytes)
-        for (size_t i = 0; i < g->out.size(); i++) out_bytes[i] = g->out[i].bytes;
+        for (size_t i = 0; i < g->out.size(); i++) out_bytes[i] = host_out_bytes(g, i);
     *n_in = (uint32_t)g->in.size();
     *n_out = (uint32_t)g->out.size();
     return FE_OK;
@@ -631,8 +661,18 @@ extern "C" int fe_graph_launch_host(fe_graph* g, const void* const* in_host, voi
     for (size_t i = 0; i < g->in.size(); i++)
         FE_CUDA_TRY(cudaMemcpyAsync(g->in[i].dev, in_host[i], g->in[i].bytes, cudaMemcpyHostToDevice, st));
     FE_CUDA_TRY(cudaGraphLaunch(g->exec, st));
-    for (size_t i = 0; i < g->out.size(); i++)
-        FE_CUDA_TRY(cudaMemcpyAsync(out_host[i], g->out[i].dev, g->out[i].bytes, cudaMemcpyDeviceToHost, st));
+    for (size_t i = 0; i < g->out.size(); i++) {
+        const uint32_t lv = g->out_level[i];
+        if (g->host_out_level >= lv) {
+            FE_CUDA_TRY(cudaMemcpyAsync(out_host[i], g->out[i].dev, g->out[i].bytes, cudaMemcpyDeviceToHost, st));
+        } else {
+            // the first host_out_level + 1 limbs of every polynomial: the same ciphertexts
+            // modulo q_0 .. q_{host_out_level} (an exact modulus drop)
+            const size_t full = (size_t)(lv + 1) * g->N * 8, part = (size_t)(g->host_out_level + 1) * g->N * 8;
+            FE_CUDA_TRY(cudaMemcpy2DAsync(out_host[i], part, g->out[i].dev, full, part, g->out[i].bytes / full,
+                                          cudaMemcpyDeviceToHost, st));
+        }
+    }
     return FE_OK;
 }
 

@@ -188,6 +188,20 @@ class MobileNetBlocks:
         if join:
             self.join()
 
+    def host_outputs(self, level=None):
+        """Pinned host buffers for launch(h_in, h_out), with the captured graphs set
+        to hand their outputs over at `level` (an exact modulus drop; None: the
+        outputs' own level)."""
+        torch = _torch()
+        for g in self.graphs:
+            g.set_host_output_level(level)
+        bufs = []
+        for o in self.outputs:
+            n, two, nl, N = o.shape
+            bufs.append(torch.empty((n, two, nl if level is None else level + 1, N), dtype=o.dtype,
+                                    pin_memory=True))
+        return bufs
+
     def join(self):
         """Make the current stream wait for every per-block stream."""
         torch = _torch()

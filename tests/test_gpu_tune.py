@@ -114,3 +114,33 @@ def test_request_chunked_graph_equals_one_chunk():
     for w_, g_ in zip(want, got):
         assert np.array_equal(g_, w_)
     assert max(errs) < 1e-3, errs
+
+
+def test_graph_host_outputs_at_level_1_are_the_dropped_limbs_and_decrypt():
+    """fe_graph_set_host_output_level: the host receives the first two limbs of
+    every output polynomial (the same ciphertexts modulo q_0 q_1), which equal
+    the device residues' first limbs and decrypt to the FP64 blocks."""
+    p = W.PARAMS["mobilenet_small"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"], p["pbits"])
+        net = MobileNetBlocks(ctx, blocks=[(8, 16, 16), (4, 64, 64)], delta=p["delta"], schedule=4)
+        net.capture(concurrent=True)
+        h_in = [t.cpu().pin_memory() for t in net.inputs]
+        full = net.host_outputs(None)
+        net.launch(h_in, full)
+        torch.cuda.synchronize()
+        low = net.host_outputs(1)
+        ib, ob = net.graphs[0].io()
+        assert ob == [low[0].numel() * 8]
+        net.launch(h_in, low)
+        torch.cuda.synchronize()
+        errs = []
+        for b in range(2):
+            assert np.array_equal(low[b].numpy(), full[b].numpy()[:, :, :2, :])
+            slots = ctx.decrypt(net.sk, low[b].to("cuda"), 1, net.delta)
+            y = ctx.unpack(net.ref_inputs[b][3], slots).cpu().numpy()
+            errs.append(float(np.abs(y - net.reference_block(b)).max()))
+        with pytest.raises(fe.FencError):
+            net.graphs[0].set_host_output_level(ctx.L)  # above the outputs' level
+    assert max(errs) < 1e-3, errs
