@@ -144,6 +144,14 @@ int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
  * and makes the butterfly probe (fe_probe_butterflies) run the 32-bit-piece
  * form instead of the forward transform's.  Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_q36(fe_ctx* ctx, int enable);
+/* Data path of an NTT pass: staged = 0 (default) lets the first round of a
+ * pass read its elements straight from global memory and the last round write
+ * them straight back, with only the rounds in between going through shared
+ * memory; staged = 1 loads the whole tile into shared memory first and stores
+ * it from there after the last round (compiled for N = 2^14 and 2^16 at radix
+ * 8; other shapes always take the direct path).  Results do not depend on it.
+ * Errors: FE_EINVAL. */
+int fe_ctx_set_ntt_staged(fe_ctx* ctx, int staged);
 /* Generator behind every sampler of the context (secret key, encryption
  * randomness and errors, evaluation keys).  Each sample is drawn from word n of
  * a stream addressed by (seed, tag):

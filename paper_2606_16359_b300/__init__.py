@@ -123,6 +123,7 @@ SIGNATURES = {
     "fe_evk_upload": (cint, [vp, vp, sz, P(i32), u32, cint, vp, sz, vp, P(vp)]),
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_ctx_set_ntt_q36": (cint, [vp, cint]),
+    "fe_ctx_set_ntt_staged": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -439,6 +440,9 @@ class Context:
 
     def set_ntt_q36(self, enable):
         check(load().fe_ctx_set_ntt_q36(self.handle, int(enable)))
+
+    def set_ntt_staged(self, staged):
+        check(load().fe_ctx_set_ntt_staged(self.handle, int(staged)))
 
     # -- primitives ------------------------------------------------------------------
     def ntt(self, data, first_mod=0, inverse=False):

@@ -76,6 +76,7 @@ struct fe_ctx {
     int narrow;
     int ntt_radix = 8;  // elements per thread per NTT round (8 or 16; 16 compiled for N = 2^14, 2^16)
     int ntt_q36 = 1;    // use the 36-bit Shoup product in the transform when every modulus is below 2^36
+    int ntt_staged = 0; // 1: NTT tiles pass through shared memory before the first and after the last round
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;
     fe::Modulus* d_mod;             // [n_mod]

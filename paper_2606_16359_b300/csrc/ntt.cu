@@ -12,11 +12,16 @@
 // the twiddle at index (ltot + lid) * (n / 2t) + floor(x / 2t); for the column
 // pass ltot = 1, lid = 0, for the row pass ltot = N1, lid = row.
 //
-// A CTA stages a tile of lines in shared memory with coalesced loads.  The
-// stages are processed in rounds of up to three: each thread keeps 8 elements
-// of a line (stride s = the round's smallest distance) in registers, runs the
-// round's butterflies there, and writes them back; so a 256-point line needs
-// three shared-memory round trips instead of eight.  Butterflies are Harvey's
+// A CTA transforms a tile of lines.  The stages are processed in rounds of up
+// to three: each thread keeps 8 elements of a line (stride s = the round's
+// smallest distance) in registers and runs the round's butterflies there, so a
+// 256-point line takes three rounds instead of eight stages.  The first round
+// reads its elements straight from global memory and the last one writes them
+// straight back (a warp's accesses cover whole 32-byte sectors); only the
+// rounds in between go through the tile in shared memory.  The staged form
+// (fe_ctx_set_ntt_staged) instead loads the whole tile into shared memory with
+// coalesced 16-byte accesses first and stores it from there after the last
+// round.  Butterflies are Harvey's
 // lazy forms with Shoup multiplication: forward values stay in [0, 4q),
 // inverse values in [0, 2q), and only the final stage reduces to [0, q)
 // (4q < 2^64 since q < 2^62); with all moduli below 2^58 the forward
@@ -152,7 +157,9 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
 // kLogN > 0 fixes the ring degree at compile time so that the tile geometry, the
 // round structure and every shift fold into constants; kLogN = 0 reads it at run time.
 // CTAs of kTile / 2^kLE threads; the bound lets 9 radix-8 CTAs (36 warps) share an SM
-template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE, bool kQ36>
+// kStaged: the whole tile passes through shared memory before the first round and
+// after the last one; otherwise those two rounds access global memory directly.
+template <int kLogN, bool kInv, bool kCol, bool kNoRed, int kLE, bool kQ36, bool kStaged>
 __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6)) ntt_pass(NttArgs a, int first) {
     constexpr int kEE = 1 << kLE;
     extern __shared__ u64 tile[];
@@ -184,8 +191,10 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
     const int rs = N2 + (N2 >> 3);
 #define RIDX(ln, x) ((ln) * rs + (x) + ((x) >> 3))
 #define CIDX(x, c) (((x) + ((x) >> 3)) * lines + (c))
-    // load: each thread issues all of its 16-byte loads before storing to shared memory
-    {
+    // global offset of element x of line ln of the tile
+#define GOFF(ln, x) (kCol ? (size_t)(x) * N2 + l0 + (ln) : (size_t)(l0 + (ln)) * N2 + (x))
+    // staged load: each thread issues all of its 16-byte loads before storing to shared memory
+    if (kStaged) {
         const int pairs = total >> 1;
 #pragma unroll 1
         for (int e0 = 0; e0 < pairs; e0 += 4 * nthreads) {
@@ -222,45 +231,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
             }
         }
     }
-    __syncthreads();
-    const int tid = threadIdx.x;
-    const int line = kCol ? tid % lines : tid / tpl;
-    const int j = kCol ? tid / lines : tid % tpl;
-    const int tw_line = kCol ? 1 : (N1 + l0 + line);
-    // rounds: exponent chunks of kLE from the top, remainder at the bottom
-    const int nr = (logn + kLE - 1) / kLE;
-#pragma unroll
-    for (int rr = 0; rr < nr; rr++) {
-        const int k = kInv ? nr - 1 - rr : rr;  // chunk index from the top
-        const int hi = logn - 1 - kLE * k;      // largest exponent of the chunk
-        const int lo = max(0, hi - (kLE - 1));
-        const int nst = hi - lo + 1;
-        u64 v[kEE];
-        int base = 0;
-        if (tid < nthr) {
-            // thread j of the line: block (j >> lo), offset (j & (s - 1)), block size kEE s
-            int blk = j >> lo;
-            base = (blk << (lo + kLE)) + (j & ((1 << lo) - 1));
-            if (E < kEE) base = blk = 0;
-#pragma unroll
-            for (int r = 0; r < kEE; r++) {
-                const int x = base + (r << lo);
-                v[r] = (r < E) ? (kCol ? tile[CIDX(x, line)] : tile[RIDX(line, x)]) : 0;
-            }
-            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q);
-        }
-        __syncthreads();
-        if (tid < nthr) {
-#pragma unroll
-            for (int r = 0; r < kEE; r++) {
-                if (r >= E) break;
-                const int x = base + (r << lo);
-                if (kCol) tile[CIDX(x, line)] = v[r];
-                else tile[RIDX(line, x)] = v[r];
-            }
-        }
-        __syncthreads();
-    }
+    if (kStaged) __syncthreads();
     // the pass that completes the transform reduces to [0, q), fused into the store
     const bool last_pass = kInv ? kCol : !kCol;
     const u64 q2 = 2 * q;
@@ -273,7 +244,62 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
         else x = x >= q2 ? x - q2 : x;
         return x >= q ? x - q : x;
     };
-    {
+    const int tid = threadIdx.x;
+    const int line = kCol ? tid % lines : tid / tpl;
+    const int j = kCol ? tid / lines : tid % tpl;
+    const int tw_line = kCol ? 1 : (N1 + l0 + line);
+    // rounds: exponent chunks of kLE from the top, remainder at the bottom
+    const int nr = (logn + kLE - 1) / kLE;
+#pragma unroll
+    for (int rr = 0; rr < nr; rr++) {
+        const int k = kInv ? nr - 1 - rr : rr;  // chunk index from the top
+        const int hi = logn - 1 - kLE * k;      // largest exponent of the chunk
+        const int lo = max(0, hi - (kLE - 1));
+        const int nst = hi - lo + 1;
+        const bool from_global = !kStaged && rr == 0, to_global = !kStaged && rr == nr - 1;
+        // a row-pass round of unit stride holds consecutive elements: 16-byte global accesses
+        const bool vec = !kCol && lo == 0 && E == kEE;
+        if (tid < nthr) {
+            u64 v[kEE];
+            // thread j of the line: block (j >> lo), offset (j & (s - 1)), block size kEE s
+            int blk = j >> lo;
+            int base = (blk << (lo + kLE)) + (j & ((1 << lo) - 1));
+            if (E < kEE) base = blk = 0;
+            if (from_global && vec) {
+#pragma unroll
+                for (int r = 0; r < kEE; r += 2) {
+                    const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(s + GOFF(line, base + r));
+                    v[r] = p.x;
+                    v[r + 1] = p.y;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kEE; r++) {
+                    const int x = base + (r << lo);
+                    v[r] = (r < E) ? (from_global ? s[GOFF(line, x)] : (kCol ? tile[CIDX(x, line)] : tile[RIDX(line, x)]))
+                                   : 0;
+                }
+            }
+            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q);
+            // each thread writes back exactly the positions it read: no barrier in between
+            if (to_global && vec) {
+#pragma unroll
+                for (int r = 0; r < kEE; r += 2)
+                    *reinterpret_cast<ulonglong2*>(d + GOFF(line, base + r)) = make_ulonglong2(fin(v[r]), fin(v[r + 1]));
+            } else {
+#pragma unroll
+                for (int r = 0; r < kEE; r++) {
+                    if (r >= E) break;
+                    const int x = base + (r << lo);
+                    if (to_global) d[GOFF(line, x)] = fin(v[r]);
+                    else if (kCol) tile[CIDX(x, line)] = v[r];
+                    else tile[RIDX(line, x)] = v[r];
+                }
+            }
+        }
+        if (!to_global) __syncthreads();
+    }
+    if (kStaged) {
         const int pairs = total >> 1;
 #pragma unroll 4
         for (int e = threadIdx.x; e < pairs; e += nthreads) {
@@ -293,6 +319,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
             }
         }
     }
+#undef GOFF
 #undef RIDX
 #undef CIDX
 }
@@ -343,25 +370,28 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
 
 int threads_for(int lines, int n, int E) { return std::max(32, lines * (n / std::min(E, n))); }
 
-template <int kLogN, bool kInv, bool kCol, int kLE = 3>
+template <int kLogN, bool kInv, bool kCol, int kLE = 3, bool kStaged = false>
 void launch_one(bool nored, bool q36, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a, int first) {
     if (q36) {
         if (nored && !kInv)
-            ntt_pass<kLogN, kInv, kCol, true, kLE, true><<<g, t, sm, st>>>(a, first);
+            ntt_pass<kLogN, kInv, kCol, true, kLE, true, kStaged><<<g, t, sm, st>>>(a, first);
         else
-            ntt_pass<kLogN, kInv, kCol, false, kLE, true><<<g, t, sm, st>>>(a, first);
+            ntt_pass<kLogN, kInv, kCol, false, kLE, true, kStaged><<<g, t, sm, st>>>(a, first);
     } else if (nored && !kInv) {
-        ntt_pass<kLogN, kInv, kCol, true, kLE, false><<<g, t, sm, st>>>(a, first);
+        ntt_pass<kLogN, kInv, kCol, true, kLE, false, kStaged><<<g, t, sm, st>>>(a, first);
     } else {
-        ntt_pass<kLogN, kInv, kCol, false, kLE, false><<<g, t, sm, st>>>(a, first);
+        ntt_pass<kLogN, kInv, kCol, false, kLE, false, kStaged><<<g, t, sm, st>>>(a, first);
     }
 }
 
 // compile-time ring degrees for the production sizes, run-time geometry otherwise
-// radix 16 (le = 4) is compiled for the production ring degrees 2^14 and 2^16
+// radix 16 (le = 4) and radix 4 (le = 2), and the staged form, are compiled for the
+// production ring degrees 2^14 and 2^16
 template <bool kInv, bool kCol>
 void launch_pass(int logN, bool nored, bool q36, dim3 g, int t, size_t sm, cudaStream_t st, const NttArgs& a,
-                 int first, int le) {
+                 int first, int le, bool staged) {
+    if (staged && le == 3 && logN == 16) return launch_one<16, kInv, kCol, 3, true>(nored, q36, g, t, sm, st, a, first);
+    if (staged && le == 3 && logN == 14) return launch_one<14, kInv, kCol, 3, true>(nored, q36, g, t, sm, st, a, first);
     if (le == 4 && logN == 16) return launch_one<16, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
     if (le == 4 && logN == 14) return launch_one<14, kInv, kCol, 4>(nored, q36, g, t, sm, st, a, first);
     if (le == 2 && logN == 16) return launch_one<16, kInv, kCol, 2>(nored, q36, g, t, sm, st, a, first);
@@ -401,20 +431,20 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     if (!kInv) {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, true>(c->logN, nored, q36, gc, tc, smc, st, a, 1, le);
+            launch_pass<false, true>(c->logN, nored, q36, gc, tc, smc, st, a, 1, le, c->ntt_staged);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, false>(c->logN, nored, q36, gr, tr, smr, st, a, 0, le);
+            launch_pass<false, false>(c->logN, nored, q36, gr, tr, smr, st, a, 0, le, c->ntt_staged);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, false>(c->logN, false, q36, gr, tr, smr, st, a, 1, le);
+            launch_pass<true, false>(c->logN, false, q36, gr, tr, smr, st, a, 1, le, c->ntt_staged);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, true>(c->logN, false, q36, gc, tc, smc, st, a, 0, le);
+            launch_pass<true, true>(c->logN, false, q36, gc, tc, smc, st, a, 0, le, c->ntt_staged);
         }
     }
     c->cnt.ntt += limbs;
@@ -455,6 +485,13 @@ extern "C" int fe_ctx_set_ntt_q36(fe_ctx* c, int enable) {
     if (!c) return fe::fail(FE_EINVAL, "null argument");
     if (enable < 0 || enable > 2) return fe::fail(FE_EINVAL, "enable must be 0, 1 or 2");
     c->ntt_q36 = enable;
+    return FE_OK;
+}
+
+extern "C" int fe_ctx_set_ntt_staged(fe_ctx* c, int staged) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (staged != 0 && staged != 1) return fe::fail(FE_EINVAL, "staged must be 0 or 1");
+    c->ntt_staged = staged;
     return FE_OK;
 }
 

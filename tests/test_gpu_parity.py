@@ -628,3 +628,28 @@ def test_ntt_36bit_shoup_form_equals_general_form_and_oracle(logN, radix):
             assert np.array_equal(res[0][0][t], pr.ntt(a[t], t))
     g.set_ntt_q36(True)
     g.set_ntt_radix(8)
+
+
+@pytest.mark.parametrize("logN", [11, 14, 16])
+def test_ntt_direct_and_staged_paths_equal_the_oracle(logN):
+    """The NTT passes read their first round straight from global memory and
+    write their last round straight back (default), or stage the whole tile
+    in shared memory (fe_ctx_set_ntt_staged(1), compiled for N = 2^14 and
+    2^16); both give the oracle's residues forward and return the input
+    inverse, on random residues and on q - 1 everywhere."""
+    g = fe.Context(logN, 3, 2, 36, 36)
+    pr = ckks.Params(logN, 3, 2, 36, 36)
+    rng = np.random.default_rng(logN + 7)
+    rnd = np.stack([rng.integers(0, q, pr.N, dtype=np.uint64) for q in pr.moduli])
+    top = np.stack([np.full(pr.N, q - 1, dtype=np.uint64) for q in pr.moduli])
+    for a in (rnd, top):
+        want = np.stack([pr.ntt(a[t], t) for t in range(len(pr.moduli))])
+        for staged in (0, 1):
+            g.set_ntt_staged(staged)
+            d = to_dev(a[None])
+            g.ntt(d)
+            assert np.array_equal(u64(d)[0], want), staged
+            g.ntt(d, inverse=True)
+            assert np.array_equal(u64(d)[0], a), staged
+    g.set_ntt_staged(0)
+    assert g.device_status() == 0
