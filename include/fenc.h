@@ -144,14 +144,18 @@ int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
  * and makes the butterfly probe (fe_probe_butterflies) run the 32-bit-piece
  * form instead of the forward transform's.  Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_q36(fe_ctx* ctx, int enable);
-/* Data path of an NTT pass: staged = 0 (default) lets the first round of a
- * pass read its elements straight from global memory and the last round write
- * them straight back, with only the rounds in between going through shared
- * memory; staged = 1 loads the whole tile into shared memory first and stores
- * it from there after the last round (compiled for N = 2^14 and 2^16 at radix
- * 8; other shapes always take the direct path).  Results do not depend on it.
- * Errors: FE_EINVAL. */
-int fe_ctx_set_ntt_staged(fe_ctx* ctx, int staged);
+/* Data path of the NTT.  path = 0 (default): two passes (column stages, then
+ * row stages of N = N1 x N2), whose first round reads its elements straight
+ * from global memory and whose last round writes them straight back, with
+ * only the rounds in between going through shared memory.  path = 1: the same
+ * two passes with the whole tile loaded into shared memory first and stored
+ * from there (compiled for N = 2^14 and 2^16 at radix 8; other shapes take
+ * path 0).  path = 2: one pass per limb on a cluster of 8 CTAs that exchange
+ * the limb through distributed shared memory between the column and the row
+ * stages, so that each limb crosses DRAM once each way (N = 2^16 only, radix
+ * 8; other ring degrees, and a device on which such a cluster does not fit,
+ * take path 0).  Results do not depend on it.  Errors: FE_EINVAL. */
+int fe_ctx_set_ntt_path(fe_ctx* ctx, int path);
 /* Generator behind every sampler of the context (secret key, encryption
  * randomness and errors, evaluation keys).  Each sample is drawn from word n of
  * a stream addressed by (seed, tag):

@@ -123,7 +123,7 @@ SIGNATURES = {
     "fe_evk_upload": (cint, [vp, vp, sz, P(i32), u32, cint, vp, sz, vp, P(vp)]),
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_ctx_set_ntt_q36": (cint, [vp, cint]),
-    "fe_ctx_set_ntt_staged": (cint, [vp, cint]),
+    "fe_ctx_set_ntt_path": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -441,8 +441,10 @@ class Context:
     def set_ntt_q36(self, enable):
         check(load().fe_ctx_set_ntt_q36(self.handle, int(enable)))
 
-    def set_ntt_staged(self, staged):
-        check(load().fe_ctx_set_ntt_staged(self.handle, int(staged)))
+    def set_ntt_path(self, path):
+        """0: two passes (first and last rounds on global memory); 1: two passes
+        staged through shared memory; 2: one pass on clusters of 8 CTAs (N = 2^16)."""
+        check(load().fe_ctx_set_ntt_path(self.handle, int(path)))
 
     # -- primitives ------------------------------------------------------------------
     def ntt(self, data, first_mod=0, inverse=False):

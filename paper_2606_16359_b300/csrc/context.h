@@ -76,7 +76,10 @@ struct fe_ctx {
     int narrow;
     int ntt_radix = 8;  // elements per thread per NTT round (8 or 16; 16 compiled for N = 2^14, 2^16)
     int ntt_q36 = 1;    // use the 36-bit Shoup product in the transform when every modulus is below 2^36
-    int ntt_staged = 0; // 1: NTT tiles pass through shared memory before the first and after the last round
+    // NTT data path: 0 two passes, first and last rounds on global memory; 1 two passes
+    // staged through shared memory; 2 one pass on clusters of 8 CTAs (N = 2^16)
+    int ntt_path = 0;
+    int ntt_cluster_ok = -1;  // whether the cluster form fits on the device (-1: not yet asked)
     std::vector<u64> mod;  // q_0..q_L, p_0..p_{k-1}
     std::vector<u64> psi;
     fe::Modulus* d_mod;             // [n_mod]
@@ -129,6 +132,8 @@ void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st);
 // throughput probe of the transform's butterfly arithmetic (blocks x 256 threads)
 // (*blocks = 0: one full wave, set on return)
 int butterfly_probe(fe_ctx* c, uint32_t* blocks, uint32_t iters, u64* out, cudaStream_t st);
+// Decides, outside any stream capture, whether the cluster form of the NTT fits on the device.
+void ntt_prepare(fe_ctx* c);
 // out-of-place: the first pass reads polynomials from src (poly stride src_stride words)
 void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);
 void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st);

@@ -19,7 +19,7 @@
 // reads its elements straight from global memory and the last one writes them
 // straight back (a warp's accesses cover whole 32-byte sectors); only the
 // rounds in between go through the tile in shared memory.  The staged form
-// (fe_ctx_set_ntt_staged) instead loads the whole tile into shared memory with
+// (fe_ctx_set_ntt_path 1) instead loads the whole tile into shared memory with
 // coalesced 16-byte accesses first and stores it from there after the last
 // round.  Butterflies are Harvey's
 // lazy forms with Shoup multiplication: forward values stay in [0, 4q),
@@ -28,6 +28,8 @@
 // transform skips reductions until its last stage (see round_stages).  The first pass may read a separate source
 // buffer (out-of-place); the second pass works in place.
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "context.h"
 
@@ -350,6 +352,169 @@ __global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __res
     out[(size_t)blockIdx.x * 256 + threadIdx.x] = acc;
 }
 
+// Single-pass transform of N = 2^16 = 256 x 256 on a cluster of 8 CTAs, one limb
+// per cluster, so that a limb crosses DRAM once each way instead of twice.
+// CTA c first owns the column block c (columns 32c .. 32c+31 of all 256 rows),
+// runs the column stages on it, then exchanges data with the other seven CTAs
+// through distributed shared memory so that it owns the row block c (rows 32c ..
+// 32c+31, all columns), and runs the row stages there (the inverse runs the row
+// stages first).  The CTA's shared memory is 8 slots of 32 x 32 elements, row
+// stride 33, slot stride 1060 words:
+//   column-block view: slot s, entry (a, b) = element (row 32 s + a, column 32 c + b)
+//   row-block view:    slot s, entry (a, b) = element (row 32 c + a, column 32 s + b)
+// so the exchange swaps CTA c's slot k with CTA k's slot c entry by entry (the
+// diagonal slot stays), with no permutation inside a slot: each entry is moved
+// by exactly one thread of the cluster, CTA min(c, k) taking the first half of
+// the pair's entries and CTA max(c, k) the second.  The row stride (1 mod 16
+// words) and the slot stride (4 mod 16) keep every round's 32 lanes at two
+// accesses per bank pair, the minimum for 8-byte words: column rounds put the
+// lanes on the 32 columns; row rounds of distance >= 4 put them on one row's 32
+// groups, and the unit-distance round on 8 rows x 4 groups.  Rounds, butterflies,
+// twiddles and the final reduction are those of ntt_pass; the first round reads
+// global memory and the last one writes it, as in its direct form.
+constexpr int kClB = 32, kClR = 33, kClSW = 1060, kClThreads = 256;
+constexpr size_t kClSmem = (size_t)8 * kClSW * sizeof(u64);
+
+template <bool kInv, bool kNoRed, bool kQ36>
+__global__ void __launch_bounds__(kClThreads, 3) ntt_cluster16(NttArgs a) {
+    namespace cg = cooperative_groups;
+    constexpr int logn = 8, n = 256, N1 = 256;
+    constexpr int kGroups = (n / 8) * kClB;  // groups of 8 elements per round and CTA
+    extern __shared__ __align__(16) u64 sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    uint32_t cid, c;
+    asm("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(c));
+    const int limb = (int)cid;
+    const int poly = limb / a.per_poly, jl = limb % a.per_poly;
+    const int mi = a.mod_map[jl];
+    const int pos = a.pos_map ? a.pos_map[jl] : jl;
+    const u64 q = a.mods[mi].q;
+    const ulonglong2* tw = a.tw + ((size_t)mi << 16);
+    u64* d = a.dst + (size_t)poly * a.poly_stride + ((size_t)pos << 16);
+    const u64* s = a.src + (size_t)poly * a.src_stride + ((size_t)pos << 16);
+    const int tid = threadIdx.x, cB = (int)c * kClB;
+    const u64 q2 = 2 * q;
+    const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
+    const u64 qinv64 = a.mods[mi].ratio_hi;
+    auto fin = [&](u64 x) -> u64 {
+        if (kInv) x = kQ36 ? shoup36(x, ni, nis, 0 - q) : shoup_lazy(x, ni, nis, q);  // [0, 2q)
+        else if (kNoRed) x -= __umul64hi(x, qinv64) * q;                              // [0, 2q)
+        else x = x >= q2 ? x - q2 : x;
+        return x >= q ? x - q : x;
+    };
+    // column stages on the column block: line = column j (lanes), element x = row
+    auto col_round = [&](int rr, bool from_global, bool to_global) {
+        const int k = kInv ? 2 - rr : rr;
+        const int hi = logn - 1 - 3 * k, lo = max(0, hi - 2), nst = hi - lo + 1;
+#pragma unroll 1
+        for (int gi = tid; gi < kGroups; gi += kClThreads) {
+            const int j = gi & 31, jj = gi >> 5;
+            const int blk = jj >> lo, base = (blk << (lo + 3)) + (jj & ((1 << lo) - 1));
+            u64 v[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const int x = base + (r << lo);
+                v[r] = from_global ? s[(size_t)x * n + cB + j] : sm[kClSW * (x >> 5) + (x & 31) * kClR + j];
+            }
+            round_stages<kInv, kNoRed, 3, kQ36>(v, blk, lo, nst, 8, logn, 1, tw, q);
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const int x = base + (r << lo);
+                if (to_global) d[(size_t)x * n + cB + j] = fin(v[r]);
+                else sm[kClSW * (x >> 5) + (x & 31) * kClR + j] = v[r];
+            }
+        }
+    };
+    // row stages on the row block: line = local row xl, element x = column
+    auto row_round = [&](int rr, bool from_global, bool to_global) {
+        const int k = kInv ? 2 - rr : rr;
+        const int hi = logn - 1 - 3 * k, lo = max(0, hi - 2), nst = hi - lo + 1;
+#pragma unroll 1
+        for (int gi = tid; gi < kGroups; gi += kClThreads) {
+            const int lane = gi & 31, w = gi >> 5;
+            // unit distance: lanes on 8 rows x 4 groups; otherwise on one row's 32 groups
+            const int xl = lo == 0 ? (lane >> 2) + 8 * (w >> 3) : w;
+            const int jj = lo == 0 ? 4 * (w & 7) + (lane & 3) : lane;
+            const int blk = jj >> lo, base = (blk << (lo + 3)) + (jj & ((1 << lo) - 1));
+            const size_t grow = (size_t)(cB + xl) * n;
+            u64 v[8];
+            if (from_global && lo == 0) {
+#pragma unroll
+                for (int r = 0; r < 8; r += 2) {
+                    const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(s + grow + base + r);
+                    v[r] = p.x;
+                    v[r + 1] = p.y;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    const int x = base + (r << lo);
+                    v[r] = from_global ? s[grow + x] : sm[kClSW * (x >> 5) + xl * kClR + (x & 31)];
+                }
+            }
+            round_stages<kInv, kNoRed, 3, kQ36>(v, blk, lo, nst, 8, logn, N1 + cB + xl, tw, q);
+            if (to_global && lo == 0) {
+#pragma unroll
+                for (int r = 0; r < 8; r += 2)
+                    *reinterpret_cast<ulonglong2*>(d + grow + base + r) = make_ulonglong2(fin(v[r]), fin(v[r + 1]));
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    const int x = base + (r << lo);
+                    if (to_global) d[grow + x] = fin(v[r]);
+                    else sm[kClSW * (x >> 5) + xl * kClR + (x & 31)] = v[r];
+                }
+            }
+        }
+    };
+    // exchange: CTA c's slot k <-> CTA k's slot c, 16 bytes per access; of each
+    // pair's 32 x 33 entries the lower rank moves the first half, the higher the second
+    auto exchange = [&]() {
+        constexpr int kHalf = kClB * kClR / 2;  // 528 entries
+        constexpr int kVec = kHalf / 2;         // 264 16-byte pairs per half
+#pragma unroll 2
+        for (int idx = tid; idx < 7 * kVec; idx += kClThreads) {
+            const int kk = ((int)c + 1 + idx / kVec) & 7;
+            const int p = 2 * (idx % kVec) + ((int)c < kk ? 0 : kHalf);
+            ulonglong2* mine = reinterpret_cast<ulonglong2*>(sm + kClSW * kk + p);
+            ulonglong2* theirs = reinterpret_cast<ulonglong2*>(cluster.map_shared_rank(sm + kClSW * c + p, kk));
+            const ulonglong2 x = *mine, y = *theirs;
+            *mine = y;
+            *theirs = x;
+        }
+    };
+    if (!kInv) {
+        col_round(0, true, false);
+        __syncthreads();
+        col_round(1, false, false);
+        __syncthreads();
+        col_round(2, false, false);
+        cluster.sync();  // every column block complete and visible to the cluster
+        exchange();
+        cluster.sync();  // every row block assembled; no remote access after this
+        row_round(0, false, false);
+        __syncthreads();
+        row_round(1, false, false);
+        __syncthreads();
+        row_round(2, false, true);
+    } else {
+        row_round(0, true, false);
+        __syncthreads();
+        row_round(1, false, false);
+        __syncthreads();
+        row_round(2, false, false);
+        cluster.sync();
+        exchange();
+        cluster.sync();
+        col_round(0, false, false);
+        __syncthreads();
+        col_round(1, false, false);
+        __syncthreads();
+        col_round(2, false, true);
+    }
+}
+
 NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, bool inverse) {
     NttArgs a;
     a.src = src ? src : s.base;
@@ -409,11 +574,79 @@ void launch_pass(int logN, bool nored, bool q36, dim3 g, int t, size_t sm, cudaS
     }
 }
 
+template <bool kInv, bool kNoRed, bool kQ36>
+cudaError_t launch_cluster(int limbs, cudaStream_t st, const NttArgs& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(8 * limbs);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 8;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ntt_cluster16<kInv, kNoRed, kQ36>, a);
+}
+
+// Whether the cluster form can run here: its shared-memory size is accepted and at
+// least one cluster of 8 CTAs fits on the device.  Decided once per context.
+template <bool kInv, bool kNoRed, bool kQ36>
+bool cluster_fits() {
+    auto kern = ntt_cluster16<kInv, kNoRed, kQ36>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(8);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 8;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+bool cluster_usable(fe_ctx* c) {
+    if (c->ntt_cluster_ok < 0) {
+        // every instance the context can launch must fit (their shared memory is identical)
+        const bool ok = cluster_fits<false, true, false>() && cluster_fits<false, false, false>() &&
+                        cluster_fits<true, false, false>() && cluster_fits<true, false, true>() &&
+                        cluster_fits<false, true, true>() && cluster_fits<false, false, true>();
+        c->ntt_cluster_ok = ok ? 1 : 0;
+    }
+    return c->ntt_cluster_ok == 1;
+}
+
 template <bool kInv>
 void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cudaStream_t st) {
     int limbs = s.per_poly * s.n_poly;
     if (limbs == 0) return;
     NttArgs a = make_args(c, s, src, src_stride, kInv);
+    if (c->ntt_path == 2 && c->logN == 16 && cluster_usable(c)) {
+        // single pass on clusters of 8 CTAs, one limb per cluster
+        const bool nored = !kInv && c->max_mod_bits <= 58;
+        const bool q36 = kInv && c->max_mod_bits <= 36 && c->ntt_q36;
+        ProfScope ps(c, PK_NTT, st, 16.0 * limbs * c->N);
+        if (q36) launch_cluster<kInv, false, true>(limbs, st, a);
+        else if (nored) launch_cluster<false, true, false>(limbs, st, a);
+        else launch_cluster<kInv, false, false>(limbs, st, a);
+        c->cnt.ntt += limbs;
+        c->cnt.launches += 1;
+        return;
+    }
     const int N = c->N, N2 = 1 << a.logN2, N1 = N / N2;
     const int C = std::min(kTile / N1, N2), R = std::min(kTile / N2, N1);
     const size_t smc = (size_t)(N1 + (N1 >> 3) + 1) * C * 8, smr = (size_t)R * (N2 + (N2 >> 3)) * 8;
@@ -431,20 +664,20 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     if (!kInv) {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, true>(c->logN, nored, q36, gc, tc, smc, st, a, 1, le, c->ntt_staged);
+            launch_pass<false, true>(c->logN, nored, q36, gc, tc, smc, st, a, 1, le, c->ntt_path == 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<false, false>(c->logN, nored, q36, gr, tr, smr, st, a, 0, le, c->ntt_staged);
+            launch_pass<false, false>(c->logN, nored, q36, gr, tr, smr, st, a, 0, le, c->ntt_path == 1);
         }
     } else {
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, false>(c->logN, false, q36, gr, tr, smr, st, a, 1, le, c->ntt_staged);
+            launch_pass<true, false>(c->logN, false, q36, gr, tr, smr, st, a, 1, le, c->ntt_path == 1);
         }
         {
             ProfScope ps(c, PK_NTT, st, bytes);
-            launch_pass<true, true>(c->logN, false, q36, gc, tc, smc, st, a, 0, le, c->ntt_staged);
+            launch_pass<true, true>(c->logN, false, q36, gc, tc, smc, st, a, 0, le, c->ntt_path == 1);
         }
     }
     c->cnt.ntt += limbs;
@@ -470,6 +703,10 @@ int butterfly_probe(fe_ctx* c, uint32_t* blocks, uint32_t iters, u64* out, cudaS
     return cudaGetLastError() == cudaSuccess ? FE_OK : fail(FE_ECUDA, "butterfly probe launch");
 }
 
+void ntt_prepare(fe_ctx* c) {
+    if (c->logN == 16) cluster_usable(c);
+}
+
 void ntt_forward(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<false>(c, s, nullptr, 0, st); }
 void ntt_inverse(fe_ctx* c, const LimbSet& s, cudaStream_t st) { run_ntt<true>(c, s, nullptr, 0, st); }
 void ntt_forward_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSet& dst, cudaStream_t st) {
@@ -488,10 +725,10 @@ extern "C" int fe_ctx_set_ntt_q36(fe_ctx* c, int enable) {
     return FE_OK;
 }
 
-extern "C" int fe_ctx_set_ntt_staged(fe_ctx* c, int staged) {
+extern "C" int fe_ctx_set_ntt_path(fe_ctx* c, int path) {
     if (!c) return fe::fail(FE_EINVAL, "null argument");
-    if (staged != 0 && staged != 1) return fe::fail(FE_EINVAL, "staged must be 0 or 1");
-    c->ntt_staged = staged;
+    if (path < 0 || path > 2) return fe::fail(FE_EINVAL, "NTT path must be 0, 1 or 2");
+    c->ntt_path = path;
     return FE_OK;
 }
 

@@ -421,6 +421,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     FE_CUDA_TRY(cudaMalloc(&c->d_dd_w, ddw.size() * sizeof(double)));
     c->allocs.push_back(c->d_dd_w);
     FE_CUDA_TRY(cudaMemcpy(c->d_dd_w, ddw.data(), ddw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    fe::ntt_prepare(c.get());
     *out = c.release();
     return FE_OK;
 }

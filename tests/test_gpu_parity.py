@@ -631,12 +631,14 @@ def test_ntt_36bit_shoup_form_equals_general_form_and_oracle(logN, radix):
 
 
 @pytest.mark.parametrize("logN", [11, 14, 16])
-def test_ntt_direct_and_staged_paths_equal_the_oracle(logN):
-    """The NTT passes read their first round straight from global memory and
-    write their last round straight back (default), or stage the whole tile
-    in shared memory (fe_ctx_set_ntt_staged(1), compiled for N = 2^14 and
-    2^16); both give the oracle's residues forward and return the input
-    inverse, on random residues and on q - 1 everywhere."""
+def test_ntt_data_paths_equal_the_oracle(logN):
+    """Every NTT data path (fe_ctx_set_ntt_path): two passes whose first and
+    last rounds touch global memory directly (0, default), two passes staged
+    through shared memory (1), one pass on 8-CTA clusters exchanging the limb
+    through distributed shared memory (2, N = 2^16); each gives the oracle's
+    residues forward and returns the input inverse, on random residues and on
+    q - 1 everywhere, in place and out of place (the key switch's ModUp
+    transforms a converted copy)."""
     g = fe.Context(logN, 3, 2, 36, 36)
     pr = ckks.Params(logN, 3, 2, 36, 36)
     rng = np.random.default_rng(logN + 7)
@@ -644,12 +646,24 @@ def test_ntt_direct_and_staged_paths_equal_the_oracle(logN):
     top = np.stack([np.full(pr.N, q - 1, dtype=np.uint64) for q in pr.moduli])
     for a in (rnd, top):
         want = np.stack([pr.ntt(a[t], t) for t in range(len(pr.moduli))])
-        for staged in (0, 1):
-            g.set_ntt_staged(staged)
+        for path in (0, 1, 2):
+            g.set_ntt_path(path)
             d = to_dev(a[None])
             g.ntt(d)
-            assert np.array_equal(u64(d)[0], want), staged
+            assert np.array_equal(u64(d)[0], want), path
             g.ntt(d, inverse=True)
-            assert np.array_equal(u64(d)[0], a), staged
-    g.set_ntt_staged(0)
+            assert np.array_equal(u64(d)[0], a), path
+    if logN == 16:
+        # a key switch transforms converted copies out of place
+        keys = ckks.KeySet(pr, 5, rot_steps=[3])
+        sk = g.sk_gen(5)
+        evk = g.evk_gen(sk, 5, [3])
+        z = rng.uniform(-1, 1, pr.N // 2)
+        oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, pr.L, 2.0 ** 25), 2, 0)
+        ct = g.encrypt(sk, torch.from_numpy(z[None]), pr.L, 2.0 ** 25, seed=2)
+        want = oracle_ct_array([ckks.rotate(pr, keys, oct_, 3)])
+        for path in (0, 1, 2):
+            g.set_ntt_path(path)
+            assert np.array_equal(u64(g.rotate(evk, ct, pr.L, 3)), want), path
+    g.set_ntt_path(0)
     assert g.device_status() == 0
