@@ -144,6 +144,14 @@ int fe_ctx_set_ntt_radix(fe_ctx* ctx, int radix);
  * and makes the butterfly probe (fe_probe_butterflies) run the 32-bit-piece
  * form instead of the forward transform's.  Errors: FE_EINVAL. */
 int fe_ctx_set_ntt_q36(fe_ctx* ctx, int enable);
+/* Form of the forward NTT's butterflies (two-pass paths).  flags bit 0: reduce
+ * every stage's sums to [0, 4q) with a compare (Harvey's lazy form) instead of
+ * letting them grow to below 35 q and reducing once at the end with a 64-bit
+ * Barrett step (the default whenever every modulus is below 2^58); bit 1: take
+ * the 36-bit Shoup product of fe_ctx_set_ntt_q36 in the forward transform too
+ * (moduli below 2^36 only).  Default 0.  Results do not depend on it.
+ * Errors: FE_EINVAL. */
+int fe_ctx_set_ntt_forward(fe_ctx* ctx, int flags);
 /* Data path of the NTT.  path = 0 (default): two passes (column stages, then
  * row stages of N = N1 x N2), whose first round reads its elements straight
  * from global memory and whose last round writes them straight back, with

@@ -124,6 +124,7 @@ SIGNATURES = {
     "fe_ctx_set_ntt_radix": (cint, [vp, cint]),
     "fe_ctx_set_ntt_q36": (cint, [vp, cint]),
     "fe_ctx_set_ntt_path": (cint, [vp, cint]),
+    "fe_ctx_set_ntt_forward": (cint, [vp, cint]),
     "fe_get_counters": (cint, [vp, P(FeCounters)]),
     "fe_counters_reset": (cint, [vp]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -440,6 +441,10 @@ class Context:
 
     def set_ntt_q36(self, enable):
         check(load().fe_ctx_set_ntt_q36(self.handle, int(enable)))
+
+    def set_ntt_forward(self, flags):
+        """bit 0: reduce every forward stage to [0, 4q); bit 1: 36-bit Shoup product forward."""
+        check(load().fe_ctx_set_ntt_forward(self.handle, int(flags)))
 
     def set_ntt_path(self, path):
         """0: two passes (first and last rounds on global memory); 1: two passes

@@ -76,6 +76,7 @@ struct fe_ctx {
     int narrow;
     int ntt_radix = 8;  // elements per thread per NTT round (8 or 16; 16 compiled for N = 2^14, 2^16)
     int ntt_q36 = 1;    // use the 36-bit Shoup product in the transform when every modulus is below 2^36
+    int ntt_fwd = 0;    // forward NTT form: bit 0 reduce to [0, 4q) every stage, bit 1 36-bit Shoup product
     // NTT data path: 0 two passes, first and last rounds on global memory; 1 two passes
     // staged through shared memory; 2 one pass on clusters of 8 CTAs (N = 2^16)
     int ntt_path = 0;

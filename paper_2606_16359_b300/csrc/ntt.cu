@@ -372,11 +372,17 @@ __global__ void __launch_bounds__(256) k_butterfly_probe(const ulonglong2* __res
 // groups, and the unit-distance round on 8 rows x 4 groups.  Rounds, butterflies,
 // twiddles and the final reduction are those of ntt_pass; the first round reads
 // global memory and the last one writes it, as in its direct form.
-constexpr int kClB = 32, kClR = 33, kClSW = 1060, kClThreads = 256;
+constexpr int kClB = 32, kClR = 33, kClSW = 1060;
 constexpr size_t kClSmem = (size_t)8 * kClSW * sizeof(u64);
 
-template <bool kInv, bool kNoRed, bool kQ36>
-__global__ void __launch_bounds__(kClThreads, 3) ntt_cluster16(NttArgs a) {
+// kT threads per CTA, kMinB CTAs per SM (three fit by shared memory).  Measured on
+// B300 (N = 2^16, 532 limbs, forward / inverse us per limb): 256 threads x 3 CTAs
+// (80 registers) 0.90 / 1.06; 384 x 3 (56 registers, spills) 0.96 / 1.06;
+// 512 x 2 (64 registers, spills) 1.03 / 1.10; the two-pass form 0.76 / 0.84.
+constexpr int kClT = 256;
+template <bool kInv, bool kNoRed, bool kQ36, int kT, int kMinB>
+__global__ void __launch_bounds__(kT, kMinB) ntt_cluster16(NttArgs a) {
+    constexpr int kClThreads = kT;
     namespace cg = cooperative_groups;
     constexpr int logn = 8, n = 256, N1 = 256;
     constexpr int kGroups = (n / 8) * kClB;  // groups of 8 elements per round and CTA
@@ -574,11 +580,11 @@ void launch_pass(int logN, bool nored, bool q36, dim3 g, int t, size_t sm, cudaS
     }
 }
 
-template <bool kInv, bool kNoRed, bool kQ36>
+template <bool kInv, bool kNoRed, bool kQ36, int kT, int kMinB>
 cudaError_t launch_cluster(int limbs, cudaStream_t st, const NttArgs& a) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(8 * limbs);
-    cfg.blockDim = dim3(kClThreads);
+    cfg.blockDim = dim3(kT);
     cfg.dynamicSmemBytes = kClSmem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -588,21 +594,21 @@ cudaError_t launch_cluster(int limbs, cudaStream_t st, const NttArgs& a) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ntt_cluster16<kInv, kNoRed, kQ36>, a);
+    return cudaLaunchKernelEx(&cfg, ntt_cluster16<kInv, kNoRed, kQ36, kT, kMinB>, a);
 }
 
 // Whether the cluster form can run here: its shared-memory size is accepted and at
 // least one cluster of 8 CTAs fits on the device.  Decided once per context.
-template <bool kInv, bool kNoRed, bool kQ36>
+template <bool kInv, bool kNoRed, bool kQ36, int kT, int kMinB>
 bool cluster_fits() {
-    auto kern = ntt_cluster16<kInv, kNoRed, kQ36>;
+    auto kern = ntt_cluster16<kInv, kNoRed, kQ36, kT, kMinB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(8);
-    cfg.blockDim = dim3(kClThreads);
+    cfg.blockDim = dim3(kT);
     cfg.dynamicSmemBytes = kClSmem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -619,12 +625,16 @@ bool cluster_fits() {
     return n > 0;
 }
 
+template <int kT, int kMinB>
+bool fits_all() {
+    return cluster_fits<false, true, false, kT, kMinB>() && cluster_fits<false, false, false, kT, kMinB>() &&
+           cluster_fits<true, false, false, kT, kMinB>() && cluster_fits<true, false, true, kT, kMinB>();
+}
+
 bool cluster_usable(fe_ctx* c) {
     if (c->ntt_cluster_ok < 0) {
         // every instance the context can launch must fit (their shared memory is identical)
-        const bool ok = cluster_fits<false, true, false>() && cluster_fits<false, false, false>() &&
-                        cluster_fits<true, false, false>() && cluster_fits<true, false, true>() &&
-                        cluster_fits<false, true, true>() && cluster_fits<false, false, true>();
+        const bool ok = fits_all<kClT, 3>();
         c->ntt_cluster_ok = ok ? 1 : 0;
     }
     return c->ntt_cluster_ok == 1;
@@ -640,9 +650,9 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
         const bool nored = !kInv && c->max_mod_bits <= 58;
         const bool q36 = kInv && c->max_mod_bits <= 36 && c->ntt_q36;
         ProfScope ps(c, PK_NTT, st, 16.0 * limbs * c->N);
-        if (q36) launch_cluster<kInv, false, true>(limbs, st, a);
-        else if (nored) launch_cluster<false, true, false>(limbs, st, a);
-        else launch_cluster<kInv, false, false>(limbs, st, a);
+        if (q36) launch_cluster<kInv, false, true, kClT, 3>(limbs, st, a);
+        else if (nored) launch_cluster<false, true, false, kClT, 3>(limbs, st, a);
+        else launch_cluster<kInv, false, false, kClT, 3>(limbs, st, a);
         c->cnt.ntt += limbs;
         c->cnt.launches += 1;
         return;
@@ -655,11 +665,14 @@ void run_ntt(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride, cud
     const bool big = c->logN == 14 || c->logN == 16;
     const int le = big && c->ntt_radix == 16 ? 4 : (big && c->ntt_radix == 4 ? 2 : 3);
     const int tc = threads_for(C, N1, 1 << le), tr = threads_for(R, N2, 1 << le);
-    const bool nored = c->max_mod_bits <= 58;
+    // forward: no reduction inside the transform when every modulus is below 2^58, unless
+    // fe_ctx_set_ntt_forward asks for Harvey's reduction to [0, 4q) at every stage (an ALU
+    // compare per butterfly in place of a 64-bit Barrett step per element at the end)
+    const bool nored = c->max_mod_bits <= 58 && !(c->ntt_fwd & 1);
     // every modulus below 2^36: the 36-bit Shoup product in the inverse passes (inputs below
     // 4 q, within its 2^42 bound).  Measured on B300 (N = 2^16, 532 limbs): inverse 0.932 ->
     // 0.908 us per limb; the forward passes were 1.6 % slower with it and keep the general form.
-    const bool q36 = kInv && c->max_mod_bits <= 36 && c->ntt_q36;
+    const bool q36 = c->max_mod_bits <= 36 && (kInv ? c->ntt_q36 != 0 : (c->ntt_fwd & 2) != 0);
     const dim3 gc(limbs * (N2 / C)), gr(limbs * (N1 / R));
     if (!kInv) {
         {
@@ -717,6 +730,13 @@ void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSe
 }
 
 }  // namespace fe
+
+extern "C" int fe_ctx_set_ntt_forward(fe_ctx* c, int flags) {
+    if (!c) return fe::fail(FE_EINVAL, "null argument");
+    if (flags < 0 || flags > 3) return fe::fail(FE_EINVAL, "forward NTT flags must be in [0, 3]");
+    c->ntt_fwd = flags;
+    return FE_OK;
+}
 
 extern "C" int fe_ctx_set_ntt_q36(fe_ctx* c, int enable) {
     if (!c) return fe::fail(FE_EINVAL, "null argument");

@@ -46,6 +46,7 @@ def bench_ntt(ctx, torch, args):
     ctx.set_ntt_radix(args.radix)
     ctx.set_ntt_q36(args.q36)
     ctx.set_ntt_path(args.path)
+    ctx.set_ntt_forward(args.fwd)
     N, nm = ctx.N, ctx.n_mod
     n_poly = max(1, (args.limbs + nm - 1) // nm)
     limbs = n_poly * nm
@@ -71,7 +72,7 @@ def bench_ntt(ctx, torch, args):
     peak, src = hbm_peak()
     for v in out.values():
         v["hbm_frac"] = v["GBps"] / peak
-    return {"kernel": "ntt", "radix": args.radix, "q36": args.q36, "path": args.path, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
+    return {"kernel": "ntt", "radix": args.radix, "q36": args.q36, "path": args.path, "fwd": args.fwd, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
             "peak_GBps": peak, "peak_source": src, **out}
 
 
@@ -333,6 +334,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--level", type=int, default=22)
     ap.add_argument("--radix", type=int, default=8, help="NTT elements per thread per round (8 or 16)")
+    ap.add_argument("--fwd", type=int, default=0, help="forward NTT form flags: 1 reduce every stage, 2 36-bit Shoup product")
     ap.add_argument("--path", type=int, default=0, help="NTT data path: 0 two passes direct (default), 1 two passes staged, 2 one pass on 8-CTA clusters (N = 2^16)")
     ap.add_argument("--q36", type=int, default=1, help="36-bit Shoup product in the inverse NTT (1, default), nowhere (0), or also in the probe (2)")
     ap.add_argument("--channels", type=int, default=128, help="channels of the layer case")

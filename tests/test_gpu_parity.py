@@ -635,7 +635,8 @@ def test_ntt_data_paths_equal_the_oracle(logN):
     """Every NTT data path (fe_ctx_set_ntt_path): two passes whose first and
     last rounds touch global memory directly (0, default), two passes staged
     through shared memory (1), one pass on 8-CTA clusters exchanging the limb
-    through distributed shared memory (2, N = 2^16); each gives the oracle's
+    through distributed shared memory (2, N = 2^16), and the forward forms of
+    fe_ctx_set_ntt_forward (per-stage reduction, 36-bit product); each gives the
     residues forward and returns the input inverse, on random residues and on
     q - 1 everywhere, in place and out of place (the key switch's ModUp
     transforms a converted copy)."""
@@ -646,13 +647,15 @@ def test_ntt_data_paths_equal_the_oracle(logN):
     top = np.stack([np.full(pr.N, q - 1, dtype=np.uint64) for q in pr.moduli])
     for a in (rnd, top):
         want = np.stack([pr.ntt(a[t], t) for t in range(len(pr.moduli))])
-        for path in (0, 1, 2):
+        for path, fwd in ((0, 0), (1, 0), (2, 0), (0, 1), (0, 2), (0, 3), (1, 3)):
             g.set_ntt_path(path)
+            g.set_ntt_forward(fwd)
             d = to_dev(a[None])
             g.ntt(d)
-            assert np.array_equal(u64(d)[0], want), path
+            assert np.array_equal(u64(d)[0], want), (path, fwd)
             g.ntt(d, inverse=True)
-            assert np.array_equal(u64(d)[0], a), path
+            assert np.array_equal(u64(d)[0], a), (path, fwd)
+        g.set_ntt_forward(0)
     if logN == 16:
         # a key switch transforms converted copies out of place
         keys = ckks.KeySet(pr, 5, rot_steps=[3])
