@@ -87,6 +87,7 @@ struct fe_ctx {
     u64* d_tw2;                     // [n_mod][N][2]  (psi^brv(j), Shoup companion)
     u64* d_itw2;                    // [n_mod][N][2]  (psi^-brv(j), Shoup companion)
     u64 *d_ninv, *d_ninv_sh;        // [n_mod] N^-1
+    u64 *d_ninvw, *d_ninvw_sh;      // [n_mod] N^-1 times the inverse twiddle at index 1
     u64 *d_pinv, *d_pinv_sh;        // [n_mod] P^-1 mod q_i (i <= L)
     u64 *d_pmod, *d_pmod_sh;        // [n_mod] P mod q_i (i <= L)
     u64 *d_qpinv, *d_qpinv_sh;      // [L+1][L+1] (q_l P)^-1 mod q_i, i < l

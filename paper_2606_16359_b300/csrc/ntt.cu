@@ -52,6 +52,8 @@ struct NttArgs {
     const ulonglong2* tw;  // [n_mod][N] (w, floor(w 2^64 / q))
     const u64* ninv;
     const u64* ninv_sh;
+    const u64* ninvw;     // N^-1 times the inverse's last-stage twiddle
+    const u64* ninvw_sh;
     int logN, logN2;
 };
 
@@ -114,9 +116,13 @@ __device__ __forceinline__ u64 shoup36(u64 a, u64 w, u64 wq, u64 nq) {
 // kNoRed (forward only, all moduli < 2^58): no reduction inside the transform;
 // each stage adds less than 2q, so values stay below (1 + 2 * 17) q < 2^64.
 // kLE = log2 of the elements a thread holds per round (3: radix 8, 4: radix 16).
+// fold (inverse only): this round ends the transform; its last stage multiplies its
+// sums by N^-1 (fni) and its differences by N^-1 times the stage's twiddle (fwn), so
+// that the N^-1 scaling costs no product of its own.
 template <bool kInv, bool kNoRed, int kLE, bool kQ36 = false>
 __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo, int nst, int E, int logn,
-                                             int tw_line, const ulonglong2* __restrict__ tw, u64 q) {
+                                             int tw_line, const ulonglong2* __restrict__ tw, u64 q,
+                                             bool fold = false, ulonglong2 fni = {}, ulonglong2 fwn = {}) {
     constexpr int kEE = 1 << kLE, kHalf = kEE / 2;
     const u64 q2 = 2 * q, nq = 0 - q;
     auto mulw = [&](u64 a, const ulonglong2& ww) -> u64 {
@@ -145,6 +151,10 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
                 const u64 T = mulw(v[r + d], ww);
                 v[r] = X + T;
                 v[r + d] = X - T + q2;
+            } else if (fold && st == nst - 1) {
+                const u64 X = v[r], Y = v[r + d];  // both in [0, 2q): X + Y below 4q
+                v[r] = mulw(X + Y, fni);
+                v[r + d] = mulw(X - Y + q2, fwn);
             } else {
                 const u64 X = v[r], Y = v[r + d];
                 u64 S = X + Y;
@@ -239,11 +249,25 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
     const u64 q2 = 2 * q;
     const u64 ni = a.ninv[mi], nis = a.ninv_sh[mi];
     const u64 qinv64 = a.mods[mi].ratio_hi;  // floor(2^64 / q)
-    auto fin = [&](u64 x) -> u64 {
+    // forward, no reductions inside the transform (values below 35 q < 2^42 when q < 2^36):
+    // quotient from one 32 x 32 product, Q' = floor((x >> 20) mu / 2^32) with
+    // mu = floor(2^52 / q) = floor(2^64 / q) >> 12, which is floor(x / q) or one less
+    // for 2^25 <= q < 2^36, so x - Q' q lies in [0, 2q)
+    auto fin = [&](u64 x, bool folded) -> u64 {
         if (!last_pass) return x;
-        if (kInv) x = kQ36 ? shoup36(x, ni, nis, 0 - q) : shoup_lazy(x, ni, nis, q);  // [0, 2q)
-        else if (kNoRed) x -= __umul64hi(x, qinv64) * q;  // [0, 2q)
-        else x = x >= q2 ? x - q2 : x;
+        if (kInv) {
+            if (!folded) x = kQ36 ? shoup36(x, ni, nis, 0 - q) : shoup_lazy(x, ni, nis, q);  // [0, 2q)
+        } else if (kNoRed) {
+            if ((q >> 36) == 0 && (q >> 25) != 0) {
+                const uint32_t mu52 = (uint32_t)(qinv64 >> 12);
+                const uint32_t Qp = (uint32_t)(((u64)(uint32_t)(x >> 20) * mu52) >> 32);
+                x -= (u64)Qp * q;
+            } else {
+                x -= __umul64hi(x, qinv64) * q;
+            }  // [0, 2q)
+        } else {
+            x = x >= q2 ? x - q2 : x;
+        }
         return x >= q ? x - q : x;
     };
     const int tid = threadIdx.x;
@@ -282,18 +306,23 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
                                    : 0;
                 }
             }
-            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q);
+            // the inverse's last round applies N^-1 in its last stage
+            const bool fold = kInv && kCol && to_global;
+            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q, fold,
+                                                  make_ulonglong2(ni, nis),
+                                                  make_ulonglong2(a.ninvw[mi], a.ninvw_sh[mi]));
             // each thread writes back exactly the positions it read: no barrier in between
             if (to_global && vec) {
 #pragma unroll
                 for (int r = 0; r < kEE; r += 2)
-                    *reinterpret_cast<ulonglong2*>(d + GOFF(line, base + r)) = make_ulonglong2(fin(v[r]), fin(v[r + 1]));
+                    *reinterpret_cast<ulonglong2*>(d + GOFF(line, base + r)) =
+                        make_ulonglong2(fin(v[r], fold), fin(v[r + 1], fold));
             } else {
 #pragma unroll
                 for (int r = 0; r < kEE; r++) {
                     if (r >= E) break;
                     const int x = base + (r << lo);
-                    if (to_global) d[GOFF(line, x)] = fin(v[r]);
+                    if (to_global) d[GOFF(line, x)] = fin(v[r], fold);
                     else if (kCol) tile[CIDX(x, line)] = v[r];
                     else tile[RIDX(line, x)] = v[r];
                 }
@@ -310,13 +339,13 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
             if (kCol) {
                 const int x = el / lines, c = el - x * lines;
                 const int x1 = (el + 1) / lines, c1 = el + 1 - x1 * lines;
-                o.x = fin(tile[CIDX(x, c)]);
-                o.y = fin(tile[CIDX(x1, c1)]);
+                o.x = fin(tile[CIDX(x, c)], false);
+                o.y = fin(tile[CIDX(x1, c1)], false);
                 *reinterpret_cast<ulonglong2*>(d + (size_t)x * N2 + l0 + c) = o;
             } else {
                 const int ln = el >> logN2, x = el & (N2 - 1);
-                o.x = fin(tile[RIDX(ln, x)]);
-                o.y = fin(tile[RIDX(ln, x + 1)]);
+                o.x = fin(tile[RIDX(ln, x)], false);
+                o.y = fin(tile[RIDX(ln, x + 1)], false);
                 *reinterpret_cast<ulonglong2*>(d + (size_t)l0 * N2 + el) = o;
             }
         }
@@ -534,6 +563,8 @@ NttArgs make_args(fe_ctx* c, const LimbSet& s, const u64* src, size_t src_stride
     a.tw = (const ulonglong2*)(inverse ? c->d_itw2 : c->d_tw2);
     a.ninv = c->d_ninv;
     a.ninv_sh = c->d_ninv_sh;
+    a.ninvw = c->d_ninvw;
+    a.ninvw_sh = c->d_ninvw_sh;
     a.logN = c->logN;
     a.logN2 = c->logN / 2;
     return a;

@@ -249,6 +249,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     }
     std::vector<u64> tw2((size_t)nm * N * 2), itw2((size_t)nm * N * 2);
     std::vector<u64> ninv(nm), ninv_sh(nm), pinv(nm, 0), pinv_sh(nm, 0), pmod(nm, 0), pmod_sh(nm, 0);
+    std::vector<u64> ninvw(nm), ninvw_sh(nm);
     {
         std::vector<std::thread> th;
         for (int i = 0; i < nm; i++)
@@ -270,6 +271,10 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
                 }
                 ninv[i] = h_invmod((u64)N % q, q);
                 ninv_sh[i] = shoup_of(ninv[i], q);
+                // the inverse transform's last stage has the single twiddle at index 1;
+                // its product with N^-1 lets that stage apply the final scaling
+                ninvw[i] = h_mulmod(itw2[2 * ((size_t)i * N + (N > 1 ? 1 : 0))], ninv[i], q);
+                ninvw_sh[i] = shoup_of(ninvw[i], q);
             });
         for (auto& t : th) t.join();
     }
@@ -309,6 +314,7 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     for (int i = 0; i < nm; i++) mods[i] = make_modulus(c->mod[i]);
     size_t o_mod = pb.put(mods.data(), nm * sizeof(Modulus));
     size_t o_ninv = pb.put(ninv.data(), nm * 8), o_ninv_sh = pb.put(ninv_sh.data(), nm * 8);
+    size_t o_ninvw = pb.put(ninvw.data(), nm * 8), o_ninvw_sh = pb.put(ninvw_sh.data(), nm * 8);
     size_t o_pinv = pb.put(pinv.data(), nm * 8), o_pinv_sh = pb.put(pinv_sh.data(), nm * 8);
     size_t o_pmod = pb.put(pmod.data(), nm * 8), o_pmod_sh = pb.put(pmod_sh.data(), nm * 8);
     size_t o_ql = pb.put(qlinv.data(), qlinv.size() * 8);
@@ -385,6 +391,8 @@ extern "C" int fe_ctx_create(const fe_params* p, fe_ctx** out) {
     c->d_mod = (Modulus*)(dpool + o_mod);
     c->d_ninv = (u64*)(dpool + o_ninv);
     c->d_ninv_sh = (u64*)(dpool + o_ninv_sh);
+    c->d_ninvw = (u64*)(dpool + o_ninvw);
+    c->d_ninvw_sh = (u64*)(dpool + o_ninvw_sh);
     c->d_pinv = (u64*)(dpool + o_pinv);
     c->d_pinv_sh = (u64*)(dpool + o_pinv_sh);
     c->d_pmod = (u64*)(dpool + o_pmod);

@@ -60,3 +60,30 @@ def test_shoup36_random():
     for _ in range(20000):
         q = rng.randrange(1 << 25, 1 << 36) | 1
         _check(rng.randrange(0, 1 << 42), rng.randrange(0, q), q)
+
+
+def fin32(x, q):
+    """The forward transform's final reduction for 2^25 <= q < 2^36 (csrc/ntt.cu):
+    Q' = floor((x >> 20) mu / 2^32) with mu = floor(2^64 / q) >> 12, one 32 x 32
+    product; the result x - Q' q before the last conditional subtraction."""
+    mu = ((1 << 64) // q) >> 12
+    t = x >> 20
+    assert t <= M32 and mu <= M32
+    Qp = (t * mu) >> 32
+    return x - Qp * q
+
+
+def test_fin32_quotient_is_exact_or_one_short():
+    """x below 35 q (the forward transform's values without inner reductions)
+    reduces to [0, 2q): Q' is floor(x / q) or one less, since the dropped low
+    20 bits of x add less than 2^20 / q <= 2^-5 and the truncation of mu less
+    than 2^22 / 2^32 to the quotient."""
+    rng = random.Random(11)
+    qs = [(1 << 36) - 5, 68719476731, 34359738421, (1 << 25) + 1, (1 << 25) + 3, 50331653]
+    for q in qs:
+        xs = [0, 1, q - 1, q, 2 * q - 1, 35 * q - 1, 34 * q, (35 * q) & ~((1 << 20) - 1)]
+        xs += [rng.randrange(35 * q) for _ in range(5000)]
+        for x in xs:
+            r = fin32(x, q)
+            assert 0 <= r < 2 * q, (q, x)
+            assert r % q == x % q
