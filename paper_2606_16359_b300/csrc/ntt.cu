@@ -119,7 +119,9 @@ __device__ __forceinline__ u64 shoup36(u64 a, u64 w, u64 wq, u64 nq) {
 // fold (inverse only): this round ends the transform; its last stage multiplies its
 // sums by N^-1 (fni) and its differences by N^-1 times the stage's twiddle (fwn), so
 // that the N^-1 scaling costs no product of its own.
-template <bool kInv, bool kNoRed, int kLE, bool kQ36 = false>
+// kPre: load every stage's twiddles before the first stage (row passes, whose
+// twiddles differ per row and come from L2), so that their latency overlaps.
+template <bool kInv, bool kNoRed, int kLE, bool kQ36 = false, bool kPre = false>
 __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo, int nst, int E, int logn,
                                              int tw_line, const ulonglong2* __restrict__ tw, u64 q,
                                              bool fold = false, ulonglong2 fni = {}, ulonglong2 fwn = {}) {
@@ -129,18 +131,33 @@ __device__ __forceinline__ void round_stages(u64 (&v)[1 << kLE], int blk, int lo
         if constexpr (kQ36) return shoup36(a, ww.x, ww.y, nq);
         else return shoup_lazy(a, ww.x, ww.y, q);
     };
+    auto load_tw = [&](int si, ulonglong2 (&w)[kHalf]) {
+        const int st = kInv ? si : kLE - 1 - si;
+        if (st >= nst) return;
+        const int lt = lo + st;
+        const int K = (tw_line << (logn - 1 - lt)) + (blk << (kLE - 1 - st));
+        const int cnt = max(1, E >> (st + 1));
+#pragma unroll
+        for (int i = 0; i < kHalf; i++)
+            if (i < (kHalf >> st) && i < cnt) w[i] = tw[K + i];
+    };
+    ulonglong2 wpre[kPre ? kLE : 1][kHalf];
+    if constexpr (kPre) {
+#pragma unroll
+        for (int si = 0; si < kLE; si++) load_tw(si, wpre[si]);
+    }
 #pragma unroll
     for (int si = 0; si < kLE; si++) {
         const int st = kInv ? si : kLE - 1 - si;  // forward: large distances first
         if (st >= nst) continue;
         const int d = 1 << st;
-        const int lt = lo + st;
-        const int K = (tw_line << (logn - 1 - lt)) + (blk << (kLE - 1 - st));
-        const int cnt = max(1, E >> (st + 1));
         ulonglong2 w[kHalf];
+        if constexpr (kPre) {
 #pragma unroll
-        for (int i = 0; i < kHalf; i++)
-            if (i < (kHalf >> st) && i < cnt) w[i] = tw[K + i];
+            for (int i = 0; i < kHalf; i++) w[i] = wpre[si][i];
+        } else {
+            load_tw(si, w);
+        }
 #pragma unroll
         for (int r = 0; r < kEE; r++) {
             if ((r & d) || r + d >= E) continue;
@@ -308,7 +325,7 @@ __global__ void __launch_bounds__(kTile >> kLE, kLE == 3 ? 9 : (kLE == 4 ? 8 : 6
             }
             // the inverse's last round applies N^-1 in its last stage
             const bool fold = kInv && kCol && to_global;
-            round_stages<kInv, kNoRed, kLE, kQ36>(v, blk, lo, nst, E, logn, tw_line, tw, q, fold,
+            round_stages<kInv, kNoRed, kLE, kQ36, !kCol>(v, blk, lo, nst, E, logn, tw_line, tw, q, fold,
                                                   make_ulonglong2(ni, nis),
                                                   make_ulonglong2(a.ninvw[mi], a.ninvw_sh[mi]));
             // each thread writes back exactly the positions it read: no barrier in between
