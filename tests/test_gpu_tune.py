@@ -144,3 +144,30 @@ def test_graph_host_outputs_at_level_1_are_the_dropped_limbs_and_decrypt():
         with pytest.raises(fe.FencError):
             net.graphs[0].set_host_output_level(ctx.L)  # above the outputs' level
     assert max(errs) < 1e-3, errs
+
+
+def test_graph_with_every_ntt_form_equals_eager_default():
+    """At N = 2^16 (where the cluster form of the NTT exists), a block captured
+    in a graph with the single-pass cluster NTT (fe_ctx_set_ntt_path(2)) and
+    with the other forward forms (fe_ctx_set_ntt_forward) gives the residues
+    of the eager run with the default two-pass transform."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(16, 4, 2, 36, 36)
+        net = MobileNetBlocks(ctx, blocks=[(8, 16, 16)], delta=2.0 ** 30, schedule=4)
+        net.run(mode=1)
+        torch.cuda.synchronize()
+        want = net.outputs[0].cpu().numpy()
+        err = float(np.abs(net.decrypt_block(0) - net.reference_block(0)).max())
+        for path, fwd in ((2, 0), (0, 3), (1, 1)):
+            ctx.set_ntt_path(path)
+            ctx.set_ntt_forward(fwd)
+            net.outputs[0].zero_()
+            net.capture()
+            net.graph.launch()
+            torch.cuda.synchronize()
+            assert np.array_equal(net.outputs[0].cpu().numpy(), want), (path, fwd)
+        ctx.set_ntt_path(0)
+        ctx.set_ntt_forward(0)
+        assert ctx.device_status() == 0
+    assert err < 1e-3, err
