@@ -29,10 +29,12 @@ def models():
         xs = [W.lenet_input(i, lenet.BS) for i in range(3)]
         l_in = [lenet.encrypt(x, seed=40 + i).cpu().pin_memory() for i, x in enumerate(xs)]
         p = W.PARAMS["mobilenet_small"]
-        # N = 2^14: a block request keeps the device busy for milliseconds, longer
-        # than the host takes to enqueue a LeNet group, so overlap is observable
+        # N = 2^14 and 128 channels: a block group keeps the device busy for
+        # several milliseconds, longer than the host takes to enqueue a LeNet
+        # group, so overlap is observable (a 32-channel block finished before
+        # the next group was enqueued once the transforms got faster)
         c_mb = fe.Context(14, p["n_q"], p["k"], p["bits"], p["pbits"])
-        mb = MobileNetBlocks(c_mb, blocks=[(32, 32, 32)], delta=p["delta"])
+        mb = MobileNetBlocks(c_mb, blocks=[(32, 128, 128)], delta=p["delta"])
         m_in = [mb.inputs[0].cpu().pin_memory()]
         torch.cuda.synchronize()
     return dict(lenet=lenet, xs=xs, wts=wts, l_in=l_in, mb=mb, m_in=m_in, stream=s)
