@@ -566,6 +566,15 @@ int fe_plan_set_hoisting(fe_plan* plan, int double_hoist);
  * ciphertexts share one kernel item (1, 2 or 4; default 4).  Results do not
  * depend on it; the autotuner picks the fastest.  Errors: FE_EINVAL. */
 int fe_plan_set_mac_ways(fe_plan* plan, uint32_t ways);
+/* Depthwise plans under double hoisting, batched path: with enable = 1
+ * (default) the MAC forms every rotated copy sigma_g((P c0, 0) + acc) on the
+ * fly from the key inner product's accumulators and the lifted input, instead
+ * of a lift pass writing the copies for the MAC to read back (the copies'
+ * store and reload are saved; same residues).  0 keeps the separate lift.
+ * Other plans and the per-primitive path always lift first.  Changes the
+ * plan's workspace layout only within fe_plan_workspace_bytes.
+ * Errors: FE_EINVAL. */
+int fe_plan_set_lift_fusion(fe_plan* plan, int enable);
 /* Keep only the first max_out_ct output ciphertexts of a plan (with the terms,
  * plaintexts and inner rotations they use); their results are unchanged.  Used
  * to time a slice of a large layer.  Errors: FE_EINVAL. */

@@ -105,6 +105,7 @@ SIGNATURES = {
     "fe_device_status": (cint, [vp, P(u32), cint]),
     "fe_ctx_set_mac_wait": (cint, [vp, u64, i32]),
     "fe_plan_set_mac_ways": (cint, [vp, u32]),
+    "fe_plan_set_lift_fusion": (cint, [vp, cint]),
     "fe_plan_set_hoisting": (cint, [vp, cint]),
     "fe_server_create": (cint, [P(FeServerConfig), P(vp)]),
     "fe_server_add_model": (cint, [vp, vp, vp, P(FeOp), u32, u32, u32, P(u32)]),
@@ -567,6 +568,10 @@ class Context:
     def plan_set_mac_ways(self, plan, ways):
         check(load().fe_plan_set_mac_ways(plan.handle, ways))
         plan.mac_ways = ways
+
+    def plan_set_lift_fusion(self, plan, enable):
+        """Depthwise double-hoisted plans: the MAC forms the rotated copies (1) or a lift pass writes them (0)."""
+        check(load().fe_plan_set_lift_fusion(plan.handle, int(enable)))
         return plan
 
     def plan_truncate(self, plan, max_out_ct):

@@ -175,6 +175,14 @@ std::vector<std::pair<int, int>> outer_order(const fe_plan* p) {
     return v;
 }
 
+// Batched path, double hoisting, depthwise (one output per MAC item, no outer
+// rotation): the MAC reads the key inner product's accumulators and the lifted
+// inputs and forms each rotated copy on the fly (k_mac_rot) instead of the lift
+// writing the copies first.  Same residues.
+bool lift_in_mac(const fe_plan* p, int mode) {
+    return mode == 1 && p->kind == 0 && p->dhoist && p->n_outer == 0 && p->depthwise && p->lift_mac;
+}
+
 size_t item_bytes(const fe_plan* p, size_t chunk, size_t R) {
     size_t groups = 0;
     for (auto& o : p->outs) groups += o.groups.size();
@@ -186,7 +194,8 @@ size_t item_bytes(const fe_plan* p, size_t chunk, size_t R) {
     n += R * (groups * sizeof(MacItem) + p->terms.size() * sizeof(MacTerm));
     if (p->dhoist) n += R * ((p->inner.size() + p->n_in) * sizeof(LiftItem) + groups * sizeof(CombineItem));
     if (p->dhoist == 2) n += R * p->n_out * sizeof(u64*);
-    return n + 21 * 256;
+    if (p->dhoist) n += R * (groups * sizeof(RotItem) + p->terms.size() * sizeof(RotTerm));
+    return n + 23 * 256;
 }
 
 }  // namespace
@@ -224,6 +233,9 @@ size_t plan_data_bytes(const fe_plan* p, size_t chunk, size_t R) {
                    R * p->n_out * z.ctw;
     size_t rs = rescale_tmp_words(c, (int)(R * p->n_out), p->level);
     size_t words = persist + std::max(std::max(std::max(inner, outer), rs), base);
+    // rotated copies formed in the MAC: the accumulators of stage 1 stay live while
+    // stage 2 writes its sums after them
+    if (lift_in_mac(p, 1)) words = std::max(words, persist + inner + base);
     return words * 8 + 24 * 256;
 }
 
@@ -412,6 +424,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     LiftItem* d_lift = cv.take<LiftItem>(dh ? std::max<size_t>(1, R * (n_in_rot + p->n_in)) : 1);
     CombineItem* d_dcb = cv.take<CombineItem>(dh ? std::max<size_t>(1, R * n_groups_all) : 1);
     u64** d_fout = cv.take<u64*>(fuse ? std::max<size_t>(1, R * p->n_out) : 1);
+    const bool lm = lift_in_mac(p, mode);
+    RotItem* d_ritems = cv.take<RotItem>(lm ? std::max<size_t>(1, R * n_groups_all) : 1);
+    RotTerm* d_rterms = cv.take<RotTerm>(lm ? std::max<size_t>(1, R * n_terms) : 1);
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small for the plan");
     Carver cd(data_ws ? (char*)data_ws : cv.p, data_ws ? data_ws_bytes : cv.left);
     u64* Rb = cd.take<u64>(R * n_in_rot * rw);
@@ -425,7 +440,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
     u64* ext1 = s1.take<u64>(R * n_mu * z.extw);
     u64* acc1 = s1.take<u64>(R * n_in_rot * z.accw);
     u64* conv1 = s1.take<u64>(dh ? 0 : R * n_in_rot * z.ctw);
-    Carver s2(scratch, scratch_bytes);  // stage 2 under double hoisting (same region)
+    // stage 2 under double hoisting: the same region, or after stage 1's accumulators
+    // when the MAC still reads them
+    Carver s2(lm ? s1.p : scratch, lm ? s1.left : scratch_bytes);
     u64* accB = s2.take<u64>(dh ? R * p->n_out * z.accw : 0);
     u64* convB = s2.take<u64>(dh ? R * p->n_out * z.ctw : 0);
     Carver s3(scratch, scratch_bytes);  // stage 3 (same region)
@@ -573,6 +590,32 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
         return rg;
     };
     const MacRange base_rg = merge(0, n_base);
+    // rotated copies formed in the MAC (lift_in_mac): the base items' terms as
+    // (accumulator, lifted input, plaintext, automorphism); every item has one output
+    std::vector<RotItem> ritems;
+    std::vector<RotTerm> rterms;
+    int n_acc_terms = 0;
+    bool lm_ok = lm;
+    for (int i = 0; lm_ok && i < base_rg.count; i++) lm_ok = dmacs[base_rg.first + i].n_out == 1;
+    if (lm_ok) {
+        rterms.reserve(R * n_terms);
+        for (size_t r = 0; r < R; r++)
+            for (const auto& t : p->terms) {
+                const uint8_t* ptp = (const uint8_t*)b_pt + (size_t)(pt_pool ? t.pt % pt_pool : t.pt) * ptb;
+                if (t.src >= 0) {
+                    const auto& in = p->inner[t.src];
+                    rterms.push_back(RotTerm{acc1 + (r * n_in_rot + t.src) * z.accw,
+                                             XP + (r * p->n_in + in.ci) * z.accw, ptp, c->galois(in.step)});
+                    n_acc_terms++;
+                } else {
+                    rterms.push_back(RotTerm{nullptr, XP + (r * p->n_in + (size_t)(-t.src - 1)) * z.accw, ptp, 1});
+                }
+            }
+        for (int i = 0; i < base_rg.count; i++) {
+            const MacItem& it = dmacs[base_rg.first + i];
+            ritems.push_back(RotItem{it.out[0], it.term0[0], it.n_terms});
+        }
+    }
     std::vector<MacRange> chunk_rg;
     for (size_t c0 = 0; c0 < order.size(); c0 += chunk)
         chunk_rg.push_back(merge(n_base + c0, n_base + std::min(order.size(), c0 + chunk)));
@@ -627,6 +670,10 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             FE_TRY(upload(lifts, d_lift, st));
             FE_TRY(upload(dcb, d_dcb, st));
         }
+        if (lm_ok) {
+            FE_TRY(upload(ritems, d_ritems, st));
+            FE_TRY(upload(rterms, d_rterms, st));
+        }
         if (fuse) FE_TRY(upload(fout, d_fout, st));
     }
     if (!(phase & 2)) return FE_OK;
@@ -657,7 +704,9 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
             i = j;
         }
         launch_keyip_grouped(c, d_in_kg, d_in_ks, (int)ikg.size(), (int)iorder.size(), lv, st, (int)n_mu_all);
-        if (dh) {
+        if (lm_ok) {  // only the lifted inputs: the MAC forms the rotated copies
+            launch_lift(c, d_lift + R * n_in_rot, (int)(R * p->n_in), lv, st, 0, (int)(R * p->n_in));
+        } else if (dh) {
             launch_lift(c, d_lift, (int)(R * (n_in_rot + p->n_in)), lv, st, (int)(R * n_in_rot),
                         (int)(R * p->n_in));
         } else {
@@ -696,8 +745,11 @@ int run_plan(fe_ctx* c, const fe_evk* evk, const fe_plan* p, const u64* b_in, co
                 launch_pmult_compact(c, tm.ct, tm.pt, macs[i].out, lv, t > 0, st);
             }
     } else {
-        launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
-                   base_rg.outputs, base_rg.ways, lv, st, dh, base_rg.ct_distinct);
+        if (lm_ok)
+            launch_mac_rot(c, d_ritems, d_rterms, base_rg.count, base_rg.ct_terms, n_acc_terms, lv, st);
+        else
+            launch_mac(c, d_mac + base_rg.first, d_terms, base_rg.count, base_rg.ct_terms, base_rg.pt_terms,
+                       base_rg.outputs, base_rg.ways, lv, st, dh, base_rg.ct_distinct);
         if (fuse) {
             moddown_rescale(c, accB, (int)n_base, lv, convB, d_fout, st);
         } else if (dh) {
@@ -1478,6 +1530,13 @@ extern "C" int fe_plan_set_mac_ways(fe_plan* p, uint32_t ways) {
     if (!p) return fail(FE_EINVAL, "null argument");
     if (ways != 1 && ways != 2 && ways != 4) return fail(FE_EINVAL, "mac ways must be 1, 2 or 4");
     p->mac_ways = (int)ways;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_set_lift_fusion(fe_plan* p, int enable) {
+    if (!p) return fail(FE_EINVAL, "null argument");
+    if (enable != 0 && enable != 1) return fail(FE_EINVAL, "enable must be 0 or 1");
+    p->lift_mac = enable;
     return FE_OK;
 }
 

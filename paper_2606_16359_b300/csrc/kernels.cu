@@ -1013,6 +1013,139 @@ void launch_mac(fe_ctx* c, const MacItem* items, const MacTerm* terms, int n_ite
     c->cnt.launches++;
 }
 
+// Rotated-term MAC (see RotTerm): one coefficient pair per thread, grid (pairs,
+// limb, item).  The automorphism maps the pair onto a pair (k_lift), so each
+// operand is one 16-byte gather; the rotated copy's value is formed exactly as
+// k_lift forms it (acc + P c0 on the q limbs, acc alone on the p limbs; acc for
+// the second polynomial) and multiplied into the sums as k_mac does, so the
+// residues equal the lift followed by the MAC.  The copies are never written:
+// the lift's store and the MAC's reload of every rotated copy are saved.
+template <int HB, bool kM36>
+__global__ void __launch_bounds__(256) k_mac_rot(const RotItem* items, const RotTerm* terms, const Modulus* mods,
+                                                 const int* ks_limbs, int nq, int np, int logN, int T) {
+    const int N = 1 << logN;
+    const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (n >= N) return;
+    const RotItem it = items[blockIdx.z];
+    const int p = blockIdx.y;
+    const Modulus m = mods[ks_limbs[p]];
+    const u64 q = m.q;
+    const size_t o0 = (size_t)p << logN, o1 = (size_t)(np + p) << logN;
+    // compact plaintext limb p: tile n / T holds T low words then T high parts
+    const size_t pt_tile_off = o0 * (4 + HB) + (size_t)(n / T) * (4 + HB) * T;
+    const int r = n % T;
+    constexpr bool kSplit = HB == 1;
+    using Acc = typename std::conditional<kM36, Acc36, typename std::conditional<kSplit, Acc40, u128>::type>::type;
+    auto zero = [](Acc& a) {
+        if constexpr (kM36) acc36_zero(a); else if constexpr (kSplit) acc40_zero(a); else a = 0;
+    };
+    auto mad = [](Acc& a, u64 x, u64 y) {
+        if constexpr (kM36) acc36_mad(a, x, split24_lo(y), split24_hi(y));
+        else if constexpr (kSplit) acc40_mad(a, x, y);
+        else a += (u128)x * y;
+    };
+    auto value = [](const Acc& a) -> u128 {
+        if constexpr (kM36) return acc36_value(a); else if constexpr (kSplit) return acc40_value(a); else return a;
+    };
+    Acc a0, a1, b0, b1;
+    zero(a0);
+    zero(a1);
+    zero(b0);
+    zero(b1);
+    for (int t = 0; t < it.n_terms; t++) {
+        const RotTerm tm = terms[it.term0 + t];
+        ulonglong2 v0, v1;
+        if (tm.acc) {
+            const uint32_t src = galois_perm(n, tm.galois, logN);
+            const uint32_t pair = src & ~1u;
+            const bool swap = src & 1u;
+            auto load2 = [&](const u64* base) -> ulonglong2 {
+                ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + pair);
+                if (swap) {
+                    const u64 x = v.x;
+                    v.x = v.y;
+                    v.y = x;
+                }
+                return v;
+            };
+            v0 = load2(tm.acc + o0);
+            v1 = load2(tm.acc + o1);
+            if (p < nq) {
+                const ulonglong2 pc = load2(tm.xp + o0);  // P c0 at the source pair
+                v0.x = add_mod(v0.x, pc.x, q);
+                v0.y = add_mod(v0.y, pc.y, q);
+            }
+        } else {
+            v0 = *reinterpret_cast<const ulonglong2*>(tm.xp + o0 + n);
+            v1 = *reinterpret_cast<const ulonglong2*>(tm.xp + o1 + n);
+        }
+        const uint8_t* pk = tm.pt + pt_tile_off;
+        const uint2 lo = *reinterpret_cast<const uint2*>(pk + (size_t)r * 4);
+        u64 hx, hy;
+        if (HB == 1) {
+            const uchar2 h = *reinterpret_cast<const uchar2*>(pk + (size_t)4 * T + r);
+            hx = h.x, hy = h.y;
+        } else if (HB == 2) {
+            const ushort2 h = *reinterpret_cast<const ushort2*>(pk + (size_t)4 * T + (size_t)r * 2);
+            hx = h.x, hy = h.y;
+        } else {
+            const uint2 h = *reinterpret_cast<const uint2*>(pk + (size_t)4 * T + (size_t)r * 4);
+            hx = h.x, hy = h.y;
+        }
+        const u64 px = (u64)lo.x | (hx << 32), py = (u64)lo.y | (hy << 32);
+        mad(a0, v0.x, px);
+        mad(a1, v0.y, py);
+        mad(b0, v1.x, px);
+        mad(b1, v1.y, py);
+        // the same folds as k_mac (a fold replaces a sum by its residue)
+        if constexpr (kM36) {
+            if ((t & 15) == 15) {
+                acc36_fold(a0);
+                acc36_fold(a1);
+                acc36_fold(b0);
+                acc36_fold(b1);
+            }
+        }
+        if ((kSplit && (t & 0x3FFF) == 0x3FFF) || (HB == 4 && (t & 15) == 15)) {
+            auto fold = [&](Acc& a) {
+                const u64 v = reduce128(value(a), m);
+                zero(a);
+                mad(a, v, 1);
+            };
+            fold(a0);
+            fold(a1);
+            fold(b0);
+            fold(b1);
+        }
+    }
+    *reinterpret_cast<ulonglong2*>(it.out + o0 + n) = make_ulonglong2(reduce128(value(a0), m), reduce128(value(a1), m));
+    *reinterpret_cast<ulonglong2*>(it.out + o1 + n) = make_ulonglong2(reduce128(value(b0), m), reduce128(value(b1), m));
+}
+
+void launch_mac_rot(fe_ctx* c, const RotItem* items, const RotTerm* terms, int n_items, int n_terms, int n_acc_terms,
+                    int level, cudaStream_t st) {
+    if (!n_items) return;
+    const int np = level + 1 + c->k, nq = level + 1;
+    // algorithmic bytes: each rotated term's accumulators (2 np limbs) and the P c0
+    // limbs (nq) it adds, each unrotated term's lifted copy (2 np), every plaintext
+    // as stored, every output written
+    ProfScope ps(c, PK_MAC, st, (double)c->N * (8.0 * ((2.0 * np + nq) * n_acc_terms + 2.0 * np * (n_terms - n_acc_terms) +
+                                                       2.0 * np * n_items) +
+                                                (4.0 + c->pt_hb) * np * n_terms));
+    const dim3 g((c->N / 2 + 255) / 256, np, n_items);
+    const int T = pt_tile(c);
+    const int* ks = c->lv[level].d_ks_limbs;
+    if (c->pt_hb == 1 && c->max_mod_bits <= 36)
+        k_mac_rot<1, true><<<g, 256, 0, st>>>(items, terms, c->d_mod, ks, nq, np, c->logN, T);
+    else if (c->pt_hb == 1)
+        k_mac_rot<1, false><<<g, 256, 0, st>>>(items, terms, c->d_mod, ks, nq, np, c->logN, T);
+    else if (c->pt_hb == 2)
+        k_mac_rot<2, false><<<g, 256, 0, st>>>(items, terms, c->d_mod, ks, nq, np, c->logN, T);
+    else
+        k_mac_rot<4, false><<<g, 256, 0, st>>>(items, terms, c->d_mod, ks, nq, np, c->logN, T);
+    c->cnt.launches++;
+}
+
 void launch_pt_compact(fe_ctx* c, const u64* in, uint8_t* out, int n_limbs, cudaStream_t st) {
     if (n_limbs <= 0) return;
     k_pt_compact<<<grid_for(c->N, n_limbs), kB, 0, st>>>(in, out, c->pt_hb, pt_tile(c), c->logN);

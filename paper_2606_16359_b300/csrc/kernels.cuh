@@ -101,6 +101,23 @@ struct MacTerm {
     const u64* ct;      // [2][l+1][N]
     const uint8_t* pt;  // compact plaintext, l+1 limbs
 };
+// PMult-MAC whose terms are rotated copies made on the fly (double hoisting with
+// one output per item: depthwise layers).  A rotated term is sigma_g((P c0, 0) +
+// acc) read straight from the key inner product's accumulators and the input's
+// lifted copy (P c0, P c1); an unrotated term is the lifted copy itself.
+struct RotTerm {
+    const u64* acc;     // [2][l+1+k][N] key inner product of the rotation, or nullptr
+    const u64* xp;      // [2][l+1+k][N] lifted input (P c0, P c1)
+    const uint8_t* pt;  // compact plaintext, l+1+k limbs
+    uint32_t galois;    // 1 for an unrotated term
+};
+struct RotItem {
+    u64* out;  // [2][l+1+k][N]
+    int term0, n_terms;
+};
+// n_acc_terms: terms with an accumulator (the profiler's byte count)
+void launch_mac_rot(fe_ctx* c, const RotItem* items_dev, const RotTerm* terms_dev, int n_items, int n_terms,
+                    int n_acc_terms, int level, cudaStream_t st);
 inline size_t pt_limb_bytes(const fe_ctx* c) { return (size_t)(4 + c->pt_hb) * c->N; }
 inline int pt_tile(const fe_ctx* c) { return c->N < 512 ? c->N : 512; }
 // n_limbs 64-bit limbs [n_limbs][N] -> compact limbs

@@ -48,6 +48,7 @@ struct fe_plan {
     int bsgs_n1 = 0;  // baby steps of the outer rotations, 0: linear
     int mac_ways = 4;  // outputs sharing one MAC item (ciphertext loads), 1, 2 or 4
     int dhoist = 0;    // 1: double hoisting (rotations and MAC on Q_l * P, one ModDown per sum)
+    int lift_mac = 1;  // double hoisting, depthwise: the MAC forms the rotated copies on the fly
     std::vector<int32_t> steps;
     double w_scale = 0;  // scale of the loaded weights (0 until fe_plan_load_weights)
     int repack = 0;      // 1: an FC-kind plan whose weights are the permutation from lin to lout

@@ -670,3 +670,29 @@ def test_ntt_data_paths_equal_the_oracle(logN):
             assert np.array_equal(u64(g.rotate(evk, ct, pr.L, 3)), want), path
     g.set_ntt_path(0)
     assert g.device_status() == 0
+
+
+@pytest.mark.parametrize("dh,S,BS", [(1, 1, 1), (2, 1, 1), (2, 2, 2)])
+def test_depthwise_rotated_copies_formed_in_the_mac(tiny, dh, S, BS):
+    """Depthwise layers under double hoisting: the batched MAC forms each rotated
+    copy sigma((P c0, 0) + acc) from the key inner product's accumulators and
+    the lifted input (fe_plan_set_lift_fusion(1), default) or reads the copies a
+    lift pass wrote (0); both give the oracle's residues, as does the
+    per-primitive path."""
+    rng = np.random.default_rng(90 + dh + S)
+    x = rng.uniform(0, 1, (BS, 4, 8, 8))
+    w = rng.normal(0, 1 / 3, (4, 1, 3, 3))
+    plan, outs = run_conv_pair(tiny, x, w, S, depthwise=True, double_hoist=dh)
+    g = tiny.g
+    steps = plan.steps
+    sk = g.sk_gen(3)
+    evk = g.evk_gen(sk, 3, steps)
+    lay = g.layout(8, 8, 4, BS, S)
+    ct = g.encrypt(sk, g.pack(lay, torch.from_numpy(x)), tiny.pr.L, 2.0 ** 25, seed=17)
+    pt = g.load_weights(plan, w, float(tiny.pr.q[tiny.pr.L]))
+    g.plan_set_lift_fusion(plan, 0)
+    unfused = u64(g.he_conv(evk, plan, pt, ct, mode=1))
+    g.plan_set_lift_fusion(plan, 1)
+    fused = u64(g.he_conv(evk, plan, pt, ct, mode=1))
+    assert np.array_equal(fused, unfused) and np.array_equal(fused, u64(outs[1]))
+    assert g.device_status() == 0
