@@ -373,14 +373,16 @@ static void fft_ld(ld *re, ld *im, u64 M, int sign) {
     }
 }
 
-/* quad-precision value of Delta * (2/N) * sum_l z_l cos(pi * t_l / N), t_l = 5^l j mod 2N */
-static __float128 encode_coef_quad(const double *z, int logN, double scale, u64 j) {
+/* quad-precision value of Delta * (2/N) * sum_l z_l cos(pi * t_l / N), t_l = 5^l j mod 2N.
+ * cq (optional): cq[t] = cosq(pi t / N) for t in [0, 2N), the same quad values the
+ * loop would compute term by term. */
+static __float128 encode_coef_quad(const double *z, int logN, double scale, u64 j, const __float128 *cq) {
     u64 N = (u64)1 << logN, twoN = 2 * N;
     __float128 acc = 0;
     u64 e = 1;
     for (u64 l = 0; l < N / 2; l++) {
         u64 t = (e * j) % twoN;
-        acc += (__float128)z[l] * cosq(M_PIq * (__float128)t / (__float128)N);
+        acc += (__float128)z[l] * (cq ? cq[t] : cosq(M_PIq * (__float128)t / (__float128)N));
         e = (e * 5) % twoN;
     }
     return acc * (__float128)scale * 2 / (__float128)N;
@@ -413,25 +415,31 @@ int or_encode(const double *z, int logN, double scale, i64 *out) {
     ld guard = bound * (ld)logN * 0x1p-52L;
     if (guard < 0x1p-30L) guard = 0x1p-30L;
     int fallbacks = 0;
+    __float128 *cq = NULL;
     for (u64 j = 0; j < N; j++) {
         ld v = (ld)scale * re[j] / (ld)N;
         ld fl = floorl(v);
         ld frac = v - fl;
         if (fabsl(frac - 0.5L) < guard) {
-            __float128 vq = encode_coef_quad(z, logN, scale, j);
+            if (!cq) { /* first fallback of this call: the cosines of every angle pi t / N */
+                cq = malloc(M * sizeof(__float128));
+                for (u64 t = 0; t < M; t++) cq[t] = cosq(M_PIq * (__float128)t / (__float128)N);
+            }
+            __float128 vq = encode_coef_quad(z, logN, scale, j, cq);
             __float128 fq = floorq(vq);
             __float128 fracq = vq - fq;
-            if (fabsq(fracq - 0.5Q) < 0x1p-40Q) { free(re); free(im); return -1; }
+            if (fabsq(fracq - 0.5Q) < 0x1p-40Q) { free(re); free(im); free(cq); return -1; }
             fl = (ld)fq;
             frac = (ld)fracq;
             fallbacks++;
         }
         ld r = frac > 0.5L ? fl + 1 : fl;
-        if (fabsl(r) > 0x1p62L) { free(re); free(im); return -2; }
+        if (fabsl(r) > 0x1p62L) { free(re); free(im); free(cq); return -2; }
         out[j] = (i64)r;
     }
     free(re);
     free(im);
+    free(cq);
     return fallbacks;
 }
 
@@ -454,5 +462,5 @@ void or_decode(const i64 *m, int logN, double scale, double *z) {
 /* Direct O(N^2) reference for encode without rounding (used by tests on tiny N). */
 void or_encode_direct_real(const double *z, int logN, double scale, double *out) {
     u64 N = (u64)1 << logN;
-    for (u64 j = 0; j < N; j++) out[j] = (double)encode_coef_quad(z, logN, scale, j);
+    for (u64 j = 0; j < N; j++) out[j] = (double)encode_coef_quad(z, logN, scale, j, NULL);
 }
