@@ -54,6 +54,11 @@ extern "C" {
 #define FE_ECUDA (-7)    /* CUDA runtime error */
 #define FE_EENCODE (-8)  /* a coefficient lies within 2^-40 of a rounding tie */
 
+/* Rotation-step value that stands for the complex conjugation of the slots
+ * (the automorphism X -> X^(2N-1), Galois element 2N - 1) wherever a rotation
+ * step is taken: fe_evk_gen, fe_evk_upload, fe_evk_alias, fe_rotate. */
+#define FE_STEP_CONJ (-2147483647 - 1)
+
 typedef struct fe_ctx fe_ctx;
 typedef struct fe_evk fe_evk;
 typedef struct fe_plan fe_plan;
@@ -840,6 +845,89 @@ int fe_device_status(fe_ctx* ctx, uint32_t* status, int reset);
  * inside stream capture. */
 int fe_profile_begin(fe_ctx* ctx, const char* kind);
 int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* bytes);
+
+/* ---- ciphertext refresh (bootstrapping) ----------------------------------- */
+/* The paper's deeper networks (SqueezeNet, ResNet18, MobileNet) refresh their
+ * ciphertexts between blocks with an existing CKKS bootstrapping (Sec. 5,
+ * Evaluation Methodology: NEXUS's, 14 levels per refresh); the paper does not
+ * print its steps.  The library implements the standard CKKS refresh for its
+ * real-slot encoding: ModRaise, CoeffToSlot (the special FFT's inverse stages
+ * in n_cts groups, one level each), EvalMod (a degree-16 Taylor cosine and r
+ * double angles, 5 + r levels) and SlotToCoeff (n_stc groups), on a context
+ * whose secret is sparse (fe_sk_gen_sparse).  All buffers are device memory in
+ * the ciphertext layout [n][2][level+1][N] unless stated; the library never
+ * frees caller buffers. */
+
+typedef struct fe_boot fe_boot;
+/* n_cts / n_stc: stage groups of CoeffToSlot / SlotToCoeff (1..log2(N/2));
+ * r: double angles (1..16); top: level after ModRaise (0: L).  The refresh
+ * needs n_cts + 5 + r + n_stc <= top and returns at level top - that depth. */
+typedef struct {
+    uint32_t n_cts, n_stc, r, top;
+} fe_boot_params;
+
+/* Sparse ternary secret of Hamming weight h (h distinct positions with signs
+ * +-1, by a partial Fisher-Yates shuffle on the generator's words of tag
+ * kind 6), written like fe_sk_gen's ([n_mod][N], NTT form).  A refresh needs a
+ * sparse secret so that the multiples of q_0 that ModRaise adds stay small
+ * (|I| <= (h + 1) / 2).  Errors: FE_EINVAL (h = 0 or h > N). */
+int fe_sk_gen_sparse(fe_ctx* ctx, uint64_t seed, uint32_t h, void* sk_dev, void* stream);
+/* Complex conjugation of the slots of n_ct ciphertexts (automorphism X -> X^(2N-1)
+ * with its key switch, Eq. 1's form); the evk must hold the step FE_STEP_CONJ.
+ * Errors: FE_EKEY. */
+int fe_conjugate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                 void* out_dev, void* stream);
+/* ModRaise: n_ct level-0 ciphertexts, read as centred integers mod q_0, reduced
+ * modulo q_0..q_top (out: level `top`).  The result decrypts to m + q_0 I.
+ * Errors: FE_ELEVEL (top > L). */
+int fe_mod_raise(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t top, void* out_dev, void* stream);
+
+/* Plaintext-matrix product by the diagonal method with baby / giant steps (the
+ * linear transforms of the refresh; any real slot-linear map):
+ *   out[o] = rescale( sum over diagonals (o, i, r) of d ⊙ Rot(in[i], r) ),
+ * d the diagonal's slot vector, Rot(v, r)[l] = v[l + r].  Offsets are split as
+ * r = giant + baby: r_lo = min offset, delta = gcd of (r - r_lo) (1 if all are
+ * equal), j = (r - r_lo) / delta, baby = (j mod n1) delta, giant = r_lo +
+ * (j div n1) n1 delta; the baby rotations of each input share one ModUp, each
+ * (output, giant) sum is rotated once.  Diagonals: n_diag triples (diag_out,
+ * diag_in, diag_offset), offsets in (-N/2, N/2), no duplicates, every output
+ * with at least one diagonal; n1 = 0 picks the power of two at or above
+ * sqrt(#distinct offsets).  The plan runs through fe_plan_query,
+ * fe_plan_rotation_steps, fe_plan_workspace_bytes and fe_plan_destroy like
+ * the layer plans.  Errors: FE_EINVAL, FE_ELEVEL (level 0 or above L). */
+int fe_plan_lintrans(fe_ctx* ctx, uint32_t n_in, uint32_t n_out, uint32_t n_diag, const uint32_t* diag_out,
+                     const uint32_t* diag_in, const int32_t* diag_offset, uint32_t n1, uint32_t level,
+                     fe_plan** out);
+/* Encode the diagonals (values_host: [n_diag][N/2] doubles, in planning order)
+ * at w_scale on q_0..q_level into pt_dev (fe_plan_query's pt_bytes).  Output
+ * scale = input scale * w_scale / q_level.  Synchronises `stream`. */
+int fe_plan_lintrans_load(fe_ctx* ctx, fe_plan* plan, const double* values_host, double w_scale, void* pt_dev,
+                          void* stream);
+/* Run the product for n_req requests (inputs [n_req][n_in], outputs
+ * [n_req][n_out] at level - 1); ws: fe_plan_workspace_bytes(plan, n_req, 0). */
+int fe_he_lintrans(fe_ctx* ctx, const fe_evk* evk, const fe_plan* plan, const void* pt_dev, const void* in_dev,
+                   void* out_dev, uint32_t n_req, void* ws, size_t ws_bytes, void* stream);
+
+/* Build a refresh: every stage group's diagonals (twiddles cos / sin(pi e / N)
+ * rounded once from quad precision; 1/2 and pi / 2^r folded into the first
+ * CoeffToSlot group, q_0 / (2 pi scale_in) into the first SlotToCoeff group)
+ * encoded on device memory the object owns, and the -X^(N/2) factor of the
+ * imaginary part.  scale_in: the declared scale of the level-0 inputs (slot
+ * values |z| <= 1 want scale_in well below q_0, e.g. q_0 / 32).  Synchronises
+ * `stream`.  Errors: FE_EINVAL, FE_ELEVEL, FE_ENOMEM, FE_ECUDA. */
+int fe_boot_create(fe_ctx* ctx, const fe_boot_params* params, double scale_in, void* stream, fe_boot** out);
+/* Rotation steps the refresh needs (mod N/2, and FE_STEP_CONJ); *n receives the
+ * count, at most `max` are written.  The evk also needs the relinearisation key. */
+int fe_boot_rotation_steps(const fe_boot* boot, int32_t* steps, uint32_t max, uint32_t* n);
+/* Level and declared scale of the refresh's outputs. */
+int fe_boot_output(const fe_boot* boot, uint32_t* level, double* scale);
+size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
+/* Refresh n_ct level-0 ciphertexts (declared scale scale_in) into out_dev at
+ * fe_boot_output's level; the outputs decrypt to the inputs' slot values.
+ * ws: fe_boot_workspace_bytes(boot, n_ct).  Errors: FE_EKEY, FE_ENOMEM. */
+int fe_he_bootstrap(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
+                    void* out_dev, void* ws, size_t ws_bytes, void* stream);
+void fe_boot_destroy(fe_boot* boot);
 
 #ifdef __cplusplus
 }

@@ -24,9 +24,16 @@ u32, u64, i32, sz, vp, dbl = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, 
                               ctypes.c_void_p, ctypes.c_double)
 cint = ctypes.c_int
 
+# rotation-step value standing for the complex conjugation of the slots (Galois element 2N - 1)
+FE_STEP_CONJ = -(1 << 31)
+
 
 class FeParams(ctypes.Structure):
     _fields_ = [("logN", u32), ("n_q", u32), ("k", u32), ("qbits", u32), ("pbits", u32)]
+
+
+class FeBootParams(ctypes.Structure):
+    _fields_ = [("n_cts", u32), ("n_stc", u32), ("r", u32), ("top", u32)]
 
 
 class FeLayout(ctypes.Structure):
@@ -191,6 +198,18 @@ SIGNATURES = {
     "fe_graph_launch_host": (cint, [vp, P(vp), P(vp), vp]),
     "fe_graph_set_host_output_level": (cint, [vp, u32]),
     "fe_graph_destroy": (None, [vp]),
+    "fe_sk_gen_sparse": (cint, [vp, u64, u32, vp, vp]),
+    "fe_conjugate": (cint, [vp, vp, vp, u32, u32, vp, vp]),
+    "fe_mod_raise": (cint, [vp, vp, u32, u32, vp, vp]),
+    "fe_plan_lintrans": (cint, [vp, u32, u32, u32, P(u32), P(u32), P(i32), u32, u32, P(vp)]),
+    "fe_plan_lintrans_load": (cint, [vp, vp, vp, dbl, vp, vp]),
+    "fe_he_lintrans": (cint, [vp, vp, vp, vp, vp, vp, u32, vp, sz, vp]),
+    "fe_boot_create": (cint, [vp, P(FeBootParams), dbl, vp, P(vp)]),
+    "fe_boot_rotation_steps": (cint, [vp, P(i32), u32, P(u32)]),
+    "fe_boot_output": (cint, [vp, P(u32), P(dbl)]),
+    "fe_boot_workspace_bytes": (sz, [vp, u32]),
+    "fe_he_bootstrap": (cint, [vp, vp, vp, vp, u32, vp, vp, sz, vp]),
+    "fe_boot_destroy": (None, [vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
     "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
 }
@@ -269,6 +288,29 @@ class Plan:
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.fe_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Boot:
+    """A ciphertext refresh built by Context.boot_create (fe_boot_create)."""
+
+    def __init__(self, ctx, handle, scale_in):
+        self.ctx, self.handle, self.scale_in = ctx, handle, scale_in
+        n = u32()
+        check(load().fe_boot_rotation_steps(handle, None, 0, ctypes.byref(n)))
+        arr = (i32 * max(1, n.value))()
+        check(load().fe_boot_rotation_steps(handle, arr, n.value, ctypes.byref(n)))
+        self.steps = [arr[i] for i in range(n.value)]
+        lv, sc = u32(), dbl()
+        check(load().fe_boot_output(handle, ctypes.byref(lv), ctypes.byref(sc)))
+        self.out_level, self.out_scale = lv.value, sc.value
+
+    def workspace_bytes(self, n_ct=1):
+        return int(load().fe_boot_workspace_bytes(self.handle, n_ct))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fe_boot_destroy(self.handle)
             self.handle = None
 
 
@@ -361,6 +403,12 @@ class Context:
     def sk_gen(self, seed):
         sk = _torch().empty((self.n_mod, self.N), dtype=_torch().int64, device="cuda")
         check(load().fe_sk_gen(self.handle, seed, _ptr(sk), _stream()))
+        return sk
+
+    def sk_gen_sparse(self, seed, h):
+        """Sparse ternary secret of Hamming weight h (fe_sk_gen_sparse)."""
+        sk = _torch().empty((self.n_mod, self.N), dtype=_torch().int64, device="cuda")
+        check(load().fe_sk_gen_sparse(self.handle, seed, h, _ptr(sk), _stream()))
         return sk
 
     def evk_gen(self, sk, seed, steps, relin=False):
@@ -467,6 +515,67 @@ class Context:
     def rotate(self, evk, ct, level, r):
         out = self.empty_ct(ct.shape[0], level)
         check(load().fe_rotate(self.handle, evk.handle, _ptr(ct), ct.shape[0], level, r, _ptr(out), _stream()))
+        return out
+
+    def conjugate(self, evk, ct, level):
+        out = self.empty_ct(ct.shape[0], level)
+        check(load().fe_conjugate(self.handle, evk.handle, _ptr(ct), ct.shape[0], level, _ptr(out), _stream()))
+        return out
+
+    def mod_raise(self, ct, top):
+        out = self.empty_ct(ct.shape[0], top)
+        check(load().fe_mod_raise(self.handle, _ptr(ct), ct.shape[0], top, _ptr(out), _stream()))
+        return out
+
+    def plan_lintrans(self, diags, n_in, n_out, level, n1=0):
+        """Plaintext-matrix product over the diagonals [(out, in, offset), ...]
+        (fe_plan_lintrans); the values are loaded with lintrans_load in this order."""
+        d = np.asarray(diags, dtype=np.int64).reshape(-1, 3)
+        o = np.ascontiguousarray(d[:, 0], dtype=np.uint32)
+        i = np.ascontiguousarray(d[:, 1], dtype=np.uint32)
+        r = np.ascontiguousarray(d[:, 2], dtype=np.int32)
+        h = vp()
+        check(load().fe_plan_lintrans(self.handle, n_in, n_out, len(d), o.ctypes.data_as(P(u32)),
+                                      i.ctypes.data_as(P(u32)), r.ctypes.data_as(P_i32), n1, level, ctypes.byref(h)))
+        p = Plan(self, h)
+        p.level = level
+        return p
+
+    def lintrans_load(self, plan, values, w_scale=None):
+        torch = _torch()
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        w_scale = float(self.moduli[plan.level]) if w_scale is None else w_scale
+        pt = torch.empty(max(8, plan.info.pt_bytes) // 8, dtype=torch.int64, device="cuda")
+        check(load().fe_plan_lintrans_load(self.handle, plan.handle, v.ctypes.data_as(vp), w_scale, _ptr(pt),
+                                           _stream()))
+        return pt
+
+    def he_lintrans(self, evk, plan, pt, ct, n_req=1, ws=None, out=None):
+        ws = self.workspace(self.workspace_bytes(plan, n_req)) if ws is None else ws
+        out = self.empty_ct(n_req * plan.info.n_out_ct, plan.level - 1) if out is None else out
+        self._check_layer_buffers(plan, pt, ct, out, n_req)
+        check(load().fe_he_lintrans(self.handle, evk.handle, plan.handle, _ptr(pt), _ptr(ct), _ptr(out), n_req,
+                                    _ptr(ws), ws.numel() * 8, _stream()))
+        return out
+
+    def boot_create(self, scale_in, n_cts=3, n_stc=3, r=6, top=0):
+        """A ciphertext refresh (fe_boot_create) for level-0 inputs at scale_in."""
+        prm = FeBootParams(n_cts, n_stc, r, top)
+        h = vp()
+        check(load().fe_boot_create(self.handle, ctypes.byref(prm), scale_in, _stream(), ctypes.byref(h)))
+        return Boot(self, h, scale_in)
+
+    def bootstrap(self, evk, boot, ct, ws=None, out=None):
+        """Refresh level-0 ciphertexts; returns them at boot.out_level (scale boot.out_scale)."""
+        n = ct.shape[0]
+        if ct.numel() != n * self.ct_words(0):
+            raise ValueError("the refresh takes level-0 ciphertexts")
+        ws = self.workspace(boot.workspace_bytes(n)) if ws is None else ws
+        out = self.empty_ct(n, boot.out_level) if out is None else out
+        if out.numel() != n * self.ct_words(boot.out_level):
+            raise ValueError("output buffer does not match the refresh's output level")
+        check(load().fe_he_bootstrap(self.handle, evk.handle, boot.handle, _ptr(ct), n, _ptr(out), _ptr(ws),
+                                     ws.numel() * 8, _stream()))
         return out
 
     def rescale(self, ct, level):

@@ -860,7 +860,7 @@ extern "C" int fe_fragment_unpack(const fe_ctx* c, const fe_layout* lay, const d
     return FE_OK;
 }
 
-static void finish_plan(fe_plan* p) {
+void fe::finish_plan(fe_plan* p) {
     std::set<int32_t> st;
     for (auto& in : p->inner) st.insert(in.step);
     p->n_outer = 0;

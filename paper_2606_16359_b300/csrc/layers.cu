@@ -69,13 +69,6 @@ bool carve_ks(Carver& cv, const fe_ctx* c, int n, int level, KsScratch* s) {
     return cv.ok;
 }
 
-// Per-limb constants of an affine map of ciphertexts (polynomial activation).
-constexpr int kMaxAffineLimbs = 64;
-struct AffineConsts {
-    u64 mul[kMaxAffineLimbs];  // factor per limb (both polynomials)
-    u64 add[kMaxAffineLimbs];  // constant per limb (c0 only: a constant message term)
-};
-
 // out = in * mul_i (+ add_i on c0), limb i of each of n ciphertexts [2][nl][N]
 __global__ void k_affine(const u64* in, u64* out, const Modulus* mods, AffineConsts k, int nl, int logN,
                          int do_mul) {
@@ -91,6 +84,8 @@ __global__ void k_affine(const u64* in, u64* out, const Modulus* mods, AffineCon
     if (limb < nl) v = add_mod(v, k.add[i], m.q);
     out[o] = v;
 }
+
+}  // namespace
 
 // the integer nearest to x, ties away from zero, reduced mod q (any finite x)
 u64 nearest_mod(double x, u64 q) {
@@ -119,8 +114,6 @@ int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const Af
     c->cnt.launches++;
     return FE_OK;
 }
-
-}  // namespace
 
 // d = relin(x (x) y) on Q_level for n pairs of ciphertexts, no rescale (CMult + relinearisation)
 int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,

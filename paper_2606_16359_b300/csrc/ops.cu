@@ -234,7 +234,8 @@ extern "C" int fe_evk_gen(fe_ctx* c, const void* sk_dev, uint64_t seed, const in
     const int N = c->N, nm = c->n_mod;
     std::set<uint32_t> seen;
     for (uint32_t i = 0; i < n_steps; i++) {
-        if (steps[i] % (N / 2) == 0) return fail(FE_EINVAL, "rotation step is a multiple of N/2");
+        if (steps[i] != FE_STEP_CONJ && steps[i] % (N / 2) == 0)
+            return fail(FE_EINVAL, "rotation step is a multiple of N/2");
         if (!seen.insert(c->galois(steps[i])).second) return fail(FE_EINVAL, "duplicate rotation step");
     }
     std::unique_ptr<fe_evk> h(new fe_evk());
@@ -305,7 +306,8 @@ extern "C" int fe_evk_upload(fe_ctx* c, const void* evk_host, size_t evk_host_by
     const int N = c->N;
     std::set<uint32_t> seen;
     for (uint32_t i = 0; i < n_steps; i++) {
-        if (steps[i] % (N / 2) == 0) return fail(FE_EINVAL, "rotation step is a multiple of N/2");
+        if (steps[i] != FE_STEP_CONJ && steps[i] % (N / 2) == 0)
+            return fail(FE_EINVAL, "rotation step is a multiple of N/2");
         if (!seen.insert(c->galois(steps[i])).second) return fail(FE_EINVAL, "duplicate rotation step");
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -334,7 +336,7 @@ extern "C" int fe_evk_alias(fe_ctx* c, fe_evk* evk, const int32_t* steps, uint32
     if (pool.empty()) return fail(FE_EKEY, "fe_evk_alias needs at least one generated key");
     uint32_t added = 0;
     for (uint32_t i = 0; i < n_steps; i++) {
-        if (steps[i] % (c->N / 2) == 0) continue;
+        if (steps[i] != FE_STEP_CONJ && steps[i] % (c->N / 2) == 0) continue;
         const uint32_t g = c->galois(steps[i]);
         if (evk->rot.count(g)) continue;
         evk->rot[g] = pool[added % pool.size()];
@@ -455,7 +457,7 @@ extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint3
     const int N = c->N;
     const u64* in = (const u64*)ct_dev;
     u64* out = (u64*)out_dev;
-    if (r % (N / 2) == 0) {
+    if (r != FE_STEP_CONJ && r % (N / 2) == 0) {
         FE_CUDA_TRY(cudaMemcpyAsync(out, in, n_ct * ct_words(c, level) * 8, cudaMemcpyDeviceToDevice, st));
         return FE_OK;
     }

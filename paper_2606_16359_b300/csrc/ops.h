@@ -46,6 +46,19 @@ int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n,
                 cudaStream_t st);
 size_t cmult_relin_bytes(const fe_ctx* c, int n, int level);
 
+// Per-limb constants of an affine map of ciphertexts (polynomial activation,
+// integer products and constants of the bootstrapping's EvalMod).
+constexpr int kMaxAffineLimbs = 64;
+struct AffineConsts {
+    u64 mul[kMaxAffineLimbs];  // factor per limb (both polynomials)
+    u64 add[kMaxAffineLimbs];  // constant per limb (c0 only: a constant message term)
+};
+// out = in * mul_i (+ add_i on c0) for n ciphertexts at `level` (do_mul false: add only)
+int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const AffineConsts& k, bool do_mul,
+                  cudaStream_t st);
+// the integer nearest to x, ties away from zero, reduced mod q (any finite x)
+u64 nearest_mod(double x, u64 q);
+
 // upload a host vector into a device region carved from a workspace
 template <class T>
 int upload(const std::vector<T>& v, T* dst, cudaStream_t st) {

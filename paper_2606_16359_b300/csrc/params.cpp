@@ -129,6 +129,7 @@ static u64 bitrev(u64 x, int bits) {
 using namespace fe;
 
 uint32_t fe_ctx::galois(int32_t r) const {
+    if (r == FE_STEP_CONJ) return (uint32_t)(2 * N - 1);  // sigma_{-1}: complex conjugation of the slots
     int64_t half = N / 2;
     int64_t rr = ((int64_t)r % half + half) % half;
     return (uint32_t)h_powmod(5, (u64)rr, (u64)2 * N);

@@ -54,11 +54,18 @@ struct fe_plan {
     int repack = 0;      // 1: an FC-kind plan whose weights are the permutation from lin to lout
     std::vector<int> rowmap;  // FC-kind: output neuron -> row of the caller's weight matrix (-1: none)
     int w_rows = 0;           // rows of the caller's weight matrix when rowmap is used
+    // FC-kind plaintext-matrix product given by its diagonals (fe_plan_lintrans):
+    // plaintext k is diagonal lt_src[k].first rotated by -lt_src[k].second
+    int lintrans = 0;
+    std::vector<std::pair<int, int32_t>> lt_src;
+    size_t lt_ndiag = 0;
 };
 
 namespace fe {
 int layout_fill(int N, fe_layout* l);
 size_t plan_workspace(const fe_plan* p, size_t chunk, size_t n_req = 1);
+// fills steps, n_outer, modup_cts and modup_slot from inner / outs
+void finish_plan(fe_plan* p);
 size_t plan_data_bytes(const fe_plan* p, size_t chunk, size_t n_req);
 size_t plan_table_bytes(const fe_plan* p, size_t chunk, size_t n_req);
 size_t plan_chunk(const fe_plan* p, size_t n_req, int mode, size_t data_bytes, bool data_only);

@@ -1,0 +1,155 @@
+"""GPU parity of the ciphertext refresh (bootstrapping; Sec. 5, Evaluation
+Methodology) against the oracle (oracle/boot.py): the sparse secret, the
+conjugation, ModRaise and the plaintext-matrix product bit for bit, the whole
+refresh bit for bit at N = 2^10, and a full-size refresh (N = 2^16, 24 primes of
+50 bits) checked by decryption against the message."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_16359_b300 as fe  # noqa: E402
+from oracle import boot, ckks  # noqa: E402
+
+
+def u64(t):
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def oracle_ct(pr, ct):
+    return np.stack([ct.c0, ct.c1])
+
+
+def to_gpu(cts):
+    a = np.stack([oracle_ct(None, c) for c in cts]).view(np.int64)
+    return torch.from_numpy(a.copy()).cuda()
+
+
+@pytest.fixture(scope="module")
+def small():
+    """N = 2^10, 20 primes of 50 bits and 4 special primes, secret weight 32."""
+    logN, n_q, k, bits, h = 10, 20, 4, 50, 32
+    pr = ckks.Params(logN, n_q, k, bits)
+    bp = boot.BootParams(pr, 3, 3, 6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(logN, n_q, k, bits)
+        assert ctx.moduli == pr.moduli
+        sk = ctx.sk_gen_sparse(11, h)
+        torch.cuda.synchronize()
+    keys = boot.SparseKeySet(pr, 11, h, rot_steps=boot.boot_rotation_steps(pr, bp), relin=True, conj=True)
+    return pr, bp, ctx, sk, keys, s
+
+
+def test_sparse_secret_equals_the_oracle(small):
+    pr, bp, ctx, sk, keys, s = small
+    assert np.array_equal(u64(sk), keys.sk.ntt)
+    assert np.count_nonzero(keys.sk.coef) == 32
+
+
+def test_mod_raise_and_conjugation_bit_exact(small):
+    pr, bp, ctx, sk, keys, s = small
+    rng = np.random.default_rng(1)
+    z = rng.uniform(-1, 1, (2, pr.N // 2))
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], 0, 2.0 ** 45), 3, i) for i in range(2)]
+    with torch.cuda.stream(s):
+        evk = ctx.evk_gen(sk, 11, [fe.FE_STEP_CONJ], relin=False)
+        raised = ctx.mod_raise(to_gpu(octs), 9)
+        cj = ctx.conjugate(evk, raised, 9)
+        torch.cuda.synchronize()
+    want_r = [boot.mod_raise(pr, c, 9) for c in octs]
+    assert np.array_equal(u64(raised), np.stack([oracle_ct(pr, c) for c in want_r]))
+    want_c = [boot.conjugate(pr, keys, c) for c in want_r]
+    assert np.array_equal(u64(cj), np.stack([oracle_ct(pr, c) for c in want_c]))
+
+
+def test_plaintext_matrix_product_bit_exact(small):
+    """Two inputs, two outputs, negative and positive offsets, a giant step of 0."""
+    pr, bp, ctx, sk, keys, s = small
+    n = pr.N // 2
+    rng = np.random.default_rng(2)
+    diags = {}
+    for (o, i) in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        for r in (-12, -4, 0, 4, 8, 20):
+            if (o + i + r) % 3:
+                diags[(o, i, r)] = rng.uniform(-1, 1, n)
+    n1, lv = 2, 7
+    steps = boot.lintrans_steps(diags, n, n1)
+    for st in steps:
+        keys.add_rotation(st)
+    zs = rng.uniform(-1, 1, (3, 2, n))
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, zs[q][i], lv, 2.0 ** 40), 5, 2 * q + i)
+            for q in range(3) for i in range(2)]
+    order = list(diags)
+    with torch.cuda.stream(s):
+        evk = ctx.evk_gen(sk, 11, steps, relin=False)
+        plan = ctx.plan_lintrans(order, 2, 2, lv, n1=n1)
+        assert sorted(x % n for x in plan.steps) == steps
+        pt = ctx.lintrans_load(plan, np.stack([diags[k] for k in order]))
+        got = u64(ctx.he_lintrans(evk, plan, pt, to_gpu(octs), n_req=3))
+        torch.cuda.synchronize()
+    for q in range(3):
+        want = boot.he_lintrans(pr, keys, octs[2 * q:2 * q + 2], diags, 2, n1)
+        assert np.array_equal(got[2 * q:2 * q + 2], np.stack([oracle_ct(pr, c) for c in want])), q
+
+
+def test_refresh_bit_exact_against_the_oracle(small):
+    """Two level-0 ciphertexts refreshed in one call equal the oracle's refresh of
+    each, residue for residue, and decrypt to the messages."""
+    pr, bp, ctx, sk, keys, s = small
+    s_in = 2.0 ** 45
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-1, 1, (2, pr.N // 2))
+    octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], 0, s_in), 7, i) for i in range(2)]
+    with torch.cuda.stream(s):
+        b = ctx.boot_create(s_in, 3, 3, 6)
+        assert sorted(x for x in b.steps if x != fe.FE_STEP_CONJ) == boot.boot_rotation_steps(pr, bp)
+        assert fe.FE_STEP_CONJ in b.steps
+        evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
+        out = ctx.bootstrap(evk, b, to_gpu(octs))
+        got = u64(out)
+        dec = ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy()
+        torch.cuda.synchronize()
+    assert b.out_level == pr.L - bp.depth
+    for i in range(2):
+        want = boot.bootstrap(pr, keys, octs[i], bp)
+        assert want.scale == b.out_scale and want.level == b.out_level
+        assert np.array_equal(got[i], oracle_ct(pr, want)), i
+    assert np.abs(dec - z).max() < 1e-4
+
+
+def test_refresh_full_size():
+    """N = 2^16 with 24 primes of 50 bits and 4 special primes, secret weight 64:
+    the refresh returns at level 23 - 17 = 6 with every slot within 1e-3 of the
+    message (decrypted on the GPU), and its time is reported."""
+    logN, n_q, k, bits = 16, 24, 4, 50
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(logN, n_q, k, bits)
+        sk = ctx.sk_gen_sparse(21, 64)
+        s_in = 2.0 ** 45
+        b = ctx.boot_create(s_in, 3, 3, 6)
+        evk = ctx.evk_gen(sk, 21, b.steps, relin=True)
+        rng = np.random.default_rng(4)
+        z = rng.uniform(-1, 1, (1, ctx.N // 2))
+        ct = ctx.encrypt(sk, z, 0, s_in, seed=5)
+        ws = ctx.workspace(b.workspace_bytes(1))
+        out = ctx.bootstrap(evk, b, ct, ws=ws)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        for _ in range(3):
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        t1.record(s)
+        torch.cuda.synchronize()
+        dec = ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy()
+    assert b.out_level == 6
+    err = float(np.abs(dec - z).max())
+    print(f"refresh N=2^16: {t0.elapsed_time(t1) / 3:.2f} ms, max error {err:.2e}")
+    assert err < 1e-3
