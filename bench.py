@@ -300,6 +300,43 @@ def cpu_oracle_all_cores(n_rot_each, max_workers=64):
     return n / dt, dt, workers, cores, model
 
 
+def refresh_bench(torch, stream, steps):
+    """Time fe_he_bootstrap at N = 2^16 (24 x 50-bit primes, 4 special primes,
+    secret weight 64; CoeffToSlot 3 levels, EvalMod 11, SlotToCoeff 3) on one
+    level-0 ciphertext; report ms, levels, key switches and the decrypted error."""
+    import paper_2606_16359_b300 as fe
+    with torch.cuda.stream(stream):
+        ctx = fe.Context(16, 24, 4, 50)
+        sk = ctx.sk_gen_sparse(31, 64)
+        s_in = 2.0 ** 45
+        b = ctx.boot_create(s_in, 3, 3, 6)
+        evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
+        z = np.random.default_rng(9).uniform(-1, 1, (1, ctx.N // 2))
+        ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
+        ws = ctx.workspace(b.workspace_bytes(1))
+        out = ctx.bootstrap(evk, b, ct, ws=ws)
+        for _ in range(2):
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        torch.cuda.synchronize()
+        ctx.reset_counters()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        e.record(stream)
+        torch.cuda.synchronize()
+        cnt = ctx.counters()
+        ms = a.elapsed_time(e) / steps
+        err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
+    ks = cnt["keyswitch"] / steps
+    res = {"ms": round(ms, 3), "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64",
+           "levels_used": 23 - b.out_level, "out_level": b.out_level, "keyswitches": ks,
+           "keyswitch_per_s": ks / (ms / 1e3), "max_abs_err": err,
+           "evk_gb": evk.buf.numel() * 8 / 1e9, "workspace_gb": ws.numel() * 8 / 1e9}
+    del out, ws, ct, evk, b, sk, ctx
+    return res
+
+
 def run_reference(args):
     dist, rank, world, local = dist_setup(args)
     if rank != 0:
@@ -348,6 +385,8 @@ def main():
                     help="outer rotations of the pointwise layers: tuned (autotuner), linear, or n1")
     ap.add_argument("--variants", type=int, default=1,
                     help="also time the one-graph form and 4 and 16 inputs per block (context fields)")
+    ap.add_argument("--no-refresh", dest="refresh", action="store_false",
+                    help="skip the ciphertext-refresh (bootstrapping) measurement")
     ap.add_argument("--ncu-step", action="store_true",
                     help="set up, run one warm step, then one batched step between cudaProfilerStart and "
                          "cudaProfilerStop (for ncu --profile-from-start off), and exit")
@@ -645,6 +684,15 @@ def run_ours(args, dist, rank, world, local):
             gc.collect()
             torch.cuda.empty_cache()
 
+    # ---- the ciphertext refresh between blocks (bootstrapping), on its own
+    # parameter set: N = 2^16, 24 primes of 50 bits, sparse secret of weight 64 ----
+    refresh = None
+    if args.refresh:
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+        refresh = refresh_bench(torch, stream, max(3, min(args.steps, 10)))
+
     cpu = None
     if rank == 0 and args.cpu_rotations > 0:
         v1, dt1 = cpu_oracle_keyswitch(args.cpu_rotations)
@@ -664,7 +712,7 @@ def run_ours(args, dist, rank, world, local):
             "metric": METRIC, "value": value, "unit": "keyswitch/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": dict(config, variants=variants),
+            "config": dict(config, variants=variants, refresh=refresh),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "keyswitch/s", "h2d_bytes_per_step": h2d,

@@ -14,4 +14,5 @@ Modules:
   counts               rotation-complexity model (Eq. 3 - Eq. 8)
   plain                FP64 plaintext network (Eq. 2 and the layers around it)
   henn                 encrypted conv / activation / pool / FC / AAC
+  boot                 the ciphertext refresh (bootstrapping) between blocks
 """

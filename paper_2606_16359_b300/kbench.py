@@ -8,12 +8,17 @@
     python -m paper_2606_16359_b300.kbench aac [--reps 5]
     python -m paper_2606_16359_b300.kbench configs [--reps 5]
     python -m paper_2606_16359_b300.kbench repack
+    python -m paper_2606_16359_b300.kbench refresh [--reps 5]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
      write each word once), butterflies (N / 2) log2 N per limb.
 alu: the integer-pipe roof of the transform's butterfly arithmetic, from a
      register-resident probe of the same lazy Shoup butterflies.
+refresh: one ciphertext refresh (bootstrapping) at N = 2^16 with 24 + 4 primes of
+     50 bits and a secret of weight 64, timed over --reps refreshes; the last
+     refresh is bracketed by two one-block butterfly-probe launches, markers for
+     a profiler's launch list.
 keyswitch: rotations (hybrid key switch + automorphism) of n ciphertexts at one
      level with one key; algorithmic bytes per key switch without key reuse
      [(l+1) + 2 dnum (l+1+k) + 2 (l+1)] N w.
@@ -324,9 +329,44 @@ def bench_configs(ctx_unused, torch, args):
     return out
 
 
+def bench_refresh(ctx_unused, torch, args):
+    import numpy as np
+
+    import paper_2606_16359_b300 as fe
+    ctx = fe.Context(16, 24, 4, 50)
+    sk = ctx.sk_gen_sparse(31, 64)
+    s_in = 2.0 ** 45
+    b = ctx.boot_create(s_in, 3, 3, 6)
+    evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
+    z = np.random.default_rng(9).uniform(-1, 1, (1, ctx.N // 2))
+    ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
+    ws = ctx.workspace(b.workspace_bytes(1))
+    out = ctx.bootstrap(evk, b, ct, ws=ws)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, e = _events(torch)
+    a.record(st)
+    for _ in range(args.reps):
+        ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+    e.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / args.reps
+    probe = torch.empty(256, dtype=torch.int64, device="cuda")
+    ctx.probe_butterflies(probe, 1, 1)
+    ctx.reset_counters()
+    ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+    cnt = ctx.counters()
+    ctx.probe_butterflies(probe, 1, 1)
+    torch.cuda.synchronize()
+    err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
+    return {"what": "refresh", "ms": ms, "reps": args.reps, "out_level": b.out_level, "max_abs_err": err,
+            "counters_per_refresh": cnt}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs", "repack"])
+    ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs", "repack",
+                                     "refresh"])
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
@@ -351,7 +391,7 @@ def main(argv=None):
         ctx = fe.Context(args.logN, 24, 4, 36, 36)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
               "layer": bench_layer, "aac": bench_aac, "configs": bench_configs,
-              "repack": bench_repack}[args.what]
+              "repack": bench_repack, "refresh": bench_refresh}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 
