@@ -860,10 +860,14 @@ int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* by
 
 typedef struct fe_boot fe_boot;
 /* n_cts / n_stc: stage groups of CoeffToSlot / SlotToCoeff (1..log2(N/2));
- * r: double angles (1..16); top: level after ModRaise (0: L).  The refresh
- * needs n_cts + 5 + r + n_stc <= top and returns at level top - that depth. */
+ * r: double angles (1..16); top: level after ModRaise (0: L); baby_ratio: every
+ * group takes n1 baby steps, the smallest power of two with n1^2 >= baby_ratio
+ * x its number of diagonal offsets (0 or 1: about the square root; larger
+ * values trade giant-step rotations, each with its own ModUp, for hoisted
+ * baby steps).  The refresh needs n_cts + 5 + r + n_stc <= top and returns at
+ * level top - that depth. */
 typedef struct {
-    uint32_t n_cts, n_stc, r, top;
+    uint32_t n_cts, n_stc, r, top, baby_ratio;
 } fe_boot_params;
 
 /* Sparse ternary secret of Hamming weight h (h distinct positions with signs

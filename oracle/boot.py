@@ -335,10 +335,12 @@ def bsgs_decompose(offsets, n1):
     return dec
 
 
-def default_n1(n_offsets):
-    """Baby steps: the power of two nearest above sqrt(number of offsets)."""
+def default_n1(n_offsets, baby_ratio=1):
+    """Baby steps: the smallest power of two n1 with n1^2 >= baby_ratio times the
+    number of offsets (baby_ratio > 1 trades giant-step rotations, each with
+    its own ModUp, for hoisted baby-step rotations)."""
     n1 = 1
-    while n1 * n1 < n_offsets:
+    while n1 * n1 < baby_ratio * n_offsets:
         n1 *= 2
     return n1
 
@@ -471,9 +473,11 @@ def eval_mod_plain(y, r):
 
 class BootParams:
     """n_cts / n_stc: stage groups (levels) of CoeffToSlot / SlotToCoeff;
-    r: double angles; top: level after ModRaise (default L)."""
+    r: double angles; top: level after ModRaise (default L); baby_ratio: the
+    baby-step rule of every group (default_n1)."""
 
-    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None):
+    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=1):
+        self.baby_ratio = baby_ratio
         self.N = pr.N
         self.k = (pr.N // 2).bit_length() - 1
         self.n_cts, self.n_stc, self.r = n_cts, n_stc, r
@@ -518,7 +522,7 @@ def boot_rotation_steps(pr, bp):
     for groups in (bp.cts_groups, bp.stc_groups):
         for grp in groups:
             offs = group_offsets(grp, n)
-            dec = bsgs_decompose(offs, default_n1(len(offs)))
+            dec = bsgs_decompose(offs, default_n1(len(offs), bp.baby_ratio))
             steps |= {v % n for g, b in dec.values() for v in (g, b)}
     return sorted(steps - {0})
 
@@ -537,7 +541,7 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None):
         trace["parts"] = (re, im)
     pair = [re, im]
     for d in cts_diagonals(pr, bp, tab):
-        pair = he_lintrans(pr, keys, pair, d, 2, default_n1(len({k[2] for k in d})))
+        pair = he_lintrans(pr, keys, pair, d, 2, default_n1(len({k[2] for k in d}), bp.baby_ratio))
     if trace is not None:
         trace["cts"] = pair
     pair = [eval_mod(pr, keys, c, bp.r) for c in pair]
@@ -545,5 +549,6 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None):
         trace["evalmod"] = pair
     sds = stc_diagonals(pr, bp, tab, scale_in)
     for gi, d in enumerate(sds):
-        pair = he_lintrans(pr, keys, pair, d, 1 if gi == len(sds) - 1 else 2, default_n1(len({k[2] for k in d})))
+        pair = he_lintrans(pr, keys, pair, d, 1 if gi == len(sds) - 1 else 2,
+                           default_n1(len({k[2] for k in d}), bp.baby_ratio))
     return pair[0]

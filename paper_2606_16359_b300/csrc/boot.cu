@@ -383,9 +383,10 @@ std::vector<int32_t> group_offsets(const std::vector<int>& stages, int n) {
     return std::vector<int32_t>(out.begin(), out.end());
 }
 
-int default_n1(size_t n_offsets) {
+// baby steps: the smallest power of two n1 with n1^2 >= ratio x the number of offsets
+int default_n1(size_t n_offsets, uint32_t ratio = 1) {
     int n1 = 1;
-    while ((size_t)n1 * n1 < n_offsets) n1 *= 2;
+    while ((size_t)n1 * n1 < (size_t)std::max<uint32_t>(1, ratio) * n_offsets) n1 *= 2;
     return n1;
 }
 
@@ -761,7 +762,8 @@ extern "C" int fe_boot_create(fe_ctx* c, const fe_boot_params* prm, double scale
         group_diagonals(N, tr, stages, inverse, kappa, parts, d, vals);
         std::unique_ptr<fe_plan> p;
         std::vector<std::pair<int, int32_t>> src;
-        FE_TRY(plan_lintrans(c, 2, parts, d, default_n1(group_offsets(stages, n).size()), level, p, src));
+        FE_TRY(plan_lintrans(c, 2, parts, d, default_n1(group_offsets(stages, n).size(), prm->baby_ratio), level, p,
+                             src));
         for (int32_t s : p->steps) steps.insert(((s % n) + n) % n);
         std::vector<const double*> vp(vals.size());
         for (size_t i = 0; i < vals.size(); i++) vp[i] = vals[i].data();

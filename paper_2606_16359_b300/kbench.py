@@ -336,12 +336,14 @@ def bench_refresh(ctx_unused, torch, args):
     ctx = fe.Context(16, 24, 4, 50)
     sk = ctx.sk_gen_sparse(31, 64)
     s_in = 2.0 ** 45
-    b = ctx.boot_create(s_in, 3, 3, 6)
+    b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=args.baby_ratio)
     evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
     z = np.random.default_rng(9).uniform(-1, 1, (1, ctx.N // 2))
     ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
     ws = ctx.workspace(b.workspace_bytes(1))
     out = ctx.bootstrap(evk, b, ct, ws=ws)
+    for _ in range(2):
+        ctx.bootstrap(evk, b, ct, ws=ws, out=out)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     a, e = _events(torch)
@@ -359,8 +361,9 @@ def bench_refresh(ctx_unused, torch, args):
     ctx.probe_butterflies(probe, 1, 1)
     torch.cuda.synchronize()
     err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
-    return {"what": "refresh", "ms": ms, "reps": args.reps, "out_level": b.out_level, "max_abs_err": err,
-            "counters_per_refresh": cnt}
+    return {"what": "refresh", "baby_ratio": args.baby_ratio, "ms": ms, "reps": args.reps,
+            "out_level": b.out_level, "max_abs_err": err, "rotation_keys": len(b.steps),
+            "evk_gb": evk.buf.numel() * 8 / 1e9, "counters_per_refresh": cnt}
 
 
 def main(argv=None):
@@ -380,6 +383,7 @@ def main(argv=None):
     ap.add_argument("--channels", type=int, default=128, help="channels of the layer case")
     ap.add_argument("--hw", type=int, default=14, help="map height = width of the layer case")
     ap.add_argument("--dw", action="store_true", help="layer case: depthwise 3x3 instead of pointwise")
+    ap.add_argument("--baby-ratio", type=int, default=1, help="refresh: baby-step rule of the stage groups")
     args = ap.parse_args(argv)
     import torch
 

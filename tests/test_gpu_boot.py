@@ -153,3 +153,23 @@ def test_refresh_full_size():
     err = float(np.abs(dec - z).max())
     print(f"refresh N=2^16: {t0.elapsed_time(t1) / 3:.2f} ms, max error {err:.2e}")
     assert err < 1e-3
+
+
+def test_refresh_with_more_baby_steps_bit_exact(small):
+    """baby_ratio = 2 (n1^2 >= 2 x the offsets of each group) changes every
+    group's baby / giant split; the residues still equal the oracle's."""
+    pr, bp, ctx, sk, keys, s = small
+    bp2 = boot.BootParams(pr, 3, 3, 6, baby_ratio=2)
+    for st in boot.boot_rotation_steps(pr, bp2):
+        keys.add_rotation(st)
+    s_in = 2.0 ** 45
+    z = np.random.default_rng(8).uniform(-1, 1, (1, pr.N // 2))
+    oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[0], 0, s_in), 9, 0)
+    with torch.cuda.stream(s):
+        b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=2)
+        assert sorted(x for x in b.steps if x != fe.FE_STEP_CONJ) == boot.boot_rotation_steps(pr, bp2)
+        evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
+        got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))
+        torch.cuda.synchronize()
+    want = boot.bootstrap(pr, keys, oct_, bp2)
+    assert np.array_equal(got[0], oracle_ct(pr, want))
