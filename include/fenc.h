@@ -864,10 +864,12 @@ typedef struct fe_boot fe_boot;
  * group takes n1 baby steps, the smallest power of two with n1^2 >= baby_ratio
  * x its number of diagonal offsets (0 or 1: about the square root; larger
  * values trade giant-step rotations, each with its own ModUp, for hoisted
- * baby steps).  The refresh needs n_cts + 5 + r + n_stc <= top and returns at
- * level top - that depth. */
+ * baby steps); double_hoist: 1 keeps every group's baby rotations on Q * P
+ * and takes one ModDown per (output, giant step) sum (fe_plan_set_hoisting 1),
+ * 0 a ModDown per rotation.  The refresh needs n_cts + 5 + r + n_stc <= top and
+ * returns at level top - that depth. */
 typedef struct {
-    uint32_t n_cts, n_stc, r, top, baby_ratio;
+    uint32_t n_cts, n_stc, r, top, baby_ratio, double_hoist;
 } fe_boot_params;
 
 /* Sparse ternary secret of Hamming weight h (h distinct positions with signs

@@ -350,13 +350,18 @@ def lintrans_steps(diags, n, n1):
     return sorted({v % n for g, b in dec.values() for v in (g, b)} - {0})
 
 
-def he_lintrans(pr, keys, cts, diags, n_out, n1, w_scale=None):
+def he_lintrans(pr, keys, cts, diags, n_out, n1, w_scale=None, hoist="single"):
     """out[o] = rescale(sum_{(o, i, r)} d ⊙ Rot(cts[i], r)) by baby / giant steps:
     for every giant step g, the sum over (i, b) of Rot(d, -g) ⊙ Rot(cts[i], b)
     (the baby rotations of each input hoisted, rotate_ext) is rotated by g (one
     rotation of the sum), the giant sums are added, and the result is rescaled
     once.  Plaintexts are encoded at w_scale (default q_level), so the declared
-    output scale equals the input scale."""
+    output scale equals the input scale.
+    hoist="double": the baby rotations stay on Q_level * P (rotate_ext_qp, the
+    unrotated inputs lifted by lift_qp), each (output, giant) sum is formed there
+    with the plaintexts on Q_level * P and takes one ModDown before its giant
+    rotation (the composition of henn.he_conv_bsgs with hoist="double")."""
+    double = hoist == "double"
     level = cts[0].level
     n = pr.N // 2
     ws = float(pr.moduli[level]) if w_scale is None else w_scale
@@ -367,11 +372,12 @@ def he_lintrans(pr, keys, cts, diags, n_out, n1, w_scale=None):
         ext = None
         for b in need:
             if b % n == 0:
-                baby[(i, b)] = ct
+                baby[(i, b)] = ckks.lift_qp(pr, ct) if double else ct
             else:
                 if ext is None:
                     ext = ckks.mod_up(pr, ct.c1, ct.level)
-                baby[(i, b)] = ckks.rotate_ext(pr, keys, ct, ext, b)
+                rot = ckks.rotate_ext_qp if double else ckks.rotate_ext
+                baby[(i, b)] = rot(pr, keys, ct, ext, b)
     out = []
     for o in range(n_out):
         groups = {}
@@ -379,12 +385,20 @@ def he_lintrans(pr, keys, cts, diags, n_out, n1, w_scale=None):
             if oo != o:
                 continue
             g, b = dec[r]
-            pt = ckks.encode(pr, np.roll(v, g), level, ws)  # pt[l] = v[(l - g) mod n]
-            term = ckks.pmult(pr, baby[(i, b)], pt)
-            groups[g] = term if g not in groups else ckks.add(pr, groups[g], term)
+            z = np.roll(v, g)  # pt[l] = v[(l - g) mod n]
+            if double:
+                groups.setdefault(g, []).append((baby[(i, b)], ckks.encode_qp(pr, z, level, ws)))
+            else:
+                term = ckks.pmult(pr, baby[(i, b)], ckks.encode(pr, z, level, ws))
+                groups[g] = term if g not in groups else ckks.add(pr, groups[g], term)
         total = None
         for g in sorted(groups):
-            acc = groups[g] if g % n == 0 else ckks.rotate(pr, keys, groups[g], g)
+            acc = groups[g]
+            if double:
+                ab, aa = ckks.mac_qp(pr, level, acc)
+                acc = ckks.mod_down_ct(pr, ab, aa, level, cts[0].scale * ws)
+            if g % n:
+                acc = ckks.rotate(pr, keys, acc, g)
             total = acc if total is None else ckks.add(pr, total, acc)
         r = ckks.rescale(pr, total)
         r.scale = cts[0].scale
@@ -474,10 +488,12 @@ def eval_mod_plain(y, r):
 class BootParams:
     """n_cts / n_stc: stage groups (levels) of CoeffToSlot / SlotToCoeff;
     r: double angles; top: level after ModRaise (default L); baby_ratio: the
-    baby-step rule of every group (default_n1)."""
+    baby-step rule of every group (default_n1); double_hoist: the groups'
+    products with hoist="double" (he_lintrans)."""
 
-    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=1):
+    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=4, double_hoist=True):
         self.baby_ratio = baby_ratio
+        self.hoist = "double" if double_hoist else "single"
         self.N = pr.N
         self.k = (pr.N // 2).bit_length() - 1
         self.n_cts, self.n_stc, self.r = n_cts, n_stc, r
@@ -541,7 +557,7 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None):
         trace["parts"] = (re, im)
     pair = [re, im]
     for d in cts_diagonals(pr, bp, tab):
-        pair = he_lintrans(pr, keys, pair, d, 2, default_n1(len({k[2] for k in d}), bp.baby_ratio))
+        pair = he_lintrans(pr, keys, pair, d, 2, default_n1(len({k[2] for k in d}), bp.baby_ratio), hoist=bp.hoist)
     if trace is not None:
         trace["cts"] = pair
     pair = [eval_mod(pr, keys, c, bp.r) for c in pair]
@@ -550,5 +566,5 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None):
     sds = stc_diagonals(pr, bp, tab, scale_in)
     for gi, d in enumerate(sds):
         pair = he_lintrans(pr, keys, pair, d, 1 if gi == len(sds) - 1 else 2,
-                           default_n1(len({k[2] for k in d}), bp.baby_ratio))
+                           default_n1(len({k[2] for k in d}), bp.baby_ratio), hoist=bp.hoist)
     return pair[0]

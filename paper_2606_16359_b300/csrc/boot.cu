@@ -264,10 +264,11 @@ int plan_lintrans(fe_ctx* c, int n_in, int n_out, const std::vector<LtDiag>& d, 
 }
 
 // plaintext k = diagonal pt_src[k].first rotated by -giant, encoded at w_scale
-// on q_0..q_level and stored compact at pt_dev
+// on q_0..q_level (and p_0..p_{k-1} when the plan is double-hoisted) and stored
+// compact at pt_dev
 int load_lintrans(fe_ctx* c, const fe_plan* p, const std::vector<std::pair<int, int32_t>>& pt_src,
                   const std::vector<const double*>& diag_vals, double w_scale, void* pt_dev, cudaStream_t st) {
-    const int N = c->N, n = N / 2, nl = p->level + 1;
+    const int N = c->N, n = N / 2, nl = p->level + 1 + (p->dhoist ? c->k : 0);
     const int chunk = std::max(1, std::min({p->n_pt, (int)((64ull << 20) / ((size_t)n * 8)),
                                             (int)((1ull << 30) / ((size_t)nl * N * 8))}));
     double* z;
@@ -285,7 +286,7 @@ int load_lintrans(fe_ctx* c, const fe_plan* p, const std::vector<std::pair<int, 
             for (int l = 0; l < n; l++) dst[l] = v[(((l - g) % n) + n) % n];  // Rot(d, -g)
         }
         FE_CUDA_TRY(cudaMemcpyAsync(z, host.data(), (size_t)cn * n * 8, cudaMemcpyHostToDevice, st));
-        rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, false);
+        rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, p->dhoist != 0);
         if (rc == FE_OK) launch_pt_compact(c, limbs, (uint8_t*)pt_dev + (size_t)s0 * nl * pt_limb_bytes(c), cn * nl, st);
         FE_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging buffer is refilled next
     }
@@ -765,10 +766,12 @@ extern "C" int fe_boot_create(fe_ctx* c, const fe_boot_params* prm, double scale
         FE_TRY(plan_lintrans(c, 2, parts, d, default_n1(group_offsets(stages, n).size(), prm->baby_ratio), level, p,
                              src));
         for (int32_t s : p->steps) steps.insert(((s % n) + n) % n);
+        p->dhoist = prm->double_hoist ? 1 : 0;
         std::vector<const double*> vp(vals.size());
         for (size_t i = 0; i < vals.size(); i++) vp[i] = vals[i].data();
+        const size_t nl = (size_t)level + 1 + (p->dhoist ? c->k : 0);
         u64* pt;
-        FE_CUDA_TRY(cudaMalloc(&pt, std::max<size_t>(16, (size_t)p->n_pt * (level + 1) * pt_limb_bytes(c))));
+        FE_CUDA_TRY(cudaMalloc(&pt, std::max<size_t>(16, (size_t)p->n_pt * nl * pt_limb_bytes(c))));
         b->pts.push_back(pt);
         FE_TRY(load_lintrans(c, p.get(), src, vp, (double)c->mod[level], pt, st));
         p->w_scale = (double)c->mod[level];

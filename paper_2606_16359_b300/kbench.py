@@ -336,7 +336,7 @@ def bench_refresh(ctx_unused, torch, args):
     ctx = fe.Context(16, 24, 4, 50)
     sk = ctx.sk_gen_sparse(31, 64)
     s_in = 2.0 ** 45
-    b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=args.baby_ratio)
+    b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=args.baby_ratio, double_hoist=args.double_hoist)
     evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
     z = np.random.default_rng(9).uniform(-1, 1, (1, ctx.N // 2))
     ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
@@ -361,7 +361,7 @@ def bench_refresh(ctx_unused, torch, args):
     ctx.probe_butterflies(probe, 1, 1)
     torch.cuda.synchronize()
     err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
-    return {"what": "refresh", "baby_ratio": args.baby_ratio, "ms": ms, "reps": args.reps,
+    return {"what": "refresh", "baby_ratio": args.baby_ratio, "double_hoist": args.double_hoist, "ms": ms, "reps": args.reps,
             "out_level": b.out_level, "max_abs_err": err, "rotation_keys": len(b.steps),
             "evk_gb": evk.buf.numel() * 8 / 1e9, "counters_per_refresh": cnt}
 
@@ -383,7 +383,8 @@ def main(argv=None):
     ap.add_argument("--channels", type=int, default=128, help="channels of the layer case")
     ap.add_argument("--hw", type=int, default=14, help="map height = width of the layer case")
     ap.add_argument("--dw", action="store_true", help="layer case: depthwise 3x3 instead of pointwise")
-    ap.add_argument("--baby-ratio", type=int, default=1, help="refresh: baby-step rule of the stage groups")
+    ap.add_argument("--baby-ratio", type=int, default=4, help="refresh: baby-step rule of the stage groups")
+    ap.add_argument("--double-hoist", type=int, default=1, help="refresh: 1 keeps the groups' baby rotations on Q P")
     args = ap.parse_args(argv)
     import torch
 

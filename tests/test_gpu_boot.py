@@ -36,7 +36,7 @@ def small():
     """N = 2^10, 20 primes of 50 bits and 4 special primes, secret weight 32."""
     logN, n_q, k, bits, h = 10, 20, 4, 50, 32
     pr = ckks.Params(logN, n_q, k, bits)
-    bp = boot.BootParams(pr, 3, 3, 6)
+    bp = boot.BootParams(pr, 3, 3, 6)  # default schedule: baby ratio 4, double hoisting
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = fe.Context(logN, n_q, k, bits)
@@ -155,18 +155,20 @@ def test_refresh_full_size():
     assert err < 1e-3
 
 
-def test_refresh_with_more_baby_steps_bit_exact(small):
-    """baby_ratio = 2 (n1^2 >= 2 x the offsets of each group) changes every
-    group's baby / giant split; the residues still equal the oracle's."""
+@pytest.mark.parametrize("ratio,double", [(1, False), (2, False)])
+def test_refresh_schedules_bit_exact(small, ratio, double):
+    """Other baby / giant splits (n1^2 >= ratio x the offsets of each group) and
+    double-hoisted groups change every group's composition; the residues still
+    equal the oracle's."""
     pr, bp, ctx, sk, keys, s = small
-    bp2 = boot.BootParams(pr, 3, 3, 6, baby_ratio=2)
+    bp2 = boot.BootParams(pr, 3, 3, 6, baby_ratio=ratio, double_hoist=double)
     for st in boot.boot_rotation_steps(pr, bp2):
         keys.add_rotation(st)
     s_in = 2.0 ** 45
     z = np.random.default_rng(8).uniform(-1, 1, (1, pr.N // 2))
     oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[0], 0, s_in), 9, 0)
     with torch.cuda.stream(s):
-        b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=2)
+        b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=ratio, double_hoist=double)
         assert sorted(x for x in b.steps if x != fe.FE_STEP_CONJ) == boot.boot_rotation_steps(pr, bp2)
         evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
         got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))

@@ -239,7 +239,8 @@ def test_conjugation_and_parts(small):
     assert np.abs(crt_slots(pr, keys.sk, im) - 2 * u.imag).max() < 1e-9
 
 
-def test_he_lintrans_matches_the_plain_product(small):
+@pytest.mark.parametrize("hoist", ["single", "double"])
+def test_he_lintrans_matches_the_plain_product(small, hoist):
     pr, bp, keys = small
     n = pr.N // 2
     rng = np.random.default_rng(4)
@@ -254,7 +255,7 @@ def test_he_lintrans_matches_the_plain_product(small):
     lv = 5
     zs = [rng.uniform(-1, 1, n) for _ in range(2)]
     cts = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, lv, 2.0 ** 40), 5, i) for i, z in enumerate(zs)]
-    out = boot.he_lintrans(pr, keys, cts, diags, 2, n1)
+    out = boot.he_lintrans(pr, keys, cts, diags, 2, n1, hoist=hoist)
     for o in range(2):
         want = sum(v * np.roll(zs[i], -r) for (oo, i, r), v in diags.items() if oo == o)
         got = ckks.decrypt(pr, keys.sk, out[o])
@@ -286,4 +287,18 @@ def test_bootstrap_refreshes_the_message(small):
     ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 7, 0)
     out = boot.bootstrap(pr, keys, ct, bp)
     assert out.level == bp.top - bp.depth == pr.L - 17
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
+
+
+def test_bootstrap_single_hoisted_refreshes_the_message(small):
+    """The refresh with square-root baby steps (ratio 1) and a ModDown per
+    rotation (single hoisting) also returns the message."""
+    pr, _, keys = small
+    bp = boot.BootParams(pr, 3, 3, 6, baby_ratio=1, double_hoist=False)
+    for st in boot.boot_rotation_steps(pr, bp):
+        keys.add_rotation(st)
+    z = np.random.default_rng(7).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 8, 0)
+    out = boot.bootstrap(pr, keys, ct, bp)
+    assert out.level == pr.L - 17
     assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
