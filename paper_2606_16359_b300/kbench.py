@@ -336,7 +336,8 @@ def bench_refresh(ctx_unused, torch, args):
     ctx = fe.Context(16, 24, 4, 50)
     sk = ctx.sk_gen_sparse(31, 64)
     s_in = 2.0 ** 45
-    b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=args.baby_ratio, double_hoist=args.double_hoist)
+    b = ctx.boot_create(s_in, args.n_cts, args.n_stc, args.double_angles, baby_ratio=args.baby_ratio,
+                        double_hoist=args.double_hoist)
     evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
     z = np.random.default_rng(9).uniform(-1, 1, (1, ctx.N // 2))
     ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
@@ -361,7 +362,8 @@ def bench_refresh(ctx_unused, torch, args):
     ctx.probe_butterflies(probe, 1, 1)
     torch.cuda.synchronize()
     err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
-    return {"what": "refresh", "baby_ratio": args.baby_ratio, "double_hoist": args.double_hoist, "ms": ms, "reps": args.reps,
+    return {"what": "refresh", "groups": [args.n_cts, args.n_stc], "double_angles": args.double_angles,
+            "levels_used": 23 - b.out_level, "baby_ratio": args.baby_ratio, "double_hoist": args.double_hoist, "ms": ms, "reps": args.reps,
             "out_level": b.out_level, "max_abs_err": err, "rotation_keys": len(b.steps),
             "evk_gb": evk.buf.numel() * 8 / 1e9, "counters_per_refresh": cnt}
 
@@ -385,6 +387,9 @@ def main(argv=None):
     ap.add_argument("--dw", action="store_true", help="layer case: depthwise 3x3 instead of pointwise")
     ap.add_argument("--baby-ratio", type=int, default=4, help="refresh: baby-step rule of the stage groups")
     ap.add_argument("--double-hoist", type=int, default=1, help="refresh: 1 keeps the groups' baby rotations on Q P")
+    ap.add_argument("--n-cts", type=int, default=3, help="refresh: CoeffToSlot stage groups (levels)")
+    ap.add_argument("--n-stc", type=int, default=3, help="refresh: SlotToCoeff stage groups (levels)")
+    ap.add_argument("--double-angles", type=int, default=6, help="refresh: EvalMod double angles")
     args = ap.parse_args(argv)
     import torch
 

@@ -155,23 +155,25 @@ def test_refresh_full_size():
     assert err < 1e-3
 
 
-@pytest.mark.parametrize("ratio,double", [(1, False), (2, False)])
-def test_refresh_schedules_bit_exact(small, ratio, double):
-    """Other baby / giant splits (n1^2 >= ratio x the offsets of each group) and
-    double-hoisted groups change every group's composition; the residues still
-    equal the oracle's."""
+@pytest.mark.parametrize("groups,r,ratio,double", [(3, 6, 1, False), (3, 6, 2, False), (2, 5, 4, True)])
+def test_refresh_schedules_bit_exact(small, groups, r, ratio, double):
+    """Other baby / giant splits (n1^2 >= ratio x the offsets of each group),
+    single-hoisted groups, and the 14-level refresh (two groups each way, five
+    double angles) change every group's composition; the residues still equal
+    the oracle's."""
     pr, bp, ctx, sk, keys, s = small
-    bp2 = boot.BootParams(pr, 3, 3, 6, baby_ratio=ratio, double_hoist=double)
+    bp2 = boot.BootParams(pr, groups, groups, r, baby_ratio=ratio, double_hoist=double)
     for st in boot.boot_rotation_steps(pr, bp2):
         keys.add_rotation(st)
     s_in = 2.0 ** 45
     z = np.random.default_rng(8).uniform(-1, 1, (1, pr.N // 2))
     oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[0], 0, s_in), 9, 0)
     with torch.cuda.stream(s):
-        b = ctx.boot_create(s_in, 3, 3, 6, baby_ratio=ratio, double_hoist=double)
+        b = ctx.boot_create(s_in, groups, groups, r, baby_ratio=ratio, double_hoist=double)
         assert sorted(x for x in b.steps if x != fe.FE_STEP_CONJ) == boot.boot_rotation_steps(pr, bp2)
         evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
         got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))
         torch.cuda.synchronize()
     want = boot.bootstrap(pr, keys, oct_, bp2)
+    assert b.out_level == want.level == pr.L - bp2.depth
     assert np.array_equal(got[0], oracle_ct(pr, want))

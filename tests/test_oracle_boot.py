@@ -302,3 +302,19 @@ def test_bootstrap_single_hoisted_refreshes_the_message(small):
     out = boot.bootstrap(pr, keys, ct, bp)
     assert out.level == pr.L - 17
     assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
+
+
+def test_bootstrap_in_fourteen_levels(small):
+    """Two CoeffToSlot groups, 5 + 5 EvalMod levels and two SlotToCoeff groups:
+    a refresh in 14 levels (the budget the paper's refresh spends) that still
+    returns the message at N = 2^8."""
+    pr, _, keys = small
+    bp = boot.BootParams(pr, 2, 2, 5)
+    assert bp.depth == 14
+    for st in boot.boot_rotation_steps(pr, bp):
+        keys.add_rotation(st)
+    z = np.random.default_rng(9).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 10, 0)
+    out = boot.bootstrap(pr, keys, ct, bp)
+    assert out.level == pr.L - 14
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
