@@ -883,6 +883,13 @@ int fe_sk_gen_sparse(fe_ctx* ctx, uint64_t seed, uint32_t h, void* sk_dev, void*
  * Errors: FE_EKEY. */
 int fe_conjugate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                  void* out_dev, void* stream);
+/* Level drop: n_ct ciphertexts at `level` modulo the smaller modulus
+ * Q_to_level = q_0 ... q_to_level (each polynomial keeps its first to_level + 1
+ * limbs); exact, the message and its scale are unchanged.  This is how a
+ * ciphertext reaches level 0 before a refresh without spending rescales.
+ * Errors: FE_ELEVEL (to_level > level or level > L), FE_EINVAL (in place). */
+int fe_mod_drop(fe_ctx* ctx, const void* ct_dev, uint32_t n_ct, uint32_t level, uint32_t to_level, void* out_dev,
+                void* stream);
 /* ModRaise: n_ct level-0 ciphertexts, read as centred integers mod q_0, reduced
  * modulo q_0..q_top (out: level `top`).  The result decrypts to m + q_0 I.
  * Errors: FE_ELEVEL (top > L). */
@@ -933,6 +940,15 @@ size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
  * ws: fe_boot_workspace_bytes(boot, n_ct).  Errors: FE_EKEY, FE_ENOMEM. */
 int fe_he_bootstrap(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
                     void* out_dev, void* ws, size_t ws_bytes, void* stream);
+/* Bring n_ct ciphertexts at `level` >= 1 with declared scale in_scale to the
+ * refresh's input: level 0 at the boot's scale_in, same slot values.  They are
+ * dropped to level 1 (exact), multiplied by B = nearest((scale_in / in_scale)
+ * q_1) and rescaled by q_1 (out: level 0).  ws: fe_boot_prepare_workspace_bytes.
+ * The slot values must stay within the range the refresh was built for
+ * (|z| <= about q_0 / (32 scale_in)).  Errors: FE_ELEVEL, FE_EINVAL, FE_ENOMEM. */
+size_t fe_boot_prepare_workspace_bytes(const fe_ctx* ctx, uint32_t n_ct);
+int fe_boot_prepare(fe_ctx* ctx, const fe_boot* boot, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                    double in_scale, void* out_dev, void* ws, size_t ws_bytes, void* stream);
 void fe_boot_destroy(fe_boot* boot);
 
 #ifdef __cplusplus

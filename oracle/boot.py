@@ -141,6 +141,20 @@ def mod_raise(pr, ct, top):
     return ckks.Ciphertext(polys[0], polys[1], top, float(q0))
 
 
+def prepare(pr, ct, scale_in):
+    """A ciphertext at level >= 1 with declared scale s, brought to the
+    refresh's input: level 0 at declared scale scale_in, same slot values.
+    The ciphertext is dropped to level 1 (exact), multiplied by the integer
+    B = nearest((scale_in / s) q_1) and rescaled by q_1."""
+    if ct.level < 1:
+        raise ValueError("prepare needs a level to rescale")
+    x = drop_level(ct, ct.level - 1)
+    B = ckks.nearest_int((scale_in / ct.scale) * float(pr.moduli[1]))
+    r = ckks.rescale(pr, ckks.mul_int(pr, x, B))
+    r.scale = scale_in
+    return r
+
+
 def mul_monomial(pr, ct, e, sign=1):
     """ct times sign X^e (exact; the scale is unchanged)."""
     m = np.zeros(pr.N, dtype=np.int64)

@@ -202,6 +202,7 @@ SIGNATURES = {
     "fe_sk_gen_sparse": (cint, [vp, u64, u32, vp, vp]),
     "fe_conjugate": (cint, [vp, vp, vp, u32, u32, vp, vp]),
     "fe_mod_raise": (cint, [vp, vp, u32, u32, vp, vp]),
+    "fe_mod_drop": (cint, [vp, vp, u32, u32, u32, vp, vp]),
     "fe_plan_lintrans": (cint, [vp, u32, u32, u32, P(u32), P(u32), P(i32), u32, u32, P(vp)]),
     "fe_plan_lintrans_load": (cint, [vp, vp, vp, dbl, vp, vp]),
     "fe_he_lintrans": (cint, [vp, vp, vp, vp, vp, vp, u32, vp, sz, vp]),
@@ -211,6 +212,8 @@ SIGNATURES = {
     "fe_boot_workspace_bytes": (sz, [vp, u32]),
     "fe_he_bootstrap": (cint, [vp, vp, vp, vp, u32, vp, vp, sz, vp]),
     "fe_boot_destroy": (None, [vp]),
+    "fe_boot_prepare_workspace_bytes": (sz, [vp, u32]),
+    "fe_boot_prepare": (cint, [vp, vp, vp, u32, u32, dbl, vp, vp, sz, vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
     "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
 }
@@ -523,6 +526,12 @@ class Context:
         check(load().fe_conjugate(self.handle, evk.handle, _ptr(ct), ct.shape[0], level, _ptr(out), _stream()))
         return out
 
+    def mod_drop(self, ct, level, to_level):
+        """The ciphertexts modulo Q_to_level (exact, same scale; fe_mod_drop)."""
+        out = self.empty_ct(ct.shape[0], to_level)
+        check(load().fe_mod_drop(self.handle, _ptr(ct), ct.shape[0], level, to_level, _ptr(out), _stream()))
+        return out
+
     def mod_raise(self, ct, top):
         out = self.empty_ct(ct.shape[0], top)
         check(load().fe_mod_raise(self.handle, _ptr(ct), ct.shape[0], top, _ptr(out), _stream()))
@@ -565,6 +574,15 @@ class Context:
         h = vp()
         check(load().fe_boot_create(self.handle, ctypes.byref(prm), scale_in, _stream(), ctypes.byref(h)))
         return Boot(self, h, scale_in)
+
+    def boot_prepare(self, boot, ct, level, in_scale):
+        """Ciphertexts at `level` (scale in_scale) to level 0 at boot.scale_in (fe_boot_prepare)."""
+        n = ct.shape[0]
+        ws = self.workspace(load().fe_boot_prepare_workspace_bytes(self.handle, n))
+        out = self.empty_ct(n, 0)
+        check(load().fe_boot_prepare(self.handle, boot.handle, _ptr(ct), n, level, float(in_scale), _ptr(out),
+                                     _ptr(ws), ws.numel() * 8, _stream()))
+        return out
 
     def bootstrap(self, evk, boot, ct, ws=None, out=None):
         """Refresh level-0 ciphertexts; returns them at boot.out_level (scale boot.out_scale)."""

@@ -669,6 +669,21 @@ extern "C" int fe_conjugate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, ui
     return fe_rotate(c, evk, ct_dev, n_ct, level, FE_STEP_CONJ, out_dev, stream);
 }
 
+extern "C" int fe_mod_drop(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t level, uint32_t to_level,
+                           void* out_dev, void* stream) {
+    FE_ALIGNED(ct_dev);
+    FE_ALIGNED(out_dev);
+    if (!c || !ct_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    if ((int)level > c->L || to_level > level) return fail(FE_ELEVEL, "levels must satisfy to_level <= level <= L");
+    if (n_ct == 0) return FE_OK;
+    if (ct_dev == out_dev && to_level != level) return fail(FE_EINVAL, "a level drop cannot run in place");
+    const size_t N = (size_t)c->N, nl = (size_t)to_level + 1;
+    // each polynomial keeps its first to_level + 1 limbs (rows of 2 n_ct polynomials)
+    FE_CUDA_TRY(cudaMemcpy2DAsync(out_dev, nl * N * 8, ct_dev, ((size_t)level + 1) * N * 8, nl * N * 8, 2 * (size_t)n_ct,
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return FE_OK;
+}
+
 extern "C" int fe_mod_raise(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t top, void* out_dev, void* stream) {
     FE_ALIGNED(ct_dev);
     FE_ALIGNED(out_dev);
@@ -851,6 +866,36 @@ extern "C" int fe_he_bootstrap(fe_ctx* c, const fe_evk* evk, const fe_boot* b, c
     if (n_ct == 0) return FE_OK;
     return boot_run(c, evk, b, (const u64*)ct_dev, (int)n_ct, (u64*)out_dev, ws, ws_bytes, (cudaStream_t)stream,
                     false, nullptr);
+}
+
+extern "C" size_t fe_boot_prepare_workspace_bytes(const fe_ctx* c, uint32_t n_ct) {
+    if (!c || n_ct == 0) return 0;
+    return 2 * (size_t)n_ct * ct_words(c, 1) * 8 + rescale_tmp_words(c, (int)n_ct, 1) * 8 + 3 * 256;
+}
+
+extern "C" int fe_boot_prepare(fe_ctx* c, const fe_boot* b, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                               double in_scale, void* out_dev, void* ws, size_t ws_bytes, void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !b || !ct_dev || !out_dev || !ws) return fail(FE_EINVAL, "null argument");
+    if (b->c != c) return fail(FE_EINVAL, "the bootstrap belongs to another context");
+    if (level < 1 || (int)level > c->L) return fail(FE_ELEVEL, "prepare needs 1 <= level <= L");
+    if (!(in_scale > 0)) return fail(FE_EINVAL, "in_scale must be positive");
+    if (n_ct == 0) return FE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    Carver cv(ws, ws_bytes);
+    u64* x = cv.take<u64>((size_t)n_ct * ct_words(c, 1));
+    u64* y = cv.take<u64>((size_t)n_ct * ct_words(c, 1));
+    u64* tmp = cv.take<u64>(rescale_tmp_words(c, (int)n_ct, 1));
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small (fe_boot_prepare_workspace_bytes)");
+    FE_TRY(fe_mod_drop(c, ct_dev, n_ct, level, 1, x, stream));
+    // B = nearest((scale_in / s) q_1): the value is unchanged at the declared scale scale_in
+    const double bq = (b->scale_in / in_scale) * (double)c->mod[1];
+    AffineConsts k{};
+    for (int i = 0; i <= 1; i++) k.mul[i] = nearest_mod(bq, c->mod[i]);
+    FE_TRY(launch_affine(c, x, y, (int)n_ct, 1, k, true, st));
+    rescale_batch(c, y, (int)n_ct, 1, (u64*)out_dev, tmp, tmp + 2 * (size_t)n_ct * c->N, st);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
 }
 
 extern "C" void fe_boot_destroy(fe_boot* b) { delete b; }

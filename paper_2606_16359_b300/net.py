@@ -5,6 +5,9 @@ encoding at S = 1 (the largest maps need S = 1 to fit a ciphertext), each
 block an independent encrypted input.  All layers' ciphertexts, plaintexts and
 keys stay resident on the device; a step runs the six HE convolutions.
 
+RefreshChain: two such blocks with the activation after each convolution and
+a ciphertext refresh (bootstrapping) between them, at the refresh's parameters.
+
 LeNet: conv5x5 1->6, x^2, avgpool2, conv5x5 6->16, x^2, avgpool2, FC 256->120->84->10
 at the largest slot batch (Sec. 5, Implementation paragraph: x^2 activation,
 pooling by fragment sums, FC by diagonals with baby-step / giant-step).
@@ -306,3 +309,97 @@ class LeNet:
     def decode_logits(self, out_ct):
         slots = self.ctx.decrypt(self.sk, out_ct, self.ctx.L - 7, self.out_scale)
         return self.ctx.fc_unpack(self.f3, slots, self.BS, 10).cpu().numpy()
+
+
+class RefreshChain:
+    """Two MobileNet-shaped blocks (depthwise 3x3, a x^2 + b x + c, pointwise,
+    the same activation) with a ciphertext refresh between them: the pattern of
+    the paper's deeper networks, which refresh their ciphertexts between blocks
+    (Sec. 5, Evaluation Methodology).  The context needs the refresh's
+    parameters (levels above the refresh's depth, moduli of about 50 bits);
+    the secret is sparse (weight h).  Block 1 runs from level L, its output is
+    brought to level 0 at the refresh's input scale (fe_boot_prepare), the
+    refresh returns it at boot.out_level, and block 2 runs from there.  The
+    library fixes every scale (fe_weight_scale, fe_plan_out_scale,
+    fe_poly_act_scale, fe_boot_output); this class only passes them along."""
+
+    def __init__(self, ctx, H, C, delta=2.0 ** 40, act=(0.5, 0.5, 0.0), h=64, scale_in=2.0 ** 44, seed=5,
+                 key_seed=41, boot_groups=(3, 3), double_angles=6):
+        torch = _torch()
+        self.ctx, self.delta, self.act = ctx, delta, tuple(float(v) for v in act)
+        a = self.act[0]
+        L = ctx.L
+        self.x, wd1, wp1 = W.mobilenet_block(seed, H, C, C, BS=1, block=0)
+        _, wd2, wp2 = W.mobilenet_block(seed, H, C, C, BS=1, block=1)
+        self.w = [(wd1, wp1), (wd2, wp2)]
+        self.boot = ctx.boot_create(scale_in, boot_groups[0], boot_groups[1], double_angles)
+        lb = self.boot.out_level
+        if lb < 4:
+            raise ValueError("the refresh leaves fewer than the 4 levels block 2 needs")
+        lay = ctx.layout(H, H, C, 1, 1)
+        self.lay = lay
+        p1d = ctx.plan_conv(lay, C, 3, depthwise=True, level=L)
+        p1p = ctx.plan_conv(p1d.out_layout, C, 1, level=L - 2)
+        p2d = ctx.plan_conv(p1p.out_layout, C, 3, depthwise=True, level=lb)
+        p2p = ctx.plan_conv(p2d.out_layout, C, 1, level=lb - 2)
+        self.plans = [(p1d, p1p, L), (p2d, p2p, lb)]
+        steps = sorted({s for p in (p1d, p1p, p2d, p2p) for s in p.steps} | set(self.boot.steps))
+        self.sk = ctx.sk_gen_sparse(key_seed, h)
+        self.evk = ctx.evk_gen(self.sk, key_seed, steps, relin=True)
+        self.n_keys = len(steps)
+        self.pts, self.scales = [], []
+        self.ws = ctx.workspace(max(p.info.workspace_bytes for p in (p1d, p1p, p2d, p2p)))
+        self.boot_ws = ctx.workspace(self.boot.workspace_bytes(p1p.info.n_out_ct))
+        s = delta
+        for (pd, pp, lv), (wd, wp) in zip(self.plans, self.w):
+            if lv != L:
+                s = self.boot.out_scale
+            ptd = ctx.load_weights(pd, wd, ctx.weight_scale(lv, s, delta, a))
+            s_d = ctx.plan_out_scale(pd, s)
+            s_a = ctx.poly_act_scale(lv - 1, s_d, a)
+            ptp = ctx.load_weights(pp, wp, ctx.weight_scale(lv - 2, s_a, delta, a))
+            s_p = ctx.plan_out_scale(pp, s_a)
+            s = ctx.poly_act_scale(lv - 3, s_p, a)
+            self.pts.append((ptd, ptp))
+            self.scales.append((s_d, s_p, s))
+        self.out_layout = p2p.out_layout
+        self.out_level = lb - 4
+        self.out_scale = s
+        slots = ctx.pack(lay, torch.from_numpy(self.x))
+        self.ct = ctx.encrypt(self.sk, slots, L, delta, seed=7)
+
+    def _block(self, i, h):
+        c = self.ctx
+        (pd, pp, lv), (ptd, ptp), (s_d, s_p, _) = self.plans[i], self.pts[i], self.scales[i]
+        h = c.he_conv(self.evk, pd, ptd, h, ws=self.ws)
+        h, _ = c.he_poly_act(self.evk, h, lv - 1, s_d, *self.act)
+        h = c.he_conv(self.evk, pp, ptp, h, ws=self.ws)
+        h, _ = c.he_poly_act(self.evk, h, lv - 3, s_p, *self.act)
+        return h
+
+    def forward(self, trace=None):
+        """Block 1, prepare, refresh, block 2; returns the output ciphertexts."""
+        c, L = self.ctx, self.ctx.L
+        h = self._block(0, self.ct)
+        if trace is not None:
+            trace["block1"] = h
+        h = c.boot_prepare(self.boot, h, L - 4, self.scales[0][2])
+        h = c.bootstrap(self.evk, self.boot, h, ws=self.boot_ws)
+        if trace is not None:
+            trace["refreshed"] = h
+        return self._block(1, h)
+
+    def decrypt(self, out):
+        slots = self.ctx.decrypt(self.sk, out, self.out_level, self.out_scale)
+        return self.ctx.unpack(self.out_layout, slots).cpu().numpy()
+
+    def reference(self):
+        """The FP64 network (torch float64) for the decrypted comparison."""
+        from . import plainref
+        y = self.x
+        for wd, wp in self.w:
+            y = plainref.conv2d(y, wd, depthwise=True)
+            y = plainref.poly_act(y, *self.act)
+            y = plainref.conv2d(y, wp)
+            y = plainref.poly_act(y, *self.act)
+        return y

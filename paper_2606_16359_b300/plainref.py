@@ -13,6 +13,12 @@ def conv2d(x, w, stride=1, depthwise=False):
     return y.numpy()
 
 
+def poly_act(x, a, b, c):
+    """a x^2 + b x + c elementwise (float64)."""
+    x = np.asarray(x, dtype=np.float64)
+    return a * x * x + b * x + c
+
+
 def lenet(x, weights):
     """The LeNet-5-shaped network in the clear (float64): two 5x5 valid convs,
     each followed by x^2 and 2x2 average pooling, then FC 256 -> 120 -> 84 -> 10

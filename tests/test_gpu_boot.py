@@ -177,3 +177,79 @@ def test_refresh_schedules_bit_exact(small, groups, r, ratio, double):
     want = boot.bootstrap(pr, keys, oct_, bp2)
     assert b.out_level == want.level == pr.L - bp2.depth
     assert np.array_equal(got[0], oracle_ct(pr, want))
+
+
+def _oracle_chain(pr, keys, cts, lay, w, act, delta, bp, scale_in):
+    """The oracle's composition of RefreshChain: block, prepare, refresh, block."""
+    from oracle import henn
+    a, b, c = act
+
+    def block(h, lay_, wd, wp):
+        lv = h[0].level
+        h, l1 = henn.he_conv(pr, keys, h, lay_, wd, depthwise=True,
+                             w_scale=henn.weight_scale(pr, lv, h[0].scale, delta, a))
+        h = henn.he_poly_act(pr, keys, h, a, b, c)
+        h, l2 = henn.he_conv(pr, keys, h, l1, wp, w_scale=henn.weight_scale(pr, lv - 2, h[0].scale, delta, a))
+        return henn.he_poly_act(pr, keys, h, a, b, c), l2
+
+    h, l2 = block(cts, lay, *w[0])
+    h = [boot.bootstrap(pr, keys, boot.prepare(pr, ct, scale_in), bp) for ct in h]
+    return block(h, l2, *w[1])
+
+
+def test_refresh_chain_bit_exact_small():
+    """Block (dw 3x3, activation, pw, activation), prepare, refresh, block at
+    N = 2^10 with 22 primes of 50 bits: every output residue equals the oracle's
+    composition of the same steps, and the decryption matches FP64."""
+    from oracle import fragment, henn, plain
+    from paper_2606_16359_b300 import net
+    logN, n_q, k, bits, h, H, C = 10, 22, 4, 50, 32, 6, 4
+    pr = ckks.Params(logN, n_q, k, bits)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(logN, n_q, k, bits)
+        ch = net.RefreshChain(ctx, H, C, h=h, key_seed=41, seed=5)
+        out = ch.forward()
+        got = u64(out)
+        y = ch.decrypt(out)
+        torch.cuda.synchronize()
+    bp = boot.BootParams(pr, 3, 3, 6)
+    lay = fragment.Layout(pr.N, H, H, C, 1, 1)
+    l1 = henn.out_layout_conv(lay, C, 3, 1)
+    l3 = henn.out_layout_conv(l1, C, 3, 1)
+    steps = set(boot.boot_rotation_steps(pr, bp))
+    for ly in (lay, l1, l3):
+        steps |= set(henn.conv_rotation_steps(ly, C, C, 3, depthwise=True))
+        steps |= set(henn.conv_rotation_steps(henn.out_layout_conv(ly, C, 3, 1), C, C, 1))
+    keys = boot.SparseKeySet(pr, 41, h, rot_steps=sorted(steps), relin=True, conj=True)
+    slots = fragment.pack(lay, ch.x)
+    cts = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, ch.delta), 7, i) for i in range(lay.n_ct)]
+    want, lo = _oracle_chain(pr, keys, cts, lay, ch.w, ch.act, ch.delta, bp, 2.0 ** 44)
+    assert want[0].level == ch.out_level and want[0].scale == ch.out_scale
+    assert np.array_equal(got, np.stack([oracle_ct(pr, c) for c in want]))
+    ref = ch.x
+    for wd, wp in ch.w:
+        ref = plain.poly_act(plain.conv2d(plain.poly_act(plain.conv2d(ref, wd, depthwise=True), *ch.act), wp),
+                             *ch.act)
+    assert np.abs(y - ref).max() < 1e-3
+
+
+def test_refresh_chain_full_size():
+    """The same chain at N = 2^16 (24 primes of 50 bits, secret weight 64) on a
+    14 x 14 x 32 map: decrypted within 1e-3 of the FP64 network."""
+    from paper_2606_16359_b300 import net
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(16, 24, 4, 50)
+        ch = net.RefreshChain(ctx, 14, 32, h=64)
+        out = ch.forward()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        out = ch.forward()
+        t1.record(s)
+        torch.cuda.synchronize()
+        y = ch.decrypt(out)
+    err = float(np.abs(y - ch.reference()).max())
+    print(f"block + refresh + block at N=2^16: {t0.elapsed_time(t1):.1f} ms, max error {err:.2e}")
+    assert ch.out_level == 2 and err < 1e-3

@@ -318,3 +318,15 @@ def test_bootstrap_in_fourteen_levels(small):
     out = boot.bootstrap(pr, keys, ct, bp)
     assert out.level == pr.L - 14
     assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
+
+
+def test_prepare_reaches_level_zero_at_the_input_scale(small):
+    """prepare keeps the slot values and lands at level 0 with the requested scale."""
+    pr, bp, keys = small
+    z = np.random.default_rng(11).uniform(-2, 2, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 9, 2.0 ** 48), 12, 0)
+    out = boot.prepare(pr, ct, 2.0 ** 44)
+    assert out.level == 0 and out.scale == 2.0 ** 44
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 1e-9
+    with pytest.raises(ValueError):
+        boot.prepare(pr, out, 2.0 ** 44)
