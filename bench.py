@@ -329,11 +329,29 @@ def refresh_bench(torch, stream, steps):
         cnt = ctx.counters()
         ms = a.elapsed_time(e) / steps
         err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
+        # kernel classes of one refresh (CUDA events per launch), and the leading
+        # class, the transform in its general 64-bit form for 50-bit moduli,
+        # against the butterfly probe run on this context's modulus q_0
+        by_class = {}
+        for kd in ("ntt", "bconv", "keyip", "combine", "mac", "rescale"):
+            ctx.profile_begin(kd)
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+            t, n, byt = ctx.profile_end()
+            by_class[kd] = {"ms": round(t, 3), "launches": n, "algorithmic_GB": round(byt / 1e9, 3)}
+        t_ntt = by_class["ntt"]["ms"]
+        limb_passes = by_class["ntt"]["algorithmic_GB"] * 1e9 / (8.0 * ctx.N)
+        bfly_rate = limb_passes * (ctx.N // 2) * (ctx.logN / 2) / (t_ntt / 1e3) / 1e9 if t_ntt else 0.0
+        bfly_peak = butterfly_roof(ctx, torch)
     ks = cnt["keyswitch"] / steps
     res = {"ms": round(ms, 3), "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64, groups 3/11/3 levels, baby ratio 4, double hoisting",
            "levels_used": 23 - b.out_level, "out_level": b.out_level, "keyswitches": ks,
            "keyswitch_per_s": ks / (ms / 1e3), "max_abs_err": err,
-           "evk_gb": evk.buf.numel() * 8 / 1e9, "workspace_gb": ws.numel() * 8 / 1e9}
+           "evk_gb": evk.buf.numel() * 8 / 1e9, "workspace_gb": ws.numel() * 8 / 1e9,
+           "by_class": by_class,
+           "roofline": {"kernel": "ntt", "bound": "alu", "achieved": bfly_rate, "peak": bfly_peak,
+                        "unit": "Gbutterfly/s", "frac": bfly_rate / bfly_peak if bfly_peak else None,
+                        "peak_source": "measured in this run: the butterfly probe on this context's 50-bit q_0 "
+                                       "(general 64-bit Shoup butterflies, register-resident, one full wave)"}}
     del out, ws, ct, evk, b, sk, ctx
     return res
 
