@@ -286,6 +286,53 @@ def cpu_oracle_keyswitch(n_rot):
     return n_rot / dt, dt
 
 
+REFRESH_SMALL = dict(logN=10, n_q=20, k=4, bits=50, h=32, scale_in=2.0 ** 45)
+
+
+def cpu_oracle_refresh():
+    """The CPU oracle's refresh (as it stands, single-threaded) of one level-0
+    ciphertext on the small refresh workload (N = 2^10, 20 + 4 primes of 50
+    bits, secret weight 32, default schedule); key generation untimed."""
+    import time as _t
+
+    from oracle import boot, ckks
+    p = REFRESH_SMALL
+    pr = ckks.Params(p["logN"], p["n_q"], p["k"], p["bits"])
+    bp = boot.BootParams(pr)
+    keys = boot.SparseKeySet(pr, 3, p["h"], rot_steps=boot.boot_rotation_steps(pr, bp), relin=True, conj=True)
+    tab = boot.cos_table(pr.N)
+    z = np.random.default_rng(12).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, p["scale_in"]), 4, 0)
+    t0 = _t.perf_counter()
+    boot.bootstrap(pr, keys, ct, bp, tab=tab)
+    return _t.perf_counter() - t0
+
+
+def gpu_refresh_small(torch, stream, reps=10):
+    """fe_he_bootstrap on the small refresh workload (the oracle's sample above)."""
+    import paper_2606_16359_b300 as fe
+    p = REFRESH_SMALL
+    with torch.cuda.stream(stream):
+        ctx = fe.Context(p["logN"], p["n_q"], p["k"], p["bits"])
+        sk = ctx.sk_gen_sparse(3, p["h"])
+        b = ctx.boot_create(p["scale_in"])
+        evk = ctx.evk_gen(sk, 3, b.steps, relin=True)
+        z = np.random.default_rng(12).uniform(-1, 1, (1, ctx.N // 2))
+        ct = ctx.encrypt(sk, z, 0, p["scale_in"], seed=4)
+        ws = ctx.workspace(b.workspace_bytes(1))
+        out = ctx.bootstrap(evk, b, ct, ws=ws)
+        for _ in range(2):
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        e.record(stream)
+        torch.cuda.synchronize()
+    return a.elapsed_time(e) / reps
+
+
 def cpu_oracle_all_cores(n_rot_each, max_workers=64):
     """The same oracle rotation on every usable host core (one process each, at
     most max_workers, about 0.5 GB of host memory apiece)."""
@@ -711,6 +758,9 @@ def run_ours(args, dist, rank, world, local):
         gc.collect()
         torch.cuda.empty_cache()
         refresh = refresh_bench(torch, stream, max(3, min(args.steps, 10)))
+        refresh["small"] = {"ms": round(gpu_refresh_small(torch, stream), 3), "reps": 10, "warmup": 3,
+                            "params": "N=2^10, 20 x 50-bit q, 4 x 50-bit p, h=32, default schedule",
+                            "cpu_oracle": "cpu_baseline.refresh"}
 
     cpu = None
     if rank == 0 and args.cpu_rotations > 0:
@@ -724,6 +774,12 @@ def run_ours(args, dist, rank, world, local):
                "single_thread": {"value": v1, "unit": "keyswitch/s", "cores": 1,
                                  "sample": f"{args.cpu_rotations} oracle rotations of one level-22 ciphertext, "
                                            f"{dt1:.1f} s"}}
+        if args.refresh:
+            t_ref = cpu_oracle_refresh()
+            cpu["refresh"] = {"value": t_ref * 1e3, "unit": "ms per refresh", "cores": 1, "kind": "oracle",
+                              "sample": "one refresh of one level-0 ciphertext at N=2^10 (20 x 50-bit q, 4 x 50-bit "
+                                        "p, h=32, default schedule), single-threaded; the GPU's time on the same "
+                                        "workload is config.refresh.small"}
 
     if rank == 0:
         clocks = clk.summary()
