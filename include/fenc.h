@@ -64,6 +64,7 @@ typedef struct fe_evk fe_evk;
 typedef struct fe_plan fe_plan;
 typedef struct fe_graph fe_graph;
 typedef struct fe_server fe_server;
+typedef struct fe_boot fe_boot;
 
 /* Parameter set.  q primes: the n_q largest primes below 2^qbits with
  * q = 1 (mod 2N); special primes: the k largest primes below 2^pbits with the
@@ -758,17 +759,24 @@ typedef struct {
     size_t hbm_reserve_bytes;  /* kept free when hbm_budget_bytes = 0 */
 } fe_server_config;
 
-enum { FE_OP_LAYER = 0, FE_OP_SQUARE = 1, FE_OP_POOL = 2 };
+enum { FE_OP_LAYER = 0, FE_OP_SQUARE = 1, FE_OP_POOL = 2, FE_OP_POLY_ACT = 3, FE_OP_REFRESH = 4 };
 /* One operation of a model, applied to the output of the previous one:
  * FE_OP_LAYER: a conv or FC plan with its plaintexts (fe_he_layer_batch);
  * FE_OP_SQUARE: x^2 (fe_he_square); FE_OP_POOL: 2x2 average pooling of the
- * fragment layout `layout` (fe_he_avgpool).  Plans and plaintexts are owned by
- * the caller and must outlive the server. */
+ * fragment layout `layout` (fe_he_avgpool); FE_OP_POLY_ACT: a x^2 + b x + c on
+ * inputs of declared scale in_scale (fe_he_poly_act, one level); FE_OP_REFRESH:
+ * the ciphertext refresh `boot` of inputs of declared scale in_scale
+ * (fe_boot_prepare then fe_he_bootstrap; the level becomes the boot's output
+ * level), which lets a served model go deeper than its levels.  Plans,
+ * plaintexts and refreshes are owned by the caller and must outlive the server. */
 typedef struct {
     int kind;
     const fe_plan* plan;
     const void* pt_dev;
     fe_layout layout;
+    double a, b, c;      /* FE_OP_POLY_ACT */
+    double in_scale;     /* FE_OP_POLY_ACT, FE_OP_REFRESH */
+    const fe_boot* boot; /* FE_OP_REFRESH */
 } fe_op;
 
 typedef struct {
@@ -858,7 +866,6 @@ int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* by
  * the ciphertext layout [n][2][level+1][N] unless stated; the library never
  * frees caller buffers. */
 
-typedef struct fe_boot fe_boot;
 /* n_cts / n_stc: stage groups of CoeffToSlot / SlotToCoeff (1..log2(N/2));
  * r: double angles (1..16); top: level after ModRaise (0: L); baby_ratio: every
  * group takes n1 baby steps, the smallest power of two with n1^2 >= baby_ratio

@@ -84,7 +84,8 @@ class FeServerConfig(ctypes.Structure):
 
 
 class FeOp(ctypes.Structure):
-    _fields_ = [("kind", cint), ("plan", vp), ("pt_dev", vp), ("layout", FeLayout)]
+    _fields_ = [("kind", cint), ("plan", vp), ("pt_dev", vp), ("layout", FeLayout), ("a", dbl), ("b", dbl),
+                ("c", dbl), ("in_scale", dbl), ("boot", vp)]
 
 
 class FeServerStats(ctypes.Structure):
@@ -96,7 +97,7 @@ class FeServerStats(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
-OP_LAYER, OP_SQUARE, OP_POOL = 0, 1, 2
+OP_LAYER, OP_SQUARE, OP_POOL, OP_POLY_ACT, OP_REFRESH = 0, 1, 2, 3, 4
 
 SIGNATURES = {
     "fe_mlp_create": (cint, [u32, u32, u32, u64, P(vp)]),
@@ -1005,13 +1006,19 @@ class Server:
         self._keep = []
 
     def add_model(self, ctx, evk, ops, in_ct, in_level):
-        """ops: list of (OP_LAYER, plan, pt) / (OP_SQUARE,) / (OP_POOL, layout)."""
+        """ops: list of (OP_LAYER, plan, pt) / (OP_SQUARE,) / (OP_POOL, layout) /
+        (OP_POLY_ACT, a, b, c, in_scale) / (OP_REFRESH, boot, in_scale)."""
         arr = (FeOp * len(ops))()
         for i, op in enumerate(ops):
             if op[0] == OP_LAYER:
                 arr[i] = FeOp(OP_LAYER, op[1].handle, _ptr(op[2]), FeLayout())
             elif op[0] == OP_SQUARE:
                 arr[i] = FeOp(OP_SQUARE, None, None, FeLayout())
+            elif op[0] == OP_POLY_ACT:
+                arr[i] = FeOp(OP_POLY_ACT, None, None, FeLayout(), float(op[1]), float(op[2]), float(op[3]),
+                              float(op[4]), None)
+            elif op[0] == OP_REFRESH:
+                arr[i] = FeOp(OP_REFRESH, None, None, FeLayout(), 0.0, 0.0, 0.0, float(op[2]), op[1].handle)
             else:
                 arr[i] = FeOp(OP_POOL, None, None, op[1])
         mid = u32(0)

@@ -118,6 +118,11 @@ size_t fe_server::group_bytes(const Model& m, uint32_t R) const {
         size_t w = 0;
         if (op.d.kind == FE_OP_LAYER) w = fe_plan_workspace_bytes(op.d.plan, R, 0);
         else if (op.d.kind == FE_OP_SQUARE) w = fe_square_workspace_bytes(m.c, R * op.in_ct, op.in_level);
+        else if (op.d.kind == FE_OP_POLY_ACT) w = fe_poly_act_workspace_bytes(m.c, R * op.in_ct, op.in_level);
+        else if (op.d.kind == FE_OP_REFRESH)  // level-0 inputs of the refresh, then its scratch
+            w = round256((size_t)R * op.in_ct * ct_words(m.c, 0) * 8) +
+                std::max(fe_boot_prepare_workspace_bytes(m.c, R * op.in_ct),
+                         fe_boot_workspace_bytes(op.d.boot, R * op.in_ct));
         ws = std::max(ws, w);
     }
     return 2 * round256(R * m.max_ct_bytes) + round256(ws);
@@ -142,6 +147,16 @@ int fe_server::launch(Group& g, const Model& m) {
             FE_TRY(fe_he_layer_batch(m.c, m.evk, op.d.plan, op.d.pt_dev, in, out, R, ws, ws_bytes, 1, st));
         } else if (op.d.kind == FE_OP_SQUARE) {
             FE_TRY(fe_he_square(m.c, m.evk, in, R * op.in_ct, op.in_level, out, ws, ws_bytes, st));
+        } else if (op.d.kind == FE_OP_POLY_ACT) {
+            double out_scale;
+            FE_TRY(fe_he_poly_act(m.c, m.evk, op.d.a, op.d.b, op.d.c, in, R * op.in_ct, op.in_level, op.d.in_scale,
+                                  out, &out_scale, ws, ws_bytes, st));
+        } else if (op.d.kind == FE_OP_REFRESH) {
+            const uint32_t n = R * op.in_ct;
+            const size_t lv0_bytes = round256((size_t)n * ct_words(m.c, 0) * 8);
+            FE_TRY(fe_boot_prepare(m.c, op.d.boot, in, n, op.in_level, op.d.in_scale, ws, ws + lv0_bytes,
+                                   ws_bytes - lv0_bytes, st));
+            FE_TRY(fe_he_bootstrap(m.c, m.evk, op.d.boot, ws, n, out, ws + lv0_bytes, ws_bytes - lv0_bytes, st));
         } else {
             // pooling sums the fragments of one request: one launch per request
             const size_t in_b = (size_t)op.in_ct * ct_words(m.c, op.in_level) * 8;
@@ -328,6 +343,19 @@ extern "C" int fe_server_add_model(fe_server* s, fe_ctx* c, const fe_evk* evk, c
             FE_TRY(layout_fill(c->N, &L));
             if (L.n_ct != n || L.S % 2) return fail(FE_EINVAL, "pool layout does not chain or has odd S");
             n = L.n_ct / 4;
+        } else if (op.d.kind == FE_OP_POLY_ACT) {
+            if (lv == 0) return fail(FE_ELEVEL, "activation at level 0");
+            if (op.d.a != 0 && !evk->relin) return fail(FE_EKEY, "the activation needs a relinearisation key");
+            if (!(op.d.in_scale > 0)) return fail(FE_EINVAL, "activation op without a positive in_scale");
+            lv -= 1;
+        } else if (op.d.kind == FE_OP_REFRESH) {
+            if (!op.d.boot) return fail(FE_EINVAL, "refresh op without a refresh");
+            if (lv == 0) return fail(FE_ELEVEL, "a refresh input needs level >= 1 (fe_boot_prepare)");
+            if (!evk->relin) return fail(FE_EKEY, "the refresh needs a relinearisation key");
+            if (!(op.d.in_scale > 0)) return fail(FE_EINVAL, "refresh op without a positive in_scale");
+            uint32_t out_level = 0;
+            FE_TRY(fe_boot_output(op.d.boot, &out_level, nullptr));
+            lv = out_level;
         } else {
             return fail(FE_EINVAL, "unknown op kind");
         }

@@ -393,6 +393,17 @@ class RefreshChain:
         slots = self.ctx.decrypt(self.sk, out, self.out_level, self.out_scale)
         return self.ctx.unpack(self.out_layout, slots).cpu().numpy()
 
+    def serve_ops(self):
+        """The chain as a request-loop model: layers, activations and the refresh."""
+        from . import OP_LAYER, OP_POLY_ACT, OP_REFRESH
+        ops = []
+        for i, ((pd, pp, lv), (ptd, ptp), (s_d, s_p, _)) in enumerate(zip(self.plans, self.pts, self.scales)):
+            if i:
+                ops.append((OP_REFRESH, self.boot, self.scales[0][2]))
+            ops += [(OP_LAYER, pd, ptd), (OP_POLY_ACT, *self.act, s_d), (OP_LAYER, pp, ptp),
+                    (OP_POLY_ACT, *self.act, s_p)]
+        return ops
+
     def reference(self):
         """The FP64 network (torch float64) for the decrypted comparison."""
         from . import plainref

@@ -156,3 +156,35 @@ def test_arrivals_during_running_groups_are_batched(models):
     assert np.array_equal(outs[0].numpy(), first.numpy())
     for i in range(6):
         assert np.array_equal(outs[i].numpy(), outs[i % 3].numpy())
+
+
+def test_served_refresh_chain_equals_the_direct_chain():
+    """A model whose operations include activations and a ciphertext refresh
+    (block, refresh, block at N = 2^10, 22 primes of 50 bits): every request's
+    served result equals the direct chain's residues, alone and batched two at
+    a time."""
+    from paper_2606_16359_b300.net import RefreshChain
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(10, 22, 4, 50)
+        ch = RefreshChain(ctx, 6, 4, h=32, key_seed=41, seed=5)
+        want = ch.forward().cpu().numpy()
+        torch.cuda.synchronize()
+    srv = fe.Server(max_batch=2, max_inflight=2)
+    try:
+        mid = srv.add_model(ctx, ch.evk, ch.serve_ops(), ch.lay.n_ct, ctx.L)
+        n_ct, lv, ib, ob = srv.model_io(mid)
+        assert lv == ch.out_level and ib == ch.ct.numel() * 8
+        inp = ch.ct.cpu().pin_memory()
+        outs = [torch.empty(ob // 8, dtype=torch.int64).pin_memory() for _ in range(3)]
+        srv.pause(True)
+        rids = [srv.submit(mid, inp, o) for o in outs]
+        srv.pause(False)
+        for rid in rids:
+            st, _ = srv.wait(rid)
+            assert st == 0
+        for o in outs:
+            assert np.array_equal(o.numpy(), want.reshape(-1))
+        assert srv.stats()["max_group"] == 2
+    finally:
+        srv.close()
