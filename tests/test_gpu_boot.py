@@ -253,3 +253,30 @@ def test_refresh_chain_full_size():
     err = float(np.abs(y - ch.reference()).max())
     print(f"block + refresh + block at N=2^16: {t0.elapsed_time(t1):.1f} ms, max error {err:.2e}")
     assert ch.out_level == 2 and err < 1e-3
+
+
+def test_refresh_steps_bit_exact_at_full_size():
+    """At the refresh's full parameter set (N = 2^16, 24 + 4 primes of 50 bits,
+    secret weight 64), the steps the oracle can afford there are compared
+    residue for residue: the sparse secret on all 28 moduli, ModRaise of a
+    level-0 ciphertext to level 23, and its conjugation (one key switch)."""
+    logN, n_q, k, bits, h = 16, 24, 4, 50, 64
+    pr = ckks.Params(logN, n_q, k, bits)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(logN, n_q, k, bits)
+        assert ctx.moduli == pr.moduli
+        sk = ctx.sk_gen_sparse(51, h)
+        evk = ctx.evk_gen(sk, 51, [fe.FE_STEP_CONJ], relin=False)
+        torch.cuda.synchronize()
+    keys = boot.SparseKeySet(pr, 51, h, conj=True)
+    assert np.array_equal(u64(sk), keys.sk.ntt)
+    z = np.random.default_rng(13).uniform(-1, 1, pr.N // 2)
+    oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 14, 0)
+    with torch.cuda.stream(s):
+        raised = ctx.mod_raise(to_gpu([oct_]), pr.L)
+        cj = ctx.conjugate(evk, raised, pr.L)
+        torch.cuda.synchronize()
+    want_r = boot.mod_raise(pr, oct_, pr.L)
+    assert np.array_equal(u64(raised)[0], oracle_ct(pr, want_r))
+    assert np.array_equal(u64(cj)[0], oracle_ct(pr, boot.conjugate(pr, keys, want_r)))
