@@ -101,6 +101,38 @@ class SparseKeySet(ckks.KeySet):
             add_conjugation(self)
 
 
+# Object tags of the two encapsulation keys (Galois elements are odd and below
+# 2N, the relinearisation key is 0, so the even values 2N and 2N + 2 are free).
+def swk_obj_to_sparse(pr):
+    return 2 * pr.N
+
+
+def swk_obj_to_dense(pr):
+    return 2 * pr.N + 2
+
+
+class Encapsulation:
+    """Sparse-secret encapsulation of a refresh: the network keeps a dense secret
+    s (ckks.KeySet) and the refresh borrows a sparse secret s' of weight h only
+    for ModRaise.  Keys: s -> s' (object 2N) and s' -> s (object 2N + 2), both
+    from the dense key set's seed, in ckks.SwitchKey's form."""
+
+    def __init__(self, keys, sparse_seed, h):
+        pr = keys.pr
+        coef = sparse_ternary(sparse_seed, pr.N, h)
+        self.s_sparse_ntt = ckks.signed_to_ntt(pr, coef, range(len(pr.moduli)))
+        self.to_sparse = ckks.SwitchKey(pr, keys.seed, swk_obj_to_sparse(pr), keys.sk.ntt, self.s_sparse_ntt)
+        self.to_dense = ckks.SwitchKey(pr, keys.seed, swk_obj_to_dense(pr), self.s_sparse_ntt, keys.sk.ntt)
+
+
+def key_switch(pr, ct, key):
+    """(c0, c1) under the key's source secret -> (c0 + d0, d1) under its
+    destination secret, (d0, d1) the hybrid key switch of c1 (Sec. 2)."""
+    d0, d1 = ckks.key_switch_ext(pr, ckks.mod_up(pr, ct.c1, ct.level), key, ct.level)
+    c0 = np.stack([C.vec_add(ct.c0[t], d0[t], pr.moduli[t]) for t in range(ct.level + 1)])
+    return ckks.Ciphertext(c0, d1, ct.level, ct.scale)
+
+
 def conj_galois(pr):
     return 2 * pr.N - 1
 
@@ -557,12 +589,19 @@ def boot_rotation_steps(pr, bp):
     return sorted(steps - {0})
 
 
-def bootstrap(pr, keys, ct, bp, tab=None, trace=None):
+def bootstrap(pr, keys, ct, bp, tab=None, trace=None, encaps=None):
     """Refresh a level-0 ciphertext (declared scale ct.scale) to level
-    bp.top - bp.depth; the result decrypts to the same slot values."""
+    bp.top - bp.depth; the result decrypts to the same slot values.
+    encaps (an Encapsulation): the input is under the dense secret of `keys`;
+    it is switched to the sparse secret at level 0, raised, and switched back
+    to the dense secret at level top before CoeffToSlot."""
     tab = cos_table(pr.N) if tab is None else tab
     scale_in = ct.scale
+    if encaps is not None:
+        ct = key_switch(pr, ct, encaps.to_sparse)
     x = mod_raise(pr, ct, bp.top)
+    if encaps is not None:
+        x = key_switch(pr, x, encaps.to_dense)
     cj = conjugate(pr, keys, x)
     re = ckks.add(pr, x, cj)
     im = mul_monomial(pr, sub(pr, x, cj), pr.N // 2, -1)

@@ -330,3 +330,33 @@ def test_prepare_reaches_level_zero_at_the_input_scale(small):
     assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 1e-9
     with pytest.raises(ValueError):
         boot.prepare(pr, out, 2.0 ** 44)
+
+
+def test_encapsulated_refresh_with_a_dense_secret():
+    """Sparse-secret encapsulation: the network's secret is the dense ternary one
+    (ckks.KeySet); the refresh switches its input to a sparse secret for
+    ModRaise and back to the dense secret at level top.  The raised ciphertext
+    decrypts (exactly, by CRT) under the dense secret to m + q_0 I with I
+    bounded by the sparse secret's weight, and the refresh returns the message."""
+    logN = 8
+    pr = ckks.Params(logN, 19, 4, 50)
+    bp = boot.BootParams(pr, 3, 3, 6)
+    keys = ckks.KeySet(pr, 17, rot_steps=boot.boot_rotation_steps(pr, bp), relin=True)
+    boot.add_conjugation(keys)
+    enc = boot.Encapsulation(keys, 18, 16)
+    assert np.count_nonzero(keys.sk.coef) > pr.N // 2  # dense
+    z = np.random.default_rng(14).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 15, 0)
+    # the raise under the sparse secret, switched back: t = m + q_0 I with small I
+    x = boot.key_switch(pr, boot.mod_raise(pr, boot.key_switch(pr, ct, enc.to_sparse), 6), enc.to_dense)
+    t = crt_coef(pr, keys.sk, x)
+    m = ckks.decrypt_coef(pr, keys.sk, ct)
+    q0 = pr.moduli[0]
+    I = [round((t[j] - int(m[j])) / q0) for j in range(pr.N)]
+    assert max(abs(v) for v in I) <= (16 + 1) // 2 + 1
+    assert max(abs(t[j] - int(m[j]) - q0 * I[j]) for j in range(pr.N)) < 2 ** 20  # key-switch noise only
+    out = boot.bootstrap(pr, keys, ct, bp, encaps=enc)
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
+    # without encapsulation, ModRaise under the dense secret exceeds the sparse secret's bound
+    t2 = crt_coef(pr, keys.sk, boot.mod_raise(pr, ct, 6))
+    assert max(abs(round((t2[j] - int(m[j])) / q0)) for j in range(pr.N)) > (16 + 1) // 2 + 1
