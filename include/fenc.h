@@ -947,6 +947,25 @@ size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
  * ws: fe_boot_workspace_bytes(boot, n_ct).  Errors: FE_EKEY, FE_ENOMEM. */
 int fe_he_bootstrap(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
                     void* out_dev, void* ws, size_t ws_bytes, void* stream);
+/* Switching key from secret sk_src to secret sk_dst (both [n_mod][N], NTT
+ * form), random streams of object tag `obj` (rotation keys use their Galois
+ * element, the relinearisation key 0), in the layout of one rotation key:
+ * key_bytes >= fe_evk_bytes(ctx, 1, 0).  Synchronises `stream`. */
+int fe_swk_gen(fe_ctx* ctx, const void* sk_src, const void* sk_dst, uint64_t seed, uint32_t obj, void* key_dev,
+               size_t key_bytes, void* stream);
+/* Hybrid key switch of n_ct ciphertexts at `level` from the key's source secret
+ * to its destination secret: (c0 + d0, d1), (d0, d1) = KS(c1) (not in place). */
+int fe_key_switch(fe_ctx* ctx, const void* key_dev, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                  void* out_dev, void* stream);
+/* Sparse-secret encapsulation: the network keeps its dense secret sk_dense (the
+ * evk of fe_he_bootstrap is sk_dense's) and the refresh borrows the sparse
+ * secret sk_sparse (fe_sk_gen_sparse) for ModRaise only.  Generates the keys
+ * dense -> sparse (object 2N) and sparse -> dense (object 2N + 2) into keys_dev
+ * (2 x fe_evk_bytes(ctx, 1, 0) bytes, caller-owned, must outlive the boot) and
+ * makes fe_he_bootstrap switch its level-0 inputs to the sparse secret, raise
+ * them and switch them back at level top (two key switches more). */
+int fe_boot_encapsulate(fe_ctx* ctx, fe_boot* boot, const void* sk_dense, const void* sk_sparse, uint64_t seed,
+                        void* keys_dev, size_t keys_bytes, void* stream);
 /* Bring n_ct ciphertexts at `level` >= 1 with declared scale in_scale to the
  * refresh's input: level 0 at the boot's scale_in, same slot values.  They are
  * dropped to level 1 (exact), multiplied by B = nearest((scale_in / in_scale)

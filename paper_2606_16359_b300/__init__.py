@@ -214,6 +214,9 @@ SIGNATURES = {
     "fe_he_bootstrap": (cint, [vp, vp, vp, vp, u32, vp, vp, sz, vp]),
     "fe_boot_destroy": (None, [vp]),
     "fe_boot_prepare_workspace_bytes": (sz, [vp, u32]),
+    "fe_swk_gen": (cint, [vp, vp, vp, u64, u32, vp, sz, vp]),
+    "fe_key_switch": (cint, [vp, vp, vp, u32, u32, vp, vp]),
+    "fe_boot_encapsulate": (cint, [vp, vp, vp, vp, u64, vp, sz, vp]),
     "fe_boot_prepare": (cint, [vp, vp, vp, u32, u32, dbl, vp, vp, sz, vp]),
     "fe_profile_begin": (cint, [vp, ctypes.c_char_p]),
     "fe_profile_end": (cint, [vp, P(dbl), P(u64), P(dbl)]),
@@ -575,6 +578,28 @@ class Context:
         h = vp()
         check(load().fe_boot_create(self.handle, ctypes.byref(prm), scale_in, _stream(), ctypes.byref(h)))
         return Boot(self, h, scale_in)
+
+    def swk_gen(self, sk_src, sk_dst, seed, obj):
+        """Switching key sk_src -> sk_dst (fe_swk_gen), one rotation key's layout."""
+        nbytes = load().fe_evk_bytes(self.handle, 1, 0)
+        key = _torch().empty(nbytes // 8, dtype=_torch().int64, device="cuda")
+        check(load().fe_swk_gen(self.handle, _ptr(sk_src), _ptr(sk_dst), seed, obj, _ptr(key), nbytes, _stream()))
+        return key
+
+    def key_switch(self, key, ct, level):
+        out = self.empty_ct(ct.shape[0], level)
+        check(load().fe_key_switch(self.handle, _ptr(key), _ptr(ct), ct.shape[0], level, _ptr(out), _stream()))
+        return out
+
+    def boot_encapsulate(self, boot, sk_dense, sk_sparse, seed):
+        """Let the refresh run under a dense secret (fe_boot_encapsulate); the two
+        keys are kept on the Boot object."""
+        nbytes = 2 * load().fe_evk_bytes(self.handle, 1, 0)
+        keys = _torch().empty(nbytes // 8, dtype=_torch().int64, device="cuda")
+        check(load().fe_boot_encapsulate(self.handle, boot.handle, _ptr(sk_dense), _ptr(sk_sparse), seed, _ptr(keys),
+                                         nbytes, _stream()))
+        boot.encaps_keys = keys
+        return keys
 
     def boot_prepare(self, boot, ct, level, in_scale):
         """Ciphertexts at `level` (scale in_scale) to level 0 at boot.scale_in (fe_boot_prepare)."""

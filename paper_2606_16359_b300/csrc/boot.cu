@@ -45,6 +45,10 @@ struct fe_boot {
     std::vector<u64*> pts;                        // their compact plaintexts (owned)
     u64* mono = nullptr;                          // NTT(-X^(N/2)) on q_0..q_top (owned)
     std::vector<int32_t> steps;                   // rotation steps (mod n) and FE_STEP_CONJ
+    // sparse-secret encapsulation (caller-owned keys, or null): dense -> sparse at
+    // level 0 before ModRaise, sparse -> dense at level top after it
+    const u64* key_to_sparse = nullptr;
+    const u64* key_to_dense = nullptr;
     ~fe_boot() {
         for (u64* p : pts) cudaFree(p);
         if (mono) cudaFree(mono);
@@ -148,13 +152,10 @@ void carve_conj(Carver& cv, const fe_ctx* c, int n, int level, ConjScratch* s) {
     s->cb = cv.take<CombineItem>(n);
 }
 
-// out = sigma_{2N-1}(in) with its key switch, n ciphertexts at `level` (the
-// rotation of Eq. 1 with the conjugation's Galois element)
-int conjugate_batch(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, u64* out, const ConjScratch& s,
-                    cudaStream_t st) {
-    const uint32_t g = c->galois(FE_STEP_CONJ);
-    const u64* key = evk_key(evk, g);
-    if (!key) return fail(FE_EKEY, "missing conjugation key (step FE_STEP_CONJ)");
+// out = sigma_g((c0, 0) + KS_key(c1)) for n ciphertexts at `level` (g = 1: a plain
+// key switch from the key's source secret to its destination secret)
+int ks_batch(fe_ctx* c, const u64* key, uint32_t g, const u64* in, int n, int level, u64* out, const ConjScratch& s,
+             cudaStream_t st) {
     const int N = c->N, nl = level + 1;
     std::vector<KsItem> ks(n);
     std::vector<CombineItem> cb(n);
@@ -169,8 +170,19 @@ int conjugate_batch(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int leve
     launch_keyip(c, s.ks, n, level, st);
     moddown_prepare(c, s.acc, n, level, s.conv, st);
     launch_combine(c, s.cb, n, level, st);
-    c->cnt.rot += n;
     c->cnt.keyswitch += n;
+    return FE_OK;
+}
+
+// out = sigma_{2N-1}(in) with its key switch, n ciphertexts at `level` (the
+// rotation of Eq. 1 with the conjugation's Galois element)
+int conjugate_batch(fe_ctx* c, const fe_evk* evk, const u64* in, int n, int level, u64* out, const ConjScratch& s,
+                    cudaStream_t st) {
+    const uint32_t g = c->galois(FE_STEP_CONJ);
+    const u64* key = evk_key(evk, g);
+    if (!key) return fail(FE_EKEY, "missing conjugation key (step FE_STEP_CONJ)");
+    FE_TRY(ks_batch(c, key, g, in, n, level, out, s, st));
+    c->cnt.rot += n;
     return FE_OK;
 }
 
@@ -620,7 +632,15 @@ int boot_run(fe_ctx* c, const fe_evk* evk, const fe_boot* b, const u64* in, int 
         return FE_OK;
     }
     if (!cv.ok) return fail(FE_ENOMEM, "bootstrap workspace too small (fe_boot_workspace_bytes)");
-    mod_raise(c, in, R, top, raised, tmp, st);
+    if (b->key_to_sparse) {
+        // the level-0 inputs (dense secret) switched to the sparse secret (into pb), raised
+        // (into cj), switched back to the dense secret at level top (into raised)
+        FE_TRY(ks_batch(c, b->key_to_sparse, 1, in, R, 0, pb, cs, st));
+        mod_raise(c, pb, R, top, cj, tmp, st);
+        FE_TRY(ks_batch(c, b->key_to_dense, 1, cj, R, top, raised, cs, st));
+    } else {
+        mod_raise(c, in, R, top, raised, tmp, st);
+    }
     FE_TRY(conjugate_batch(c, evk, raised, R, top, cj, cs, st));
     k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (top + 1), R), kB, 0, st>>>(raised, cj, b->mono, pa, c->d_mod, top + 1,
                                                                           c->logN);
@@ -866,6 +886,51 @@ extern "C" int fe_he_bootstrap(fe_ctx* c, const fe_evk* evk, const fe_boot* b, c
     if (n_ct == 0) return FE_OK;
     return boot_run(c, evk, b, (const u64*)ct_dev, (int)n_ct, (u64*)out_dev, ws, ws_bytes, (cudaStream_t)stream,
                     false, nullptr);
+}
+
+extern "C" int fe_key_switch(fe_ctx* c, const void* key_dev, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                             void* out_dev, void* stream) {
+    FE_ALIGNED(key_dev); FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);
+    if (!c || !key_dev || !ct_dev || !out_dev) return fail(FE_EINVAL, "null argument");
+    if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
+    if (n_ct == 0) return FE_OK;
+    if (ct_dev == out_dev) return fail(FE_EINVAL, "a key switch cannot run in place");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t need = 0;
+    {
+        Carver dry(nullptr, SIZE_MAX);
+        ConjScratch cs;
+        carve_conj(dry, c, (int)n_ct, (int)level, &cs);
+        need = SIZE_MAX - dry.left;
+    }
+    void* ws;
+    FE_CUDA_TRY(cudaMallocAsync(&ws, need, st));
+    Carver cv(ws, need);
+    ConjScratch cs;
+    carve_conj(cv, c, (int)n_ct, (int)level, &cs);
+    const int rc = ks_batch(c, (const u64*)key_dev, 1, (const u64*)ct_dev, (int)n_ct, (int)level, (u64*)out_dev, cs,
+                            st);
+    cudaFreeAsync(ws, st);
+    FE_TRY(rc);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+extern "C" int fe_boot_encapsulate(fe_ctx* c, fe_boot* b, const void* sk_dense, const void* sk_sparse, uint64_t seed,
+                                   void* keys_dev, size_t keys_bytes, void* stream) {
+    FE_ALIGNED(keys_dev);
+    if (!c || !b || !sk_dense || !sk_sparse || !keys_dev) return fail(FE_EINVAL, "null argument");
+    if (b->c != c) return fail(FE_EINVAL, "the bootstrap belongs to another context");
+    const size_t one = fe_evk_bytes(c, 1, 0);
+    if (keys_bytes < 2 * one) return fail(FE_ENOMEM, "encapsulation key buffer too small (2 keys)");
+    u64* k0 = (u64*)keys_dev;
+    u64* k1 = k0 + one / 8;
+    // object tags 2N and 2N + 2: Galois elements are odd and the relinearisation key is 0
+    FE_TRY(fe_swk_gen(c, sk_dense, sk_sparse, seed, (uint32_t)(2 * c->N), k0, one, stream));
+    FE_TRY(fe_swk_gen(c, sk_sparse, sk_dense, seed, (uint32_t)(2 * c->N + 2), k1, one, stream));
+    b->key_to_sparse = k0;
+    b->key_to_dense = k1;
+    return FE_OK;
 }
 
 extern "C" size_t fe_boot_prepare_workspace_bytes(const fe_ctx* c, uint32_t n_ct) {

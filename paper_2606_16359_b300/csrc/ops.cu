@@ -295,6 +295,47 @@ extern "C" int fe_evk_gen(fe_ctx* c, const void* sk_dev, uint64_t seed, const in
     return FE_OK;
 }
 
+extern "C" int fe_swk_gen(fe_ctx* c, const void* sk_src, const void* sk_dst, uint64_t seed, uint32_t obj,
+                          void* key_dev, size_t key_bytes, void* stream) {
+    FE_ALIGNED(sk_src); FE_ALIGNED(sk_dst); FE_ALIGNED(key_dev);
+    if (!c || !sk_src || !sk_dst || !key_dev) return fail(FE_EINVAL, "null argument");
+    if (key_bytes < fe_evk_bytes(c, 1, 0)) return fail(FE_ENOMEM, "key buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = c->N, nm = c->n_mod;
+    std::vector<u64> pmod(nm);
+    for (int t = 0; t < nm; t++) {
+        u64 P = 1;
+        for (int j = 0; j < c->k; j++) P = h_mulmod(P, c->mod[c->L + 1 + j] % c->mod[t], c->mod[t]);
+        pmod[t] = P;
+    }
+    u64 *e_ntt, *d_pmod;
+    i64* e;
+    FE_CUDA_TRY(cudaMallocAsync(&e_ntt, (size_t)nm * N * 8, st));
+    FE_CUDA_TRY(cudaMallocAsync(&e, (size_t)N * 8, st));
+    FE_CUDA_TRY(cudaMallocAsync(&d_pmod, nm * 8, st));
+    FE_CUDA_TRY(cudaMemcpyAsync(d_pmod, pmod.data(), nm * 8, cudaMemcpyHostToDevice, st));
+    // b_j = e_j - a_j s_dst + [t in digit j] (P mod t) s_src, the layout of one rotation key
+    u64* key = (u64*)key_dev;
+    for (int j = 0; j < c->dnum; j++) {
+        u64* b = key + (size_t)j * 2 * nm * N;
+        u64* a = b + (size_t)nm * N;
+        launch_sample_uniform_limbs(c, seed, make_tag(kTagKeyA, obj, j, 0), a, nm, c->d_identity_map, st);
+        launch_sample_signed(c, seed, make_tag(kTagKeyE, obj, j, 0), 1, e, st);
+        launch_signed_to_limbs(c, e, e_ntt, 0, nm, (size_t)N, st);
+        ntt_forward(c, LimbSet{e_ntt, (size_t)nm * N, nm, 1, c->d_identity_map}, st);
+        const int lo = j * c->k, hi = std::min((j + 1) * c->k, c->L + 1);
+        k_key_b<<<grid_for(N, nm), kB, 0, st>>>(b, a, e_ntt, (const u64*)sk_src, (const u64*)sk_dst, 1, d_pmod, lo,
+                                                hi, c->d_mod, c->logN);
+        c->cnt.launches++;
+    }
+    cudaFreeAsync(e_ntt, st);
+    cudaFreeAsync(e, st);
+    cudaFreeAsync(d_pmod, st);
+    FE_CUDA_TRY(cudaStreamSynchronize(st));
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
 extern "C" int fe_evk_upload(fe_ctx* c, const void* evk_host, size_t evk_host_bytes, const int32_t* steps,
                              uint32_t n_steps, int relin, void* evk_dev, size_t evk_dev_bytes, void* stream,
                              fe_evk** out) {

@@ -317,14 +317,15 @@ class RefreshChain:
     the paper's deeper networks, which refresh their ciphertexts between blocks
     (Sec. 5, Evaluation Methodology).  The context needs the refresh's
     parameters (levels above the refresh's depth, moduli of about 50 bits);
-    the secret is sparse (weight h).  Block 1 runs from level L, its output is
+    the secret is sparse (weight h), or, with encapsulate, dense with a sparse
+    secret borrowed by the refresh (fe_boot_encapsulate).  Block 1 runs from level L, its output is
     brought to level 0 at the refresh's input scale (fe_boot_prepare), the
     refresh returns it at boot.out_level, and block 2 runs from there.  The
     library fixes every scale (fe_weight_scale, fe_plan_out_scale,
     fe_poly_act_scale, fe_boot_output); this class only passes them along."""
 
     def __init__(self, ctx, H, C, delta=2.0 ** 40, act=(0.5, 0.5, 0.0), h=64, scale_in=2.0 ** 44, seed=5,
-                 key_seed=41, boot_groups=(3, 3), double_angles=6):
+                 key_seed=41, boot_groups=(3, 3), double_angles=6, encapsulate=False):
         torch = _torch()
         self.ctx, self.delta, self.act = ctx, delta, tuple(float(v) for v in act)
         a = self.act[0]
@@ -344,7 +345,13 @@ class RefreshChain:
         p2p = ctx.plan_conv(p2d.out_layout, C, 1, level=lb - 2)
         self.plans = [(p1d, p1p, L), (p2d, p2p, lb)]
         steps = sorted({s for p in (p1d, p1p, p2d, p2p) for s in p.steps} | set(self.boot.steps))
-        self.sk = ctx.sk_gen_sparse(key_seed, h)
+        if encapsulate:
+            # the network under the dense secret; the refresh borrows a sparse one for ModRaise
+            self.sk = ctx.sk_gen(key_seed)
+            self.sk_sparse = ctx.sk_gen_sparse(key_seed + 1, h)
+            ctx.boot_encapsulate(self.boot, self.sk, self.sk_sparse, key_seed)
+        else:
+            self.sk = ctx.sk_gen_sparse(key_seed, h)
         self.evk = ctx.evk_gen(self.sk, key_seed, steps, relin=True)
         self.n_keys = len(steps)
         self.pts, self.scales = [], []

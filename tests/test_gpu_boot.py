@@ -234,14 +234,16 @@ def test_refresh_chain_bit_exact_small():
     assert np.abs(y - ref).max() < 1e-3
 
 
-def test_refresh_chain_full_size():
-    """The same chain at N = 2^16 (24 primes of 50 bits, secret weight 64) on a
-    14 x 14 x 32 map: decrypted within 1e-3 of the FP64 network."""
+@pytest.mark.parametrize("encapsulate", [False, True])
+def test_refresh_chain_full_size(encapsulate):
+    """The same chain at N = 2^16 (24 primes of 50 bits) on a 14 x 14 x 32 map,
+    under a sparse secret of weight 64, or under a dense secret with the sparse
+    one borrowed by the refresh: decrypted within 1e-3 of the FP64 network."""
     from paper_2606_16359_b300 import net
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = fe.Context(16, 24, 4, 50)
-        ch = net.RefreshChain(ctx, 14, 32, h=64)
+        ch = net.RefreshChain(ctx, 14, 32, h=64, encapsulate=encapsulate)
         out = ch.forward()
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -251,7 +253,8 @@ def test_refresh_chain_full_size():
         torch.cuda.synchronize()
         y = ch.decrypt(out)
     err = float(np.abs(y - ch.reference()).max())
-    print(f"block + refresh + block at N=2^16: {t0.elapsed_time(t1):.1f} ms, max error {err:.2e}")
+    print(f"block + refresh + block at N=2^16 (encapsulated: {encapsulate}): {t0.elapsed_time(t1):.1f} ms, "
+          f"max error {err:.2e}")
     assert ch.out_level == 2 and err < 1e-3
 
 
@@ -280,3 +283,36 @@ def test_refresh_steps_bit_exact_at_full_size():
     want_r = boot.mod_raise(pr, oct_, pr.L)
     assert np.array_equal(u64(raised)[0], oracle_ct(pr, want_r))
     assert np.array_equal(u64(cj)[0], oracle_ct(pr, boot.conjugate(pr, keys, want_r)))
+
+
+def test_encapsulated_refresh_bit_exact():
+    """Sparse-secret encapsulation at N = 2^10: a dense secret (fe_sk_gen) for the
+    ciphertext and the refresh's keys, a sparse one (weight 32) borrowed for
+    ModRaise; the generic key switch and the refresh equal the oracle's."""
+    logN, n_q, k, bits, h = 10, 20, 4, 50, 32
+    pr = ckks.Params(logN, n_q, k, bits)
+    bp = boot.BootParams(pr, 3, 3, 6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(logN, n_q, k, bits)
+        sk = ctx.sk_gen(61)
+        sp = ctx.sk_gen_sparse(62, h)
+        b = ctx.boot_create(2.0 ** 45)
+        ctx.boot_encapsulate(b, sk, sp, 61)
+        evk = ctx.evk_gen(sk, 61, b.steps, relin=True)
+        torch.cuda.synchronize()
+    keys = ckks.KeySet(pr, 61, rot_steps=boot.boot_rotation_steps(pr, bp), relin=True)
+    boot.add_conjugation(keys)
+    enc = boot.Encapsulation(keys, 62, h)
+    z = np.random.default_rng(15).uniform(-1, 1, pr.N // 2)
+    oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 16, 0)
+    lv = 5
+    octs5 = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, lv, 2.0 ** 45), 17, 0)
+    with torch.cuda.stream(s):
+        ks = u64(ctx.key_switch(b.encaps_keys[:b.encaps_keys.numel() // 2], to_gpu([octs5]), lv))
+        got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))
+        torch.cuda.synchronize()
+    assert np.array_equal(ks[0], oracle_ct(pr, boot.key_switch(pr, octs5, enc.to_sparse)))
+    want = boot.bootstrap(pr, keys, oct_, bp, encaps=enc)
+    assert np.array_equal(got[0], oracle_ct(pr, want))
+    assert np.abs(ckks.decrypt(pr, keys.sk, want) - z).max() < 1e-4
