@@ -55,8 +55,8 @@ def bench_ntt(ctx, torch, args):
     N, nm = ctx.N, ctx.n_mod
     n_poly = max(1, (args.limbs + nm - 1) // nm)
     limbs = n_poly * nm
-    # residues below 2^35 are valid for every modulus of 36 bits
-    d = torch.randint(0, 2 ** 35, (n_poly, nm, N), dtype=torch.int64, device="cuda")
+    # residues below 2^(bits - 1) are valid for every modulus of `bits` bits
+    d = torch.randint(0, 2 ** (args.qbits - 1), (n_poly, nm, N), dtype=torch.int64, device="cuda")
     out = {}
     for inv in (False, True):
         for _ in range(2):
@@ -77,7 +77,7 @@ def bench_ntt(ctx, torch, args):
     peak, src = hbm_peak()
     for v in out.values():
         v["hbm_frac"] = v["GBps"] / peak
-    return {"kernel": "ntt", "radix": args.radix, "q36": args.q36, "path": args.path, "fwd": args.fwd, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
+    return {"kernel": "ntt", "qbits": args.qbits, "radix": args.radix, "q36": args.q36, "path": args.path, "fwd": args.fwd, "logN": ctx.logN, "limbs": limbs, "bytes_in": limbs * N * 8,
             "peak_GBps": peak, "peak_source": src, **out}
 
 
@@ -374,6 +374,8 @@ def main(argv=None):
     ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs", "repack",
                                      "refresh"])
     ap.add_argument("--logN", type=int, default=16)
+    ap.add_argument("--qbits", type=int, default=36,
+                    help="modulus bits of the 24 + 4 primes (36: the convolution parameters; 50: the refresh's)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--iters", type=int, default=400)
@@ -400,7 +402,7 @@ def main(argv=None):
 
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
-        ctx = fe.Context(args.logN, 24, 4, 36, 36)
+        ctx = fe.Context(args.logN, 24, 4, args.qbits, args.qbits)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
               "layer": bench_layer, "aac": bench_aac, "configs": bench_configs,
               "repack": bench_repack, "refresh": bench_refresh}[args.what]
