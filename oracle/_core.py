@@ -44,6 +44,7 @@ _sig = {
     "or_sample_ternary": (None, [u64, u64, P, ctypes.c_int]),
     "or_sample_cbd21": (None, [u64, u64, P, ctypes.c_int]),
     "or_encode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, P]),
+    "or_encode_complex": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_double, P]),
     "or_decode": (None, [P, ctypes.c_int, ctypes.c_double, P]),
     "or_encode_direct_real": (None, [P, ctypes.c_int, ctypes.c_double, P]),
 }
@@ -235,6 +236,19 @@ def encode(z, logN, scale):
     assert z.size == (1 << logN) // 2
     out = np.empty(1 << logN, dtype=np.int64)
     rc = _lib.or_encode(_p(z), logN, float(scale), _p(out))
+    if rc < 0:
+        raise EncodeError(f"encode failed with status {rc}")
+    return out
+
+
+def encode_complex(z, logN, scale):
+    """Round(scale * tau^-1(z)) for complex slot values z (N/2 of them)."""
+    z = np.asarray(z, dtype=np.complex128)
+    assert z.size == (1 << logN) // 2
+    zr = np.ascontiguousarray(z.real)
+    zi = np.ascontiguousarray(z.imag)
+    out = np.empty(1 << logN, dtype=np.int64)
+    rc = _lib.or_encode_complex(_p(zr), _p(zi), logN, float(scale), _p(out))
     if rc < 0:
         raise EncodeError(f"encode failed with status {rc}")
     return out

@@ -361,6 +361,45 @@ def group_diagonals(N, tab, stages, inverse, kappa, parts):
     return out
 
 
+def group_diagonals_complex(N, tab, stages, inverse, kappa):
+    """Complex diagonals of one group acting on one ciphertext's complex slots:
+    {(0, 0, r): d_r}, d_r[o] = G[o][(o + r) mod n] = 2^-halvings (cos + i sin)(pi e / N),
+    each part times kappa in one IEEE product when kappa != 1; all-zero diagonals
+    are left out."""
+    n = N // 2
+    out = {}
+    for r in group_offsets(stages, n):
+        re = np.zeros(n)
+        im = np.zeros(n)
+        for o in range(n):
+            ent = group_entry(N, stages, inverse, o, (o + r) % n)
+            if ent is None:
+                continue
+            e, hv = ent
+            c = math.ldexp(cos_pi(tab, N, e), -hv)
+            s = math.ldexp(sin_pi(tab, N, e), -hv)
+            if kappa != 1.0:
+                c = c * kappa
+                s = s * kappa
+            re[o] = c
+            im[o] = s
+        if np.any(re != 0.0) or np.any(im != 0.0):
+            out[(0, 0, r)] = re + 1j * im
+    return out
+
+
+def encode_c(pr, z, level, scale):
+    """Plaintext of complex slot values z on q_0..q_level (NTT form)."""
+    m = C.encode_complex(z, pr.logN, scale)
+    return ckks.Plaintext(ckks.signed_to_ntt(pr, m, range(level + 1)), level, scale)
+
+
+def encode_qp_c(pr, z, level, scale):
+    """The same on Q_level * P (dict limb -> NTT residues)."""
+    m = C.encode_complex(z, pr.logN, scale)
+    return {t: pr.ntt(C.from_signed(m, pr.moduli[t]), t) for t in pr.ks_limbs(level)}
+
+
 # ---------------------------------------------------------------------------
 # Plaintext-matrix products by the diagonal method with baby / giant steps
 # ---------------------------------------------------------------------------
@@ -432,10 +471,12 @@ def he_lintrans(pr, keys, cts, diags, n_out, n1, w_scale=None, hoist="single"):
                 continue
             g, b = dec[r]
             z = np.roll(v, g)  # pt[l] = v[(l - g) mod n]
+            cplx = np.iscomplexobj(z)
             if double:
-                groups.setdefault(g, []).append((baby[(i, b)], ckks.encode_qp(pr, z, level, ws)))
+                pt = (encode_qp_c if cplx else ckks.encode_qp)(pr, z, level, ws)
+                groups.setdefault(g, []).append((baby[(i, b)], pt))
             else:
-                term = ckks.pmult(pr, baby[(i, b)], ckks.encode(pr, z, level, ws))
+                term = ckks.pmult(pr, baby[(i, b)], (encode_c if cplx else ckks.encode)(pr, z, level, ws))
                 groups[g] = term if g not in groups else ckks.add(pr, groups[g], term)
         total = None
         for g in sorted(groups):
@@ -535,9 +576,14 @@ class BootParams:
     """n_cts / n_stc: stage groups (levels) of CoeffToSlot / SlotToCoeff;
     r: double angles; top: level after ModRaise (default L); baby_ratio: the
     baby-step rule of every group (default_n1); double_hoist: the groups'
-    products with hoist="double" (he_lintrans)."""
+    products with hoist="double" (he_lintrans); form: "real" (the transforms on
+    the pair (re, im) in real form) or "complex" (on one ciphertext with complex
+    diagonals, the real and imaginary parts split after CoeffToSlot)."""
 
-    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=4, double_hoist=True):
+    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=4, double_hoist=True, form="real"):
+        if form not in ("real", "complex"):
+            raise ValueError("form must be 'real' or 'complex'")
+        self.form = form
         self.baby_ratio = baby_ratio
         self.hoist = "double" if double_hoist else "single"
         self.N = pr.N
@@ -577,6 +623,27 @@ def stc_diagonals(pr, bp, tab, scale_in):
     return out
 
 
+def cts_diagonals_complex(pr, bp, tab):
+    """The CoeffToSlot groups as complex diagonals on one ciphertext, in the order
+    applied; the first carries kappa = pi / 2^r (the 1/2 of the later split
+    and the EvalMod pre-scaling pi / 2^(r-1))."""
+    out = []
+    for gi, grp in enumerate(bp.cts_groups):
+        kappa = math.ldexp(math.pi, -bp.r) if gi == 0 else 1.0
+        out.append(group_diagonals_complex(pr.N, tab, sorted(grp, reverse=True), True, kappa))
+    return out
+
+
+def stc_diagonals_complex(pr, bp, tab, scale_in):
+    """The SlotToCoeff groups as complex diagonals, in the order applied; the
+    first carries kappa = (q_0 / (2 pi)) / scale_in."""
+    out = []
+    for gi, grp in enumerate(bp.stc_groups):
+        kappa = stc_kappa(pr.moduli[0], scale_in) if gi == 0 else 1.0
+        out.append(group_diagonals_complex(pr.N, tab, sorted(grp), False, kappa))
+    return out
+
+
 def boot_rotation_steps(pr, bp):
     """Rotation steps of every group (mod n), the conjugation excluded."""
     n = pr.N // 2
@@ -602,6 +669,8 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None, encaps=None):
     x = mod_raise(pr, ct, bp.top)
     if encaps is not None:
         x = key_switch(pr, x, encaps.to_dense)
+    if bp.form == "complex":
+        return _bootstrap_complex(pr, keys, x, bp, tab, scale_in, trace)
     cj = conjugate(pr, keys, x)
     re = ckks.add(pr, x, cj)
     im = mul_monomial(pr, sub(pr, x, cj), pr.N // 2, -1)
@@ -621,3 +690,27 @@ def bootstrap(pr, keys, ct, bp, tab=None, trace=None, encaps=None):
         pair = he_lintrans(pr, keys, pair, d, 1 if gi == len(sds) - 1 else 2,
                            default_n1(len({k[2] for k in d}), bp.baby_ratio), hoist=bp.hoist)
     return pair[0]
+
+
+def _bootstrap_complex(pr, keys, x, bp, tab, scale_in, trace):
+    """The complex form from the raised ciphertext x:
+      CoeffToSlot on x with complex diagonals (slots: (pi / 2^r) R (t_lo + i t_hi) / q_0),
+      re = w + conj(w), im = -X^(N/2) (w - conj(w)) (one conjugation),
+      EvalMod on both, v = e_re + X^(N/2) e_im (slots e_re + i e_im),
+      SlotToCoeff on v with complex diagonals (its real part is the message;
+      the imaginary part is noise)."""
+    n = pr.N // 2
+    for d in cts_diagonals_complex(pr, bp, tab):
+        x = he_lintrans(pr, keys, [x], d, 1, default_n1(len({k[2] for k in d}), bp.baby_ratio), hoist=bp.hoist)[0]
+    if trace is not None:
+        trace["cts"] = x
+    cj = conjugate(pr, keys, x)
+    re = ckks.add(pr, x, cj)
+    im = mul_monomial(pr, sub(pr, x, cj), n, -1)
+    e_re, e_im = eval_mod(pr, keys, re, bp.r), eval_mod(pr, keys, im, bp.r)
+    if trace is not None:
+        trace["evalmod"] = [e_re, e_im]
+    v = ckks.add(pr, e_re, mul_monomial(pr, e_im, n, 1))
+    for d in stc_diagonals_complex(pr, bp, tab, scale_in):
+        v = he_lintrans(pr, keys, [v], d, 1, default_n1(len({k[2] for k in d}), bp.baby_ratio), hoist=bp.hoist)[0]
+    return v

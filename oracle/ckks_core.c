@@ -443,6 +443,77 @@ int or_encode(const double *z, int logN, double scale, i64 *out) {
     return fallbacks;
 }
 
+/* quad-precision value of Delta * (2/N) * sum_l (re_l cos(pi t_l / N) + im_l sin(pi t_l / N)),
+ * t_l = 5^l j mod 2N: the coefficient of the complex slot vector re + i im.  cq as above;
+ * sin(pi t / N) is read as cq[(t + 3N/2) mod 2N] = cos(pi (t - N/2) / N). */
+static __float128 encode_coef_quad_complex(const double *re, const double *im, int logN, double scale, u64 j,
+                                           const __float128 *cq) {
+    u64 N = (u64)1 << logN, twoN = 2 * N;
+    __float128 acc = 0;
+    u64 e = 1;
+    for (u64 l = 0; l < N / 2; l++) {
+        u64 t = (e * j) % twoN;
+        acc += (__float128)re[l] * cq[t] + (__float128)im[l] * cq[(t + 3 * N / 2) % twoN];
+        e = (e * 5) % twoN;
+    }
+    return acc * (__float128)scale * 2 / (__float128)N;
+}
+
+/*
+ * Encode N/2 complex slot values re + i im at scale `scale` into N signed
+ * coefficients: the real polynomial whose value at zeta^(5^l) is scale (re_l + i im_l)
+ * and at the conjugate root its conjugate.  Path: long-double FFT of length 2N
+ * over A with A[5^l] = z_l, A[2N - 5^l] = conj(z_l) (a conjugate-symmetric
+ * sequence, so the transform is real); m_j = scale DFT(A)[j] / N.  The guard band
+ * and the quad fallback are those of or_encode (with |z_l| in the bound).
+ * Returns as or_encode.
+ */
+int or_encode_complex(const double *zr, const double *zi, int logN, double scale, i64 *out) {
+    u64 N = (u64)1 << logN, M = 2 * N;
+    ld *re = calloc(M, sizeof(ld)), *im = calloc(M, sizeof(ld));
+    u64 e = 1;
+    ld l1 = 0;
+    for (u64 l = 0; l < N / 2; l++) {
+        re[e] += zr[l];
+        im[e] += zi[l];
+        re[M - e] += zr[l];
+        im[M - e] -= zi[l];
+        l1 += sqrtl((ld)zr[l] * zr[l] + (ld)zi[l] * zi[l]);
+        e = (e * 5) % M;
+    }
+    fft_ld(re, im, M, -1);
+    ld bound = (ld)scale * 2.0L * l1 / (ld)N;
+    ld guard = bound * (ld)logN * 0x1p-52L;
+    if (guard < 0x1p-30L) guard = 0x1p-30L;
+    int fallbacks = 0;
+    __float128 *cq = NULL;
+    for (u64 j = 0; j < N; j++) {
+        ld v = (ld)scale * re[j] / (ld)N;
+        ld fl = floorl(v);
+        ld frac = v - fl;
+        if (fabsl(frac - 0.5L) < guard) {
+            if (!cq) {
+                cq = malloc(M * sizeof(__float128));
+                for (u64 t = 0; t < M; t++) cq[t] = cosq(M_PIq * (__float128)t / (__float128)N);
+            }
+            __float128 vq = encode_coef_quad_complex(zr, zi, logN, scale, j, cq);
+            __float128 fq = floorq(vq);
+            __float128 fracq = vq - fq;
+            if (fabsq(fracq - 0.5Q) < 0x1p-40Q) { free(re); free(im); free(cq); return -1; }
+            fl = (ld)fq;
+            frac = (ld)fracq;
+            fallbacks++;
+        }
+        ld r = frac > 0.5L ? fl + 1 : fl;
+        if (fabsl(r) > 0x1p62L) { free(re); free(im); free(cq); return -2; }
+        out[j] = (i64)r;
+    }
+    free(re);
+    free(im);
+    free(cq);
+    return fallbacks;
+}
+
 /* Decode N signed coefficients into N/2 slot values:
  * z_l = Re( sum_j m_j zeta^(5^l j) ) / Delta. */
 void or_decode(const i64 *m, int logN, double scale, double *z) {

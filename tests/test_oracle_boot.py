@@ -360,3 +360,67 @@ def test_encapsulated_refresh_with_a_dense_secret():
     # without encapsulation, ModRaise under the dense secret exceeds the sparse secret's bound
     t2 = crt_coef(pr, keys.sk, boot.mod_raise(pr, ct, 6))
     assert max(abs(round((t2[j] - int(m[j])) / q0)) for j in range(pr.N)) > (16 + 1) // 2 + 1
+
+
+@pytest.mark.parametrize("logN", [4, 6, 8])
+def test_complex_encode_matches_the_embedding(logN):
+    """encode_complex(z) is the real polynomial whose slot vector U0 (m_lo + i m_hi)
+    is scale z (within rounding), and equals encode for real z."""
+    N = 1 << logN
+    n = N // 2
+    rng = np.random.default_rng(logN)
+    z = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+    m = C.encode_complex(z, logN, 2.0 ** 30)
+    u = u0_matrix(N) @ (m[:n] + 1j * m[n:]) / 2.0 ** 30
+    assert np.abs(u - z).max() < n * 2.0 ** -30
+    zr = rng.uniform(-1, 1, n)
+    assert np.array_equal(C.encode_complex(zr + 0j, logN, 2.0 ** 40), C.encode(zr, logN, 2.0 ** 40))
+
+
+@pytest.mark.parametrize("logN,groups", [(6, 2), (8, 3)])
+def test_complex_form_diagonals_apply_the_transforms(logN, groups):
+    """The complex-form CoeffToSlot diagonals applied with np.roll to u give
+    (pi / 2^r) R U0^-1 u, and the SlotToCoeff diagonals applied to R v give
+    kappa U0 v."""
+    N = 1 << logN
+    n = N // 2
+    k = n.bit_length() - 1
+    pr = ckks.Params(logN, 18, 1, 50)
+    bp = boot.BootParams(pr, groups, groups, 6, form="complex")
+    tab = boot.cos_table(N)
+    rng = np.random.default_rng(logN + 1)
+
+    def apply(d, v):
+        out = np.zeros(n, dtype=complex)
+        for (o, i, r), dv in d.items():
+            out += dv * np.roll(v, -r)
+        return out
+
+    u = rng.normal(size=n) + 1j * rng.normal(size=n)
+    v = u
+    for d in boot.cts_diagonals_complex(pr, bp, tab):
+        v = apply(d, v)
+    w = np.linalg.solve(u0_matrix(N), u)
+    wb = np.array([w[brv(j, k)] for j in range(n)])
+    assert np.abs(v - math.pi / 2 ** bp.r * wb).max() < 1e-11
+    y = rng.normal(size=n) + 1j * rng.normal(size=n)
+    v = np.array([y[brv(j, k)] for j in range(n)])
+    s_in = 2.0 ** 40
+    for d in boot.stc_diagonals_complex(pr, bp, tab, s_in):
+        v = apply(d, v)
+    want = boot.stc_kappa(pr.moduli[0], s_in) * (u0_matrix(N) @ y)
+    assert np.abs(v - want).max() < 1e-12 * np.abs(want).max() * n
+
+
+def test_bootstrap_complex_form_refreshes_the_message(small):
+    """The complex form (transforms on one ciphertext, the split after
+    CoeffToSlot) returns the message at the same level as the real form."""
+    pr, _, keys = small
+    bp = boot.BootParams(pr, 3, 3, 6, form="complex")
+    for st in boot.boot_rotation_steps(pr, bp):
+        keys.add_rotation(st)
+    z = np.random.default_rng(16).uniform(-1, 1, pr.N // 2)
+    ct = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z, 0, 2.0 ** 45), 18, 0)
+    out = boot.bootstrap(pr, keys, ct, bp)
+    assert out.level == pr.L - 17
+    assert np.abs(ckks.decrypt(pr, keys.sk, out) - z).max() < 4e-4
