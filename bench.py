@@ -350,7 +350,7 @@ def cpu_oracle_all_cores(n_rot_each, max_workers=64):
 def refresh_bench(torch, stream, steps):
     """Time fe_he_bootstrap at N = 2^16 (24 x 50-bit primes, 4 special primes,
     secret weight 64; CoeffToSlot 3 levels, EvalMod 11, SlotToCoeff 3; stage
-    groups with n1^2 >= 4 x their offsets, double-hoisted) on one level-0
+    groups with n1^2 >= 4 x their offsets, double-hoisted, complex form) on one level-0
     ciphertext; report ms, levels, key switches and the decrypted error."""
     import paper_2606_16359_b300 as fe
     with torch.cuda.stream(stream):
@@ -390,7 +390,7 @@ def refresh_bench(torch, stream, steps):
         bfly_rate = limb_passes * (ctx.N // 2) * (ctx.logN / 2) / (t_ntt / 1e3) / 1e9 if t_ntt else 0.0
         bfly_peak = butterfly_roof(ctx, torch)
     ks = cnt["keyswitch"] / steps
-    res = {"ms": round(ms, 3), "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64, groups 3/11/3 levels, baby ratio 4, double hoisting",
+    res = {"ms": round(ms, 3), "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64, groups 3/11/3 levels, baby ratio 4, double hoisting, complex form",
            "levels_used": 23 - b.out_level, "out_level": b.out_level, "keyswitches": ks,
            "keyswitch_per_s": ks / (ms / 1e3), "max_abs_err": err,
            "evk_gb": evk.buf.numel() * 8 / 1e9, "workspace_gb": ws.numel() * 8 / 1e9,

@@ -873,10 +873,14 @@ int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* by
  * values trade giant-step rotations, each with its own ModUp, for hoisted
  * baby steps); double_hoist: 1 keeps every group's baby rotations on Q * P
  * and takes one ModDown per (output, giant step) sum (fe_plan_set_hoisting 1),
- * 0 a ModDown per rotation.  The refresh needs n_cts + 5 + r + n_stc <= top and
- * returns at level top - that depth. */
+ * 0 a ModDown per rotation; form: 0 runs the transforms on the pair (re, im)
+ * of real-slot ciphertexts with real diagonals (the output has real slots), 1 on
+ * one ciphertext with complex diagonals (half the rotations; the real and
+ * imaginary parts are split after CoeffToSlot by one conjugation and joined
+ * before SlotToCoeff; the output's imaginary parts are noise).  The refresh
+ * needs n_cts + 5 + r + n_stc <= top and returns at level top - that depth. */
 typedef struct {
-    uint32_t n_cts, n_stc, r, top, baby_ratio, double_hoist;
+    uint32_t n_cts, n_stc, r, top, baby_ratio, double_hoist, form;
 } fe_boot_params;
 
 /* Sparse ternary secret of Hamming weight h (h distinct positions with signs

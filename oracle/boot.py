@@ -580,7 +580,7 @@ class BootParams:
     the pair (re, im) in real form) or "complex" (on one ciphertext with complex
     diagonals, the real and imaginary parts split after CoeffToSlot)."""
 
-    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=4, double_hoist=True, form="real"):
+    def __init__(self, pr, n_cts=3, n_stc=3, r=6, top=None, baby_ratio=4, double_hoist=True, form="complex"):
         if form not in ("real", "complex"):
             raise ValueError("form must be 'real' or 'complex'")
         self.form = form

@@ -34,7 +34,7 @@ class FeParams(ctypes.Structure):
 
 class FeBootParams(ctypes.Structure):
     _fields_ = [("n_cts", u32), ("n_stc", u32), ("r", u32), ("top", u32), ("baby_ratio", u32),
-                ("double_hoist", u32)]
+                ("double_hoist", u32), ("form", u32)]
 
 
 class FeLayout(ctypes.Structure):
@@ -572,9 +572,11 @@ class Context:
                                     _ptr(ws), ws.numel() * 8, _stream()))
         return out
 
-    def boot_create(self, scale_in, n_cts=3, n_stc=3, r=6, top=0, baby_ratio=4, double_hoist=True):
-        """A ciphertext refresh (fe_boot_create) for level-0 inputs at scale_in."""
-        prm = FeBootParams(n_cts, n_stc, r, top, baby_ratio, 1 if double_hoist else 0)
+    def boot_create(self, scale_in, n_cts=3, n_stc=3, r=6, top=0, baby_ratio=4, double_hoist=True, form="complex"):
+        """A ciphertext refresh (fe_boot_create) for level-0 inputs at scale_in
+        (form: "real" or "complex", see fe_boot_params)."""
+        prm = FeBootParams(n_cts, n_stc, r, top, baby_ratio, 1 if double_hoist else 0,
+                           {"real": 0, "complex": 1}[form])
         h = vp()
         check(load().fe_boot_create(self.handle, ctypes.byref(prm), scale_in, _stream(), ctypes.byref(h)))
         return Boot(self, h, scale_in)

@@ -40,6 +40,7 @@ double boot_cos_pi_table_entry(int N, int e);  // boot_tables.cpp
 struct fe_boot {
     fe_ctx* c = nullptr;
     int n_cts = 0, n_stc = 0, r = 0, top = 0, depth = 0;
+    int form = 0;  // 0: transforms on the pair (re, im) in real form; 1: on one ciphertext, complex diagonals
     double scale_in = 0, out_scale = 0;
     std::vector<std::unique_ptr<fe_plan>> plans;  // CoeffToSlot groups, then SlotToCoeff groups (order applied)
     std::vector<u64*> pts;                        // their compact plaintexts (owned)
@@ -106,6 +107,20 @@ __global__ void k_boot_parts(const u64* x, const u64* cj, const u64* mono, u64* 
     const u64 a = x[o], b = cj[o];
     pair[((size_t)(2 * z) * 2 * nl + limb) * N + n] = add_mod(a, b, m.q);
     pair[((size_t)(2 * z + 1) * 2 * nl + limb) * N + n] = mul_mod(sub_mod(a, b, m.q), mono[(size_t)i * N + n], m);
+}
+
+// complex form: v[z] = e[2z] + X^(N/2) e[2z+1] = e[2z] - mono e[2z+1] (slots e_re + i e_im),
+// z over n ciphertexts at nl limbs, mono = NTT(-X^(N/2))
+__global__ void k_boot_join(const u64* e, const u64* mono, u64* v, const Modulus* mods, int nl, int logN) {
+    const int N = 1 << logN;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int limb = blockIdx.y, z = blockIdx.z;  // limb over 2 nl
+    const int i = limb % nl;
+    const Modulus m = mods[i];
+    const u64 a = e[((size_t)(2 * z) * 2 * nl + limb) * N + n];
+    const u64 b = e[((size_t)(2 * z + 1) * 2 * nl + limb) * N + n];
+    v[((size_t)z * 2 * nl + limb) * N + n] = sub_mod(a, mul_mod(b, mono[(size_t)i * N + n], m), m.q);
 }
 
 // ---------------------------------------------------------------------------
@@ -278,16 +293,19 @@ int plan_lintrans(fe_ctx* c, int n_in, int n_out, const std::vector<LtDiag>& d, 
 // plaintext k = diagonal pt_src[k].first rotated by -giant, encoded at w_scale
 // on q_0..q_level (and p_0..p_{k-1} when the plan is double-hoisted) and stored
 // compact at pt_dev
+// (diag_im: imaginary parts of complex diagonals, or null for real ones)
 int load_lintrans(fe_ctx* c, const fe_plan* p, const std::vector<std::pair<int, int32_t>>& pt_src,
-                  const std::vector<const double*>& diag_vals, double w_scale, void* pt_dev, cudaStream_t st) {
+                  const std::vector<const double*>& diag_vals, double w_scale, void* pt_dev, cudaStream_t st,
+                  const std::vector<const double*>* diag_im = nullptr) {
     const int N = c->N, n = N / 2, nl = p->level + 1 + (p->dhoist ? c->k : 0);
     const int chunk = std::max(1, std::min({p->n_pt, (int)((64ull << 20) / ((size_t)n * 8)),
                                             (int)((1ull << 30) / ((size_t)nl * N * 8))}));
-    double* z;
+    double *z, *zi = nullptr;
     u64* limbs;
     FE_CUDA_TRY(cudaMallocAsync(&z, (size_t)chunk * n * 8, st));
+    if (diag_im) FE_CUDA_TRY(cudaMallocAsync(&zi, (size_t)chunk * n * 8, st));
     FE_CUDA_TRY(cudaMallocAsync(&limbs, (size_t)chunk * nl * N * 8, st));
-    std::vector<double> host((size_t)chunk * n);
+    std::vector<double> host((size_t)chunk * n), host_im(diag_im ? (size_t)chunk * n : 0);
     int rc = FE_OK;
     for (int s0 = 0; s0 < p->n_pt && rc == FE_OK; s0 += chunk) {
         const int cn = std::min(chunk, p->n_pt - s0);
@@ -296,13 +314,20 @@ int load_lintrans(fe_ctx* c, const fe_plan* p, const std::vector<std::pair<int, 
             const int64_t g = pt_src[s0 + k].second;
             double* dst = host.data() + (size_t)k * n;
             for (int l = 0; l < n; l++) dst[l] = v[(((l - g) % n) + n) % n];  // Rot(d, -g)
+            if (diag_im) {
+                const double* vi = (*diag_im)[pt_src[s0 + k].first];
+                double* di = host_im.data() + (size_t)k * n;
+                for (int l = 0; l < n; l++) di[l] = vi[(((l - g) % n) + n) % n];
+            }
         }
         FE_CUDA_TRY(cudaMemcpyAsync(z, host.data(), (size_t)cn * n * 8, cudaMemcpyHostToDevice, st));
-        rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, p->dhoist != 0);
+        if (diag_im) FE_CUDA_TRY(cudaMemcpyAsync(zi, host_im.data(), (size_t)cn * n * 8, cudaMemcpyHostToDevice, st));
+        rc = encode_batch(c, z, cn, p->level, w_scale, limbs, st, p->dhoist != 0, zi);
         if (rc == FE_OK) launch_pt_compact(c, limbs, (uint8_t*)pt_dev + (size_t)s0 * nl * pt_limb_bytes(c), cn * nl, st);
         FE_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging buffer is refilled next
     }
     cudaFreeAsync(z, st);
+    if (zi) cudaFreeAsync(zi, st);
     cudaFreeAsync(limbs, st);
     FE_CUDA_TRY(cudaStreamSynchronize(st));
     return rc;
@@ -407,8 +432,11 @@ int default_n1(size_t n_offsets, uint32_t ratio = 1) {
 // (re', im') = (Re G re - Im G im, Im G re + Re G im), for parts = 1 re' only;
 // d_r[o] = G[o][(o + r) mod n] = sign 2^-halvings cis(pi e / N), times kappa in
 // one IEEE product when kappa != 1; all-zero vectors are left out.
+// parts = 0: the complex form, one diagonal (0, 0, r) per offset with its real
+// parts in vals and imaginary parts in vals_im (left out when both are zero).
 void group_diagonals(int N, const Trig& tr, const std::vector<int>& stages, bool inverse, double kappa, int parts,
-                     std::vector<LtDiag>& diags, std::vector<std::vector<double>>& vals) {
+                     std::vector<LtDiag>& diags, std::vector<std::vector<double>>& vals,
+                     std::vector<std::vector<double>>* vals_im = nullptr) {
     const int n = N / 2;
     int bits = 0;
     for (int s : stages) bits |= 1 << (s - 1);
@@ -447,6 +475,14 @@ void group_diagonals(int N, const Trig& tr, const std::vector<int>& stages, bool
                 if (a != 0.0) return true;
             return false;
         };
+        if (parts == 0) {
+            if (nonzero(re) || nonzero(im)) {
+                diags.push_back({0, 0, r});
+                vals.push_back(re);
+                vals_im->push_back(im);
+            }
+            continue;
+        }
         std::vector<double> nim(n);
         for (int o = 0; o < n; o++) nim[o] = -im[o];
         const std::vector<std::pair<std::pair<int, int>, const std::vector<double>*>> cand =
@@ -641,12 +677,47 @@ int boot_run(fe_ctx* c, const fe_evk* evk, const fe_boot* b, const u64* in, int 
     } else {
         mod_raise(c, in, R, top, raised, tmp, st);
     }
+    const size_t shared_bytes = std::max(plan_ws, ev_ws);
+    if (b->form == 1) {
+        // complex form: CoeffToSlot on the raised ciphertexts, the split at lv0,
+        // EvalMod, the join, SlotToCoeff (every transform one in, one out)
+        u64* x = raised;
+        int pi = 0;
+        for (; pi < b->n_cts; pi++) {
+            u64* dst = x == pa ? pb : pa;
+            FE_TRY(run_plan(c, evk, b->plans[pi].get(), x, b->pts[pi], dst, shared, shared_bytes, 1, st, 3, R));
+            x = dst;
+        }
+        FE_TRY(conjugate_batch(c, evk, x, R, lv0, cj, cs, st));
+        u64* pair = x == pa ? pb : pa;
+        k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (lv0 + 1), R), kB, 0, st>>>(x, cj, b->mono, pair, c->d_mod,
+                                                                              lv0 + 1, c->logN);
+        c->cnt.launches++;
+        FE_CUDA_TRY(cudaGetLastError());
+        EvCtx e{c, evk, 2 * R, st, nullptr, shared, shared_bytes};
+        Ev xe{pair, lv0, (double)c->mod[0]}, y{};
+        FE_TRY(eval_mod(e, xe, b->r, bufs, y));
+        if (y.scale != b->out_scale || y.level != top - b->n_cts - 5 - b->r)
+            return fail(FE_EINVAL, "bootstrap: EvalMod scale bookkeeping disagrees with the plan");
+        u64* v = x;  // the CoeffToSlot output is no longer needed
+        k_boot_join<<<dim3((N + kB - 1) / kB, 2 * (y.level + 1), R), kB, 0, st>>>(y.p, b->mono, v, c->d_mod,
+                                                                                 y.level + 1, c->logN);
+        c->cnt.launches++;
+        FE_CUDA_TRY(cudaGetLastError());
+        u64* cur = v;
+        for (; pi < (int)b->plans.size(); pi++) {
+            const bool last = pi + 1 == (int)b->plans.size();
+            u64* dst = last ? out : (cur == pa ? pb : pa);
+            FE_TRY(run_plan(c, evk, b->plans[pi].get(), cur, b->pts[pi], dst, shared, shared_bytes, 1, st, 3, R));
+            cur = dst;
+        }
+        return FE_OK;
+    }
     FE_TRY(conjugate_batch(c, evk, raised, R, top, cj, cs, st));
     k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (top + 1), R), kB, 0, st>>>(raised, cj, b->mono, pa, c->d_mod, top + 1,
                                                                           c->logN);
     c->cnt.launches++;
     FE_CUDA_TRY(cudaGetLastError());
-    const size_t shared_bytes = std::max(plan_ws, ev_ws);
     int pi = 0;
     for (; pi < b->n_cts; pi++) {
         FE_TRY(run_plan(c, evk, b->plans[pi].get(), pa, b->pts[pi], pb, shared, shared_bytes, 1, st, 3, R));
@@ -784,6 +855,8 @@ extern "C" int fe_boot_create(fe_ctx* c, const fe_boot_params* prm, double scale
     b->top = top;
     b->depth = n_cts + 5 + r + n_stc;
     b->scale_in = scale_in;
+    if (prm->form > 1) return fail(FE_EINVAL, "bootstrap form must be 0 (real) or 1 (complex)");
+    b->form = (int)prm->form;
     const Trig tr(N);
     auto groups_cts = stage_groups(k, n_cts);
     std::reverse(groups_cts.begin(), groups_cts.end());  // applied from the top stages down
@@ -794,28 +867,30 @@ extern "C" int fe_boot_create(fe_ctx* c, const fe_boot_params* prm, double scale
         std::sort(stages.begin(), stages.end());
         if (inverse) std::reverse(stages.begin(), stages.end());  // S_hi^-1 meets the vector first
         std::vector<LtDiag> d;
-        std::vector<std::vector<double>> vals;
-        group_diagonals(N, tr, stages, inverse, kappa, parts, d, vals);
+        std::vector<std::vector<double>> vals, vals_im;
+        group_diagonals(N, tr, stages, inverse, kappa, parts, d, vals, &vals_im);
         std::unique_ptr<fe_plan> p;
         std::vector<std::pair<int, int32_t>> src;
-        FE_TRY(plan_lintrans(c, 2, parts, d, default_n1(group_offsets(stages, n).size(), prm->baby_ratio), level, p,
-                             src));
+        // real form: the pair (re, im) in, parts out; complex form (parts 0): one in, one out
+        FE_TRY(plan_lintrans(c, parts ? 2 : 1, parts ? parts : 1, d,
+                             default_n1(group_offsets(stages, n).size(), prm->baby_ratio), level, p, src));
         for (int32_t s : p->steps) steps.insert(((s % n) + n) % n);
         p->dhoist = prm->double_hoist ? 1 : 0;
-        std::vector<const double*> vp(vals.size());
+        std::vector<const double*> vp(vals.size()), vpi(vals_im.size());
         for (size_t i = 0; i < vals.size(); i++) vp[i] = vals[i].data();
+        for (size_t i = 0; i < vals_im.size(); i++) vpi[i] = vals_im[i].data();
         const size_t nl = (size_t)level + 1 + (p->dhoist ? c->k : 0);
         u64* pt;
         FE_CUDA_TRY(cudaMalloc(&pt, std::max<size_t>(16, (size_t)p->n_pt * nl * pt_limb_bytes(c))));
         b->pts.push_back(pt);
-        FE_TRY(load_lintrans(c, p.get(), src, vp, (double)c->mod[level], pt, st));
+        FE_TRY(load_lintrans(c, p.get(), src, vp, (double)c->mod[level], pt, st, parts ? nullptr : &vpi));
         p->w_scale = (double)c->mod[level];
         b->plans.push_back(std::move(p));
         return FE_OK;
     };
     int level = top;
     for (size_t gi = 0; gi < groups_cts.size(); gi++, level--)
-        FE_TRY(add_group(groups_cts[gi], true, gi == 0 ? std::ldexp(M_PI, -r) : 1.0, 2, level));
+        FE_TRY(add_group(groups_cts[gi], true, gi == 0 ? std::ldexp(M_PI, -r) : 1.0, b->form ? 0 : 2, level));
     // EvalMod: 5 + r levels; its output scale follows from the declared scales
     {
         const int lv0 = level;
@@ -832,8 +907,8 @@ extern "C" int fe_boot_create(fe_ctx* c, const fe_boot_params* prm, double scale
     }
     const double kappa_stc = ((double)c->mod[0] / (2.0 * M_PI)) / scale_in;
     for (size_t gi = 0; gi < groups_stc.size(); gi++, level--)
-        FE_TRY(add_group(groups_stc[gi], false, gi == 0 ? kappa_stc : 1.0, gi + 1 == groups_stc.size() ? 1 : 2,
-                         level));
+        FE_TRY(add_group(groups_stc[gi], false, gi == 0 ? kappa_stc : 1.0,
+                         b->form ? 0 : (gi + 1 == groups_stc.size() ? 1 : 2), level));
     // -X^(N/2) on q_0..q_top, NTT form
     {
         i64* v;

@@ -142,8 +142,9 @@ void ntt_inverse_from(fe_ctx* c, const u64* src, size_t src_stride, const LimbSe
 
 int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st);
 // qp: the plaintexts on Q_level * P (l+1+k limbs in key-switching order) instead of Q_level
+// slots_im (optional): imaginary parts of complex slot values ([n][N/2])
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
-                 cudaStream_t st, bool qp = false);
+                 cudaStream_t st, bool qp = false, const double* slots_im = nullptr);
 int decode_batch(fe_ctx* c, const double* mdd, int n, double scale, double* slots, cudaStream_t st);
 
 // Records CUDA events around one launch when its kernel class is being profiled,

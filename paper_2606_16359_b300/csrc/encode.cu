@@ -1,6 +1,7 @@
 // Canonical-embedding encode / decode in double-double arithmetic.
 //
 // For real slot values z_l (slot l <-> root zeta^(e_l), e_l = 5^l mod 2N,
+// complex values: z_l at e_l and its conjugate at 2N - e_l in G below;
 // zeta = exp(i pi / N)) the encoded coefficients are
 //   m_j = round( Delta * (2/N) * sum_l z_l cos(pi e_l j / N) ).
 // Written over the odd exponents e = 2t + 1 (each slot appears at e_l and at
@@ -75,13 +76,17 @@ __device__ __forceinline__ cdd root(const double* w, int j, int sign) {
 
 __device__ __forceinline__ int brv(int x, int logN) { return (int)(__brev((unsigned)x) >> (32 - logN)); }
 
-// X[n][brv(t)] = G[t] = z[n][slot(2t+1)]
-__global__ void k_enc_scatter(const double* z, const int* t2slot, cdd* X, int logN) {
+// X[n][brv(t)] = G[t] = z[n][slot(2t+1)], and with imaginary parts zi the
+// complex slot value, conjugated where 2t + 1 is the conjugate root 2N - 5^l
+// (t odd: 5^l = 1 mod 4 while 2N - 5^l = 3 mod 4)
+__global__ void k_enc_scatter(const double* z, const double* zi, const int* t2slot, cdd* X, int logN) {
     const int N = 1 << logN;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
-    const double v = z[(size_t)blockIdx.y * (N / 2) + t2slot[t]];
-    X[(size_t)blockIdx.y * N + brv(t, logN)] = {{v, 0.0}, {0.0, 0.0}};
+    const size_t si = (size_t)blockIdx.y * (N / 2) + t2slot[t];
+    const double v = z[si];
+    const double vi = zi ? ((t & 1) ? -zi[si] : zi[si]) : 0.0;
+    X[(size_t)blockIdx.y * N + brv(t, logN)] = {{v, 0.0}, {vi, 0.0}};
 }
 
 // one radix-2 DIT stage of span 2^s: X[a] +- w^k X[b], w = exp(sign 2 pi i / 2^s)
@@ -149,7 +154,7 @@ __global__ void k_dec_gather(const cdd* F, const int* slot2t, double inv_scale, 
 }  // namespace
 
 int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale, u64* pt,
-                 cudaStream_t st, bool qp) {
+                 cudaStream_t st, bool qp, const double* slots_im) {
     if (n <= 0) return FE_OK;
     const int N = c->N, logN = c->logN;
     // process in chunks so that the complex double-double scratch stays bounded
@@ -163,8 +168,8 @@ int encode_batch(fe_ctx* c, const double* slots, int n, int level, double scale,
     const int* mod_map = qp ? c->lv[level].d_ks_limbs : c->d_identity_map;
     for (int s0 = 0; s0 < n; s0 += chunk) {
         int cn = std::min(chunk, n - s0);
-        k_enc_scatter<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(slots + (size_t)s0 * (N / 2),
-                                                                c->d_t2slot, X, logN);
+        k_enc_scatter<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(
+            slots + (size_t)s0 * (N / 2), slots_im ? slots_im + (size_t)s0 * (N / 2) : nullptr, c->d_t2slot, X, logN);
         for (int s = 1; s <= logN; s++)
             k_fft_stage<<<dim3((N / 2 + 255) / 256, cn), 256, 0, st>>>(X, c->d_dd_w, logN, s, -1);
         k_enc_round<<<dim3((N + 255) / 256, cn), 256, 0, st>>>(X, c->d_dd_w, scale, logN, c->d_mod, mod_map,

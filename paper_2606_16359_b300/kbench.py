@@ -337,7 +337,7 @@ def bench_refresh(ctx_unused, torch, args):
     sk = ctx.sk_gen_sparse(31, 64)
     s_in = 2.0 ** 45
     b = ctx.boot_create(s_in, args.n_cts, args.n_stc, args.double_angles, baby_ratio=args.baby_ratio,
-                        double_hoist=args.double_hoist)
+                        double_hoist=args.double_hoist, form=args.form)
     evk = ctx.evk_gen(sk, 31, b.steps, relin=True)
     z = np.random.default_rng(9).uniform(-1, 1, (args.n_ct, ctx.N // 2))
     ct = ctx.encrypt(sk, z, 0, s_in, seed=10)
@@ -362,7 +362,7 @@ def bench_refresh(ctx_unused, torch, args):
     ctx.probe_butterflies(probe, 1, 1)
     torch.cuda.synchronize()
     err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
-    return {"what": "refresh", "n_ct": args.n_ct, "ms_per_ct": ms / args.n_ct,
+    return {"what": "refresh", "form": args.form, "n_ct": args.n_ct, "ms_per_ct": ms / args.n_ct,
             "groups": [args.n_cts, args.n_stc], "double_angles": args.double_angles,
             "levels_used": 23 - b.out_level, "baby_ratio": args.baby_ratio, "double_hoist": args.double_hoist, "ms": ms, "reps": args.reps,
             "out_level": b.out_level, "max_abs_err": err, "rotation_keys": len(b.steps),
@@ -394,6 +394,7 @@ def main(argv=None):
     ap.add_argument("--n-stc", type=int, default=3, help="refresh: SlotToCoeff stage groups (levels)")
     ap.add_argument("--double-angles", type=int, default=6, help="refresh: EvalMod double angles")
     ap.add_argument("--n-ct", type=int, default=1, help="refresh: ciphertexts refreshed in one call")
+    ap.add_argument("--form", default="complex", choices=["real", "complex"], help="refresh: transform form")
     args = ap.parse_args(argv)
     import torch
 

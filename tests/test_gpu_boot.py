@@ -124,17 +124,18 @@ def test_refresh_bit_exact_against_the_oracle(small):
     assert np.abs(dec - z).max() < 1e-4
 
 
-def test_refresh_full_size():
+@pytest.mark.parametrize("form", ["real", "complex"])
+def test_refresh_full_size(form):
     """N = 2^16 with 24 primes of 50 bits and 4 special primes, secret weight 64:
-    the refresh returns at level 23 - 17 = 6 with every slot within 1e-3 of the
-    message (decrypted on the GPU), and its time is reported."""
+    the refresh (both forms) returns at level 23 - 17 = 6 with every slot within
+    1e-3 of the message (decrypted on the GPU), and its time is reported."""
     logN, n_q, k, bits = 16, 24, 4, 50
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = fe.Context(logN, n_q, k, bits)
         sk = ctx.sk_gen_sparse(21, 64)
         s_in = 2.0 ** 45
-        b = ctx.boot_create(s_in, 3, 3, 6)
+        b = ctx.boot_create(s_in, 3, 3, 6, form=form)
         evk = ctx.evk_gen(sk, 21, b.steps, relin=True)
         rng = np.random.default_rng(4)
         z = rng.uniform(-1, 1, (1, ctx.N // 2))
@@ -151,25 +152,27 @@ def test_refresh_full_size():
         dec = ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy()
     assert b.out_level == 6
     err = float(np.abs(dec - z).max())
-    print(f"refresh N=2^16: {t0.elapsed_time(t1) / 3:.2f} ms, max error {err:.2e}")
+    print(f"refresh N=2^16 ({form} form): {t0.elapsed_time(t1) / 3:.2f} ms, max error {err:.2e}")
     assert err < 1e-3
 
 
-@pytest.mark.parametrize("groups,r,ratio,double", [(3, 6, 1, False), (3, 6, 2, False), (2, 5, 4, True)])
-def test_refresh_schedules_bit_exact(small, groups, r, ratio, double):
+@pytest.mark.parametrize("groups,r,ratio,double,form", [(3, 6, 1, False, "real"), (3, 6, 2, False, "real"),
+                                                      (2, 5, 4, True, "real"), (3, 6, 4, True, "complex"),
+                                                      (2, 5, 4, True, "complex"), (3, 6, 1, False, "complex")])
+def test_refresh_schedules_bit_exact(small, groups, r, ratio, double, form):
     """Other baby / giant splits (n1^2 >= ratio x the offsets of each group),
     single-hoisted groups, and the 14-level refresh (two groups each way, five
     double angles) change every group's composition; the residues still equal
     the oracle's."""
     pr, bp, ctx, sk, keys, s = small
-    bp2 = boot.BootParams(pr, groups, groups, r, baby_ratio=ratio, double_hoist=double)
+    bp2 = boot.BootParams(pr, groups, groups, r, baby_ratio=ratio, double_hoist=double, form=form)
     for st in boot.boot_rotation_steps(pr, bp2):
         keys.add_rotation(st)
     s_in = 2.0 ** 45
     z = np.random.default_rng(8).uniform(-1, 1, (1, pr.N // 2))
     oct_ = ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[0], 0, s_in), 9, 0)
     with torch.cuda.stream(s):
-        b = ctx.boot_create(s_in, groups, groups, r, baby_ratio=ratio, double_hoist=double)
+        b = ctx.boot_create(s_in, groups, groups, r, baby_ratio=ratio, double_hoist=double, form=form)
         assert sorted(x for x in b.steps if x != fe.FE_STEP_CONJ) == boot.boot_rotation_steps(pr, bp2)
         evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
         got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))

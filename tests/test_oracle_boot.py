@@ -412,11 +412,12 @@ def test_complex_form_diagonals_apply_the_transforms(logN, groups):
     assert np.abs(v - want).max() < 1e-12 * np.abs(want).max() * n
 
 
-def test_bootstrap_complex_form_refreshes_the_message(small):
-    """The complex form (transforms on one ciphertext, the split after
-    CoeffToSlot) returns the message at the same level as the real form."""
+def test_bootstrap_real_form_refreshes_the_message(small):
+    """The real form (transforms on the pair (re, im) of real-slot ciphertexts,
+    the split before CoeffToSlot) returns the message at the same level as the
+    complex form (the default)."""
     pr, _, keys = small
-    bp = boot.BootParams(pr, 3, 3, 6, form="complex")
+    bp = boot.BootParams(pr, 3, 3, 6, form="real")
     for st in boot.boot_rotation_steps(pr, bp):
         keys.add_rotation(st)
     z = np.random.default_rng(16).uniform(-1, 1, pr.N // 2)
