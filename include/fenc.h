@@ -861,10 +861,11 @@ int fe_profile_end(fe_ctx* ctx, double* total_ms, uint64_t* launches, double* by
  * print its steps.  The library implements the standard CKKS refresh for its
  * real-slot encoding: ModRaise, CoeffToSlot (the special FFT's inverse stages
  * in n_cts groups, one level each), EvalMod (a degree-16 Taylor cosine and r
- * double angles, 5 + r levels) and SlotToCoeff (n_stc groups), on a context
- * whose secret is sparse (fe_sk_gen_sparse).  All buffers are device memory in
- * the ciphertext layout [n][2][level+1][N] unless stated; the library never
- * frees caller buffers. */
+ * double angles, 5 + r levels) and SlotToCoeff (n_stc groups).  ModRaise needs
+ * a sparse secret (fe_sk_gen_sparse): either the context's secret, or one the
+ * refresh borrows from a network with a dense secret (fe_boot_encapsulate).
+ * All buffers are device memory in the ciphertext layout [n][2][level+1][N]
+ * unless stated; the library never frees caller buffers. */
 
 /* n_cts / n_stc: stage groups of CoeffToSlot / SlotToCoeff (1..log2(N/2));
  * r: double angles (1..16); top: level after ModRaise (0: L); baby_ratio: every
@@ -945,6 +946,7 @@ int fe_boot_create(fe_ctx* ctx, const fe_boot_params* params, double scale_in, v
 int fe_boot_rotation_steps(const fe_boot* boot, int32_t* steps, uint32_t max, uint32_t* n);
 /* Level and declared scale of the refresh's outputs. */
 int fe_boot_output(const fe_boot* boot, uint32_t* level, double* scale);
+/* Device workspace of fe_he_bootstrap for n_ct ciphertexts (0 for n_ct = 0). */
 size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
 /* Refresh n_ct level-0 ciphertexts (declared scale scale_in) into out_dev at
  * fe_boot_output's level; the outputs decrypt to the inputs' slot values.
@@ -952,13 +954,17 @@ size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
 int fe_he_bootstrap(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
                     void* out_dev, void* ws, size_t ws_bytes, void* stream);
 /* Switching key from secret sk_src to secret sk_dst (both [n_mod][N], NTT
- * form), random streams of object tag `obj` (rotation keys use their Galois
- * element, the relinearisation key 0), in the layout of one rotation key:
- * key_bytes >= fe_evk_bytes(ctx, 1, 0).  Synchronises `stream`. */
+ * form) for the hybrid key switch that rotations use (Eq. 1's KS), random
+ * streams of object tag `obj` (rotation keys use their Galois element, the
+ * relinearisation key 0), in the layout of one rotation key into caller-owned
+ * key_dev: key_bytes >= fe_evk_bytes(ctx, 1, 0).  Synchronises `stream`.
+ * Errors: FE_EINVAL (null or misaligned pointer), FE_ENOMEM (key_bytes). */
 int fe_swk_gen(fe_ctx* ctx, const void* sk_src, const void* sk_dst, uint64_t seed, uint32_t obj, void* key_dev,
                size_t key_bytes, void* stream);
-/* Hybrid key switch of n_ct ciphertexts at `level` from the key's source secret
- * to its destination secret: (c0 + d0, d1), (d0, d1) = KS(c1) (not in place). */
+/* Hybrid key switch (Eq. 1's KS without the automorphism) of n_ct ciphertexts
+ * at `level` from the key's source secret to its destination secret:
+ * (c0 + d0, d1), (d0, d1) = KS(c1).  Scratch from the stream-ordered allocator.
+ * Errors: FE_EINVAL (null pointer, in place), FE_ELEVEL (level > L). */
 int fe_key_switch(fe_ctx* ctx, const void* key_dev, const void* ct_dev, uint32_t n_ct, uint32_t level,
                   void* out_dev, void* stream);
 /* Sparse-secret encapsulation: the network keeps its dense secret sk_dense (the
@@ -967,7 +973,9 @@ int fe_key_switch(fe_ctx* ctx, const void* key_dev, const void* ct_dev, uint32_t
  * dense -> sparse (object 2N) and sparse -> dense (object 2N + 2) into keys_dev
  * (2 x fe_evk_bytes(ctx, 1, 0) bytes, caller-owned, must outlive the boot) and
  * makes fe_he_bootstrap switch its level-0 inputs to the sparse secret, raise
- * them and switch them back at level top (two key switches more). */
+ * them and switch them back at level top (two key switches more).
+ * Synchronises `stream`.  Errors: FE_EINVAL (null pointer, another context's
+ * boot), FE_ENOMEM (keys_bytes). */
 int fe_boot_encapsulate(fe_ctx* ctx, fe_boot* boot, const void* sk_dense, const void* sk_sparse, uint64_t seed,
                         void* keys_dev, size_t keys_bytes, void* stream);
 /* Bring n_ct ciphertexts at `level` >= 1 with declared scale in_scale to the
