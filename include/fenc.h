@@ -781,9 +781,10 @@ typedef struct {
 
 typedef struct {
     uint64_t submitted, completed, rejected, groups, max_group;
-    uint64_t max_inflight;  /* most groups whose device intervals overlapped (each from the
-                               moment its stream starts the input copies to its completion,
-                               timed with CUDA events) */
+    uint64_t max_inflight;  /* peak concurrency: the most groups whose device intervals (each
+                               from the moment its stream starts the input copies to its
+                               completion, timed with CUDA events) held one instant; at most
+                               the configured max_inflight */
     size_t peak_bytes, budget_bytes;
     double p50_ms, p99_ms, mean_ms, wall_s;  /* latency: submit -> result in the host buffer */
 } fe_server_stats_t;

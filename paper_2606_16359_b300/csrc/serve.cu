@@ -199,10 +199,19 @@ void fe_server::loop() {
             if (e == cudaSuccess && cudaEventElapsedTime(&t_s, epoch, g.start) == cudaSuccess &&
                 cudaEventElapsedTime(&t_e, epoch, g.done) == cudaSuccess) {
                 intervals.push_back({t_s, t_e});
-                // groups whose device intervals overlapped this one's
-                uint64_t over = 1;
+                // peak concurrency: the most intervals that hold one instant.  A
+                // largest set of pairwise-overlapping intervals all hold the latest
+                // start among them, so the starts that fall inside this interval
+                // (its own included) are the only instants to count; the set is
+                // found when its last member retires.
+                auto held = [&](float p) {
+                    uint64_t k = 0;
+                    for (const auto& iv : intervals) k += iv.first <= p && p < iv.second;
+                    return k;
+                };
+                uint64_t over = std::max<uint64_t>(1, held(t_s));
                 for (const auto& iv : intervals)
-                    if (&iv != &intervals.back() && iv.first < t_e && t_s < iv.second) over++;
+                    if (iv.first > t_s && iv.first < t_e) over = std::max(over, held(iv.first));
                 max_inflight_seen = std::max(max_inflight_seen, over);
                 if (intervals.size() > 4096) intervals.erase(intervals.begin(), intervals.begin() + 2048);
             }

@@ -96,7 +96,7 @@ def test_alone_equals_mix_and_decrypts(models):
         assert np.array_equal(out.numpy(), alone[k]), k
     assert stats["completed"] == len(kinds) and stats["rejected"] == 0
     assert stats["max_group"] >= 2, stats        # requests of one model were batched
-    assert stats["max_inflight"] >= 2, stats     # groups of both models overlapped on the device
+    assert 2 <= stats["max_inflight"] <= 3, stats  # groups overlapped on the device, at most 3 at once
     assert 0 < stats["p50_ms"] <= stats["p99_ms"]
     # decrypted logits of a served LeNet request against the FP64 network
     lenet = M["lenet"]
