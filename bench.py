@@ -351,7 +351,8 @@ def refresh_bench(torch, stream, steps):
     """Time fe_he_bootstrap at N = 2^16 (24 x 50-bit primes, 4 special primes,
     secret weight 64; CoeffToSlot 3 levels, EvalMod 11, SlotToCoeff 3; stage
     groups with n1^2 >= 4 x their offsets, double-hoisted, complex form) on one level-0
-    ciphertext; report ms, levels, key switches and the decrypted error."""
+    ciphertext; report ms (direct calls and one captured graph), levels, key
+    switches and the decrypted error."""
     import paper_2606_16359_b300 as fe
     with torch.cuda.stream(stream):
         ctx = fe.Context(16, 24, 4, 50)
@@ -376,6 +377,20 @@ def refresh_bench(torch, stream, steps):
         cnt = ctx.counters()
         ms = a.elapsed_time(e) / steps
         err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
+        # the same refresh replayed as one captured graph (fe_boot_graph_capture)
+        want = out.clone()
+        g = ctx.boot_graph_capture(evk, b, ct, out, ws)
+        for _ in range(2):
+            g.launch()
+        torch.cuda.synchronize()
+        graph_equal = bool(torch.equal(out, want))
+        a.record(stream)
+        for _ in range(steps):
+            g.launch()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms_graph = a.elapsed_time(e) / steps
+        del g, want
         # kernel classes of one refresh (CUDA events per launch), and the leading
         # class, the transform in its general 64-bit form for 50-bit moduli,
         # against the butterfly probe run on this context's modulus q_0
@@ -390,7 +405,8 @@ def refresh_bench(torch, stream, steps):
         bfly_rate = limb_passes * (ctx.N // 2) * (ctx.logN / 2) / (t_ntt / 1e3) / 1e9 if t_ntt else 0.0
         bfly_peak = butterfly_roof(ctx, torch)
     ks = cnt["keyswitch"] / steps
-    res = {"ms": round(ms, 3), "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64, groups 3/11/3 levels, baby ratio 4, double hoisting, complex form",
+    res = {"ms": round(ms, 3), "ms_graph": round(ms_graph, 3), "graph_equals_direct": graph_equal,
+           "steps": steps, "warmup": 3, "params": "N=2^16, 24 x 50-bit q, 4 x 50-bit p, h=64, groups 3/11/3 levels, baby ratio 4, double hoisting, complex form",
            "levels_used": 23 - b.out_level, "out_level": b.out_level, "keyswitches": ks,
            "keyswitch_per_s": ks / (ms / 1e3), "max_abs_err": err,
            "evk_gb": evk.buf.numel() * 8 / 1e9, "workspace_gb": ws.numel() * 8 / 1e9,

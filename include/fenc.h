@@ -654,7 +654,13 @@ int fe_compress_masked(fe_ctx* ctx, const fe_evk* evk, const fe_layout* lay, uin
  * layers run in the order given, so a layer may read an earlier layer's output.
  * Every layer's item tables are uploaded into workspace_dev before capture (its
  * size: fe_graph_workspace_bytes(plans, n, 1)), so the graph replays kernels
- * only.  Counters are not advanced by graph launches. */
+ * only.  Counters are not advanced by graph launches.  The calls that run a
+ * plan or a key switch directly (fe_he_conv, fe_he_fc, fe_he_layer_batch,
+ * fe_he_lintrans, fe_he_repack, fe_rotate, fe_he_bootstrap and the like) copy
+ * such tables from host memory on every call; when their stream is being
+ * captured by the caller, the tables travel as kernel parameters instead (one
+ * small copy kernel per 2 KB, kept by value in the graph), so the caller's
+ * graph replays them correctly, with those extra launches. */
 int fe_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_plan* const* plans_host,
                      const void* const* pts_host, const void* const* ins_host,
                      void* const* outs_host, uint32_t n, void* workspace_dev,
@@ -954,6 +960,19 @@ size_t fe_boot_workspace_bytes(const fe_boot* boot, uint32_t n_ct);
  * ws: fe_boot_workspace_bytes(boot, n_ct).  Errors: FE_EKEY, FE_ENOMEM. */
 int fe_he_bootstrap(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
                     void* out_dev, void* ws, size_t ws_bytes, void* stream);
+/* Capture the refresh of n_ct >= 1 ciphertexts from ct_dev into out_dev as one
+ * CUDA graph (stream capture on `stream`, not the legacy default stream): the
+ * transforms' item tables are uploaded into ws first (fe_boot_workspace_bytes
+ * (boot, n_ct); ws must stay untouched while the graph lives), then the
+ * launches alone are captured, so that fe_graph_launch replays the whole
+ * refresh and gives the residues of fe_he_bootstrap on the same buffers.
+ * fe_graph_io reports ct_dev as the input and out_dev as the output (level
+ * fe_boot_output), so fe_graph_launch_host applies; release with
+ * fe_graph_destroy.  Synchronises `stream` before the capture.  (A caller's
+ * own capture of fe_he_bootstrap also replays correctly, but carries every
+ * table in copy kernels.)  Errors: FE_EINVAL, FE_EKEY, FE_ENOMEM, FE_ECUDA. */
+int fe_boot_graph_capture(fe_ctx* ctx, const fe_evk* evk, const fe_boot* boot, const void* ct_dev, uint32_t n_ct,
+                          void* out_dev, void* ws, size_t ws_bytes, void* stream, fe_graph** out);
 /* Switching key from secret sk_src to secret sk_dst (both [n_mod][N], NTT
  * form) for the hybrid key switch that rotations use (Eq. 1's KS), random
  * streams of object tag `obj` (rotation keys use their Galois element, the

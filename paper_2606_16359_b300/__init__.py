@@ -212,6 +212,7 @@ SIGNATURES = {
     "fe_boot_output": (cint, [vp, P(u32), P(dbl)]),
     "fe_boot_workspace_bytes": (sz, [vp, u32]),
     "fe_he_bootstrap": (cint, [vp, vp, vp, vp, u32, vp, vp, sz, vp]),
+    "fe_boot_graph_capture": (cint, [vp, vp, vp, vp, u32, vp, vp, sz, vp, P(vp)]),
     "fe_boot_destroy": (None, [vp]),
     "fe_boot_prepare_workspace_bytes": (sz, [vp, u32]),
     "fe_swk_gen": (cint, [vp, vp, vp, u64, u32, vp, sz, vp]),
@@ -624,6 +625,17 @@ class Context:
         check(load().fe_he_bootstrap(self.handle, evk.handle, boot.handle, _ptr(ct), n, _ptr(out), _ptr(ws),
                                      ws.numel() * 8, _stream()))
         return out
+
+    def boot_graph_capture(self, evk, boot, ct, out, ws):
+        """One CUDA graph of the refresh of ct (level 0) into out, on the current
+        (non-default) stream; replays give bootstrap()'s residues on the same buffers."""
+        n = ct.shape[0]
+        if ct.numel() != n * self.ct_words(0) or out.numel() != n * self.ct_words(boot.out_level):
+            raise ValueError("the refresh takes level-0 ciphertexts into boot.out_level outputs")
+        h = ctypes.c_void_p()
+        check(load().fe_boot_graph_capture(self.handle, evk.handle, boot.handle, _ptr(ct), n, _ptr(out), _ptr(ws),
+                                           ws.numel() * 8, _stream(), ctypes.byref(h)))
+        return Graph(h, (evk, boot, ct, out, ws))
 
     def rescale(self, ct, level):
         out = self.empty_ct(ct.shape[0], level - 1)

@@ -107,7 +107,7 @@ int token_rotate(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u
         std::vector<u64> kh(level + 1);
         const u64 m = (u64)ms;  // a power of two below the modulus
         for (int i = 0; i <= level; i++) kh[i] = m % c->mod[i];
-        FE_CUDA_TRY(cudaMemcpyAsync(k, kh.data(), kh.size() * 8, cudaMemcpyHostToDevice, st));
+        FE_TRY(copy_host_table(k, kh.data(), kh.size() * 8, st));
         k_mul_const<<<dim3((c->N + kB - 1) / kB, 2 * (level + 1), 1), kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1,
                                                                                  c->logN);
         c->cnt.launches++;

@@ -32,6 +32,7 @@
 #include <set>
 #include <vector>
 
+#include "graph.h"
 #include "plan.h"
 #include "prng.cuh"
 
@@ -524,6 +525,7 @@ struct EvCtx {
     Carver* scratch;  // per-operation scratch (reset after each operation)
     char* scratch_base;
     size_t scratch_bytes;
+    bool launch = true;  // false: levels, scales and buffers only (no launch)
 };
 
 size_t ct_bytes(const fe_ctx* c, int n, int level) { return (size_t)n * ct_words(c, level) * 8; }
@@ -536,8 +538,10 @@ int ev_mul(EvCtx& e, const Ev& a, const Ev& b, Ev& out) {
     u64* d = cv.take<u64>((size_t)e.n * ct_words(c, lv));
     u64* tmp = cv.take<u64>(rescale_tmp_words(c, e.n, lv));
     if (!cv.ok) return fail(FE_ENOMEM, "bootstrap workspace too small");
-    FE_TRY(cmult_relin(c, e.evk, a.p, b.p, e.n, lv, d, cv, e.st));
-    rescale_batch(c, d, e.n, lv, out.p, tmp, tmp + 2 * (size_t)e.n * c->N, e.st);
+    if (e.launch) {
+        FE_TRY(cmult_relin(c, e.evk, a.p, b.p, e.n, lv, d, cv, e.st));
+        rescale_batch(c, d, e.n, lv, out.p, tmp, tmp + 2 * (size_t)e.n * c->N, e.st);
+    }
     out.level = lv - 1;
     out.scale = (a.scale * b.scale) / (double)c->mod[lv];
     return FE_OK;
@@ -554,8 +558,10 @@ int ev_cmul(EvCtx& e, const Ev& a, double coef, double s_t, Ev& out) {
     const double x = ((coef * s_t) * (double)c->mod[lv]) / a.scale;
     AffineConsts k{};
     for (int i = 0; i <= lv; i++) k.mul[i] = nearest_mod(x, c->mod[i]);
-    FE_TRY(launch_affine(c, a.p, d, e.n, lv, k, true, e.st));
-    rescale_batch(c, d, e.n, lv, out.p, tmp, tmp + 2 * (size_t)e.n * c->N, e.st);
+    if (e.launch) {
+        FE_TRY(launch_affine(c, a.p, d, e.n, lv, k, true, e.st));
+        rescale_batch(c, d, e.n, lv, out.p, tmp, tmp + 2 * (size_t)e.n * c->N, e.st);
+    }
     out.level = lv - 1;
     out.scale = s_t;
     return FE_OK;
@@ -571,14 +577,14 @@ int ev_affine(EvCtx& e, Ev& a, int64_t mul, double coef) {
         k.mul[i] = mul >= 0 ? (u64)mul % q : q - (u64)(-mul) % q;
         k.add[i] = nearest_mod(x, q);
     }
-    return launch_affine(c, a.p, a.p, e.n, a.level, k, mul != 1, e.st);
+    return e.launch ? launch_affine(c, a.p, a.p, e.n, a.level, k, mul != 1, e.st) : FE_OK;
 }
 
 // the first (level + 1 - times) limbs of each polynomial
 int ev_drop(EvCtx& e, const Ev& a, int times, Ev& out) {
     const fe_ctx* c = e.c;
     const int nl = a.level + 1 - times;
-    if (out.p != a.p || times) {
+    if (e.launch && (out.p != a.p || times)) {
         FE_CUDA_TRY(cudaMemcpy2DAsync(out.p, (size_t)nl * c->N * 8, a.p, (size_t)(a.level + 1) * c->N * 8,
                                       (size_t)nl * c->N * 8, 2 * (size_t)e.n, cudaMemcpyDeviceToDevice, e.st));
     }
@@ -588,7 +594,7 @@ int ev_drop(EvCtx& e, const Ev& a, int times, Ev& out) {
 }
 
 int ev_add(EvCtx& e, Ev& acc, const Ev& b) {
-    launch_add(e.c, acc.p, b.p, acc.p, e.n, acc.level, e.st);
+    if (e.launch) launch_add(e.c, acc.p, b.p, acc.p, e.n, acc.level, e.st);
     return FE_OK;
 }
 
@@ -641,12 +647,16 @@ int eval_mod(EvCtx& e, Ev x, int r, u64* const* bufs, Ev& result) {
 }
 
 // ---------------------------------------------------------------------------
-// the refresh: buffers carved in one pass (dry: sizes only)
+// the refresh: buffers carved in one pass (dry: sizes only).  phase bit 1
+// uploads the transforms' item tables, bit 2 launches; every transform keeps
+// its tables in a region of its own, so that the launches of phase 2 alone can
+// be captured in a graph after phase 1 (fe_boot_graph_capture).
 // ---------------------------------------------------------------------------
 
 int boot_run(fe_ctx* c, const fe_evk* evk, const fe_boot* b, const u64* in, int R, u64* out, void* ws,
-             size_t ws_bytes, cudaStream_t st, bool dry, size_t* need) {
+             size_t ws_bytes, cudaStream_t st, bool dry, size_t* need, int phase = 3) {
     const int N = c->N, top = b->top;
+    const bool L = (phase & 2) != 0;
     Carver cv(dry ? nullptr : ws, dry ? SIZE_MAX : ws_bytes);
     u64* raised = cv.take<u64>((size_t)R * ct_words(c, top));
     u64* cj = cv.take<u64>((size_t)R * ct_words(c, top));
@@ -658,82 +668,107 @@ int boot_run(fe_ctx* c, const fe_evk* evk, const fe_boot* b, const u64* in, int 
     const int lv0 = top - b->n_cts;
     u64* bufs[8];
     for (int i = 0; i < 8; i++) bufs[i] = cv.take<u64>(2 * (size_t)R * ct_words(c, lv0));
-    size_t plan_ws = 0;
-    for (auto& p : b->plans) plan_ws = std::max(plan_ws, fe_plan_workspace_bytes(p.get(), (uint32_t)R, 0));
+    // the transforms' data region (rotated copies, sums, scratch), shared with
+    // EvalMod, and one item-table region per transform
+    size_t data = 0;
+    for (auto& p : b->plans) {
+        const size_t def = fe_plan_workspace_bytes(p.get(), (uint32_t)R, 0);
+        data = std::max(data, plan_data_bytes(p.get(), plan_chunk(p.get(), R, 1, def, false), R));
+    }
+    data = (data + 255) & ~(size_t)255;
     const size_t ev_ws = cmult_relin_bytes(c, 2 * R, lv0) + ct_bytes(c, 2 * R, lv0) +
                          rescale_tmp_words(c, 2 * R, lv0) * 8 + 8 * 256;
-    char* shared = cv.take<char>(std::max(plan_ws, ev_ws));
+    const size_t shared_bytes = std::max(data, ev_ws);
+    char* shared = cv.take<char>(shared_bytes);
+    std::vector<char*> tab(b->plans.size());
+    std::vector<size_t> tab_bytes(b->plans.size());
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        const fe_plan* p = b->plans[i].get();
+        tab_bytes[i] = (plan_table_bytes(p, plan_chunk(p, R, 1, data, true), R) + 255) & ~(size_t)255;
+        tab[i] = cv.take<char>(tab_bytes[i]);
+    }
     if (dry) {
         *need = SIZE_MAX - cv.left;
         return FE_OK;
     }
     if (!cv.ok) return fail(FE_ENOMEM, "bootstrap workspace too small (fe_boot_workspace_bytes)");
-    if (b->key_to_sparse) {
-        // the level-0 inputs (dense secret) switched to the sparse secret (into pb), raised
-        // (into cj), switched back to the dense secret at level top (into raised)
-        FE_TRY(ks_batch(c, b->key_to_sparse, 1, in, R, 0, pb, cs, st));
-        mod_raise(c, pb, R, top, cj, tmp, st);
-        FE_TRY(ks_batch(c, b->key_to_dense, 1, cj, R, top, raised, cs, st));
-    } else {
-        mod_raise(c, in, R, top, raised, tmp, st);
+    auto transform = [&](size_t pi, const u64* src, u64* dst) {
+        return run_plan(c, evk, b->plans[pi].get(), src, b->pts[pi], dst, tab[pi], tab_bytes[pi], 1, st, phase, R, 0,
+                        shared, data);
+    };
+    if (L) {
+        if (b->key_to_sparse) {
+            // the level-0 inputs (dense secret) switched to the sparse secret (into pb), raised
+            // (into cj), switched back to the dense secret at level top (into raised)
+            FE_TRY(ks_batch(c, b->key_to_sparse, 1, in, R, 0, pb, cs, st));
+            mod_raise(c, pb, R, top, cj, tmp, st);
+            FE_TRY(ks_batch(c, b->key_to_dense, 1, cj, R, top, raised, cs, st));
+        } else {
+            mod_raise(c, in, R, top, raised, tmp, st);
+        }
     }
-    const size_t shared_bytes = std::max(plan_ws, ev_ws);
+    EvCtx e{c, evk, 2 * R, st, nullptr, shared, shared_bytes};
+    e.launch = L;
     if (b->form == 1) {
         // complex form: CoeffToSlot on the raised ciphertexts, the split at lv0,
         // EvalMod, the join, SlotToCoeff (every transform one in, one out)
         u64* x = raised;
-        int pi = 0;
-        for (; pi < b->n_cts; pi++) {
+        size_t pi = 0;
+        for (; pi < (size_t)b->n_cts; pi++) {
             u64* dst = x == pa ? pb : pa;
-            FE_TRY(run_plan(c, evk, b->plans[pi].get(), x, b->pts[pi], dst, shared, shared_bytes, 1, st, 3, R));
+            FE_TRY(transform(pi, x, dst));
             x = dst;
         }
-        FE_TRY(conjugate_batch(c, evk, x, R, lv0, cj, cs, st));
         u64* pair = x == pa ? pb : pa;
-        k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (lv0 + 1), R), kB, 0, st>>>(x, cj, b->mono, pair, c->d_mod,
-                                                                              lv0 + 1, c->logN);
-        c->cnt.launches++;
-        FE_CUDA_TRY(cudaGetLastError());
-        EvCtx e{c, evk, 2 * R, st, nullptr, shared, shared_bytes};
+        if (L) {
+            FE_TRY(conjugate_batch(c, evk, x, R, lv0, cj, cs, st));
+            k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (lv0 + 1), R), kB, 0, st>>>(x, cj, b->mono, pair, c->d_mod,
+                                                                                  lv0 + 1, c->logN);
+            c->cnt.launches++;
+            FE_CUDA_TRY(cudaGetLastError());
+        }
         Ev xe{pair, lv0, (double)c->mod[0]}, y{};
         FE_TRY(eval_mod(e, xe, b->r, bufs, y));
         if (y.scale != b->out_scale || y.level != top - b->n_cts - 5 - b->r)
             return fail(FE_EINVAL, "bootstrap: EvalMod scale bookkeeping disagrees with the plan");
         u64* v = x;  // the CoeffToSlot output is no longer needed
-        k_boot_join<<<dim3((N + kB - 1) / kB, 2 * (y.level + 1), R), kB, 0, st>>>(y.p, b->mono, v, c->d_mod,
-                                                                                 y.level + 1, c->logN);
-        c->cnt.launches++;
-        FE_CUDA_TRY(cudaGetLastError());
+        if (L) {
+            k_boot_join<<<dim3((N + kB - 1) / kB, 2 * (y.level + 1), R), kB, 0, st>>>(y.p, b->mono, v, c->d_mod,
+                                                                                     y.level + 1, c->logN);
+            c->cnt.launches++;
+            FE_CUDA_TRY(cudaGetLastError());
+        }
         u64* cur = v;
-        for (; pi < (int)b->plans.size(); pi++) {
-            const bool last = pi + 1 == (int)b->plans.size();
+        for (; pi < b->plans.size(); pi++) {
+            const bool last = pi + 1 == b->plans.size();
             u64* dst = last ? out : (cur == pa ? pb : pa);
-            FE_TRY(run_plan(c, evk, b->plans[pi].get(), cur, b->pts[pi], dst, shared, shared_bytes, 1, st, 3, R));
+            FE_TRY(transform(pi, cur, dst));
             cur = dst;
         }
         return FE_OK;
     }
-    FE_TRY(conjugate_batch(c, evk, raised, R, top, cj, cs, st));
-    k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (top + 1), R), kB, 0, st>>>(raised, cj, b->mono, pa, c->d_mod, top + 1,
-                                                                          c->logN);
-    c->cnt.launches++;
-    FE_CUDA_TRY(cudaGetLastError());
-    int pi = 0;
-    for (; pi < b->n_cts; pi++) {
-        FE_TRY(run_plan(c, evk, b->plans[pi].get(), pa, b->pts[pi], pb, shared, shared_bytes, 1, st, 3, R));
+    if (L) {
+        FE_TRY(conjugate_batch(c, evk, raised, R, top, cj, cs, st));
+        k_boot_parts<<<dim3((N + kB - 1) / kB, 2 * (top + 1), R), kB, 0, st>>>(raised, cj, b->mono, pa, c->d_mod,
+                                                                              top + 1, c->logN);
+        c->cnt.launches++;
+        FE_CUDA_TRY(cudaGetLastError());
+    }
+    size_t pi = 0;
+    for (; pi < (size_t)b->n_cts; pi++) {
+        FE_TRY(transform(pi, pa, pb));
         std::swap(pa, pb);
     }
     // EvalMod on the 2R parts (pa holds [R][2] ciphertexts at lv0, i.e. 2R in a row)
-    EvCtx e{c, evk, 2 * R, st, nullptr, shared, shared_bytes};
     Ev x{pa, lv0, (double)c->mod[0]}, y{};
     FE_TRY(eval_mod(e, x, b->r, bufs, y));
     if (y.scale != b->out_scale || y.level != top - b->n_cts - 5 - b->r)
         return fail(FE_EINVAL, "bootstrap: EvalMod scale bookkeeping disagrees with the plan");
     const u64* cur = y.p;
-    for (; pi < (int)b->plans.size(); pi++) {
-        const bool last = pi + 1 == (int)b->plans.size();
+    for (; pi < b->plans.size(); pi++) {
+        const bool last = pi + 1 == b->plans.size();
         u64* dst = last ? out : (cur == pa ? pb : pa);
-        FE_TRY(run_plan(c, evk, b->plans[pi].get(), cur, b->pts[pi], dst, shared, shared_bytes, 1, st, 3, R));
+        FE_TRY(transform(pi, cur, dst));
         cur = dst;
     }
     return FE_OK;
@@ -961,6 +996,46 @@ extern "C" int fe_he_bootstrap(fe_ctx* c, const fe_evk* evk, const fe_boot* b, c
     if (n_ct == 0) return FE_OK;
     return boot_run(c, evk, b, (const u64*)ct_dev, (int)n_ct, (u64*)out_dev, ws, ws_bytes, (cudaStream_t)stream,
                     false, nullptr);
+}
+
+extern "C" int fe_boot_graph_capture(fe_ctx* c, const fe_evk* evk, const fe_boot* b, const void* ct_dev,
+                                     uint32_t n_ct, void* out_dev, void* ws, size_t ws_bytes, void* stream,
+                                     fe_graph** out) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev); FE_ALIGNED(ws);
+    if (!c || !evk || !b || !ct_dev || !out_dev || !ws || !out) return fail(FE_EINVAL, "null argument");
+    if (b->c != c) return fail(FE_EINVAL, "the bootstrap belongs to another context");
+    if (!evk->relin) return fail(FE_EKEY, "the refresh needs the relinearisation key");
+    if (n_ct == 0) return fail(FE_EINVAL, "n_ct must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!st) return fail(FE_EINVAL, "graph capture needs a non-default stream");
+    // the transforms' item tables go to their regions of ws first; then the
+    // launches alone are captured (they read the tables when the graph runs)
+    FE_TRY(boot_run(c, evk, b, (const u64*)ct_dev, (int)n_ct, (u64*)out_dev, ws, ws_bytes, st, false, nullptr, 1));
+    FE_CUDA_TRY(cudaStreamSynchronize(st));
+    FE_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc =
+        boot_run(c, evk, b, (const u64*)ct_dev, (int)n_ct, (u64*)out_dev, ws, ws_bytes, st, false, nullptr, 2);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc != FE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(FE_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    std::unique_ptr<fe_graph> g(new fe_graph());
+    g->graph = graph;
+    const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(FE_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(ie));
+    }
+    const uint32_t out_level = (uint32_t)(b->top - b->depth);
+    g->in.push_back({const_cast<void*>(ct_dev), (size_t)n_ct * ct_words(c, 0) * 8});
+    g->out.push_back({out_dev, (size_t)n_ct * ct_words(c, (int)out_level) * 8});
+    g->out_level.push_back(out_level);
+    g->N = (size_t)c->N;
+    *out = g.release();
+    return FE_OK;
 }
 
 extern "C" int fe_key_switch(fe_ctx* c, const void* key_dev, const void* ct_dev, uint32_t n_ct, uint32_t level,

@@ -8,22 +8,8 @@
 #include <cmath>
 #include <memory>
 
+#include "graph.h"
 #include "plan.h"
-
-struct fe_graph {
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-    // the captured sequence's external inputs (layer inputs no earlier layer writes)
-    // and final outputs (layer outputs no later layer reads), in layer order
-    struct Io {
-        void* dev;
-        size_t bytes;
-    };
-    std::vector<Io> in, out;
-    std::vector<uint32_t> out_level;  // level of each final output ciphertext array
-    uint32_t host_out_level = UINT32_MAX;  // outputs copied to the host at this level (UINT32_MAX: their own)
-    size_t N = 0;
-};
 
 namespace fe {
 namespace {

@@ -1,6 +1,7 @@
 // Scheme operations: key generation, encryption, decryption, ModUp / ModDown,
 // rotation (Eq. 1), rescale, and the primitive entry points of the C ABI.
 #include <algorithm>
+#include <cstring>
 #include <memory>
 #include <set>
 
@@ -202,6 +203,31 @@ int sk_gen(fe_ctx* c, uint64_t seed, u64* sk, cudaStream_t st) {
     ntt_forward(c, LimbSet{sk, (size_t)c->n_mod * c->N, c->n_mod, 1, c->d_identity_map}, st);
     FE_CUDA_TRY(cudaFreeAsync(s, st));
     FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
+// Copies of per-call host tables inside a stream capture: each piece of the
+// table travels as a kernel parameter (copied by value when the launch is
+// captured), so the graph rewrites the table from its own copy on every replay.
+namespace {
+constexpr int kParamBytes = 2048;
+struct ParamBlock {
+    unsigned char b[kParamBytes];
+};
+__global__ void k_copy_param(unsigned char* dst, ParamBlock p, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = p.b[i];
+}
+}  // namespace
+
+int copy_by_params(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    const unsigned char* s = (const unsigned char*)src;
+    for (size_t off = 0; off < bytes; off += kParamBytes) {
+        ParamBlock p;
+        const int n = (int)std::min<size_t>(kParamBytes, bytes - off);
+        std::memcpy(p.b, s + off, (size_t)n);
+        k_copy_param<<<1, 256, 0, st>>>((unsigned char*)dst + off, p, n);
+        FE_CUDA_TRY(cudaGetLastError());
+    }
     return FE_OK;
 }
 

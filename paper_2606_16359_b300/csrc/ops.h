@@ -59,12 +59,28 @@ int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const Af
 // the integer nearest to x, ties away from zero, reduced mod q (any finite x)
 u64 nearest_mod(double x, u64 q);
 
+// the bytes of a host table carried to dst by kernel parameters (pieces of
+// 2 KB, one launch each)
+int copy_by_params(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+// copy a per-call host table into device memory on `st`.  The source is
+// ordinary (pageable) host memory that the caller frees on return, so a
+// stream capture must not record it as a copy: the replay would read freed
+// memory.  Under capture the table goes by kernel parameters instead, which
+// the graph keeps by value.
+inline int copy_host_table(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    FE_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return copy_by_params(dst, src, bytes, st);
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return FE_OK;
+}
+
 // upload a host vector into a device region carved from a workspace
 template <class T>
 int upload(const std::vector<T>& v, T* dst, cudaStream_t st) {
     if (v.empty()) return FE_OK;
-    FE_CUDA_TRY(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    return FE_OK;
+    return copy_host_table(dst, v.data(), v.size() * sizeof(T), st);
 }
 
 }  // namespace fe

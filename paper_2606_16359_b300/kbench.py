@@ -8,7 +8,7 @@
     python -m paper_2606_16359_b300.kbench aac [--reps 5]
     python -m paper_2606_16359_b300.kbench configs [--reps 5]
     python -m paper_2606_16359_b300.kbench repack
-    python -m paper_2606_16359_b300.kbench refresh [--reps 5]
+    python -m paper_2606_16359_b300.kbench refresh [--reps 5] [--graph 1]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -18,7 +18,9 @@ alu: the integer-pipe roof of the transform's butterfly arithmetic, from a
 refresh: one ciphertext refresh (bootstrapping) at N = 2^16 with 24 + 4 primes of
      50 bits and a secret of weight 64, timed over --reps refreshes; the last
      refresh is bracketed by two one-block butterfly-probe launches, markers for
-     a profiler's launch list.
+     a profiler's launch list.  --graph 1 captures the refresh in one CUDA
+     graph (fe_boot_graph_capture; checked equal to the direct call) and times
+     its replays.
 keyswitch: rotations (hybrid key switch + automorphism) of n ciphertexts at one
      level with one key; algorithmic bytes per key switch without key reuse
      [(l+1) + 2 dnum (l+1+k) + 2 (l+1)] N w.
@@ -346,11 +348,23 @@ def bench_refresh(ctx_unused, torch, args):
     for _ in range(2):
         ctx.bootstrap(evk, b, ct, ws=ws, out=out)
     torch.cuda.synchronize()
+    run = lambda: ctx.bootstrap(evk, b, ct, ws=ws, out=out)  # noqa: E731
+    if args.graph:
+        # one graph of the whole refresh (fe_boot_graph_capture: item tables
+        # uploaded first, launches captured), checked against the direct call
+        want = out.clone()
+        g = ctx.boot_graph_capture(evk, b, ct, out, ws)
+        out.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        if not torch.equal(out, want):
+            raise RuntimeError("the replayed refresh differs from the direct call")
+        run = g.launch
     st = torch.cuda.current_stream()
     a, e = _events(torch)
     a.record(st)
     for _ in range(args.reps):
-        ctx.bootstrap(evk, b, ct, ws=ws, out=out)
+        run()
     e.record(st)
     torch.cuda.synchronize()
     ms = a.elapsed_time(e) / args.reps
@@ -362,7 +376,7 @@ def bench_refresh(ctx_unused, torch, args):
     ctx.probe_butterflies(probe, 1, 1)
     torch.cuda.synchronize()
     err = float(np.abs(ctx.decrypt(sk, out, b.out_level, b.out_scale).cpu().numpy() - z).max())
-    return {"what": "refresh", "form": args.form, "n_ct": args.n_ct, "ms_per_ct": ms / args.n_ct,
+    return {"what": "refresh", "form": args.form, "graph": bool(args.graph), "n_ct": args.n_ct, "ms_per_ct": ms / args.n_ct,
             "groups": [args.n_cts, args.n_stc], "double_angles": args.double_angles,
             "levels_used": 23 - b.out_level, "baby_ratio": args.baby_ratio, "double_hoist": args.double_hoist, "ms": ms, "reps": args.reps,
             "out_level": b.out_level, "max_abs_err": err, "rotation_keys": len(b.steps),
@@ -395,6 +409,7 @@ def main(argv=None):
     ap.add_argument("--double-angles", type=int, default=6, help="refresh: EvalMod double angles")
     ap.add_argument("--n-ct", type=int, default=1, help="refresh: ciphertexts refreshed in one call")
     ap.add_argument("--form", default="complex", choices=["real", "complex"], help="refresh: transform form")
+    ap.add_argument("--graph", type=int, default=0, help="refresh: 1 times replays of one captured graph")
     args = ap.parse_args(argv)
     import torch
 

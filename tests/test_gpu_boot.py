@@ -124,6 +124,68 @@ def test_refresh_bit_exact_against_the_oracle(small):
     assert np.abs(dec - z).max() < 1e-4
 
 
+def test_refresh_graph_replays_the_direct_refresh(small):
+    """fe_boot_graph_capture: one captured graph of the refresh of two
+    ciphertexts, replayed on two batches copied into its input buffer, gives the
+    direct call's residues for each batch, and the oracle's."""
+    pr, bp, ctx, sk, keys, s = small
+    s_in = 2.0 ** 45
+    rng = np.random.default_rng(12)
+    z = rng.uniform(-1, 1, (2, 2, pr.N // 2))
+    octs = [[ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[j][i], 0, s_in), 7, 10 + 2 * j + i) for i in range(2)]
+            for j in range(2)]
+    with torch.cuda.stream(s):
+        b = ctx.boot_create(s_in, 3, 3, 6)
+        evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
+        ws = ctx.workspace(b.workspace_bytes(2))
+        x = to_gpu(octs[0])
+        out = ctx.empty_ct(2, b.out_level)
+        g = ctx.boot_graph_capture(evk, b, x, out, ws)
+        (ib,), (ob,) = g.io()
+        assert ib == x.numel() * 8 and ob == out.numel() * 8
+        replayed = []
+        for j in range(2):
+            x.copy_(to_gpu(octs[j]))
+            g.launch()
+            replayed.append(u64(out).copy())
+        direct = [u64(ctx.bootstrap(evk, b, to_gpu(octs[j]))) for j in range(2)]
+        torch.cuda.synchronize()
+    for j in range(2):
+        assert np.array_equal(replayed[j], direct[j]), j
+    want = boot.bootstrap(pr, keys, octs[1][0], bp)
+    assert np.array_equal(replayed[1][0], oracle_ct(pr, want))
+
+
+def test_caller_capture_of_the_refresh_replays_it(small):
+    """A caller's own stream capture (torch.cuda.CUDAGraph) of fe_he_bootstrap:
+    the per-call item tables travel in the graph by value, so replays on new
+    inputs give the direct call's residues."""
+    pr, bp, ctx, sk, keys, s = small
+    s_in = 2.0 ** 45
+    z = np.random.default_rng(13).uniform(-1, 1, (2, 1, pr.N // 2))
+    with torch.cuda.stream(s):
+        b = ctx.boot_create(s_in, 3, 3, 6)
+        evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
+        ws = ctx.workspace(b.workspace_bytes(1))
+        cts = [ctx.encrypt(sk, z[j], 0, s_in, seed=14 + j) for j in range(2)]
+        direct = [ctx.bootstrap(evk, b, cts[j]).clone() for j in range(2)]
+        x = cts[0].clone()
+        out = ctx.empty_ct(1, b.out_level)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        g.capture_begin()
+        ctx.bootstrap(evk, b, x, ws=ws, out=out)
+        g.capture_end()
+        replayed = []
+        for j in range(2):
+            x.copy_(cts[j])
+            g.replay()
+            replayed.append(out.clone())
+        torch.cuda.synchronize()
+    for j in range(2):
+        assert torch.equal(replayed[j], direct[j]), j
+
+
 @pytest.mark.parametrize("form", ["real", "complex"])
 def test_refresh_full_size(form):
     """N = 2^16 with 24 primes of 50 bits and 4 special primes, secret weight 64:
