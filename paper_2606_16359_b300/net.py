@@ -312,39 +312,46 @@ class LeNet:
 
 
 class RefreshChain:
-    """Two MobileNet-shaped blocks (depthwise 3x3, a x^2 + b x + c, pointwise,
-    the same activation) with a ciphertext refresh between them: the pattern of
-    the paper's deeper networks, which refresh their ciphertexts between blocks
-    (Sec. 5, Evaluation Methodology).  The context needs the refresh's
-    parameters (levels above the refresh's depth, moduli of about 50 bits);
-    the secret is sparse (weight h), or, with encapsulate, dense with a sparse
-    secret borrowed by the refresh (fe_boot_encapsulate).  Block 1 runs from level L, its output is
+    """n_blocks MobileNet-shaped blocks (depthwise 3x3, a x^2 + b x + c,
+    pointwise, the same activation; two by default) with a ciphertext refresh
+    between consecutive blocks: the pattern of the paper's deeper networks,
+    which refresh their ciphertexts between blocks (Sec. 5, Evaluation
+    Methodology).  The context needs the refresh's parameters (levels above the
+    refresh's depth, moduli of about 50 bits); the secret is sparse (weight h),
+    or, with encapsulate, dense with a sparse secret borrowed by the refresh
+    (fe_boot_encapsulate).  Block 1 runs from level L; every block's output is
     brought to level 0 at the refresh's input scale (fe_boot_prepare), the
-    refresh returns it at boot.out_level, and block 2 runs from there.  The
-    library fixes every scale (fe_weight_scale, fe_plan_out_scale,
+    refresh returns it at boot.out_level, and the next block runs from there.
+    The library fixes every scale (fe_weight_scale, fe_plan_out_scale,
     fe_poly_act_scale, fe_boot_output); this class only passes them along."""
 
     def __init__(self, ctx, H, C, delta=2.0 ** 40, act=(0.5, 0.5, 0.0), h=64, scale_in=2.0 ** 44, seed=5,
-                 key_seed=41, boot_groups=(3, 3), double_angles=6, encapsulate=False):
+                 key_seed=41, boot_groups=(3, 3), double_angles=6, encapsulate=False, n_blocks=2):
         torch = _torch()
         self.ctx, self.delta, self.act = ctx, delta, tuple(float(v) for v in act)
         a = self.act[0]
         L = ctx.L
-        self.x, wd1, wp1 = W.mobilenet_block(seed, H, C, C, BS=1, block=0)
-        _, wd2, wp2 = W.mobilenet_block(seed, H, C, C, BS=1, block=1)
-        self.w = [(wd1, wp1), (wd2, wp2)]
+        if n_blocks < 1:
+            raise ValueError("n_blocks must be positive")
+        self.x = W.mobilenet_block(seed, H, C, C, BS=1, block=0)[0]
+        self.w = [W.mobilenet_block(seed, H, C, C, BS=1, block=i)[1:] for i in range(n_blocks)]
         self.boot = ctx.boot_create(scale_in, boot_groups[0], boot_groups[1], double_angles)
         lb = self.boot.out_level
-        if lb < 4:
-            raise ValueError("the refresh leaves fewer than the 4 levels block 2 needs")
+        # a block spends 4 levels; a block that a refresh follows must end at level 1 or above
+        if n_blocks > 1 and (lb < 4 or (n_blocks > 2 and lb < 5) or L < 5):
+            raise ValueError("the refresh leaves too few levels for the blocks after it")
         lay = ctx.layout(H, H, C, 1, 1)
         self.lay = lay
-        p1d = ctx.plan_conv(lay, C, 3, depthwise=True, level=L)
-        p1p = ctx.plan_conv(p1d.out_layout, C, 1, level=L - 2)
-        p2d = ctx.plan_conv(p1p.out_layout, C, 3, depthwise=True, level=lb)
-        p2p = ctx.plan_conv(p2d.out_layout, C, 1, level=lb - 2)
-        self.plans = [(p1d, p1p, L), (p2d, p2p, lb)]
-        steps = sorted({s for p in (p1d, p1p, p2d, p2p) for s in p.steps} | set(self.boot.steps))
+        self.plans = []
+        cur = lay
+        for i in range(n_blocks):
+            lv = L if i == 0 else lb
+            pd = ctx.plan_conv(cur, C, 3, depthwise=True, level=lv)
+            pp = ctx.plan_conv(pd.out_layout, C, 1, level=lv - 2)
+            self.plans.append((pd, pp, lv))
+            cur = pp.out_layout
+        all_plans = [p for pd, pp, _ in self.plans for p in (pd, pp)]
+        steps = sorted({s for p in all_plans for s in p.steps} | set(self.boot.steps))
         if encapsulate:
             # the network under the dense secret; the refresh borrows a sparse one for ModRaise
             self.sk = ctx.sk_gen(key_seed)
@@ -355,8 +362,8 @@ class RefreshChain:
         self.evk = ctx.evk_gen(self.sk, key_seed, steps, relin=True)
         self.n_keys = len(steps)
         self.pts, self.scales = [], []
-        self.ws = ctx.workspace(max(p.info.workspace_bytes for p in (p1d, p1p, p2d, p2p)))
-        self.boot_ws = ctx.workspace(self.boot.workspace_bytes(p1p.info.n_out_ct))
+        self.ws = ctx.workspace(max(p.info.workspace_bytes for p in all_plans))
+        self.boot_ws = ctx.workspace(self.boot.workspace_bytes(self.plans[0][1].info.n_out_ct))
         s = delta
         for (pd, pp, lv), (wd, wp) in zip(self.plans, self.w):
             if lv != L:
@@ -369,8 +376,8 @@ class RefreshChain:
             s = ctx.poly_act_scale(lv - 3, s_p, a)
             self.pts.append((ptd, ptp))
             self.scales.append((s_d, s_p, s))
-        self.out_layout = p2p.out_layout
-        self.out_level = lb - 4
+        self.out_layout = self.plans[-1][1].out_layout
+        self.out_level = self.plans[-1][2] - 4
         self.out_scale = s
         slots = ctx.pack(lay, torch.from_numpy(self.x))
         self.ct = ctx.encrypt(self.sk, slots, L, delta, seed=7)
@@ -385,16 +392,20 @@ class RefreshChain:
         return h
 
     def forward(self, trace=None):
-        """Block 1, prepare, refresh, block 2; returns the output ciphertexts."""
-        c, L = self.ctx, self.ctx.L
+        """Block 1, then (prepare, refresh, next block) for each further block;
+        returns the output ciphertexts.  trace receives the first block's
+        output ("block1") and the first refresh's ("refreshed")."""
+        c = self.ctx
         h = self._block(0, self.ct)
         if trace is not None:
             trace["block1"] = h
-        h = c.boot_prepare(self.boot, h, L - 4, self.scales[0][2])
-        h = c.bootstrap(self.evk, self.boot, h, ws=self.boot_ws)
-        if trace is not None:
-            trace["refreshed"] = h
-        return self._block(1, h)
+        for i in range(1, len(self.plans)):
+            h = c.boot_prepare(self.boot, h, self.plans[i - 1][2] - 4, self.scales[i - 1][2])
+            h = c.bootstrap(self.evk, self.boot, h, ws=self.boot_ws)
+            if trace is not None and i == 1:
+                trace["refreshed"] = h
+            h = self._block(i, h)
+        return h
 
     def decrypt(self, out):
         slots = self.ctx.decrypt(self.sk, out, self.out_level, self.out_scale)
@@ -406,7 +417,7 @@ class RefreshChain:
         ops = []
         for i, ((pd, pp, lv), (ptd, ptp), (s_d, s_p, _)) in enumerate(zip(self.plans, self.pts, self.scales)):
             if i:
-                ops.append((OP_REFRESH, self.boot, self.scales[0][2]))
+                ops.append((OP_REFRESH, self.boot, self.scales[i - 1][2]))
             ops += [(OP_LAYER, pd, ptd), (OP_POLY_ACT, *self.act, s_d), (OP_LAYER, pp, ptp),
                     (OP_POLY_ACT, *self.act, s_p)]
         return ops

@@ -245,7 +245,8 @@ def test_refresh_schedules_bit_exact(small, groups, r, ratio, double, form):
 
 
 def _oracle_chain(pr, keys, cts, lay, w, act, delta, bp, scale_in):
-    """The oracle's composition of RefreshChain: block, prepare, refresh, block."""
+    """The oracle's composition of RefreshChain: block, then (prepare, refresh,
+    block) for each further block."""
     from oracle import henn
     a, b, c = act
 
@@ -257,35 +258,43 @@ def _oracle_chain(pr, keys, cts, lay, w, act, delta, bp, scale_in):
         h, l2 = henn.he_conv(pr, keys, h, l1, wp, w_scale=henn.weight_scale(pr, lv - 2, h[0].scale, delta, a))
         return henn.he_poly_act(pr, keys, h, a, b, c), l2
 
-    h, l2 = block(cts, lay, *w[0])
-    h = [boot.bootstrap(pr, keys, boot.prepare(pr, ct, scale_in), bp) for ct in h]
-    return block(h, l2, *w[1])
+    h, ly = block(cts, lay, *w[0])
+    for wd, wp in w[1:]:
+        h = [boot.bootstrap(pr, keys, boot.prepare(pr, ct, scale_in), bp) for ct in h]
+        h, ly = block(h, ly, wd, wp)
+    return h, ly
 
 
-def test_refresh_chain_bit_exact_small():
-    """Block (dw 3x3, activation, pw, activation), prepare, refresh, block at
-    N = 2^10 with 22 primes of 50 bits: every output residue equals the oracle's
-    composition of the same steps, and the decryption matches FP64."""
+@pytest.mark.parametrize("n_blocks,n_q,H", [(2, 22, 6), (3, 23, 8)])
+def test_refresh_chain_bit_exact_small(n_blocks, n_q, H):
+    """Block (dw 3x3, activation, pw, activation), then prepare, refresh and
+    block again, at N = 2^10 with n_q primes of 50 bits (two blocks and one
+    refresh; three blocks and two refreshes, which need a fifth level after the
+    refresh): every output residue equals the oracle's composition of the same
+    steps, and the decryption matches FP64.  Each unpadded 3x3 depthwise
+    convolution shrinks the H x H map by 2."""
     from oracle import fragment, henn, plain
     from paper_2606_16359_b300 import net
-    logN, n_q, k, bits, h, H, C = 10, 22, 4, 50, 32, 6, 4
+    logN, k, bits, h, C = 10, 4, 50, 32, 4
     pr = ckks.Params(logN, n_q, k, bits)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = fe.Context(logN, n_q, k, bits)
-        ch = net.RefreshChain(ctx, H, C, h=h, key_seed=41, seed=5)
+        ch = net.RefreshChain(ctx, H, C, h=h, key_seed=41, seed=5, n_blocks=n_blocks)
+        assert len(ch.w) == n_blocks
         out = ch.forward()
         got = u64(out)
         y = ch.decrypt(out)
         torch.cuda.synchronize()
     bp = boot.BootParams(pr, 3, 3, 6)
     lay = fragment.Layout(pr.N, H, H, C, 1, 1)
-    l1 = henn.out_layout_conv(lay, C, 3, 1)
-    l3 = henn.out_layout_conv(l1, C, 3, 1)
     steps = set(boot.boot_rotation_steps(pr, bp))
-    for ly in (lay, l1, l3):
+    ly = lay
+    for _ in range(n_blocks):
         steps |= set(henn.conv_rotation_steps(ly, C, C, 3, depthwise=True))
-        steps |= set(henn.conv_rotation_steps(henn.out_layout_conv(ly, C, 3, 1), C, C, 1))
+        ly = henn.out_layout_conv(ly, C, 3, 1)
+        steps |= set(henn.conv_rotation_steps(ly, C, C, 1))
+        ly = henn.out_layout_conv(ly, C, 1, 1)
     keys = boot.SparseKeySet(pr, 41, h, rot_steps=sorted(steps), relin=True, conj=True)
     slots = fragment.pack(lay, ch.x)
     cts = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, slots[i], pr.L, ch.delta), 7, i) for i in range(lay.n_ct)]
@@ -299,16 +308,18 @@ def test_refresh_chain_bit_exact_small():
     assert np.abs(y - ref).max() < 1e-3
 
 
-@pytest.mark.parametrize("encapsulate", [False, True])
-def test_refresh_chain_full_size(encapsulate):
+@pytest.mark.parametrize("encapsulate,n_blocks", [(False, 2), (True, 2), (True, 3)])
+def test_refresh_chain_full_size(encapsulate, n_blocks):
     """The same chain at N = 2^16 (24 primes of 50 bits) on a 14 x 14 x 32 map,
     under a sparse secret of weight 64, or under a dense secret with the sparse
-    one borrowed by the refresh: decrypted within 1e-3 of the FP64 network."""
+    one borrowed by the refresh; two blocks, or three with two refreshes (12
+    convolution and activation levels on a 23-level chain): decrypted within
+    1e-3 of the FP64 network."""
     from paper_2606_16359_b300 import net
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         ctx = fe.Context(16, 24, 4, 50)
-        ch = net.RefreshChain(ctx, 14, 32, h=64, encapsulate=encapsulate)
+        ch = net.RefreshChain(ctx, 14, 32, h=64, encapsulate=encapsulate, n_blocks=n_blocks)
         out = ch.forward()
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,8 +329,8 @@ def test_refresh_chain_full_size(encapsulate):
         torch.cuda.synchronize()
         y = ch.decrypt(out)
     err = float(np.abs(y - ch.reference()).max())
-    print(f"block + refresh + block at N=2^16 (encapsulated: {encapsulate}): {t0.elapsed_time(t1):.1f} ms, "
-          f"max error {err:.2e}")
+    print(f"{n_blocks} blocks, {n_blocks - 1} refreshes at N=2^16 (encapsulated: {encapsulate}): "
+          f"{t0.elapsed_time(t1):.1f} ms, max error {err:.2e}")
     assert ch.out_level == 2 and err < 1e-3
 
 
