@@ -9,8 +9,11 @@
 //
 // These layers are composed from the library's primitives (rotation, PMult,
 // addition, CMult with relinearisation, rescale) in a fixed order, so that
-// their residues equal the oracle's step for step; their scratch comes from the
-// stream-ordered allocator.
+// their residues equal the oracle's step for step.  Each call encodes the
+// 2 (n - 1) token masks once, runs every token rotation, product and rescale
+// on the S ciphertexts together and the position sums on all n score
+// diagonals together; per ciphertext the steps are those of the oracle.
+// Scratch comes from the stream-ordered allocator.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -91,67 +94,87 @@ int drop_limb(fe_ctx* c, const u64* x, int n, int level, u64* out, cudaStream_t 
     return FE_OK;
 }
 
-// token-wise rotation of one ciphertext at `level` by r tokens (one level):
-// out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n)), masks at ms;
-// r = 0: rescale(x times the integer ms)
-int token_rotate(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int level, int r, double ms,
-                 u64* out, cudaStream_t st) {
+// out = M_lo (x) a + M_hi (x) b per limb for n ciphertexts (both masks shared):
+// the two PMults and the addition of a token rotation in one pass
+__global__ void k_mask_pair(const u64* a, const u64* b, const u64* mlo, const u64* mhi, u64* out,
+                            const Modulus* mods, int nl, int logN) {
+    const int N = 1 << logN;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int limb = blockIdx.y, ci = blockIdx.z;  // limb over 2 nl
+    const int i = limb % nl;
+    const Modulus m = mods[i];
+    const size_t o = ((size_t)ci * 2 * nl + limb) * N + x, mo = (size_t)i * N + x;
+    out[o] = add_mod(mul_mod(a[o], mlo[mo], m), mul_mod(b[o], mhi[mo], m), m.q);
+}
+
+// The token masks of every r = 1 .. n - 1 at `level`, encoded once per call:
+// plaintext 2 (r - 1) selects the tokens t < n - r, 2 (r - 1) + 1 the others.
+struct TokenMasks {
+    Dev buf;
+    u64* pts = nullptr;
+    size_t pt_words = 0;
+    explicit TokenMasks(cudaStream_t st) : buf(st) {}
+    const u64* lo(int r) const { return pts + (size_t)(2 * (r - 1)) * pt_words; }
+    const u64* hi(int r) const { return pts + (size_t)(2 * (r - 1) + 1) * pt_words; }
+};
+int make_token_masks(fe_ctx* c, const fe_token_layout& T, int level, double ms, TokenMasks& M, cudaStream_t st) {
+    const int half = c->N / 2, n = (int)T.n_tok;
+    if (n < 2) return FE_OK;
+    const size_t n_pt = 2 * (size_t)(n - 1);
+    M.pt_words = (size_t)(level + 1) * c->N;
+    M.pts = M.buf.get<u64>(n_pt * M.pt_words);
+    Dev sb(st);
+    double* slots = sb.get<double>(n_pt * half);
+    if (!M.pts || !slots) return fail(FE_ENOMEM, "token mask scratch");
+    for (int r = 1; r < n; r++) {
+        double* lo = slots + (size_t)(2 * (r - 1)) * half;
+        k_token_mask<<<(half + kB - 1) / kB, kB, 0, st>>>(lo, lo + half, n, r, half);
+        c->cnt.launches++;
+    }
+    FE_CUDA_TRY(cudaGetLastError());
+    return fe_encode(c, slots, (uint32_t)n_pt, (uint32_t)level, ms, M.pts, st);
+}
+
+// token-wise rotation of n ciphertexts at `level` by r tokens (one level):
+// out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n));
+// r = 0: rescale(x times the integer ms).  tmp: 3 n ciphertexts at `level`.
+int token_rotate(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int n_ct, int level, int r,
+                 double ms, const TokenMasks& M, u64* tmp, u64* out, cudaStream_t st) {
     const size_t ctw = ct_words(c, level);
-    Dev buf(st);
-    u64* tmp = buf.get<u64>(2 * ctw);
-    if (!tmp) return fail(FE_ENOMEM, "token rotation scratch");
+    const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
     if (r == 0) {
-        Dev kb(st);
-        u64* k = kb.get<u64>(level + 1);
-        if (!k) return fail(FE_ENOMEM, "token rotation scratch");
         std::vector<u64> kh(level + 1);
         const u64 m = (u64)ms;  // a power of two below the modulus
         for (int i = 0; i <= level; i++) kh[i] = m % c->mod[i];
+        u64* k = tmp + n_ct * ctw;  // the per-limb constants (level + 1 words)
         FE_TRY(copy_host_table(k, kh.data(), kh.size() * 8, st));
-        k_mul_const<<<dim3((c->N + kB - 1) / kB, 2 * (level + 1), 1), kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1,
-                                                                                 c->logN);
+        k_mul_const<<<grid, kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1, c->logN);
         c->cnt.launches++;
         FE_CUDA_TRY(cudaGetLastError());
-        return fe_rescale(c, tmp, 1, level, out, st);
+        return fe_rescale(c, tmp, n_ct, level, out, st);
     }
-    const int half = c->N / 2, n = (int)T.n_tok;
-    Dev sb(st), pb(st);
-    double* slots = sb.get<double>(2 * (size_t)half);
-    u64* pts = pb.get<u64>(2 * (size_t)(level + 1) * c->N);
-    if (!slots || !pts) return fail(FE_ENOMEM, "token rotation scratch");
-    k_token_mask<<<(half + kB - 1) / kB, kB, 0, st>>>(slots, slots + half, n, r, half);
-    c->cnt.launches++;
-    FE_TRY(fe_encode(c, slots, 2, level, ms, pts, st));
     u64* a = tmp;
-    u64* b = tmp + ctw;
-    FE_TRY(fe_rotate(c, evk, x, 1, level, r, a, st));
-    FE_TRY(fe_rotate(c, evk, x, 1, level, r - n, b, st));
-    FE_TRY(fe_pmult(c, a, pts, 1, level, a, st));
-    FE_TRY(fe_pmult(c, b, pts + (size_t)(level + 1) * c->N, 1, level, b, st));
-    FE_TRY(fe_add(c, a, b, 1, level, a, st));
-    return fe_rescale(c, a, 1, level, out, st);
+    u64* b = tmp + n_ct * ctw;
+    u64* s = tmp + 2 * n_ct * ctw;
+    FE_TRY(fe_rotate(c, evk, x, n_ct, level, r, a, st));
+    FE_TRY(fe_rotate(c, evk, x, n_ct, level, r - (int)T.n_tok, b, st));
+    k_mask_pair<<<grid, kB, 0, st>>>(a, b, M.lo(r), M.hi(r), s, c->d_mod, level + 1, c->logN);
+    c->cnt.launches++;
+    c->cnt.pmult += 2 * n_ct;
+    FE_CUDA_TRY(cudaGetLastError());
+    return fe_rescale(c, s, n_ct, level, out, st);
 }
 
-// acc += Rot(acc, 2^k n) for k = 0 .. log2(P) - 1 (one ciphertext at `level`)
-int position_sum(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, u64* acc, int level, cudaStream_t st) {
-    Dev rb(st);
-    u64* rot = rb.get<u64>(ct_words(c, level));
-    if (!rot) return fail(FE_ENOMEM, "position sum scratch");
+// acc += Rot(acc, 2^k n) for k = 0 .. log2(P) - 1, n_ct ciphertexts at `level`
+// (rot: n_ct ciphertexts of scratch)
+int position_sum(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, u64* acc, int n_ct, int level, u64* rot,
+                 cudaStream_t st) {
     for (uint32_t step = T.n_tok; step < (uint32_t)c->N / 2; step *= 2) {
-        FE_TRY(fe_rotate(c, evk, acc, 1, level, (int32_t)step, rot, st));
-        FE_TRY(fe_add(c, acc, rot, 1, level, acc, st));
+        FE_TRY(fe_rotate(c, evk, acc, n_ct, level, (int32_t)step, rot, st));
+        FE_TRY(fe_add(c, acc, rot, n_ct, level, acc, st));
     }
     return FE_OK;
-}
-
-// d = relin(x (x) y) at `level` (one pair)
-int cmult_one(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int level, u64* d, cudaStream_t st) {
-    const size_t bytes = cmult_relin_bytes(c, 1, level);
-    Dev wb(st);
-    char* ws = wb.get<char>(bytes);
-    if (!ws) return fail(FE_ENOMEM, "CMult scratch");
-    Carver cv(ws, bytes);
-    return cmult_relin(c, evk, x, y, 1, level, d, cv, st);
 }
 
 int check_common(fe_ctx* c, const fe_evk* evk, const fe_token_layout* lay, fe_token_layout* T) {
@@ -202,25 +225,37 @@ extern "C" int fe_he_attention_scores(fe_ctx* c, const fe_evk* evk, const fe_tok
     FE_ALIGNED(out_dev);
     if (level < 2 || (int)level > c->L) return fail(FE_ELEVEL, "the attention scores need two levels");
     cudaStream_t st = (cudaStream_t)stream;
-    const int lv = (int)level;
+    const int lv = (int)level, n = (int)T.n_tok, S = (int)T.n_ct;
     const double ms = mask_scale_pow2(c, lv);
     const size_t ctw = ct_words(c, lv), ctw1 = ct_words(c, lv - 1), ctw2 = ct_words(c, lv - 2);
-    Dev qb(st), wb(st);
-    u64* qd = qb.get<u64>(T.n_ct * ctw1);          // Q with one limb dropped
-    u64* work = wb.get<u64>(3 * ctw1);              // rotated K, product, running sum
-    if (!qd || !work) return fail(FE_ENOMEM, "attention scratch");
-    FE_TRY(drop_limb(c, (const u64*)q_dev, (int)T.n_ct, lv, qd, st));
-    u64 *kr = work, *prod = work + ctw1, *acc = work + 2 * ctw1;
-    for (uint32_t r = 0; r < T.n_tok; r++) {
-        for (uint32_t s = 0; s < T.n_ct; s++) {
-            FE_TRY(token_rotate(c, evk, T, (const u64*)k_dev + s * ctw, lv, (int)r, ms, kr, st));
-            FE_TRY(cmult_one(c, evk, qd + s * ctw1, kr, lv - 1, s == 0 ? acc : prod, st));
-            if (s) FE_TRY(fe_add(c, acc, prod, 1, lv - 1, acc, st));
+    TokenMasks M(st);
+    FE_TRY(make_token_masks(c, T, lv, ms, M, st));
+    const size_t cm_bytes = cmult_relin_bytes(c, S, lv - 1);
+    Dev qb(st), wb(st), tb(st), cb(st), rb(st);
+    u64* qd = qb.get<u64>(S * ctw1);                    // Q with one limb dropped
+    u64* work = wb.get<u64>(2 * S * ctw1 + ctw1);       // rotated K, products, running sum
+    u64* tmp = tb.get<u64>(3 * S * ctw);                // token rotation scratch
+    char* cm = cb.get<char>(cm_bytes);                  // CMult scratch
+    u64* rot = rb.get<u64>((size_t)n * ctw2);           // position-sum scratch
+    if (!qd || !work || !tmp || !cm || !rot) return fail(FE_ENOMEM, "attention scratch");
+    FE_TRY(drop_limb(c, (const u64*)q_dev, S, lv, qd, st));
+    u64 *kr = work, *prod = work + S * ctw1, *acc = work + 2 * S * ctw1;
+    // diagonal r: sum over s of Q_s times K_s rotated by r tokens, rescaled; then
+    // every diagonal's position sums at once
+    for (int r = 0; r < n; r++) {
+        FE_TRY(token_rotate(c, evk, T, (const u64*)k_dev, S, lv, r, ms, M, tmp, kr, st));
+        Carver cv(cm, cm_bytes);
+        FE_TRY(cmult_relin(c, evk, qd, kr, S, lv - 1, prod, cv, st));
+        const u64* sum = prod;
+        if (S > 1) {
+            FE_TRY(fe_add(c, prod, prod + ctw1, 1, lv - 1, acc, st));
+            for (int q = 2; q < S; q++) FE_TRY(fe_add(c, acc, prod + q * ctw1, 1, lv - 1, acc, st));
+            sum = acc;
         }
-        u64* d = (u64*)out_dev + r * ctw2;
-        FE_TRY(fe_rescale(c, acc, 1, lv - 1, d, st));
-        FE_TRY(position_sum(c, evk, T, d, lv - 2, st));
+        FE_TRY(fe_rescale(c, sum, 1, lv - 1, (u64*)out_dev + r * ctw2, st));
     }
+    FE_TRY(position_sum(c, evk, T, (u64*)out_dev, n, lv - 2, rot, st));
+    (void)ctw;
     // scales as the operations change them: K rotated (k ms) / q_l, product q (.),
     // rescale by q_{l-1}
     const double kr_scale = (k_scale * ms) / (double)c->mod[lv];
@@ -242,40 +277,48 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
     if (v_level < 1 || (int)v_level > c->L || d_level < 1 || (int)d_level > c->L)
         return fail(FE_ELEVEL, "level out of range");
     cudaStream_t st = (cudaStream_t)stream;
-    const int vl = (int)v_level, dl = (int)d_level;
+    const int vl = (int)v_level, dl = (int)d_level, n = (int)T.n_tok, S = (int)T.n_ct;
     const int ml = std::min(vl - 1, dl);  // level of the products
     if (ml < 1) return fail(FE_ELEVEL, "the attention output needs a level to rescale");
     const double ms = mask_scale_pow2(c, vl);
-    const size_t ctwv = ct_words(c, vl), ctwd = ct_words(c, dl), ctwm = ct_words(c, ml);
-    Dev wb(st), tb(st);
-    u64* work = wb.get<u64>(3 * ct_words(c, vl - 1));
-    u64* tmp = tb.get<u64>(2 * ct_words(c, std::max(vl - 1, dl)));
-    if (!work || !tmp) return fail(FE_ENOMEM, "attention scratch");
-    u64 *vr = work, *prod = work + ct_words(c, vl - 1), *acc = work + 2 * ct_words(c, vl - 1);
-    for (uint32_t s = 0; s < T.n_ct; s++) {
-        for (uint32_t r = 0; r < T.n_tok; r++) {
-            FE_TRY(token_rotate(c, evk, T, (const u64*)v_dev + s * ctwv, vl, (int)r, ms, vr, st));
-            // drop the higher of the two to the products' level, one limb at a time
-            const u64* x = (const u64*)d_dev + r * ctwd;
-            const u64* y = vr;
-            u64* bx = tmp;
-            u64* by = tmp + ct_words(c, std::max(vl - 1, dl));
-            for (int l = dl; l > ml; l--) {
-                u64* dst = (x == bx) ? by : bx;
-                FE_TRY(drop_limb(c, x, 1, l, dst, st));
-                x = dst;
-            }
-            for (int l = vl - 1; l > ml; l--) {
-                u64* dst = (y == bx || x == bx) ? by : bx;
-                FE_TRY(drop_limb(c, y, 1, l, dst, st));
-                y = dst;
-            }
-            FE_TRY(cmult_one(c, evk, x, y, ml, r == 0 ? acc : prod, st));
-            if (r) FE_TRY(fe_add(c, acc, prod, 1, ml, acc, st));
+    const size_t ctwv = ct_words(c, vl), ctwv1 = ct_words(c, vl - 1), ctwd = ct_words(c, dl),
+                 ctwm = ct_words(c, ml);
+    TokenMasks M(st);
+    FE_TRY(make_token_masks(c, T, vl, ms, M, st));
+    const size_t cm_bytes = cmult_relin_bytes(c, S, ml);
+    const size_t wide = std::max(ctwv1, ctwd);
+    Dev wb(st), tb(st), db(st), cb(st);
+    u64* work = wb.get<u64>(S * ctwv1 + 2 * S * ctwm);  // rotated V, products, sums
+    u64* tmp = tb.get<u64>(3 * S * ctwv);                // token rotation scratch
+    u64* drop = db.get<u64>(2 * S * wide + S * ctwm);    // level drops, D_r for every s
+    char* cm = cb.get<char>(cm_bytes);
+    if (!work || !tmp || !drop || !cm) return fail(FE_ENOMEM, "attention scratch");
+    u64 *vr = work, *prod = work + S * ctwv1, *acc = prod + S * ctwm;
+    u64 *bx = drop, *by = drop + S * wide, *drep = drop + 2 * S * wide;
+    // output s: sum over r of D_r times V_s rotated by r tokens, every s at once
+    for (int r = 0; r < n; r++) {
+        FE_TRY(token_rotate(c, evk, T, (const u64*)v_dev, S, vl, r, ms, M, tmp, vr, st));
+        // drop D_r and the rotated V to the products' level, one limb at a time
+        const u64* x = (const u64*)d_dev + r * ctwd;
+        for (int l = dl; l > ml; l--) {
+            u64* dst = (x == bx) ? by : bx;
+            FE_TRY(drop_limb(c, x, 1, l, dst, st));
+            x = dst;
         }
-        FE_TRY(fe_rescale(c, acc, 1, ml, (u64*)out_dev + s * ct_words(c, ml - 1), st));
+        for (int q = 0; q < S; q++)
+            FE_CUDA_TRY(cudaMemcpyAsync(drep + q * ctwm, x, ctwm * 8, cudaMemcpyDeviceToDevice, st));
+        const u64* y = vr;
+        for (int l = vl - 1; l > ml; l--) {
+            u64* dst = (y == bx) ? by : bx;
+            FE_TRY(drop_limb(c, y, S, l, dst, st));
+            y = dst;
+        }
+        Carver cv(cm, cm_bytes);
+        FE_TRY(cmult_relin(c, evk, drep, y, S, ml, r == 0 ? acc : prod, cv, st));
+        if (r) FE_TRY(fe_add(c, acc, prod, S, ml, acc, st));
     }
-    (void)ctwm;
+    FE_TRY(fe_rescale(c, acc, S, ml, (u64*)out_dev, st));
+    (void)ctwv;
     const double vr_scale = (v_scale * ms) / (double)c->mod[vl];
     if (out_level) *out_level = (uint32_t)(ml - 1);
     if (out_scale) *out_scale = (d_scale * vr_scale) / (double)c->mod[ml];

@@ -561,7 +561,6 @@ extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint3
     cudaFreeAsync(acc, st);
     cudaFreeAsync(conv, st);
     cudaFreeAsync(items, st);
-    FE_CUDA_TRY(cudaStreamSynchronize(st));
     FE_CUDA_TRY(cudaGetLastError());
     return FE_OK;
 }
@@ -578,7 +577,6 @@ extern "C" int fe_rescale(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t
     FE_CUDA_TRY(cudaMallocAsync(&tmp, rescale_tmp_words(c, n_ct, level) * 8, st));
     rescale_batch(c, (const u64*)ct_dev, n_ct, level, (u64*)out_dev, tmp, tmp + 2 * (size_t)n_ct * c->N, st);
     cudaFreeAsync(tmp, st);
-    FE_CUDA_TRY(cudaStreamSynchronize(st));
     FE_CUDA_TRY(cudaGetLastError());
     return FE_OK;
 }

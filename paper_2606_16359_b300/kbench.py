@@ -9,6 +9,7 @@
     python -m paper_2606_16359_b300.kbench configs [--reps 5]
     python -m paper_2606_16359_b300.kbench repack
     python -m paper_2606_16359_b300.kbench refresh [--reps 5] [--graph 1]
+    python -m paper_2606_16359_b300.kbench transformer [--tokens 128] [--embed 768] [--reps 3]
 
 ntt: forward and inverse negacyclic NTT over a batch of limbs of the 36-bit
      moduli (N = 2^logN); algorithmic bytes 2 N w per limb transform (read and
@@ -21,6 +22,8 @@ refresh: one ciphertext refresh (bootstrapping) at N = 2^16 with 24 + 4 primes o
      a profiler's launch list.  --graph 1 captures the refresh in one CUDA
      graph (fe_boot_graph_capture; checked equal to the direct call) and times
      its replays.
+transformer: the Sec. 7 extension at BERT-base shapes (a projection, the
+     attention products, an FFN), N = 2^16 with the convolution parameters.
 keyswitch: rotations (hybrid key switch + automorphism) of n ciphertexts at one
      level with one key; algorithmic bytes per key switch without key reuse
      [(l+1) + 2 dnum (l+1+k) + 2 (l+1)] N w.
@@ -278,6 +281,99 @@ def bench_repack(ctx, torch, args):
     return {"kernel": "repack_plans", "logN": ctx.logN, "level": L, "blocks": out}
 
 
+def bench_transformer(ctx, torch, args):
+    """The transformer extension (Sec. 7) at N = 2^16, 24 + 4 primes of --qbits
+    bits (36: the convolution parameters; 50: the refresh's), scale
+    2^(qbits - 4), BERT-base shapes: n = 128
+    tokens, E = 768, S from fe_choose_token_fragment (gamma = 6).  Timed (CUDA
+    events, one warm-up, --reps runs): a projection E -> E; the attention
+    products Q K^T (its n diagonals) and (Q K^T) V with token-wise rotations;
+    an FFN E' -> 4 E' -> E' with 0.125 x^2 + 0.5 x + 0.25 between, E' = 256,
+    the widest whose hidden layer fits the P = N / (2 n) positions at the same
+    S.  Inputs U[-1, 1) (Q and K scaled by E^(-1/4) / 2.3 and V by 1/4, so
+    that every product stays near unit size); weights N(0, 1 / fan_in).
+    Reports ms, key switches and the decryption's max error against FP64."""
+    import numpy as np
+
+    import paper_2606_16359_b300 as fe
+    n, E, gam, Ef = args.tokens, args.embed, 6.0, 256
+    S = fe.choose_token_fragment(E, n, gam)["S"]
+    L, delta = ctx.L, 2.0 ** (args.qbits - 4)
+    a, b, c = 0.125, 0.5, 0.25
+    rng = np.random.default_rng(21)
+    lay = ctx.token_layout(n, E, S)
+    lay_f = ctx.token_layout(n, Ef, S)
+    p_proj = ctx.plan_token_linear(lay, E, L)
+    p_f1 = ctx.plan_token_linear(lay_f, 4 * Ef, L)
+    p_f2 = ctx.plan_token_linear(p_f1.token_out, Ef, L - 2)
+    steps = sorted(set(ctx.attention_rotation_steps(lay)) |
+                   {s for p in (p_proj, p_f1, p_f2) for s in p.steps})
+    sk = ctx.sk_gen(5)
+    evk = ctx.evk_gen(sk, 5, steps, relin=True)
+    x = rng.uniform(-1, 1, (n, E))
+    wp = rng.normal(0, 1 / np.sqrt(E), (E, E))
+    qa = E ** -0.25 / 2.3
+    Q, K = (rng.uniform(-qa, qa, (n, E)) for _ in range(2))
+    V = rng.uniform(-0.25, 0.25, (n, E))
+    xf = rng.uniform(-1, 1, (n, Ef))
+    w1 = rng.normal(0, 1 / np.sqrt(Ef), (4 * Ef, Ef))
+    w2 = rng.normal(0, 1 / np.sqrt(4 * Ef), (Ef, 4 * Ef))
+    enc = lambda X, ly, sd: ctx.encrypt(sk, ctx.token_pack(ly, torch.from_numpy(X)), L, delta, sd)  # noqa: E731
+    ct_x, ct_q, ct_k, ct_v, ct_f = enc(x, lay, 1), enc(Q, lay, 2), enc(K, lay, 3), enc(V, lay, 4), enc(xf, lay_f, 6)
+    pt_p = ctx.load_weights(p_proj, wp, ctx.weight_scale(L, delta, delta))
+    pt_1 = ctx.load_weights(p_f1, w1, ctx.weight_scale(L, delta, delta, a))
+    s1 = ctx.plan_out_scale(p_f1, delta)
+    s_act = ctx.poly_act_scale(L - 1, s1, a)
+    pt_2 = ctx.load_weights(p_f2, w2, ctx.weight_scale(L - 2, s_act, delta))
+
+    def projection():
+        return ctx.he_fc(evk, p_proj, pt_p, ct_x)
+
+    def attention():
+        D, d_scale = ctx.he_attention_scores(evk, lay, ct_q, ct_k, L, delta, delta)
+        return ctx.he_attention_apply(evk, lay, D, L - 2, d_scale, ct_v, L, delta)
+
+    def ffn():
+        h = ctx.he_fc(evk, p_f1, pt_1, ct_f)
+        h, _ = ctx.he_poly_act(evk, h, L - 1, s1, a, b, c)
+        return ctx.he_fc(evk, p_f2, pt_2, h)
+
+    def timed(fn):
+        r = fn()
+        torch.cuda.synchronize()
+        ctx.reset_counters()
+        fn()
+        torch.cuda.synchronize()
+        ks = ctx.counters()["keyswitch"]
+        st = torch.cuda.current_stream()
+        t0, t1 = _events(torch)
+        t0.record(st)
+        for _ in range(args.reps):
+            fn()
+        t1.record(st)
+        torch.cuda.synchronize()
+        return r, t0.elapsed_time(t1) / args.reps, ks
+
+    res = {"what": "transformer", "logN": ctx.logN, "qbits": args.qbits, "scale_log2": args.qbits - 4,
+           "level": L, "tokens": n, "embed": E, "S": S,
+           "rotation_keys": len(steps), "evk_gb": round(evk.buf.numel() * 8 / 1e9, 1), "reps": args.reps}
+    out, ms, ks = timed(projection)
+    y = ctx.token_unpack(p_proj.token_out, ctx.decrypt(sk, out, L - 1, ctx.plan_out_scale(p_proj, delta)))
+    res["projection"] = {"ms": ms, "keyswitches": ks,
+                         "max_abs_err": float(np.abs(y.cpu().numpy() - x @ wp.T).max())}
+    (O, o_level, o_scale), ms, ks = timed(attention)
+    y = ctx.token_unpack(lay, ctx.decrypt(sk, O, o_level, o_scale))
+    res["attention"] = {"ms": ms, "keyswitches": ks, "out_level": o_level,
+                        "max_abs_err": float(np.abs(y.cpu().numpy() - (Q @ K.T) @ V).max())}
+    out, ms, ks = timed(ffn)
+    y = ctx.token_unpack(p_f2.token_out, ctx.decrypt(sk, out, L - 3, ctx.plan_out_scale(p_f2, s_act)))
+    t = xf @ w1.T
+    res["ffn"] = {"embed": Ef, "hidden": 4 * Ef, "ms": ms, "keyswitches": ks,
+                  "max_abs_err": float(np.abs(y.cpu().numpy() - (a * t * t + b * t + c) @ w2.T).max())}
+    assert ctx.device_status() == 0
+    return res
+
+
 def bench_configs(ctx_unused, torch, args):
     """The two small configurations end to end on the GPU: the single 5x5 conv
     1 -> 6 at N = 2^13 (S = 4) and the LeNet-shaped network at N = 2^14
@@ -386,7 +482,9 @@ def bench_refresh(ctx_unused, torch, args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["ntt", "alu", "keyswitch", "mac", "layer", "aac", "configs", "repack",
-                                     "refresh"])
+                                     "refresh", "transformer"])
+    ap.add_argument("--tokens", type=int, default=128, help="transformer: tokens n")
+    ap.add_argument("--embed", type=int, default=768, help="transformer: embedding dimension E")
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--qbits", type=int, default=36,
                     help="modulus bits of the 24 + 4 primes (36: the convolution parameters; 50: the refresh's)")
@@ -421,7 +519,7 @@ def main(argv=None):
         ctx = fe.Context(args.logN, 24, 4, args.qbits, args.qbits)
         fn = {"ntt": bench_ntt, "alu": bench_alu, "keyswitch": bench_keyswitch, "mac": bench_mac,
               "layer": bench_layer, "aac": bench_aac, "configs": bench_configs,
-              "repack": bench_repack, "refresh": bench_refresh}[args.what]
+              "repack": bench_repack, "refresh": bench_refresh, "transformer": bench_transformer}[args.what]
         print(json.dumps(fn(ctx, torch, args)), flush=True)
     return 0
 
