@@ -136,34 +136,67 @@ int make_token_masks(fe_ctx* c, const fe_token_layout& T, int level, double ms, 
     return fe_encode(c, slots, (uint32_t)n_pt, (uint32_t)level, ms, M.pts, st);
 }
 
-// token-wise rotation of n ciphertexts at `level` by r tokens (one level):
-// out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n));
-// r = 0: rescale(x times the integer ms).  tmp: 3 n ciphertexts at `level`.
-int token_rotate(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int n_ct, int level, int r,
-                 double ms, const TokenMasks& M, u64* tmp, u64* out, cudaStream_t st) {
-    const size_t ctw = ct_words(c, level);
+// Token-wise rotation of n ciphertexts at `level` by r tokens (one level):
+// out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n)).
+// r = 0: rescale(x times the integer ms), token_rotate0; r > 0: the two
+// rotations come in a and b (rotate_many, hoisted over every r of a chunk) and
+// token_unmask applies the masks.  tmp: n ciphertexts at `level` plus level + 1 words.
+int token_rotate0(fe_ctx* c, const u64* x, int n_ct, int level, double ms, u64* tmp, u64* out, cudaStream_t st) {
     const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
-    if (r == 0) {
-        std::vector<u64> kh(level + 1);
-        const u64 m = (u64)ms;  // a power of two below the modulus
-        for (int i = 0; i <= level; i++) kh[i] = m % c->mod[i];
-        u64* k = tmp + n_ct * ctw;  // the per-limb constants (level + 1 words)
-        FE_TRY(copy_host_table(k, kh.data(), kh.size() * 8, st));
-        k_mul_const<<<grid, kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1, c->logN);
-        c->cnt.launches++;
-        FE_CUDA_TRY(cudaGetLastError());
-        return fe_rescale(c, tmp, n_ct, level, out, st);
-    }
-    u64* a = tmp;
-    u64* b = tmp + n_ct * ctw;
-    u64* s = tmp + 2 * n_ct * ctw;
-    FE_TRY(fe_rotate(c, evk, x, n_ct, level, r, a, st));
-    FE_TRY(fe_rotate(c, evk, x, n_ct, level, r - (int)T.n_tok, b, st));
-    k_mask_pair<<<grid, kB, 0, st>>>(a, b, M.lo(r), M.hi(r), s, c->d_mod, level + 1, c->logN);
+    std::vector<u64> kh(level + 1);
+    const u64 m = (u64)ms;  // a power of two below the modulus
+    for (int i = 0; i <= level; i++) kh[i] = m % c->mod[i];
+    u64* k = tmp + n_ct * ct_words(c, level);  // the per-limb constants
+    FE_TRY(copy_host_table(k, kh.data(), kh.size() * 8, st));
+    k_mul_const<<<grid, kB, 0, st>>>(x, tmp, c->d_mod, k, level + 1, c->logN);
+    c->cnt.launches++;
+    FE_CUDA_TRY(cudaGetLastError());
+    return fe_rescale(c, tmp, n_ct, level, out, st);
+}
+int token_unmask(fe_ctx* c, const u64* a, const u64* b, int n_ct, int level, int r, const TokenMasks& M, u64* tmp,
+                 u64* out, cudaStream_t st) {
+    const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
+    k_mask_pair<<<grid, kB, 0, st>>>(a, b, M.lo(r), M.hi(r), tmp, c->d_mod, level + 1, c->logN);
     c->cnt.launches++;
     c->cnt.pmult += 2 * n_ct;
     FE_CUDA_TRY(cudaGetLastError());
-    return fe_rescale(c, s, n_ct, level, out, st);
+    return fe_rescale(c, tmp, n_ct, level, out, st);
+}
+
+// Every token rotation of n_ct ciphertexts x at `level`, r = 0 .. n - 1, in
+// order: the rotations by r and r - n of a chunk of r values hoisted together
+// (rb: 2 chunk n_ct ciphertexts), then each r's masks; each result (n_ct
+// ciphertexts at level - 1 in kr) goes to use(r, kr).
+template <class Use>
+int token_rotations(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int n_ct, int level,
+                    double ms, const TokenMasks& M, int chunk, u64* rb, u64* tmp, u64* kr, Use&& use,
+                    cudaStream_t st) {
+    const int n = (int)T.n_tok;
+    const size_t ctw = ct_words(c, level);
+    FE_TRY(token_rotate0(c, x, n_ct, level, ms, tmp, kr, st));
+    FE_TRY(use(0, kr));
+    std::vector<int32_t> steps;
+    for (int r0 = 1; r0 < n; r0 += chunk) {
+        const int rn = std::min(chunk, n - r0);
+        steps.clear();
+        for (int r = r0; r < r0 + rn; r++) {
+            steps.push_back(r);
+            steps.push_back(r - n);
+        }
+        FE_TRY(rotate_many(c, evk, x, n_ct, level, steps.data(), 2 * rn, rb, st));
+        for (int i = 0; i < rn; i++) {
+            const u64* a = rb + (size_t)(2 * i) * n_ct * ctw;
+            FE_TRY(token_unmask(c, a, a + n_ct * ctw, n_ct, level, r0 + i, M, tmp, kr, st));
+            FE_TRY(use(r0 + i, kr));
+        }
+    }
+    return FE_OK;
+}
+
+// r values per hoisted chunk: the rotated copies (2 chunk n_ct ciphertexts) within 2 GB
+int rotation_chunk(const fe_ctx* c, int n_tok, int n_ct, int level) {
+    const size_t per_r = 2 * (size_t)n_ct * ct_words(c, level) * 8;
+    return (int)std::max<size_t>(1, std::min<size_t>(std::max(1, n_tok - 1), (2ull << 30) / per_r));
 }
 
 // acc += Rot(acc, 2^k n) for k = 0 .. log2(P) - 1, n_ct ciphertexts at `level`
@@ -231,31 +264,32 @@ extern "C" int fe_he_attention_scores(fe_ctx* c, const fe_evk* evk, const fe_tok
     TokenMasks M(st);
     FE_TRY(make_token_masks(c, T, lv, ms, M, st));
     const size_t cm_bytes = cmult_relin_bytes(c, S, lv - 1);
-    Dev qb(st), wb(st), tb(st), cb(st), rb(st);
+    const int chunk = rotation_chunk(c, n, S, lv);
+    Dev qb(st), wb(st), tb(st), cb(st), rb(st), hb(st);
     u64* qd = qb.get<u64>(S * ctw1);                    // Q with one limb dropped
     u64* work = wb.get<u64>(2 * S * ctw1 + ctw1);       // rotated K, products, running sum
-    u64* tmp = tb.get<u64>(3 * S * ctw);                // token rotation scratch
+    u64* tmp = tb.get<u64>(S * ctw + 2 * c->N);         // token rotation scratch
     char* cm = cb.get<char>(cm_bytes);                  // CMult scratch
     u64* rot = rb.get<u64>((size_t)n * ctw2);           // position-sum scratch
-    if (!qd || !work || !tmp || !cm || !rot) return fail(FE_ENOMEM, "attention scratch");
+    u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctw);  // hoisted rotations of K
+    if (!qd || !work || !tmp || !cm || !rot || !hoist) return fail(FE_ENOMEM, "attention scratch");
     FE_TRY(drop_limb(c, (const u64*)q_dev, S, lv, qd, st));
     u64 *kr = work, *prod = work + S * ctw1, *acc = work + 2 * S * ctw1;
     // diagonal r: sum over s of Q_s times K_s rotated by r tokens, rescaled; then
     // every diagonal's position sums at once
-    for (int r = 0; r < n; r++) {
-        FE_TRY(token_rotate(c, evk, T, (const u64*)k_dev, S, lv, r, ms, M, tmp, kr, st));
+    auto diagonal = [&](int r, const u64* krr) -> int {
         Carver cv(cm, cm_bytes);
-        FE_TRY(cmult_relin(c, evk, qd, kr, S, lv - 1, prod, cv, st));
+        FE_TRY(cmult_relin(c, evk, qd, krr, S, lv - 1, prod, cv, st));
         const u64* sum = prod;
         if (S > 1) {
             FE_TRY(fe_add(c, prod, prod + ctw1, 1, lv - 1, acc, st));
             for (int q = 2; q < S; q++) FE_TRY(fe_add(c, acc, prod + q * ctw1, 1, lv - 1, acc, st));
             sum = acc;
         }
-        FE_TRY(fe_rescale(c, sum, 1, lv - 1, (u64*)out_dev + r * ctw2, st));
-    }
+        return fe_rescale(c, sum, 1, lv - 1, (u64*)out_dev + r * ctw2, st);
+    };
+    FE_TRY(token_rotations(c, evk, T, (const u64*)k_dev, S, lv, ms, M, chunk, hoist, tmp, kr, diagonal, st));
     FE_TRY(position_sum(c, evk, T, (u64*)out_dev, n, lv - 2, rot, st));
-    (void)ctw;
     // scales as the operations change them: K rotated (k ms) / q_l, product q (.),
     // rescale by q_{l-1}
     const double kr_scale = (k_scale * ms) / (double)c->mod[lv];
@@ -287,17 +321,18 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
     FE_TRY(make_token_masks(c, T, vl, ms, M, st));
     const size_t cm_bytes = cmult_relin_bytes(c, S, ml);
     const size_t wide = std::max(ctwv1, ctwd);
-    Dev wb(st), tb(st), db(st), cb(st);
+    const int chunk = rotation_chunk(c, n, S, vl);
+    Dev wb(st), tb(st), db(st), cb(st), hb(st);
     u64* work = wb.get<u64>(S * ctwv1 + 2 * S * ctwm);  // rotated V, products, sums
-    u64* tmp = tb.get<u64>(3 * S * ctwv);                // token rotation scratch
+    u64* tmp = tb.get<u64>(S * ctwv + 2 * c->N);         // token rotation scratch
     u64* drop = db.get<u64>(2 * S * wide + S * ctwm);    // level drops, D_r for every s
     char* cm = cb.get<char>(cm_bytes);
-    if (!work || !tmp || !drop || !cm) return fail(FE_ENOMEM, "attention scratch");
+    u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctwv);  // hoisted rotations of V
+    if (!work || !tmp || !drop || !cm || !hoist) return fail(FE_ENOMEM, "attention scratch");
     u64 *vr = work, *prod = work + S * ctwv1, *acc = prod + S * ctwm;
     u64 *bx = drop, *by = drop + S * wide, *drep = drop + 2 * S * wide;
     // output s: sum over r of D_r times V_s rotated by r tokens, every s at once
-    for (int r = 0; r < n; r++) {
-        FE_TRY(token_rotate(c, evk, T, (const u64*)v_dev, S, vl, r, ms, M, tmp, vr, st));
+    auto term = [&](int r, const u64* vrr) -> int {
         // drop D_r and the rotated V to the products' level, one limb at a time
         const u64* x = (const u64*)d_dev + r * ctwd;
         for (int l = dl; l > ml; l--) {
@@ -307,7 +342,7 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
         }
         for (int q = 0; q < S; q++)
             FE_CUDA_TRY(cudaMemcpyAsync(drep + q * ctwm, x, ctwm * 8, cudaMemcpyDeviceToDevice, st));
-        const u64* y = vr;
+        const u64* y = vrr;
         for (int l = vl - 1; l > ml; l--) {
             u64* dst = (y == bx) ? by : bx;
             FE_TRY(drop_limb(c, y, S, l, dst, st));
@@ -316,7 +351,9 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
         Carver cv(cm, cm_bytes);
         FE_TRY(cmult_relin(c, evk, drep, y, S, ml, r == 0 ? acc : prod, cv, st));
         if (r) FE_TRY(fe_add(c, acc, prod, S, ml, acc, st));
-    }
+        return FE_OK;
+    };
+    FE_TRY(token_rotations(c, evk, T, (const u64*)v_dev, S, vl, ms, M, chunk, hoist, tmp, vr, term, st));
     FE_TRY(fe_rescale(c, acc, S, ml, (u64*)out_dev, st));
     (void)ctwv;
     const double vr_scale = (v_scale * ms) / (double)c->mod[vl];

@@ -514,6 +514,78 @@ extern "C" int fe_probe_butterflies(fe_ctx* c, uint32_t blocks, uint32_t iters, 
     return FE_OK;
 }
 
+namespace fe {
+int rotate_many(fe_ctx* c, const fe_evk* evk, const u64* in, int n_ct, int level, const int32_t* steps,
+                int n_steps, u64* out, cudaStream_t st) {
+    if (n_ct <= 0 || n_steps <= 0) return FE_OK;
+    const int N = c->N, nl = level + 1;
+    const size_t ctw = ct_words(c, level), aw = acc_words(c, level), ew = ext_words(c, level);
+    std::vector<const u64*> key(n_steps, nullptr);
+    std::vector<uint32_t> gal(n_steps, 1);
+    for (int j = 0; j < n_steps; j++) {
+        if (steps[j] != FE_STEP_CONJ && steps[j] % (N / 2) == 0) continue;  // the identity
+        gal[j] = c->galois(steps[j]);
+        key[j] = evk_key(evk, gal[j]);
+        if (!key[j]) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(steps[j]));
+    }
+    const size_t per_step = (size_t)n_ct * (aw + ctw) * 8;
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_steps, (4ull << 30) / per_step));
+    u64 *coef = nullptr, *ext = nullptr, *acc = nullptr, *conv = nullptr;
+    void* items = nullptr;
+    const size_t item_bytes = (size_t)chunk * n_ct * (sizeof(KsItem) + sizeof(CombineItem)) + (size_t)chunk * sizeof(KsGroup);
+    int rc = FE_OK;
+    if (cudaMallocAsync(&coef, (size_t)n_ct * nl * N * 8, st) != cudaSuccess ||
+        cudaMallocAsync(&ext, (size_t)n_ct * ew * 8, st) != cudaSuccess ||
+        cudaMallocAsync(&acc, (size_t)chunk * n_ct * aw * 8, st) != cudaSuccess ||
+        cudaMallocAsync(&conv, (size_t)chunk * n_ct * ctw * 8, st) != cudaSuccess ||
+        cudaMallocAsync(&items, item_bytes, st) != cudaSuccess)
+        rc = fail(FE_ENOMEM, "hoisted rotation scratch");
+    if (rc == FE_OK) modup(c, in + (size_t)nl * N, ctw, n_ct, level, coef, ext, st);
+    KsItem* dks = (KsItem*)items;
+    CombineItem* dcb = (CombineItem*)(dks + (size_t)chunk * n_ct);
+    KsGroup* dkg = (KsGroup*)(dcb + (size_t)chunk * n_ct);
+    for (int j0 = 0; rc == FE_OK && j0 < n_steps; j0 += chunk) {
+        const int jn = std::min(chunk, n_steps - j0);
+        std::vector<KsItem> ks;
+        std::vector<CombineItem> cb;
+        std::vector<KsGroup> kg;
+        for (int j = j0; j < j0 + jn; j++) {
+            u64* o = out + (size_t)j * n_ct * ctw;
+            if (!key[j]) {
+                if (cudaMemcpyAsync(o, in, (size_t)n_ct * ctw * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    rc = fail(FE_ECUDA, "hoisted rotation copy");
+                continue;
+            }
+            kg.push_back(KsGroup{key[j], (int)ks.size(), n_ct});
+            for (int i = 0; i < n_ct; i++) {
+                const size_t k = ks.size();
+                ks.push_back(KsItem{ext + i * ew, key[j], acc + k * aw});
+                cb.push_back(CombineItem{acc + k * aw, conv + k * ctw, in + i * ctw, nullptr, o + i * ctw, gal[j], 0});
+            }
+        }
+        if (ks.empty() || rc != FE_OK) continue;
+        const int m = (int)ks.size();
+        rc = upload(ks, dks, st);
+        if (rc == FE_OK) rc = upload(cb, dcb, st);
+        if (rc == FE_OK) rc = upload(kg, dkg, st);
+        if (rc != FE_OK) break;
+        launch_keyip_grouped(c, dkg, dks, (int)kg.size(), m, level, st, n_ct);
+        moddown_prepare(c, acc, m, level, conv, st);
+        launch_combine(c, dcb, m, level, st);
+        c->cnt.rot += m;
+        c->cnt.keyswitch += m;
+    }
+    if (coef) cudaFreeAsync(coef, st);
+    if (ext) cudaFreeAsync(ext, st);
+    if (acc) cudaFreeAsync(acc, st);
+    if (conv) cudaFreeAsync(conv, st);
+    if (items) cudaFreeAsync(items, st);
+    FE_TRY(rc);
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+}  // namespace fe
+
 extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                          int32_t r, void* out_dev, void* stream) {
     FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);

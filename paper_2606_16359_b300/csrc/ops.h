@@ -23,6 +23,14 @@ inline size_t ct_words(const fe_ctx* c, int level) { return 2 * (size_t)(level +
 // ([n][dnum][l+1+k][N], NTT form).
 void modup(fe_ctx* c, const u64* src, size_t src_stride, int n, int level, u64* coef, u64* ext,
            cudaStream_t st);
+// Rotations of n_ct ciphertexts at `level` by each of n_steps steps with one
+// ModUp per ciphertext for all steps: out holds [n_steps][n_ct] ciphertexts,
+// each the residues fe_rotate gives (the key switch precedes the
+// automorphism, so the extended digits of c1 serve every step).  Scratch from
+// the stream-ordered allocator; steps are taken in chunks whose accumulators
+// fit 4 GB.  Errors: FE_EKEY (a missing key), FE_ENOMEM, FE_ECUDA.
+int rotate_many(fe_ctx* c, const fe_evk* evk, const u64* in, int n_ct, int level, const int32_t* steps,
+                int n_steps, u64* out, cudaStream_t st);
 // ModDown preparation for n accumulators acc [n][2][l+1+k][N] (NTT form): the P limbs are
 // inverse-transformed in place, converted to Q_level into conv [n][2][l+1][N] and transformed.
 void moddown_prepare(fe_ctx* c, u64* acc, int n, int level, u64* conv, cudaStream_t st);
