@@ -365,6 +365,15 @@ def bench_transformer(ctx, torch, args):
     y = ctx.token_unpack(lay, ctx.decrypt(sk, O, o_level, o_scale))
     res["attention"] = {"ms": ms, "keyswitches": ks, "out_level": o_level,
                         "max_abs_err": float(np.abs(y.cpu().numpy() - (Q @ K.T) @ V).max())}
+    if args.classes:
+        # CUDA-event time of each kernel class over one attention call (one call per class)
+        by = {}
+        for kd in ("ntt", "bconv", "keyip", "combine", "mac", "rescale", "encode"):
+            ctx.profile_begin(kd)
+            attention()
+            t, nl, byt = ctx.profile_end()
+            by[kd] = {"ms": round(t, 2), "launches": nl}
+        res["attention"]["by_class"] = by
     out, ms, ks = timed(ffn)
     y = ctx.token_unpack(p_f2.token_out, ctx.decrypt(sk, out, L - 3, ctx.plan_out_scale(p_f2, s_act)))
     t = xf @ w1.T
@@ -485,6 +494,7 @@ def main(argv=None):
                                      "refresh", "transformer"])
     ap.add_argument("--tokens", type=int, default=128, help="transformer: tokens n")
     ap.add_argument("--embed", type=int, default=768, help="transformer: embedding dimension E")
+    ap.add_argument("--classes", type=int, default=0, help="transformer: 1 adds the attention's time by kernel class")
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--qbits", type=int, default=36,
                     help="modulus bits of the 24 + 4 primes (36: the convolution parameters; 50: the refresh's)")
