@@ -151,6 +151,7 @@ SIGNATURES = {
     "fe_ntt": (cint, [vp, vp, u32, u32, u32, cint, vp]),
     "fe_probe_butterflies": (cint, [vp, u32, u32, vp, P(u64), vp]),
     "fe_rotate": (cint, [vp, vp, vp, u32, u32, i32, vp, vp]),
+    "fe_rotate_many": (cint, [vp, vp, vp, u32, u32, P(i32), u32, vp, vp]),
     "fe_rescale": (cint, [vp, vp, u32, u32, vp, vp]),
     "fe_rescale_noalloc": (cint, [vp, vp, u32, u32, vp, vp]),
     "fe_pmult": (cint, [vp, vp, vp, u32, u32, vp, vp]),
@@ -524,6 +525,14 @@ class Context:
     def rotate(self, evk, ct, level, r):
         out = self.empty_ct(ct.shape[0], level)
         check(load().fe_rotate(self.handle, evk.handle, _ptr(ct), ct.shape[0], level, r, _ptr(out), _stream()))
+        return out
+
+    def rotate_many(self, evk, ct, level, steps):
+        """Hoisted rotations: returns [len(steps), n_ct, 2, level + 1, N], entry j = rotate(ct, steps[j])."""
+        n, k = ct.shape[0], len(steps)
+        out = _torch().empty((k, n, 2, level + 1, self.N), dtype=_torch().int64, device="cuda")
+        arr = (i32 * max(1, k))(*steps)
+        check(load().fe_rotate_many(self.handle, evk.handle, _ptr(ct), n, level, arr, k, _ptr(out), _stream()))
         return out
 
     def conjugate(self, evk, ct, level):

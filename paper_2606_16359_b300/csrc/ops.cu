@@ -586,6 +586,17 @@ int rotate_many(fe_ctx* c, const fe_evk* evk, const u64* in, int n_ct, int level
 }
 }  // namespace fe
 
+extern "C" int fe_rotate_many(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
+                              const int32_t* steps, uint32_t n_steps, void* out_dev, void* stream) {
+    FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);
+    if (!c || !evk || !ct_dev || !out_dev || (n_steps && !steps)) return fail(FE_EINVAL, "null argument");
+    if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
+    if (n_ct == 0 || n_steps == 0) return FE_OK;
+    if (n_ct > (1u << 20) || n_steps > (1u << 20)) return fail(FE_EINVAL, "n_ct and n_steps must be below 2^20");
+    return rotate_many(c, evk, (const u64*)ct_dev, (int)n_ct, (int)level, steps, (int)n_steps, (u64*)out_dev,
+                       (cudaStream_t)stream);
+}
+
 extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                          int32_t r, void* out_dev, void* stream) {
     FE_ALIGNED(ct_dev); FE_ALIGNED(out_dev);

@@ -182,10 +182,16 @@ def test_rotate_rescale_pmult_add_parity(which, tiny, ks2):
     octs = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], pr.L, 2.0 ** 25), 2, i) for i in range(2)]
     ct = g.encrypt(sk, torch.from_numpy(z), pr.L, 2.0 ** 25, seed=2)
     assert np.array_equal(u64(ct), oracle_ct_array(octs))
+    wants = {}
     for r in steps:
         got = g.rotate(evk, ct, pr.L, r)
-        want = oracle_ct_array([ckks.rotate(pr, keys, c, r) for c in octs])
-        assert np.array_equal(u64(got), want), r
+        wants[r] = oracle_ct_array([ckks.rotate(pr, keys, c, r) for c in octs])
+        assert np.array_equal(u64(got), wants[r]), r
+    # hoisted: one ModUp per ciphertext for every step (and the identity step 0)
+    many = u64(g.rotate_many(evk, ct, pr.L, steps + [0]))
+    for j, r in enumerate(steps):
+        assert np.array_equal(many[j], wants[r]), r
+    assert np.array_equal(many[len(steps)], u64(ct))
     w = rng.uniform(-1, 1, (2, pr.N // 2))
     pts = g.encode(torch.from_numpy(w), pr.L, float(pr.q[pr.L]))
     opts = [ckks.encode(pr, w[i], pr.L, float(pr.q[pr.L])) for i in range(2)]
