@@ -138,9 +138,8 @@ int make_token_masks(fe_ctx* c, const fe_token_layout& T, int level, double ms, 
 
 // Token-wise rotation of n ciphertexts at `level` by r tokens (one level):
 // out (level - 1) = rescale(M_lo (x) Rot(x, r) + M_hi (x) Rot(x, r - n)).
-// r = 0: rescale(x times the integer ms), token_rotate0; r > 0: the two
-// rotations come in a and b (rotate_many, hoisted over every r of a chunk) and
-// token_unmask applies the masks.  tmp: n ciphertexts at `level` plus level + 1 words.
+// r = 0: rescale(x times the integer ms), token_rotate0 (tmp: n ciphertexts at
+// `level` plus level + 1 words); r > 0: token_rotations below.
 int token_rotate0(fe_ctx* c, const u64* x, int n_ct, int level, double ms, u64* tmp, u64* out, cudaStream_t st) {
     const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
     std::vector<u64> kh(level + 1);
@@ -153,20 +152,14 @@ int token_rotate0(fe_ctx* c, const u64* x, int n_ct, int level, double ms, u64* 
     FE_CUDA_TRY(cudaGetLastError());
     return fe_rescale(c, tmp, n_ct, level, out, st);
 }
-int token_unmask(fe_ctx* c, const u64* a, const u64* b, int n_ct, int level, int r, const TokenMasks& M, u64* tmp,
-                 u64* out, cudaStream_t st) {
-    const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
-    k_mask_pair<<<grid, kB, 0, st>>>(a, b, M.lo(r), M.hi(r), tmp, c->d_mod, level + 1, c->logN);
-    c->cnt.launches++;
-    c->cnt.pmult += 2 * n_ct;
-    FE_CUDA_TRY(cudaGetLastError());
-    return fe_rescale(c, tmp, n_ct, level, out, st);
-}
 
 // Every token rotation of n_ct ciphertexts x at `level`, r = 0 .. n - 1, in
-// order: the rotations by r and r - n of a chunk of r values hoisted together
-// (rb: 2 chunk n_ct ciphertexts), then each r's masks; each result (n_ct
-// ciphertexts at level - 1 in kr) goes to use(r, kr).
+// order, a chunk of r values at a time: the rotations by r and r - n hoisted
+// together into rb (2 chunk n_ct ciphertexts), each r's masks applied with the
+// result compacted in place to the front of rb (result i overwrites rotated
+// copies that results before it already consumed), and one rescale of the
+// chunk into kr (chunk n_ct ciphertexts at level - 1, [r][ct]); then
+// use(r0, rn, kr) for r = r0 .. r0 + rn - 1.  r = 0 comes alone.
 template <class Use>
 int token_rotations(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, const u64* x, int n_ct, int level,
                     double ms, const TokenMasks& M, int chunk, u64* rb, u64* tmp, u64* kr, Use&& use,
@@ -174,8 +167,9 @@ int token_rotations(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, cons
     const int n = (int)T.n_tok;
     const size_t ctw = ct_words(c, level);
     FE_TRY(token_rotate0(c, x, n_ct, level, ms, tmp, kr, st));
-    FE_TRY(use(0, kr));
+    FE_TRY(use(0, 1, kr));
     std::vector<int32_t> steps;
+    const dim3 grid((c->N + kB - 1) / kB, 2 * (level + 1), n_ct);
     for (int r0 = 1; r0 < n; r0 += chunk) {
         const int rn = std::min(chunk, n - r0);
         steps.clear();
@@ -186,9 +180,14 @@ int token_rotations(fe_ctx* c, const fe_evk* evk, const fe_token_layout& T, cons
         FE_TRY(rotate_many(c, evk, x, n_ct, level, steps.data(), 2 * rn, rb, st));
         for (int i = 0; i < rn; i++) {
             const u64* a = rb + (size_t)(2 * i) * n_ct * ctw;
-            FE_TRY(token_unmask(c, a, a + n_ct * ctw, n_ct, level, r0 + i, M, tmp, kr, st));
-            FE_TRY(use(r0 + i, kr));
+            k_mask_pair<<<grid, kB, 0, st>>>(a, a + n_ct * ctw, M.lo(r0 + i), M.hi(r0 + i), rb + (size_t)i * n_ct * ctw,
+                                            c->d_mod, level + 1, c->logN);
+            c->cnt.launches++;
+            c->cnt.pmult += 2 * n_ct;
         }
+        FE_CUDA_TRY(cudaGetLastError());
+        FE_TRY(fe_rescale(c, rb, (uint32_t)(rn * n_ct), level, kr, st));
+        FE_TRY(use(r0, rn, kr));
     }
     return FE_OK;
 }
@@ -263,32 +262,40 @@ extern "C" int fe_he_attention_scores(fe_ctx* c, const fe_evk* evk, const fe_tok
     const size_t ctw = ct_words(c, lv), ctw1 = ct_words(c, lv - 1), ctw2 = ct_words(c, lv - 2);
     TokenMasks M(st);
     FE_TRY(make_token_masks(c, T, lv, ms, M, st));
-    const size_t cm_bytes = cmult_relin_bytes(c, S, lv - 1);
     const int chunk = rotation_chunk(c, n, S, lv);
-    Dev qb(st), wb(st), tb(st), cb(st), rb(st), hb(st);
-    u64* qd = qb.get<u64>(S * ctw1);                    // Q with one limb dropped
-    u64* work = wb.get<u64>(2 * S * ctw1 + ctw1);       // rotated K, products, running sum
-    u64* tmp = tb.get<u64>(S * ctw + 2 * c->N);         // token rotation scratch
-    char* cm = cb.get<char>(cm_bytes);                  // CMult scratch
-    u64* rot = rb.get<u64>((size_t)n * ctw2);           // position-sum scratch
-    u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctw);  // hoisted rotations of K
-    if (!qd || !work || !tmp || !cm || !rot || !hoist) return fail(FE_ENOMEM, "attention scratch");
-    FE_TRY(drop_limb(c, (const u64*)q_dev, S, lv, qd, st));
-    u64 *kr = work, *prod = work + S * ctw1, *acc = work + 2 * S * ctw1;
-    // diagonal r: sum over s of Q_s times K_s rotated by r tokens, rescaled; then
-    // every diagonal's position sums at once
-    auto diagonal = [&](int r, const u64* krr) -> int {
+    const size_t cm_bytes = cmult_relin_bytes(c, chunk * S, lv - 1);
+    const size_t cw = (size_t)chunk * S * ctw1;  // one chunk's ciphertexts at lv - 1
+    Dev wb(st), tb(st), cb(st), rb(st), hb(st);
+    u64* work = wb.get<u64>(3 * cw + (size_t)chunk * ctw1);  // Q copies, rotated K, products, sums
+    u64* tmp = tb.get<u64>(S * ctw + 2 * c->N);              // token rotation scratch (r = 0)
+    char* cm = cb.get<char>(cm_bytes);                       // CMult scratch
+    u64* rot = rb.get<u64>((size_t)n * ctw2);                // position-sum scratch
+    u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctw);   // hoisted rotations of K
+    if (!work || !tmp || !cm || !rot || !hoist) return fail(FE_ENOMEM, "attention scratch");
+    u64 *qrep = work, *kr = work + cw, *prod = work + 2 * cw, *sums = work + 3 * cw;
+    // Q with one limb dropped, once per r of a chunk
+    FE_TRY(drop_limb(c, (const u64*)q_dev, S, lv, qrep, st));
+    for (int i = 1; i < chunk; i++)
+        FE_CUDA_TRY(cudaMemcpyAsync(qrep + (size_t)i * S * ctw1, qrep, (size_t)S * ctw1 * 8, cudaMemcpyDeviceToDevice,
+                                    st));
+    // diagonal r: sum over s of Q_s times K_s rotated by r tokens, rescaled; the
+    // CMults of a chunk of r values at once; then every diagonal's position sums
+    auto diagonals = [&](int r0, int rn, const u64* krr) -> int {
         Carver cv(cm, cm_bytes);
-        FE_TRY(cmult_relin(c, evk, qd, krr, S, lv - 1, prod, cv, st));
+        FE_TRY(cmult_relin(c, evk, qrep, krr, rn * S, lv - 1, prod, cv, st));
         const u64* sum = prod;
         if (S > 1) {
-            FE_TRY(fe_add(c, prod, prod + ctw1, 1, lv - 1, acc, st));
-            for (int q = 2; q < S; q++) FE_TRY(fe_add(c, acc, prod + q * ctw1, 1, lv - 1, acc, st));
-            sum = acc;
+            for (int i = 0; i < rn; i++) {
+                const u64* p = prod + (size_t)i * S * ctw1;
+                u64* a = sums + (size_t)i * ctw1;
+                FE_TRY(fe_add(c, p, p + ctw1, 1, lv - 1, a, st));
+                for (int q = 2; q < S; q++) FE_TRY(fe_add(c, a, p + q * ctw1, 1, lv - 1, a, st));
+            }
+            sum = sums;
         }
-        return fe_rescale(c, sum, 1, lv - 1, (u64*)out_dev + r * ctw2, st);
+        return fe_rescale(c, sum, (uint32_t)rn, lv - 1, (u64*)out_dev + (size_t)r0 * ctw2, st);
     };
-    FE_TRY(token_rotations(c, evk, T, (const u64*)k_dev, S, lv, ms, M, chunk, hoist, tmp, kr, diagonal, st));
+    FE_TRY(token_rotations(c, evk, T, (const u64*)k_dev, S, lv, ms, M, chunk, hoist, tmp, kr, diagonals, st));
     FE_TRY(position_sum(c, evk, T, (u64*)out_dev, n, lv - 2, rot, st));
     // scales as the operations change them: K rotated (k ms) / q_l, product q (.),
     // rescale by q_{l-1}
@@ -319,41 +326,53 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
                  ctwm = ct_words(c, ml);
     TokenMasks M(st);
     FE_TRY(make_token_masks(c, T, vl, ms, M, st));
-    const size_t cm_bytes = cmult_relin_bytes(c, S, ml);
     const size_t wide = std::max(ctwv1, ctwd);
     const int chunk = rotation_chunk(c, n, S, vl);
+    const size_t cm_bytes = cmult_relin_bytes(c, chunk * S, ml);
+    const size_t cs = (size_t)chunk * S;  // ciphertexts of one chunk
     Dev wb(st), tb(st), db(st), cb(st), hb(st);
-    u64* work = wb.get<u64>(S * ctwv1 + 2 * S * ctwm);  // rotated V, products, sums
-    u64* tmp = tb.get<u64>(S * ctwv + 2 * c->N);         // token rotation scratch
-    u64* drop = db.get<u64>(2 * S * wide + S * ctwm);    // level drops, D_r for every s
+    u64* work = wb.get<u64>(cs * ctwv1 + cs * ctwm + S * ctwm);  // rotated V, products, sums
+    u64* tmp = tb.get<u64>(S * ctwv + 2 * c->N);                  // token rotation scratch (r = 0)
+    u64* drop = db.get<u64>(2 * cs * wide + cs * ctwm);           // level drops, D_r for every s
     char* cm = cb.get<char>(cm_bytes);
-    u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctwv);  // hoisted rotations of V
+    u64* hoist = hb.get<u64>(2 * cs * ctwv);                      // hoisted rotations of V
     if (!work || !tmp || !drop || !cm || !hoist) return fail(FE_ENOMEM, "attention scratch");
-    u64 *vr = work, *prod = work + S * ctwv1, *acc = prod + S * ctwm;
-    u64 *bx = drop, *by = drop + S * wide, *drep = drop + 2 * S * wide;
-    // output s: sum over r of D_r times V_s rotated by r tokens, every s at once
-    auto term = [&](int r, const u64* vrr) -> int {
-        // drop D_r and the rotated V to the products' level, one limb at a time
-        const u64* x = (const u64*)d_dev + r * ctwd;
-        for (int l = dl; l > ml; l--) {
-            u64* dst = (x == bx) ? by : bx;
-            FE_TRY(drop_limb(c, x, 1, l, dst, st));
-            x = dst;
+    u64 *vr = work, *prod = work + cs * ctwv1, *acc = prod + cs * ctwm;
+    u64 *bx = drop, *by = drop + cs * wide, *drep = drop + 2 * cs * wide;
+    // output s: sum over r of D_r times V_s rotated by r tokens, every s and a
+    // chunk of r values at once
+    auto terms = [&](int r0, int rn, const u64* vrr) -> int {
+        // D_r dropped to the products' level (one limb at a time), one copy per s
+        for (int i = 0; i < rn; i++) {
+            const u64* x = (const u64*)d_dev + (size_t)(r0 + i) * ctwd;
+            for (int l = dl; l > ml; l--) {
+                u64* dst = (x == bx) ? by : bx;
+                FE_TRY(drop_limb(c, x, 1, l, dst, st));
+                x = dst;
+            }
+            for (int q = 0; q < S; q++)
+                FE_CUDA_TRY(cudaMemcpyAsync(drep + ((size_t)i * S + q) * ctwm, x, ctwm * 8, cudaMemcpyDeviceToDevice,
+                                            st));
         }
-        for (int q = 0; q < S; q++)
-            FE_CUDA_TRY(cudaMemcpyAsync(drep + q * ctwm, x, ctwm * 8, cudaMemcpyDeviceToDevice, st));
+        // the rotated V of the chunk dropped the same way
         const u64* y = vrr;
         for (int l = vl - 1; l > ml; l--) {
             u64* dst = (y == bx) ? by : bx;
-            FE_TRY(drop_limb(c, y, S, l, dst, st));
+            FE_TRY(drop_limb(c, y, rn * S, l, dst, st));
             y = dst;
         }
         Carver cv(cm, cm_bytes);
-        FE_TRY(cmult_relin(c, evk, drep, y, S, ml, r == 0 ? acc : prod, cv, st));
-        if (r) FE_TRY(fe_add(c, acc, prod, S, ml, acc, st));
+        FE_TRY(cmult_relin(c, evk, drep, y, rn * S, ml, prod, cv, st));
+        for (int i = 0; i < rn; i++) {
+            const u64* p = prod + (size_t)i * S * ctwm;
+            if (r0 + i == 0)
+                FE_CUDA_TRY(cudaMemcpyAsync(acc, p, (size_t)S * ctwm * 8, cudaMemcpyDeviceToDevice, st));
+            else
+                FE_TRY(fe_add(c, acc, p, S, ml, acc, st));
+        }
         return FE_OK;
     };
-    FE_TRY(token_rotations(c, evk, T, (const u64*)v_dev, S, vl, ms, M, chunk, hoist, tmp, vr, term, st));
+    FE_TRY(token_rotations(c, evk, T, (const u64*)v_dev, S, vl, ms, M, chunk, hoist, tmp, vr, terms, st));
     FE_TRY(fe_rescale(c, acc, S, ml, (u64*)out_dev, st));
     (void)ctwv;
     const double vr_scale = (v_scale * ms) / (double)c->mod[vl];
