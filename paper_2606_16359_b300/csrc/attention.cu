@@ -374,7 +374,6 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
     };
     FE_TRY(token_rotations(c, evk, T, (const u64*)v_dev, S, vl, ms, M, chunk, hoist, tmp, vr, terms, st));
     FE_TRY(fe_rescale(c, acc, S, ml, (u64*)out_dev, st));
-    (void)ctwv;
     const double vr_scale = (v_scale * ms) / (double)c->mod[vl];
     if (out_level) *out_level = (uint32_t)(ml - 1);
     if (out_scale) *out_scale = (d_scale * vr_scale) / (double)c->mod[ml];
