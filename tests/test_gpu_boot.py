@@ -124,18 +124,23 @@ def test_refresh_bit_exact_against_the_oracle(small):
     assert np.abs(dec - z).max() < 1e-4
 
 
-def test_refresh_graph_replays_the_direct_refresh(small):
+@pytest.mark.parametrize("form", ["complex", "real"])
+def test_refresh_graph_replays_the_direct_refresh(small, form):
     """fe_boot_graph_capture: one captured graph of the refresh of two
-    ciphertexts, replayed on two batches copied into its input buffer, gives the
-    direct call's residues for each batch, and the oracle's."""
-    pr, bp, ctx, sk, keys, s = small
+    ciphertexts (either transform form), replayed on two batches copied into its
+    input buffer, gives the direct call's residues for each batch, and the
+    oracle's."""
+    pr, _, ctx, sk, keys, s = small
+    bp = boot.BootParams(pr, 3, 3, 6, form=form)
+    for st in boot.boot_rotation_steps(pr, bp):
+        keys.add_rotation(st)
     s_in = 2.0 ** 45
     rng = np.random.default_rng(12)
     z = rng.uniform(-1, 1, (2, 2, pr.N // 2))
     octs = [[ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[j][i], 0, s_in), 7, 10 + 2 * j + i) for i in range(2)]
             for j in range(2)]
     with torch.cuda.stream(s):
-        b = ctx.boot_create(s_in, 3, 3, 6)
+        b = ctx.boot_create(s_in, 3, 3, 6, form=form)
         evk = ctx.evk_gen(sk, 11, b.steps, relin=True)
         ws = ctx.workspace(b.workspace_bytes(2))
         x = to_gpu(octs[0])
@@ -364,7 +369,8 @@ def test_refresh_steps_bit_exact_at_full_size():
 def test_encapsulated_refresh_bit_exact():
     """Sparse-secret encapsulation at N = 2^10: a dense secret (fe_sk_gen) for the
     ciphertext and the refresh's keys, a sparse one (weight 32) borrowed for
-    ModRaise; the generic key switch and the refresh equal the oracle's."""
+    ModRaise; the generic key switch and the refresh equal the oracle's, and so
+    does the refresh captured as one graph and run through host buffers."""
     logN, n_q, k, bits, h = 10, 20, 4, 50, 32
     pr = ckks.Params(logN, n_q, k, bits)
     bp = boot.BootParams(pr, 3, 3, 6)
@@ -387,8 +393,19 @@ def test_encapsulated_refresh_bit_exact():
     with torch.cuda.stream(s):
         ks = u64(ctx.key_switch(b.encaps_keys[:b.encaps_keys.numel() // 2], to_gpu([octs5]), lv))
         got = u64(ctx.bootstrap(evk, b, to_gpu([oct_])))
+        # the same refresh as one captured graph (its two key switches carry their
+        # tables in the graph), run through host buffers
+        x = to_gpu([oct_])
+        y = ctx.empty_ct(1, b.out_level)
+        g = ctx.boot_graph_capture(evk, b, x, y, ctx.workspace(b.workspace_bytes(1)))
+        h_in = x.cpu().pin_memory()
+        h_out = torch.empty(y.numel(), dtype=torch.int64).pin_memory()
+        x.zero_()
+        g.launch_host([h_in], [h_out])
         torch.cuda.synchronize()
+        got_graph = h_out.numpy().view(np.uint64).reshape(got.shape)
     assert np.array_equal(ks[0], oracle_ct(pr, boot.key_switch(pr, octs5, enc.to_sparse)))
     want = boot.bootstrap(pr, keys, oct_, bp, encaps=enc)
     assert np.array_equal(got[0], oracle_ct(pr, want))
+    assert np.array_equal(got_graph, got)
     assert np.abs(ckks.decrypt(pr, keys.sk, want) - z).max() < 1e-4
