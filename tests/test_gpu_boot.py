@@ -339,6 +339,45 @@ def test_refresh_chain_full_size(encapsulate, n_blocks):
     assert ch.out_level == 2 and err < 1e-3
 
 
+def test_refresh_chain_captured_as_one_graph():
+    """The whole block-refresh-block network at N = 2^16 (dense secret,
+    encapsulated refresh) captured by the caller as one CUDA graph
+    (torch.cuda.CUDAGraph around RefreshChain.forward): every library call in it
+    carries its per-call tables in the graph, so the replay gives the direct
+    forward pass's residues; both times are reported."""
+    from paper_2606_16359_b300 import net
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fe.Context(16, 24, 4, 50)
+        ch = net.RefreshChain(ctx, 14, 32, h=64, encapsulate=True)
+        want = ch.forward()
+        for _ in range(2):
+            ch.forward()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        for _ in range(3):
+            ch.forward()
+        t1.record(s)
+        torch.cuda.synchronize()
+        ms_direct = t0.elapsed_time(t1) / 3
+        g = torch.cuda.CUDAGraph()
+        g.capture_begin()
+        got = ch.forward()
+        g.capture_end()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
+        t0.record(s)
+        for _ in range(3):
+            g.replay()
+        t1.record(s)
+        torch.cuda.synchronize()
+        ms_graph = t0.elapsed_time(t1) / 3
+        assert torch.equal(got, want)
+    print(f"block + refresh + block at N=2^16, dense secret: {ms_direct:.1f} ms direct, {ms_graph:.1f} ms as one graph")
+
+
 def test_refresh_steps_bit_exact_at_full_size():
     """At the refresh's full parameter set (N = 2^16, 24 + 4 primes of 50 bits,
     secret weight 64), the steps the oracle can afford there are compared
