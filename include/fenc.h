@@ -445,7 +445,12 @@ int fe_plan_token_linear(fe_ctx* ctx, const fe_token_layout* in_lay, uint32_t E_
  * d_level)), rescaled once: *out_level = m - 1, *out_scale = (d_scale
  * ((v_scale ms) / q_{v_level})) / q_m.  Softmax and other non-linear parts of
  * attention are not included.  Composed from the library's primitives with
- * stream-ordered scratch.  Errors: FE_EKEY, FE_ELEVEL, FE_EINVAL, FE_ENOMEM. */
+ * stream-ordered scratch.  Each call encodes its 2 (n_tok - 1) masks once
+ * (2 (n_tok - 1) (level + 1) N 8 bytes: 3.2 GB at n_tok = 128, level 23,
+ * N = 2^16) and hoists the token rotations of a chunk of offsets (about 2 GB
+ * of rotated copies, plus the chunk's CMult scratch); synchronises `stream`
+ * once, after the mask encode.  Errors: FE_EKEY, FE_ELEVEL, FE_EINVAL,
+ * FE_ENOMEM, FE_EENCODE. */
 int fe_attention_rotation_steps(const fe_ctx* ctx, const fe_token_layout* lay, int32_t* steps, uint32_t max,
                                 uint32_t* n_steps);
 int fe_he_attention_scores(fe_ctx* ctx, const fe_evk* evk, const fe_token_layout* lay, const void* q_dev,
