@@ -290,7 +290,8 @@ def bench_transformer(ctx, torch, args):
     products Q K^T (its n diagonals) and (Q K^T) V with token-wise rotations;
     an FFN E' -> 4 E' -> E' with 0.125 x^2 + 0.5 x + 0.25 between, E' = 256,
     the widest whose hidden layer fits the P = N / (2 n) positions at the same
-    S.  Inputs U[-1, 1) (Q and K scaled by E^(-1/4) / 2.3 and V by 1/4, so
+    S; --hoist 1 runs the linear layers double-hoisted.  Inputs U[-1, 1) (Q
+    and K scaled by E^(-1/4) / 2.3 and V by 1/4, so
     that every product stays near unit size); weights N(0, 1 / fan_in).
     Reports ms, key switches and the decryption's max error against FP64."""
     import numpy as np
@@ -306,6 +307,8 @@ def bench_transformer(ctx, torch, args):
     p_proj = ctx.plan_token_linear(lay, E, L)
     p_f1 = ctx.plan_token_linear(lay_f, 4 * Ef, L)
     p_f2 = ctx.plan_token_linear(p_f1.token_out, Ef, L - 2)
+    for p in (p_proj, p_f1, p_f2):
+        ctx.plan_set_hoisting(p, args.hoist)
     steps = sorted(set(ctx.attention_rotation_steps(lay)) |
                    {s for p in (p_proj, p_f1, p_f2) for s in p.steps})
     sk = ctx.sk_gen(5)
@@ -355,6 +358,7 @@ def bench_transformer(ctx, torch, args):
         return r, t0.elapsed_time(t1) / args.reps, ks
 
     res = {"what": "transformer", "logN": ctx.logN, "qbits": args.qbits, "scale_log2": args.qbits - 4,
+           "linear_hoisting": args.hoist,
            "level": L, "tokens": n, "embed": E, "S": S,
            "rotation_keys": len(steps), "evk_gb": round(evk.buf.numel() * 8 / 1e9, 1), "reps": args.reps}
     out, ms, ks = timed(projection)
@@ -495,6 +499,8 @@ def main(argv=None):
     ap.add_argument("--tokens", type=int, default=128, help="transformer: tokens n")
     ap.add_argument("--embed", type=int, default=768, help="transformer: embedding dimension E")
     ap.add_argument("--classes", type=int, default=0, help="transformer: 1 adds the attention's time by kernel class")
+    ap.add_argument("--hoist", type=int, default=0,
+                    help="transformer: hoisting of the linear layers (0 single, 1 double: baby rotations on Q P)")
     ap.add_argument("--logN", type=int, default=16)
     ap.add_argument("--qbits", type=int, default=36,
                     help="modulus bits of the 24 + 4 primes (36: the convolution parameters; 50: the refresh's)")
