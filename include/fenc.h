@@ -299,8 +299,9 @@ int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct,
  * FE_STEP_CONJ allowed), out_dev [n_steps][n_ct] ciphertexts at `level`.
  * One ModUp per input ciphertext serves all steps, and each step's key is
  * read once for all n_ct; every output equals fe_rotate's residues.  Scratch
- * from the stream-ordered allocator.  Errors: FE_EINVAL, FE_ELEVEL, FE_EKEY
- * (a step without its key), FE_ENOMEM. */
+ * from the stream-ordered allocator.  Errors: FE_EINVAL (null pointer, outputs
+ * overlapping the inputs), FE_ELEVEL, FE_EKEY (a step without its key),
+ * FE_ENOMEM. */
 int fe_rotate_many(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
                    const int32_t* steps_host, uint32_t n_steps, void* out_dev, void* stream);
 /* Rescale n_ct ciphertexts from `level` to level-1: (c - [c]_{q_l}) q_l^-1 with

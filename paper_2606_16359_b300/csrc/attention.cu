@@ -77,7 +77,11 @@ struct Dev {
     }
     template <class T>
     T* get(size_t count) {
-        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) return nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), st) != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();  // the caller reports FE_ENOMEM; nothing stays pending
+            return nullptr;
+        }
         return (T*)p;
     }
 };

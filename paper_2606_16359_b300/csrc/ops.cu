@@ -538,8 +538,10 @@ int rotate_many(fe_ctx* c, const fe_evk* evk, const u64* in, int n_ct, int level
         cudaMallocAsync(&ext, (size_t)n_ct * ew * 8, st) != cudaSuccess ||
         cudaMallocAsync(&acc, (size_t)chunk * n_ct * aw * 8, st) != cudaSuccess ||
         cudaMallocAsync(&conv, (size_t)chunk * n_ct * ctw * 8, st) != cudaSuccess ||
-        cudaMallocAsync(&items, item_bytes, st) != cudaSuccess)
+        cudaMallocAsync(&items, item_bytes, st) != cudaSuccess) {
+        (void)cudaGetLastError();  // an allocation failure is reported as FE_ENOMEM, not left pending
         rc = fail(FE_ENOMEM, "hoisted rotation scratch");
+    }
     if (rc == FE_OK) modup(c, in + (size_t)nl * N, ctw, n_ct, level, coef, ext, st);
     KsItem* dks = (KsItem*)items;
     CombineItem* dcb = (CombineItem*)(dks + (size_t)chunk * n_ct);
@@ -593,6 +595,9 @@ extern "C" int fe_rotate_many(fe_ctx* c, const fe_evk* evk, const void* ct_dev, 
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     if (n_ct == 0 || n_steps == 0) return FE_OK;
     if (n_ct > (1u << 20) || n_steps > (1u << 20)) return fail(FE_EINVAL, "n_ct and n_steps must be below 2^20");
+    const size_t in_b = (size_t)n_ct * ct_words(c, (int)level) * 8, out_b = in_b * n_steps;
+    const char *i0 = (const char*)ct_dev, *o0 = (const char*)out_dev;
+    if (o0 < i0 + in_b && i0 < o0 + out_b) return fail(FE_EINVAL, "the outputs overlap the inputs");
     return rotate_many(c, evk, (const u64*)ct_dev, (int)n_ct, (int)level, steps, (int)n_steps, (u64*)out_dev,
                        (cudaStream_t)stream);
 }

@@ -82,6 +82,12 @@ def test_rejected_calls_return_their_status_and_leave_the_context_usable(g, keys
         ("null context", lambda: lib.fe_rescale(None, P(ct), 1, g.L, P(out), s), fe.FE_EINVAL),
         ("no-alloc rescale at level 0", lambda: lib.fe_rescale_noalloc(g.handle, P(ct), 1, 0, P(out), s),
          fe.FE_ELEVEL),
+        ("hoisted rotations in place", lambda: lib.fe_rotate_many(g.handle, evk.handle, P(ct), 1, g.L,
+                                                                  (ctypes.c_int32 * 2)(1, 1), 2, P(ct), s),
+         fe.FE_EINVAL),
+        ("hoisted rotation without its key", lambda: lib.fe_rotate_many(g.handle, evk.handle, P(ct), 1, g.L,
+                                                                        (ctypes.c_int32 * 2)(1, 2), 2, P(out), s),
+         fe.FE_EKEY),
     ]
     # every call that takes device buffers rejects a misaligned one before launching
     slots = torch.zeros((2, g.N // 2), dtype=torch.float64, device="cuda")
