@@ -22,11 +22,16 @@ namespace fe {
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 
+// A failed call is reported once: its error (if not sticky, e.g. a failed
+// allocation) is cleared so that a later call's cudaGetLastError() check does
+// not report it again.
 #define FE_CUDA_TRY(expr)                                                                  \
     do {                                                                                   \
         cudaError_t _e = (expr);                                                           \
-        if (_e != cudaSuccess)                                                             \
+        if (_e != cudaSuccess) {                                                           \
+            (void)cudaGetLastError();                                                      \
             return ::fe::fail(FE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+        }                                                                                  \
     } while (0)
 
 // device buffers must start on a 16-byte boundary (the kernels use 16-byte accesses)
