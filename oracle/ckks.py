@@ -475,8 +475,10 @@ def rescale(pr, ct):
     return Ciphertext(one(ct.c0), one(ct.c1), lv - 1, ct.scale / ql)
 
 
-def cmult_relin(pr, keys, x, y):
-    """Ciphertext product (d0, d1, d2) followed by relinearisation of d2."""
+def tensor(pr, x, y):
+    """Ciphertext product before relinearisation: (d0, d1, d2) = (x0 y0,
+    x0 y1 + x1 y0, x1 y1) per limb, with level and scale; decrypts under
+    (1, s, s^2) to the product of the messages."""
     assert x.level == y.level
     lv = x.level
     d0 = np.empty_like(x.c0)
@@ -487,10 +489,29 @@ def cmult_relin(pr, keys, x, y):
         d0[t] = C.vec_mul(x.c0[t], y.c0[t], q)
         d1[t] = C.vec_add(C.vec_mul(x.c0[t], y.c1[t], q), C.vec_mul(x.c1[t], y.c0[t], q), q)
         d2[t] = C.vec_mul(x.c1[t], y.c1[t], q)
+    return (d0, d1, d2, lv, x.scale * y.scale)
+
+
+def tensor_add(pr, a, b):
+    """Sum of two products of tensor() at one level and scale (per limb mod q)."""
+    assert a[3] == b[3] and a[4] == b[4]
+    lv = a[3]
+    parts = tuple(np.stack([C.vec_add(a[k][t], b[k][t], pr.moduli[t]) for t in range(lv + 1)]) for k in range(3))
+    return parts + (lv, a[4])
+
+
+def relinearize(pr, keys, d):
+    """(d0, d1, d2) -> (d0, d1) + KS_{s^2 -> s}(d2) with the relinearisation key."""
+    d0, d1, d2, lv, scale = d
     e0, e1 = key_switch_ext(pr, mod_up(pr, d2, lv), keys.relin, lv)
     c0 = np.stack([C.vec_add(d0[t], e0[t], pr.moduli[t]) for t in range(lv + 1)])
     c1 = np.stack([C.vec_add(d1[t], e1[t], pr.moduli[t]) for t in range(lv + 1)])
-    return Ciphertext(c0, c1, lv, x.scale * y.scale)
+    return Ciphertext(c0, c1, lv, scale)
+
+
+def cmult_relin(pr, keys, x, y):
+    """Ciphertext product (d0, d1, d2) followed by relinearisation of d2."""
+    return relinearize(pr, keys, tensor(pr, x, y))
 
 
 # ---------------------------------------------------------------------------

@@ -728,19 +728,21 @@ def he_attention_scores(pr, keys, q_cts, k_cts, tl, mask_scale=None):
     D_r[i] = A[i][(i + r) mod n] = sum_e Q[i][e] K[(i + r) mod n][e], r < n.
     For each r: K's fragment ciphertexts rotated token-wise by r (token_rotate,
     one level), each multiplied by Q's matching fragment (one level dropped to
-    meet them) with relinearisation, summed over the S fragments, rescaled, and
-    summed over the positions (position_sum), so D_r holds A[i][(i + r) mod n]
-    at slot f n + i of every position f.  Two levels; the output scale is
-    s_q s_k' / q_{l-1}, s_k' the rotated K's scale."""
+    meet them), the S products summed before relinearisation (one
+    relinearisation per diagonal), rescaled, and summed over the positions
+    (position_sum), so D_r holds A[i][(i + r) mod n] at slot f n + i of every
+    position f.  Two levels; the output scale is s_q s_k' / q_{l-1}, s_k' the
+    rotated K's scale."""
     level = q_cts[0].level
     ms = mask_scale_pow2(pr, level) if mask_scale is None else mask_scale
     qd = [drop_level(q) for q in q_cts]
     out = []
     for r in range(tl.n_tok):
         acc = None
-        for s, (q, k) in enumerate(zip(qd, k_cts)):
-            acc = _add(pr, acc, ckks.cmult_relin(pr, keys, q, token_rotate(pr, keys, k, tl, r, ms)))
-        d = ckks.rescale(pr, acc)
+        for q, k in zip(qd, k_cts):
+            t = ckks.tensor(pr, q, token_rotate(pr, keys, k, tl, r, ms))
+            acc = t if acc is None else ckks.tensor_add(pr, acc, t)
+        d = ckks.rescale(pr, ckks.relinearize(pr, keys, acc))
         out.append(position_sum(pr, keys, d, tl))
     return out
 
@@ -749,10 +751,10 @@ def he_attention_apply(pr, keys, d_cts, v_cts, tl, mask_scale=None):
     """O = A V from the n diagonals of A (as he_attention_scores leaves them,
     replicated over positions) and V in the fragmented layout tl:
     O[i][e] = sum_r D_r[i] V[(i + r) mod n][e].  For each fragment ciphertext of V
-    and each r: V rotated token-wise by r (one level), multiplied by D_r with
-    relinearisation after the higher of the two has limbs dropped to meet the
-    other; the sum over r is rescaled once.  Output in V's layout, one level
-    below the lower of V's rotated copies and D's."""
+    and each r: V rotated token-wise by r (one level), multiplied by D_r after
+    the higher of the two has limbs dropped to meet the other; the n products
+    are summed before one relinearisation, then rescaled once.  Output in V's
+    layout, one level below the lower of V's rotated copies and D's."""
     level = v_cts[0].level
     ms = mask_scale_pow2(pr, level) if mask_scale is None else mask_scale
     out = []
@@ -765,8 +767,9 @@ def he_attention_apply(pr, keys, d_cts, v_cts, tl, mask_scale=None):
                 dr = drop_level(dr)
             while vr.level > dr.level:
                 vr = drop_level(vr)
-            acc = _add(pr, acc, ckks.cmult_relin(pr, keys, dr, vr))
-        out.append(ckks.rescale(pr, acc))
+            t = ckks.tensor(pr, dr, vr)
+            acc = t if acc is None else ckks.tensor_add(pr, acc, t)
+        out.append(ckks.rescale(pr, ckks.relinearize(pr, keys, acc)))
     return out
 
 

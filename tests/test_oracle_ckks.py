@@ -160,6 +160,50 @@ def test_pmult_rescale_and_cmult(keyed):
     assert np.abs(ckks.decrypt(pr, keys.sk, sq) - z * z).max() < 1e-3
 
 
+def test_tensor_decrypts_to_the_negacyclic_product(keyed):
+    """The unrelinearised product: d0 + d1 s + d2 s^2 on q_0, back in the
+    coefficient domain, equals the schoolbook negacyclic product (Python
+    integers) of the two decrypted polynomials, exactly mod q_0."""
+    from oracle import _core as C
+    pr, keys = keyed
+    rng = np.random.default_rng(21)
+    x = ckks.encrypt(pr, keys.sk, ckks.encode(pr, rng.uniform(-1, 1, pr.N // 2), pr.L, 2.0 ** 12), 3, 0)
+    y = ckks.encrypt(pr, keys.sk, ckks.encode(pr, rng.uniform(-1, 1, pr.N // 2), pr.L, 2.0 ** 12), 3, 1)
+    d0, d1, d2, lv, scale = ckks.tensor(pr, x, y)
+    assert lv == pr.L and scale == 2.0 ** 24
+    q, N = pr.moduli[0], pr.N
+    sv = [int(v) for v in keys.sk.ntt[0]]
+    dec = np.array([(int(d0[0][i]) + int(d1[0][i]) * sv[i] + int(d2[0][i]) * sv[i] * sv[i]) % q for i in range(N)],
+                   dtype=np.uint64)
+    got = [int(v) for v in C.centre(pr.intt(dec, 0), q)]
+    mx = [int(v) for v in ckks.decrypt_coef(pr, keys.sk, x)]
+    my = [int(v) for v in ckks.decrypt_coef(pr, keys.sk, y)]
+    prod = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            if k < N:
+                prod[k] += mx[i] * my[j]
+            else:
+                prod[k - N] -= mx[i] * my[j]
+    want = [((v + q // 2) % q) - q // 2 for v in prod]
+    assert got == want
+
+
+def test_products_summed_before_one_relinearisation(keyed):
+    """Two products summed in tensor form and relinearised once decrypt to
+    z1 w1 + z2 w2, like the sum of two relinearised products."""
+    pr, keys = keyed
+    rng = np.random.default_rng(22)
+    z = rng.uniform(-1, 1, (4, pr.N // 2))
+    c = [ckks.encrypt(pr, keys.sk, ckks.encode(pr, z[i], pr.L, 2.0 ** 30), 4, i) for i in range(4)]
+    lazy = ckks.relinearize(pr, keys, ckks.tensor_add(pr, ckks.tensor(pr, c[0], c[1]), ckks.tensor(pr, c[2], c[3])))
+    eager = ckks.add(pr, ckks.cmult_relin(pr, keys, c[0], c[1]), ckks.cmult_relin(pr, keys, c[2], c[3]))
+    want = z[0] * z[1] + z[2] * z[3]
+    for ct in (lazy, eager):
+        assert np.abs(ckks.decrypt(pr, keys.sk, ckks.rescale(pr, ct)) - want).max() < 1e-3
+
+
 def test_double_hoisted_rotation_moddown_equals_rotation(keyed):
     """A rotation kept on Q P and brought down alone equals the rotation exactly;
     the lifted ciphertext comes back exactly; a double-hoisted sum decrypts to
