@@ -434,16 +434,18 @@ int fe_plan_token_linear(fe_ctx* ctx, const fe_token_layout* in_lay, uint32_t E_
  * the relinearisation key.
  * fe_he_attention_scores: Q and K ([S][2][level+1][N] each, scales q_scale,
  * k_scale) -> the n_tok diagonals D_r[i] = A[i][(i + r) mod n] of A = Q K^T
- * (out_dev: [n_tok][2][level-1][N] at level - 2): for each r, the sum over the
- * S fragments of relin(Q' (x) K_r) (Q' = Q with one limb dropped, K_r K rotated
- * token-wise by r), rescaled, then summed over the P positions (acc +=
+ * (out_dev: [n_tok][2][level-1][N] at level - 2): for each r, the S fragment
+ * products Q' (x) K_r (Q' = Q with one limb dropped, K_r K rotated token-wise
+ * by r) summed before one relinearisation, rescaled, then summed over the P
+ * positions (acc +=
  * Rot(acc, 2^k n)), so D_r holds A[i][(i + r) mod n] at slot f n + i of every
  * position f.  *out_scale = (q_scale ((k_scale ms) / q_l)) / q_{l-1}.
  * fe_he_attention_apply: D (n_tok ciphertexts at d_level, scale d_scale) and V
- * ([S] at v_level) -> O = A V in V's layout: for each fragment of V,
- * sum over r of relin(D_r (x) V_r), V_r V rotated token-wise by r, the higher
- * of the two with limbs dropped to meet the other (level m = min(v_level - 1,
- * d_level)), rescaled once: *out_level = m - 1, *out_scale = (d_scale
+ * ([S] at v_level) -> O = A V in V's layout: for each fragment of V, the n
+ * products D_r (x) V_r (V_r V rotated token-wise by r, the higher of the two
+ * with limbs dropped to meet the other, level m = min(v_level - 1, d_level))
+ * summed before one relinearisation, rescaled once: *out_level = m - 1,
+ * *out_scale = (d_scale
  * ((v_scale ms) / q_{v_level})) / q_m.  Softmax and other non-linear parts of
  * attention are not included.  Composed from the library's primitives with
  * stream-ordered scratch.  Each call encodes its 2 (n_tok - 1) masks once

@@ -98,6 +98,23 @@ int drop_limb(fe_ctx* c, const u64* x, int n, int level, u64* out, cudaStream_t 
     return FE_OK;
 }
 
+// out = a + b over rows of N residues, row r modulo q_(r mod nl) (products
+// (d0, d1, d2) of level nl - 1 laid out [..][3][nl][N], summed before one
+// relinearisation)
+__global__ void k_add_rows(const u64* a, const u64* b, u64* out, const Modulus* mods, int nl, int logN) {
+    const int N = 1 << logN;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const size_t o = (size_t)blockIdx.y * N + x;
+    out[o] = add_mod(a[o], b[o], mods[blockIdx.y % nl].q);
+}
+int add_rows(fe_ctx* c, const u64* a, const u64* b, u64* out, int rows, int nl, cudaStream_t st) {
+    k_add_rows<<<dim3((c->N + kB - 1) / kB, rows), kB, 0, st>>>(a, b, out, c->d_mod, nl, c->logN);
+    c->cnt.launches++;
+    FE_CUDA_TRY(cudaGetLastError());
+    return FE_OK;
+}
+
 // out = M_lo (x) a + M_hi (x) b per limb for n ciphertexts (both masks shared):
 // the two PMults and the addition of a token rotation in one pass
 __global__ void k_mask_pair(const u64* a, const u64* b, const u64* mlo, const u64* mhi, u64* out,
@@ -267,37 +284,43 @@ extern "C" int fe_he_attention_scores(fe_ctx* c, const fe_evk* evk, const fe_tok
     TokenMasks M(st);
     FE_TRY(make_token_masks(c, T, lv, ms, M, st));
     const int chunk = rotation_chunk(c, n, S, lv);
-    const size_t cm_bytes = cmult_relin_bytes(c, chunk * S, lv - 1);
-    const size_t cw = (size_t)chunk * S * ctw1;  // one chunk's ciphertexts at lv - 1
-    Dev wb(st), tb(st), cb(st), rb(st), hb(st);
-    u64* work = wb.get<u64>(3 * cw + (size_t)chunk * ctw1);  // Q copies, rotated K, products, sums
+    const size_t cw = (size_t)chunk * S * ctw1;             // one chunk's ciphertexts at lv - 1
+    const size_t tw = 3 * (size_t)lv * c->N;                 // one product (d0, d1, d2) at lv - 1
+    const size_t rl_bytes = relin_tensors_bytes(c, chunk, lv - 1);
+    Dev wb(st), tb(st), cb(st), rb(st), hb(st), pb(st);
+    u64* work = wb.get<u64>(2 * cw + (size_t)chunk * ctw1);  // Q copies, rotated K, relinearised sums
     u64* tmp = tb.get<u64>(S * ctw + 2 * c->N);              // token rotation scratch (r = 0)
-    char* cm = cb.get<char>(cm_bytes);                       // CMult scratch
+    char* rl = cb.get<char>(rl_bytes);                       // relinearisation scratch
     u64* rot = rb.get<u64>((size_t)n * ctw2);                // position-sum scratch
     u64* hoist = hb.get<u64>(2 * (size_t)chunk * S * ctw);   // hoisted rotations of K
-    if (!work || !tmp || !cm || !rot || !hoist) return fail(FE_ENOMEM, "attention scratch");
-    u64 *qrep = work, *kr = work + cw, *prod = work + 2 * cw, *sums = work + 3 * cw;
+    u64* prods = pb.get<u64>(((size_t)chunk * S + chunk) * tw);  // products, their sums per r
+    if (!work || !tmp || !rl || !rot || !hoist || !prods) return fail(FE_ENOMEM, "attention scratch");
+    u64 *qrep = work, *kr = work + cw, *rel = work + 2 * cw;
+    u64 *t3 = prods, *sum3 = prods + (size_t)chunk * S * tw;
     // Q with one limb dropped, once per r of a chunk
     FE_TRY(drop_limb(c, (const u64*)q_dev, S, lv, qrep, st));
     for (int i = 1; i < chunk; i++)
         FE_CUDA_TRY(cudaMemcpyAsync(qrep + (size_t)i * S * ctw1, qrep, (size_t)S * ctw1 * 8, cudaMemcpyDeviceToDevice,
                                     st));
-    // diagonal r: sum over s of Q_s times K_s rotated by r tokens, rescaled; the
-    // CMults of a chunk of r values at once; then every diagonal's position sums
+    // diagonal r: the S products Q_s (x) K_s rotated by r tokens, summed, one
+    // relinearisation, rescaled (a chunk of r values at once); then every
+    // diagonal's position sums
     auto diagonals = [&](int r0, int rn, const u64* krr) -> int {
-        Carver cv(cm, cm_bytes);
-        FE_TRY(cmult_relin(c, evk, qrep, krr, rn * S, lv - 1, prod, cv, st));
-        const u64* sum = prod;
+        launch_tensor(c, qrep, krr, t3, rn * S, lv - 1, st);
+        const u64* sums = t3;
         if (S > 1) {
             for (int i = 0; i < rn; i++) {
-                const u64* p = prod + (size_t)i * S * ctw1;
-                u64* a = sums + (size_t)i * ctw1;
-                FE_TRY(fe_add(c, p, p + ctw1, 1, lv - 1, a, st));
-                for (int q = 2; q < S; q++) FE_TRY(fe_add(c, a, p + q * ctw1, 1, lv - 1, a, st));
+                const u64* p = t3 + (size_t)i * S * tw;
+                u64* a = sum3 + (size_t)i * tw;
+                FE_TRY(add_rows(c, p, p + tw, a, 3 * lv, lv, st));
+                for (int q = 2; q < S; q++) FE_TRY(add_rows(c, a, p + q * tw, a, 3 * lv, lv, st));
             }
-            sum = sums;
+            sums = sum3;
         }
-        return fe_rescale(c, sum, (uint32_t)rn, lv - 1, (u64*)out_dev + (size_t)r0 * ctw2, st);
+        Carver cv(rl, rl_bytes);
+        FE_TRY(relin_tensors(c, evk, sums, rn, lv - 1, rel, cv, st));
+        c->cnt.cmult += rn * S;
+        return fe_rescale(c, rel, (uint32_t)rn, lv - 1, (u64*)out_dev + (size_t)r0 * ctw2, st);
     };
     FE_TRY(token_rotations(c, evk, T, (const u64*)k_dev, S, lv, ms, M, chunk, hoist, tmp, kr, diagonals, st));
     FE_TRY(position_sum(c, evk, T, (u64*)out_dev, n, lv - 2, rot, st));
@@ -332,19 +355,22 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
     FE_TRY(make_token_masks(c, T, vl, ms, M, st));
     const size_t wide = std::max(ctwv1, ctwd);
     const int chunk = rotation_chunk(c, n, S, vl);
-    const size_t cm_bytes = cmult_relin_bytes(c, chunk * S, ml);
-    const size_t cs = (size_t)chunk * S;  // ciphertexts of one chunk
-    Dev wb(st), tb(st), db(st), cb(st), hb(st);
-    u64* work = wb.get<u64>(cs * ctwv1 + cs * ctwm + S * ctwm);  // rotated V, products, sums
+    const size_t cs = (size_t)chunk * S;      // ciphertexts of one chunk
+    const size_t tw = 3 * (size_t)(ml + 1) * c->N;  // one product (d0, d1, d2) at ml
+    const size_t rl_bytes = relin_tensors_bytes(c, S, ml);
+    Dev wb(st), tb(st), db(st), cb(st), hb(st), pb(st);
+    u64* work = wb.get<u64>(cs * ctwv1 + S * ctwm);               // rotated V, relinearised sums
     u64* tmp = tb.get<u64>(S * ctwv + 2 * c->N);                  // token rotation scratch (r = 0)
     u64* drop = db.get<u64>(2 * cs * wide + cs * ctwm);           // level drops, D_r for every s
-    char* cm = cb.get<char>(cm_bytes);
+    char* rl = cb.get<char>(rl_bytes);                            // relinearisation scratch
     u64* hoist = hb.get<u64>(2 * cs * ctwv);                      // hoisted rotations of V
-    if (!work || !tmp || !drop || !cm || !hoist) return fail(FE_ENOMEM, "attention scratch");
-    u64 *vr = work, *prod = work + cs * ctwv1, *acc = prod + cs * ctwm;
+    u64* prods = pb.get<u64>((cs + S) * tw);                      // products, their sums per s
+    if (!work || !tmp || !drop || !rl || !hoist || !prods) return fail(FE_ENOMEM, "attention scratch");
+    u64 *vr = work, *rel = work + cs * ctwv1;
     u64 *bx = drop, *by = drop + cs * wide, *drep = drop + 2 * cs * wide;
-    // output s: sum over r of D_r times V_s rotated by r tokens, every s and a
-    // chunk of r values at once
+    u64 *t3 = prods, *acc3 = prods + cs * tw;
+    // output s: the n products D_r (x) V_s rotated by r tokens summed over r
+    // (a chunk of r values at once), one relinearisation, rescaled once
     auto terms = [&](int r0, int rn, const u64* vrr) -> int {
         // D_r dropped to the products' level (one limb at a time), one copy per s
         for (int i = 0; i < rn; i++) {
@@ -365,19 +391,23 @@ extern "C" int fe_he_attention_apply(fe_ctx* c, const fe_evk* evk, const fe_toke
             FE_TRY(drop_limb(c, y, rn * S, l, dst, st));
             y = dst;
         }
-        Carver cv(cm, cm_bytes);
-        FE_TRY(cmult_relin(c, evk, drep, y, rn * S, ml, prod, cv, st));
+        launch_tensor(c, drep, y, t3, rn * S, ml, st);
         for (int i = 0; i < rn; i++) {
-            const u64* p = prod + (size_t)i * S * ctwm;
+            const u64* p = t3 + (size_t)i * S * tw;
             if (r0 + i == 0)
-                FE_CUDA_TRY(cudaMemcpyAsync(acc, p, (size_t)S * ctwm * 8, cudaMemcpyDeviceToDevice, st));
+                FE_CUDA_TRY(cudaMemcpyAsync(acc3, p, (size_t)S * tw * 8, cudaMemcpyDeviceToDevice, st));
             else
-                FE_TRY(fe_add(c, acc, p, S, ml, acc, st));
+                FE_TRY(add_rows(c, acc3, p, acc3, (int)(3 * S * (ml + 1)), ml + 1, st));
         }
         return FE_OK;
     };
     FE_TRY(token_rotations(c, evk, T, (const u64*)v_dev, S, vl, ms, M, chunk, hoist, tmp, vr, terms, st));
-    FE_TRY(fe_rescale(c, acc, S, ml, (u64*)out_dev, st));
+    {
+        Carver cv(rl, rl_bytes);
+        FE_TRY(relin_tensors(c, evk, acc3, S, ml, rel, cv, st));
+        c->cnt.cmult += n * S;
+    }
+    FE_TRY(fe_rescale(c, rel, S, ml, (u64*)out_dev, st));
     const double vr_scale = (v_scale * ms) / (double)c->mod[vl];
     if (out_level) *out_level = (uint32_t)(ml - 1);
     if (out_scale) *out_scale = (d_scale * vr_scale) / (double)c->mod[ml];

@@ -101,14 +101,13 @@ int launch_affine(fe_ctx* c, const u64* in, u64* out, int n, int level, const Af
     return FE_OK;
 }
 
-// d = relin(x (x) y) on Q_level for n pairs of ciphertexts, no rescale (CMult + relinearisation)
-int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,
-                cudaStream_t st) {
+// d = relin of n products (d0, d1, d2) [n][3][nl][N] on Q_level: (d0, d1) + KS(d2)
+int relin_tensors(fe_ctx* c, const fe_evk* evk, const u64* d012, int n, int level, u64* d, Carver& cv,
+                  cudaStream_t st) {
     const int N = c->N, nl = level + 1;
     KsScratch s;
     carve_ks(cv, c, n, level, &s);
     CombineItem* dcb = cv.take<CombineItem>(n);
-    u64* d012 = cv.take<u64>((size_t)n * 3 * nl * N);
     if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
     std::vector<KsItem> ks(n);
     std::vector<CombineItem> cb(n);
@@ -122,13 +121,26 @@ int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n,
     FE_TRY(upload(ks, s.ks, st));
     FE_TRY(upload(kg, s.kg, st));
     FE_TRY(upload(cb, dcb, st));
-    launch_tensor(c, x, y, d012, n, level, st);
     modup(c, d012 + 2 * (size_t)nl * N, 3 * (size_t)nl * N, n, level, s.coef, s.ext, st);
     launch_keyip_grouped(c, s.kg, s.ks, 1, n, level, st);
     moddown_prepare(c, s.acc, n, level, s.conv, st);
     launch_combine(c, dcb, n, level, st);
-    c->cnt.cmult += n;
     c->cnt.keyswitch += n;
+    return FE_OK;
+}
+
+size_t relin_tensors_bytes(const fe_ctx* c, int n, int level) {
+    return ks_scratch_bytes(c, n, level) + (size_t)n * sizeof(CombineItem) + 2 * 256;
+}
+
+// d = relin(x (x) y) on Q_level for n pairs of ciphertexts, no rescale (CMult + relinearisation)
+int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,
+                cudaStream_t st) {
+    u64* d012 = cv.take<u64>((size_t)n * 3 * (level + 1) * c->N);
+    if (!cv.ok) return fail(FE_ENOMEM, "workspace too small");
+    launch_tensor(c, x, y, d012, n, level, st);
+    FE_TRY(relin_tensors(c, evk, d012, n, level, d, cv, st));
+    c->cnt.cmult += n;
     return FE_OK;
 }
 

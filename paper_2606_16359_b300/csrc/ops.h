@@ -53,6 +53,12 @@ const u64* evk_key(const fe_evk* evk, uint32_t galois);
 int cmult_relin(fe_ctx* c, const fe_evk* evk, const u64* x, const u64* y, int n, int level, u64* d, Carver& cv,
                 cudaStream_t st);
 size_t cmult_relin_bytes(const fe_ctx* c, int n, int level);
+// d = relin of n ciphertext products (d0, d1, d2) [n][3][level+1][N] (as
+// launch_tensor leaves them, or sums of them): (d0, d1) + KS(d2); scratch
+// carved from cv (relin_tensors_bytes)
+int relin_tensors(fe_ctx* c, const fe_evk* evk, const u64* d012, int n, int level, u64* d, Carver& cv,
+                  cudaStream_t st);
+size_t relin_tensors_bytes(const fe_ctx* c, int n, int level);
 
 // Per-limb constants of an affine map of ciphertexts (polynomial activation,
 // integer products and constants of the bootstrapping's EvalMod).
