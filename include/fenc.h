@@ -290,8 +290,9 @@ int fe_ntt(fe_ctx* ctx, void* data_dev, uint32_t n_poly, uint32_t n_limbs, uint3
  * times the launch on `stream`.  Errors: FE_EINVAL, FE_ECUDA. */
 int fe_probe_butterflies(fe_ctx* ctx, uint32_t blocks, uint32_t iters, void* out_dev,
                          uint64_t* butterflies, void* stream);
-/* Left rotation of n_ct ciphertexts by r slots (Eq. 1): out = sigma_g((c0,0) + KS(c1)).
- * Errors: FE_EKEY when the key for r is missing. */
+/* Left rotation of n_ct ciphertexts by r slots (Eq. 1): out = sigma_g((c0,0) + KS(c1)),
+ * the key read once for all n_ct.  Errors: FE_EKEY when the key for r is missing,
+ * FE_EINVAL (null pointer, out overlapping the input). */
 int fe_rotate(fe_ctx* ctx, const fe_evk* evk, const void* ct_dev, uint32_t n_ct, uint32_t level,
               int32_t r, void* out_dev, void* stream);
 /* Hoisted rotations (Eq. 1 for several steps of one input): n_ct ciphertexts

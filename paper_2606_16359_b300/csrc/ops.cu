@@ -608,49 +608,14 @@ extern "C" int fe_rotate(fe_ctx* c, const fe_evk* evk, const void* ct_dev, uint3
     if (!c || !evk || !ct_dev || !out_dev) return fail(FE_EINVAL, "null argument");
     if ((int)level > c->L) return fail(FE_ELEVEL, "level above L");
     if (n_ct == 0) return FE_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int N = c->N;
-    const u64* in = (const u64*)ct_dev;
-    u64* out = (u64*)out_dev;
-    if (r != FE_STEP_CONJ && r % (N / 2) == 0) {
-        FE_CUDA_TRY(cudaMemcpyAsync(out, in, n_ct * ct_words(c, level) * 8, cudaMemcpyDeviceToDevice, st));
-        return FE_OK;
-    }
-    uint32_t g = c->galois(r);
-    const u64* key = evk_key(evk, g);
-    if (!key) return fail(FE_EKEY, "missing rotation key for step " + std::to_string(r));
-    const int nl = level + 1;
-    u64 *coef, *ext, *acc, *conv;
-    void* items;
-    FE_CUDA_TRY(cudaMallocAsync(&coef, (size_t)n_ct * nl * N * 8, st));
-    FE_CUDA_TRY(cudaMallocAsync(&ext, n_ct * ext_words(c, level) * 8, st));
-    FE_CUDA_TRY(cudaMallocAsync(&acc, n_ct * acc_words(c, level) * 8, st));
-    FE_CUDA_TRY(cudaMallocAsync(&conv, n_ct * ct_words(c, level) * 8, st));
-    FE_CUDA_TRY(cudaMallocAsync(&items, n_ct * (sizeof(KsItem) + sizeof(CombineItem)), st));
-    std::vector<KsItem> ks(n_ct);
-    std::vector<CombineItem> cb(n_ct);
-    for (uint32_t i = 0; i < n_ct; i++) {
-        ks[i] = KsItem{ext + i * ext_words(c, level), key, acc + i * acc_words(c, level)};
-        cb[i] = CombineItem{acc + i * acc_words(c, level), conv + i * ct_words(c, level),
-                            in + i * ct_words(c, level), nullptr, out + i * ct_words(c, level), g, 0};
-    }
-    KsItem* dks = (KsItem*)items;
-    CombineItem* dcb = (CombineItem*)(dks + n_ct);
-    FE_TRY(upload(ks, dks, st));
-    FE_TRY(upload(cb, dcb, st));
-    modup(c, in + (size_t)nl * N, ct_words(c, level), n_ct, level, coef, ext, st);
-    launch_keyip(c, dks, n_ct, level, st);
-    moddown_prepare(c, acc, n_ct, level, conv, st);
-    launch_combine(c, dcb, n_ct, level, st);
-    c->cnt.rot += n_ct;
-    c->cnt.keyswitch += n_ct;
-    cudaFreeAsync(coef, st);
-    cudaFreeAsync(ext, st);
-    cudaFreeAsync(acc, st);
-    cudaFreeAsync(conv, st);
-    cudaFreeAsync(items, st);
-    FE_CUDA_TRY(cudaGetLastError());
-    return FE_OK;
+    if (n_ct > (1u << 20)) return fail(FE_EINVAL, "n_ct must be below 2^20");
+    const size_t bytes = (size_t)n_ct * ct_words(c, (int)level) * 8;
+    const char *i0 = (const char*)ct_dev, *o0 = (const char*)out_dev;
+    if (o0 < i0 + bytes && i0 < o0 + bytes) return fail(FE_EINVAL, "a rotation cannot run in place");
+    // one step of the hoisted form: ModUp, the key inner product with the key
+    // read once for all n_ct ciphertexts, ModDown, automorphism
+    return rotate_many(c, evk, (const u64*)ct_dev, (int)n_ct, (int)level, &r, 1, (u64*)out_dev,
+                       (cudaStream_t)stream);
 }
 
 extern "C" int fe_rescale(fe_ctx* c, const void* ct_dev, uint32_t n_ct, uint32_t level, void* out_dev,
